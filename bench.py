@@ -1,0 +1,357 @@
+#!/usr/bin/env python3
+"""Benchmark: loopy belief propagation edge-state message updates per second.
+
+Workload (default): the 2D Ising grid 1000x1000 (1,998,000 pairwise factors,
+7,992,000 edge-states), couplings J~U[-1,1] as [J,-J,-J,J], fields h~N(0,1), damping
+0.5, 200 flooding iterations, FP32 messages. One step = one cold-start run at T=1
+(sum-product) and one at T=0 (max-product), each followed by normalised beliefs and
+the MAP decode. One update = one new factor-to-variable value for one edge-state in
+one iteration, so a step is 2 x 200 x 7,992,000 updates.
+
+Prints one JSON line. Under torchrun (N > 1) every rank runs its own replica (seed =
+rank): the graph does not shard, so there is no collective on the data path; the
+barrier and the max over ranks of the timed duration are the only communication.
+
+--impl reference times the FP64 oracle (the plain CPU restatement of the method) on
+the host cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "LBP edge-state msg updates/s (batched vs per-graph) at 1e-4; p50/p99 serve latency"
+UNIT = "edge-state updates/s"
+FALLBACK_HBM_GBS = 6800.0
+L2_FLUSH_BYTES = 512 << 20
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--side", type=int, default=1000)
+    ap.add_argument("--iters", type=int, default=200)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-iters", type=int, default=40, help="oracle iterations per T in the CPU baseline sample")
+    ap.add_argument("--ref-iters", type=int, default=16, help="oracle iterations per T in one reference step")
+    return ap.parse_args()
+
+
+def workload_config(args, n_gpus):
+    return {
+        "workload": f"ising{args.side}x{args.side}",
+        "description": f"2D Ising {args.side}x{args.side} binary, 4-neighbour pairwise enumeration factors, "
+                       f"J~U[-1,1] as [J,-J,-J,J], h~N(0,1) as [-h,h], damping 0.5, {args.iters} iterations, "
+                       "one T=1 (sum-product) and one T=0 (max-product) cold-start run per step",
+        "iterations": args.iters,
+        "temperatures": [1.0, 0.0],
+        "damping": 0.5,
+        "messages": "fp32",
+        "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MiB write)",
+        "parallelism": f"replicas x{n_gpus}" if n_gpus > 1 else "single GPU",
+    }
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        for k in ("hbm_gbs", "hbm_GBs", "hbm"):
+            if k in d:
+                return float(d[k]), "measured"
+    except (OSError, ValueError):
+        pass
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_source_hash() -> str:
+    with open(os.path.join(ROOT, "paper_2202_04110_gb300", "csrc", "kernels.cu"), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def profiled_traffic(kernel: str, workload: str):
+    """dram bytes per launch recorded from an ncu capture in profiles/, if the kernel
+    source has not changed since."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}_{workload}.md")
+    try:
+        txt = open(path).read()
+    except OSError:
+        return None
+    m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", txt)
+    h = re.search(r"kernels_cu_sha256_16:\s*([0-9a-f]+)", txt)
+    if not m or not h or h.group(1) != kernel_source_hash():
+        return None
+    return float(m.group(1))
+
+
+class ClockSampler:
+    """nvidia-smi samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def cpu_sample(problem, iters: int):
+    """Time the FP64 oracle on the host cores: `iters` iterations at T=1 and at T=0."""
+    import oracle
+    oracle.build()
+    t0 = time.perf_counter()
+    for T in (1.0, 0.0):
+        oracle.run_bp(problem.graph, problem.log_pot, problem.evidence, T, problem.damping, iters)
+    dt = time.perf_counter() - t0
+    updates = 2 * iters * problem.graph.n_edge_states
+    return updates / dt, dt, oracle.num_threads()
+
+
+def run_reference(args):
+    world, rank, _ = dist_setup()
+    if rank != 0:
+        return
+    from paper_2202_04110_gb300 import workloads as W
+    p = W.ising_large(0, T=1.0, side=args.side, n_iters=args.iters)
+    vals = []
+    for _ in range(args.warmup):
+        cpu_sample(p, args.ref_iters)
+    total_updates, total_s, cores = 0, 0.0, 1
+    for _ in range(args.steps):
+        v, dt, cores = cpu_sample(p, args.ref_iters)
+        vals.append(v)
+        total_updates += 2 * args.ref_iters * p.graph.n_edge_states
+        total_s += dt
+    value = total_updates / total_s
+    sample = (f"{args.ref_iters} iterations at T=1 and {args.ref_iters} at T=0 per step on the full "
+              f"{args.side}x{args.side} grid (FP64 oracle, OpenMP)")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload_config(args, world),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    world, rank, local = dist_setup()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        dist = None
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+
+    from paper_2202_04110_gb300 import binding, build
+    from paper_2202_04110_gb300 import workloads as W
+    build.build()
+    p = W.ising_large(seed=rank, T=1.0, side=args.side, n_iters=args.iters)
+    g = binding.Graph(p.graph)
+    I = g.info
+    lp = torch.as_tensor(p.log_pot).to(dev)
+    ev = torch.as_tensor(p.evidence).to(dev)
+    msgs = g.new_msgs()
+    bel = torch.empty(I["n_var_states"], dtype=torch.float32, device=dev)
+    dec = torch.empty(I["n_vars"], dtype=torch.int32, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    temps = (1.0, 0.0)
+
+    def step():
+        for T in temps:
+            msgs.zero_()
+            g.run_bp(lp, ev, T, 0.5, args.iters, msgs)
+            g.beliefs(ev, msgs, True, out=bel)
+            g.decode(ev, msgs, out=dec)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    ES = I["n_edge_states"]
+    updates_per_step = len(temps) * args.iters * ES
+    launches_per_step = len(temps) * (args.iters * I["launches_per_iter"] + 2)
+
+    sampler = ClockSampler(torch.cuda.current_device())
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    g.set_profiling(True)
+    g.pass_times()  # reset
+    step_ms = []
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        step_ms.append((e0, e1))
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    clocks = sampler.stop()
+    var_ms, fac_ms, n_var, n_fac = g.pass_times()
+    g.set_profiling(False)
+    ms = [a.elapsed_time(b) for a, b in step_ms]
+    total_ms = float(sum(ms))
+    if dist is not None:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * updates_per_step * args.steps / (total_ms / 1e3)
+    flags = g.flags(clear=True)
+
+    # roofline of the dominant kernel: algorithmic bytes per launch / mean launch time
+    V, VS, E = I["n_vars"], I["n_var_states"], I["n_edges"]
+    n_cfg_total = 4 * I["n_factors"]
+    fac_bytes = 4 * (2 * ES + n_cfg_total + E + VS)  # m_old + m_new + log-potentials + edge index + beliefs
+    var_bytes = 4 * (ES + 2 * VS + E + V + 1)       # messages + evidence + beliefs + CSR
+    fac_avg_s = fac_ms / 1e3 / max(n_fac, 1)
+    var_avg_s = var_ms / 1e3 / max(n_var, 1)
+    peak, peak_src = measured_peaks()
+    wl = f"ising{args.side}x{args.side}"
+    fac_gbs = fac_bytes / fac_avg_s / 1e9
+    var_gbs = var_bytes / var_avg_s / 1e9
+    iter_bytes = 8 * ES + 4 * n_cfg_total + 4 * VS + 4 * E
+    iter_s = (var_ms + fac_ms) / 1e3 / max(n_fac, 1)
+    dominant = "k_pair2" if fac_ms >= var_ms else "k_var_thread2"
+    roof = {"bound": "hbm", "kernel": dominant,
+            "achieved": round(fac_gbs if dominant == "k_pair2" else var_gbs, 1),
+            "peak": peak, "unit": "GB/s", "peak_source": f"{peak_src} HBM copy bandwidth",
+            "frac": round((fac_gbs if dominant == "k_pair2" else var_gbs) / peak, 4),
+            "traffic": profiled_traffic(dominant, wl),
+            "algorithmic_bytes_per_launch": fac_bytes if dominant == "k_pair2" else var_bytes,
+            "mean_launch_us": round(1e6 * (fac_avg_s if dominant == "k_pair2" else var_avg_s), 2),
+            "other_kernels": {
+                "k_var_thread2": {"achieved": round(var_gbs, 1), "frac": round(var_gbs / peak, 4),
+                                  "algorithmic_bytes_per_launch": var_bytes,
+                                  "mean_launch_us": round(1e6 * var_avg_s, 2)}},
+            "iteration": {"algorithmic_bytes": iter_bytes, "mean_us": round(1e6 * iter_s, 2),
+                          "achieved": round(iter_bytes / iter_s / 1e9, 1),
+                          "frac": round(iter_bytes / iter_s / 1e9 / peak, 4)}}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": workload_config(args, world), "roofline": roof, "clocks": clocks,
+            "gpu_launches": launches_per_step * args.steps, "device_flags": flags,
+            "step_ms": [round(x, 3) for x in ms]}
+
+    # end to end through the host-buffer C-ABI call (copies inside the timed region)
+    if not args.no_e2e:
+        lp_h = torch.empty(p.log_pot.size, dtype=torch.float32, pin_memory=True).numpy()
+        ev_h = torch.empty(p.evidence.size, dtype=torch.float32, pin_memory=True).numpy()
+        lp_h[:] = p.log_pot
+        ev_h[:] = p.evidence
+        bel_h = torch.empty(VS, dtype=torch.float32, pin_memory=True).numpy()
+        dec_h = torch.empty(V, dtype=torch.int32, pin_memory=True).numpy()
+
+        def e2e_step():
+            for T in temps:
+                g.infer_host(lp_h, ev_h, T, 0.5, args.iters, bel_h, dec_h)
+
+        for _ in range(max(1, args.warmup)):
+            e2e_step()
+        if dist is not None:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            e2e_step()
+        dt = time.perf_counter() - t0
+        if dist is not None:
+            t = torch.tensor([dt], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            dt = float(t.item())
+        line["e2e"] = {"value": world * updates_per_step * args.steps / dt, "unit": UNIT,
+                       "h2d_bytes_per_step": len(temps) * 4 * (p.log_pot.size + p.evidence.size),
+                       "d2h_bytes_per_step": len(temps) * 4 * (VS + V),
+                       "call": "pgm_infer_host (pinned host buffers, blocking)"}
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, dt, cores = cpu_sample(p, args.cpu_iters)
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                "sample": f"{args.cpu_iters} iterations at T=1 and {args.cpu_iters} at T=0 on the "
+                                          f"full {args.side}x{args.side} grid, FP64, {dt:.1f} s"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

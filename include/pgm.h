@@ -1,0 +1,219 @@
+/*
+ * pgm.h -- C ABI of the GB300 loopy belief propagation engine.
+ *
+ * The engine runs log-space loopy belief propagation (LBP) over a flat factor graph,
+ * the method of PGMax (arXiv 2202.04110): discrete variables with varying numbers of
+ * states and factor graphs of arbitrary topology (Sec. 3, "Easy specification of
+ * general factor graphs"), enumeration factors listed by their valid configurations
+ * (Sec. 4.2), logical factors with message updates linear in the fan-in (Sec. 3),
+ * parallel message updates with damping (Sec. 3, after Pretti 2005), all messages kept
+ * in flat arrays updated by gather/scatter (Sec. 4 "A fully flat array-based LBP
+ * implementation"), LBP as a pure function of explicit message state (Sec. 3,
+ * Sec. 4.3), MAP decoding (Sec. 4.1).
+ *
+ * Conventions for every call:
+ *  - Return value: PGM_OK (0) or a negative pgm_status. pgm_last_error() returns a
+ *    thread-local message describing the last failure of the calling thread.
+ *  - "host" pointers are read during the call only; the caller keeps ownership.
+ *  - "device" pointers are CUDA global-memory pointers on the device the graph was
+ *    built on, owned by the caller, and must stay valid until the work queued on
+ *    `stream` has finished. All device work is asynchronous on `stream` (a
+ *    cudaStream_t passed as void*; NULL is the legacy default stream).
+ *  - Flat layouts:
+ *      evidence / beliefs [n_var_states]: variable-major, K_v log-space values for
+ *        variable v, in variable order.
+ *      log_pot [n_potentials]: enumeration groups in order; a group with
+ *        shared_potentials = 0 holds n_fac * n_cfg values (factor-major), a group with
+ *        shared_potentials = 1 holds one table of n_cfg values used by all its factors.
+ *      msgs [n_edge_states]: the factor-to-variable messages. Edges are enumerated
+ *        group by group, enumeration groups first and logical groups after, factor by
+ *        factor; an enumeration factor contributes its neighbours in order, a logical
+ *        factor its parents in order and then its child. Each edge holds K_v
+ *        log-space values of its variable.
+ *  - Graph handles are not thread-safe: calls on one pgm_graph from several host
+ *    threads must be serialised by the caller, and work on one graph queued on
+ *    different streams must not overlap (the graph owns one scratch area).
+ */
+#ifndef PGM_H
+#define PGM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t pgm_status;
+
+#define PGM_OK 0
+#define PGM_EINVAL (-1)    /* invalid argument or malformed graph */
+#define PGM_ENOMEM (-2)    /* device or host allocation failed */
+#define PGM_ECUDA (-3)     /* a CUDA runtime call failed */
+#define PGM_ENOTSUP (-4)   /* valid but unsupported request */
+#define PGM_EBUSY (-5)     /* not admitted now (serving) */
+#define PGM_ETIMEDOUT (-6) /* a bounded wait ran out */
+
+#define PGM_LOGIC_OR 0  /* child = OR(parents)  */
+#define PGM_LOGIC_AND 1 /* child = AND(parents) */
+
+/* Bits of the device status word (pgm_device_flags). */
+#define PGM_FLAG_CONTRADICTION 1u /* a message or belief had every state at -inf */
+#define PGM_FLAG_NAN 2u           /* a NaN reached a belief */
+
+/* Limits of this build (checked by pgm_build). */
+#define PGM_MAX_STATES 256        /* states per variable */
+#define PGM_MAX_ENUM_ARITY 8      /* neighbours of an enumeration factor */
+#define PGM_MAX_ENUM_STATE_SUM 64 /* sum of K over one enumeration factor's neighbours */
+
+typedef struct pgm_graph pgm_graph;
+
+/*
+ * Enumeration factors (Sec. 4.2: "explicitly enumerating the valid configurations").
+ * All factors of a group share arity, configuration list and the state counts of their
+ * j-th neighbours. Configurations that are not listed have log-potential -inf.
+ */
+typedef struct {
+    int32_t arity;             /* neighbours per factor, 1..PGM_MAX_ENUM_ARITY */
+    int32_t n_cfg;             /* listed configurations, >= 1 */
+    const int32_t *cfg;        /* host [n_cfg * arity]: state of neighbour j in config c */
+    int32_t n_fac;             /* factors in the group, >= 0 */
+    const int32_t *vars;       /* host [n_fac * arity]: neighbour j of factor f */
+    int32_t shared_potentials; /* 0: n_fac * n_cfg log-potentials; 1: one n_cfg table */
+} pgm_enum_group;
+
+/*
+ * Logical factors (Sec. 3: "logical factors with linear message updates"): child =
+ * OP(parents) over binary variables, log-potential 0 on valid configurations and -inf
+ * otherwise. A factor may have zero parents (OR of nothing is 0, AND of nothing is 1).
+ */
+typedef struct {
+    int32_t kind;            /* PGM_LOGIC_OR or PGM_LOGIC_AND */
+    int32_t n_fac;           /* factors in the group */
+    const int32_t *par_off;  /* host [n_fac + 1], par_off[0] = 0, non-decreasing */
+    const int32_t *parents;  /* host [par_off[n_fac]] */
+    const int32_t *child;    /* host [n_fac] */
+} pgm_logic_group;
+
+typedef struct {
+    int32_t n_vars;            /* >= 1 */
+    const int32_t *num_states; /* host [n_vars], each in 1..PGM_MAX_STATES */
+    int32_t n_enum_groups;
+    const pgm_enum_group *enum_groups;
+    int32_t n_logic_groups;
+    const pgm_logic_group *logic_groups;
+} pgm_graph_desc;
+
+typedef struct {
+    int64_t n_vars;
+    int64_t n_var_states;  /* length of evidence / beliefs */
+    int64_t n_factors;
+    int64_t n_edges;
+    int64_t n_edge_states; /* length of msgs */
+    int64_t n_potentials;  /* length of log_pot */
+    int32_t max_states;
+    int32_t max_degree;    /* largest number of factors on one variable */
+    int64_t device_bytes;  /* device memory held by the graph (indices + scratch) */
+    int32_t launches_per_iter; /* kernel launches of one pgm_run_bp iteration */
+    int32_t reserved;
+} pgm_info;
+
+/*
+ * Compile a factor graph (Sec. 4: flatten messages into 1-D arrays and keep the
+ * global indices of variable states and factor configurations). Validates the
+ * description, builds the flat index arrays on the host, copies them once to the
+ * current CUDA device, and allocates the graph's scratch (one message buffer and one
+ * belief buffer). Blocking. On success *out owns all of it until pgm_free.
+ * Errors: PGM_EINVAL (state index >= K, variable out of range, non-binary variable in
+ * a logical factor, a group whose j-th neighbours differ in state count, sizes beyond
+ * int32 or the limits above), PGM_ENOMEM, PGM_ECUDA.
+ */
+pgm_status pgm_build(const pgm_graph_desc *desc, pgm_graph **out);
+
+/*
+ * Host-only: validate a description and report the sizes its compiled graph will have
+ * (device_bytes = index arrays + scratch), without touching any GPU. Same errors as
+ * pgm_build's validation.
+ */
+pgm_status pgm_check_desc(const pgm_graph_desc *desc, pgm_info *info);
+
+/* Release a graph and its device memory (synchronises its device). NULL is a no-op. */
+void pgm_free(pgm_graph *g);
+
+/* Sizes of a compiled graph. */
+pgm_status pgm_graph_info(const pgm_graph *g, pgm_info *info);
+
+/*
+ * n_iters flooding LBP iterations (Sec. 3: parallel updates with damping).
+ * Each iteration, from the current messages m:
+ *   b_v = e_v + sum_f m_{f->v};  m_{v->f} = b_v - m_{f->v}          (variable side)
+ *   mt_{f->i}(x) = LSE_T{ phi_f(c) + sum_{j != i} m_{j->f}(c_j) : c_i = x }
+ *                                           (enumeration; closed forms for OR / AND)
+ *   m_{f->i} <- norm( delta * m_{f->i} + (1 - delta) * norm(mt_{f->i}) )
+ * where LSE_T(z) = T log sum exp(z / T) (T = 1 sum-product, T = 0 max-product) and
+ * norm subtracts the maximum over the edge's states (an all -inf message becomes 0
+ * and raises PGM_FLAG_CONTRADICTION).
+ *   log_pot  device [n_potentials] (may be NULL when n_potentials = 0)
+ *   evidence device [n_var_states]
+ *   msgs     device [n_edge_states], in/out: zeros for a cold start, the previous
+ *            result for a warm start (messages are explicit state, Sec. 3).
+ * Errors: PGM_EINVAL (T < 0 or not finite, damping outside [0, 1), n_iters < 0, NULL
+ * pointers), PGM_ECUDA.
+ */
+pgm_status pgm_run_bp(pgm_graph *g, const float *log_pot, const float *evidence, float T,
+                      float damping, int32_t n_iters, float *msgs, void *stream);
+
+/*
+ * Beliefs b_v = e_v + sum_f m_{f->v} (device out [n_var_states]). normalise = 1
+ * writes the normalised log-beliefs b_v - LSE_1(b_v) (log-marginals for T = 1).
+ * A variable whose beliefs are all -inf stays -inf and raises PGM_FLAG_CONTRADICTION.
+ */
+pgm_status pgm_beliefs(pgm_graph *g, const float *evidence, const float *msgs, float *out,
+                       int32_t normalise, void *stream);
+
+/*
+ * MAP decode (Sec. 4.1): out[v] = argmax_x b_v(x), lowest state on exact ties
+ * (device out [n_vars] int32).
+ */
+pgm_status pgm_decode(pgm_graph *g, const float *evidence, const float *msgs, int32_t *out,
+                      void *stream);
+
+/*
+ * End-to-end inference from HOST buffers (the call of a user without device memory of
+ * their own): copies log_pot [n_potentials] and evidence [n_var_states] from host
+ * memory to graph-owned device buffers, runs n_iters iterations from zero messages
+ * (pgm_run_bp), and copies the normalised log-beliefs [n_var_states] (if beliefs is
+ * not NULL) and the MAP decode [n_vars] (if decode is not NULL) back to host memory.
+ * Blocking: returns after the results are in host memory. Host buffers that are
+ * page-locked (cudaHostAlloc / pinned) transfer faster. The device buffers are
+ * allocated on the first call and kept until pgm_free.
+ */
+pgm_status pgm_infer_host(pgm_graph *g, const float *log_pot, const float *evidence, float T,
+                          float damping, int32_t n_iters, float *beliefs, int32_t *decode,
+                          void *stream);
+
+/*
+ * Per-pass timing with CUDA events on the launching stream. enable = 1 makes every
+ * following pgm_run_bp record an event before and after the variable pass and the
+ * factor pass of each iteration; pgm_pass_times synchronises, returns the summed
+ * durations (milliseconds) and launch counts since the last reset, and resets them.
+ * Used by the benchmark to attribute time to kernels.
+ */
+pgm_status pgm_set_profiling(pgm_graph *g, int32_t enable);
+pgm_status pgm_pass_times(pgm_graph *g, double *var_ms, double *factor_ms, int64_t *n_var,
+                          int64_t *n_factor);
+
+/*
+ * Read (and, with clear = 1, reset) the graph's device status word, a set of
+ * PGM_FLAG_* bits raised by kernels. Synchronises `stream` first.
+ */
+pgm_status pgm_device_flags(pgm_graph *g, uint32_t *flags, int32_t clear, void *stream);
+
+/* Thread-local description of the calling thread's last error ("" if none). */
+const char *pgm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PGM_H */

@@ -1,0 +1,275 @@
+"""Thin ctypes binding over libpgm.so (include/pgm.h).
+
+Argument marshalling only: every step of belief propagation runs in the library's CUDA
+kernels. PyTorch supplies device memory and the current stream. There is no CPU
+fallback: when the library is missing or CUDA is unavailable, calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libpgm.so")
+
+PGM_OK = 0
+STATUS_NAMES = {-1: "PGM_EINVAL", -2: "PGM_ENOMEM", -3: "PGM_ECUDA", -4: "PGM_ENOTSUP",
+                -5: "PGM_EBUSY", -6: "PGM_ETIMEDOUT"}
+FLAG_CONTRADICTION = 1
+FLAG_NAN = 2
+
+# Every symbol include/pgm.h declares.
+EXPORTED = ["pgm_build", "pgm_check_desc", "pgm_free", "pgm_graph_info", "pgm_run_bp", "pgm_beliefs",
+            "pgm_decode", "pgm_infer_host", "pgm_set_profiling", "pgm_pass_times",
+            "pgm_device_flags", "pgm_last_error"]
+
+
+class PgmError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+class EnumGroupC(ctypes.Structure):
+    _fields_ = [("arity", ctypes.c_int32), ("n_cfg", ctypes.c_int32), ("cfg", ctypes.c_void_p),
+                ("n_fac", ctypes.c_int32), ("vars", ctypes.c_void_p),
+                ("shared_potentials", ctypes.c_int32)]
+
+
+class LogicGroupC(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("n_fac", ctypes.c_int32), ("par_off", ctypes.c_void_p),
+                ("parents", ctypes.c_void_p), ("child", ctypes.c_void_p)]
+
+
+class GraphDescC(ctypes.Structure):
+    _fields_ = [("n_vars", ctypes.c_int32), ("num_states", ctypes.c_void_p),
+                ("n_enum_groups", ctypes.c_int32), ("enum_groups", ctypes.POINTER(EnumGroupC)),
+                ("n_logic_groups", ctypes.c_int32), ("logic_groups", ctypes.POINTER(LogicGroupC))]
+
+
+class InfoC(ctypes.Structure):
+    _fields_ = [("n_vars", ctypes.c_int64), ("n_var_states", ctypes.c_int64),
+                ("n_factors", ctypes.c_int64), ("n_edges", ctypes.c_int64),
+                ("n_edge_states", ctypes.c_int64), ("n_potentials", ctypes.c_int64),
+                ("max_states", ctypes.c_int32), ("max_degree", ctypes.c_int32),
+                ("device_bytes", ctypes.c_int64), ("launches_per_iter", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+_lib = None
+
+
+def load_library(path: str | None = None):
+    """Load libpgm.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise RuntimeError(f"libpgm.so not built ({p}); run paper_2202_04110_gb300.build.build()")
+    lib = ctypes.CDLL(p)
+    vp, i32, f32 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_float
+    lib.pgm_build.restype = i32
+    lib.pgm_build.argtypes = [ctypes.POINTER(GraphDescC), ctypes.POINTER(vp)]
+    lib.pgm_check_desc.restype = i32
+    lib.pgm_check_desc.argtypes = [ctypes.POINTER(GraphDescC), ctypes.POINTER(InfoC)]
+    lib.pgm_free.restype = None
+    lib.pgm_free.argtypes = [vp]
+    lib.pgm_graph_info.restype = i32
+    lib.pgm_graph_info.argtypes = [vp, ctypes.POINTER(InfoC)]
+    lib.pgm_run_bp.restype = i32
+    lib.pgm_run_bp.argtypes = [vp, vp, vp, f32, f32, i32, vp, vp]
+    lib.pgm_beliefs.restype = i32
+    lib.pgm_beliefs.argtypes = [vp, vp, vp, vp, i32, vp]
+    lib.pgm_decode.restype = i32
+    lib.pgm_decode.argtypes = [vp, vp, vp, vp, vp]
+    lib.pgm_infer_host.restype = i32
+    lib.pgm_infer_host.argtypes = [vp, vp, vp, f32, f32, i32, vp, vp, vp]
+    lib.pgm_set_profiling.restype = i32
+    lib.pgm_set_profiling.argtypes = [vp, i32]
+    lib.pgm_pass_times.restype = i32
+    lib.pgm_pass_times.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                   ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
+    lib.pgm_device_flags.restype = i32
+    lib.pgm_device_flags.argtypes = [vp, ctypes.POINTER(ctypes.c_uint32), i32, vp]
+    lib.pgm_last_error.restype = ctypes.c_char_p
+    lib.pgm_last_error.argtypes = []
+    _lib = lib
+    return lib
+
+
+def check(status: int):
+    if status != PGM_OK:
+        msg = load_library().pgm_last_error().decode(errors="replace")
+        raise PgmError(status, msg)
+
+
+def marshal_desc(fg):
+    """Build a pgm_graph_desc from a workloads.FactorGraph; returns (desc, keepalive)."""
+    keep = []
+
+    def arr(a):
+        a = np.ascontiguousarray(a, dtype=np.int32)
+        if a.size == 0:
+            a = np.zeros(1, np.int32)
+        keep.append(a)
+        return a.ctypes.data
+
+    eg = (EnumGroupC * max(1, len(fg.enum_groups)))()
+    for i, g in enumerate(fg.enum_groups):
+        eg[i] = EnumGroupC(g.arity, g.n_cfg, arr(g.cfg), g.n_fac, arr(g.vars), int(bool(g.shared)))
+    lg = (LogicGroupC * max(1, len(fg.logic_groups)))()
+    for i, g in enumerate(fg.logic_groups):
+        lg[i] = LogicGroupC(int(g.kind), g.n_fac, arr(g.par_off), arr(g.parents), arr(g.child))
+    keep += [eg, lg]
+    d = GraphDescC(fg.n_vars, arr(fg.num_states), len(fg.enum_groups),
+                   ctypes.cast(eg, ctypes.POINTER(EnumGroupC)), len(fg.logic_groups),
+                   ctypes.cast(lg, ctypes.POINTER(LogicGroupC)))
+    return d, keep
+
+
+def check_desc(fg) -> dict:
+    """Host-only validation and size report of a workloads.FactorGraph (no GPU)."""
+    lib = load_library()
+    desc, keep = marshal_desc(fg)
+    info = InfoC()
+    check(lib.pgm_check_desc(ctypes.byref(desc), ctypes.byref(info)))
+    del keep
+    return {k: getattr(info, k) for k, _ in InfoC._fields_}
+
+
+def _stream_ptr(stream=None) -> int:
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+def _dptr(t, dtype=None, numel=None, name="tensor") -> int:
+    import torch
+    if t is None:
+        return 0
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError(f"{name} must have dtype {dtype}")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"{name} must have {numel} elements, has {t.numel()}")
+    return int(t.data_ptr())
+
+
+class Graph:
+    """A compiled factor graph resident on the current CUDA device."""
+
+    def __init__(self, fg):
+        lib = load_library()
+        desc, keep = marshal_desc(fg)
+        h = ctypes.c_void_p()
+        check(lib.pgm_build(ctypes.byref(desc), ctypes.byref(h)))
+        del keep
+        self._h = h
+        info = InfoC()
+        check(lib.pgm_graph_info(h, ctypes.byref(info)))
+        self.info = {k: getattr(info, k) for k, _ in InfoC._fields_}
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load_library().pgm_free(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # --- calls ---------------------------------------------------------------------
+    def new_msgs(self):
+        import torch
+        return torch.zeros(max(self.info["n_edge_states"], 1), dtype=torch.float32, device="cuda")[: self.info["n_edge_states"]]
+
+    def run_bp(self, log_pot, evidence, T: float, damping: float, n_iters: int, msgs, stream=None):
+        """In-place: msgs <- n_iters LBP iterations from msgs (pgm_run_bp)."""
+        import torch
+        I = self.info
+        lp = _dptr(log_pot, torch.float32, I["n_potentials"], "log_pot") if I["n_potentials"] else 0
+        check(load_library().pgm_run_bp(self._h, lp, _dptr(evidence, torch.float32, I["n_var_states"], "evidence"),
+                                        float(T), float(damping), int(n_iters),
+                                        _dptr(msgs, torch.float32, I["n_edge_states"], "msgs"),
+                                        _stream_ptr(stream)))
+        return msgs
+
+    def beliefs(self, evidence, msgs, normalise: bool = True, out=None, stream=None):
+        import torch
+        I = self.info
+        if out is None:
+            out = torch.empty(I["n_var_states"], dtype=torch.float32, device="cuda")
+        check(load_library().pgm_beliefs(self._h, _dptr(evidence, torch.float32, I["n_var_states"], "evidence"),
+                                         _dptr(msgs, torch.float32, I["n_edge_states"], "msgs"),
+                                         _dptr(out, torch.float32, I["n_var_states"], "out"),
+                                         int(bool(normalise)), _stream_ptr(stream)))
+        return out
+
+    def decode(self, evidence, msgs, out=None, stream=None):
+        import torch
+        I = self.info
+        if out is None:
+            out = torch.empty(I["n_vars"], dtype=torch.int32, device="cuda")
+        check(load_library().pgm_decode(self._h, _dptr(evidence, torch.float32, I["n_var_states"], "evidence"),
+                                        _dptr(msgs, torch.float32, I["n_edge_states"], "msgs"),
+                                        _dptr(out, torch.int32, I["n_vars"], "out"), _stream_ptr(stream)))
+        return out
+
+    def infer_host(self, log_pot: np.ndarray, evidence: np.ndarray, T: float, damping: float,
+                   n_iters: int, beliefs: np.ndarray | None = None, decode: np.ndarray | None = None,
+                   stream=None):
+        """pgm_infer_host on host numpy buffers (pinned numpy views are fastest)."""
+        I = self.info
+        lp = np.ascontiguousarray(log_pot, np.float32)
+        ev = np.ascontiguousarray(evidence, np.float32)
+        if lp.size != I["n_potentials"] or ev.size != I["n_var_states"]:
+            raise ValueError("log_pot / evidence sizes do not match the graph")
+        if beliefs is None:
+            beliefs = np.empty(I["n_var_states"], np.float32)
+        if decode is None:
+            decode = np.empty(I["n_vars"], np.int32)
+        check(load_library().pgm_infer_host(self._h, lp.ctypes.data if lp.size else None, ev.ctypes.data,
+                                            float(T), float(damping), int(n_iters), beliefs.ctypes.data,
+                                            decode.ctypes.data, _stream_ptr(stream)))
+        return beliefs, decode
+
+    def set_profiling(self, enable: bool):
+        check(load_library().pgm_set_profiling(self._h, int(bool(enable))))
+
+    def pass_times(self):
+        """(variable-pass ms, factor-pass ms, variable launches, factor launches) since the
+        last call, from CUDA events recorded on the launching stream."""
+        tv, tf = ctypes.c_double(), ctypes.c_double()
+        nv, nf = ctypes.c_int64(), ctypes.c_int64()
+        check(load_library().pgm_pass_times(self._h, ctypes.byref(tv), ctypes.byref(tf), ctypes.byref(nv), ctypes.byref(nf)))
+        return tv.value, tf.value, nv.value, nf.value
+
+    def flags(self, clear: bool = False, stream=None) -> int:
+        f = ctypes.c_uint32(0)
+        check(load_library().pgm_device_flags(self._h, ctypes.byref(f), int(bool(clear)), _stream_ptr(stream)))
+        return int(f.value)
+
+
+def infer(problem, n_iters: int | None = None, T: float | None = None, graph: Graph | None = None):
+    """Cold-start LBP on a workloads.Problem on the GPU. Returns (graph, msgs,
+    normalised log-beliefs, decode) as CUDA tensors."""
+    import torch
+    g = graph or Graph(problem.graph)
+    lp = torch.as_tensor(problem.log_pot, dtype=torch.float32).cuda()
+    ev = torch.as_tensor(problem.evidence, dtype=torch.float32).cuda()
+    msgs = g.new_msgs()
+    g.run_bp(lp, ev, problem.T if T is None else T, problem.damping,
+             problem.n_iters if n_iters is None else n_iters, msgs)
+    return g, msgs, g.beliefs(ev, msgs, True), g.decode(ev, msgs)

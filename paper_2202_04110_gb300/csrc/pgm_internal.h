@@ -1,0 +1,143 @@
+// Internal layout of a compiled factor graph (host compiler <-> kernels).
+//
+// The flat layout follows PGMax's fully flat array design (arXiv 2202.04110, Sec. 4):
+// every factor-to-variable message lives in one 1-D array indexed by edge-state, and
+// the compiler keeps the global indices of variable states and factor configurations.
+// Only factor-to-variable messages are stored; variable-to-factor messages are
+// recomputed each iteration from the beliefs (b_v - m_{f->v}).
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+namespace pgm {
+
+constexpr int kMaxArity = 8;
+constexpr int kMaxStateSum = 64;
+constexpr int kMaxStates = 256;
+constexpr int kVarBlockDegree = 64;  // variables with more factors use a block each
+constexpr int kLogicSmallFan = 4;    // logical groups up to this fan-in: thread per factor
+
+// Factor-pass kernel variants.
+enum FactorVariant : int32_t {
+    kPair2 = 0,   // dense pairwise table, both variables with 2 states
+    kPair4 = 1,
+    kPair8 = 2,
+    kPair16 = 3,
+    kEnumGeneric = 4,  // any listed-configuration factor within the limits
+    kLogicSmall = 5,   // OR / AND, fan-in <= kLogicSmallFan, thread per factor
+    kLogicWarp = 6,    // OR / AND, any fan-in, warp per factor
+    kNumFactorVariants = 7
+};
+
+// One enumeration group as seen by a launch. Edges of factor f are
+// edge_base + f * arity + j; their edge-states start at es_base + f * es_per_fac + Koff[j].
+struct EnumSeg {
+    int32_t block_begin;  // first block of the launch that works on this group
+    int32_t n_fac;
+    int32_t edge_base;
+    int32_t es_base;
+    int32_t es_per_fac;
+    int32_t pot_base;     // first log-potential of the group
+    int32_t shared;       // 1: one table of n_cfg values for all factors
+    int32_t n_cfg;
+    int32_t arity;
+    int32_t cfg_base;     // offset of the group's [n_cfg * arity] table in the uint8 pool
+    int32_t K[kMaxArity];
+    int32_t Koff[kMaxArity];
+};
+
+// One logical group as seen by a launch. Factor f owns edges
+// edge_base + par_off[f] + f + (0..n-1 parents, n child); every edge has 2 states, so
+// edge e's states are at es_base + 2 * (e - edge_base).
+struct LogicSeg {
+    int32_t block_begin;
+    int32_t n_fac;
+    int32_t kind;         // 0 OR, 1 AND
+    int32_t edge_base;
+    int32_t es_base;
+    int32_t paroff_base;  // offset of the group's par_off[n_fac + 1] in the pool
+    int32_t max_fan;
+    int32_t pad;
+};
+
+// Device-side view of a graph's index arrays (all int32, device memory).
+struct DevGraph {
+    int32_t V, VS, E, ES;
+    const int32_t *vs_off;   // [V + 1]  first state of each variable
+    const int32_t *vin_off;  // [V + 1]  CSR: incoming edges of each variable
+    const int32_t *vin_es;   // [E]      first edge-state of each incoming edge
+    const int32_t *edge_vs;  // [E]      first variable-state of each edge's variable
+    const uint8_t *cfg_pool;
+    const int32_t *paroff_pool;
+    uint32_t *flags;         // device status word
+};
+
+struct FactorLaunch {
+    int32_t variant;
+    int32_t n_seg;
+    const void *segs;  // device EnumSeg[] or LogicSeg[]
+    int32_t n_blocks;
+    int32_t threads;
+    int32_t smem;      // dynamic shared memory bytes
+    int32_t max_fan;   // logical warp launches: largest fan-in
+};
+
+struct VarLaunch {
+    int32_t block_mode;      // 0: thread per variable, 1: block per variable
+    int32_t n;               // variables in the list
+    const int32_t *list;     // device list, or nullptr for the identity 0..n-1
+    int32_t n_blocks;
+    int32_t threads;
+};
+
+struct Plan {
+    std::vector<FactorLaunch> factor;
+    std::vector<VarLaunch> var;
+    int32_t kfix;  // 2 when every variable is binary (vectorised variable pass), else 0
+};
+
+// Host-side result of the graph compiler (compile.cpp).
+struct HostEnumGroup {
+    int32_t variant;
+    EnumSeg seg;  // block_begin filled by the planner
+};
+struct HostLogicGroup {
+    int32_t variant;
+    LogicSeg seg;
+};
+
+struct HostLayout {
+    int64_t V = 0, VS = 0, E = 0, ES = 0, F = 0, P = 0;
+    int32_t max_states = 0, max_degree = 0;
+    std::vector<int32_t> vs_off, vin_off, vin_es, edge_vs;
+    std::vector<uint8_t> cfg_pool;
+    std::vector<int32_t> paroff_pool;
+    std::vector<HostEnumGroup> enum_groups;
+    std::vector<HostLogicGroup> logic_groups;
+    std::vector<int32_t> var_small, var_large;  // degree buckets
+    bool var_small_identity = false;
+    bool all_binary = false;
+};
+
+struct GraphDescView;  // forward (defined in compile.cpp from the C-ABI struct)
+
+// Returns "" on success, else an error message.
+std::string compile_graph(const void *desc /* const pgm_graph_desc* */, HostLayout *out);
+
+// Kernel launchers (kernels.cu). Each returns cudaGetLastError() of its launches.
+cudaError_t launch_var_pass(const DevGraph &G, const Plan &P, const float *ev, const float *m,
+                            float *b, int mode, int32_t *decode, cudaStream_t s);
+cudaError_t launch_factor_pass(const DevGraph &G, const Plan &P, const float *log_pot,
+                               const float *b, const float *ev, const float *m_old,
+                               float *m_new, float T, float damping, cudaStream_t s);
+// Configure kernel attributes (large dynamic shared memory) once per process/device.
+cudaError_t prepare_kernels(int max_smem_bytes);
+
+// Variable-pass modes.
+enum VarMode : int { kVarBeliefs = 0, kVarNormalised = 1, kVarDecode = 2 };
+
+}  // namespace pgm

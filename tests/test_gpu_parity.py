@@ -1,0 +1,179 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Normalised log-beliefs agree to 1e-4 absolute after the same fixed iteration count and
+MAP decodes are equal except at oracle ties within 1e-6. Inputs are seeded synthetic
+graphs shaped like the benchmark workloads (Ising, Potts, RBM, binary deconvolution with
+OR / AND factors) plus random graphs with mixed state counts, sparse configuration
+lists and logical factors, at sizes that span several thread blocks with ragged tails.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2202_04110_gb300 import workloads as W
+from tests._parity import assert_beliefs_close, assert_decode_ok
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2202_04110_gb300 import build
+    build.build()
+    from paper_2202_04110_gb300 import binding
+    return binding
+
+
+def _gpu_infer(binding, graph, log_pot, evidence, T, damping, n_iters):
+    import torch
+    g = binding.Graph(graph)
+    lp = torch.as_tensor(np.asarray(log_pot, np.float32)).cuda()
+    ev = torch.as_tensor(np.asarray(evidence, np.float32)).cuda()
+    msgs = g.new_msgs()
+    g.run_bp(lp, ev, T, damping, n_iters, msgs)
+    nb = g.beliefs(ev, msgs, True).cpu().numpy()
+    dec = g.decode(ev, msgs).cpu().numpy()
+    flags = g.flags(clear=True)
+    return g, msgs, nb, dec, flags
+
+
+def _check(binding, graph, log_pot, evidence, T, damping, n_iters, what="", atol=1e-4):
+    _, _, nb, dec, flags = _gpu_infer(binding, graph, log_pot, evidence, T, damping, n_iters)
+    msgs, ofl = oracle.run_bp(graph, log_pot, evidence, T, damping, n_iters)
+    _, onb, odec, ofl2 = oracle.beliefs(graph, evidence, msgs)
+    err = assert_beliefs_close(nb, onb, atol=atol, what=what)
+    assert_decode_ok(dec, onb, graph.num_states, what=what)
+    assert bool(flags & 1) == bool((ofl | ofl2) & 1), (flags, ofl, ofl2)
+    return err
+
+
+def test_ising_10x10(gpu):
+    p = W.ising_small(0)
+    _check(gpu, p.graph, p.log_pot, p.evidence, p.T, p.damping, p.n_iters, "ising10x10")
+
+
+@pytest.mark.parametrize("T", [0.0, 1.0])
+@pytest.mark.parametrize("shape", [(1, 2), (3, 1), (17, 29), (64, 65)])
+def test_ising_ragged(gpu, T, shape):
+    p = W.ising_grid(*shape, seed=shape[0] * 31 + shape[1], T=T, n_iters=40)
+    _check(gpu, p.graph, p.log_pot, p.evidence, T, 0.5, 40, f"ising{shape}")
+
+
+@pytest.mark.parametrize("K", [2, 4, 8, 16])
+@pytest.mark.parametrize("T", [0.0, 1.0])
+def test_potts(gpu, K, T):
+    p = W.potts_grid(23, K, seed=K, T=T, n_iters=30)
+    _check(gpu, p.graph, p.log_pot, p.evidence, T, 0.5, 30, f"potts K={K}")
+
+
+@pytest.mark.parametrize("T", [0.0, 1.0])
+def test_rbm_high_degree(gpu, T):
+    """Visible variables have degree 150 > 64: block-per-variable path."""
+    p = W.rbm(100, 150, seed=5, w_std=0.1, T=T, n_iters=60)
+    _check(gpu, p.graph, p.log_pot, p.evidence, T, 0.5, 60, "rbm")
+
+
+@pytest.mark.parametrize("seed", range(10))
+@pytest.mark.parametrize("T", [0.0, 1.0, 0.5])
+@pytest.mark.parametrize("damping", [0.0, 0.5])
+def test_random_loopy(gpu, seed, T, damping):
+    g, lp, ev = W.random_graph(seed, n_vars=40, max_K=4, n_pair=70, n_triple=6, n_or=5, n_and=5,
+                               sparse=True, shared=(seed % 2 == 1))
+    _check(gpu, g, lp, ev, T, damping, 12, f"random seed={seed}")
+
+
+@pytest.mark.parametrize("seed", range(6))
+@pytest.mark.parametrize("T", [0.0, 1.0])
+def test_random_tree(gpu, seed, T):
+    g, lp, ev = W.random_factor_tree(200 + seed, n_vars=60, max_K=4, shared=(seed % 2 == 0))
+    _check(gpu, g, lp, ev, T, 0.0, 61, f"tree seed={seed}")
+
+
+@pytest.mark.parametrize("T", [0.0, 1.0])
+def test_deconvolution_small(gpu, T):
+    """OR fan-in 5..180 (warp-per-factor path) and 2-parent AND (thread path)."""
+    p = W.deconvolution(3, n_img=3, T=T, n_iters=60)
+    _check(gpu, p.graph, p.log_pot, p.evidence, T, 0.5, 60, "deconv")
+
+
+def test_wide_or_factor(gpu):
+    """A single OR factor with 1000 parents: several 32-parent rounds of the warp scans."""
+    n = 1000
+    rng = np.random.default_rng(9)
+    fg = W.FactorGraph(np.full(n + 1, 2, np.int32), [],
+                       [W.LogicGroup(W.OR, np.array([0, n], np.int32), np.arange(n, dtype=np.int32),
+                                     np.array([n], np.int32))])
+    ev = rng.normal(-3, 1, size=(n + 1) * 2).astype(np.float32)
+    for T in (0.0, 1.0):
+        _check(gpu, fg, np.zeros(0, np.float32), ev, T, 0.5, 5, f"wide OR T={T}")
+
+
+def test_edge_cases(gpu):
+    # no factors at all: beliefs are the normalised evidence
+    fg = W.FactorGraph(np.array([3, 1, 2], np.int32))
+    ev = np.array([0.1, 2.0, -1.0, 5.0, 0.3, 0.2], np.float32)
+    _check(gpu, fg, np.zeros(0, np.float32), ev, 1.0, 0.5, 3, "no factors")
+    # zero iterations
+    p = W.ising_grid(5, 6, 1)
+    _check(gpu, p.graph, p.log_pot, p.evidence, 1.0, 0.5, 0, "zero iterations")
+    # zero-parent OR (child forced to 0) and zero-parent AND (child forced to 1)
+    fg = W.FactorGraph(np.array([2, 2, 2], np.int32), [W.EnumGroup(W.PAIR2_CFG.copy(), np.array([[0, 2]], np.int32))],
+                       [W.LogicGroup(W.OR, np.array([0, 0], np.int32), np.zeros(0, np.int32), np.array([0], np.int32)),
+                        W.LogicGroup(W.AND, np.array([0, 0], np.int32), np.zeros(0, np.int32), np.array([1], np.int32))])
+    lp = np.array([0.5, -0.2, 0.1, 0.3], np.float32)
+    ev = np.array([0.0, 0.4, 0.0, -0.4, 0.2, 0.0], np.float32)
+    for T in (0.0, 1.0):
+        _check(gpu, fg, lp, ev, T, 0.5, 6, "empty logical")
+
+
+def test_warm_start_and_determinism(gpu):
+    import torch
+    p = W.ising_grid(31, 33, 4, T=1.0)
+    g = gpu.Graph(p.graph)
+    lp = torch.as_tensor(p.log_pot).cuda()
+    ev = torch.as_tensor(p.evidence).cuda()
+    a = g.new_msgs()
+    g.run_bp(lp, ev, 1.0, 0.5, 5, a)
+    g.run_bp(lp, ev, 1.0, 0.5, 6, a)
+    b = g.new_msgs()
+    g.run_bp(lp, ev, 1.0, 0.5, 11, b)
+    assert torch.equal(a, b)
+    c = g.new_msgs()
+    g.run_bp(lp, ev, 1.0, 0.5, 11, c)
+    assert torch.equal(b, c)
+    # the GPU messages track the oracle's
+    om, _ = oracle.run_bp(p.graph, p.log_pot, p.evidence, 1.0, 0.5, 11)
+    np.testing.assert_allclose(c.cpu().numpy(), om, atol=1e-4)
+
+
+def test_invalid_arguments(gpu):
+    import torch
+    p = W.ising_grid(4, 4, 0)
+    g = gpu.Graph(p.graph)
+    lp = torch.as_tensor(p.log_pot).cuda()
+    ev = torch.as_tensor(p.evidence).cuda()
+    m = g.new_msgs()
+    for T, d, n in ((-1.0, 0.5, 3), (float("nan"), 0.5, 3), (1.0, 1.0, 3), (1.0, -0.1, 3), (1.0, 0.5, -1)):
+        with pytest.raises(gpu.PgmError) as ei:
+            g.run_bp(lp, ev, T, d, n, m)
+        assert ei.value.status == -1
+    with pytest.raises(ValueError):
+        g.run_bp(lp, ev[:-1], 1.0, 0.5, 1, m)
+
+
+@pytest.mark.parametrize("T", [1.0, 0.0])
+def test_ising_1000x1000_full(gpu, T):
+    """The full 1000x1000 Ising workload (1,998,000 factors, 200 iterations): every
+    normalised log-belief and decode against the oracle."""
+    p = W.ising_large(0, T=T)
+    _check(gpu, p.graph, p.log_pot, p.evidence, T, p.damping, p.n_iters, f"ising1000 T={T}")
+
+
+def test_deconvolution_full_size(gpu):
+    """The full deconvolution graph (W degree 10,000; OR fan-in 5..180), max-product,
+    100 iterations, every belief against the oracle."""
+    p = W.deconvolution(0, n_iters=100)
+    _check(gpu, p.graph, p.log_pot, p.evidence, 0.0, 0.5, 100, "deconv full")
