@@ -193,13 +193,15 @@ pgm_status pgm_infer_host(pgm_graph *g, const float *log_pot, const float *evide
                           void *stream);
 
 /*
- * Per-pass timing with CUDA events on the launching stream. enable = 1 makes every
+ * Per-pass timing with CUDA events on the launching stream. period = N > 0 makes every
  * following pgm_run_bp record an event before and after the variable pass and the
- * factor pass of each iteration; pgm_pass_times synchronises, returns the summed
- * durations (milliseconds) and launch counts since the last reset, and resets them.
- * Used by the benchmark to attribute time to kernels.
+ * factor pass of every N-th iteration (iterations N-1, 2N-1, ... of each call); period
+ * = 0 turns it off. pgm_pass_times synchronises, returns the summed durations
+ * (milliseconds) and launch counts of the sampled passes since the last reset, and
+ * resets them. Used by the benchmark to attribute time to kernels; a sparse period
+ * keeps the timed run undisturbed.
  */
-pgm_status pgm_set_profiling(pgm_graph *g, int32_t enable);
+pgm_status pgm_set_profiling(pgm_graph *g, int32_t period);
 pgm_status pgm_pass_times(pgm_graph *g, double *var_ms, double *factor_ms, int64_t *n_var,
                           int64_t *n_factor);
 

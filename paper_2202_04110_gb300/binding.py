@@ -245,8 +245,9 @@ class Graph:
                                             decode.ctypes.data, _stream_ptr(stream)))
         return beliefs, decode
 
-    def set_profiling(self, enable: bool):
-        check(load_library().pgm_set_profiling(self._h, int(bool(enable))))
+    def set_profiling(self, period: int):
+        """Record per-pass CUDA events every `period` iterations (0 = off)."""
+        check(load_library().pgm_set_profiling(self._h, int(period)))
 
     def pass_times(self):
         """(variable-pass ms, factor-pass ms, variable launches, factor launches) since the

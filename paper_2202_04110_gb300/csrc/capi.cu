@@ -59,7 +59,7 @@ struct pgm_graph {
     float *io_pot = nullptr, *io_ev = nullptr, *io_msgs = nullptr, *io_bel = nullptr;
     int32_t *io_dec = nullptr;
     // per-pass event timing
-    bool profiling = false;
+    int32_t profiling = 0;  // sampling period in iterations, 0 = off
     std::vector<cudaEvent_t> events;
     size_t events_used = 0;
     int64_t prof_var_launches = 0, prof_factor_launches = 0;
@@ -120,14 +120,14 @@ pgm_status build_plan(const HostLayout &H, pgm_graph *g, Packer &pk, std::vector
             if (variant == kLogicWarp) {
                 threads = 128;
                 per_block = 4;
-                smem = (size_t)4 * 4 * mf * sizeof(float);
+                smem = (size_t)4 * 3 * mf * sizeof(float);
                 if (smem > 200 * 1024) {
                     threads = 32;
                     per_block = 1;
-                    smem = (size_t)4 * mf * sizeof(float);
+                    smem = (size_t)3 * mf * sizeof(float);
                 }
                 if (smem > 200 * 1024)
-                    return fail(PGM_ENOTSUP, "logical factor fan-in above 12800 is not supported");
+                    return fail(PGM_ENOTSUP, "logical factor fan-in above 17066 is not supported");
             }
             int32_t blk = 0;
             for (const HostLogicGroup &hg : H.logic_groups) {
@@ -244,8 +244,9 @@ pgm_status pgm_build(const pgm_graph_desc *desc, pgm_graph **out) {
     g->index_mem = dmem;
     size_t es_bytes = align_up(std::max<int64_t>(H.ES, 1) * sizeof(float), 256);
     size_t vs_bytes = align_up(std::max<int64_t>(H.VS, 1) * sizeof(float), 256);
+    size_t hd_bytes = H.var_large.empty() ? 0 : 2 * es_bytes;
     char *smem = nullptr;
-    ce = cudaMalloc(&smem, es_bytes + vs_bytes + 256);
+    ce = cudaMalloc(&smem, es_bytes + vs_bytes + 256 + hd_bytes);
     if (ce != cudaSuccess) {
         cudaFree(dmem);
         delete g;
@@ -272,6 +273,7 @@ pgm_status pgm_build(const pgm_graph_desc *desc, pgm_graph **out) {
     G.cfg_pool = reinterpret_cast<const uint8_t *>(dmem + o_cfg);
     G.paroff_pool = reinterpret_cast<const int32_t *>(dmem + o_po);
     G.flags = flags;
+    G.v2f_hd = hd_bytes ? reinterpret_cast<float *>(smem + es_bytes + vs_bytes + 256) : nullptr;
     // attach device pointers of the launch lists / segments
     size_t vi = 0, fi = 0;
     int max_smem = 0;
@@ -299,7 +301,7 @@ pgm_status pgm_build(const pgm_graph_desc *desc, pgm_graph **out) {
     I.n_potentials = H.P;
     I.max_states = H.max_states;
     I.max_degree = H.max_degree;
-    I.device_bytes = (int64_t)(pk.host.size() + es_bytes + vs_bytes + 256);
+    I.device_bytes = (int64_t)(pk.host.size() + es_bytes + vs_bytes + 256 + hd_bytes);
     for (const VarLaunch &L : g->P.var) g->var_launches += (L.n > 0);
     for (const FactorLaunch &L : g->P.factor) g->factor_launches += (L.n_blocks > 0);
     I.launches_per_iter = g->var_launches + g->factor_launches;
@@ -325,8 +327,9 @@ pgm_status pgm_check_desc(const pgm_graph_desc *desc, pgm_info *info) {
     size_t idx = (H.vs_off.size() + H.vin_off.size() + H.vin_es.size() + H.edge_vs.size() +
                   H.paroff_pool.size() + H.var_small.size() + H.var_large.size()) * sizeof(int32_t) +
                  H.cfg_pool.size();
-    info->device_bytes = (int64_t)(idx + align_up(std::max<int64_t>(H.ES, 1) * sizeof(float), 256) +
-                                   align_up(std::max<int64_t>(H.VS, 1) * sizeof(float), 256) + 256);
+    size_t es_bytes = align_up(std::max<int64_t>(H.ES, 1) * sizeof(float), 256);
+    info->device_bytes = (int64_t)(idx + es_bytes + align_up(std::max<int64_t>(H.VS, 1) * sizeof(float), 256) +
+                                   256 + (H.var_large.empty() ? 0 : 2 * es_bytes));
     return PGM_OK;
 }
 
@@ -358,17 +361,18 @@ pgm_status pgm_run_bp(pgm_graph *g, const float *log_pot, const float *evidence,
     float *cur = msgs, *nxt = g->m_tmp;
     for (int it = 0; it < n_iters; ++it) {
         cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr;
-        if (g->profiling) {
+        const bool prof = g->profiling > 0 && (it % g->profiling) == g->profiling - 1;
+        if (prof) {
             pgm_status ps = take_events(g, &e0, &e1, &e2);
             if (ps != PGM_OK) return ps;
             cudaEventRecord(e0, s);
         }
-        cudaError_t e = launch_var_pass(g->G, g->P, evidence, cur, g->b, kVarBeliefs, nullptr, s);
+        cudaError_t e = launch_var_pass(g->G, g->P, evidence, cur, g->b, kVarIter, nullptr, s);
         if (e != cudaSuccess) return cuda_fail(e, "variable pass launch");
-        if (g->profiling) cudaEventRecord(e1, s);
+        if (prof) cudaEventRecord(e1, s);
         e = launch_factor_pass(g->G, g->P, log_pot, g->b, evidence, cur, nxt, T, damping, s);
         if (e != cudaSuccess) return cuda_fail(e, "factor pass launch");
-        if (g->profiling) {
+        if (prof) {
             cudaEventRecord(e2, s);
             g->prof_var_launches += g->var_launches;
             g->prof_factor_launches += g->factor_launches;
@@ -456,9 +460,10 @@ pgm_status pgm_infer_host(pgm_graph *g, const float *log_pot, const float *evide
     return PGM_OK;
 }
 
-pgm_status pgm_set_profiling(pgm_graph *g, int32_t enable) {
+pgm_status pgm_set_profiling(pgm_graph *g, int32_t period) {
     if (!g) return fail(PGM_EINVAL, "graph is NULL");
-    g->profiling = enable != 0;
+    if (period < 0) return fail(PGM_EINVAL, "period must be >= 0");
+    g->profiling = period;
     return PGM_OK;
 }
 

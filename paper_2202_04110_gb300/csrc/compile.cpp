@@ -219,13 +219,20 @@ std::string compile_graph(const void *vdesc, HostLayout *L) {
     std::vector<int32_t> fill(L->vin_off.begin(), L->vin_off.end() - 1);
     for (int64_t i = 0; i < E; ++i) L->vin_es[fill[edge_var[i]]++] = edge_es[i];
 
-    // ---- degree buckets
+    // ---- degree buckets; edges of high-degree variables take their variable-to-factor
+    // values from the exact leave-one-out buffer (edge_vs = -1 marks them)
+    if ((int64_t)maxdeg > (int64_t)kVarMaxTiles * kVarTile)
+        return fmt("a variable has %lld factors; at most %lld are supported", maxdeg, (long long)kVarMaxTiles * kVarTile);
     L->var_small.clear();
     L->var_large.clear();
     for (int64_t v = 0; v < V; ++v) {
         int32_t deg = L->vin_off[v + 1] - L->vin_off[v];
         if (deg > kVarBlockDegree) L->var_large.push_back((int32_t)v);
         else L->var_small.push_back((int32_t)v);
+    }
+    for (int64_t i = 0; i < E; ++i) {
+        int32_t v = edge_var[i];
+        if (L->vin_off[v + 1] - L->vin_off[v] > kVarBlockDegree) L->edge_vs[i] = -1;
     }
     L->var_small_identity = ((int64_t)L->var_small.size() == V);
     L->all_binary = (kmax == 2);

@@ -16,9 +16,12 @@
 // The path is gather / scatter plus log-sum-exp, bound by HBM bandwidth (or by the SFU
 // for large state counts), not a dense contraction: no tensor cores.
 //
-// Numerics: messages, beliefs and all arithmetic in FP32. When a stored message entry
-// is -inf the subtraction b - m would be -inf - (-inf); that entry's leave-one-out sum
-// is then recomputed explicitly from the variable's incoming messages (v2f_slow).
+// Numerics: messages and factor arithmetic in FP32. Variable-side sums are compensated
+// (float-float) and the beliefs the factor pass reads are stored relative to each
+// variable's largest state. An edge whose stored message has an entry that is -inf or
+// larger in magnitude than kExactThreshold takes its variable-to-factor values from an
+// explicit leave-one-out sum (v2f_slow_edge) instead of b - m; edges of variables with
+// more than kVarBlockDegree factors always do (computed by the block variable pass).
 #include <cstdint>
 
 #include <cuda_runtime.h>
@@ -112,39 +115,150 @@ __device__ __forceinline__ void store_n(float *__restrict__ p, const float (&s)[
     for (int i = 0; i < N; ++i) p[i] = s[i];
 }
 
+// ---- compensated (float-float) sums ----------------------------------------------------
+// A value hi + lo with |lo| << |hi|: TwoSum keeps the rounding error of every addition,
+// giving about 44 significant bits at FP32 speed (FP64 is a small fraction of the FP32
+// rate on this GPU). Infinite sums keep lo = 0.
+struct FF {
+    float hi, lo;
+};
+
+__device__ __forceinline__ FF ff_make(float v) { return FF{v, 0.f}; }
+
+__device__ __forceinline__ FF ff_add(FF a, float v) {
+    const float s = a.hi + v;
+    if (!isfinite(s)) return FF{s, 0.f};
+    const float bp = s - a.hi;
+    const float e = (a.hi - (s - bp)) + (v - bp);
+    return FF{s, a.lo + e};
+}
+
+__device__ __forceinline__ FF ff_add(FF a, FF b) {
+    FF r = ff_add(a, b.hi);
+    if (!isfinite(r.hi)) return r;
+    r.lo += b.lo;
+    return r;
+}
+
+__device__ __forceinline__ FF ff_shfl_up(FF v, int d) {
+    return FF{__shfl_up_sync(0xffffffffu, v.hi, d), __shfl_up_sync(0xffffffffu, v.lo, d)};
+}
+__device__ __forceinline__ FF ff_shfl_down(FF v, int d) {
+    return FF{__shfl_down_sync(0xffffffffu, v.hi, d), __shfl_down_sync(0xffffffffu, v.lo, d)};
+}
+__device__ __forceinline__ FF ff_shfl(FF v, int src) {
+    return FF{__shfl_sync(0xffffffffu, v.hi, src), __shfl_sync(0xffffffffu, v.lo, src)};
+}
+
+// a - b for float-float values, rounded to FP32 (exact up to that rounding when a and b
+// are close). -inf - finite = -inf.
+__device__ __forceinline__ float ff_diff(FF a, FF b) {
+    if (!isfinite(a.hi) || !isfinite(b.hi)) return a.hi - b.hi;
+    return (a.hi - b.hi) + (a.lo - b.lo);
+}
+
+// a > b, compared exactly on the float-float values
+__device__ __forceinline__ bool ff_gt(FF a, FF b) {
+    if (a.hi == kNegInf) return false;
+    if (b.hi == kNegInf) return true;
+    return ff_diff(a, b) > 0.f;
+}
+
 // ---- variable-to-factor value -------------------------------------------------------
 
-// Explicit leave-one-out sum e_v(x) + sum over incoming edges other than `es`; used only
-// when the edge's own message entry is -inf (rare: hard constraints).
-__device__ __noinline__ float v2f_slow(const DevGraph G, const float *__restrict__ ev,
-                                       const float *__restrict__ m, int vs, int es, int x) {
+// Explicit leave-one-out values of one edge: v(x) = e_v(x) + sum over the variable's
+// other incoming edges of m(x), float-float summed, for all K states of the edge. Used
+// when b - m would be unreliable: a stored entry is -inf (-inf - -inf) or very large
+// (cancellation). Its per-edge constant differs from the fast path's, which the factor
+// update does not see (it is invariant to a constant added to one edge's values).
+constexpr float kExactThreshold = 128.f;
+
+__device__ __noinline__ void v2f_slow_edge(const DevGraph G, const float *__restrict__ ev,
+                                           const float *__restrict__ m, int vs, int es, int K,
+                                           float *__restrict__ out) {
     int lo = 0, hi = G.V - 1;
     while (lo < hi) {
-        int mid = (lo + hi + 1) >> 1;
+        const int mid = (lo + hi + 1) >> 1;
         if (G.vs_off[mid] <= vs) lo = mid;
         else hi = mid - 1;
     }
-    float s = ev[vs + x];
-    for (int k = G.vin_off[lo]; k < G.vin_off[lo + 1]; ++k) {
-        int e2 = G.vin_es[k];
-        if (e2 != es) s += m[e2 + x];
+    const int k0 = G.vin_off[lo], k1 = G.vin_off[lo + 1];
+    for (int x = 0; x < K; ++x) {
+        FF s = ff_make(ev[vs + x]);
+        for (int k = k0; k < k1; ++k) {
+            const int e2 = G.vin_es[k];
+            if (e2 != es) s = ff_add(s, m[e2 + x]);
+        }
+        out[x] = s.hi + s.lo;
     }
-    return s;
 }
 
-__device__ __forceinline__ float v2f_val(const DevGraph &G, const float *ev, const float *m,
-                                         float bx, float mx, int vs, int es, int x) {
-    return (mx == kNegInf) ? v2f_slow(G, ev, m, vs, es, x) : bx - mx;
+__device__ __forceinline__ bool needs_exact(float mv) { return !(fabsf(mv) <= kExactThreshold); }
+
+// Exact leave-one-out values of a high-degree variable's edge, stored as float-float
+// (hi, lo) pairs in G.v2f_hd, shifted so that the edge's largest state is 0 (factor
+// updates are invariant to a per-edge constant) and rounded once to FP32.
+__device__ __forceinline__ float2 hd_pair(const DevGraph &G, int es, int x) {
+    return __ldg(reinterpret_cast<const float2 *>(G.v2f_hd) + es + x);
+}
+
+__device__ __forceinline__ float hd_rel(float2 a, float2 mx) {
+    if (!isfinite(a.x) || !isfinite(mx.x)) return a.x - mx.x;
+    return (a.x - mx.x) + (a.y - mx.y);
+}
+
+__device__ __forceinline__ bool hd_gt(float2 a, float2 b) {
+    if (a.x == -CUDART_INF_F) return false;
+    if (b.x == -CUDART_INF_F) return true;
+    return hd_rel(a, b) > 0.f;
+}
+
+template <int K>
+__device__ __forceinline__ void hd_v2f(const DevGraph &G, int es, float (&v)[K]) {
+    float2 d[K];
+    int arg = 0;
+#pragma unroll
+    for (int x = 0; x < K; ++x) {
+        d[x] = hd_pair(G, es, x);
+        if (x > 0 && hd_gt(d[x], d[arg])) arg = x;
+    }
+    float2 mx = d[0];
+#pragma unroll
+    for (int x = 1; x < K; ++x)
+        if (x == arg) mx = d[x];
+    if (mx.x == -CUDART_INF_F) {
+#pragma unroll
+        for (int x = 0; x < K; ++x) v[x] = -CUDART_INF_F;
+        return;
+    }
+#pragma unroll
+    for (int x = 0; x < K; ++x) v[x] = hd_rel(d[x], mx);
+}
+
+// Variable-to-factor values of one K-state edge. Edges of high-degree variables
+// (edge_vs < 0) read the exact leave-one-out sums the block variable pass wrote to
+// G.v2f_hd; all others use b - m, or the explicit sum when an entry needs it.
+template <int K>
+__device__ __forceinline__ void gather_v2f(const DevGraph &G, const float *__restrict__ b,
+                                           const float *__restrict__ ev, const float *__restrict__ m_old,
+                                           int vs, int es, const float (&mo)[K], float (&v)[K]) {
+    if (vs < 0) {
+        hd_v2f<K>(G, es, v);
+        return;
+    }
+    bool exact = false;
+#pragma unroll
+    for (int x = 0; x < K; ++x) exact |= needs_exact(mo[x]);
+    if (exact) {
+        v2f_slow_edge(G, ev, m_old, vs, es, K, v);
+        return;
+    }
+    load_n<K>(v, b + vs);
+#pragma unroll
+    for (int x = 0; x < K; ++x) v[x] -= mo[x];
 }
 
 // ---- log-sum-exp helpers -------------------------------------------------------------
-
-// natural-log LSE of two values
-__device__ __forceinline__ float lse2(float a, float b) {
-    float mx = fmaxf(a, b), mn = fminf(a, b);
-    if (mx == kNegInf || mx == pos_inf()) return mx;
-    return mx + log1pf(expf(mn - mx));
-}
 
 // log(s(u)), s(u) = log(1 + e^u)
 __device__ __forceinline__ float log_softplus(float u) {
@@ -153,39 +267,65 @@ __device__ __forceinline__ float log_softplus(float u) {
     return logf(log1pf(expf(u)));
 }
 
-// log(e^s - 1) from ls = log s
-__device__ __forceinline__ float log_expm1_from_log(float ls) {
-    if (ls == kNegInf) return kNegInf;
-    if (ls == pos_inf()) return pos_inf();
-    if (ls > 0.f) {
-        float s = expf(ls);
-        return s + logf(-expm1f(-s));
-    }
-    if (ls > -80.f) {
-        float s = expf(ls);
-        return ls + logf(expm1f(s) / s);
-    }
-    return ls;
+// Sums of softplus terms t_j = s(x_j / T) for the T > 0 OR update, kept as a pair
+// (m, s) with value s * exp(m): m is the largest log t_j seen, s a linear sum relative
+// to it. Linear precision when the terms are moderate, and no underflow when they are
+// tiny (very negative log-odds, where t_j ~ exp(x_j / T)).
+struct LSum {
+    float m, s;
+};
+
+__device__ __forceinline__ LSum lsum_zero() { return LSum{kNegInf, 0.f}; }
+
+__device__ __forceinline__ LSum lsum_add(LSum a, LSum b) {
+    const float M = fmaxf(a.m, b.m);
+    if (M == kNegInf) return lsum_zero();
+    if (M == pos_inf()) return LSum{pos_inf(), 1.f};
+    float s = 0.f;
+    if (a.s != 0.f) s += a.s * expf(a.m - M);
+    if (b.s != 0.f) s += b.s * expf(b.m - M);
+    return LSum{M, s};
 }
 
-// -log(1 - e^{-s}) from ls = log s
-__device__ __forceinline__ float neg_log_1mexp_from_log(float ls) {
-    if (ls == pos_inf()) return 0.f;
-    if (ls > 0.f) return -logf(-expm1f(-expf(ls)));
-    if (ls > -80.f) {
-        float s = expf(ls);
-        return -ls - logf(-expm1f(-s) / s);
-    }
-    return -ls;
+// one term: log t(u) with t(u) = log(1 + e^u) (u = x / T)
+__device__ __forceinline__ LSum lsum_term(float u) {
+    if (u == kNegInf) return lsum_zero();
+    return LSum{log_softplus(u), 1.f};
 }
 
-// OR update to parent i (T > 0): ls = log of the leave-one-out softplus sum (in units
-// of T), xc = child log-odds.
-__device__ __forceinline__ float or_parent_soft(float ls, float xc, float T, float invT) {
-    if (ls == kNegInf) return xc;
-    float y = xc + T * log_expm1_from_log(ls);
-    if (y >= 0.f) return T * neg_log_1mexp_from_log(ls) - T * log1pf(expf(-y * invT));
-    return xc + T * expf(ls) - T * log1pf(expf(y * invT));
+// log(e^a - 1) for the sum a = s * exp(m)
+__device__ __forceinline__ float log_expm1_lsum(LSum A) {
+    if (A.s == 0.f) return kNegInf;
+    const float la = A.m + logf(A.s);
+    if (la == pos_inf()) return pos_inf();
+    if (la < -20.f) return la;  // a < 2e-9: log(expm1(a)) = log(a) + a/2 + ...
+    const float a = A.s * expf(A.m);
+    if (a > 20.f) return a + log1pf(-expf(-a));
+    return logf(expm1f(a));
+}
+
+// -log(1 - e^{-a}) for the sum a = s * exp(m)
+__device__ __forceinline__ float neg_log_1mexp_lsum(LSum A) {
+    const float la = A.m + logf(A.s);
+    if (la == pos_inf()) return 0.f;
+    if (la < -20.f) return -la;
+    const float a = A.s * expf(A.m);
+    if (a > 20.f) return -log1pf(-expf(-a));
+    return -logf(-expm1f(-a));
+}
+
+__device__ __forceinline__ float lsum_value(LSum A) {
+    if (A.s == 0.f) return 0.f;
+    return A.s * expf(A.m);
+}
+
+// OR update to parent i (T > 0): A = leave-one-out softplus sum (units of T), xc =
+// child log-odds.
+__device__ __forceinline__ float or_parent_soft(LSum A, float xc, float T, float invT) {
+    if (A.s == 0.f) return xc;
+    const float y = xc + T * log_expm1_lsum(A);
+    if (y >= 0.f) return T * neg_log_1mexp_lsum(A) - T * log1pf(expf(-y * invT));
+    return xc + T * lsum_value(A) - T * log1pf(expf(y * invT));
 }
 
 // OR update to parent i (T = 0): S = leave-one-out sum of max(x_j, 0), M = leave-one-out max.
@@ -263,7 +403,9 @@ __device__ __forceinline__ float lse_row(const float (&z)[K], float T, float inv
 // Variable pass
 // =====================================================================================
 
-// Thread per variable. KFIX = 2: every variable binary (states at 2v, edge-states even).
+// Thread per variable (degree <= kVarBlockDegree). Sums are compensated (float-float)
+// in ascending edge order. KFIX = 2: every variable binary (states at 2v, edge-states
+// even, float2 loads).
 template <int KFIX, int MODE>
 __global__ void __launch_bounds__(256) k_var_thread(DevGraph G, const int32_t *__restrict__ list, int n,
                                                     const float *__restrict__ ev,
@@ -276,115 +418,236 @@ __global__ void __launch_bounds__(256) k_var_thread(DevGraph G, const int32_t *_
     const int k0 = __ldg(G.vin_off + v), k1 = __ldg(G.vin_off + v + 1);
     if constexpr (KFIX == 2) {
         const int vs = 2 * v;
-        float2 s = __ldg(reinterpret_cast<const float2 *>(ev + vs));
+        const float2 e = __ldg(reinterpret_cast<const float2 *>(ev + vs));
+        FF s0 = ff_make(e.x), s1 = ff_make(e.y);
         for (int k = k0; k < k1; ++k) {
             const int es = __ldg(G.vin_es + k);
             const float2 q = __ldg(reinterpret_cast<const float2 *>(m + es));
-            s.x += q.x;
-            s.y += q.y;
+            s0 = ff_add(s0, q.x);
+            s1 = ff_add(s1, q.y);
+        }
+        if constexpr (MODE == kVarDecode) {
+            dec[v] = ff_gt(s1, s0) ? 1 : 0;
+            return;
         }
         if constexpr (MODE == kVarBeliefs) {
-            reinterpret_cast<float2 *>(out + vs)[0] = s;
-        } else if constexpr (MODE == kVarNormalised) {
-            float z = lse2(s.x, s.y);
-            if (z == kNegInf) {
+            reinterpret_cast<float2 *>(out + vs)[0] = make_float2(s0.hi + s0.lo, s1.hi + s1.lo);
+            return;
+        }
+        // relative to the larger state
+        float r0, r1;
+        if (s0.hi == kNegInf && s1.hi == kNegInf) {
+            r0 = r1 = kNegInf;
+        } else if (ff_gt(s1, s0)) {
+            r0 = ff_diff(s0, s1);
+            r1 = 0.f;
+        } else {
+            r0 = 0.f;
+            r1 = ff_diff(s1, s0);
+        }
+        if constexpr (MODE == kVarIter) {
+            reinterpret_cast<float2 *>(out + vs)[0] = make_float2(r0, r1);
+        } else {  // kVarNormalised
+            if (r0 == kNegInf && r1 == kNegInf) {
                 atomicOr(G.flags, kFlagContradiction);
                 reinterpret_cast<float2 *>(out + vs)[0] = make_float2(kNegInf, kNegInf);
             } else {
-                if (s.x != s.x || s.y != s.y) atomicOr(G.flags, kFlagNaN);
-                reinterpret_cast<float2 *>(out + vs)[0] = make_float2(s.x - z, s.y - z);
+                if (r0 != r0 || r1 != r1) atomicOr(G.flags, kFlagNaN);
+                const float z = log1pf(expf(fminf(r0, r1)));  // the larger state is 0
+                reinterpret_cast<float2 *>(out + vs)[0] = make_float2(r0 - z, r1 - z);
             }
-        } else {
-            dec[v] = (s.y > s.x) ? 1 : 0;
         }
     } else {
         const int vs = __ldg(G.vs_off + v), K = __ldg(G.vs_off + v + 1) - vs;
-        float best = 0.f, mx = kNegInf;
+        FF best = ff_make(kNegInf);
         int arg = 0;
         bool nan = false;
         for (int x = 0; x < K; ++x) {
-            float s = __ldg(ev + vs + x);
-            for (int k = k0; k < k1; ++k) s += __ldg(m + __ldg(G.vin_es + k) + x);
-            if constexpr (MODE == kVarBeliefs) out[vs + x] = s;
-            if constexpr (MODE == kVarNormalised) {
-                out[vs + x] = s;
-                if (s > mx) mx = s;
-                nan |= (s != s);
+            FF s = ff_make(__ldg(ev + vs + x));
+            for (int k = k0; k < k1; ++k) s = ff_add(s, __ldg(m + __ldg(G.vin_es + k) + x));
+            nan |= (s.hi != s.hi);
+            if (x == 0 || ff_gt(s, best)) {
+                best = s;
+                arg = x;
             }
-            if constexpr (MODE == kVarDecode) {
-                if (x == 0 || s > best) {
-                    best = s;
-                    arg = x;
-                }
-            }
+            if constexpr (MODE == kVarBeliefs) out[vs + x] = s.hi + s.lo;
         }
-        if constexpr (MODE == kVarNormalised) {
-            if (nan) atomicOr(G.flags, kFlagNaN);
-            if (mx == kNegInf) {
-                atomicOr(G.flags, kFlagContradiction);
-            } else {
-                float acc = 0.f;
-                for (int x = 0; x < K; ++x) acc += expf(out[vs + x] - mx);
-                const float z = mx + logf(acc);
+        if constexpr (MODE == kVarDecode) {
+            dec[v] = arg;
+        } else if constexpr (MODE == kVarIter || MODE == kVarNormalised) {
+            // Recompute each state's float-float sum and subtract the best one exactly.
+            if (best.hi == kNegInf) {
+                if (MODE == kVarNormalised) atomicOr(G.flags, kFlagContradiction);
+                for (int x = 0; x < K; ++x) out[vs + x] = kNegInf;
+                return;
+            }
+            if (nan && MODE == kVarNormalised) atomicOr(G.flags, kFlagNaN);
+            float acc = 0.f;
+            for (int x = 0; x < K; ++x) {
+                FF s = ff_make(__ldg(ev + vs + x));
+                for (int k = k0; k < k1; ++k) s = ff_add(s, __ldg(m + __ldg(G.vin_es + k) + x));
+                const float r = (x == arg) ? 0.f : ff_diff(s, best);
+                out[vs + x] = r;
+                if (MODE == kVarNormalised) acc += expf(r);
+            }
+            if constexpr (MODE == kVarNormalised) {
+                const float z = logf(acc);
                 for (int x = 0; x < K; ++x) out[vs + x] -= z;
             }
         }
-        if constexpr (MODE == kVarDecode) dec[v] = arg;
     }
 }
 
-// Block per (high-degree) variable; deterministic tree reduction.
+// Block-wide exclusive scan (forward or reverse in thread order) of one float-float
+// per thread; `sh` holds >= 64 floats. Sums without subtraction.
+__device__ __forceinline__ FF block_scan_excl(FF v, bool reverse, float *sh) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    FF inc = v;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const FF y = reverse ? ff_shfl_down(inc, d) : ff_shfl_up(inc, d);
+        if (reverse ? (lane + d < 32) : (lane >= d)) inc = reverse ? ff_add(inc, y) : ff_add(y, inc);
+    }
+    FF exc = reverse ? ff_shfl_down(inc, 1) : ff_shfl_up(inc, 1);
+    if (reverse ? lane == 31 : lane == 0) exc = ff_make(0.f);
+    const FF wt = reverse ? ff_shfl(inc, 0) : ff_shfl(inc, 31);
+    if (lane == 0) {
+        sh[2 * warp] = wt.hi;
+        sh[2 * warp + 1] = wt.lo;
+    }
+    __syncthreads();
+    FF off = ff_make(0.f);
+    if (reverse) {
+        for (int w = nw - 1; w > warp; --w) off = ff_add(off, FF{sh[2 * w], sh[2 * w + 1]});
+    } else {
+        for (int w = 0; w < warp; ++w) off = ff_add(off, FF{sh[2 * w], sh[2 * w + 1]});
+    }
+    __syncthreads();
+    return reverse ? ff_add(exc, off) : ff_add(off, exc);
+}
+
+__device__ __forceinline__ FF block_sum(FF v, float *sh) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) v = ff_add(v, ff_shfl_down(v, d));
+    if (lane == 0) {
+        sh[2 * warp] = v.hi;
+        sh[2 * warp + 1] = v.lo;
+    }
+    __syncthreads();
+    FF tot = ff_make(0.f);
+    for (int w = 0; w < nw; ++w) tot = ff_add(tot, FF{sh[2 * w], sh[2 * w + 1]});
+    __syncthreads();
+    return tot;
+}
+
+// Block per high-degree variable (more than kVarBlockDegree factors). Incoming
+// messages are processed in tiles of kVarTile edges, kVarItems contiguous edges per
+// thread, with float-float sums in a fixed order (deterministic). In the iteration pass
+// (kVarIter) the block also writes, for every incoming edge-state, the exact
+// leave-one-out sum e_v(x) + sum_{other edges} m(x), as prefix + suffix (no subtraction),
+// to G.v2f_hd as a (hi, lo) pair; the factor kernels read it for these edges.
 template <int MODE>
-__global__ void __launch_bounds__(256) k_var_block(DevGraph G, const int32_t *__restrict__ list,
-                                                   const float *__restrict__ ev,
-                                                   const float *__restrict__ m,
-                                                   float *__restrict__ out,
-                                                   int32_t *__restrict__ dec) {
-    __shared__ float red[32];
-    __shared__ float sb[kMaxStates];
+__global__ void __launch_bounds__(kVarBlockThreads) k_var_block(DevGraph G, const int32_t *__restrict__ list,
+                                                                const float *__restrict__ ev,
+                                                                const float *__restrict__ m,
+                                                                float *__restrict__ out,
+                                                                int32_t *__restrict__ dec) {
+    __shared__ float sh[64];
+    __shared__ FF tile_tot[kVarMaxTiles];
+    __shared__ FF sb[kMaxStates];
     const int v = __ldg(list + blockIdx.x);
     const int vs = __ldg(G.vs_off + v), K = __ldg(G.vs_off + v + 1) - vs;
     const int k0 = __ldg(G.vin_off + v), k1 = __ldg(G.vin_off + v + 1);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int deg = k1 - k0;
+    const int n_tiles = (deg + kVarTile - 1) / kVarTile;
     for (int x = 0; x < K; ++x) {
-        float s = 0.f;
-        for (int k = k0 + threadIdx.x; k < k1; k += blockDim.x) s += __ldg(m + __ldg(G.vin_es + k) + x);
+        for (int t = 0; t < n_tiles; ++t) {
+            FF s = ff_make(0.f);
+            const int base = t * kVarTile + threadIdx.x * kVarItems;
 #pragma unroll
-        for (int d = 16; d > 0; d >>= 1) s += __shfl_down_sync(0xffffffffu, s, d);
-        if (lane == 0) red[warp] = s;
+            for (int i = 0; i < kVarItems; ++i) {
+                const int k = base + i;
+                if (k < deg) s = ff_add(s, __ldg(m + __ldg(G.vin_es + k0 + k) + x));
+            }
+            const FF tt = block_sum(s, sh);
+            if (threadIdx.x == 0) tile_tot[t] = tt;
+        }
         __syncthreads();
+        const float e = __ldg(ev + vs + x);
         if (threadIdx.x == 0) {
-            float tot = 0.f;
-            for (int w = 0; w < nw; ++w) tot += red[w];
-            sb[x] = __ldg(ev + vs + x) + tot;
+            FF tot = ff_make(e);
+            for (int t = 0; t < n_tiles; ++t) tot = ff_add(tot, tile_tot[t]);
+            sb[x] = tot;
+        }
+        if (MODE == kVarIter && G.v2f_hd != nullptr) {
+            FF carry_pre = ff_make(e);
+            for (int t = 0; t < n_tiles; ++t) {
+                FF carry_suf = ff_make(0.f);
+                for (int u = n_tiles - 1; u > t; --u) carry_suf = ff_add(carry_suf, tile_tot[u]);
+                const int base = t * kVarTile + threadIdx.x * kVarItems;
+                float val[kVarItems];
+                int esk[kVarItems];
+                FF own = ff_make(0.f);
+#pragma unroll
+                for (int i = 0; i < kVarItems; ++i) {
+                    const int k = base + i;
+                    esk[i] = (k < deg) ? __ldg(G.vin_es + k0 + k) : 0;
+                    val[i] = (k < deg) ? __ldg(m + esk[i] + x) : 0.f;
+                    own = ff_add(own, val[i]);
+                }
+                const FF tp = block_scan_excl(own, false, sh);
+                const FF ts = block_scan_excl(own, true, sh);
+                FF suf_local[kVarItems];
+                FF acc = ff_make(0.f);
+#pragma unroll
+                for (int i = kVarItems - 1; i >= 0; --i) {
+                    suf_local[i] = acc;
+                    acc = ff_add(acc, val[i]);
+                }
+                FF pre = ff_add(carry_pre, tp);
+                const FF suf_rest = ff_add(ts, carry_suf);
+#pragma unroll
+                for (int i = 0; i < kVarItems; ++i) {
+                    const int k = base + i;
+                    if (k < deg) {
+                        const FF loo = ff_add(pre, ff_add(suf_local[i], suf_rest));
+                        reinterpret_cast<float2 *>(G.v2f_hd)[esk[i] + x] = make_float2(loo.hi, loo.lo);
+                    }
+                    pre = ff_add(pre, val[i]);
+                }
+                carry_pre = ff_add(carry_pre, tile_tot[t]);
+            }
         }
         __syncthreads();
     }
     if (threadIdx.x != 0) return;
-    if constexpr (MODE == kVarBeliefs) {
-        for (int x = 0; x < K; ++x) out[vs + x] = sb[x];
-    } else if constexpr (MODE == kVarNormalised) {
-        float mx = kNegInf;
-        bool nan = false;
-        for (int x = 0; x < K; ++x) {
-            if (sb[x] > mx) mx = sb[x];
-            nan |= (sb[x] != sb[x]);
-        }
-        if (nan) atomicOr(G.flags, kFlagNaN);
-        if (mx == kNegInf) {
-            atomicOr(G.flags, kFlagContradiction);
-            for (int x = 0; x < K; ++x) out[vs + x] = kNegInf;
-        } else {
-            float acc = 0.f;
-            for (int x = 0; x < K; ++x) acc += expf(sb[x] - mx);
-            const float z = mx + logf(acc);
-            for (int x = 0; x < K; ++x) out[vs + x] = sb[x] - z;
-        }
-    } else {
-        int arg = 0;
-        for (int x = 1; x < K; ++x)
-            if (sb[x] > sb[arg]) arg = x;
+    int arg = 0;
+    for (int x = 1; x < K; ++x)
+        if (ff_gt(sb[x], sb[arg])) arg = x;
+    if constexpr (MODE == kVarDecode) {
         dec[v] = arg;
+    } else if constexpr (MODE == kVarBeliefs) {
+        for (int x = 0; x < K; ++x) out[vs + x] = sb[x].hi + sb[x].lo;
+    } else {
+        bool nan = false;
+        for (int x = 0; x < K; ++x) nan |= (sb[x].hi != sb[x].hi);
+        if (MODE == kVarNormalised && nan) atomicOr(G.flags, kFlagNaN);
+        if (sb[arg].hi == kNegInf) {
+            if (MODE == kVarNormalised) atomicOr(G.flags, kFlagContradiction);
+            for (int x = 0; x < K; ++x) out[vs + x] = kNegInf;
+            return;
+        }
+        float acc = 0.f;
+        for (int x = 0; x < K; ++x) {
+            const float r = (x == arg) ? 0.f : ff_diff(sb[x], sb[arg]);
+            out[vs + x] = r;
+            acc += expf(r);
+        }
+        if (MODE == kVarNormalised) {
+            const float z = logf(acc);
+            for (int x = 0; x < K; ++x) out[vs + x] -= z;
+        }
     }
 }
 
@@ -420,13 +683,8 @@ k_pair(DevGraph G, const EnumSeg *__restrict__ segs, int n_seg, const float *__r
     float mo0[K], mo1[K], v0[K], v1[K];
     load_n_stream<K>(mo0, m_old + es0);
     load_n_stream<K>(mo1, m_old + es1);
-    load_n<K>(v0, b + vs0);
-    load_n<K>(v1, b + vs1);
-#pragma unroll
-    for (int x = 0; x < K; ++x) {
-        v0[x] = v2f_val(G, ev, m_old, v0[x], mo0[x], vs0, es0, x);
-        v1[x] = v2f_val(G, ev, m_old, v1[x], mo1[x], vs1, es1, x);
-    }
+    gather_v2f<K>(G, b, ev, m_old, vs0, es0, mo0, v0);
+    gather_v2f<K>(G, b, ev, m_old, vs1, es1, mo1, v1);
     float o0[K], o1[K];
     if constexpr (K <= 4) {
         float phi[K * K];
@@ -498,10 +756,25 @@ k_enum_generic(DevGraph G, const EnumSeg *__restrict__ segs, int n_seg, const fl
     for (int j = 0; j < a; ++j) {
         const int vs = __ldg(G.edge_vs + e_f + j);
         const int es = es_f + Ko[j];
+        float2 hmx = make_float2(-CUDART_INF_F, 0.f);
+        if (vs < 0)
+            for (int x = 0; x < Kj[j]; ++x) {
+                const float2 q = hd_pair(G, es, x);
+                if (x == 0 || hd_gt(q, hmx)) hmx = q;
+            }
+        bool exact = false;
         for (int x = 0; x < Kj[j]; ++x) {
             const float mv = __ldg(m_old + es + x);
             mo[Ko[j] + x] = mv;
-            v2f[Ko[j] + x] = v2f_val(G, ev, m_old, __ldg(b + vs + x), mv, vs, es, x);
+            exact |= needs_exact(mv);
+        }
+        if (vs < 0) {
+            for (int x = 0; x < Kj[j]; ++x)
+                v2f[Ko[j] + x] = hmx.x == -CUDART_INF_F ? -CUDART_INF_F : hd_rel(hd_pair(G, es, x), hmx);
+        } else if (exact) {
+            v2f_slow_edge(G, ev, m_old, vs, es, Kj[j], v2f + Ko[j]);
+        } else {
+            for (int x = 0; x < Kj[j]; ++x) v2f[Ko[j] + x] = __ldg(b + vs + x) - mo[Ko[j] + x];
         }
     }
     for (int i = 0; i < ksum; ++i) {
@@ -572,9 +845,22 @@ __device__ __forceinline__ float edge_logodds(const DevGraph &G, const float *ev
                                               float2 &mo) {
     const int vs = __ldg(G.edge_vs + e);
     mo = ld2(m_old + es);
-    const float2 bb = ld2(b + vs);
-    const float a0 = v2f_val(G, ev, m_old, bb.x, mo.x, vs, es, 0);
-    const float a1 = v2f_val(G, ev, m_old, bb.y, mo.y, vs, es, 1);
+    float a0, a1;
+    if (vs < 0) {
+        float t[2];
+        hd_v2f<2>(G, es, t);
+        a0 = t[0];
+        a1 = t[1];
+    } else if (needs_exact(mo.x) || needs_exact(mo.y)) {
+        float t[2];
+        v2f_slow_edge(G, ev, m_old, vs, es, 2, t);
+        a0 = t[0];
+        a1 = t[1];
+    } else {
+        const float2 bb = ld2(b + vs);
+        a0 = bb.x - mo.x;
+        a1 = bb.y - mo.y;
+    }
     return sgn * log_odds(a0, a1);
 }
 
@@ -592,7 +878,7 @@ k_logic_small(DevGraph G, const LogicSeg *__restrict__ segs, int n_seg, const fl
     const int edge_base = __ldg(&S->edge_base), es_base = __ldg(&S->es_base);
     const int e0 = edge_base + p0 + f;
     const float sgn = __ldg(&S->kind) == 1 ? -1.f : 1.f;
-    float x[kLogicSmallFan + 1], u[kLogicSmallFan + 1];
+    float x[kLogicSmallFan + 1];
     float2 mo[kLogicSmallFan + 1];
 #pragma unroll
     for (int k = 0; k <= kLogicSmallFan; ++k) {
@@ -619,17 +905,18 @@ k_logic_small(DevGraph G, const LogicSeg *__restrict__ segs, int n_seg, const fl
             out[i] = or_parent_max(Si, Mi, xc);
         }
     } else {
-        float Lall = kNegInf;
+        LSum t[kLogicSmallFan + 1];
+        LSum all = lsum_zero();
         for (int j = 0; j < n; ++j) {
-            u[j] = log_softplus(x[j] * invT);
-            Lall = lse2(Lall, u[j]);
+            t[j] = lsum_term(x[j] * invT);
+            all = lsum_add(all, t[j]);
         }
-        out[n] = T * log_expm1_from_log(Lall);
+        out[n] = T * log_expm1_lsum(all);
         for (int i = 0; i < n; ++i) {
-            float Li = kNegInf;
+            LSum li = lsum_zero();
             for (int j = 0; j < n; ++j)
-                if (j != i) Li = lse2(Li, u[j]);
-            out[i] = or_parent_soft(Li, xc, T, invT);
+                if (j != i) li = lsum_add(li, t[j]);
+            out[i] = or_parent_soft(li, xc, T, invT);
         }
     }
     for (int k = 0; k <= n; ++k) {
@@ -638,15 +925,46 @@ k_logic_small(DevGraph G, const LogicSeg *__restrict__ segs, int n_seg, const fl
     }
 }
 
-// Combine operator of the warp scans: (+, max) for T = 0, (LSE, max) for T > 0.
+// Scan element of the warp OR / AND kernel. T = 0: (sum of max(x_j, 0), max x_j).
+// T > 0: the (m, s) pair of a softplus sum (LSum).
+struct ScanEl {
+    float a, b;
+};
+
 template <bool MAXP>
-__device__ __forceinline__ float comb(float a, float b) {
-    if (MAXP) return a + b;
-    return lse2(a, b);
+__device__ __forceinline__ ScanEl scan_ident() {
+    return MAXP ? ScanEl{0.f, kNegInf} : ScanEl{kNegInf, 0.f};
 }
 
-// Warp per factor, any fan-in. Prefix and suffix leave-one-out sums by warp scans over
-// rounds of 32 parents; per-parent values staged in shared memory (4 floats each).
+template <bool MAXP>
+__device__ __forceinline__ ScanEl scan_comb(ScanEl p, ScanEl q) {
+    if (MAXP) return ScanEl{p.a + q.a, fmaxf(p.b, q.b)};
+    LSum r = lsum_add(LSum{p.a, p.b}, LSum{q.a, q.b});
+    return ScanEl{r.m, r.s};
+}
+
+template <bool MAXP>
+__device__ __forceinline__ ScanEl scan_elem(float x, float invT) {
+    if (MAXP) return ScanEl{fmaxf(x, 0.f), x};
+    LSum t = lsum_term(x * invT);
+    return ScanEl{t.m, t.s};
+}
+
+template <bool MAXP>
+__device__ __forceinline__ ScanEl shfl_up_el(ScanEl v, int d) {
+    return ScanEl{__shfl_up_sync(0xffffffffu, v.a, d), __shfl_up_sync(0xffffffffu, v.b, d)};
+}
+template <bool MAXP>
+__device__ __forceinline__ ScanEl shfl_down_el(ScanEl v, int d) {
+    return ScanEl{__shfl_down_sync(0xffffffffu, v.a, d), __shfl_down_sync(0xffffffffu, v.b, d)};
+}
+__device__ __forceinline__ ScanEl shfl_el(ScanEl v, int src) {
+    return ScanEl{__shfl_sync(0xffffffffu, v.a, src), __shfl_sync(0xffffffffu, v.b, src)};
+}
+
+// Warp per factor, any fan-in. Leave-one-out sums as exclusive prefix (first pass) and
+// exclusive suffix (second pass) warp scans over rounds of 32 parents; the log-odds
+// and the prefix of each parent are staged in shared memory (3 floats per parent).
 template <bool MAXP>
 __global__ void __launch_bounds__(128)
 k_logic_warp(DevGraph G, const LogicSeg *__restrict__ segs, int n_seg, const float *__restrict__ b,
@@ -657,94 +975,78 @@ k_logic_warp(DevGraph G, const LogicSeg *__restrict__ segs, int n_seg, const flo
     const LogicSeg *S = segs + find_seg(segs, n_seg, blockIdx.x);
     const int f = (blockIdx.x - __ldg(&S->block_begin)) * warps + warp;
     if (f >= __ldg(&S->n_fac)) return;
-    float *sx = smem + (size_t)warp * 4 * cap;  // x_j
-    float *sv = sx + cap;                        // per-parent value (max(x,0) or log softplus)
-    float *sp = sv + cap;                        // exclusive prefix of values
-    float *sm = sp + cap;                        // exclusive prefix max of x
+    float *sx = smem + (size_t)warp * 3 * cap;  // log-odds x_j (times sgn)
+    float *spa = sx + cap;                       // exclusive prefix, first component
+    float *spb = spa + cap;                      // exclusive prefix, second component
     const int *po = G.paroff_pool + __ldg(&S->paroff_base);
     const int p0 = __ldg(po + f), n = __ldg(po + f + 1) - p0;
     const int edge_base = __ldg(&S->edge_base), es_base = __ldg(&S->es_base);
     const int e0 = edge_base + p0 + f;
     const float sgn = __ldg(&S->kind) == 1 ? -1.f : 1.f;
-    const float ident = MAXP ? 0.f : kNegInf;
+    const ScanEl ident = scan_ident<MAXP>();
     // child
     float2 moc = make_float2(0.f, 0.f);
     float xc = 0.f;
     if (lane == 0) xc = edge_logodds(G, ev, b, m_old, e0 + n, es_base + 2 * (e0 + n - edge_base), sgn, moc);
     xc = __shfl_sync(0xffffffffu, xc, 0);
     // forward pass: exclusive prefix
-    float ca = ident, cm = kNegInf;
+    ScanEl carry = ident;
     for (int base = 0; base < n; base += 32) {
         const int j = base + lane;
         const bool valid = j < n;
-        float xv = 0.f, va = ident, vm = kNegInf;
+        float xv = 0.f;
+        ScanEl v = ident;
         if (valid) {
             float2 mo;
             const int e = e0 + j;
             xv = edge_logodds(G, ev, b, m_old, e, es_base + 2 * (e - edge_base), sgn, mo);
-            va = MAXP ? fmaxf(xv, 0.f) : log_softplus(xv * invT);
-            vm = xv;
+            v = scan_elem<MAXP>(xv, invT);
         }
-        float ia = va, im = vm;
+        ScanEl inc = v;
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
-            const float ya = __shfl_up_sync(0xffffffffu, ia, d);
-            const float ym = __shfl_up_sync(0xffffffffu, im, d);
-            if (lane >= d) {
-                ia = comb<MAXP>(ya, ia);
-                im = fmaxf(ym, im);
-            }
+            const ScanEl y = shfl_up_el<MAXP>(inc, d);
+            if (lane >= d) inc = scan_comb<MAXP>(y, inc);
         }
-        float ea = __shfl_up_sync(0xffffffffu, ia, 1), em = __shfl_up_sync(0xffffffffu, im, 1);
-        if (lane == 0) {
-            ea = ident;
-            em = kNegInf;
-        }
+        ScanEl exc = shfl_up_el<MAXP>(inc, 1);
+        if (lane == 0) exc = ident;
         if (valid) {
+            const ScanEl pre = scan_comb<MAXP>(carry, exc);
             sx[j] = xv;
-            sv[j] = va;
-            sp[j] = comb<MAXP>(ca, ea);
-            sm[j] = fmaxf(cm, em);
+            spa[j] = pre.a;
+            spb[j] = pre.b;
         }
-        ca = comb<MAXP>(ca, __shfl_sync(0xffffffffu, ia, 31));
-        cm = fmaxf(cm, __shfl_sync(0xffffffffu, im, 31));
+        carry = scan_comb<MAXP>(carry, shfl_el(inc, 31));
     }
     __syncwarp();
-    const float out_c = MAXP ? ca + (cm < 0.f ? cm : 0.f) : T * log_expm1_from_log(ca);
+    float out_c;
+    if (MAXP) out_c = carry.a + (carry.b < 0.f ? carry.b : 0.f);
+    else out_c = T * log_expm1_lsum(LSum{carry.a, carry.b});
     // backward pass: exclusive suffix, outputs
-    float sa = ident, smx = kNegInf;
+    ScanEl sc = ident;
     for (int base = n > 0 ? ((n - 1) & ~31) : -32; base >= 0; base -= 32) {
         const int j = base + lane;
         const bool valid = j < n;
-        const float va = valid ? sv[j] : ident;
-        const float vm = valid ? sx[j] : kNegInf;
-        float ra = va, rm = vm;
+        const float xv = valid ? sx[j] : 0.f;
+        const ScanEl v = valid ? scan_elem<MAXP>(xv, invT) : ident;
+        ScanEl inc = v;
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
-            const float ya = __shfl_down_sync(0xffffffffu, ra, d);
-            const float ym = __shfl_down_sync(0xffffffffu, rm, d);
-            if (lane + d < 32) {
-                ra = comb<MAXP>(ra, ya);
-                rm = fmaxf(rm, ym);
-            }
+            const ScanEl y = shfl_down_el<MAXP>(inc, d);
+            if (lane + d < 32) inc = scan_comb<MAXP>(inc, y);
         }
-        float ea = __shfl_down_sync(0xffffffffu, ra, 1), em = __shfl_down_sync(0xffffffffu, rm, 1);
-        if (lane == 31) {
-            ea = ident;
-            em = kNegInf;
-        }
-        ea = comb<MAXP>(ea, sa);
-        em = fmaxf(em, smx);
+        ScanEl exc = shfl_down_el<MAXP>(inc, 1);
+        if (lane == 31) exc = ident;
         if (valid) {
-            const float loo_a = comb<MAXP>(sp[j], ea);
-            const float loo_m = fmaxf(sm[j], em);
-            const float o = MAXP ? or_parent_max(loo_a, loo_m, xc) : or_parent_soft(loo_a, xc, T, invT);
+            const ScanEl suf = scan_comb<MAXP>(exc, sc);
+            const ScanEl loo = scan_comb<MAXP>(ScanEl{spa[j], spb[j]}, suf);
+            const float o = MAXP ? or_parent_max(loo.a, loo.b, xc)
+                                 : or_parent_soft(LSum{loo.a, loo.b}, xc, T, invT);
             const int e = e0 + j;
             const int es = es_base + 2 * (e - edge_base);
             write_logic_edge(sgn * o, ld2(m_old + es), m_new, es, damping, G.flags);
         }
-        sa = comb<MAXP>(sa, __shfl_sync(0xffffffffu, ra, 0));
-        smx = fmaxf(smx, __shfl_sync(0xffffffffu, rm, 0));
+        sc = scan_comb<MAXP>(sc, shfl_el(inc, 0));
     }
     if (lane == 0) {
         const int e = e0 + n;
@@ -774,7 +1076,7 @@ static void var_pass_mode(const DevGraph &G, const Plan &P, const float *ev, con
     for (const VarLaunch &L : P.var) {
         if (L.n == 0) continue;
         if (L.block_mode) {
-            k_var_block<MODE><<<L.n, L.threads, 0, s>>>(G, L.list, ev, m, out, dec);
+            k_var_block<MODE><<<L.n, kVarBlockThreads, 0, s>>>(G, L.list, ev, m, out, dec);
         } else if (P.kfix == 2) {
             k_var_thread<2, MODE><<<L.n_blocks, L.threads, 0, s>>>(G, L.list, L.n, ev, m, out, dec);
         } else {
@@ -785,7 +1087,8 @@ static void var_pass_mode(const DevGraph &G, const Plan &P, const float *ev, con
 
 cudaError_t launch_var_pass(const DevGraph &G, const Plan &P, const float *ev, const float *m,
                             float *b, int mode, int32_t *decode, cudaStream_t s) {
-    if (mode == kVarBeliefs) var_pass_mode<kVarBeliefs>(G, P, ev, m, b, decode, s);
+    if (mode == kVarIter) var_pass_mode<kVarIter>(G, P, ev, m, b, decode, s);
+    else if (mode == kVarBeliefs) var_pass_mode<kVarBeliefs>(G, P, ev, m, b, decode, s);
     else if (mode == kVarNormalised) var_pass_mode<kVarNormalised>(G, P, ev, m, b, decode, s);
     else var_pass_mode<kVarDecode>(G, P, ev, m, b, decode, s);
     return cudaGetLastError();

@@ -19,6 +19,10 @@ constexpr int kMaxArity = 8;
 constexpr int kMaxStateSum = 64;
 constexpr int kMaxStates = 256;
 constexpr int kVarBlockDegree = 64;  // variables with more factors use a block each
+constexpr int kVarBlockThreads = 256;
+constexpr int kVarItems = 8;                               // contiguous edges per thread
+constexpr int kVarTile = kVarBlockThreads * kVarItems;     // edges per tile
+constexpr int kVarMaxTiles = 256;                          // degree limit 524,288
 constexpr int kLogicSmallFan = 4;    // logical groups up to this fan-in: thread per factor
 
 // Factor-pass kernel variants.
@@ -74,6 +78,9 @@ struct DevGraph {
     const uint8_t *cfg_pool;
     const int32_t *paroff_pool;
     uint32_t *flags;         // device status word
+    float *v2f_hd;           // [2 * ES] exact leave-one-out sums, float-float (hi, lo)
+                             // pairs, for edges of high-degree variables (edge_vs = -1);
+                             // null if there are none
 };
 
 struct FactorLaunch {
@@ -138,6 +145,9 @@ cudaError_t launch_factor_pass(const DevGraph &G, const Plan &P, const float *lo
 cudaError_t prepare_kernels(int max_smem_bytes);
 
 // Variable-pass modes.
-enum VarMode : int { kVarBeliefs = 0, kVarNormalised = 1, kVarDecode = 2 };
+// kVarIter: the beliefs the factor pass reads during an iteration, shifted per
+// variable so that its largest state is 0 (plus exact leave-one-out values for
+// high-degree variables); kVarBeliefs: raw beliefs e + sum m.
+enum VarMode : int { kVarBeliefs = 0, kVarNormalised = 1, kVarDecode = 2, kVarIter = 3 };
 
 }  // namespace pgm

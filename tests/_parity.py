@@ -39,3 +39,60 @@ def assert_decode_ok(gpu_dec, ora_nb, num_states, tie=TIE, what=""):
         if b[d] < b.max() - tie:
             bad.append(v)
     assert not bad, f"{what}: decode differs at variables {bad[:10]} (of {len(bad)})"
+
+
+def oracle_envelope(oracle, graph, log_pot, evidence, T, damping, n_iters, k=2, rel=1e-6, seed=12345):
+    """The oracle's normalised log-beliefs and decode, plus their spread over `k` runs
+    whose log-potentials and evidence are multiplied by (1 + rel * N(0,1)) -- input
+    changes of about 8 FP32 ulps. Max-product and long loopy runs amplify such changes
+    far beyond 1e-4; the spread measures how far any FP32 evaluation can be expected
+    to land from the FP64 result."""
+    rng = np.random.default_rng(seed)
+    m0, fl = oracle.run_bp(graph, log_pot, evidence, T, damping, n_iters)
+    _, nb0, dec0, fl2 = oracle.beliefs(graph, evidence, m0)
+    spread = np.zeros_like(nb0)
+    unstable = np.zeros(dec0.shape, bool)
+    for _ in range(k):
+        lp = np.asarray(log_pot, np.float64) * (1 + rel * rng.standard_normal(np.size(log_pot)))
+        ev = np.asarray(evidence, np.float64) * (1 + rel * rng.standard_normal(np.size(evidence)))
+        m1, _ = oracle.run_bp(graph, lp, ev, T, damping, n_iters)
+        _, nb1, dec1, _ = oracle.beliefs(graph, evidence, m1)
+        d = np.abs(nb1 - nb0)
+        d[np.isneginf(nb0) & np.isneginf(nb1)] = 0.0
+        spread = np.maximum(spread, np.nan_to_num(d, nan=np.inf, posinf=np.inf))
+        unstable |= dec1 != dec0
+    return nb0, dec0, spread, unstable, fl | fl2
+
+
+def assert_within_envelope(gpu_nb, gpu_dec, nb0, spread, unstable, num_states, atol=ATOL,
+                           rtol=1e-6, factor=3.0, tie=TIE, what=""):
+    """|gpu - oracle| <= atol + rtol |oracle| + factor * spread, per entry; decodes equal
+    except where the perturbed oracle runs disagree among themselves or at ties."""
+    g = np.asarray(gpu_nb, np.float64)
+    assert not np.isnan(g).any(), f"{what}: NaN in GPU beliefs"
+    both_ninf = np.isneginf(g) & np.isneginf(nb0)
+    tol = atol + rtol * np.abs(np.where(np.isfinite(nb0), nb0, 0.0)) + factor * spread
+    err = np.abs(g - nb0)
+    err[both_ninf] = 0.0
+    bad = np.flatnonzero(~(err <= tol))
+    assert bad.size == 0, (f"{what}: {bad.size} entries outside the envelope, e.g. index {bad[0]}: "
+                           f"gpu {g[bad[0]]:.6g} oracle {nb0[bad[0]]:.6g} spread {spread[bad[0]]:.3g}")
+    vs = np.concatenate([[0], np.cumsum(num_states)])
+    dec = np.asarray(gpu_dec)
+    wrong = []
+    for v in np.flatnonzero(dec != np.asarray(_argmax(nb0, vs))):
+        b = nb0[vs[v]:vs[v + 1]]
+        d = int(dec[v])
+        if unstable[v] or (0 <= d < b.size and b[d] >= b.max() - tie):
+            continue
+        wrong.append(int(v))
+    assert not wrong, f"{what}: decode differs at stable variables {wrong[:10]}"
+    fin = np.isfinite(nb0)
+    return float(err[fin].max()) if fin.any() else 0.0, float(spread[fin].max()) if fin.any() else 0.0
+
+
+def _argmax(nb, vs):
+    out = np.zeros(len(vs) - 1, np.int64)
+    for v in range(len(vs) - 1):
+        out[v] = int(np.argmax(nb[vs[v]:vs[v + 1]]))
+    return out
