@@ -242,7 +242,7 @@ def run_ours(args):
         dist.barrier()
     torch.cuda.synchronize()
     sampler.start()
-    g.set_profiling(PROFILE_PERIOD)
+    g.set_profiling(min(PROFILE_PERIOD, args.iters))
     g.pass_times()  # reset
     step_ms = []
     for _ in range(args.steps):

@@ -70,7 +70,7 @@ def _load():
         lib.og_bp.restype = ctypes.c_int
         lib.og_bp.argtypes = [ctypes.POINTER(_Graph), ctypes.c_void_p, ctypes.c_void_p,
                               ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int,
-                              ctypes.c_void_p, ctypes.c_void_p]
+                              ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
         lib.og_beliefs.restype = ctypes.c_int
         lib.og_beliefs.argtypes = [ctypes.POINTER(_Graph), ctypes.c_void_p, ctypes.c_void_p,
                                    ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
@@ -137,8 +137,9 @@ def sizes(graph) -> dict:
 
 
 def run_bp(graph, log_pot, evidence, T: float, damping: float, n_iters: int,
-           msgs: np.ndarray | None = None, logic_brute: bool = False):
+           msgs: np.ndarray | None = None, logic_brute: bool = False, round_f32: bool = False):
     """Flooding LBP for ``n_iters`` iterations from ``msgs`` (zeros when None).
+    ``round_f32`` rounds the messages to FP32 after every iteration (FP32 storage model).
     Returns (messages [ES] float64, flags)."""
     lib = _load()
     m = _Marshalled(graph)
@@ -150,7 +151,7 @@ def run_bp(graph, log_pot, evidence, T: float, damping: float, n_iters: int,
     ev = np.ascontiguousarray(evidence, np.float64)
     fl = np.zeros(1, np.uint32)
     rc = lib.og_bp(ctypes.byref(m.g), _ptr(lp), _ptr(ev), float(T), float(damping),
-                   int(n_iters), int(logic_brute), _ptr(out), _ptr(fl))
+                   int(n_iters), int(logic_brute), int(round_f32), _ptr(out), _ptr(fl))
     if rc != 0:
         raise ValueError("oracle: invalid T, damping or n_iters")
     return out[:ES], int(fl[0])

@@ -426,10 +426,14 @@ int og_sizes(const og_graph *g, int64_t *out6) {
 
 /*
  * n_iters flooding iterations starting from the messages in msgs ([ES], in/out; zeros
- * for a cold start). logic_brute = 1 evaluates logical factors by brute force.
+ * for a cold start). use_brute = 1 evaluates logical factors by brute force.
+ * round_f32 = 1 rounds the messages to FP32 after every iteration (the arithmetic stays
+ * FP64): a model of FP32 message storage, used to measure how far FP32 storage alone
+ * moves a run.
  */
 int og_bp(const og_graph *g, const double *log_pot, const double *evidence, double T,
-          double damping, int n_iters, int use_brute, double *msgs, uint32_t *flags) {
+          double damping, int n_iters, int use_brute, int round_f32, double *msgs,
+          uint32_t *flags) {
     if (T < 0.0 || damping < 0.0 || damping >= 1.0 || n_iters < 0) return -1;
     og_layout L;
     layout_build(g, &L);
@@ -471,6 +475,9 @@ int og_bp(const og_graph *g, const double *log_pot, const double *evidence, doub
         }
         fl |= itfl;
         memcpy(msgs, mt, sizeof(double) * (size_t)L.ES);
+        /* storage model of an implementation that keeps its messages in FP32 */
+        if (round_f32)
+            for (int64_t i = 0; i < L.ES; ++i) msgs[i] = (double)(float)msgs[i];
     }
     if (flags) *flags |= fl;
     free(v2f);

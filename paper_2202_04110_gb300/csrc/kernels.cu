@@ -36,7 +36,6 @@ constexpr uint32_t kFlagContradiction = 1u;
 constexpr uint32_t kFlagNaN = 2u;
 
 #define kNegInf (-CUDART_INF_F)
-__device__ __forceinline__ float pos_inf() { return CUDART_INF_F; }
 
 template <class Seg>
 __device__ __forceinline__ int find_seg(const Seg *__restrict__ segs, int n, int blk) {
@@ -260,72 +259,60 @@ __device__ __forceinline__ void gather_v2f(const DevGraph &G, const float *__res
 
 // ---- log-sum-exp helpers -------------------------------------------------------------
 
+
+// T > 0 logical factors: the closed forms chain several exp / log evaluations per edge;
+// in FP32 their rounding errors are biased, which long runs on logical-factor graphs
+// amplify. They are therefore evaluated in FP64 from the FP32 inputs (the outputs are
+// rounded once to FP32). Sums of softplus terms s(x_j / T) are kept as logarithms,
+// log A = LSE_j log s(x_j / T), so that very negative log-odds do not underflow.
+
 // log(s(u)), s(u) = log(1 + e^u)
-__device__ __forceinline__ float log_softplus(float u) {
-    if (u < -15.f) return u + log1pf(-0.5f * expf(u));
-    if (u > 0.f) return logf(u + log1pf(expf(-u)));
-    return logf(log1pf(expf(u)));
+__device__ __forceinline__ double log_softplus_d(double u) {
+    if (u < -30.0) return u + log1p(-0.5 * exp(u));
+    if (u > 0.0) return log(u + log1p(exp(-u)));
+    return log(log1p(exp(u)));
 }
 
-// Sums of softplus terms t_j = s(x_j / T) for the T > 0 OR update, kept as a pair
-// (m, s) with value s * exp(m): m is the largest log t_j seen, s a linear sum relative
-// to it. Linear precision when the terms are moderate, and no underflow when they are
-// tiny (very negative log-odds, where t_j ~ exp(x_j / T)).
-struct LSum {
-    float m, s;
-};
-
-__device__ __forceinline__ LSum lsum_zero() { return LSum{kNegInf, 0.f}; }
-
-__device__ __forceinline__ LSum lsum_add(LSum a, LSum b) {
-    const float M = fmaxf(a.m, b.m);
-    if (M == kNegInf) return lsum_zero();
-    if (M == pos_inf()) return LSum{pos_inf(), 1.f};
-    float s = 0.f;
-    if (a.s != 0.f) s += a.s * expf(a.m - M);
-    if (b.s != 0.f) s += b.s * expf(b.m - M);
-    return LSum{M, s};
+__device__ __forceinline__ double lse2_d(double a, double b) {
+    const double mx = fmax(a, b);
+    if (mx == -CUDART_INF || mx == CUDART_INF) return mx;
+    return mx + log1p(exp(fmin(a, b) - mx));
 }
 
-// one term: log t(u) with t(u) = log(1 + e^u) (u = x / T)
-__device__ __forceinline__ LSum lsum_term(float u) {
-    if (u == kNegInf) return lsum_zero();
-    return LSum{log_softplus(u), 1.f};
+// log(e^a - 1) from la = log a
+__device__ __forceinline__ double log_expm1_from_log_d(double la) {
+    if (la == -CUDART_INF) return -CUDART_INF;
+    if (la == CUDART_INF) return CUDART_INF;
+    if (la > 0.0) {
+        const double a = exp(la);
+        return a + log(-expm1(-a));
+    }
+    if (la > -700.0) {
+        const double a = exp(la);
+        return la + log(expm1(a) / a);
+    }
+    return la;
 }
 
-// log(e^a - 1) for the sum a = s * exp(m)
-__device__ __forceinline__ float log_expm1_lsum(LSum A) {
-    if (A.s == 0.f) return kNegInf;
-    const float la = A.m + logf(A.s);
-    if (la == pos_inf()) return pos_inf();
-    if (la < -20.f) return la;  // a < 2e-9: log(expm1(a)) = log(a) + a/2 + ...
-    const float a = A.s * expf(A.m);
-    if (a > 20.f) return a + log1pf(-expf(-a));
-    return logf(expm1f(a));
+// -log(1 - e^{-a}) from la = log a
+__device__ __forceinline__ double neg_log_1mexp_from_log_d(double la) {
+    if (la == CUDART_INF) return 0.0;
+    if (la > 0.0) return -log(-expm1(-exp(la)));
+    if (la > -700.0) {
+        const double a = exp(la);
+        return -la - log(-expm1(-a) / a);
+    }
+    return -la;
 }
 
-// -log(1 - e^{-a}) for the sum a = s * exp(m)
-__device__ __forceinline__ float neg_log_1mexp_lsum(LSum A) {
-    const float la = A.m + logf(A.s);
-    if (la == pos_inf()) return 0.f;
-    if (la < -20.f) return -la;
-    const float a = A.s * expf(A.m);
-    if (a > 20.f) return -log1pf(-expf(-a));
-    return -logf(-expm1f(-a));
-}
-
-__device__ __forceinline__ float lsum_value(LSum A) {
-    if (A.s == 0.f) return 0.f;
-    return A.s * expf(A.m);
-}
-
-// OR update to parent i (T > 0): A = leave-one-out softplus sum (units of T), xc =
-// child log-odds.
-__device__ __forceinline__ float or_parent_soft(LSum A, float xc, float T, float invT) {
-    if (A.s == 0.f) return xc;
-    const float y = xc + T * log_expm1_lsum(A);
-    if (y >= 0.f) return T * neg_log_1mexp_lsum(A) - T * log1pf(expf(-y * invT));
-    return xc + T * lsum_value(A) - T * log1pf(expf(y * invT));
+// OR update to parent i (T > 0): la = log of the leave-one-out softplus sum (units of
+// T), xc = child log-odds.
+__device__ __forceinline__ float or_parent_soft(double la, float xc_f, double T) {
+    const double xc = xc_f;
+    if (la == -CUDART_INF) return xc_f;
+    const double y = xc + T * log_expm1_from_log_d(la);
+    if (y >= 0.0) return (float)(T * neg_log_1mexp_from_log_d(la) - T * log1p(exp(-y / T)));
+    return (float)(xc + T * exp(la) - T * log1p(exp(y / T)));
 }
 
 // OR update to parent i (T = 0): S = leave-one-out sum of max(x_j, 0), M = leave-one-out max.
@@ -905,18 +892,19 @@ k_logic_small(DevGraph G, const LogicSeg *__restrict__ segs, int n_seg, const fl
             out[i] = or_parent_max(Si, Mi, xc);
         }
     } else {
-        LSum t[kLogicSmallFan + 1];
-        LSum all = lsum_zero();
+        const double Td = T;
+        double t[kLogicSmallFan + 1];
+        double all = -CUDART_INF;
         for (int j = 0; j < n; ++j) {
-            t[j] = lsum_term(x[j] * invT);
-            all = lsum_add(all, t[j]);
+            t[j] = (x[j] == kNegInf) ? -CUDART_INF : log_softplus_d((double)x[j] / Td);
+            all = lse2_d(all, t[j]);
         }
-        out[n] = T * log_expm1_lsum(all);
+        out[n] = (float)(Td * log_expm1_from_log_d(all));
         for (int i = 0; i < n; ++i) {
-            LSum li = lsum_zero();
+            double li = -CUDART_INF;
             for (int j = 0; j < n; ++j)
-                if (j != i) li = lsum_add(li, t[j]);
-            out[i] = or_parent_soft(li, xc, T, invT);
+                if (j != i) li = lse2_d(li, t[j]);
+            out[i] = or_parent_soft(li, xc, Td);
         }
     }
     for (int k = 0; k <= n; ++k) {
@@ -925,29 +913,35 @@ k_logic_small(DevGraph G, const LogicSeg *__restrict__ segs, int n_seg, const fl
     }
 }
 
-// Scan element of the warp OR / AND kernel. T = 0: (sum of max(x_j, 0), max x_j).
-// T > 0: the (m, s) pair of a softplus sum (LSum).
+// Scan element of the warp OR / AND kernel. T = 0: (a, b) = (sum of max(x_j, 0),
+// max x_j) in FP32. T > 0: a single FP64 log-sum (LSE of log s(x_j / T)) held in the
+// bits of (a, b).
 struct ScanEl {
     float a, b;
 };
 
+__device__ __forceinline__ double el_d(ScanEl e) {
+    return __hiloint2double(__float_as_int(e.a), __float_as_int(e.b));
+}
+__device__ __forceinline__ ScanEl d_el(double d) {
+    return ScanEl{__int_as_float(__double2hiint(d)), __int_as_float(__double2loint(d))};
+}
+
 template <bool MAXP>
 __device__ __forceinline__ ScanEl scan_ident() {
-    return MAXP ? ScanEl{0.f, kNegInf} : ScanEl{kNegInf, 0.f};
+    return MAXP ? ScanEl{0.f, kNegInf} : d_el(-CUDART_INF);
 }
 
 template <bool MAXP>
 __device__ __forceinline__ ScanEl scan_comb(ScanEl p, ScanEl q) {
     if (MAXP) return ScanEl{p.a + q.a, fmaxf(p.b, q.b)};
-    LSum r = lsum_add(LSum{p.a, p.b}, LSum{q.a, q.b});
-    return ScanEl{r.m, r.s};
+    return d_el(lse2_d(el_d(p), el_d(q)));
 }
 
 template <bool MAXP>
-__device__ __forceinline__ ScanEl scan_elem(float x, float invT) {
+__device__ __forceinline__ ScanEl scan_elem(float x, double T) {
     if (MAXP) return ScanEl{fmaxf(x, 0.f), x};
-    LSum t = lsum_term(x * invT);
-    return ScanEl{t.m, t.s};
+    return d_el(x == kNegInf ? -CUDART_INF : log_softplus_d((double)x / T));
 }
 
 template <bool MAXP>
@@ -1000,7 +994,7 @@ k_logic_warp(DevGraph G, const LogicSeg *__restrict__ segs, int n_seg, const flo
             float2 mo;
             const int e = e0 + j;
             xv = edge_logodds(G, ev, b, m_old, e, es_base + 2 * (e - edge_base), sgn, mo);
-            v = scan_elem<MAXP>(xv, invT);
+            v = scan_elem<MAXP>(xv, (double)T);
         }
         ScanEl inc = v;
 #pragma unroll
@@ -1021,14 +1015,14 @@ k_logic_warp(DevGraph G, const LogicSeg *__restrict__ segs, int n_seg, const flo
     __syncwarp();
     float out_c;
     if (MAXP) out_c = carry.a + (carry.b < 0.f ? carry.b : 0.f);
-    else out_c = T * log_expm1_lsum(LSum{carry.a, carry.b});
+    else out_c = (float)((double)T * log_expm1_from_log_d(el_d(carry)));
     // backward pass: exclusive suffix, outputs
     ScanEl sc = ident;
     for (int base = n > 0 ? ((n - 1) & ~31) : -32; base >= 0; base -= 32) {
         const int j = base + lane;
         const bool valid = j < n;
         const float xv = valid ? sx[j] : 0.f;
-        const ScanEl v = valid ? scan_elem<MAXP>(xv, invT) : ident;
+        const ScanEl v = valid ? scan_elem<MAXP>(xv, (double)T) : ident;
         ScanEl inc = v;
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
@@ -1040,8 +1034,7 @@ k_logic_warp(DevGraph G, const LogicSeg *__restrict__ segs, int n_seg, const flo
         if (valid) {
             const ScanEl suf = scan_comb<MAXP>(exc, sc);
             const ScanEl loo = scan_comb<MAXP>(ScanEl{spa[j], spb[j]}, suf);
-            const float o = MAXP ? or_parent_max(loo.a, loo.b, xc)
-                                 : or_parent_soft(LSum{loo.a, loo.b}, xc, T, invT);
+            const float o = MAXP ? or_parent_max(loo.a, loo.b, xc) : or_parent_soft(el_d(loo), xc, (double)T);
             const int e = e0 + j;
             const int es = es_base + 2 * (e - edge_base);
             write_logic_edge(sgn * o, ld2(m_old + es), m_new, es, damping, G.flags);
