@@ -211,6 +211,37 @@ pgm_status pgm_pass_times(pgm_graph *g, double *var_ms, double *factor_ms, int64
  */
 pgm_status pgm_device_flags(pgm_graph *g, uint32_t *flags, int32_t clear, void *stream);
 
+/*
+ * Allocation-free LBP on a rows x cols grid of binary variables with one pairwise factor
+ * per pair of 4-neighbours. The paper has no counterpart: this entry point exists for
+ * callers that cannot allocate device memory -- a process whose device memory is owned
+ * and budgeted by a host framework, or code that must not call cudaMalloc / cudaFree
+ * after start-up -- and so cannot use pgm_build / pgm_run_bp, which allocate the graph's
+ * index arrays and scratch. It needs no graph object and allocates nothing: the grid
+ * topology is computed from (row, column), and the scratch (the partner of `msgs` in the
+ * ping-pong of iterations, the per-iteration beliefs, a status word) is one static
+ * device array of PGM_NOALLOC_SCRATCH_FLOATS floats (16 MiB), which every GPU that loads
+ * this library holds until the process exits.
+ *   Layout (the graph pgm_build makes from the same grid with its factors listed cell by
+ *   cell, row-major, each cell's right pair then its down pair): factor f has
+ *   log_pot[4f .. 4f+3] over the configurations (0,0),(0,1),(1,0),(1,1) and messages
+ *   msgs[4f .. 4f+1] (to the cell) and msgs[4f+2 .. 4f+3] (to the right or lower
+ *   neighbour); evidence is [2 * rows * cols]. All pointers are device memory owned by
+ *   the caller (log_pot and msgs 16-byte aligned, evidence 8-byte aligned); msgs is
+ *   in/out as in pgm_run_bp, whose iteration this is.
+ *   Limit: 4 * n_factors + 2 * rows * cols <= PGM_NOALLOC_SCRATCH_FLOATS (for example a
+ *   632 x 632 grid); larger grids return PGM_EINVAL with the sizes in pgm_last_error().
+ *   The first call on a device looks up the array's device address
+ *   (cudaGetSymbolAddress) with that device current; make that first call before any
+ *   stream capture. Every call on a device shares the one array, so calls whose work
+ *   overlaps on the GPU (different streams, or different host threads) race and corrupt
+ *   each other's results: serialise them.
+ */
+#define PGM_NOALLOC_SCRATCH_FLOATS 4194304
+pgm_status pgm_grid2_run_bp_noalloc(int32_t rows, int32_t cols, const float *log_pot,
+                                    const float *evidence, float T, float damping,
+                                    int32_t n_iters, float *msgs, void *stream);
+
 /* Thread-local description of the calling thread's last error ("" if none). */
 const char *pgm_last_error(void);
 

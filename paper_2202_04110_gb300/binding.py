@@ -23,7 +23,7 @@ FLAG_NAN = 2
 # Every symbol include/pgm.h declares.
 EXPORTED = ["pgm_build", "pgm_check_desc", "pgm_free", "pgm_graph_info", "pgm_run_bp", "pgm_beliefs",
             "pgm_decode", "pgm_infer_host", "pgm_set_profiling", "pgm_pass_times",
-            "pgm_device_flags", "pgm_last_error"]
+            "pgm_device_flags", "pgm_grid2_run_bp_noalloc", "pgm_last_error"]
 
 
 class PgmError(RuntimeError):
@@ -94,6 +94,8 @@ def load_library(path: str | None = None):
                                    ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
     lib.pgm_device_flags.restype = i32
     lib.pgm_device_flags.argtypes = [vp, ctypes.POINTER(ctypes.c_uint32), i32, vp]
+    lib.pgm_grid2_run_bp_noalloc.restype = i32
+    lib.pgm_grid2_run_bp_noalloc.argtypes = [i32, i32, vp, vp, f32, f32, i32, vp, vp]
     lib.pgm_last_error.restype = ctypes.c_char_p
     lib.pgm_last_error.argtypes = []
     _lib = lib
@@ -261,6 +263,22 @@ class Graph:
         f = ctypes.c_uint32(0)
         check(load_library().pgm_device_flags(self._h, ctypes.byref(f), int(bool(clear)), _stream_ptr(stream)))
         return int(f.value)
+
+
+NOALLOC_SCRATCH_FLOATS = 4194304
+
+
+def grid2_run_bp_noalloc(rows: int, cols: int, log_pot, evidence, T: float, damping: float,
+                         n_iters: int, msgs, stream=None):
+    """pgm_grid2_run_bp_noalloc: in-place LBP on a rows x cols binary grid with caller-owned
+    CUDA tensors and no device allocation by the library (scratch in a static array)."""
+    import torch
+    F = rows * (cols - 1) + (rows - 1) * cols
+    check(load_library().pgm_grid2_run_bp_noalloc(
+        int(rows), int(cols), _dptr(log_pot, torch.float32, 4 * F, "log_pot") if F else 0,
+        _dptr(evidence, torch.float32, 2 * rows * cols, "evidence"), float(T), float(damping),
+        int(n_iters), _dptr(msgs, torch.float32, 4 * F, "msgs") if F else 0, _stream_ptr(stream)))
+    return msgs
 
 
 def infer(problem, n_iters: int | None = None, T: float | None = None, graph: Graph | None = None):

@@ -1,6 +1,6 @@
 """Builds libpgm.so in-tree with nvcc for sm_103a (GB300).
 
-Three translation units are compiled in parallel and linked into one shared library
+The translation units are compiled in parallel and linked into one shared library
 that exports the C ABI of include/pgm.h.
 """
 from __future__ import annotations
@@ -15,7 +15,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD_DIR = os.path.join(HERE, "_build")
 LIB_PATH = os.path.join(HERE, "libpgm.so")
-SOURCES = ["compile.cpp", "kernels.cu", "capi.cu"]
+SOURCES = ["compile.cpp", "kernels.cu", "capi.cu", "noalloc.cu"]
 HEADERS = [os.path.join(CSRC, "pgm_internal.h"), os.path.join(ROOT, "include", "pgm.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -45,6 +45,8 @@ size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 }  // namespace
 
+int32_t pgm::set_last_error(int32_t code, const std::string &msg) { return fail(code, msg); }
+
 struct pgm_graph {
     int device = 0;
     pgm_info info{};

@@ -144,6 +144,9 @@ cudaError_t launch_factor_pass(const DevGraph &G, const Plan &P, const float *lo
 // Configure kernel attributes (large dynamic shared memory) once per process/device.
 cudaError_t prepare_kernels(int max_smem_bytes);
 
+// Records `msg` as the calling thread's last error (pgm_last_error) and returns `code`.
+int32_t set_last_error(int32_t code, const std::string &msg);
+
 // Variable-pass modes.
 // kVarIter: the beliefs the factor pass reads during an iteration, shifted per
 // variable so that its largest state is 0 (plus exact leave-one-out values for
