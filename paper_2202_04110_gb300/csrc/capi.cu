@@ -224,6 +224,7 @@ pgm_status pgm_build(const pgm_graph_desc *desc, pgm_graph **out) {
     size_t o_edge_vs = pk.add(H.edge_vs.data(), H.edge_vs.size());
     size_t o_cfg = pk.add(H.cfg_pool.data(), H.cfg_pool.size());
     size_t o_po = pk.add(H.paroff_pool.data(), H.paroff_pool.size());
+    size_t o_tab4 = H.vin_tab4.empty() ? 0 : pk.add(H.vin_tab4.data(), H.vin_tab4.size());
     std::vector<size_t> seg_off;
     std::vector<int> seg_kind;
     pgm_status st = build_plan(H, g, pk, seg_off, seg_kind);
@@ -274,6 +275,7 @@ pgm_status pgm_build(const pgm_graph_desc *desc, pgm_graph **out) {
     G.edge_vs = reinterpret_cast<const int32_t *>(dmem + o_edge_vs);
     G.cfg_pool = reinterpret_cast<const uint8_t *>(dmem + o_cfg);
     G.paroff_pool = reinterpret_cast<const int32_t *>(dmem + o_po);
+    G.vin_tab4 = H.vin_tab4.empty() ? nullptr : reinterpret_cast<const int4 *>(dmem + o_tab4);
     G.flags = flags;
     G.v2f_hd = hd_bytes ? reinterpret_cast<float *>(smem + es_bytes + vs_bytes + 256) : nullptr;
     // attach device pointers of the launch lists / segments

@@ -238,6 +238,15 @@ std::string compile_graph(const void *vdesc, HostLayout *L) {
     L->all_binary = (kmax == 2);
     for (int64_t v = 0; v < V && L->all_binary; ++v)
         if (K[v] != 2) L->all_binary = false;
+    // binary graphs whose variables all have at most 4 factors (grids): a padded table of
+    // incoming edge-states, one 16-byte row per variable
+    L->vin_tab4.clear();
+    if (L->all_binary && maxdeg <= 4) {
+        L->vin_tab4.assign(4 * V, -1);
+        for (int64_t v = 0; v < V; ++v)
+            for (int32_t k = L->vin_off[v]; k < L->vin_off[v + 1]; ++k)
+                L->vin_tab4[4 * v + (k - L->vin_off[v])] = L->vin_es[k];
+    }
     return "";
 }
 

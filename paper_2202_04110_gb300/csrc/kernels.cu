@@ -377,7 +377,8 @@ __device__ __forceinline__ float lse_row(const float (&z)[K], float T, float inv
     for (int y = 0; y < K; ++y) mx = fmaxf(mx, z[y]);
     if (MAXP || mx == kNegInf) return mx;
     if constexpr (K == 2) {
-        return mx + T * log1pf(expf((fminf(z[0], z[1]) - mx) * invT));
+        // log(1 + e^-d), d >= 0, with the SFU exp2 / log2 (absolute error below 3e-7)
+        return mx + T * __logf(1.f + __expf((fminf(z[0], z[1]) - mx) * invT));
     } else {
         float s = 0.f;
 #pragma unroll
@@ -481,6 +482,59 @@ __global__ void __launch_bounds__(256) k_var_thread(DevGraph G, const int32_t *_
                 const float z = logf(acc);
                 for (int x = 0; x < K; ++x) out[vs + x] -= z;
             }
+        }
+    }
+}
+
+// Thread per variable for binary graphs whose variables all have at most 4 factors:
+// one 16-byte row of incoming edge-states per variable (-1 = none), all four message
+// gathers issued before the compensated sums (in ascending edge order, as the CSR path).
+template <int MODE>
+__global__ void __launch_bounds__(256) k_var_tab4(DevGraph G, int n, const float *__restrict__ ev,
+                                                  const float *__restrict__ m, float *__restrict__ out,
+                                                  int32_t *__restrict__ dec) {
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= n) return;
+    const int4 t = __ldcs(G.vin_tab4 + v);
+    const float2 e = __ldcs(reinterpret_cast<const float2 *>(ev) + v);
+    const float2 z = make_float2(0.f, 0.f);
+    const float2 q0 = t.x >= 0 ? __ldg(reinterpret_cast<const float2 *>(m + t.x)) : z;
+    const float2 q1 = t.y >= 0 ? __ldg(reinterpret_cast<const float2 *>(m + t.y)) : z;
+    const float2 q2 = t.z >= 0 ? __ldg(reinterpret_cast<const float2 *>(m + t.z)) : z;
+    const float2 q3 = t.w >= 0 ? __ldg(reinterpret_cast<const float2 *>(m + t.w)) : z;
+    FF s0 = ff_make(e.x), s1 = ff_make(e.y);
+    if (t.x >= 0) { s0 = ff_add(s0, q0.x); s1 = ff_add(s1, q0.y); }
+    if (t.y >= 0) { s0 = ff_add(s0, q1.x); s1 = ff_add(s1, q1.y); }
+    if (t.z >= 0) { s0 = ff_add(s0, q2.x); s1 = ff_add(s1, q2.y); }
+    if (t.w >= 0) { s0 = ff_add(s0, q3.x); s1 = ff_add(s1, q3.y); }
+    if constexpr (MODE == kVarDecode) {
+        dec[v] = ff_gt(s1, s0) ? 1 : 0;
+        return;
+    }
+    if constexpr (MODE == kVarBeliefs) {
+        reinterpret_cast<float2 *>(out)[v] = make_float2(s0.hi + s0.lo, s1.hi + s1.lo);
+        return;
+    }
+    float r0, r1;
+    if (s0.hi == kNegInf && s1.hi == kNegInf) {
+        r0 = r1 = kNegInf;
+    } else if (ff_gt(s1, s0)) {
+        r0 = ff_diff(s0, s1);
+        r1 = 0.f;
+    } else {
+        r0 = 0.f;
+        r1 = ff_diff(s1, s0);
+    }
+    if constexpr (MODE == kVarIter) {
+        reinterpret_cast<float2 *>(out)[v] = make_float2(r0, r1);
+    } else {
+        if (r0 == kNegInf && r1 == kNegInf) {
+            atomicOr(G.flags, kFlagContradiction);
+            reinterpret_cast<float2 *>(out)[v] = make_float2(kNegInf, kNegInf);
+        } else {
+            if (r0 != r0 || r1 != r1) atomicOr(G.flags, kFlagNaN);
+            const float zz = log1pf(expf(fminf(r0, r1)));
+            reinterpret_cast<float2 *>(out)[v] = make_float2(r0 - zz, r1 - zz);
         }
     }
 }
@@ -642,44 +696,22 @@ __global__ void __launch_bounds__(kVarBlockThreads) k_var_block(DevGraph G, cons
 // Factor pass: dense pairwise tables (Ising, RBM, Potts), thread per factor
 // =====================================================================================
 
+// The factor-to-variable update of one dense pairwise factor from its two
+// variable-to-factor vectors v0, v1 and stored messages mo0, mo1; writes the damped,
+// normalised messages.
 template <int K, bool MAXP>
-__global__ void __launch_bounds__(K >= 16 ? 128 : 256)
-k_pair(DevGraph G, const EnumSeg *__restrict__ segs, int n_seg, const float *__restrict__ pot,
-       const float *__restrict__ b, const float *__restrict__ ev, const float *__restrict__ m_old,
-       float *__restrict__ m_new, float T, float invT, float damping) {
-    __shared__ float tab[K * K];
-    const EnumSeg *S = segs + find_seg(segs, n_seg, blockIdx.x);
-    const int n_fac = __ldg(&S->n_fac), shared = __ldg(&S->shared), pot_base = __ldg(&S->pot_base);
-    if (shared) {
-        for (int i = threadIdx.x; i < K * K; i += blockDim.x) tab[i] = __ldg(pot + pot_base + i);
-        __syncthreads();
-    }
-    const int f = (blockIdx.x - __ldg(&S->block_begin)) * blockDim.x + threadIdx.x;
-    if (f >= n_fac) return;
-    const int e = __ldg(&S->edge_base) + 2 * f;
-    const int es0 = __ldg(&S->es_base) + 2 * K * f, es1 = es0 + K;
-    int vs0, vs1;
-    if ((e & 1) == 0) {
-        int2 q = __ldg(reinterpret_cast<const int2 *>(G.edge_vs + e));
-        vs0 = q.x;
-        vs1 = q.y;
-    } else {
-        vs0 = __ldg(G.edge_vs + e);
-        vs1 = __ldg(G.edge_vs + e + 1);
-    }
-    float mo0[K], mo1[K], v0[K], v1[K];
-    load_n_stream<K>(mo0, m_old + es0);
-    load_n_stream<K>(mo1, m_old + es1);
-    gather_v2f<K>(G, b, ev, m_old, vs0, es0, mo0, v0);
-    gather_v2f<K>(G, b, ev, m_old, vs1, es1, mo1, v1);
+__device__ __forceinline__ void pair_update(const float *phi_sh, const float *phi_g, float (&v0)[K],
+                                            float (&v1)[K], const float (&mo0)[K], const float (&mo1)[K],
+                                            float *m_new0, float *m_new1, float T, float invT,
+                                            float damping, uint32_t *flags) {
     float o0[K], o1[K];
     if constexpr (K <= 4) {
         float phi[K * K];
-        if (shared) {
+        if (phi_sh) {
 #pragma unroll
-            for (int i = 0; i < K * K; ++i) phi[i] = tab[i];
+            for (int i = 0; i < K * K; ++i) phi[i] = phi_sh[i];
         } else {
-            load_n<K * K>(phi, pot + pot_base + (size_t)f * (K * K));
+            load_n_stream<K * K>(phi, phi_g);
         }
 #pragma unroll
         for (int x = 0; x < K; ++x) {
@@ -696,26 +728,90 @@ k_pair(DevGraph G, const EnumSeg *__restrict__ segs, int n_seg, const float *__r
             o1[y] = lse_row<K, MAXP>(z, T, invT);
         }
     } else {
-        const float *phig = pot + pot_base + (size_t)f * (K * K);
 #pragma unroll
         for (int x = 0; x < K; ++x) {
             float z[K];
 #pragma unroll
-            for (int y = 0; y < K; ++y) z[y] = (shared ? tab[x * K + y] : __ldg(phig + x * K + y)) + v1[y];
+            for (int y = 0; y < K; ++y) z[y] = (phi_sh ? phi_sh[x * K + y] : __ldg(phi_g + x * K + y)) + v1[y];
             o0[x] = lse_row<K, MAXP>(z, T, invT);
         }
 #pragma unroll
         for (int y = 0; y < K; ++y) {
             float z[K];
 #pragma unroll
-            for (int x = 0; x < K; ++x) z[x] = (shared ? tab[x * K + y] : __ldg(phig + x * K + y)) + v0[x];
+            for (int x = 0; x < K; ++x) z[x] = (phi_sh ? phi_sh[x * K + y] : __ldg(phi_g + x * K + y)) + v0[x];
             o1[y] = lse_row<K, MAXP>(z, T, invT);
         }
     }
-    finish_k<K>(o0, mo0, damping, G.flags);
-    finish_k<K>(o1, mo1, damping, G.flags);
-    store_n<K>(m_new + es0, o0);
-    store_n<K>(m_new + es1, o1);
+    finish_k<K>(o0, mo0, damping, flags);
+    finish_k<K>(o1, mo1, damping, flags);
+    store_n<K>(m_new0, o0);
+    store_n<K>(m_new1, o1);
+}
+
+// The rare case of a pairwise factor: an edge of a high-degree variable, or a stored
+// message entry that is -inf or large. Kept out of line so that the common path holds
+// no state across a call.
+template <int K, bool MAXP>
+__device__ __noinline__ void pair_factor_rare(const DevGraph G, const float *phi_sh, const float *phi_g,
+                                              const float *b, const float *ev, const float *m_old,
+                                              float *m_new, int vs0, int vs1, int es0, int es1, float T,
+                                              float invT, float damping) {
+    float mo0[K], mo1[K], v0[K], v1[K];
+    load_n<K>(mo0, m_old + es0);
+    load_n<K>(mo1, m_old + es1);
+    gather_v2f<K>(G, b, ev, m_old, vs0, es0, mo0, v0);
+    gather_v2f<K>(G, b, ev, m_old, vs1, es1, mo1, v1);
+    pair_update<K, MAXP>(phi_sh, phi_g, v0, v1, mo0, mo1, m_new + es0, m_new + es1, T, invT, damping, G.flags);
+}
+
+// Dense pairwise tables (Ising, RBM, Potts): thread per factor.
+template <int K, bool MAXP>
+__global__ void __launch_bounds__(K >= 16 ? 128 : 256, K == 2 ? 8 : 1)
+k_pair(DevGraph G, const EnumSeg *__restrict__ segs, int n_seg, const float *__restrict__ pot,
+       const float *__restrict__ b, const float *__restrict__ ev, const float *__restrict__ m_old,
+       float *__restrict__ m_new, float T, float invT, float damping) {
+    __shared__ float tab[K * K];
+    const EnumSeg *S = segs + find_seg(segs, n_seg, blockIdx.x);
+    const int n_fac = __ldg(&S->n_fac), shared = __ldg(&S->shared), pot_base = __ldg(&S->pot_base);
+    if (shared) {
+        for (int i = threadIdx.x; i < K * K; i += blockDim.x) tab[i] = __ldg(pot + pot_base + i);
+        __syncthreads();
+    }
+    const int f = (blockIdx.x - __ldg(&S->block_begin)) * blockDim.x + threadIdx.x;
+    if (f >= n_fac) return;
+    const int e = __ldg(&S->edge_base) + 2 * f;
+    const int es0 = __ldg(&S->es_base) + 2 * K * f, es1 = es0 + K;
+    int vs0, vs1;
+    if ((e & 1) == 0) {
+        const int2 q = __ldcs(reinterpret_cast<const int2 *>(G.edge_vs + e));
+        vs0 = q.x;
+        vs1 = q.y;
+    } else {
+        vs0 = __ldcs(G.edge_vs + e);
+        vs1 = __ldcs(G.edge_vs + e + 1);
+    }
+    const float *phi_sh = shared ? tab : nullptr;
+    const float *phi_g = pot + pot_base + (size_t)f * (K * K);
+    float mo0[K], mo1[K];
+    load_n<K>(mo0, m_old + es0);
+    load_n<K>(mo1, m_old + es1);
+    bool rare = (vs0 < 0) | (vs1 < 0);
+#pragma unroll
+    for (int x = 0; x < K; ++x) rare |= needs_exact(mo0[x]) | needs_exact(mo1[x]);
+    if (rare) {
+        pair_factor_rare<K, MAXP>(G, phi_sh, phi_g, b, ev, m_old, m_new, vs0, vs1, es0, es1, T, invT, damping);
+        return;
+    }
+    float v0[K], v1[K];
+    load_n<K>(v0, b + vs0);
+    load_n<K>(v1, b + vs1);
+#pragma unroll
+    for (int x = 0; x < K; ++x) {
+        v0[x] -= mo0[x];
+        v1[x] -= mo1[x];
+    }
+    pair_update<K, MAXP>(phi_sh, phi_g, v0, v1, mo0, mo1, m_new + es0, m_new + es1, T, invT, damping, G.flags);
 }
 
 // =====================================================================================
@@ -1066,6 +1162,11 @@ cudaError_t prepare_kernels(int max_smem_bytes) {
 template <int MODE>
 static void var_pass_mode(const DevGraph &G, const Plan &P, const float *ev, const float *m,
                           float *out, int32_t *dec, cudaStream_t s) {
+    if (G.vin_tab4 != nullptr) {
+        const int n = G.V;
+        k_var_tab4<MODE><<<(n + 255) / 256, 256, 0, s>>>(G, n, ev, m, out, dec);
+        return;
+    }
     for (const VarLaunch &L : P.var) {
         if (L.n == 0) continue;
         if (L.block_mode) {

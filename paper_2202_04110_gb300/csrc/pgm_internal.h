@@ -78,6 +78,9 @@ struct DevGraph {
     const uint8_t *cfg_pool;
     const int32_t *paroff_pool;
     uint32_t *flags;         // device status word
+    const int4 *vin_tab4;    // [V] when every variable is binary with <= 4 factors: the
+                             // first edge-states of its incoming edges, ascending, padded
+                             // with -1 (else null)
     float *v2f_hd;           // [2 * ES] exact leave-one-out sums, float-float (hi, lo)
                              // pairs, for edges of high-degree variables (edge_vs = -1);
                              // null if there are none
@@ -128,6 +131,7 @@ struct HostLayout {
     std::vector<int32_t> var_small, var_large;  // degree buckets
     bool var_small_identity = false;
     bool all_binary = false;
+    std::vector<int32_t> vin_tab4;  // [4 * V] (see DevGraph::vin_tab4), empty if unused
 };
 
 struct GraphDescView;  // forward (defined in compile.cpp from the C-ABI struct)
