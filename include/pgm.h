@@ -115,8 +115,17 @@ typedef struct {
     int32_t max_degree;    /* largest number of factors on one variable */
     int64_t device_bytes;  /* device memory held by the graph (indices + scratch) */
     int32_t launches_per_iter; /* kernel launches of one pgm_run_bp iteration */
-    int32_t reserved;
+    int32_t n_members;         /* graphs in the batch (1 for pgm_build) */
 } pgm_info;
+
+/* Where one member of a batch lives in the flat arrays of the batched graph. */
+typedef struct {
+    int64_t var_off, n_vars;               /* variables */
+    int64_t vs_off, n_var_states;          /* evidence / beliefs */
+    int64_t edge_off, n_edges;             /* edges */
+    int64_t es_off, n_edge_states;         /* messages */
+    int64_t pot_off, n_potentials;         /* log-potentials */
+} pgm_member;
 
 /*
  * Compile a factor graph (Sec. 4: flatten messages into 1-D arrays and keep the
@@ -136,6 +145,21 @@ pgm_status pgm_build(const pgm_graph_desc *desc, pgm_graph **out);
  * pgm_build's validation.
  */
 pgm_status pgm_check_desc(const pgm_graph_desc *desc, pgm_info *info);
+
+/*
+ * Batch of many graphs (Sec. 4.3: processing batches of models in parallel). Compiles n
+ * descriptions into one graph whose flat arrays hold the members one after the other:
+ * member i's variables, evidence, beliefs, edges, messages and log-potentials are
+ * contiguous ranges (pgm_batch_member) laid out exactly as pgm_build lays out that
+ * member alone, with its variable indices shifted. Every pass of pgm_run_bp on the
+ * batch is one launch per kernel variant over all members, and a member's results are
+ * those of the member alone (the per-factor and per-variable arithmetic does not depend
+ * on the batch). Same errors as pgm_build, per description.
+ */
+pgm_status pgm_build_batch(const pgm_graph_desc *const *descs, int32_t n, pgm_graph **out);
+
+/* Offsets of member i (0 <= i < pgm_info.n_members) of a batch. */
+pgm_status pgm_batch_member(const pgm_graph *g, int32_t i, pgm_member *m);
 
 /* Release a graph and its device memory (synchronises its device). NULL is a no-op. */
 void pgm_free(pgm_graph *g);
@@ -241,6 +265,41 @@ pgm_status pgm_device_flags(pgm_graph *g, uint32_t *flags, int32_t clear, void *
 pgm_status pgm_grid2_run_bp_noalloc(int32_t rows, int32_t cols, const float *log_pot,
                                     const float *evidence, float T, float damping,
                                     int32_t n_iters, float *msgs, void *stream);
+
+/*
+ * Options of a graph. PGM_OPT_CUDA_GRAPH (default 1): pgm_run_bp with n_iters >= 2
+ * (and per-pass profiling off) records the whole call -- every kernel of every
+ * iteration and the final copy -- as a CUDA graph the first time it sees a given
+ * (log_pot, evidence, msgs, T, damping, n_iters), on a private stream, and afterwards
+ * replays it on the caller's stream (one launch per call; up to 8 cached per graph,
+ * least recently used dropped). 0 launches the kernels one by one and drops the cache.
+ * A cached graph holds the pointers it was recorded with: buffers that are freed and
+ * reused at the same address with the same meaning are fine.
+ */
+#define PGM_OPT_CUDA_GRAPH 1
+pgm_status pgm_set_option(pgm_graph *g, int32_t option, int64_t value);
+
+/*
+ * Launch-shape autotuner: for every factor-pass launch of the graph (one per kernel
+ * variant, covering all groups of that variant) times each thread-block shape the
+ * kernel allows -- threads per block for the thread-per-factor kernels, warps per
+ * block (factors per block) for the warp-per-factor logical kernel -- on the given
+ * inputs, and keeps the fastest; likewise the block size of the thread-per-variable
+ * pass. Allocates two temporary message buffers (freed before returning), blocks until
+ * done, drops the cached CUDA graphs. Results are unchanged by the shapes.
+ */
+pgm_status pgm_autotune(pgm_graph *g, const float *log_pot, const float *evidence, float T,
+                        float damping, void *stream);
+
+/*
+ * Launch i of one iteration (0 <= i < pgm_info.launches_per_iter): kind 0 = variable
+ * pass (variant 0 thread per variable, 1 block per variable, 2 padded 4-edge table),
+ * kind 1 = factor pass (variant: 0..3 dense pairwise K = 2, 4, 8, 16; 4 listed
+ * configurations; 5 OR/AND thread per factor; 6 OR/AND warp per factor); threads per
+ * block and blocks. Any output pointer may be NULL.
+ */
+pgm_status pgm_launch_info(const pgm_graph *g, int32_t i, int32_t *kind, int32_t *variant,
+                           int32_t *threads, int32_t *n_blocks);
 
 /* Thread-local description of the calling thread's last error ("" if none). */
 const char *pgm_last_error(void);

@@ -21,9 +21,11 @@ FLAG_CONTRADICTION = 1
 FLAG_NAN = 2
 
 # Every symbol include/pgm.h declares.
-EXPORTED = ["pgm_build", "pgm_check_desc", "pgm_free", "pgm_graph_info", "pgm_run_bp", "pgm_beliefs",
+EXPORTED = ["pgm_build", "pgm_build_batch", "pgm_batch_member", "pgm_check_desc", "pgm_free", "pgm_graph_info", "pgm_run_bp", "pgm_beliefs",
             "pgm_decode", "pgm_infer_host", "pgm_set_profiling", "pgm_pass_times",
-            "pgm_device_flags", "pgm_grid2_run_bp_noalloc", "pgm_last_error"]
+            "pgm_device_flags", "pgm_grid2_run_bp_noalloc", "pgm_set_option", "pgm_autotune",
+            "pgm_launch_info", "pgm_last_error"]
+OPT_CUDA_GRAPH = 1
 
 
 class PgmError(RuntimeError):
@@ -55,7 +57,13 @@ class InfoC(ctypes.Structure):
                 ("n_edge_states", ctypes.c_int64), ("n_potentials", ctypes.c_int64),
                 ("max_states", ctypes.c_int32), ("max_degree", ctypes.c_int32),
                 ("device_bytes", ctypes.c_int64), ("launches_per_iter", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("n_members", ctypes.c_int32)]
+
+
+class MemberC(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int64) for n in ("var_off", "n_vars", "vs_off", "n_var_states", "edge_off",
+                                              "n_edges", "es_off", "n_edge_states", "pot_off",
+                                              "n_potentials")]
 
 
 _lib = None
@@ -73,6 +81,10 @@ def load_library(path: str | None = None):
     vp, i32, f32 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_float
     lib.pgm_build.restype = i32
     lib.pgm_build.argtypes = [ctypes.POINTER(GraphDescC), ctypes.POINTER(vp)]
+    lib.pgm_build_batch.restype = i32
+    lib.pgm_build_batch.argtypes = [ctypes.POINTER(ctypes.POINTER(GraphDescC)), i32, ctypes.POINTER(vp)]
+    lib.pgm_batch_member.restype = i32
+    lib.pgm_batch_member.argtypes = [vp, i32, ctypes.POINTER(MemberC)]
     lib.pgm_check_desc.restype = i32
     lib.pgm_check_desc.argtypes = [ctypes.POINTER(GraphDescC), ctypes.POINTER(InfoC)]
     lib.pgm_free.restype = None
@@ -96,6 +108,12 @@ def load_library(path: str | None = None):
     lib.pgm_device_flags.argtypes = [vp, ctypes.POINTER(ctypes.c_uint32), i32, vp]
     lib.pgm_grid2_run_bp_noalloc.restype = i32
     lib.pgm_grid2_run_bp_noalloc.argtypes = [i32, i32, vp, vp, f32, f32, i32, vp, vp]
+    lib.pgm_autotune.restype = i32
+    lib.pgm_autotune.argtypes = [vp, vp, vp, f32, f32, vp]
+    lib.pgm_launch_info.restype = i32
+    lib.pgm_launch_info.argtypes = [vp, i32] + [ctypes.POINTER(i32)] * 4
+    lib.pgm_set_option.restype = i32
+    lib.pgm_set_option.argtypes = [vp, i32, ctypes.c_int64]
     lib.pgm_last_error.restype = ctypes.c_char_p
     lib.pgm_last_error.argtypes = []
     _lib = lib
@@ -164,18 +182,31 @@ def _dptr(t, dtype=None, numel=None, name="tensor") -> int:
 
 
 class Graph:
-    """A compiled factor graph resident on the current CUDA device."""
+    """A compiled factor graph resident on the current CUDA device. `fg` is one
+    workloads.FactorGraph (pgm_build) or a list of them (pgm_build_batch)."""
 
     def __init__(self, fg):
         lib = load_library()
-        desc, keep = marshal_desc(fg)
         h = ctypes.c_void_p()
-        check(lib.pgm_build(ctypes.byref(desc), ctypes.byref(h)))
-        del keep
+        if isinstance(fg, (list, tuple)):
+            descs, keeps = zip(*[marshal_desc(x) for x in fg])
+            arr = (ctypes.POINTER(GraphDescC) * len(descs))(*[ctypes.pointer(d) for d in descs])
+            check(lib.pgm_build_batch(arr, len(descs), ctypes.byref(h)))
+            del keeps, arr
+        else:
+            desc, keep = marshal_desc(fg)
+            check(lib.pgm_build(ctypes.byref(desc), ctypes.byref(h)))
+            del keep
         self._h = h
         info = InfoC()
         check(lib.pgm_graph_info(h, ctypes.byref(info)))
         self.info = {k: getattr(info, k) for k, _ in InfoC._fields_}
+
+    def member(self, i: int) -> dict:
+        """Offsets of member i of a batch (pgm_batch_member)."""
+        m = MemberC()
+        check(load_library().pgm_batch_member(self._h, int(i), ctypes.byref(m)))
+        return {k: getattr(m, k) for k, _ in MemberC._fields_}
 
     @property
     def handle(self):
@@ -246,6 +277,26 @@ class Graph:
                                             float(T), float(damping), int(n_iters), beliefs.ctypes.data,
                                             decode.ctypes.data, _stream_ptr(stream)))
         return beliefs, decode
+
+    def autotune(self, log_pot, evidence, T: float, damping: float, stream=None):
+        """pgm_autotune: pick the fastest launch shapes on these inputs."""
+        import torch
+        I = self.info
+        lp = _dptr(log_pot, torch.float32, I["n_potentials"], "log_pot") if I["n_potentials"] else 0
+        check(load_library().pgm_autotune(self._h, lp, _dptr(evidence, torch.float32, I["n_var_states"], "evidence"),
+                                          float(T), float(damping), _stream_ptr(stream)))
+
+    def launches(self) -> list:
+        """[(kind, variant, threads, blocks)] of one iteration (pgm_launch_info)."""
+        out = []
+        for i in range(self.info["launches_per_iter"]):
+            v = [ctypes.c_int32() for _ in range(4)]
+            check(load_library().pgm_launch_info(self._h, i, *[ctypes.byref(x) for x in v]))
+            out.append(tuple(x.value for x in v))
+        return out
+
+    def set_option(self, option: int, value: int):
+        check(load_library().pgm_set_option(self._h, int(option), int(value)))
 
     def set_profiling(self, period: int):
         """Record per-pass CUDA events every `period` iterations (0 = off)."""

@@ -66,6 +66,21 @@ struct pgm_graph {
     size_t events_used = 0;
     int64_t prof_var_launches = 0, prof_factor_launches = 0;
     int32_t var_launches = 0, factor_launches = 0;
+    std::vector<HostMember> members;
+    std::vector<std::vector<char>> factor_segs_host;  // host copy of each factor launch's segments
+    // CUDA graphs of whole pgm_run_bp calls, keyed by their arguments (LRU)
+    struct CachedRun {
+        const float *log_pot, *evidence;
+        float *msgs;
+        uint32_t T_bits, damping_bits;
+        int32_t n_iters;
+        cudaGraphExec_t exec;
+        uint64_t last_use;
+    };
+    int32_t use_cuda_graph = 1;
+    cudaStream_t capture_stream = nullptr;
+    std::vector<CachedRun> runs;
+    uint64_t use_clock = 0;
 };
 
 namespace {
@@ -148,6 +163,8 @@ pgm_status build_plan(const HostLayout &H, pgm_graph *g, Packer &pk, std::vector
             P.factor.push_back(L);
             seg_off.push_back(pk.add(segs.data(), segs.size()));
             seg_kind.push_back(variant);
+            g->factor_segs_host.emplace_back(reinterpret_cast<const char *>(segs.data()),
+                                             reinterpret_cast<const char *>(segs.data() + segs.size()));
         } else {
             std::vector<EnumSeg> segs;
             int threads = (variant == kPair16 || variant == kEnumGeneric) ? 128 : 256;
@@ -166,6 +183,8 @@ pgm_status build_plan(const HostLayout &H, pgm_graph *g, Packer &pk, std::vector
             P.factor.push_back(L);
             seg_off.push_back(pk.add(segs.data(), segs.size()));
             seg_kind.push_back(variant);
+            g->factor_segs_host.emplace_back(reinterpret_cast<const char *>(segs.data()),
+                                             reinterpret_cast<const char *>(segs.data() + segs.size()));
         }
     }
     return PGM_OK;
@@ -203,12 +222,12 @@ extern "C" {
 
 const char *pgm_last_error(void) { return g_last_error.c_str(); }
 
-pgm_status pgm_build(const pgm_graph_desc *desc, pgm_graph **out) {
+static pgm_status build_from_descs(const void *const *descs, int n, pgm_graph **out) {
     g_last_error.clear();
     if (!out) return fail(PGM_EINVAL, "out is NULL");
     *out = nullptr;
     HostLayout H;
-    std::string err = compile_graph(desc, &H);
+    std::string err = compile_graph(descs, n, &H);
     if (!err.empty()) return fail(PGM_EINVAL, err);
     pgm_graph *g = new (std::nothrow) pgm_graph();
     if (!g) return fail(PGM_ENOMEM, "host allocation failed");
@@ -309,7 +328,37 @@ pgm_status pgm_build(const pgm_graph_desc *desc, pgm_graph **out) {
     for (const VarLaunch &L : g->P.var) g->var_launches += (L.n > 0);
     for (const FactorLaunch &L : g->P.factor) g->factor_launches += (L.n_blocks > 0);
     I.launches_per_iter = g->var_launches + g->factor_launches;
+    I.n_members = (int32_t)H.members.size();
+    g->members = H.members;
     *out = g;
+    return PGM_OK;
+}
+
+pgm_status pgm_build(const pgm_graph_desc *desc, pgm_graph **out) {
+    const void *one = desc;
+    return build_from_descs(&one, 1, out);
+}
+
+pgm_status pgm_build_batch(const pgm_graph_desc *const *descs, int32_t n, pgm_graph **out) {
+    if (n < 1 || !descs) return fail(PGM_EINVAL, "a batch needs n >= 1 descriptions");
+    std::vector<const void *> v(descs, descs + n);
+    return build_from_descs(v.data(), n, out);
+}
+
+pgm_status pgm_batch_member(const pgm_graph *g, int32_t i, pgm_member *m) {
+    if (!g || !m) return fail(PGM_EINVAL, "NULL argument");
+    if (i < 0 || i >= (int32_t)g->members.size()) return fail(PGM_EINVAL, "member index out of range");
+    const HostMember &h = g->members[i];
+    m->var_off = h.var_off;
+    m->n_vars = h.n_vars;
+    m->vs_off = h.vs_off;
+    m->n_var_states = h.n_var_states;
+    m->edge_off = h.edge_off;
+    m->n_edges = h.n_edges;
+    m->es_off = h.es_off;
+    m->n_edge_states = h.n_edge_states;
+    m->pot_off = h.pot_off;
+    m->n_potentials = h.n_potentials;
     return PGM_OK;
 }
 
@@ -317,7 +366,8 @@ pgm_status pgm_check_desc(const pgm_graph_desc *desc, pgm_info *info) {
     g_last_error.clear();
     if (!info) return fail(PGM_EINVAL, "info is NULL");
     HostLayout H;
-    std::string err = compile_graph(desc, &H);
+    const void *one = desc;
+    std::string err = compile_graph(&one, 1, &H);
     if (!err.empty()) return fail(PGM_EINVAL, err);
     std::memset(info, 0, sizeof *info);
     info->n_vars = H.V;
@@ -328,6 +378,7 @@ pgm_status pgm_check_desc(const pgm_graph_desc *desc, pgm_info *info) {
     info->n_potentials = H.P;
     info->max_states = H.max_states;
     info->max_degree = H.max_degree;
+    info->n_members = 1;
     size_t idx = (H.vs_off.size() + H.vin_off.size() + H.vin_es.size() + H.edge_vs.size() +
                   H.paroff_pool.size() + H.var_small.size() + H.var_large.size()) * sizeof(int32_t) +
                  H.cfg_pool.size();
@@ -337,6 +388,8 @@ pgm_status pgm_check_desc(const pgm_graph_desc *desc, pgm_info *info) {
     return PGM_OK;
 }
 
+static void drop_cached_runs(pgm_graph *g);
+
 void pgm_free(pgm_graph *g) {
     if (!g) return;
     DeviceGuard dg(g->device);
@@ -345,6 +398,8 @@ void pgm_free(pgm_graph *g) {
     if (g->scratch_mem) cudaFree(g->scratch_mem);
     if (g->host_io_mem) cudaFree(g->host_io_mem);
     for (cudaEvent_t e : g->events) cudaEventDestroy(e);
+    drop_cached_runs(g);
+    if (g->capture_stream) cudaStreamDestroy(g->capture_stream);
     delete g;
 }
 
@@ -354,18 +409,14 @@ pgm_status pgm_graph_info(const pgm_graph *g, pgm_info *info) {
     return PGM_OK;
 }
 
-pgm_status pgm_run_bp(pgm_graph *g, const float *log_pot, const float *evidence, float T,
-                      float damping, int32_t n_iters, float *msgs, void *stream) {
-    pgm_status st = check_run_args(g, log_pot, evidence, T, damping, n_iters, msgs);
-    if (st != PGM_OK) return st;
-    if (n_iters == 0 || g->info.n_edge_states == 0) return PGM_OK;
-    DeviceGuard dg(g->device);
-    if (!dg.ok) return fail(PGM_ECUDA, "cudaSetDevice failed");
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
+// Enqueue n_iters iterations (and the final copy back into msgs) on stream s.
+static pgm_status enqueue_iterations(pgm_graph *g, const float *log_pot, const float *evidence, float T,
+                                     float damping, int32_t n_iters, float *msgs, cudaStream_t s,
+                                     bool profile) {
     float *cur = msgs, *nxt = g->m_tmp;
     for (int it = 0; it < n_iters; ++it) {
         cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr;
-        const bool prof = g->profiling > 0 && (it % g->profiling) == g->profiling - 1;
+        const bool prof = profile && g->profiling > 0 && (it % g->profiling) == g->profiling - 1;
         if (prof) {
             pgm_status ps = take_events(g, &e0, &e1, &e2);
             if (ps != PGM_OK) return ps;
@@ -389,6 +440,233 @@ pgm_status pgm_run_bp(pgm_graph *g, const float *log_pot, const float *evidence,
         if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(msgs)");
     }
     return PGM_OK;
+}
+
+static uint32_t float_bits(float x) {
+    uint32_t u;
+    std::memcpy(&u, &x, sizeof u);
+    return u;
+}
+
+// The cached CUDA graph of a pgm_run_bp call with these arguments, captured on the
+// graph's private stream on first use.
+static pgm_status cached_run(pgm_graph *g, const float *log_pot, const float *evidence, float T,
+                             float damping, int32_t n_iters, float *msgs, cudaGraphExec_t *out) {
+    const uint32_t tb = float_bits(T), db = float_bits(damping);
+    for (auto &r : g->runs)
+        if (r.log_pot == log_pot && r.evidence == evidence && r.msgs == msgs && r.T_bits == tb &&
+            r.damping_bits == db && r.n_iters == n_iters) {
+            r.last_use = ++g->use_clock;
+            *out = r.exec;
+            return PGM_OK;
+        }
+    if (!g->capture_stream) {
+        cudaError_t e = cudaStreamCreateWithFlags(&g->capture_stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamCreate");
+    }
+    cudaError_t e = cudaStreamBeginCapture(g->capture_stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamBeginCapture");
+    pgm_status st = enqueue_iterations(g, log_pot, evidence, T, damping, n_iters, msgs, g->capture_stream, false);
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(g->capture_stream, &graph);
+    if (st != PGM_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return st;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+    if (g->runs.size() >= 8) {
+        size_t lru = 0;
+        for (size_t i = 1; i < g->runs.size(); ++i)
+            if (g->runs[i].last_use < g->runs[lru].last_use) lru = i;
+        cudaGraphExecDestroy(g->runs[lru].exec);
+        g->runs.erase(g->runs.begin() + lru);
+    }
+    g->runs.push_back({log_pot, evidence, msgs, tb, db, n_iters, exec, ++g->use_clock});
+    *out = exec;
+    return PGM_OK;
+}
+
+static void drop_cached_runs(pgm_graph *g) {
+    for (auto &r : g->runs) cudaGraphExecDestroy(r.exec);
+    g->runs.clear();
+}
+
+pgm_status pgm_run_bp(pgm_graph *g, const float *log_pot, const float *evidence, float T,
+                      float damping, int32_t n_iters, float *msgs, void *stream) {
+    pgm_status st = check_run_args(g, log_pot, evidence, T, damping, n_iters, msgs);
+    if (st != PGM_OK) return st;
+    if (n_iters == 0 || g->info.n_edge_states == 0) return PGM_OK;
+    DeviceGuard dg(g->device);
+    if (!dg.ok) return fail(PGM_ECUDA, "cudaSetDevice failed");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (g->use_cuda_graph && g->profiling == 0 && n_iters >= 2) {
+        cudaGraphExec_t exec = nullptr;
+        st = cached_run(g, log_pot, evidence, T, damping, n_iters, msgs, &exec);
+        if (st != PGM_OK) return st;
+        cudaError_t e = cudaGraphLaunch(exec, s);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
+        return PGM_OK;
+    }
+    return enqueue_iterations(g, log_pot, evidence, T, damping, n_iters, msgs, s, true);
+}
+
+// Thread-block shapes a factor launch may use (within the kernels' launch bounds).
+static std::vector<int> shape_candidates(int variant) {
+    switch (variant) {
+        case kPair2: case kPair4: case kPair8: case kLogicSmall: return {64, 128, 256};
+        case kPair16: return {64, 128};
+        case kEnumGeneric: return {32, 64, 128};
+        case kLogicWarp: return {32, 64, 128};
+        default: return {};
+    }
+}
+
+// Re-plan factor launch li for `threads` threads per block: block ranges of its segments,
+// grid size, shared memory; uploads the segments. Returns false if the shape does not fit.
+static bool replan_factor_launch(pgm_graph *g, size_t li, int threads, cudaStream_t s) {
+    FactorLaunch &L = g->P.factor[li];
+    std::vector<char> &host = g->factor_segs_host[li];
+    const bool logic = (L.variant == kLogicSmall || L.variant == kLogicWarp);
+    const int per_block = (L.variant == kLogicWarp) ? threads / 32 : threads;
+    size_t smem = 0;
+    if (L.variant == kLogicWarp) {
+        smem = (size_t)per_block * 3 * L.max_fan * sizeof(float);
+        if (smem > 200 * 1024) return false;
+    }
+    int32_t blk = 0;
+    if (logic) {
+        LogicSeg *segs = reinterpret_cast<LogicSeg *>(host.data());
+        for (int i = 0; i < L.n_seg; ++i) {
+            segs[i].block_begin = blk;
+            blk += (segs[i].n_fac + per_block - 1) / per_block;
+        }
+    } else {
+        EnumSeg *segs = reinterpret_cast<EnumSeg *>(host.data());
+        for (int i = 0; i < L.n_seg; ++i) {
+            segs[i].block_begin = blk;
+            blk += (segs[i].n_fac + per_block - 1) / per_block;
+        }
+    }
+    if (cudaMemcpyAsync(const_cast<void *>(L.segs), host.data(), host.size(), cudaMemcpyHostToDevice, s) != cudaSuccess)
+        return false;
+    L.threads = threads;
+    L.n_blocks = blk;
+    L.smem = (int32_t)smem;
+    return true;
+}
+
+pgm_status pgm_autotune(pgm_graph *g, const float *log_pot, const float *evidence, float T,
+                        float damping, void *stream) {
+    pgm_status st = check_run_args(g, log_pot, evidence, T, damping, 1, g ? g->m_tmp : nullptr);
+    if (st != PGM_OK) return st;
+    if (g->info.n_edge_states == 0) return PGM_OK;
+    DeviceGuard dg(g->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const size_t es_bytes = (size_t)g->info.n_edge_states * sizeof(float);
+    float *m_in = nullptr, *m_out = nullptr;
+    if (cudaMalloc(&m_in, 2 * es_bytes) != cudaSuccess) return fail(PGM_ENOMEM, "cudaMalloc(autotune buffers)");
+    m_out = m_in + g->info.n_edge_states;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaMemsetAsync(m_in, 0, es_bytes, s);
+    // one real iteration so that the messages and beliefs are not trivial
+    enqueue_iterations(g, log_pot, evidence, T, damping, 1, m_in, s, false);
+    launch_var_pass(g->G, g->P, evidence, m_in, g->b, kVarIter, nullptr, s);
+    for (size_t li = 0; li < g->P.factor.size(); ++li) {
+        const int orig = g->P.factor[li].threads;
+        int best = orig;
+        float best_ms = 1e30f;
+        for (int c : shape_candidates(g->P.factor[li].variant)) {
+            if (!replan_factor_launch(g, li, c, s)) continue;
+            Plan one;
+            one.kfix = g->P.kfix;
+            one.factor.push_back(g->P.factor[li]);
+            launch_factor_pass(g->G, one, log_pot, g->b, evidence, m_in, m_out, T, damping, s);
+            cudaEventRecord(e0, s);
+            for (int r = 0; r < 5; ++r)
+                launch_factor_pass(g->G, one, log_pot, g->b, evidence, m_in, m_out, T, damping, s);
+            cudaEventRecord(e1, s);
+            cudaEventSynchronize(e1);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (cudaGetLastError() == cudaSuccess && ms < best_ms) {
+                best_ms = ms;
+                best = c;
+            }
+        }
+        replan_factor_launch(g, li, best, s);
+    }
+    // thread-per-variable launches: block size
+    for (VarLaunch &L : g->P.var) {
+        if (L.block_mode || L.n == 0 || g->G.vin_tab4) continue;
+        int best = L.threads;
+        float best_ms = 1e30f;
+        for (int c : {128, 256}) {
+            L.threads = c;
+            L.n_blocks = (L.n + c - 1) / c;
+            Plan one;
+            one.kfix = g->P.kfix;
+            one.var.push_back(L);
+            launch_var_pass(g->G, one, evidence, m_in, g->b, kVarIter, nullptr, s);
+            cudaEventRecord(e0, s);
+            for (int r = 0; r < 5; ++r) launch_var_pass(g->G, one, evidence, m_in, g->b, kVarIter, nullptr, s);
+            cudaEventRecord(e1, s);
+            cudaEventSynchronize(e1);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best_ms) {
+                best_ms = ms;
+                best = c;
+            }
+        }
+        L.threads = best;
+        L.n_blocks = (L.n + best - 1) / best;
+    }
+    cudaError_t e = cudaStreamSynchronize(s);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(m_in);
+    drop_cached_runs(g);
+    if (e != cudaSuccess) return cuda_fail(e, "autotune");
+    return PGM_OK;
+}
+
+pgm_status pgm_launch_info(const pgm_graph *g, int32_t i, int32_t *kind, int32_t *variant,
+                           int32_t *threads, int32_t *n_blocks) {
+    if (!g) return fail(PGM_EINVAL, "graph is NULL");
+    const int32_t nv = (int32_t)g->P.var.size(), nf = (int32_t)g->P.factor.size();
+    if (i < 0 || i >= nv + nf) return fail(PGM_EINVAL, "launch index out of range");
+    if (i < nv) {
+        const VarLaunch &L = g->P.var[i];
+        if (kind) *kind = 0;
+        if (variant) *variant = L.block_mode ? 1 : (g->G.vin_tab4 ? 2 : 0);
+        if (threads) *threads = L.block_mode ? kVarBlockThreads : (g->G.vin_tab4 ? 256 : L.threads);
+        if (n_blocks) *n_blocks = L.n_blocks;
+    } else {
+        const FactorLaunch &L = g->P.factor[i - nv];
+        if (kind) *kind = 1;
+        if (variant) *variant = L.variant;
+        if (threads) *threads = L.threads;
+        if (n_blocks) *n_blocks = L.n_blocks;
+    }
+    return PGM_OK;
+}
+
+pgm_status pgm_set_option(pgm_graph *g, int32_t option, int64_t value) {
+    if (!g) return fail(PGM_EINVAL, "graph is NULL");
+    switch (option) {
+        case PGM_OPT_CUDA_GRAPH:
+            g->use_cuda_graph = value != 0;
+            if (!g->use_cuda_graph) drop_cached_runs(g);
+            return PGM_OK;
+        default:
+            return fail(PGM_EINVAL, "unknown option");
+    }
 }
 
 pgm_status pgm_beliefs(pgm_graph *g, const float *evidence, const float *msgs, float *out,

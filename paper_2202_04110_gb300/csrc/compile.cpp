@@ -40,88 +40,108 @@ bool is_dense_pair(const pgm_enum_group &g, int K0, int K1) {
 
 }  // namespace
 
-std::string compile_graph(const void *vdesc, HostLayout *L) {
-    const pgm_graph_desc *d = static_cast<const pgm_graph_desc *>(vdesc);
-    if (!d) return "desc is NULL";
-    if (d->n_vars < 1) return "n_vars must be >= 1";
-    if (!d->num_states) return "num_states is NULL";
-    if (d->n_enum_groups < 0 || d->n_logic_groups < 0) return "negative group count";
-    if (d->n_enum_groups > 0 && !d->enum_groups) return "enum_groups is NULL";
-    if (d->n_logic_groups > 0 && !d->logic_groups) return "logic_groups is NULL";
-    const int64_t V = d->n_vars;
+std::string compile_graph(const void *const *vdescs, int n_desc, HostLayout *L) {
+    if (n_desc < 1) return "no graph descriptions";
+    if (!vdescs) return "desc is NULL";
+    std::vector<const pgm_graph_desc *> D(n_desc);
+    int64_t V = 0;
+    for (int m = 0; m < n_desc; ++m) {
+        const pgm_graph_desc *d = static_cast<const pgm_graph_desc *>(vdescs[m]);
+        if (!d) return fmt("desc %lld is NULL", m);
+        if (d->n_vars < 1) return fmt("desc %lld: n_vars must be >= 1", m);
+        if (!d->num_states) return fmt("desc %lld: num_states is NULL", m);
+        if (d->n_enum_groups < 0 || d->n_logic_groups < 0) return fmt("desc %lld: negative group count", m);
+        if (d->n_enum_groups > 0 && !d->enum_groups) return fmt("desc %lld: enum_groups is NULL", m);
+        if (d->n_logic_groups > 0 && !d->logic_groups) return fmt("desc %lld: logic_groups is NULL", m);
+        D[m] = d;
+        V += d->n_vars;
+    }
+    if (V > kI32Max) return "too many variables for int32 indexing";
     L->V = V;
     L->vs_off.assign(V + 1, 0);
+    std::vector<int32_t> Kall(V);
+    std::vector<int64_t> voff(n_desc + 1, 0);
     int32_t kmax = 0;
+    for (int m = 0; m < n_desc; ++m) {
+        voff[m + 1] = voff[m] + D[m]->n_vars;
+        for (int64_t v = 0; v < D[m]->n_vars; ++v) {
+            int32_t k = D[m]->num_states[v];
+            if (k < 1 || k > kMaxStates) return fmt("variable %lld has %lld states (1..256 allowed)", voff[m] + v, k);
+            Kall[voff[m] + v] = k;
+        }
+    }
     for (int64_t v = 0; v < V; ++v) {
-        int32_t k = d->num_states[v];
-        if (k < 1 || k > kMaxStates) return fmt("variable %lld has %lld states (1..256 allowed)", v, k);
-        kmax = std::max(kmax, k);
-        int64_t nx = (int64_t)L->vs_off[v] + k;
+        kmax = std::max(kmax, Kall[v]);
+        int64_t nx = (int64_t)L->vs_off[v] + Kall[v];
         if (nx > kI32Max) return "too many variable states for int32 indexing";
         L->vs_off[v + 1] = (int32_t)nx;
     }
     L->VS = L->vs_off[V];
     L->max_states = kmax;
-    const int32_t *K = d->num_states;
+    const int32_t *K = Kall.data();
 
-    // ---- count edges and validate groups
+    // ---- count edges and validate groups (variable indices are local to each member)
     int64_t E = 0, F = 0, P = 0, ES = 0;
-    for (int gi = 0; gi < d->n_enum_groups; ++gi) {
-        const pgm_enum_group &g = d->enum_groups[gi];
-        if (g.arity < 1 || g.arity > kMaxArity) return fmt("enum group %lld: arity %lld not in 1..8", gi, g.arity);
-        if (g.n_cfg < 1) return fmt("enum group %lld: n_cfg must be >= 1", gi);
-        if (g.n_fac < 0) return fmt("enum group %lld: negative n_fac", gi);
-        if (!g.cfg) return fmt("enum group %lld: cfg is NULL", gi);
-        if (g.n_fac > 0 && !g.vars) return fmt("enum group %lld: vars is NULL", gi);
-        int32_t ksum = 0;
-        for (int j = 0; j < g.arity && g.n_fac > 0; ++j) {
-            int32_t v0 = g.vars[j];
-            if (v0 < 0 || v0 >= V) return fmt("enum group %lld: variable %lld out of range", gi, v0);
-            ksum += K[v0];
-        }
-        if (ksum > kMaxStateSum) return fmt("enum group %lld: state sum %lld exceeds 64", gi, ksum);
-        for (int64_t f = 0; f < g.n_fac; ++f)
-            for (int j = 0; j < g.arity; ++j) {
-                int32_t v = g.vars[f * g.arity + j];
-                if (v < 0 || v >= V) return fmt("enum group %lld: variable %lld out of range", gi, v);
-                if (K[v] != K[g.vars[j]])
-                    return fmt("enum group %lld: factor %lld neighbour %lld differs in state count", gi, f, j);
+    for (int m = 0; m < n_desc; ++m) {
+        const pgm_graph_desc *d = D[m];
+        const int64_t Vm = d->n_vars, vo = voff[m];
+        for (int gi = 0; gi < d->n_enum_groups; ++gi) {
+            const pgm_enum_group &g = d->enum_groups[gi];
+            if (g.arity < 1 || g.arity > kMaxArity) return fmt("enum group %lld: arity %lld not in 1..8", gi, g.arity);
+            if (g.n_cfg < 1) return fmt("enum group %lld: n_cfg must be >= 1", gi);
+            if (g.n_fac < 0) return fmt("enum group %lld: negative n_fac", gi);
+            if (!g.cfg) return fmt("enum group %lld: cfg is NULL", gi);
+            if (g.n_fac > 0 && !g.vars) return fmt("enum group %lld: vars is NULL", gi);
+            int32_t ksum = 0;
+            for (int j = 0; j < g.arity && g.n_fac > 0; ++j) {
+                int32_t v0 = g.vars[j];
+                if (v0 < 0 || v0 >= Vm) return fmt("enum group %lld: variable %lld out of range", gi, v0);
+                ksum += K[vo + v0];
             }
-        for (int c = 0; c < g.n_cfg; ++c)
-            for (int j = 0; j < g.arity; ++j) {
-                int32_t s = g.cfg[c * g.arity + j];
-                int32_t kj = g.n_fac > 0 ? K[g.vars[j]] : kMaxStates;
-                if (s < 0 || s >= kj) return fmt("enum group %lld: config %lld state %lld out of range", gi, c, s);
+            if (ksum > kMaxStateSum) return fmt("enum group %lld: state sum %lld exceeds 64", gi, ksum);
+            for (int64_t f = 0; f < g.n_fac; ++f)
+                for (int j = 0; j < g.arity; ++j) {
+                    int32_t v = g.vars[f * g.arity + j];
+                    if (v < 0 || v >= Vm) return fmt("enum group %lld: variable %lld out of range", gi, v);
+                    if (K[vo + v] != K[vo + g.vars[j]])
+                        return fmt("enum group %lld: factor %lld neighbour %lld differs in state count", gi, f, j);
+                }
+            for (int c = 0; c < g.n_cfg; ++c)
+                for (int j = 0; j < g.arity; ++j) {
+                    int32_t s = g.cfg[c * g.arity + j];
+                    int32_t kj = g.n_fac > 0 ? K[vo + g.vars[j]] : kMaxStates;
+                    if (s < 0 || s >= kj) return fmt("enum group %lld: config %lld state %lld out of range", gi, c, s);
+                }
+            E += (int64_t)g.n_fac * g.arity;
+            ES += (int64_t)g.n_fac * ksum;
+            F += g.n_fac;
+            P += g.shared_potentials ? g.n_cfg : (int64_t)g.n_cfg * g.n_fac;
+        }
+        for (int gi = 0; gi < d->n_logic_groups; ++gi) {
+            const pgm_logic_group &g = d->logic_groups[gi];
+            if (g.kind != PGM_LOGIC_OR && g.kind != PGM_LOGIC_AND) return fmt("logic group %lld: unknown kind %lld", gi, g.kind);
+            if (g.n_fac < 0) return fmt("logic group %lld: negative n_fac", gi);
+            if (!g.par_off) return fmt("logic group %lld: par_off is NULL", gi);
+            if (g.par_off[0] != 0) return fmt("logic group %lld: par_off[0] must be 0", gi);
+            for (int64_t f = 0; f < g.n_fac; ++f)
+                if (g.par_off[f + 1] < g.par_off[f]) return fmt("logic group %lld: par_off decreases at %lld", gi, f);
+            int64_t npar = g.par_off[g.n_fac];
+            if (npar > 0 && !g.parents) return fmt("logic group %lld: parents is NULL", gi);
+            if (g.n_fac > 0 && !g.child) return fmt("logic group %lld: child is NULL", gi);
+            for (int64_t q = 0; q < npar; ++q) {
+                int32_t v = g.parents[q];
+                if (v < 0 || v >= Vm) return fmt("logic group %lld: parent %lld out of range", gi, v);
+                if (K[vo + v] != 2) return fmt("logic group %lld: parent %lld is not binary", gi, v);
             }
-        E += (int64_t)g.n_fac * g.arity;
-        ES += (int64_t)g.n_fac * ksum;
-        F += g.n_fac;
-        P += g.shared_potentials ? g.n_cfg : (int64_t)g.n_cfg * g.n_fac;
-    }
-    for (int gi = 0; gi < d->n_logic_groups; ++gi) {
-        const pgm_logic_group &g = d->logic_groups[gi];
-        if (g.kind != PGM_LOGIC_OR && g.kind != PGM_LOGIC_AND) return fmt("logic group %lld: unknown kind %lld", gi, g.kind);
-        if (g.n_fac < 0) return fmt("logic group %lld: negative n_fac", gi);
-        if (!g.par_off) return fmt("logic group %lld: par_off is NULL", gi);
-        if (g.par_off[0] != 0) return fmt("logic group %lld: par_off[0] must be 0", gi);
-        for (int64_t f = 0; f < g.n_fac; ++f)
-            if (g.par_off[f + 1] < g.par_off[f]) return fmt("logic group %lld: par_off decreases at %lld", gi, f);
-        int64_t npar = g.par_off[g.n_fac];
-        if (npar > 0 && !g.parents) return fmt("logic group %lld: parents is NULL", gi);
-        if (g.n_fac > 0 && !g.child) return fmt("logic group %lld: child is NULL", gi);
-        for (int64_t q = 0; q < npar; ++q) {
-            int32_t v = g.parents[q];
-            if (v < 0 || v >= V) return fmt("logic group %lld: parent %lld out of range", gi, v);
-            if (K[v] != 2) return fmt("logic group %lld: parent %lld is not binary", gi, v);
+            for (int64_t f = 0; f < g.n_fac; ++f) {
+                int32_t v = g.child[f];
+                if (v < 0 || v >= Vm) return fmt("logic group %lld: child %lld out of range", gi, v);
+                if (K[vo + v] != 2) return fmt("logic group %lld: child %lld is not binary", gi, v);
+            }
+            E += npar + g.n_fac;
+            ES += 2 * (npar + g.n_fac);
+            F += g.n_fac;
         }
-        for (int64_t f = 0; f < g.n_fac; ++f) {
-            int32_t v = g.child[f];
-            if (v < 0 || v >= V) return fmt("logic group %lld: child %lld out of range", gi, v);
-            if (K[v] != 2) return fmt("logic group %lld: child %lld is not binary", gi, v);
-        }
-        E += npar + g.n_fac;
-        ES += 2 * (npar + g.n_fac);
-        F += g.n_fac;
     }
     if (E > kI32Max || ES > kI32Max || P > kI32Max) return "graph too large for int32 indexing";
     L->E = E;
@@ -129,81 +149,99 @@ std::string compile_graph(const void *vdesc, HostLayout *L) {
     L->F = F;
     L->P = P;
 
-    // ---- edges, factor-major, with their variable-state offsets
+    // ---- edges, member by member (each member: enumeration groups, then logical
+    // groups), factor-major, with their variable-state offsets
     L->edge_vs.assign(E, 0);
     std::vector<int32_t> edge_es(E + 1, 0), edge_var(E, 0);
     int64_t e = 0, es = 0, pot = 0;
-    for (int gi = 0; gi < d->n_enum_groups; ++gi) {
-        const pgm_enum_group &g = d->enum_groups[gi];
-        HostEnumGroup hg{};
-        EnumSeg &s = hg.seg;
-        s.n_fac = g.n_fac;
-        s.edge_base = (int32_t)e;
-        s.es_base = (int32_t)es;
-        s.pot_base = (int32_t)pot;
-        s.shared = g.shared_potentials ? 1 : 0;
-        s.n_cfg = g.n_cfg;
-        s.arity = g.arity;
-        s.cfg_base = (int32_t)L->cfg_pool.size();
-        int32_t off = 0;
-        for (int j = 0; j < g.arity; ++j) {
-            s.K[j] = g.n_fac > 0 ? K[g.vars[j]] : 1;
-            s.Koff[j] = off;
-            off += s.K[j];
-        }
-        s.es_per_fac = off;
-        for (int c = 0; c < g.n_cfg * g.arity; ++c) L->cfg_pool.push_back((uint8_t)g.cfg[c]);
-        int K0 = s.K[0], K1 = g.arity > 1 ? s.K[1] : 0;
-        hg.variant = kEnumGeneric;
-        if (g.n_fac > 0 && is_dense_pair(g, K0, K1)) {
-            if (K0 == 2) hg.variant = kPair2;
-            else if (K0 == 4) hg.variant = kPair4;
-            else if (K0 == 8) hg.variant = kPair8;
-            else if (K0 == 16) hg.variant = kPair16;
-        }
-        for (int64_t f = 0; f < g.n_fac; ++f)
+    L->members.clear();
+    for (int m = 0; m < n_desc; ++m) {
+        const pgm_graph_desc *d = D[m];
+        const int32_t vo = (int32_t)voff[m];
+        HostMember mem{};
+        mem.var_off = vo;
+        mem.n_vars = d->n_vars;
+        mem.vs_off = L->vs_off[vo];
+        mem.n_var_states = L->vs_off[vo + d->n_vars] - L->vs_off[vo];
+        mem.edge_off = e;
+        mem.es_off = es;
+        mem.pot_off = pot;
+        for (int gi = 0; gi < d->n_enum_groups; ++gi) {
+            const pgm_enum_group &g = d->enum_groups[gi];
+            HostEnumGroup hg{};
+            EnumSeg &s = hg.seg;
+            s.n_fac = g.n_fac;
+            s.edge_base = (int32_t)e;
+            s.es_base = (int32_t)es;
+            s.pot_base = (int32_t)pot;
+            s.shared = g.shared_potentials ? 1 : 0;
+            s.n_cfg = g.n_cfg;
+            s.arity = g.arity;
+            s.cfg_base = (int32_t)L->cfg_pool.size();
+            int32_t off = 0;
             for (int j = 0; j < g.arity; ++j) {
-                int32_t v = g.vars[f * g.arity + j];
-                edge_var[e] = v;
-                L->edge_vs[e] = L->vs_off[v];
-                edge_es[e] = (int32_t)es;
-                es += K[v];
-                ++e;
+                s.K[j] = g.n_fac > 0 ? K[vo + g.vars[j]] : 1;
+                s.Koff[j] = off;
+                off += s.K[j];
             }
-        pot += g.shared_potentials ? g.n_cfg : (int64_t)g.n_cfg * g.n_fac;
-        if (g.n_fac > 0) L->enum_groups.push_back(hg);
-    }
-    for (int gi = 0; gi < d->n_logic_groups; ++gi) {
-        const pgm_logic_group &g = d->logic_groups[gi];
-        HostLogicGroup hg{};
-        LogicSeg &s = hg.seg;
-        s.n_fac = g.n_fac;
-        s.kind = g.kind;
-        s.edge_base = (int32_t)e;
-        s.es_base = (int32_t)es;
-        s.paroff_base = (int32_t)L->paroff_pool.size();
-        int32_t mf = 0;
-        for (int64_t f = 0; f <= g.n_fac; ++f) L->paroff_pool.push_back(g.par_off[f]);
-        for (int64_t f = 0; f < g.n_fac; ++f) {
-            mf = std::max(mf, g.par_off[f + 1] - g.par_off[f]);
-            for (int32_t q = g.par_off[f]; q < g.par_off[f + 1]; ++q) {
-                int32_t v = g.parents[q];
+            s.es_per_fac = off;
+            for (int c = 0; c < g.n_cfg * g.arity; ++c) L->cfg_pool.push_back((uint8_t)g.cfg[c]);
+            int K0 = s.K[0], K1 = g.arity > 1 ? s.K[1] : 0;
+            hg.variant = kEnumGeneric;
+            if (g.n_fac > 0 && is_dense_pair(g, K0, K1)) {
+                if (K0 == 2) hg.variant = kPair2;
+                else if (K0 == 4) hg.variant = kPair4;
+                else if (K0 == 8) hg.variant = kPair8;
+                else if (K0 == 16) hg.variant = kPair16;
+            }
+            for (int64_t f = 0; f < g.n_fac; ++f)
+                for (int j = 0; j < g.arity; ++j) {
+                    int32_t v = vo + g.vars[f * g.arity + j];
+                    edge_var[e] = v;
+                    L->edge_vs[e] = L->vs_off[v];
+                    edge_es[e] = (int32_t)es;
+                    es += K[v];
+                    ++e;
+                }
+            pot += g.shared_potentials ? g.n_cfg : (int64_t)g.n_cfg * g.n_fac;
+            if (g.n_fac > 0) L->enum_groups.push_back(hg);
+        }
+        for (int gi = 0; gi < d->n_logic_groups; ++gi) {
+            const pgm_logic_group &g = d->logic_groups[gi];
+            HostLogicGroup hg{};
+            LogicSeg &s = hg.seg;
+            s.n_fac = g.n_fac;
+            s.kind = g.kind;
+            s.edge_base = (int32_t)e;
+            s.es_base = (int32_t)es;
+            s.paroff_base = (int32_t)L->paroff_pool.size();
+            int32_t mf = 0;
+            for (int64_t f = 0; f <= g.n_fac; ++f) L->paroff_pool.push_back(g.par_off[f]);
+            for (int64_t f = 0; f < g.n_fac; ++f) {
+                mf = std::max(mf, g.par_off[f + 1] - g.par_off[f]);
+                for (int32_t q = g.par_off[f]; q < g.par_off[f + 1]; ++q) {
+                    int32_t v = vo + g.parents[q];
+                    edge_var[e] = v;
+                    L->edge_vs[e] = L->vs_off[v];
+                    edge_es[e] = (int32_t)es;
+                    es += 2;
+                    ++e;
+                }
+                int32_t v = vo + g.child[f];
                 edge_var[e] = v;
                 L->edge_vs[e] = L->vs_off[v];
                 edge_es[e] = (int32_t)es;
                 es += 2;
                 ++e;
             }
-            int32_t v = g.child[f];
-            edge_var[e] = v;
-            L->edge_vs[e] = L->vs_off[v];
-            edge_es[e] = (int32_t)es;
-            es += 2;
-            ++e;
+            s.max_fan = mf;
+            hg.variant = (mf <= kLogicSmallFan) ? kLogicSmall : kLogicWarp;
+            if (g.n_fac > 0) L->logic_groups.push_back(hg);
         }
-        s.max_fan = mf;
-        hg.variant = (mf <= kLogicSmallFan) ? kLogicSmall : kLogicWarp;
-        if (g.n_fac > 0) L->logic_groups.push_back(hg);
+        mem.n_edges = e - mem.edge_off;
+        mem.n_edge_states = es - mem.es_off;
+        mem.n_potentials = pot - mem.pot_off;
+        L->members.push_back(mem);
     }
 
     // ---- variable -> incoming edge-state CSR (ascending edge id)

@@ -120,6 +120,13 @@ struct HostLogicGroup {
     LogicSeg seg;
 };
 
+// Offsets of one member of a batch (a single graph is a batch of one) in the flat
+// arrays of the compiled graph.
+struct HostMember {
+    int64_t var_off, n_vars, vs_off, n_var_states, edge_off, n_edges, es_off, n_edge_states,
+        pot_off, n_potentials;
+};
+
 struct HostLayout {
     int64_t V = 0, VS = 0, E = 0, ES = 0, F = 0, P = 0;
     int32_t max_states = 0, max_degree = 0;
@@ -132,12 +139,12 @@ struct HostLayout {
     bool var_small_identity = false;
     bool all_binary = false;
     std::vector<int32_t> vin_tab4;  // [4 * V] (see DevGraph::vin_tab4), empty if unused
+    std::vector<HostMember> members;
 };
 
-struct GraphDescView;  // forward (defined in compile.cpp from the C-ABI struct)
-
-// Returns "" on success, else an error message.
-std::string compile_graph(const void *desc /* const pgm_graph_desc* */, HostLayout *out);
+// Compiles n_desc graph descriptions (const pgm_graph_desc*) into one graph whose flat
+// arrays hold the members one after the other. Returns "" on success, else an error.
+std::string compile_graph(const void *const *descs, int n_desc, HostLayout *out);
 
 // Kernel launchers (kernels.cu). Each returns cudaGetLastError() of its launches.
 cudaError_t launch_var_pass(const DevGraph &G, const Plan &P, const float *ev, const float *m,

@@ -1,0 +1,110 @@
+"""Batched uneven graphs (pgm_build_batch) and the launch machinery around them.
+
+* Every member's messages and beliefs are bitwise identical alone and inside a mixed
+  batch: the per-factor and per-variable arithmetic does not depend on the batch.
+* A seeded subset of the 256-Potts-grid + RBM workload (T=1, 100 iterations) matches the
+  FP64 oracle to 1e-4.
+* The launch-shape autotuner and CUDA-graph replay change no result.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2202_04110_gb300 import workloads as W
+from tests._parity import assert_beliefs_close, assert_decode_ok
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2202_04110_gb300 import build
+    build.build()
+    from paper_2202_04110_gb300 import binding
+    return binding
+
+
+def _mixed_members():
+    ms = [W.potts_grid(19, 4, 1, T=1.0), W.ising_grid(23, 31, 2, T=1.0), W.potts_grid(33, 16, 3, T=1.0),
+          W.rbm(70, 90, 4, T=1.0), W.potts_grid(16, 2, 5, T=1.0), W.potts_grid(40, 8, 6, T=1.0),
+          W.deconvolution(7, n_img=2, T=1.0)]
+    g, lp, ev = W.random_graph(8, n_vars=30, max_K=4, n_pair=50, n_triple=4, n_or=4, n_and=4)
+    ms.append(W.Problem("random", g, lp, ev, 1.0, 0.5, 20))
+    return ms
+
+
+def _run(binding, graph_or_list, lp, ev, T, n_iters, damping=0.5):
+    import torch
+    g = binding.Graph(graph_or_list)
+    lpt = torch.as_tensor(np.asarray(lp, np.float32)).cuda()
+    evt = torch.as_tensor(np.asarray(ev, np.float32)).cuda()
+    m = g.new_msgs()
+    g.run_bp(lpt, evt, T, damping, n_iters, m)
+    nb = g.beliefs(evt, m, True)
+    dec = g.decode(evt, m)
+    return g, m.cpu().numpy(), nb.cpu().numpy(), dec.cpu().numpy()
+
+
+@pytest.mark.parametrize("T", [1.0, 0.0])
+def test_members_alone_equal_in_batch(gpu, T):
+    members = _mixed_members()
+    batch = W.union(members)
+    gb, mb, nbb, decb = _run(gpu, [p.graph for p in members], batch.log_pot, batch.evidence, T, 17)
+    assert gb.info["n_members"] == len(members)
+    for i, p in enumerate(members):
+        off = gb.member(i)
+        _, m1, nb1, dec1 = _run(gpu, p.graph, p.log_pot, p.evidence, T, 17)
+        assert off["n_edge_states"] == m1.size and off["n_var_states"] == nb1.size
+        ms = mb[off["es_off"]: off["es_off"] + off["n_edge_states"]]
+        np.testing.assert_array_equal(ms, m1, err_msg=f"messages of member {i} ({p.name})")
+        np.testing.assert_array_equal(nbb[off["vs_off"]: off["vs_off"] + off["n_var_states"]], nb1)
+        np.testing.assert_array_equal(decb[off["var_off"]: off["var_off"] + off["n_vars"]], dec1)
+
+
+def test_batch_union_layout_matches_single_graph(gpu):
+    """The batch lays members out exactly as one graph built from their disjoint union."""
+    members = _mixed_members()[:4]
+    batch = W.union(members)
+    _, mb, nbb, _ = _run(gpu, [p.graph for p in members], batch.log_pot, batch.evidence, 1.0, 9)
+    _, mu, nbu, _ = _run(gpu, batch.graph, batch.log_pot, batch.evidence, 1.0, 9)
+    np.testing.assert_array_equal(mb, mu)
+    np.testing.assert_array_equal(nbb, nbu)
+
+
+def test_potts_rbm_subset_vs_oracle(gpu):
+    """A seeded subset of the batched workload: 16 Potts grids (side 16..64, K in
+    {2,4,8,16}) plus the 784x500 RBM, T=1, damping 0.5, 100 iterations."""
+    members = W.potts_batch_members(seed=0, n_grids=16, hi=64, n_iters=100)
+    members.append(W.rbm(784, 500, 1, w_std=0.1, T=1.0, damping=0.5, n_iters=100))
+    batch = W.union(members)
+    _, m, nb, dec = _run(gpu, [p.graph for p in members], batch.log_pot, batch.evidence, 1.0, 100)
+    om, _ = oracle.run_bp(batch.graph, batch.log_pot, batch.evidence, 1.0, 0.5, 100)
+    _, onb, _, _ = oracle.beliefs(batch.graph, batch.evidence, om)
+    assert_beliefs_close(nb, onb, what="potts+rbm subset")
+    assert_decode_ok(dec, onb, batch.graph.num_states, what="potts+rbm subset")
+
+
+def test_autotune_and_cuda_graph_do_not_change_results(gpu):
+    import torch
+    members = _mixed_members()
+    batch = W.union(members)
+    graphs = [p.graph for p in members]
+    lp = torch.as_tensor(batch.log_pot).cuda()
+    ev = torch.as_tensor(batch.evidence).cuda()
+    g = gpu.Graph(graphs)
+    g.set_option(gpu.OPT_CUDA_GRAPH, 0)
+    ref = g.new_msgs()
+    g.run_bp(lp, ev, 1.0, 0.5, 13, ref)
+    before = g.launches()
+    g.autotune(lp, ev, 1.0, 0.5)
+    after = g.launches()
+    assert len(before) == len(after)
+    for k in (0, 1):
+        g.set_option(gpu.OPT_CUDA_GRAPH, k)
+        for rep in range(2):  # second call replays the cached CUDA graph
+            m = g.new_msgs()
+            g.run_bp(lp, ev, 1.0, 0.5, 13, m)
+            assert torch.equal(m, ref), (k, rep, before, after)
