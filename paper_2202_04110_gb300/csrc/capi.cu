@@ -49,6 +49,7 @@ int32_t pgm::set_last_error(int32_t code, const std::string &msg) { return fail(
 
 struct pgm_graph {
     int device = 0;
+    int n_sm = 1;
     pgm_info info{};
     DevGraph G{};
     Plan P{};
@@ -97,31 +98,46 @@ struct Packer {
     }
 };
 
+// Lanes that work on one variable: K for the K-lane kernels, else 1 (per block for
+// kVarBlock).
+int var_lanes(int kind) {
+    switch (kind) {
+        case kVarGroup4: return 4;
+        case kVarGroup8: return 8;
+        case kVarGroup16: return 16;
+        default: return 1;
+    }
+}
+
+// Lanes that work on one factor: K for the K-lane pairwise kernels, 32 for the warp
+// logical kernel, else 1.
+int lanes_per_factor(int variant) {
+    switch (variant) {
+        case kPair4: return 4;
+        case kPair8: return 8;
+        case kPair16: return 16;
+        case kLogicWarp: return 32;
+        default: return 1;
+    }
+}
+
 pgm_status build_plan(const HostLayout &H, pgm_graph *g, Packer &pk, std::vector<size_t> &seg_off,
                       std::vector<int> &seg_kind) {
-    // variable pass
+    // variable pass: one launch per non-empty bucket of variables
     Plan &P = g->P;
-    P.kfix = H.all_binary ? 2 : 0;
-    {
+    for (int kind = 0; kind < kNumVarKinds; ++kind) {
+        const std::vector<int32_t> &bucket = H.var_bucket[kind];
+        if (bucket.empty()) continue;
         VarLaunch L{};
-        L.block_mode = 0;
-        L.n = (int32_t)H.var_small.size();
+        L.kind = kind;
+        L.n = (int32_t)bucket.size();
         L.threads = 256;
-        L.n_blocks = (L.n + 255) / 256;
+        L.n_blocks = (kind == kVarBlock) ? L.n : (int32_t)(((int64_t)L.n * var_lanes(kind) + 255) / 256);
+        L.dense_binary = H.all_binary ? 1 : 0;
         L.list = nullptr;
         P.var.push_back(L);
-        seg_off.push_back(H.var_small_identity ? (size_t)-1 : pk.add(H.var_small.data(), H.var_small.size()));
+        seg_off.push_back(H.var_bucket_identity[kind] ? (size_t)-1 : pk.add(bucket.data(), bucket.size()));
         seg_kind.push_back(-1);
-    }
-    if (!H.var_large.empty()) {
-        VarLaunch L{};
-        L.block_mode = 1;
-        L.n = (int32_t)H.var_large.size();
-        L.threads = 256;
-        L.n_blocks = L.n;
-        P.var.push_back(L);
-        seg_off.push_back(pk.add(H.var_large.data(), H.var_large.size()));
-        seg_kind.push_back(-2);
     }
     // factor pass: one launch per variant, all groups of that variant as segments
     for (int variant = 0; variant < kNumFactorVariants; ++variant) {
@@ -167,19 +183,21 @@ pgm_status build_plan(const HostLayout &H, pgm_graph *g, Packer &pk, std::vector
                                              reinterpret_cast<const char *>(segs.data() + segs.size()));
         } else {
             std::vector<EnumSeg> segs;
-            int threads = (variant == kPair16 || variant == kEnumGeneric) ? 128 : 256;
+            int threads = (variant == kEnumGeneric) ? 128 : 256;
+            const int per_block = threads / lanes_per_factor(variant);
             int32_t blk = 0;
             for (const HostEnumGroup &hg : H.enum_groups) {
                 if (hg.variant != variant) continue;
                 EnumSeg s = hg.seg;
                 s.block_begin = blk;
-                blk += (s.n_fac + threads - 1) / threads;
+                blk += (s.n_fac + per_block - 1) / per_block;
                 segs.push_back(s);
             }
             if (segs.empty()) continue;
             L.n_seg = (int32_t)segs.size();
             L.n_blocks = blk;
             L.threads = threads;
+            L.max_blocks = g->n_sm * 8;
             P.factor.push_back(L);
             seg_off.push_back(pk.add(segs.data(), segs.size()));
             seg_kind.push_back(variant);
@@ -236,6 +254,8 @@ static pgm_status build_from_descs(const void *const *descs, int n, pgm_graph **
         delete g;
         return cuda_fail(ce, "cudaGetDevice");
     }
+    if (cudaDeviceGetAttribute(&g->n_sm, cudaDevAttrMultiProcessorCount, g->device) != cudaSuccess || g->n_sm < 1)
+        g->n_sm = 1;
     Packer pk;
     size_t o_vs = pk.add(H.vs_off.data(), H.vs_off.size());
     size_t o_vin_off = pk.add(H.vin_off.data(), H.vin_off.size());
@@ -266,7 +286,7 @@ static pgm_status build_from_descs(const void *const *descs, int n, pgm_graph **
     g->index_mem = dmem;
     size_t es_bytes = align_up(std::max<int64_t>(H.ES, 1) * sizeof(float), 256);
     size_t vs_bytes = align_up(std::max<int64_t>(H.VS, 1) * sizeof(float), 256);
-    size_t hd_bytes = H.var_large.empty() ? 0 : 2 * es_bytes;
+    size_t hd_bytes = H.var_bucket[kVarBlock].empty() ? 0 : 2 * es_bytes;
     char *smem = nullptr;
     ce = cudaMalloc(&smem, es_bytes + vs_bytes + 256 + hd_bytes);
     if (ce != cudaSuccess) {
@@ -379,12 +399,13 @@ pgm_status pgm_check_desc(const pgm_graph_desc *desc, pgm_info *info) {
     info->max_states = H.max_states;
     info->max_degree = H.max_degree;
     info->n_members = 1;
+    size_t nb = 0;
+    for (int kk = 0; kk < kNumVarKinds; ++kk) nb += H.var_bucket_identity[kk] ? 0 : H.var_bucket[kk].size();
     size_t idx = (H.vs_off.size() + H.vin_off.size() + H.vin_es.size() + H.edge_vs.size() +
-                  H.paroff_pool.size() + H.var_small.size() + H.var_large.size()) * sizeof(int32_t) +
-                 H.cfg_pool.size();
+                  H.paroff_pool.size() + nb + H.vin_tab4.size()) * sizeof(int32_t) + H.cfg_pool.size();
     size_t es_bytes = align_up(std::max<int64_t>(H.ES, 1) * sizeof(float), 256);
     info->device_bytes = (int64_t)(idx + es_bytes + align_up(std::max<int64_t>(H.VS, 1) * sizeof(float), 256) +
-                                   256 + (H.var_large.empty() ? 0 : 2 * es_bytes));
+                                   256 + (H.var_bucket[kVarBlock].empty() ? 0 : 2 * es_bytes));
     return PGM_OK;
 }
 
@@ -517,8 +538,7 @@ pgm_status pgm_run_bp(pgm_graph *g, const float *log_pot, const float *evidence,
 // Thread-block shapes a factor launch may use (within the kernels' launch bounds).
 static std::vector<int> shape_candidates(int variant) {
     switch (variant) {
-        case kPair2: case kPair4: case kPair8: case kLogicSmall: return {64, 128, 256};
-        case kPair16: return {64, 128};
+        case kPair2: case kPair4: case kPair8: case kPair16: case kLogicSmall: return {64, 128, 256};
         case kEnumGeneric: return {32, 64, 128};
         case kLogicWarp: return {32, 64, 128};
         default: return {};
@@ -531,7 +551,7 @@ static bool replan_factor_launch(pgm_graph *g, size_t li, int threads, cudaStrea
     FactorLaunch &L = g->P.factor[li];
     std::vector<char> &host = g->factor_segs_host[li];
     const bool logic = (L.variant == kLogicSmall || L.variant == kLogicWarp);
-    const int per_block = (L.variant == kLogicWarp) ? threads / 32 : threads;
+    const int per_block = threads / lanes_per_factor(L.variant);
     size_t smem = 0;
     if (L.variant == kLogicWarp) {
         smem = (size_t)per_block * 3 * L.max_fan * sizeof(float);
@@ -584,7 +604,6 @@ pgm_status pgm_autotune(pgm_graph *g, const float *log_pot, const float *evidenc
         for (int c : shape_candidates(g->P.factor[li].variant)) {
             if (!replan_factor_launch(g, li, c, s)) continue;
             Plan one;
-            one.kfix = g->P.kfix;
             one.factor.push_back(g->P.factor[li]);
             launch_factor_pass(g->G, one, log_pot, g->b, evidence, m_in, m_out, T, damping, s);
             cudaEventRecord(e0, s);
@@ -603,14 +622,13 @@ pgm_status pgm_autotune(pgm_graph *g, const float *log_pot, const float *evidenc
     }
     // thread-per-variable launches: block size
     for (VarLaunch &L : g->P.var) {
-        if (L.block_mode || L.n == 0 || g->G.vin_tab4) continue;
+        if (L.kind == kVarBlock || L.n == 0 || g->G.vin_tab4) continue;
         int best = L.threads;
         float best_ms = 1e30f;
         for (int c : {128, 256}) {
             L.threads = c;
-            L.n_blocks = (L.n + c - 1) / c;
+            L.n_blocks = (int32_t)(((int64_t)L.n * var_lanes(L.kind) + c - 1) / c);
             Plan one;
-            one.kfix = g->P.kfix;
             one.var.push_back(L);
             launch_var_pass(g->G, one, evidence, m_in, g->b, kVarIter, nullptr, s);
             cudaEventRecord(e0, s);
@@ -625,7 +643,7 @@ pgm_status pgm_autotune(pgm_graph *g, const float *log_pot, const float *evidenc
             }
         }
         L.threads = best;
-        L.n_blocks = (L.n + best - 1) / best;
+        L.n_blocks = (int32_t)(((int64_t)L.n * var_lanes(L.kind) + best - 1) / best);
     }
     cudaError_t e = cudaStreamSynchronize(s);
     cudaEventDestroy(e0);
@@ -644,9 +662,9 @@ pgm_status pgm_launch_info(const pgm_graph *g, int32_t i, int32_t *kind, int32_t
     if (i < nv) {
         const VarLaunch &L = g->P.var[i];
         if (kind) *kind = 0;
-        if (variant) *variant = L.block_mode ? 1 : (g->G.vin_tab4 ? 2 : 0);
-        if (threads) *threads = L.block_mode ? kVarBlockThreads : (g->G.vin_tab4 ? 256 : L.threads);
-        if (n_blocks) *n_blocks = L.n_blocks;
+        if (variant) *variant = g->G.vin_tab4 ? 6 : L.kind;
+        if (threads) *threads = L.kind == kVarBlock ? kVarBlockThreads : (g->G.vin_tab4 ? 256 : L.threads);
+        if (n_blocks) *n_blocks = g->G.vin_tab4 ? (int32_t)((g->info.n_vars + 255) / 256) : L.n_blocks;
     } else {
         const FactorLaunch &L = g->P.factor[i - nv];
         if (kind) *kind = 1;

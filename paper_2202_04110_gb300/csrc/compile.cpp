@@ -261,18 +261,33 @@ std::string compile_graph(const void *const *vdescs, int n_desc, HostLayout *L) 
     // values from the exact leave-one-out buffer (edge_vs = -1 marks them)
     if ((int64_t)maxdeg > (int64_t)kVarMaxTiles * kVarTile)
         return fmt("a variable has %lld factors; at most %lld are supported", maxdeg, (long long)kVarMaxTiles * kVarTile);
-    L->var_small.clear();
-    L->var_large.clear();
+    for (int kk = 0; kk < kNumVarKinds; ++kk) L->var_bucket[kk].clear();
     for (int64_t v = 0; v < V; ++v) {
-        int32_t deg = L->vin_off[v + 1] - L->vin_off[v];
-        if (deg > kVarBlockDegree) L->var_large.push_back((int32_t)v);
-        else L->var_small.push_back((int32_t)v);
+        const int32_t k0 = L->vin_off[v], k1 = L->vin_off[v + 1];
+        int kind;
+        if (k1 - k0 > kVarBlockDegree) {
+            kind = kVarBlock;
+        } else if (K[v] == 2) {
+            bool even = (L->vs_off[v] & 1) == 0;
+            for (int32_t k = k0; k < k1 && even; ++k) even = (L->vin_es[k] & 1) == 0;
+            kind = even ? kVarBinary : kVarGeneric;
+        } else if (K[v] == 4) {
+            kind = kVarGroup4;
+        } else if (K[v] == 8) {
+            kind = kVarGroup8;
+        } else if (K[v] == 16) {
+            kind = kVarGroup16;
+        } else {
+            kind = kVarGeneric;
+        }
+        L->var_bucket[kind].push_back((int32_t)v);
     }
+    for (int kk = 0; kk < kNumVarKinds; ++kk) L->var_bucket_identity[kk] = ((int64_t)L->var_bucket[kk].size() == V);
     for (int64_t i = 0; i < E; ++i) {
         int32_t v = edge_var[i];
         if (L->vin_off[v + 1] - L->vin_off[v] > kVarBlockDegree) L->edge_vs[i] = -1;
     }
-    L->var_small_identity = ((int64_t)L->var_small.size() == V);
+
     L->all_binary = (kmax == 2);
     for (int64_t v = 0; v < V && L->all_binary; ++v)
         if (K[v] != 2) L->all_binary = false;

@@ -396,7 +396,7 @@ __device__ __forceinline__ float lse_row(const float (&z)[K], float T, float inv
 // even, float2 loads).
 template <int KFIX, int MODE>
 __global__ void __launch_bounds__(256) k_var_thread(DevGraph G, const int32_t *__restrict__ list, int n,
-                                                    const float *__restrict__ ev,
+                                                    int dense_binary, const float *__restrict__ ev,
                                                     const float *__restrict__ m,
                                                     float *__restrict__ out,
                                                     int32_t *__restrict__ dec) {
@@ -405,7 +405,7 @@ __global__ void __launch_bounds__(256) k_var_thread(DevGraph G, const int32_t *_
     const int v = list ? __ldg(list + t) : t;
     const int k0 = __ldg(G.vin_off + v), k1 = __ldg(G.vin_off + v + 1);
     if constexpr (KFIX == 2) {
-        const int vs = 2 * v;
+        const int vs = dense_binary ? 2 * v : __ldg(G.vs_off + v);
         const float2 e = __ldg(reinterpret_cast<const float2 *>(ev + vs));
         FF s0 = ff_make(e.x), s1 = ff_make(e.y);
         for (int k = k0; k < k1; ++k) {
@@ -470,16 +470,16 @@ __global__ void __launch_bounds__(256) k_var_thread(DevGraph G, const int32_t *_
                 return;
             }
             if (nan && MODE == kVarNormalised) atomicOr(G.flags, kFlagNaN);
-            float acc = 0.f;
+            float acc = 0.f;  // sum over the other states of e^r (the best state adds 1)
             for (int x = 0; x < K; ++x) {
                 FF s = ff_make(__ldg(ev + vs + x));
                 for (int k = k0; k < k1; ++k) s = ff_add(s, __ldg(m + __ldg(G.vin_es + k) + x));
                 const float r = (x == arg) ? 0.f : ff_diff(s, best);
                 out[vs + x] = r;
-                if (MODE == kVarNormalised) acc += expf(r);
+                if (MODE == kVarNormalised && x != arg) acc += expf(r);
             }
             if constexpr (MODE == kVarNormalised) {
-                const float z = logf(acc);
+                const float z = log1pf(acc);
                 for (int x = 0; x < K; ++x) out[vs + x] -= z;
             }
         }
@@ -536,6 +536,57 @@ __global__ void __launch_bounds__(256) k_var_tab4(DevGraph G, int n, const float
             const float zz = log1pf(expf(fminf(r0, r1)));
             reinterpret_cast<float2 *>(out)[v] = make_float2(r0 - zz, r1 - zz);
         }
+    }
+}
+
+// K lanes per variable (K = 4, 8, 16): lane x sums state x over the incoming edges
+// (coalesced across the group), float-float, ascending edge order; the best state is
+// found across the group (exact comparison, lowest state on ties).
+template <int K, int MODE>
+__global__ void __launch_bounds__(256) k_var_group(DevGraph G, const int32_t *__restrict__ list, int n,
+                                                   const float *__restrict__ ev, const float *__restrict__ m,
+                                                   float *__restrict__ out, int32_t *__restrict__ dec) {
+    const int x = threadIdx.x & (K - 1);
+    const int t_raw = (blockIdx.x * blockDim.x + threadIdx.x) / K;
+    const bool valid = t_raw < n;
+    const int t = valid ? t_raw : n - 1;
+    const int v = list ? __ldg(list + t) : t;
+    const int vs = __ldg(G.vs_off + v);
+    const int k0 = __ldg(G.vin_off + v), k1 = __ldg(G.vin_off + v + 1);
+    FF s = ff_make(__ldg(ev + vs + x));
+    for (int k = k0; k < k1; ++k) s = ff_add(s, __ldg(m + __ldg(G.vin_es + k) + x));
+    // best state: the largest rounded sum, lowest state among equal ones (states whose
+    // float-float sums differ by less than one FP32 ulp count as tied)
+    const float rs = s.hi + s.lo;
+    float mx = rs;
+#pragma unroll
+    for (int d = K / 2; d > 0; d >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, d, K));
+    const unsigned gshift = (threadIdx.x & 31) & ~(K - 1);
+    const unsigned at_max = (__ballot_sync(0xffffffffu, rs == mx) >> gshift) & ((1u << K) - 1u);
+    const int arg = at_max ? __ffs(at_max) - 1 : 0;
+    const FF best{__shfl_sync(0xffffffffu, s.hi, arg, K), __shfl_sync(0xffffffffu, s.lo, arg, K)};
+    if constexpr (MODE == kVarDecode) {
+        if (valid && x == 0) dec[v] = arg;
+        return;
+    }
+    if constexpr (MODE == kVarBeliefs) {
+        if (valid) out[vs + x] = s.hi + s.lo;
+        return;
+    }
+    const bool dead = best.hi == kNegInf;  // every state -inf
+    const float r = dead ? kNegInf : (x == arg ? 0.f : ff_diff(s, best));
+    if constexpr (MODE == kVarIter) {
+        if (valid) out[vs + x] = r;
+    } else {
+        float acc = (x == arg || dead) ? 0.f : expf(r);
+#pragma unroll
+        for (int d = K / 2; d > 0; d >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, d, K);
+        const bool nan = __any_sync(0xffffffffu, s.hi != s.hi);
+        if (valid && x == 0) {
+            if (dead) atomicOr(G.flags, kFlagContradiction);
+            if (nan) atomicOr(G.flags, kFlagNaN);
+        }
+        if (valid) out[vs + x] = dead ? kNegInf : r - log1pf(acc);
     }
 }
 
@@ -597,7 +648,7 @@ __global__ void __launch_bounds__(kVarBlockThreads) k_var_block(DevGraph G, cons
     __shared__ float sh[64];
     __shared__ FF tile_tot[kVarMaxTiles];
     __shared__ FF sb[kMaxStates];
-    const int v = __ldg(list + blockIdx.x);
+    const int v = list ? __ldg(list + blockIdx.x) : (int)blockIdx.x;
     const int vs = __ldg(G.vs_off + v), K = __ldg(G.vs_off + v + 1) - vs;
     const int k0 = __ldg(G.vin_off + v), k1 = __ldg(G.vin_off + v + 1);
     const int deg = k1 - k0;
@@ -679,14 +730,14 @@ __global__ void __launch_bounds__(kVarBlockThreads) k_var_block(DevGraph G, cons
             for (int x = 0; x < K; ++x) out[vs + x] = kNegInf;
             return;
         }
-        float acc = 0.f;
+        float acc = 0.f;  // sum over the other states of e^r (the best state adds 1)
         for (int x = 0; x < K; ++x) {
             const float r = (x == arg) ? 0.f : ff_diff(sb[x], sb[arg]);
             out[vs + x] = r;
-            acc += expf(r);
+            if (x != arg) acc += expf(r);
         }
         if (MODE == kVarNormalised) {
-            const float z = logf(acc);
+            const float z = log1pf(acc);
             for (int x = 0; x < K; ++x) out[vs + x] -= z;
         }
     }
@@ -699,13 +750,45 @@ __global__ void __launch_bounds__(kVarBlockThreads) k_var_block(DevGraph G, cons
 // The factor-to-variable update of one dense pairwise factor from its two
 // variable-to-factor vectors v0, v1 and stored messages mo0, mo1; writes the damped,
 // normalised messages.
+// Linear-domain form for a table shared by the group (sum-product only): with
+// E[x][y] = exp((phi(x,y) - tmax) / T) precomputed per block and w(y) = exp((v(y) - vmax) / T),
+//   LSE_T over y of [phi(x,y) + v(y)] = T log(sum_y E[x][y] w(y)) + vmax + tmax.
+// The sum is at least E[x][y*] >= exp(-(table range) / T), so nothing underflows when
+// the range is at most 60 T (checked per block).
+template <int K>
+__device__ __forceinline__ void lse_rows_linear(const float *tabE, bool transpose, const float (&v)[K],
+                                                float tmax, float T, float invT, float (&o)[K]) {
+    float vmax = kNegInf;
+#pragma unroll
+    for (int y = 0; y < K; ++y) vmax = fmaxf(vmax, v[y]);
+    if (vmax == kNegInf) {
+#pragma unroll
+        for (int x = 0; x < K; ++x) o[x] = kNegInf;
+        return;
+    }
+    float w[K];
+#pragma unroll
+    for (int y = 0; y < K; ++y) w[y] = __expf((v[y] - vmax) * invT);
+#pragma unroll
+    for (int x = 0; x < K; ++x) {
+        float s = 0.f;
+#pragma unroll
+        for (int y = 0; y < K; ++y) s = fmaf(transpose ? tabE[y * K + x] : tabE[x * K + y], w[y], s);
+        o[x] = T * logf(s) + vmax + tmax;
+    }
+}
+
 template <int K, bool MAXP>
 __device__ __forceinline__ void pair_update(const float *phi_sh, const float *phi_g, float (&v0)[K],
                                             float (&v1)[K], const float (&mo0)[K], const float (&mo1)[K],
                                             float *m_new0, float *m_new1, float T, float invT,
-                                            float damping, uint32_t *flags) {
+                                            float damping, uint32_t *flags,
+                                            const float *tabE = nullptr, float tmax = 0.f) {
     float o0[K], o1[K];
-    if constexpr (K <= 4) {
+    if (!MAXP && K >= 4 && tabE != nullptr) {
+        lse_rows_linear<K>(tabE, false, v1, tmax, T, invT, o0);
+        lse_rows_linear<K>(tabE, true, v0, tmax, T, invT, o1);
+    } else if constexpr (K <= 4) {
         float phi[K * K];
         if (phi_sh) {
 #pragma unroll
@@ -749,6 +832,28 @@ __device__ __forceinline__ void pair_update(const float *phi_sh, const float *ph
     store_n<K>(m_new1, o1);
 }
 
+// Per block: E[i] = exp((tab[i] - tmax) / T) for a shared table, when its range is at
+// most 60 T; returns false (E unused) otherwise or for max-product.
+template <int K, bool MAXP>
+__device__ __forceinline__ bool prepare_linear_table(const float *tab, float *tabE, float *tinfo, float invT) {
+    if (MAXP || K < 4) return false;
+    if (threadIdx.x == 0) {
+        float mx = kNegInf, mn = CUDART_INF_F;
+        for (int i = 0; i < K * K; ++i) {
+            mx = fmaxf(mx, tab[i]);
+            mn = fminf(mn, tab[i]);
+        }
+        tinfo[0] = mx;
+        tinfo[1] = (isfinite(mx) && isfinite(mn) && (mx - mn) * invT <= 60.f) ? 1.f : 0.f;
+    }
+    __syncthreads();
+    const bool use = tinfo[1] != 0.f;
+    if (use)
+        for (int i = threadIdx.x; i < K * K; i += blockDim.x) tabE[i] = expf((tab[i] - tinfo[0]) * invT);
+    __syncthreads();
+    return use;
+}
+
 // The rare case of a pairwise factor: an edge of a high-degree variable, or a stored
 // message entry that is -inf or large. Kept out of line so that the common path holds
 // no state across a call.
@@ -772,11 +877,15 @@ k_pair(DevGraph G, const EnumSeg *__restrict__ segs, int n_seg, const float *__r
        const float *__restrict__ b, const float *__restrict__ ev, const float *__restrict__ m_old,
        float *__restrict__ m_new, float T, float invT, float damping) {
     __shared__ float tab[K * K];
+    __shared__ float tabE[K >= 4 ? K * K : 1];
+    __shared__ float tinfo[2];
     const EnumSeg *S = segs + find_seg(segs, n_seg, blockIdx.x);
     const int n_fac = __ldg(&S->n_fac), shared = __ldg(&S->shared), pot_base = __ldg(&S->pot_base);
+    bool linear = false;
     if (shared) {
         for (int i = threadIdx.x; i < K * K; i += blockDim.x) tab[i] = __ldg(pot + pot_base + i);
         __syncthreads();
+        linear = prepare_linear_table<K, MAXP>(tab, tabE, tinfo, invT);
     }
     const int f = (blockIdx.x - __ldg(&S->block_begin)) * blockDim.x + threadIdx.x;
     if (f >= n_fac) return;
@@ -811,7 +920,256 @@ k_pair(DevGraph G, const EnumSeg *__restrict__ segs, int n_seg, const float *__r
         v0[x] -= mo0[x];
         v1[x] -= mo1[x];
     }
-    pair_update<K, MAXP>(phi_sh, phi_g, v0, v1, mo0, mo1, m_new + es0, m_new + es1, T, invT, damping, G.flags);
+    pair_update<K, MAXP>(phi_sh, phi_g, v0, v1, mo0, mo1, m_new + es0, m_new + es1, T, invT, damping, G.flags,
+                         linear ? tabE : nullptr, linear ? tinfo[0] : 0.f);
+}
+
+// ---- K lanes per factor (K = 4, 8, 16): lane x owns state x of both edges ----------
+
+template <int K>
+__device__ __forceinline__ float group_max(float v) {
+#pragma unroll
+    for (int d = K / 2; d > 0; d >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, d, K));
+    return v;
+}
+
+// normalise-damp-normalise of one edge's state x across its K-lane group
+template <int K>
+__device__ __forceinline__ float group_finish(float t, float mo, float damping, uint32_t *flags, bool lead) {
+    float mx = group_max<K>(t);
+    if (mx == kNegInf) {
+        t = 0.f;
+        if (lead) atomicOr(flags, kFlagContradiction);
+    } else {
+        t -= mx;
+    }
+    if (damping != 0.f) t = damping * mo + (1.f - damping) * t;
+    mx = group_max<K>(t);
+    if (mx == kNegInf) {
+        t = 0.f;
+        if (lead) atomicOr(flags, kFlagContradiction);
+    } else {
+        t -= mx;
+    }
+    return t;
+}
+
+// Variable-to-factor value of state x of one edge, for the rare cases: an edge of a
+// high-degree variable (float-float leave-one-out pairs, normalised across the group) or
+// a stored entry that is -inf or large (explicit leave-one-out sum).
+// Called by the K lanes of one group together (gmask = those lanes).
+template <int K>
+__device__ __noinline__ float group_v2f_rare(const DevGraph G, const float *ev, const float *m_old, int vs,
+                                             int es, int x, unsigned gmask) {
+    if (vs < 0) {
+        const float2 p = hd_pair(G, es, x);
+        // the edge's largest state, compared exactly on the pairs
+        float2 best = p;
+#pragma unroll
+        for (int d = K / 2; d > 0; d >>= 1) {
+            float2 o = make_float2(__shfl_xor_sync(gmask, best.x, d, K), __shfl_xor_sync(gmask, best.y, d, K));
+            if (hd_gt(o, best)) best = o;
+        }
+        if (best.x == -CUDART_INF_F) return -CUDART_INF_F;
+        return hd_rel(p, best);
+    }
+    int lo = 0, hi = G.V - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (G.vs_off[mid] <= vs) lo = mid;
+        else hi = mid - 1;
+    }
+    FF s = ff_make(ev[vs + x]);
+    for (int k = G.vin_off[lo]; k < G.vin_off[lo + 1]; ++k) {
+        const int e2 = G.vin_es[k];
+        if (e2 != es) s = ff_add(s, m_old[e2 + x]);
+    }
+    return s.hi + s.lo;
+}
+
+// LSE_T over y of (a(y) + v(y)) where lane y of the group holds v(y); a(y) from `row`.
+template <int K, bool MAXP>
+__device__ __forceinline__ float group_lse(float v, const float (&a)[K], float T, float invT) {
+    float z[K];
+    float mx = kNegInf;
+#pragma unroll
+    for (int y = 0; y < K; ++y) {
+        z[y] = a[y] + __shfl_sync(0xffffffffu, v, y, K);
+        mx = fmaxf(mx, z[y]);
+    }
+    if (MAXP || mx == kNegInf) return mx;
+    float s = 0.f;
+#pragma unroll
+    for (int y = 0; y < K; ++y) s += expf((z[y] - mx) * invT);
+    return mx + T * logf(s);
+}
+
+// Row stride of the padded exp tables: K + 4 floats keeps rows 16-byte aligned and makes
+// the float4 row reads of 8 consecutive lanes fall on distinct bank groups.
+template <int K>
+constexpr int kRowPad = K + 4;
+
+// Per block, for a shared K x K table phi (row-major, phi[x*K + y]): tab[y*K + x] =
+// phi(y, x) (column reads by lane x are contiguous) and tabT[y*K + x] = phi(x, y) (row
+// reads by lane x are contiguous); for sum-product, when the table's range is at most
+// 60 T (tinfo[1] = 1), E = exp((phi - max phi) / T) padded row-major in tabE (row x of E)
+// and tabET (row x of E^T).
+template <int K, bool MAXP>
+__device__ __forceinline__ void group_tables(const float *__restrict__ phi, float *tab, float *tabT, float *tabE,
+                                             float *tabET, float *tinfo, float invT) {
+    for (int i = threadIdx.x; i < K * K; i += blockDim.x) {
+        const float p = __ldg(phi + i);
+        tab[i] = p;
+        tabT[(i % K) * K + i / K] = p;
+    }
+    if (!MAXP && threadIdx.x < 32) {
+        float mx = kNegInf, mn = CUDART_INF_F;
+        for (int i = threadIdx.x; i < K * K; i += 32) {
+            const float p = __ldg(phi + i);
+            mx = fmaxf(mx, p);
+            mn = fminf(mn, p);
+        }
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) {
+            mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, d));
+            mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, d));
+        }
+        if (threadIdx.x == 0) {
+            tinfo[0] = mx;
+            tinfo[1] = (isfinite(mx) && isfinite(mn) && (mx - mn) * invT <= 60.f) ? 1.f : 0.f;
+        }
+    }
+    __syncthreads();
+    if (!MAXP && tinfo[1] != 0.f) {
+        for (int i = threadIdx.x; i < K * K; i += blockDim.x) {
+            const int r = i / K, c = i % K;
+            const float e = expf((tab[i] - tinfo[0]) * invT);
+            tabE[r * kRowPad<K> + c] = e;   // E(r, c)
+            tabET[c * kRowPad<K> + r] = e;  // E^T(c, r)
+        }
+    }
+    __syncthreads();
+}
+
+// Dense pairwise tables with K states (Potts): K lanes per factor. The launch's
+// factors are cut into chunks of blockDim / K factors ("virtual blocks", numbered as in
+// the segments' block ranges); each physical block walks a contiguous range of chunks
+// and rebuilds its shared-memory tables only when the chunk's group changes, so the
+// per-table work is paid once per block rather than once per chunk.
+template <int K, bool MAXP>
+__global__ void __launch_bounds__(256, 4)
+k_pair_group(DevGraph G, const EnumSeg *__restrict__ segs, int n_seg, int n_vblocks, const float *__restrict__ pot,
+             const float *__restrict__ b, const float *__restrict__ ev, const float *__restrict__ m_old,
+             float *__restrict__ m_new, float T, float invT, float damping) {
+    __shared__ float tab[K * K], tabT[K * K];
+    __shared__ __align__(16) float tabE[MAXP ? 4 : K * kRowPad<K>];
+    __shared__ __align__(16) float tabET[MAXP ? 4 : K * kRowPad<K>];
+    __shared__ __align__(16) float wsh[MAXP ? 4 : 2 * 256];  // per lane: w1, then w0 at +blockDim
+    __shared__ float tinfo[2];
+    const int per = (n_vblocks + gridDim.x - 1) / gridDim.x;
+    const int vb_begin = blockIdx.x * per;
+    const int vb_end = min(vb_begin + per, n_vblocks);
+    const int x = threadIdx.x & (K - 1);
+    int cur = -1;
+    int si = vb_begin < vb_end ? find_seg(segs, n_seg, vb_begin) : 0;
+    bool linear = false, shared = false;
+    // chunk coordinates and the loads that do not depend on other loads, one chunk ahead
+    int nsi = si, nvs0 = 0, nvs1 = 0;
+    float nmo0 = 0.f, nmo1 = 0.f;
+    auto fetch = [&](int vb, int &s_idx, int &vs0_, int &vs1_, float &mo0_, float &mo1_) {
+        while (s_idx + 1 < n_seg && __ldg(&segs[s_idx + 1].block_begin) <= vb) ++s_idx;
+        const EnumSeg *Sx = segs + s_idx;
+        const int nf = __ldg(&Sx->n_fac);
+        int ff = (vb - __ldg(&Sx->block_begin)) * (blockDim.x / K) + threadIdx.x / K;
+        if (ff >= nf) ff = nf - 1;
+        const int ee = __ldg(&Sx->edge_base) + 2 * ff;
+        const int e0 = __ldg(&Sx->es_base) + 2 * K * ff;
+        vs0_ = __ldg(G.edge_vs + ee);
+        vs1_ = __ldg(G.edge_vs + ee + 1);
+        mo0_ = __ldg(m_old + e0 + x);
+        mo1_ = __ldg(m_old + e0 + K + x);
+    };
+    if (vb_begin < vb_end) fetch(vb_begin, nsi, nvs0, nvs1, nmo0, nmo1);
+    for (int vb = vb_begin; vb < vb_end; ++vb) {
+        si = nsi;
+        const int vs0 = nvs0, vs1 = nvs1;
+        const float mo0 = nmo0, mo1 = nmo1;
+        const EnumSeg *S = segs + si;
+        const int n_fac = __ldg(&S->n_fac), pot_base = __ldg(&S->pot_base);
+        // beliefs of this chunk, then the next chunk's independent loads
+        const bool fast0 = vs0 >= 0, fast1 = vs1 >= 0;
+        const float bb0 = fast0 ? __ldg(b + vs0 + x) : 0.f;
+        const float bb1 = fast1 ? __ldg(b + vs1 + x) : 0.f;
+        if (vb + 1 < vb_end) fetch(vb + 1, nsi, nvs0, nvs1, nmo0, nmo1);
+        if (si != cur) {  // uniform across the block
+            cur = si;
+            shared = __ldg(&S->shared) != 0;
+            __syncthreads();
+            if (shared) {
+                group_tables<K, MAXP>(pot + pot_base, tab, tabT, tabE, tabET, tinfo, invT);
+                linear = !MAXP && tinfo[1] != 0.f;
+            } else {
+                linear = false;
+            }
+        }
+        const int f_raw = (vb - __ldg(&S->block_begin)) * (blockDim.x / K) + threadIdx.x / K;
+        const bool valid = f_raw < n_fac;
+        const int f = valid ? f_raw : n_fac - 1;  // idle lanes shadow the last factor, store nothing
+        const int es0 = __ldg(&S->es_base) + 2 * K * f, es1 = es0 + K;
+        // rare-case vote within the group (uniform across its K lanes): any state of the
+        // edge needing the exact path
+        const unsigned gmask = ((1u << K) - 1u) << ((threadIdx.x & 31) & ~(K - 1));
+        const unsigned b0 = __ballot_sync(0xffffffffu, needs_exact(mo0)) & gmask;
+        const unsigned b1 = __ballot_sync(0xffffffffu, needs_exact(mo1)) & gmask;
+        float v0, v1;
+        if (vs0 < 0 || b0) v0 = group_v2f_rare<K>(G, ev, m_old, vs0, es0, x, gmask);
+        else v0 = bb0 - mo0;
+        if (vs1 < 0 || b1) v1 = group_v2f_rare<K>(G, ev, m_old, vs1, es1, x, gmask);
+        else v1 = bb1 - mo1;
+        float o0, o1;
+        if (!MAXP && linear) {
+            // to variable 0, state x: row x of E against w1; to variable 1: column x against w0
+            const float vmax1 = group_max<K>(v1), vmax0 = group_max<K>(v0);
+            const float w1 = vmax1 == kNegInf ? 0.f : __expf((v1 - vmax1) * invT);
+            const float w0 = vmax0 == kNegInf ? 0.f : __expf((v0 - vmax0) * invT);
+            // stage the group's weights; the group's lanes are in one warp
+            const int gbase = threadIdx.x & ~(K - 1);
+            wsh[threadIdx.x] = w1;
+            wsh[blockDim.x + threadIdx.x] = w0;
+            __syncwarp();
+            const float4 *er = reinterpret_cast<const float4 *>(tabE + x * kRowPad<K>);   // row x of E
+            const float4 *ec = reinterpret_cast<const float4 *>(tabET + x * kRowPad<K>);  // row x of E^T
+            const float4 *w1v = reinterpret_cast<const float4 *>(wsh + gbase);
+            const float4 *w0v = reinterpret_cast<const float4 *>(wsh + blockDim.x + gbase);
+            float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+            for (int j = 0; j < K / 4; ++j) {
+                const float4 a = er[j], wa = w1v[j], c = ec[j], wc = w0v[j];
+                s0 = fmaf(a.x, wa.x, fmaf(a.y, wa.y, fmaf(a.z, wa.z, fmaf(a.w, wa.w, s0))));
+                s1 = fmaf(c.x, wc.x, fmaf(c.y, wc.y, fmaf(c.z, wc.z, fmaf(c.w, wc.w, s1))));
+            }
+            __syncwarp();
+            o0 = vmax1 == kNegInf ? kNegInf : T * logf(s0) + vmax1 + tinfo[0];
+            o1 = vmax0 == kNegInf ? kNegInf : T * logf(s1) + vmax0 + tinfo[0];
+        } else {
+            float row[K], col[K];
+            const float *phi_g = pot + pot_base + (size_t)f * (K * K);
+#pragma unroll
+            for (int y = 0; y < K; ++y) {
+                row[y] = shared ? tabT[y * K + x] : __ldg(phi_g + x * K + y);
+                col[y] = shared ? tab[y * K + x] : __ldg(phi_g + y * K + x);
+            }
+            o0 = group_lse<K, MAXP>(v1, row, T, invT);
+            o1 = group_lse<K, MAXP>(v0, col, T, invT);
+        }
+        const bool lead = valid && x == 0;
+        o0 = group_finish<K>(o0, mo0, damping, G.flags, lead);
+        o1 = group_finish<K>(o1, mo1, damping, G.flags, lead);
+        if (valid) {
+            m_new[es0 + x] = o0;
+            m_new[es1 + x] = o1;
+        }
+    }
 }
 
 // =====================================================================================
@@ -1169,12 +1527,25 @@ static void var_pass_mode(const DevGraph &G, const Plan &P, const float *ev, con
     }
     for (const VarLaunch &L : P.var) {
         if (L.n == 0) continue;
-        if (L.block_mode) {
-            k_var_block<MODE><<<L.n, kVarBlockThreads, 0, s>>>(G, L.list, ev, m, out, dec);
-        } else if (P.kfix == 2) {
-            k_var_thread<2, MODE><<<L.n_blocks, L.threads, 0, s>>>(G, L.list, L.n, ev, m, out, dec);
-        } else {
-            k_var_thread<0, MODE><<<L.n_blocks, L.threads, 0, s>>>(G, L.list, L.n, ev, m, out, dec);
+        switch (L.kind) {
+            case kVarBlock:
+                k_var_block<MODE><<<L.n, kVarBlockThreads, 0, s>>>(G, L.list, ev, m, out, dec);
+                break;
+            case kVarBinary:
+                k_var_thread<2, MODE><<<L.n_blocks, L.threads, 0, s>>>(G, L.list, L.n, L.dense_binary, ev, m, out, dec);
+                break;
+            case kVarGroup4:
+                k_var_group<4, MODE><<<L.n_blocks, L.threads, 0, s>>>(G, L.list, L.n, ev, m, out, dec);
+                break;
+            case kVarGroup8:
+                k_var_group<8, MODE><<<L.n_blocks, L.threads, 0, s>>>(G, L.list, L.n, ev, m, out, dec);
+                break;
+            case kVarGroup16:
+                k_var_group<16, MODE><<<L.n_blocks, L.threads, 0, s>>>(G, L.list, L.n, ev, m, out, dec);
+                break;
+            default:
+                k_var_thread<0, MODE><<<L.n_blocks, L.threads, 0, s>>>(G, L.list, L.n, 0, ev, m, out, dec);
+                break;
         }
     }
 }
@@ -1202,13 +1573,13 @@ static void factor_pass_t(const DevGraph &G, const Plan &P, const float *pot, co
                 k_pair<2, MAXP><<<L.n_blocks, L.threads, 0, s>>>(G, es, L.n_seg, pot, b, ev, m_old, m_new, T, invT, damping);
                 break;
             case kPair4:
-                k_pair<4, MAXP><<<L.n_blocks, L.threads, 0, s>>>(G, es, L.n_seg, pot, b, ev, m_old, m_new, T, invT, damping);
+                k_pair_group<4, MAXP><<<min(L.n_blocks, L.max_blocks), L.threads, 0, s>>>(G, es, L.n_seg, L.n_blocks, pot, b, ev, m_old, m_new, T, invT, damping);
                 break;
             case kPair8:
-                k_pair<8, MAXP><<<L.n_blocks, L.threads, 0, s>>>(G, es, L.n_seg, pot, b, ev, m_old, m_new, T, invT, damping);
+                k_pair_group<8, MAXP><<<min(L.n_blocks, L.max_blocks), L.threads, 0, s>>>(G, es, L.n_seg, L.n_blocks, pot, b, ev, m_old, m_new, T, invT, damping);
                 break;
             case kPair16:
-                k_pair<16, MAXP><<<L.n_blocks, L.threads, 0, s>>>(G, es, L.n_seg, pot, b, ev, m_old, m_new, T, invT, damping);
+                k_pair_group<16, MAXP><<<min(L.n_blocks, L.max_blocks), L.threads, 0, s>>>(G, es, L.n_seg, L.n_blocks, pot, b, ev, m_old, m_new, T, invT, damping);
                 break;
             case kEnumGeneric:
                 k_enum_generic<MAXP><<<L.n_blocks, L.threads, 0, s>>>(G, es, L.n_seg, pot, b, ev, m_old, m_new, T, invT, damping);

@@ -94,20 +94,33 @@ struct FactorLaunch {
     int32_t threads;
     int32_t smem;      // dynamic shared memory bytes
     int32_t max_fan;   // logical warp launches: largest fan-in
+    int32_t max_blocks;  // K-lane pairwise launches: physical blocks (each walks a range
+                         // of the n_blocks chunks)
+};
+
+// Variable-pass kernel variants (buckets of variables).
+enum VarKind : int32_t {
+    kVarGeneric = 0,  // thread per variable, any K
+    kVarBlock = 1,    // block per variable, degree > kVarBlockDegree
+    kVarBinary = 2,   // thread per binary variable (float2 loads)
+    kVarGroup4 = 3,   // K lanes per variable, K = 4, 8, 16
+    kVarGroup8 = 4,
+    kVarGroup16 = 5,
+    kNumVarKinds = 6
 };
 
 struct VarLaunch {
-    int32_t block_mode;      // 0: thread per variable, 1: block per variable
+    int32_t kind;            // VarKind
     int32_t n;               // variables in the list
     const int32_t *list;     // device list, or nullptr for the identity 0..n-1
     int32_t n_blocks;
     int32_t threads;
+    int32_t dense_binary;    // every variable of the graph is binary (state offset = 2 v)
 };
 
 struct Plan {
     std::vector<FactorLaunch> factor;
     std::vector<VarLaunch> var;
-    int32_t kfix;  // 2 when every variable is binary (vectorised variable pass), else 0
 };
 
 // Host-side result of the graph compiler (compile.cpp).
@@ -135,8 +148,8 @@ struct HostLayout {
     std::vector<int32_t> paroff_pool;
     std::vector<HostEnumGroup> enum_groups;
     std::vector<HostLogicGroup> logic_groups;
-    std::vector<int32_t> var_small, var_large;  // degree buckets
-    bool var_small_identity = false;
+    std::vector<int32_t> var_bucket[kNumVarKinds];  // variables of each VarKind, ascending
+    bool var_bucket_identity[kNumVarKinds] = {};     // bucket is 0..V-1
     bool all_binary = false;
     std::vector<int32_t> vin_tab4;  // [4 * V] (see DevGraph::vin_tab4), empty if unused
     std::vector<HostMember> members;
