@@ -80,6 +80,10 @@ def _load():
                                         ctypes.c_double, ctypes.c_int, ctypes.c_void_p]
         lib.og_sizes.restype = ctypes.c_int
         lib.og_sizes.argtypes = [ctypes.POINTER(_Graph), ctypes.c_void_p]
+        lib.og_grad.restype = ctypes.c_int
+        lib.og_grad.argtypes = [ctypes.POINTER(_Graph), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double,
+                                ctypes.c_double, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                ctypes.c_void_p]
         lib.og_num_threads.restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -195,6 +199,34 @@ def logic_update(kind: int, v2f: np.ndarray, T: float, brute: bool = False) -> n
     out = np.zeros_like(v)
     lib.og_logic_update(int(kind), n, _ptr(v), float(T), int(brute), _ptr(out))
     return out
+
+
+def grad(graph, log_pot, evidence, T: float, damping: float, n_iters: int, g_nb):
+    """Gradient of L = sum(g_nb * normalised log-beliefs) after n_iters iterations from
+    zero messages, w.r.t. (log-potentials, evidence). T > 0, enumeration factors only."""
+    lib = _load()
+    m = _Marshalled(graph)
+    lp = np.ascontiguousarray(log_pot, np.float64)
+    if lp.size == 0:
+        lp = np.zeros(1)
+    ev = np.ascontiguousarray(evidence, np.float64)
+    gn = np.ascontiguousarray(g_nb, np.float64)
+    dlp = np.zeros(max(graph.n_potentials, 1), np.float64)
+    dev = np.zeros(graph.n_var_states, np.float64)
+    rc = lib.og_grad(ctypes.byref(m.g), _ptr(lp), _ptr(ev), float(T), float(damping), int(n_iters),
+                     _ptr(gn), _ptr(dlp), _ptr(dev))
+    if rc == -2:
+        raise ValueError("oracle grad: logical factors are not supported")
+    if rc != 0:
+        raise ValueError("oracle grad: invalid T, damping or n_iters")
+    return dlp[:graph.n_potentials], dev
+
+
+def loss(graph, log_pot, evidence, T, damping, n_iters, g_nb) -> float:
+    """L = sum(g_nb * normalised log-beliefs) after n_iters iterations from zero messages."""
+    msgs, _ = run_bp(graph, log_pot, evidence, T, damping, n_iters)
+    _, nb, _, _ = beliefs(graph, evidence, msgs)
+    return float(np.dot(np.asarray(g_nb, np.float64), nb))
 
 
 def num_threads() -> int:

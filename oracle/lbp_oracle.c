@@ -50,6 +50,7 @@
 #define OG_AND 1
 #define OG_FLAG_CONTRADICTION 1u
 #define OG_FLAG_NAN 2u
+#define PGM_ORACLE_KMAX 256
 
 typedef struct {
     int32_t n_vars;
@@ -552,4 +553,163 @@ int og_num_threads(void) {
 #else
     return 1;
 #endif
+}
+
+/* ---- adjoint (gradient) -------------------------------------------------------------- */
+
+/* argmax over K values, lowest index on ties */
+static int argmax_k(const double *m, int K) {
+    int a = 0;
+    for (int x = 1; x < K; ++x)
+        if (m[x] > m[a]) a = x;
+    return a;
+}
+
+/*
+ * Gradient of L = sum_v sum_x g[v,x] * nb[v,x], nb = b - LSE_1(b), the normalised
+ * log-beliefs after n_iters flooding iterations from zero messages, with respect to the
+ * log-potentials and the evidence (the "grad" of Sec. 4.3: LBP inside a differentiable
+ * system). T > 0 and enumeration factors only (returns -2 for logical factors).
+ * Reverse-mode chain rule through each forward step, in reverse order:
+ *   beliefs   nb = b - LSE(b):         db = g - softmax(b) * sum(g)
+ *   b = e + sum m:                     de += db, dm_{g->v} += db
+ *   normalise m_t = d - d[argmax]:     dd = dm - (sum dm) * onehot(argmax)
+ *   damping d = delta m_{t-1} + (1 - delta) n:   dm_{t-1} += delta dd, dn = (1 - delta) dd
+ *   normalise n = mt - mt[argmax]:     dmt = dn - (sum dn) * onehot(argmax)
+ *   factor mt_i(x) = T log sum_{c: c_i = x} exp(s_{-i}(c) / T), s_{-i}(c) = phi(c) + sum_{j != i} v_j(c_j):
+ *       with p = exp((s_{-i}(c) - mt_i(c_i)) / T):  dphi(c) += dmt_i(c_i) p,  dv_j(c_j) += dmt_i(c_i) p (j != i)
+ *   leave-one-out v_{f->v} = e_v + sum_{g != f} m_{g->v}:  de += dv,  dm_{g->v} += dv (g != f)
+ * All intermediate message states are kept (small graphs).
+ */
+int og_grad(const og_graph *g, const double *log_pot, const double *evidence, double T, double damping,
+            int n_iters, const double *g_nb, double *d_log_pot, double *d_evidence) {
+    if (!(T > 0.0) || damping < 0.0 || damping >= 1.0 || n_iters < 0) return -1;
+    if (g->n_logic > 0) return -2;
+    og_layout L;
+    layout_build(g, &L);
+    const int64_t ES = L.ES, VS = L.VS;
+    int64_t P = 0;
+    for (int k = 0; k < g->n_enum; ++k) P += g->e_shared[k] ? g->e_ncfg[k] : (int64_t)g->e_ncfg[k] * g->e_nfac[k];
+    double *hist = (double *)calloc((size_t)(n_iters + 1) * (size_t)(ES > 0 ? ES : 1), sizeof(double));
+    double *v2f = (double *)malloc(sizeof(double) * (size_t)(ES > 0 ? ES : 1));
+    double *mt = (double *)malloc(sizeof(double) * (size_t)(ES > 0 ? ES : 1));
+    double *dm = (double *)calloc((size_t)(ES > 0 ? ES : 1), sizeof(double));
+    double *dm_prev = (double *)calloc((size_t)(ES > 0 ? ES : 1), sizeof(double));
+    double *dv = (double *)calloc((size_t)(ES > 0 ? ES : 1), sizeof(double));
+    double *vals = (double *)malloc(sizeof(double) * (size_t)max_ncfg(g));
+    uint32_t fl = 0;
+    /* forward, keeping every message state */
+    for (int t = 1; t <= n_iters; ++t) {
+        const double *mo = hist + (size_t)(t - 1) * ES;
+        double *mn = hist + (size_t)t * ES;
+        var_to_factor(g, &L, evidence, mo, v2f);
+        for (int k = 0; k < g->n_enum; ++k)
+            for (int64_t f = 0; f < g->e_nfac[k]; ++f) enum_factor(g, &L, k, f, log_pot, T, v2f, mt, vals);
+        for (int64_t e = 0; e < L.E; ++e) {
+            int K = (int)(L.es_off[e + 1] - L.es_off[e]);
+            damp_normalise(mt + L.es_off[e], mo + L.es_off[e], K, damping, &fl);
+        }
+        memcpy(mn, mt, sizeof(double) * (size_t)ES);
+    }
+    for (int64_t i = 0; i < P; ++i) d_log_pot[i] = 0.0;
+    for (int64_t i = 0; i < VS; ++i) d_evidence[i] = 0.0;
+    /* beliefs: db = g - softmax(b) sum(g); de += db; dm_e = db_{v(e)} */
+    {
+        const double *mfin = hist + (size_t)n_iters * ES;
+        for (int64_t v = 0; v < L.V; ++v) {
+            int K = g->num_states[v];
+            double b[PGM_ORACLE_KMAX], sg = 0.0;
+            for (int x = 0; x < K; ++x) {
+                double s = evidence[L.vs_off[v] + x];
+                for (int64_t q = L.vin_off[v]; q < L.vin_off[v + 1]; ++q) s += mfin[L.es_off[L.vin_edge[q]] + x];
+                b[x] = s;
+                sg += g_nb[L.vs_off[v] + x];
+            }
+            double z = lse_T(b, K, 1.0);
+            for (int x = 0; x < K; ++x) {
+                double db = g_nb[L.vs_off[v] + x] - exp(b[x] - z) * sg;
+                d_evidence[L.vs_off[v] + x] += db;
+                for (int64_t q = L.vin_off[v]; q < L.vin_off[v + 1]; ++q) dm[L.es_off[L.vin_edge[q]] + x] = db;
+            }
+        }
+    }
+    /* iterations, last to first */
+    for (int t = n_iters; t >= 1; --t) {
+        const double *mo = hist + (size_t)(t - 1) * ES;
+        var_to_factor(g, &L, evidence, mo, v2f);
+        for (int k = 0; k < g->n_enum; ++k)
+            for (int64_t f = 0; f < g->e_nfac[k]; ++f) enum_factor(g, &L, k, f, log_pot, T, v2f, mt, vals);
+        for (int64_t i = 0; i < ES; ++i) {
+            dm_prev[i] = 0.0;
+            dv[i] = 0.0;
+        }
+        /* normalise, damp, normalise: backward per edge; dm becomes d(mt) */
+        for (int64_t e = 0; e < L.E; ++e) {
+            int K = (int)(L.es_off[e + 1] - L.es_off[e]);
+            double *me = mt + L.es_off[e];
+            const double *mold = mo + L.es_off[e];
+            double n[PGM_ORACLE_KMAX], d[PGM_ORACLE_KMAX];
+            int a1 = argmax_k(me, K);
+            for (int x = 0; x < K; ++x) n[x] = me[x] - me[a1];
+            for (int x = 0; x < K; ++x) d[x] = (damping != 0.0) ? damping * mold[x] + (1.0 - damping) * n[x] : n[x];
+            int a2 = argmax_k(d, K);
+            double *gm = dm + L.es_off[e];
+            double sd = 0.0, dd[PGM_ORACLE_KMAX];
+            for (int x = 0; x < K; ++x) sd += gm[x];
+            for (int x = 0; x < K; ++x) dd[x] = gm[x] - (x == a2 ? sd : 0.0);
+            double dn[PGM_ORACLE_KMAX], sn = 0.0;
+            for (int x = 0; x < K; ++x) {
+                dm_prev[L.es_off[e] + x] += damping * dd[x];
+                dn[x] = (damping != 0.0 ? (1.0 - damping) : 1.0) * dd[x];
+                sn += dn[x];
+            }
+            for (int x = 0; x < K; ++x) gm[x] = dn[x] - (x == a1 ? sn : 0.0);
+        }
+        /* factor backward */
+        for (int k = 0; k < g->n_enum; ++k) {
+            int a = g->e_arity[k], nc = g->e_ncfg[k];
+            const int32_t *cfg = g->e_cfg[k];
+            for (int64_t f = 0; f < g->e_nfac[k]; ++f) {
+                int64_t e0 = L.enum_edge0[k] + f * a;
+                int64_t poff = L.enum_pot0[k] + (g->e_shared[k] ? 0 : f * nc);
+                for (int c = 0; c < nc; ++c) {
+                    for (int i = 0; i < a; ++i) {
+                        double s = log_pot[poff + c];
+                        for (int j = 0; j < a; ++j)
+                            if (j != i) s += v2f[L.es_off[e0 + j] + cfg[c * a + j]];
+                        int64_t ii = L.es_off[e0 + i] + cfg[c * a + i];
+                        if (s == -INFINITY) continue;
+                        double p = exp((s - mt[ii]) / T);
+                        double w = dm[ii] * p;
+                        d_log_pot[poff + c] += w;
+                        for (int j = 0; j < a; ++j)
+                            if (j != i) dv[L.es_off[e0 + j] + cfg[c * a + j]] += w;
+                    }
+                }
+            }
+        }
+        /* leave-one-out backward: v_{f->v} = e_v + sum_{g != f} m_{g->v} */
+        for (int64_t v = 0; v < L.V; ++v) {
+            int K = g->num_states[v];
+            for (int x = 0; x < K; ++x) {
+                double tot = 0.0;
+                for (int64_t q = L.vin_off[v]; q < L.vin_off[v + 1]; ++q) tot += dv[L.es_off[L.vin_edge[q]] + x];
+                d_evidence[L.vs_off[v] + x] += tot;
+                for (int64_t q = L.vin_off[v]; q < L.vin_off[v + 1]; ++q) {
+                    int64_t i = L.es_off[L.vin_edge[q]] + x;
+                    dm_prev[i] += tot - dv[i];
+                }
+            }
+        }
+        memcpy(dm, dm_prev, sizeof(double) * (size_t)ES);
+    }
+    free(hist);
+    free(v2f);
+    free(mt);
+    free(dm);
+    free(dm_prev);
+    free(dv);
+    free(vals);
+    layout_free(&L);
+    return 0;
 }
