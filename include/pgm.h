@@ -230,6 +230,27 @@ pgm_status pgm_pass_times(pgm_graph *g, double *var_ms, double *factor_ms, int64
                           int64_t *n_factor);
 
 /*
+ * Gradient (Sec. 4.3: LBP as part of an end-to-end differentiable system): the
+ * vector-Jacobian product of the normalised log-beliefs after n_iters iterations from
+ * zero messages (pgm_run_bp then pgm_beliefs(normalise = 1)) with the cotangent
+ * d_beliefs [n_var_states], i.e. the gradient of L = sum(d_beliefs * (b - LSE_1(b)))
+ * with respect to the log-potentials (d_log_pot [n_potentials]) and the evidence
+ * (d_evidence [n_var_states]); both outputs are overwritten. Reverse mode through the
+ * unrolled iterations: the forward keeps a checkpoint of the messages every ckpt_every
+ * iterations and the reverse pass recomputes each segment from its checkpoint
+ * (device scratch of (ceil(n_iters / ckpt_every) + min(ckpt_every, n_iters) + 5) x
+ * n_edge_states floats, stream-ordered allocation freed before the call's work ends).
+ * Gradients of log-potentials shared by a group are summed over its factors in
+ * arbitrary order (atomic adds); everything else is deterministic.
+ * Errors: PGM_ENOTSUP for T = 0 (max-product is not differentiable) or graphs with
+ * logical factors; PGM_EINVAL for a non-finite or negative T, damping outside [0, 1),
+ * n_iters < 0, ckpt_every < 1, NULL pointers.
+ */
+pgm_status pgm_grad(pgm_graph *g, const float *log_pot, const float *evidence, float T, float damping,
+                    int32_t n_iters, int32_t ckpt_every, const float *d_beliefs, float *d_log_pot,
+                    float *d_evidence, void *stream);
+
+/*
  * Read (and, with clear = 1, reset) the graph's device status word, a set of
  * PGM_FLAG_* bits raised by kernels. Synchronises `stream` first.
  */

@@ -24,7 +24,7 @@ FLAG_NAN = 2
 EXPORTED = ["pgm_build", "pgm_build_batch", "pgm_batch_member", "pgm_check_desc", "pgm_free", "pgm_graph_info", "pgm_run_bp", "pgm_beliefs",
             "pgm_decode", "pgm_infer_host", "pgm_set_profiling", "pgm_pass_times",
             "pgm_device_flags", "pgm_grid2_run_bp_noalloc", "pgm_set_option", "pgm_autotune",
-            "pgm_launch_info", "pgm_last_error"]
+            "pgm_launch_info", "pgm_grad", "pgm_last_error"]
 OPT_CUDA_GRAPH = 1
 
 
@@ -112,6 +112,8 @@ def load_library(path: str | None = None):
     lib.pgm_autotune.argtypes = [vp, vp, vp, f32, f32, vp]
     lib.pgm_launch_info.restype = i32
     lib.pgm_launch_info.argtypes = [vp, i32] + [ctypes.POINTER(i32)] * 4
+    lib.pgm_grad.restype = i32
+    lib.pgm_grad.argtypes = [vp, vp, vp, f32, f32, i32, i32, vp, vp, vp, vp]
     lib.pgm_set_option.restype = i32
     lib.pgm_set_option.argtypes = [vp, i32, ctypes.c_int64]
     lib.pgm_last_error.restype = ctypes.c_char_p
@@ -295,6 +297,21 @@ class Graph:
             out.append(tuple(x.value for x in v))
         return out
 
+    def grad(self, log_pot, evidence, T: float, damping: float, n_iters: int, ckpt_every: int, d_beliefs,
+             stream=None):
+        """pgm_grad: (d_log_pot, d_evidence) of sum(d_beliefs * normalised log-beliefs)."""
+        import torch
+        I = self.info
+        d_lp = torch.empty(max(I["n_potentials"], 1), dtype=torch.float32, device="cuda")[: I["n_potentials"]]
+        d_ev = torch.empty(I["n_var_states"], dtype=torch.float32, device="cuda")
+        lp = _dptr(log_pot, torch.float32, I["n_potentials"], "log_pot") if I["n_potentials"] else 0
+        check(load_library().pgm_grad(self._h, lp, _dptr(evidence, torch.float32, I["n_var_states"], "evidence"),
+                                      float(T), float(damping), int(n_iters), int(ckpt_every),
+                                      _dptr(d_beliefs, torch.float32, I["n_var_states"], "d_beliefs"),
+                                      _dptr(d_lp, torch.float32, I["n_potentials"], "d_log_pot") if I["n_potentials"] else 0,
+                                      _dptr(d_ev, torch.float32, I["n_var_states"], "d_evidence"), _stream_ptr(stream)))
+        return d_lp, d_ev
+
     def set_option(self, option: int, value: int):
         check(load_library().pgm_set_option(self._h, int(option), int(value)))
 
@@ -343,3 +360,43 @@ def infer(problem, n_iters: int | None = None, T: float | None = None, graph: Gr
     g.run_bp(lp, ev, problem.T if T is None else T, problem.damping,
              problem.n_iters if n_iters is None else n_iters, msgs)
     return g, msgs, g.beliefs(ev, msgs, True), g.decode(ev, msgs)
+
+
+def _lbp_function():
+    import torch
+
+    class LBPFunction(torch.autograd.Function):
+        """Normalised log-beliefs after n_iters LBP iterations from zero messages, as a
+        differentiable function of (log_pot, evidence): forward through pgm_run_bp and
+        pgm_beliefs, backward through pgm_grad (checkpoint every ckpt_every iterations)."""
+
+        @staticmethod
+        def forward(ctx, log_pot, evidence, graph, T, damping, n_iters, ckpt_every):
+            lp = log_pot.detach().contiguous()
+            ev = evidence.detach().contiguous()
+            msgs = graph.new_msgs()
+            graph.run_bp(lp, ev, T, damping, n_iters, msgs)
+            nb = graph.beliefs(ev, msgs, True)
+            ctx.save_for_backward(lp, ev)
+            ctx.cfg = (graph, T, damping, n_iters, ckpt_every)
+            return nb
+
+        @staticmethod
+        def backward(ctx, g):
+            lp, ev = ctx.saved_tensors
+            graph, T, damping, n_iters, ckpt_every = ctx.cfg
+            d_lp, d_ev = graph.grad(lp, ev, T, damping, n_iters, ckpt_every, g.contiguous())
+            return d_lp, d_ev, None, None, None, None, None
+
+    return LBPFunction
+
+
+_LBP = None
+
+
+def lbp_beliefs(log_pot, evidence, graph: Graph, T: float, damping: float, n_iters: int, ckpt_every: int = 10):
+    """Differentiable normalised log-beliefs (torch.autograd.Function over the C ABI)."""
+    global _LBP
+    if _LBP is None:
+        _LBP = _lbp_function()
+    return _LBP.apply(log_pot, evidence, graph, T, damping, n_iters, ckpt_every)

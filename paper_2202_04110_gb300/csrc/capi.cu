@@ -1,6 +1,7 @@
 // C-ABI entry points (include/pgm.h): graph build and upload, launch planning, the
 // flooding LBP run loop, belief read-out and decode.
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -68,6 +69,9 @@ struct pgm_graph {
     int64_t prof_var_launches = 0, prof_factor_launches = 0;
     int32_t var_launches = 0, factor_launches = 0;
     std::vector<HostMember> members;
+    FactorLaunch adj_launch{};      // pgm_grad: every enumeration group, thread per factor
+    size_t adj_seg_off = (size_t)-1;
+    bool has_logic = false;
     std::vector<std::vector<char>> factor_segs_host;  // host copy of each factor launch's segments
     // CUDA graphs of whole pgm_run_bp calls, keyed by their arguments (LRU)
     struct CachedRun {
@@ -138,6 +142,24 @@ pgm_status build_plan(const HostLayout &H, pgm_graph *g, Packer &pk, std::vector
         P.var.push_back(L);
         seg_off.push_back(H.var_bucket_identity[kind] ? (size_t)-1 : pk.add(bucket.data(), bucket.size()));
         seg_kind.push_back(-1);
+    }
+    // adjoint factor launch: every enumeration group, thread per factor
+    {
+        std::vector<EnumSeg> segs;
+        int32_t blk = 0;
+        for (const HostEnumGroup &hg : H.enum_groups) {
+            EnumSeg s = hg.seg;
+            s.block_begin = blk;
+            blk += (s.n_fac + 127) / 128;
+            segs.push_back(s);
+        }
+        g->adj_launch = FactorLaunch{};
+        g->adj_launch.variant = kEnumGeneric;
+        g->adj_launch.n_seg = (int32_t)segs.size();
+        g->adj_launch.n_blocks = blk;
+        g->adj_launch.threads = 128;
+        g->adj_seg_off = segs.empty() ? (size_t)-1 : pk.add(segs.data(), segs.size());
+        g->has_logic = !H.logic_groups.empty();
     }
     // factor pass: one launch per variant, all groups of that variant as segments
     for (int variant = 0; variant < kNumFactorVariants; ++variant) {
@@ -330,6 +352,7 @@ static pgm_status build_from_descs(const void *const *descs, int n, pgm_graph **
             max_smem = std::max(max_smem, L.smem);
         }
     }
+    if (g->adj_seg_off != (size_t)-1) g->adj_launch.segs = dmem + g->adj_seg_off;
     ce = prepare_kernels(max_smem);
     if (ce != cudaSuccess) {
         pgm_free(g);
@@ -673,6 +696,83 @@ pgm_status pgm_launch_info(const pgm_graph *g, int32_t i, int32_t *kind, int32_t
         if (n_blocks) *n_blocks = L.n_blocks;
     }
     return PGM_OK;
+}
+
+// One iteration from `in` into `out` (out != in).
+static pgm_status one_iteration(pgm_graph *g, const float *log_pot, const float *evidence, float T, float damping,
+                                const float *in, float *out, cudaStream_t s) {
+    cudaError_t e = launch_var_pass(g->G, g->P, evidence, in, g->b, kVarIter, nullptr, s);
+    if (e == cudaSuccess) e = launch_factor_pass(g->G, g->P, log_pot, g->b, evidence, in, out, T, damping, s);
+    if (e != cudaSuccess) return cuda_fail(e, "iteration launch");
+    return PGM_OK;
+}
+
+pgm_status pgm_grad(pgm_graph *g, const float *log_pot, const float *evidence, float T, float damping,
+                    int32_t n_iters, int32_t ckpt_every, const float *d_beliefs, float *d_log_pot,
+                    float *d_evidence, void *stream) {
+    if (!g) return fail(PGM_EINVAL, "graph is NULL");
+    if (!(T > 0.f) || !std::isfinite(T))
+        return fail(T == 0.f ? PGM_ENOTSUP : PGM_EINVAL, "pgm_grad needs a finite T > 0 (max-product has no gradient)");
+    if (g->has_logic) return fail(PGM_ENOTSUP, "pgm_grad supports enumeration factors only");
+    if (!(damping >= 0.f && damping < 1.f)) return fail(PGM_EINVAL, "damping must be in [0, 1)");
+    if (n_iters < 0 || ckpt_every < 1) return fail(PGM_EINVAL, "n_iters >= 0 and ckpt_every >= 1 required");
+    if (!evidence || !d_beliefs || !d_evidence || (g->info.n_potentials > 0 && (!log_pot || !d_log_pot)))
+        return fail(PGM_EINVAL, "NULL argument");
+    DeviceGuard dg(g->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int64_t ES = std::max<int64_t>(g->info.n_edge_states, 1);
+    const size_t esb = align_up((size_t)ES * sizeof(float), 256);
+    const int n_ck = n_iters > 0 ? (n_iters + ckpt_every - 1) / ckpt_every : 0;
+    const int seg_len = std::min(ckpt_every, std::max(n_iters, 1));
+    // checkpoints, one segment of recomputed states, two message buffers, two adjoint
+    // buffers, the variable-to-factor adjoint
+    const size_t total = esb * ((size_t)n_ck + (size_t)seg_len + 5);
+    char *mem = nullptr;
+    cudaError_t e = cudaMallocAsync(&mem, total, s);
+    if (e != cudaSuccess) return fail(PGM_ENOMEM, std::string("cudaMallocAsync(grad): ") + cudaGetErrorString(e));
+    auto buf = [&](size_t i) { return reinterpret_cast<float *>(mem + i * esb); };
+    float *ck = buf(0), *rec = buf(n_ck), *mA = buf(n_ck + seg_len), *mB = buf(n_ck + seg_len + 1);
+    float *adjA = buf(n_ck + seg_len + 2), *adjB = buf(n_ck + seg_len + 3), *dv = buf(n_ck + seg_len + 4);
+    auto ckp = [&](int i) { return ck + (size_t)i * (esb / sizeof(float)); };
+    auto recp = [&](int i) { return rec + (size_t)i * (esb / sizeof(float)); };
+    pgm_status st = PGM_OK;
+    if (g->info.n_potentials > 0) e = cudaMemsetAsync(d_log_pot, 0, (size_t)g->info.n_potentials * sizeof(float), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(mA, 0, esb, s);
+    if (e != cudaSuccess) st = cuda_fail(e, "cudaMemsetAsync(grad)");
+    // forward with a checkpoint every ckpt_every iterations
+    for (int t = 0; t < n_iters && st == PGM_OK; ++t) {
+        if (t % ckpt_every == 0) {
+            e = cudaMemcpyAsync(ckp(t / ckpt_every), mA, esb, cudaMemcpyDeviceToDevice, s);
+            if (e != cudaSuccess) st = cuda_fail(e, "checkpoint copy");
+        }
+        if (st == PGM_OK) st = one_iteration(g, log_pot, evidence, T, damping, mA, mB, s);
+        std::swap(mA, mB);
+    }
+    // the belief read-out in reverse
+    if (st == PGM_OK) {
+        e = launch_adj_beliefs(g->G, evidence, mA, d_beliefs, d_evidence, adjA, s);
+        if (e != cudaSuccess) st = cuda_fail(e, "adjoint beliefs launch");
+    }
+    // segments in reverse: recompute the states from the checkpoint, then step back
+    for (int sgi = n_ck - 1; sgi >= 0 && st == PGM_OK; --sgi) {
+        const int t0 = sgi * ckpt_every, t1 = std::min(t0 + ckpt_every, (int)n_iters);
+        e = cudaMemcpyAsync(recp(0), ckp(sgi), esb, cudaMemcpyDeviceToDevice, s);
+        if (e != cudaSuccess) st = cuda_fail(e, "recompute copy");
+        for (int i = 1; i < t1 - t0 && st == PGM_OK; ++i)
+            st = one_iteration(g, log_pot, evidence, T, damping, recp(i - 1), recp(i), s);
+        for (int t = t1; t > t0 && st == PGM_OK; --t) {
+            const float *m_prev = recp(t - 1 - t0);
+            e = launch_var_pass(g->G, g->P, evidence, m_prev, g->b, kVarIter, nullptr, s);
+            if (e == cudaSuccess)
+                e = launch_adj_factor(g->G, g->adj_launch, log_pot, g->b, evidence, m_prev, adjA, dv, d_log_pot, T,
+                                      damping, s);
+            if (e == cudaSuccess) e = launch_adj_var(g->G, adjA, dv, adjB, d_evidence, damping, s);
+            if (e != cudaSuccess) st = cuda_fail(e, "adjoint step launch");
+            std::swap(adjA, adjB);
+        }
+    }
+    cudaFreeAsync(mem, s);
+    return st;
 }
 
 pgm_status pgm_set_option(pgm_graph *g, int32_t option, int64_t value) {

@@ -1501,6 +1501,163 @@ k_logic_warp(DevGraph G, const LogicSeg *__restrict__ segs, int n_seg, const flo
     }
 }
 
+// =====================================================================================
+// Adjoint (gradient of L = sum g * normalised log-beliefs w.r.t. log-potentials and
+// evidence, T > 0, enumeration factors). Message adjoints sum to zero over each edge's
+// states (normalised beliefs are invariant to per-edge constants), so both
+// normalisations of an iteration are transparent in reverse; damping scales by delta
+// and 1 - delta.
+// =====================================================================================
+
+// Belief read-out: db = g - softmax(b) * sum(g); d_evidence = db; adjoint of every
+// incoming message = db of its variable. Thread per variable.
+__global__ void __launch_bounds__(128) k_adj_beliefs(DevGraph G, const float *__restrict__ ev,
+                                                     const float *__restrict__ m, const float *__restrict__ gnb,
+                                                     float *__restrict__ d_ev, float *__restrict__ adj) {
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= G.V) return;
+    const int vs = G.vs_off[v], K = G.vs_off[v + 1] - vs, k0 = G.vin_off[v], k1 = G.vin_off[v + 1];
+    FF best = ff_make(kNegInf);
+    int arg = 0;
+    float sg = 0.f;
+    for (int x = 0; x < K; ++x) {
+        FF s = ff_make(ev[vs + x]);
+        for (int k = k0; k < k1; ++k) s = ff_add(s, m[G.vin_es[k] + x]);
+        if (x == 0 || ff_gt(s, best)) {
+            best = s;
+            arg = x;
+        }
+        sg += gnb[vs + x];
+    }
+    float z = 0.f;
+    for (int x = 0; x < K; ++x) {
+        FF s = ff_make(ev[vs + x]);
+        for (int k = k0; k < k1; ++k) s = ff_add(s, m[G.vin_es[k] + x]);
+        if (x != arg) z += expf(ff_diff(s, best));
+    }
+    const float lz = log1pf(z);
+    for (int x = 0; x < K; ++x) {
+        FF s = ff_make(ev[vs + x]);
+        for (int k = k0; k < k1; ++k) s = ff_add(s, m[G.vin_es[k] + x]);
+        const float r = (x == arg) ? 0.f : ff_diff(s, best);
+        const float db = gnb[vs + x] - expf(r - lz) * sg;
+        d_ev[vs + x] = db;
+        for (int k = k0; k < k1; ++k) adj[G.vin_es[k] + x] = db;
+    }
+}
+
+// Factor step in reverse, thread per enumeration factor: with gamma_i = (1 - delta) *
+// adjoint of edge i and p_i(c) = exp((s_{-i}(c) - LSE_T{s_{-i}(c') : c'_i = c_i}) / T),
+//   d log_pot(c) += sum_i gamma_i(c_i) p_i(c)
+//   dv2f_j(y)     = sum_{i != j} sum_{c: c_j = y} gamma_i(c_i) p_i(c)
+// The variable-to-factor values are recomputed exactly as the forward factor pass does.
+__global__ void __launch_bounds__(128)
+k_adj_factor(DevGraph G, const EnumSeg *__restrict__ segs, int n_seg, const float *__restrict__ pot,
+             const float *__restrict__ b, const float *__restrict__ ev, const float *__restrict__ m_old,
+             const float *__restrict__ adj, float *__restrict__ dv2f, float *__restrict__ d_pot, float T,
+             float invT, float damping) {
+    const EnumSeg *S = segs + find_seg(segs, n_seg, blockIdx.x);
+    const int f = (blockIdx.x - S->block_begin) * blockDim.x + threadIdx.x;
+    if (f >= S->n_fac) return;
+    const int a = S->arity, nc = S->n_cfg, ksum = S->es_per_fac;
+    int Kj[kMaxArity], Ko[kMaxArity];
+    for (int j = 0; j < a; ++j) {
+        Kj[j] = S->K[j];
+        Ko[j] = S->Koff[j];
+    }
+    const int es_f = S->es_base + f * ksum;
+    const int e_f = S->edge_base + f * a;
+    float v2f[kMaxStateSum], gam[kMaxStateSum], lm[kMaxStateSum], ls[kMaxStateSum], dv[kMaxStateSum];
+    const float w1 = (damping != 0.f) ? 1.f - damping : 1.f;
+    for (int j = 0; j < a; ++j) {
+        const int vs = G.edge_vs[e_f + j];
+        const int es = es_f + Ko[j];
+        bool exact = false;
+        for (int x = 0; x < Kj[j]; ++x) exact |= needs_exact(m_old[es + x]);
+        if (vs < 0) {
+            float2 hmx = make_float2(-CUDART_INF_F, 0.f);
+            for (int x = 0; x < Kj[j]; ++x) {
+                const float2 q = hd_pair(G, es, x);
+                if (x == 0 || hd_gt(q, hmx)) hmx = q;
+            }
+            for (int x = 0; x < Kj[j]; ++x)
+                v2f[Ko[j] + x] = hmx.x == -CUDART_INF_F ? -CUDART_INF_F : hd_rel(hd_pair(G, es, x), hmx);
+        } else if (exact) {
+            v2f_slow_edge(G, ev, m_old, vs, es, Kj[j], v2f + Ko[j]);
+        } else {
+            for (int x = 0; x < Kj[j]; ++x) v2f[Ko[j] + x] = b[vs + x] - m_old[es + x];
+        }
+        for (int x = 0; x < Kj[j]; ++x) {
+            gam[Ko[j] + x] = w1 * adj[es + x];
+            dv[Ko[j] + x] = 0.f;
+        }
+    }
+    for (int i = 0; i < ksum; ++i) {
+        lm[i] = kNegInf;
+        ls[i] = 0.f;
+    }
+    const uint8_t *cfg = G.cfg_pool + S->cfg_base;
+    const float *phi = pot + S->pot_base + (S->shared ? 0 : (size_t)f * nc);
+    // LSE_T over the configurations consistent with each (edge, state)
+    for (int c = 0; c < nc; ++c) {
+        const uint8_t *cc = cfg + c * a;
+        for (int i = 0; i < a; ++i) {
+            float s = phi[c];
+            for (int j = 0; j < a; ++j)
+                if (j != i) s += v2f[Ko[j] + cc[j]];
+            const int idx = Ko[i] + cc[i];
+            if (s > lm[idx]) {
+                ls[idx] = ls[idx] * expf((lm[idx] - s) * invT) + 1.f;
+                lm[idx] = s;
+            } else if (s > kNegInf) {
+                ls[idx] += expf((s - lm[idx]) * invT);
+            }
+        }
+    }
+    for (int i = 0; i < ksum; ++i)
+        if (lm[i] != kNegInf) lm[i] += T * logf(ls[i]);
+    float *dphi = d_pot + S->pot_base + (S->shared ? 0 : (size_t)f * nc);
+    for (int c = 0; c < nc; ++c) {
+        const uint8_t *cc = cfg + c * a;
+        float dc = 0.f;
+        for (int i = 0; i < a; ++i) {
+            float s = phi[c];
+            for (int j = 0; j < a; ++j)
+                if (j != i) s += v2f[Ko[j] + cc[j]];
+            const int idx = Ko[i] + cc[i];
+            if (s == kNegInf || lm[idx] == kNegInf) continue;
+            const float w = gam[idx] * expf((s - lm[idx]) * invT);
+            dc += w;
+            for (int j = 0; j < a; ++j)
+                if (j != i) dv[Ko[j] + cc[j]] += w;
+        }
+        if (S->shared) atomicAdd(dphi + c, dc);
+        else dphi[c] += dc;
+    }
+    for (int i = 0; i < ksum; ++i) dv2f[es_f + i] = dv[i];
+}
+
+// Variable step in reverse, thread per variable: db(x) = sum over incoming edges of
+// dv2f(x); d_evidence += db; adjoint of message m_{t-1} on each incoming edge =
+// delta * adjoint_t - dv2f + db.
+__global__ void __launch_bounds__(128) k_adj_var(DevGraph G, const float *__restrict__ adj,
+                                                 const float *__restrict__ dv2f, float *__restrict__ adj_prev,
+                                                 float *__restrict__ d_ev, float damping) {
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= G.V) return;
+    const int vs = G.vs_off[v], K = G.vs_off[v + 1] - vs, k0 = G.vin_off[v], k1 = G.vin_off[v + 1];
+    for (int x = 0; x < K; ++x) {
+        FF db = ff_make(0.f);
+        for (int k = k0; k < k1; ++k) db = ff_add(db, dv2f[G.vin_es[k] + x]);
+        const float d = db.hi + db.lo;
+        d_ev[vs + x] += d;
+        for (int k = k0; k < k1; ++k) {
+            const int i = G.vin_es[k] + x;
+            adj_prev[i] = damping * adj[i] - dv2f[i] + d;
+        }
+    }
+}
+
 }  // namespace
 
 // =====================================================================================
@@ -1601,6 +1758,31 @@ cudaError_t launch_factor_pass(const DevGraph &G, const Plan &P, const float *lo
                                float *m_new, float T, float damping, cudaStream_t s) {
     if (T == 0.f) factor_pass_t<true>(G, P, log_pot, b, ev, m_old, m_new, T, damping, s);
     else factor_pass_t<false>(G, P, log_pot, b, ev, m_old, m_new, T, damping, s);
+    return cudaGetLastError();
+}
+
+}  // namespace pgm
+
+namespace pgm {
+
+cudaError_t launch_adj_beliefs(const DevGraph &G, const float *ev, const float *m, const float *gnb, float *d_ev,
+                               float *adj, cudaStream_t s) {
+    k_adj_beliefs<<<(G.V + 127) / 128, 128, 0, s>>>(G, ev, m, gnb, d_ev, adj);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adj_factor(const DevGraph &G, const FactorLaunch &L, const float *pot, const float *b,
+                              const float *ev, const float *m_old, const float *adj, float *dv2f, float *d_pot,
+                              float T, float damping, cudaStream_t s) {
+    if (L.n_blocks == 0) return cudaSuccess;
+    k_adj_factor<<<L.n_blocks, L.threads, 0, s>>>(G, static_cast<const EnumSeg *>(L.segs), L.n_seg, pot, b, ev,
+                                                  m_old, adj, dv2f, d_pot, T, 1.f / T, damping);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adj_var(const DevGraph &G, const float *adj, const float *dv2f, float *adj_prev, float *d_ev,
+                           float damping, cudaStream_t s) {
+    k_adj_var<<<(G.V + 127) / 128, 128, 0, s>>>(G, adj, dv2f, adj_prev, d_ev, damping);
     return cudaGetLastError();
 }
 
