@@ -238,7 +238,7 @@ pgm_status pgm_pass_times(pgm_graph *g, double *var_ms, double *factor_ms, int64
  * (d_evidence [n_var_states]); both outputs are overwritten. Reverse mode through the
  * unrolled iterations: the forward keeps a checkpoint of the messages every ckpt_every
  * iterations and the reverse pass recomputes each segment from its checkpoint
- * (device scratch of (ceil(n_iters / ckpt_every) + min(ckpt_every, n_iters) + 5) x
+ * (device scratch of (ceil(n_iters / ckpt_every) + min(ckpt_every, n_iters) + 6) x
  * n_edge_states floats, stream-ordered allocation freed before the call's work ends).
  * Gradients of log-potentials shared by a group are summed over its factors in
  * arbitrary order (atomic adds); everything else is deterministic.

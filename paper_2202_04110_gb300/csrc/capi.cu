@@ -726,13 +726,14 @@ pgm_status pgm_grad(pgm_graph *g, const float *log_pot, const float *evidence, f
     const int seg_len = std::min(ckpt_every, std::max(n_iters, 1));
     // checkpoints, one segment of recomputed states, two message buffers, two adjoint
     // buffers, the variable-to-factor adjoint
-    const size_t total = esb * ((size_t)n_ck + (size_t)seg_len + 5);
+    const size_t total = esb * ((size_t)n_ck + (size_t)seg_len + 6);
     char *mem = nullptr;
     cudaError_t e = cudaMallocAsync(&mem, total, s);
     if (e != cudaSuccess) return fail(PGM_ENOMEM, std::string("cudaMallocAsync(grad): ") + cudaGetErrorString(e));
     auto buf = [&](size_t i) { return reinterpret_cast<float *>(mem + i * esb); };
     float *ck = buf(0), *rec = buf(n_ck), *mA = buf(n_ck + seg_len), *mB = buf(n_ck + seg_len + 1);
     float *adjA = buf(n_ck + seg_len + 2), *adjB = buf(n_ck + seg_len + 3), *dv = buf(n_ck + seg_len + 4);
+    float *ddamp = buf(n_ck + seg_len + 5);
     auto ckp = [&](int i) { return ck + (size_t)i * (esb / sizeof(float)); };
     auto recp = [&](int i) { return rec + (size_t)i * (esb / sizeof(float)); };
     pgm_status st = PGM_OK;
@@ -764,9 +765,9 @@ pgm_status pgm_grad(pgm_graph *g, const float *log_pot, const float *evidence, f
             const float *m_prev = recp(t - 1 - t0);
             e = launch_var_pass(g->G, g->P, evidence, m_prev, g->b, kVarIter, nullptr, s);
             if (e == cudaSuccess)
-                e = launch_adj_factor(g->G, g->adj_launch, log_pot, g->b, evidence, m_prev, adjA, dv, d_log_pot, T,
-                                      damping, s);
-            if (e == cudaSuccess) e = launch_adj_var(g->G, adjA, dv, adjB, d_evidence, damping, s);
+                e = launch_adj_factor(g->G, g->adj_launch, log_pot, g->b, evidence, m_prev, adjA, dv, ddamp,
+                                      d_log_pot, T, damping, s);
+            if (e == cudaSuccess) e = launch_adj_var(g->G, ddamp, dv, adjB, d_evidence, s);
             if (e != cudaSuccess) st = cuda_fail(e, "adjoint step launch");
             std::swap(adjA, adjB);
         }

@@ -1503,10 +1503,13 @@ k_logic_warp(DevGraph G, const LogicSeg *__restrict__ segs, int n_seg, const flo
 
 // =====================================================================================
 // Adjoint (gradient of L = sum g * normalised log-beliefs w.r.t. log-potentials and
-// evidence, T > 0, enumeration factors). Message adjoints sum to zero over each edge's
-// states (normalised beliefs are invariant to per-edge constants), so both
-// normalisations of an iteration are transparent in reverse; damping scales by delta
-// and 1 - delta.
+// evidence, T > 0, enumeration factors). Reverse of each forward step of an iteration:
+// the two max-normalisations (the adjoint's sum moves to the argmax state), damping
+// (delta to the previous messages, 1 - delta to the factor output), the factor's
+// log-sum-exp (a softmax over its configurations), the variable-side sums. In exact
+// arithmetic message adjoints sum to zero over each edge's states, but the projection
+// of the normalisations must still be applied: rounding seeds a constant component
+// that the reverse factor map would otherwise amplify.
 // =====================================================================================
 
 // Belief read-out: db = g - softmax(b) * sum(g); d_evidence = db; adjoint of every
@@ -1546,16 +1549,18 @@ __global__ void __launch_bounds__(128) k_adj_beliefs(DevGraph G, const float *__
     }
 }
 
-// Factor step in reverse, thread per enumeration factor: with gamma_i = (1 - delta) *
-// adjoint of edge i and p_i(c) = exp((s_{-i}(c) - LSE_T{s_{-i}(c') : c'_i = c_i}) / T),
+// Factor step in reverse, thread per enumeration factor. From the adjoint a of the new
+// messages: dd = a - sum(a) [x == argmax d] (second normalisation), the damping term
+// delta * dd goes to `ddamp`, dn = (1 - delta) dd, gamma = dn - sum(dn) [x == argmax mt]
+// (first normalisation), and with p_i(c) = exp((s_{-i}(c) - mt_i(c_i)) / T):
 //   d log_pot(c) += sum_i gamma_i(c_i) p_i(c)
 //   dv2f_j(y)     = sum_{i != j} sum_{c: c_j = y} gamma_i(c_i) p_i(c)
-// The variable-to-factor values are recomputed exactly as the forward factor pass does.
+// The variable-to-factor values and mt are recomputed as the forward factor pass does.
 __global__ void __launch_bounds__(128)
 k_adj_factor(DevGraph G, const EnumSeg *__restrict__ segs, int n_seg, const float *__restrict__ pot,
              const float *__restrict__ b, const float *__restrict__ ev, const float *__restrict__ m_old,
-             const float *__restrict__ adj, float *__restrict__ dv2f, float *__restrict__ d_pot, float T,
-             float invT, float damping) {
+             const float *__restrict__ adj, float *__restrict__ dv2f, float *__restrict__ ddamp,
+             float *__restrict__ d_pot, float T, float invT, float damping) {
     const EnumSeg *S = segs + find_seg(segs, n_seg, blockIdx.x);
     const int f = (blockIdx.x - S->block_begin) * blockDim.x + threadIdx.x;
     if (f >= S->n_fac) return;
@@ -1568,7 +1573,6 @@ k_adj_factor(DevGraph G, const EnumSeg *__restrict__ segs, int n_seg, const floa
     const int es_f = S->es_base + f * ksum;
     const int e_f = S->edge_base + f * a;
     float v2f[kMaxStateSum], gam[kMaxStateSum], lm[kMaxStateSum], ls[kMaxStateSum], dv[kMaxStateSum];
-    const float w1 = (damping != 0.f) ? 1.f - damping : 1.f;
     for (int j = 0; j < a; ++j) {
         const int vs = G.edge_vs[e_f + j];
         const int es = es_f + Ko[j];
@@ -1587,18 +1591,15 @@ k_adj_factor(DevGraph G, const EnumSeg *__restrict__ segs, int n_seg, const floa
         } else {
             for (int x = 0; x < Kj[j]; ++x) v2f[Ko[j] + x] = b[vs + x] - m_old[es + x];
         }
-        for (int x = 0; x < Kj[j]; ++x) {
-            gam[Ko[j] + x] = w1 * adj[es + x];
-            dv[Ko[j] + x] = 0.f;
-        }
     }
     for (int i = 0; i < ksum; ++i) {
         lm[i] = kNegInf;
         ls[i] = 0.f;
+        dv[i] = 0.f;
     }
     const uint8_t *cfg = G.cfg_pool + S->cfg_base;
     const float *phi = pot + S->pot_base + (S->shared ? 0 : (size_t)f * nc);
-    // LSE_T over the configurations consistent with each (edge, state)
+    // mt: LSE_T over the configurations consistent with each (edge, state)
     for (int c = 0; c < nc; ++c) {
         const uint8_t *cc = cfg + c * a;
         for (int i = 0; i < a; ++i) {
@@ -1616,6 +1617,34 @@ k_adj_factor(DevGraph G, const EnumSeg *__restrict__ segs, int n_seg, const floa
     }
     for (int i = 0; i < ksum; ++i)
         if (lm[i] != kNegInf) lm[i] += T * logf(ls[i]);
+    // reverse of normalise - damp - normalise, per edge
+    const float w1 = (damping != 0.f) ? 1.f - damping : 1.f;
+    for (int j = 0; j < a; ++j) {
+        const int K = Kj[j], o = Ko[j], es = es_f + o;
+        int a1 = 0;
+        for (int x = 1; x < K; ++x)
+            if (lm[o + x] > lm[o + a1]) a1 = x;
+        const float mx = lm[o + a1];
+        int a2 = 0;
+        float d2 = 0.f, sa = 0.f;
+        for (int x = 0; x < K; ++x) {
+            const float n = (mx == kNegInf) ? 0.f : lm[o + x] - mx;
+            const float d = (damping != 0.f) ? damping * m_old[es + x] + w1 * n : n;
+            if (x == 0 || d > d2) {
+                d2 = d;
+                a2 = x;
+            }
+            sa += adj[es + x];
+        }
+        float sn = 0.f;
+        for (int x = 0; x < K; ++x) {
+            const float dd = adj[es + x] - (x == a2 ? sa : 0.f);
+            ddamp[es + x] = damping * dd;
+            gam[o + x] = w1 * dd;
+            sn += gam[o + x];
+        }
+        gam[o + a1] -= sn;
+    }
     float *dphi = d_pot + S->pot_base + (S->shared ? 0 : (size_t)f * nc);
     for (int c = 0; c < nc; ++c) {
         const uint8_t *cc = cfg + c * a;
@@ -1639,10 +1668,10 @@ k_adj_factor(DevGraph G, const EnumSeg *__restrict__ segs, int n_seg, const floa
 
 // Variable step in reverse, thread per variable: db(x) = sum over incoming edges of
 // dv2f(x); d_evidence += db; adjoint of message m_{t-1} on each incoming edge =
-// delta * adjoint_t - dv2f + db.
-__global__ void __launch_bounds__(128) k_adj_var(DevGraph G, const float *__restrict__ adj,
+// ddamp - dv2f + db (ddamp: the damping term from k_adj_factor).
+__global__ void __launch_bounds__(128) k_adj_var(DevGraph G, const float *__restrict__ ddamp,
                                                  const float *__restrict__ dv2f, float *__restrict__ adj_prev,
-                                                 float *__restrict__ d_ev, float damping) {
+                                                 float *__restrict__ d_ev) {
     const int v = blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= G.V) return;
     const int vs = G.vs_off[v], K = G.vs_off[v + 1] - vs, k0 = G.vin_off[v], k1 = G.vin_off[v + 1];
@@ -1653,7 +1682,7 @@ __global__ void __launch_bounds__(128) k_adj_var(DevGraph G, const float *__rest
         d_ev[vs + x] += d;
         for (int k = k0; k < k1; ++k) {
             const int i = G.vin_es[k] + x;
-            adj_prev[i] = damping * adj[i] - dv2f[i] + d;
+            adj_prev[i] = ddamp[i] - dv2f[i] + d;
         }
     }
 }
@@ -1772,17 +1801,17 @@ cudaError_t launch_adj_beliefs(const DevGraph &G, const float *ev, const float *
 }
 
 cudaError_t launch_adj_factor(const DevGraph &G, const FactorLaunch &L, const float *pot, const float *b,
-                              const float *ev, const float *m_old, const float *adj, float *dv2f, float *d_pot,
-                              float T, float damping, cudaStream_t s) {
+                              const float *ev, const float *m_old, const float *adj, float *dv2f, float *ddamp,
+                              float *d_pot, float T, float damping, cudaStream_t s) {
     if (L.n_blocks == 0) return cudaSuccess;
     k_adj_factor<<<L.n_blocks, L.threads, 0, s>>>(G, static_cast<const EnumSeg *>(L.segs), L.n_seg, pot, b, ev,
-                                                  m_old, adj, dv2f, d_pot, T, 1.f / T, damping);
+                                                  m_old, adj, dv2f, ddamp, d_pot, T, 1.f / T, damping);
     return cudaGetLastError();
 }
 
-cudaError_t launch_adj_var(const DevGraph &G, const float *adj, const float *dv2f, float *adj_prev, float *d_ev,
-                           float damping, cudaStream_t s) {
-    k_adj_var<<<(G.V + 127) / 128, 128, 0, s>>>(G, adj, dv2f, adj_prev, d_ev, damping);
+cudaError_t launch_adj_var(const DevGraph &G, const float *ddamp, const float *dv2f, float *adj_prev, float *d_ev,
+                           cudaStream_t s) {
+    k_adj_var<<<(G.V + 127) / 128, 128, 0, s>>>(G, ddamp, dv2f, adj_prev, d_ev);
     return cudaGetLastError();
 }
 

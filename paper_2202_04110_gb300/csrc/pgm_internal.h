@@ -169,10 +169,10 @@ cudaError_t launch_factor_pass(const DevGraph &G, const Plan &P, const float *lo
 cudaError_t launch_adj_beliefs(const DevGraph &G, const float *ev, const float *m, const float *gnb, float *d_ev,
                                float *adj, cudaStream_t s);
 cudaError_t launch_adj_factor(const DevGraph &G, const FactorLaunch &L, const float *pot, const float *b,
-                              const float *ev, const float *m_old, const float *adj, float *dv2f, float *d_pot,
-                              float T, float damping, cudaStream_t s);
-cudaError_t launch_adj_var(const DevGraph &G, const float *adj, const float *dv2f, float *adj_prev, float *d_ev,
-                           float damping, cudaStream_t s);
+                              const float *ev, const float *m_old, const float *adj, float *dv2f, float *ddamp,
+                              float *d_pot, float T, float damping, cudaStream_t s);
+cudaError_t launch_adj_var(const DevGraph &G, const float *ddamp, const float *dv2f, float *adj_prev, float *d_ev,
+                           cudaStream_t s);
 // Configure kernel attributes (large dynamic shared memory) once per process/device.
 cudaError_t prepare_kernels(int max_smem_bytes);
 
