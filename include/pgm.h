@@ -323,6 +323,67 @@ pgm_status pgm_autotune(pgm_graph *g, const float *log_pot, const float *evidenc
 pgm_status pgm_launch_info(const pgm_graph *g, int32_t i, int32_t *kind, int32_t *variant,
                            int32_t *threads, int32_t *n_blocks);
 
+/*
+ * Serving loop: continuous admission of inference requests onto one GPU.
+ * A request is a graph description with its log-potentials and evidence (host memory,
+ * copied at submission), T, damping and an iteration count; its result is the
+ * normalised log-beliefs and the MAP decode after n_iters iterations from zero messages
+ * (pgm_run_bp + pgm_beliefs + pgm_decode). Requests queue in arrival order; up to
+ * max_in_flight of them are on the GPU at once, each on its own stream, and the one at
+ * the head of the queue is admitted as soon as a slot is free and its device memory
+ * (compiled graph, scratch, inputs, outputs; stream-ordered allocations) fits
+ * memory_budget_bytes together with the requests in flight. Kernels of in-flight
+ * requests overlap on the device; a request's messages stay resident until it
+ * finishes; max_in_flight = 1 runs one request at a time in arrival order. Results are
+ * those of the same request run alone. Latency = submission to results in host memory.
+ * The server's worker threads are its own; all calls are thread-safe.
+ */
+typedef struct pgm_server pgm_server;
+
+typedef struct {
+    int64_t memory_budget_bytes; /* device memory for requests in flight, > 0 */
+    int32_t max_in_flight;       /* concurrent requests (worker threads and streams), 1..64 */
+    int32_t max_pending;         /* queued requests before pgm_serve_submit returns PGM_EBUSY */
+} pgm_server_config;
+
+typedef struct {
+    int64_t submitted, completed, failed, pending, in_flight;
+    int64_t bytes_in_use, peak_bytes; /* device memory accounted to requests in flight */
+    int64_t updates_done;             /* edge-state message updates of completed requests */
+    double span_s;                    /* first submission to last completion, seconds */
+} pgm_server_stats;
+
+/* Create a server on the current device (starts max_in_flight worker threads). */
+pgm_status pgm_serve_create(const pgm_server_config *cfg, pgm_server **out);
+
+/*
+ * Queue a request; *id identifies it. The description and host arrays are copied (they
+ * may be freed on return); the graph is compiled and validated by the worker that
+ * admits it (errors are reported by pgm_serve_poll / pgm_serve_wait). Never waits for
+ * the GPU. Errors: PGM_EINVAL (argument checks), PGM_EBUSY (queue full).
+ */
+pgm_status pgm_serve_submit(pgm_server *s, const pgm_graph_desc *desc, const float *log_pot,
+                            const float *evidence, float T, float damping, int32_t n_iters,
+                            int64_t *id);
+
+/*
+ * Result of request `id`: PGM_EBUSY while it is queued or running; otherwise copies the
+ * normalised log-beliefs [n_var_states] and decode [n_vars] into the host buffers (each
+ * may be NULL), writes the latency in seconds, forgets the request and returns its
+ * status (PGM_ENOMEM if it alone exceeds the memory budget, a build or CUDA error).
+ */
+pgm_status pgm_serve_poll(pgm_server *s, int64_t id, float *beliefs, int32_t *decode,
+                          double *latency_s);
+
+/* pgm_serve_poll that waits up to timeout_us microseconds; PGM_ETIMEDOUT if not done. */
+pgm_status pgm_serve_wait(pgm_server *s, int64_t id, int64_t timeout_us, float *beliefs,
+                          int32_t *decode, double *latency_s);
+
+pgm_status pgm_serve_stats(pgm_server *s, pgm_server_stats *stats);
+
+/* Stop admitting, finish the requests in flight, drop the queue, join the workers. */
+void pgm_serve_destroy(pgm_server *s);
+
 /* Thread-local description of the calling thread's last error ("" if none). */
 const char *pgm_last_error(void);
 

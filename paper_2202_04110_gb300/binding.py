@@ -24,7 +24,8 @@ FLAG_NAN = 2
 EXPORTED = ["pgm_build", "pgm_build_batch", "pgm_batch_member", "pgm_check_desc", "pgm_free", "pgm_graph_info", "pgm_run_bp", "pgm_beliefs",
             "pgm_decode", "pgm_infer_host", "pgm_set_profiling", "pgm_pass_times",
             "pgm_device_flags", "pgm_grid2_run_bp_noalloc", "pgm_set_option", "pgm_autotune",
-            "pgm_launch_info", "pgm_grad", "pgm_last_error"]
+            "pgm_launch_info", "pgm_grad", "pgm_serve_create", "pgm_serve_submit", "pgm_serve_poll",
+            "pgm_serve_wait", "pgm_serve_stats", "pgm_serve_destroy", "pgm_last_error"]
 OPT_CUDA_GRAPH = 1
 
 
@@ -58,6 +59,16 @@ class InfoC(ctypes.Structure):
                 ("max_states", ctypes.c_int32), ("max_degree", ctypes.c_int32),
                 ("device_bytes", ctypes.c_int64), ("launches_per_iter", ctypes.c_int32),
                 ("n_members", ctypes.c_int32)]
+
+
+class ServerConfigC(ctypes.Structure):
+    _fields_ = [("memory_budget_bytes", ctypes.c_int64), ("max_in_flight", ctypes.c_int32),
+                ("max_pending", ctypes.c_int32)]
+
+
+class ServerStatsC(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int64) for n in ("submitted", "completed", "failed", "pending", "in_flight",
+                                              "bytes_in_use", "peak_bytes", "updates_done")] + [("span_s", ctypes.c_double)]
 
 
 class MemberC(ctypes.Structure):
@@ -114,6 +125,18 @@ def load_library(path: str | None = None):
     lib.pgm_launch_info.argtypes = [vp, i32] + [ctypes.POINTER(i32)] * 4
     lib.pgm_grad.restype = i32
     lib.pgm_grad.argtypes = [vp, vp, vp, f32, f32, i32, i32, vp, vp, vp, vp]
+    lib.pgm_serve_create.restype = i32
+    lib.pgm_serve_create.argtypes = [ctypes.POINTER(ServerConfigC), ctypes.POINTER(vp)]
+    lib.pgm_serve_submit.restype = i32
+    lib.pgm_serve_submit.argtypes = [vp, ctypes.POINTER(GraphDescC), vp, vp, f32, f32, i32, ctypes.POINTER(ctypes.c_int64)]
+    lib.pgm_serve_poll.restype = i32
+    lib.pgm_serve_poll.argtypes = [vp, ctypes.c_int64, vp, vp, ctypes.POINTER(ctypes.c_double)]
+    lib.pgm_serve_wait.restype = i32
+    lib.pgm_serve_wait.argtypes = [vp, ctypes.c_int64, ctypes.c_int64, vp, vp, ctypes.POINTER(ctypes.c_double)]
+    lib.pgm_serve_stats.restype = i32
+    lib.pgm_serve_stats.argtypes = [vp, ctypes.POINTER(ServerStatsC)]
+    lib.pgm_serve_destroy.restype = None
+    lib.pgm_serve_destroy.argtypes = [vp]
     lib.pgm_set_option.restype = i32
     lib.pgm_set_option.argtypes = [vp, i32, ctypes.c_int64]
     lib.pgm_last_error.restype = ctypes.c_char_p
@@ -400,3 +423,62 @@ def lbp_beliefs(log_pot, evidence, graph: Graph, T: float, damping: float, n_ite
     if _LBP is None:
         _LBP = _lbp_function()
     return _LBP.apply(log_pot, evidence, graph, T, damping, n_iters, ckpt_every)
+
+
+class Server:
+    """The serving loop (pgm_serve_*): submit requests, poll or wait for results."""
+
+    def __init__(self, memory_budget_bytes: int, max_in_flight: int, max_pending: int = 1 << 20):
+        lib = load_library()
+        cfg = ServerConfigC(int(memory_budget_bytes), int(max_in_flight), int(max_pending))
+        h = ctypes.c_void_p()
+        check(lib.pgm_serve_create(ctypes.byref(cfg), ctypes.byref(h)))
+        self._h = h
+        self._shapes = {}
+
+    def submit(self, fg, log_pot, evidence, T: float, damping: float, n_iters: int) -> int:
+        desc, keep = marshal_desc(fg)
+        lp = np.ascontiguousarray(log_pot, np.float32)
+        ev = np.ascontiguousarray(evidence, np.float32)
+        rid = ctypes.c_int64()
+        check(load_library().pgm_serve_submit(self._h, ctypes.byref(desc), lp.ctypes.data if lp.size else None,
+                                              ev.ctypes.data, float(T), float(damping), int(n_iters),
+                                              ctypes.byref(rid)))
+        del keep
+        self._shapes[rid.value] = (fg.n_var_states, fg.n_vars)
+        return rid.value
+
+    def _result(self, fn, rid, *args):
+        VS, V = self._shapes[rid]
+        bel = np.empty(VS, np.float32)
+        dec = np.empty(V, np.int32)
+        lat = ctypes.c_double()
+        st = fn(self._h, ctypes.c_int64(rid), *args, bel.ctypes.data, dec.ctypes.data, ctypes.byref(lat))
+        if st == -5:
+            return None
+        self._shapes.pop(rid, None)
+        check(st)
+        return bel, dec, lat.value
+
+    def poll(self, rid: int):
+        """(beliefs, decode, latency_s) when done, else None."""
+        return self._result(load_library().pgm_serve_poll, rid)
+
+    def wait(self, rid: int, timeout_s: float):
+        return self._result(load_library().pgm_serve_wait, rid, ctypes.c_int64(int(timeout_s * 1e6)))
+
+    def stats(self) -> dict:
+        st = ServerStatsC()
+        check(load_library().pgm_serve_stats(self._h, ctypes.byref(st)))
+        return {k: getattr(st, k) for k, _ in ServerStatsC._fields_}
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load_library().pgm_serve_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -51,6 +51,8 @@ int32_t pgm::set_last_error(int32_t code, const std::string &msg) { return fail(
 struct pgm_graph {
     int device = 0;
     int n_sm = 1;
+    bool ordered = false;              // allocations stream-ordered on alloc_stream
+    cudaStream_t alloc_stream = nullptr;
     pgm_info info{};
     DevGraph G{};
     Plan P{};
@@ -262,7 +264,10 @@ extern "C" {
 
 const char *pgm_last_error(void) { return g_last_error.c_str(); }
 
-static pgm_status build_from_descs(const void *const *descs, int n, pgm_graph **out) {
+// Build a graph. With `ordered`, every allocation, copy and free of the graph is
+// stream-ordered on `s` (no device-wide synchronisation; used by the serving loop).
+static pgm_status build_from_descs(const void *const *descs, int n, pgm_graph **out, cudaStream_t s = nullptr,
+                                   bool ordered = false) {
     g_last_error.clear();
     if (!out) return fail(PGM_EINVAL, "out is NULL");
     *out = nullptr;
@@ -293,15 +298,19 @@ static pgm_status build_from_descs(const void *const *descs, int n, pgm_graph **
         delete g;
         return st;
     }
+    g->ordered = ordered;
+    g->alloc_stream = s;
     char *dmem = nullptr;
-    ce = cudaMalloc(&dmem, pk.host.size());
+    ce = ordered ? cudaMallocAsync(&dmem, pk.host.size(), s) : cudaMalloc(&dmem, pk.host.size());
     if (ce != cudaSuccess) {
         delete g;
         return fail(PGM_ENOMEM, std::string("cudaMalloc(index arrays): ") + cudaGetErrorString(ce));
     }
-    ce = cudaMemcpy(dmem, pk.host.data(), pk.host.size(), cudaMemcpyHostToDevice);
+    ce = ordered ? cudaMemcpyAsync(dmem, pk.host.data(), pk.host.size(), cudaMemcpyHostToDevice, s)
+                 : cudaMemcpy(dmem, pk.host.data(), pk.host.size(), cudaMemcpyHostToDevice);
     if (ce != cudaSuccess) {
-        cudaFree(dmem);
+        if (ordered) cudaFreeAsync(dmem, s);
+        else cudaFree(dmem);
         delete g;
         return cuda_fail(ce, "cudaMemcpy(index arrays)");
     }
@@ -310,9 +319,11 @@ static pgm_status build_from_descs(const void *const *descs, int n, pgm_graph **
     size_t vs_bytes = align_up(std::max<int64_t>(H.VS, 1) * sizeof(float), 256);
     size_t hd_bytes = H.var_bucket[kVarBlock].empty() ? 0 : 2 * es_bytes;
     char *smem = nullptr;
-    ce = cudaMalloc(&smem, es_bytes + vs_bytes + 256 + hd_bytes);
+    ce = ordered ? cudaMallocAsync(&smem, es_bytes + vs_bytes + 256 + hd_bytes, s)
+                 : cudaMalloc(&smem, es_bytes + vs_bytes + 256 + hd_bytes);
     if (ce != cudaSuccess) {
-        cudaFree(dmem);
+        if (ordered) cudaFreeAsync(dmem, s);
+        else cudaFree(dmem);
         delete g;
         return fail(PGM_ENOMEM, std::string("cudaMalloc(scratch): ") + cudaGetErrorString(ce));
     }
@@ -320,7 +331,7 @@ static pgm_status build_from_descs(const void *const *descs, int n, pgm_graph **
     g->m_tmp = reinterpret_cast<float *>(smem);
     g->b = reinterpret_cast<float *>(smem + es_bytes);
     uint32_t *flags = reinterpret_cast<uint32_t *>(smem + es_bytes + vs_bytes);
-    ce = cudaMemset(flags, 0, 256);
+    ce = ordered ? cudaMemsetAsync(flags, 0, 256, s) : cudaMemset(flags, 0, 256);
     if (ce != cudaSuccess) {
         pgm_free(g);
         return cuda_fail(ce, "cudaMemset(flags)");
@@ -382,6 +393,18 @@ pgm_status pgm_build(const pgm_graph_desc *desc, pgm_graph **out) {
     return build_from_descs(&one, 1, out);
 }
 
+}  // extern "C"
+
+pgm_status pgm::build_graph_on_stream(const pgm_graph_desc *desc, cudaStream_t s, pgm_graph **out) {
+    const void *one = desc;
+    pgm_status st = build_from_descs(&one, 1, out, s, true);
+    if (st == PGM_OK) (*out)->use_cuda_graph = 0;
+    return st;
+}
+
+extern "C" {
+
+
 pgm_status pgm_build_batch(const pgm_graph_desc *const *descs, int32_t n, pgm_graph **out) {
     if (n < 1 || !descs) return fail(PGM_EINVAL, "a batch needs n >= 1 descriptions");
     std::vector<const void *> v(descs, descs + n);
@@ -437,7 +460,14 @@ static void drop_cached_runs(pgm_graph *g);
 void pgm_free(pgm_graph *g) {
     if (!g) return;
     DeviceGuard dg(g->device);
-    cudaDeviceSynchronize();
+    if (g->ordered) {
+        if (g->index_mem) cudaFreeAsync(g->index_mem, g->alloc_stream);
+        if (g->scratch_mem) cudaFreeAsync(g->scratch_mem, g->alloc_stream);
+        if (g->host_io_mem) cudaFreeAsync(g->host_io_mem, g->alloc_stream);
+        g->index_mem = g->scratch_mem = g->host_io_mem = nullptr;
+    } else {
+        cudaDeviceSynchronize();
+    }
     if (g->index_mem) cudaFree(g->index_mem);
     if (g->scratch_mem) cudaFree(g->scratch_mem);
     if (g->host_io_mem) cudaFree(g->host_io_mem);

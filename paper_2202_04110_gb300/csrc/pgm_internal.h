@@ -13,6 +13,8 @@
 
 #include <cuda_runtime.h>
 
+#include "../../include/pgm.h"
+
 namespace pgm {
 
 constexpr int kMaxArity = 8;
@@ -175,6 +177,10 @@ cudaError_t launch_adj_var(const DevGraph &G, const float *ddamp, const float *d
                            cudaStream_t s);
 // Configure kernel attributes (large dynamic shared memory) once per process/device.
 cudaError_t prepare_kernels(int max_smem_bytes);
+
+// Build a graph whose allocations, uploads and frees (pgm_free) are stream-ordered on
+// `s`, with CUDA-graph replay off (used by the serving loop; capi.cu).
+int32_t build_graph_on_stream(const pgm_graph_desc *desc, cudaStream_t s, pgm_graph **out);
 
 // Records `msg` as the calling thread's last error (pgm_last_error) and returns `code`.
 int32_t set_last_error(int32_t code, const std::string &msg);
