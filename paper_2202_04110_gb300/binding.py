@@ -456,7 +456,8 @@ class Server:
         st = fn(self._h, ctypes.c_int64(rid), *args, bel.ctypes.data, dec.ctypes.data, ctypes.byref(lat))
         if st == -5:
             return None
-        self._shapes.pop(rid, None)
+        if st != -6:  # a timed-out request is still pending
+            self._shapes.pop(rid, None)
         check(st)
         return bel, dec, lat.value
 
