@@ -49,6 +49,10 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched vs per-graph measurement")
     ap.add_argument("--batch-grids", type=int, default=256)
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
+    ap.add_argument("--serve-rate", type=float, default=2000.0, help="mean Poisson arrival rate (requests/s)")
+    ap.add_argument("--serve-duration", type=float, default=1.0, help="seconds of arrivals per serving run")
+    ap.add_argument("--serve-slots", type=int, default=16)
     ap.add_argument("--cpu-iters", type=int, default=40, help="oracle iterations per T in the CPU baseline sample")
     ap.add_argument("--ref-iters", type=int, default=16, help="oracle iterations per T in one reference step")
     return ap.parse_args()
@@ -255,6 +259,62 @@ def measure_batched(args, binding, W, torch, dev):
             "speedup": t_single / t_batched, "autotune_s": round(tune_s, 2), "launch_shapes": launches}
 
 
+def serve_run(binding, templates, descs, arrivals, slots, budget):
+    """Submit `arrivals` on schedule to a server with `slots` in-flight requests; wait
+    for all; latencies (s) and throughput (updates/s over first submission to last
+    completion)."""
+    srv = binding.Server(memory_budget_bytes=budget, max_in_flight=slots)
+    ids = []
+    t0 = time.perf_counter()
+    for t_arr, ti, iters in arrivals:
+        now = time.perf_counter() - t0
+        if t_arr > now:
+            time.sleep(t_arr - now)
+        p = templates[ti]
+        ids.append(srv.submit(p.graph, p.log_pot, p.evidence, p.T, 0.5, iters, desc=descs[ti]))
+    t_sub = time.perf_counter() - t0
+    lat = []
+    for i in ids:
+        _, _, l = srv.wait(i, 600.0)
+        lat.append(l)
+    st = srv.stats()
+    srv.close()
+    lat = sorted(lat)
+    q = lambda f: 1e3 * lat[min(len(lat) - 1, int(f * len(lat)))]
+    return {"requests": len(ids), "p50_ms": round(q(0.50), 2), "p99_ms": round(q(0.99), 2),
+            "mean_ms": round(1e3 * sum(lat) / len(lat), 2),
+            "throughput": st["updates_done"] / st["span_s"] if st["span_s"] > 0 else None,
+            "offered_rate_achieved": round(len(ids) / t_sub, 1), "span_s": round(st["span_s"], 3),
+            "peak_bytes": st["peak_bytes"], "failed": st["failed"]}
+
+
+def measure_serving(args, binding, W):
+    """Serving workload: Poisson arrivals of grid requests (side U{16..512}, K in {2,4,16},
+    T in {0,1}, 50-200 iterations, damping 0.5) drawn from 48 seeded templates; the
+    continuous server (admission by slots and memory) against the FIFO baseline (one
+    request at a time) on the same arrivals, and a load sweep."""
+    templates = W.serving_templates(seed=0)
+    descs = [binding.marshal_desc(p.graph) for p in templates]
+    budget = 40 << 30
+    rate, dur = args.serve_rate, args.serve_duration
+    out = {"workload": "Poisson arrivals of Ising / Potts grid requests: side U{16..512}, K in {2,4,16}, "
+                       "T in {0,1}, 50-200 iterations, damping 0.5 (48 seeded templates)",
+           "rate_req_s": rate, "duration_s": dur, "slots": args.serve_slots, "memory_budget_bytes": budget,
+           "latency": "submission to results in host memory", "unit": UNIT}
+    warm = W.poisson_arrivals(99, 200.0, 0.1, len(templates))
+    serve_run(binding, templates, descs, warm, args.serve_slots, budget)
+    arr = W.poisson_arrivals(1, rate, dur, len(templates))
+    out["continuous"] = serve_run(binding, templates, descs, arr, args.serve_slots, budget)
+    out["fifo"] = serve_run(binding, templates, descs, arr, 1, budget)
+    out["sweep"] = []
+    for f in (0.25, 0.5):
+        a = W.poisson_arrivals(2, rate * f, dur, len(templates))
+        r = serve_run(binding, templates, descs, a, args.serve_slots, budget)
+        r["rate_req_s"] = rate * f
+        out["sweep"].append(r)
+    return out
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -405,6 +465,8 @@ def run_ours(args):
 
     if not args.no_batch:
         line["batched"] = measure_batched(args, binding, W, torch, dev)
+    if not args.no_serve and world == 1:
+        line["serving"] = measure_serving(args, binding, W)
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, dt, cores = cpu_sample(p, args.cpu_iters)

@@ -436,8 +436,10 @@ class Server:
         self._h = h
         self._shapes = {}
 
-    def submit(self, fg, log_pot, evidence, T: float, damping: float, n_iters: int) -> int:
-        desc, keep = marshal_desc(fg)
+    def submit(self, fg, log_pot, evidence, T: float, damping: float, n_iters: int, desc=None) -> int:
+        """Queue a request. `desc` may be a (desc, keepalive) pair from marshal_desc(fg),
+        reused across submissions of the same graph."""
+        desc, keep = desc if desc is not None else marshal_desc(fg)
         lp = np.ascontiguousarray(log_pot, np.float32)
         ev = np.ascontiguousarray(evidence, np.float32)
         rid = ctypes.c_int64()

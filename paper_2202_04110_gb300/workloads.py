@@ -451,3 +451,30 @@ def random_factor_tree(seed: int, n_vars: int = 9, max_K: int = 3, shared: bool 
     log_pot = (np.concatenate(pots) if pots else np.zeros(0)).astype(np.float32)
     evidence = rng.normal(0, scale, int(Karr.sum())).astype(np.float32)
     return g, log_pot, evidence
+
+
+def serving_templates(seed: int = 0, n: int = 48, lo: int = 16, hi: int = 512, Ks=(2, 4, 16)):
+    """Request templates of the serving workload: grids with side ~ U{lo..hi}, K ~ U(Ks)
+    (K = 2: Ising, else Potts), T ~ U{0, 1}; damping 0.5."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n):
+        side = int(rng.integers(lo, hi + 1))
+        K = int(rng.choice(np.asarray(Ks)))
+        T = float(rng.choice([0.0, 1.0]))
+        sd = int(rng.integers(0, 2**31 - 1))
+        p = ising_grid(side, side, sd, T=T) if K == 2 else potts_grid(side, K, sd, T=T)
+        out.append(p)
+    return out
+
+
+def poisson_arrivals(seed: int, rate: float, duration: float, n_templates: int, it_lo: int = 50, it_hi: int = 200):
+    """Seeded Poisson arrival times in [0, duration) with a template index and an
+    iteration count ~ U{it_lo..it_hi} per arrival."""
+    rng = np.random.default_rng(seed)
+    t, out = 0.0, []
+    while True:
+        t += float(rng.exponential(1.0 / rate))
+        if t >= duration:
+            return out
+        out.append((t, int(rng.integers(0, n_templates)), int(rng.integers(it_lo, it_hi + 1))))
