@@ -154,6 +154,19 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def aggregate_ranks(dist, local_ms: float, updates_per_rank: float, device=None):
+    """Whole-job throughput over replicas: the slowest rank's time (all-reduce MAX) and
+    the updates of all ranks. Returns (max_ms, updates/s)."""
+    world = dist.get_world_size() if dist is not None else 1
+    ms = local_ms
+    if dist is not None and world > 1:
+        import torch
+        t = torch.tensor([local_ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms, world * updates_per_rank / (ms / 1e3)
+
+
 def dist_setup():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -387,12 +400,7 @@ def run_ours(args):
     var_ms, fac_ms, n_var, n_fac = g.pass_times()
     g.set_profiling(0)
     ms = [a.elapsed_time(b) for a, b in step_ms]
-    total_ms = float(sum(ms))
-    if dist is not None:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * updates_per_step * args.steps / (total_ms / 1e3)
+    total_ms, value = aggregate_ranks(dist, float(sum(ms)), updates_per_step * args.steps, dev)
     flags = g.flags(clear=True)
 
     # roofline of the dominant kernel: algorithmic bytes per launch / mean launch time
