@@ -220,10 +220,13 @@ pgm_status pgm_infer_host(pgm_graph *g, const float *log_pot, const float *evide
  * Per-pass timing with CUDA events on the launching stream. period = N > 0 makes every
  * following pgm_run_bp record an event before and after the variable pass and the
  * factor pass of every N-th iteration (iterations N-1, 2N-1, ... of each call); period
- * = 0 turns it off. pgm_pass_times synchronises, returns the summed durations
- * (milliseconds) and launch counts of the sampled passes since the last reset, and
- * resets them. Used by the benchmark to attribute time to kernels; a sparse period
- * keeps the timed run undisturbed.
+ * = 0 turns it off. With PGM_OPT_CUDA_GRAPH on, the records are event nodes of the
+ * call's CUDA graph (graphs are cached per period), so the times are those of the
+ * replayed graph; launching a cached graph again first waits for its previous replay
+ * if that replay's times have not been collected. pgm_pass_times synchronises,
+ * returns the summed durations (milliseconds) and launch counts of the sampled passes
+ * since the last reset, and resets them. Used by the benchmark to attribute time to
+ * kernels; a sparse period keeps the timed run undisturbed.
  */
 pgm_status pgm_set_profiling(pgm_graph *g, int32_t period);
 pgm_status pgm_pass_times(pgm_graph *g, double *var_ms, double *factor_ms, int64_t *n_var,
@@ -298,7 +301,28 @@ pgm_status pgm_grid2_run_bp_noalloc(int32_t rows, int32_t cols, const float *log
  * reused at the same address with the same meaning are fine.
  */
 #define PGM_OPT_CUDA_GRAPH 1
+/*
+ * PGM_OPT_LOG_RATIO (default 4; 0 = off): on a binary pairwise graph (every variable
+ * binary, every factor a 2 x 2 enumeration factor, no variable with more than 64
+ * factors), pgm_run_bp with n_iters >= the value keeps one number per edge and
+ * direction during the iterations: the log-ratio d = m(1) - m(0) of each max-
+ * normalised factor-to-variable message (the normalisation of Sec. 3 makes one entry
+ * 0, so the encoding loses nothing) and of each variable-to-factor message, the latter
+ * an exact leave-one-out sum rather than belief minus message. msgs is converted at
+ * the start (messages that are not max-normalised are normalised, which the update
+ * does not see) and written back in the [n_edge_states] layout at the end. The
+ * iteration is the same; results differ from the option-off path by rounding only.
+ * Negative values: PGM_EINVAL. pgm_launch_info / launches_per_iter do not count the 2
+ * conversion launches per run.
+ */
+#define PGM_OPT_LOG_RATIO 2
 pgm_status pgm_set_option(pgm_graph *g, int32_t option, int64_t value);
+/*
+ * The option's effective value in *value: for PGM_OPT_CUDA_GRAPH the setting; for
+ * PGM_OPT_LOG_RATIO the setting if the graph qualifies, else 0. PGM_EINVAL for
+ * a NULL argument or an unknown option. No device work.
+ */
+pgm_status pgm_get_option(const pgm_graph *g, int32_t option, int64_t *value);
 
 /*
  * Launch-shape autotuner: for every factor-pass launch of the graph (one per kernel

@@ -23,10 +23,11 @@ FLAG_NAN = 2
 # Every symbol include/pgm.h declares.
 EXPORTED = ["pgm_build", "pgm_build_batch", "pgm_batch_member", "pgm_check_desc", "pgm_free", "pgm_graph_info", "pgm_run_bp", "pgm_beliefs",
             "pgm_decode", "pgm_infer_host", "pgm_set_profiling", "pgm_pass_times",
-            "pgm_device_flags", "pgm_grid2_run_bp_noalloc", "pgm_set_option", "pgm_autotune",
+            "pgm_device_flags", "pgm_grid2_run_bp_noalloc", "pgm_set_option", "pgm_get_option", "pgm_autotune",
             "pgm_launch_info", "pgm_grad", "pgm_serve_create", "pgm_serve_submit", "pgm_serve_poll",
             "pgm_serve_wait", "pgm_serve_stats", "pgm_serve_destroy", "pgm_last_error"]
 OPT_CUDA_GRAPH = 1
+OPT_LOG_RATIO = 2
 
 
 class PgmError(RuntimeError):
@@ -139,6 +140,8 @@ def load_library(path: str | None = None):
     lib.pgm_serve_destroy.argtypes = [vp]
     lib.pgm_set_option.restype = i32
     lib.pgm_set_option.argtypes = [vp, i32, ctypes.c_int64]
+    lib.pgm_get_option.restype = i32
+    lib.pgm_get_option.argtypes = [vp, i32, vp]
     lib.pgm_last_error.restype = ctypes.c_char_p
     lib.pgm_last_error.argtypes = []
     _lib = lib
@@ -337,6 +340,12 @@ class Graph:
 
     def set_option(self, option: int, value: int):
         check(load_library().pgm_set_option(self._h, int(option), int(value)))
+
+    def get_option(self, option: int) -> int:
+        """Effective value of an option (pgm_get_option)."""
+        v = ctypes.c_int64()
+        check(load_library().pgm_get_option(self._h, int(option), ctypes.byref(v)))
+        return int(v.value)
 
     def set_profiling(self, period: int):
         """Record per-pass CUDA events every `period` iterations (0 = off)."""

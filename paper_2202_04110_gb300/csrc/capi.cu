@@ -81,10 +81,19 @@ struct pgm_graph {
         float *msgs;
         uint32_t T_bits, damping_bits;
         int32_t n_iters;
+        int32_t prof_period;             // per-pass timing captured in the graph (0 = none)
         cudaGraphExec_t exec;
         uint64_t last_use;
+        std::vector<cudaEvent_t> ev;     // event triples recorded by each replay
+        int64_t nv = 0, nf = 0;          // sampled launches per replay
+        bool pending = false;            // a replay whose times are not collected yet
     };
+    // capture in progress: where take_events puts the graph's events
+    std::vector<cudaEvent_t> *capture_events = nullptr;
+    int64_t capture_nv = 0, capture_nf = 0;
+    double graph_var_ms = 0.0, graph_factor_ms = 0.0;  // collected from replays
     int32_t use_cuda_graph = 1;
+    int32_t log_ratio_min_iters = 4;  // PGM_OPT_LOG_RATIO
     cudaStream_t capture_stream = nullptr;
     std::vector<CachedRun> runs;
     uint64_t use_clock = 0;
@@ -229,10 +238,29 @@ pgm_status build_plan(const HostLayout &H, pgm_graph *g, Packer &pk, std::vector
                                              reinterpret_cast<const char *>(segs.data() + segs.size()));
         }
     }
+    // log-ratio iterations: a binary pairwise graph (every edge has 2 states at 2e)
+    bool lr = H.all_binary && H.logic_groups.empty() && !H.enum_groups.empty() && H.ES == 2 * H.E &&
+              H.E % 2 == 0 && H.var_bucket[kVarBlock].empty();
+    for (const HostEnumGroup &hg : H.enum_groups) lr = lr && hg.variant == kPair2;
+    for (int kind = 0; kind < kNumVarKinds; ++kind)
+        if (kind != kVarBinary) lr = lr && H.var_bucket[kind].empty();
+    P.lr = lr;
     return PGM_OK;
 }
 
 pgm_status take_events(pgm_graph *g, cudaEvent_t *a, cudaEvent_t *b, cudaEvent_t *c) {
+    if (g->capture_events) {  // new events owned by the graph being captured
+        cudaEvent_t ev[3];
+        for (int i = 0; i < 3; ++i) {
+            cudaError_t e = cudaEventCreate(&ev[i]);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaEventCreate");
+            g->capture_events->push_back(ev[i]);
+        }
+        *a = ev[0];
+        *b = ev[1];
+        *c = ev[2];
+        return PGM_OK;
+    }
     while (g->events.size() < g->events_used + 3) {
         cudaEvent_t ev;
         cudaError_t e = cudaEventCreate(&ev);
@@ -484,31 +512,58 @@ pgm_status pgm_graph_info(const pgm_graph *g, pgm_info *info) {
 }
 
 // Enqueue n_iters iterations (and the final copy back into msgs) on stream s.
+// On binary pairwise graphs (Plan::lr) runs long enough to repay the two conversions
+// iterate on log-ratios: msgs is packed into d = m_tmp[0, E), the variable pass writes
+// the variable-to-factor values to lam = m_tmp[E, 2E), the factor pass updates d in
+// place, and d is unpacked into msgs at the end.
+static bool log_ratio_run(const pgm_graph *g, int32_t n_iters) {
+    return g->P.lr && g->log_ratio_min_iters > 0 && n_iters >= g->log_ratio_min_iters;
+}
+
 static pgm_status enqueue_iterations(pgm_graph *g, const float *log_pot, const float *evidence, float T,
                                      float damping, int32_t n_iters, float *msgs, cudaStream_t s,
                                      bool profile) {
     float *cur = msgs, *nxt = g->m_tmp;
+    const bool lr = log_ratio_run(g, n_iters);
+    const int32_t E = (int32_t)g->info.n_edges;
+    float *d = g->m_tmp, *lam = g->m_tmp + E;
+    if (lr) {
+        cudaError_t e = launch_lr_pack(msgs, E, d, s);
+        if (e != cudaSuccess) return cuda_fail(e, "log-ratio pack launch");
+    }
     for (int it = 0; it < n_iters; ++it) {
         cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr;
         const bool prof = profile && g->profiling > 0 && (it % g->profiling) == g->profiling - 1;
+        // inside a stream capture the records become event nodes of the graph
+        const unsigned rec_flags = g->capture_events ? cudaEventRecordExternal : cudaEventRecordDefault;
         if (prof) {
             pgm_status ps = take_events(g, &e0, &e1, &e2);
             if (ps != PGM_OK) return ps;
-            cudaEventRecord(e0, s);
+            cudaEventRecordWithFlags(e0, s, rec_flags);
         }
-        cudaError_t e = launch_var_pass(g->G, g->P, evidence, cur, g->b, kVarIter, nullptr, s);
+        cudaError_t e = lr ? launch_lr_var_pass(g->G, g->P, evidence, d, lam, s)
+                           : launch_var_pass(g->G, g->P, evidence, cur, g->b, kVarIter, nullptr, s);
         if (e != cudaSuccess) return cuda_fail(e, "variable pass launch");
-        if (prof) cudaEventRecord(e1, s);
-        e = launch_factor_pass(g->G, g->P, log_pot, g->b, evidence, cur, nxt, T, damping, s);
+        if (prof) cudaEventRecordWithFlags(e1, s, rec_flags);
+        e = lr ? launch_lr_factor_pass(g->G, g->P, log_pot, lam, d, T, damping, s)
+               : launch_factor_pass(g->G, g->P, log_pot, g->b, evidence, cur, nxt, T, damping, s);
         if (e != cudaSuccess) return cuda_fail(e, "factor pass launch");
         if (prof) {
-            cudaEventRecord(e2, s);
-            g->prof_var_launches += g->var_launches;
-            g->prof_factor_launches += g->factor_launches;
+            cudaEventRecordWithFlags(e2, s, rec_flags);
+            if (g->capture_events) {
+                g->capture_nv += g->var_launches;
+                g->capture_nf += g->factor_launches;
+            } else {
+                g->prof_var_launches += g->var_launches;
+                g->prof_factor_launches += g->factor_launches;
+            }
         }
-        std::swap(cur, nxt);
+        if (!lr) std::swap(cur, nxt);
     }
-    if (cur != msgs) {
+    if (lr) {
+        cudaError_t e = launch_lr_unpack(d, E, msgs, s);
+        if (e != cudaSuccess) return cuda_fail(e, "log-ratio unpack launch");
+    } else if (cur != msgs) {
         cudaError_t e = cudaMemcpyAsync(msgs, cur, (size_t)g->info.n_edge_states * sizeof(float),
                                         cudaMemcpyDeviceToDevice, s);
         if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(msgs)");
@@ -522,16 +577,43 @@ static uint32_t float_bits(float x) {
     return u;
 }
 
+// Adds the per-pass times of a cached run's last replay (if not collected yet) to the
+// graph's totals; waits for that replay to finish.
+static pgm_status collect_run_times(pgm_graph *g, pgm_graph::CachedRun &r) {
+    if (!r.pending) return PGM_OK;
+    r.pending = false;
+    for (size_t k = 0; k + 3 <= r.ev.size(); k += 3) {
+        cudaError_t e = cudaEventSynchronize(r.ev[k + 2]);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaEventSynchronize");
+        float a = 0.f, b = 0.f;
+        cudaEventElapsedTime(&a, r.ev[k], r.ev[k + 1]);
+        cudaEventElapsedTime(&b, r.ev[k + 1], r.ev[k + 2]);
+        g->graph_var_ms += a;
+        g->graph_factor_ms += b;
+    }
+    g->prof_var_launches += r.nv;
+    g->prof_factor_launches += r.nf;
+    return PGM_OK;
+}
+
+static void destroy_run(pgm_graph::CachedRun &r) {
+    cudaGraphExecDestroy(r.exec);
+    for (cudaEvent_t e : r.ev) cudaEventDestroy(e);
+    r.ev.clear();
+}
+
 // The cached CUDA graph of a pgm_run_bp call with these arguments, captured on the
 // graph's private stream on first use.
 static pgm_status cached_run(pgm_graph *g, const float *log_pot, const float *evidence, float T,
-                             float damping, int32_t n_iters, float *msgs, cudaGraphExec_t *out) {
+                             float damping, int32_t n_iters, float *msgs, cudaGraphExec_t *out,
+                             pgm_graph::CachedRun **run) {
     const uint32_t tb = float_bits(T), db = float_bits(damping);
     for (auto &r : g->runs)
         if (r.log_pot == log_pot && r.evidence == evidence && r.msgs == msgs && r.T_bits == tb &&
-            r.damping_bits == db && r.n_iters == n_iters) {
+            r.damping_bits == db && r.n_iters == n_iters && r.prof_period == g->profiling) {
             r.last_use = ++g->use_clock;
             *out = r.exec;
+            *run = &r;
             return PGM_OK;
         }
     if (!g->capture_stream) {
@@ -540,32 +622,54 @@ static pgm_status cached_run(pgm_graph *g, const float *log_pot, const float *ev
     }
     cudaError_t e = cudaStreamBeginCapture(g->capture_stream, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamBeginCapture");
-    pgm_status st = enqueue_iterations(g, log_pot, evidence, T, damping, n_iters, msgs, g->capture_stream, false);
+    std::vector<cudaEvent_t> events;
+    g->capture_events = &events;
+    g->capture_nv = g->capture_nf = 0;
+    pgm_status st = enqueue_iterations(g, log_pot, evidence, T, damping, n_iters, msgs, g->capture_stream,
+                                       g->profiling > 0);
+    g->capture_events = nullptr;
     cudaGraph_t graph = nullptr;
     e = cudaStreamEndCapture(g->capture_stream, &graph);
+    auto drop_events = [&]() {
+        for (cudaEvent_t ev : events) cudaEventDestroy(ev);
+    };
     if (st != PGM_OK) {
         if (graph) cudaGraphDestroy(graph);
+        drop_events();
         return st;
     }
+    if (e != cudaSuccess) drop_events();
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
     cudaGraphExec_t exec = nullptr;
     e = cudaGraphInstantiate(&exec, graph, 0);
     cudaGraphDestroy(graph);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+    if (e != cudaSuccess) {
+        drop_events();
+        return cuda_fail(e, "cudaGraphInstantiate");
+    }
     if (g->runs.size() >= 8) {
         size_t lru = 0;
         for (size_t i = 1; i < g->runs.size(); ++i)
             if (g->runs[i].last_use < g->runs[lru].last_use) lru = i;
-        cudaGraphExecDestroy(g->runs[lru].exec);
+        collect_run_times(g, g->runs[lru]);
+        destroy_run(g->runs[lru]);
         g->runs.erase(g->runs.begin() + lru);
     }
-    g->runs.push_back({log_pot, evidence, msgs, tb, db, n_iters, exec, ++g->use_clock});
+    pgm_graph::CachedRun r{log_pot, evidence, msgs, tb, db, n_iters, g->profiling, exec, ++g->use_clock};
+    r.ev = std::move(events);
+    r.nv = g->capture_nv;
+    r.nf = g->capture_nf;
+    g->runs.push_back(std::move(r));
     *out = exec;
+    *run = &g->runs.back();
     return PGM_OK;
 }
 
 static void drop_cached_runs(pgm_graph *g) {
-    for (auto &r : g->runs) cudaGraphExecDestroy(r.exec);
+    for (auto &r : g->runs) {
+        collect_run_times(g, r);
+        destroy_run(r);
+    }
     g->runs.clear();
 }
 
@@ -577,12 +681,16 @@ pgm_status pgm_run_bp(pgm_graph *g, const float *log_pot, const float *evidence,
     DeviceGuard dg(g->device);
     if (!dg.ok) return fail(PGM_ECUDA, "cudaSetDevice failed");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    if (g->use_cuda_graph && g->profiling == 0 && n_iters >= 2) {
+    if (g->use_cuda_graph && n_iters >= 2) {
         cudaGraphExec_t exec = nullptr;
-        st = cached_run(g, log_pot, evidence, T, damping, n_iters, msgs, &exec);
+        pgm_graph::CachedRun *run = nullptr;
+        st = cached_run(g, log_pot, evidence, T, damping, n_iters, msgs, &exec, &run);
+        if (st != PGM_OK) return st;
+        st = collect_run_times(g, *run);  // the previous replay's times, before they are overwritten
         if (st != PGM_OK) return st;
         cudaError_t e = cudaGraphLaunch(exec, s);
         if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
+        run->pending = !run->ev.empty();
         return PGM_OK;
     }
     return enqueue_iterations(g, log_pot, evidence, T, damping, n_iters, msgs, s, true);
@@ -813,6 +921,25 @@ pgm_status pgm_set_option(pgm_graph *g, int32_t option, int64_t value) {
             g->use_cuda_graph = value != 0;
             if (!g->use_cuda_graph) drop_cached_runs(g);
             return PGM_OK;
+        case PGM_OPT_LOG_RATIO:
+            if (value < 0 || value > INT32_MAX) return fail(PGM_EINVAL, "PGM_OPT_LOG_RATIO must be >= 0");
+            if (value != g->log_ratio_min_iters) drop_cached_runs(g);
+            g->log_ratio_min_iters = (int32_t)value;
+            return PGM_OK;
+        default:
+            return fail(PGM_EINVAL, "unknown option");
+    }
+}
+
+pgm_status pgm_get_option(const pgm_graph *g, int32_t option, int64_t *value) {
+    if (!g || !value) return fail(PGM_EINVAL, "NULL argument");
+    switch (option) {
+        case PGM_OPT_CUDA_GRAPH:
+            *value = g->use_cuda_graph != 0;
+            return PGM_OK;
+        case PGM_OPT_LOG_RATIO:
+            *value = g->P.lr ? g->log_ratio_min_iters : 0;
+            return PGM_OK;
         default:
             return fail(PGM_EINVAL, "unknown option");
     }
@@ -902,7 +1029,12 @@ pgm_status pgm_pass_times(pgm_graph *g, double *var_ms, double *factor_ms, int64
                           int64_t *n_factor) {
     if (!g) return fail(PGM_EINVAL, "graph is NULL");
     DeviceGuard dg(g->device);
-    double tv = 0.0, tf = 0.0;
+    for (auto &r : g->runs) {
+        pgm_status st = collect_run_times(g, r);
+        if (st != PGM_OK) return st;
+    }
+    double tv = g->graph_var_ms, tf = g->graph_factor_ms;
+    g->graph_var_ms = g->graph_factor_ms = 0.0;
     for (size_t k = 0; k + 3 <= g->events_used; k += 3) {
         cudaError_t e = cudaEventSynchronize(g->events[k + 2]);
         if (e != cudaSuccess) return cuda_fail(e, "cudaEventSynchronize");

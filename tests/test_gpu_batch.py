@@ -39,6 +39,9 @@ def _mixed_members():
 def _run(binding, graph_or_list, lp, ev, T, n_iters, damping=0.5):
     import torch
     g = binding.Graph(graph_or_list)
+    # the edge-state arithmetic throughout: a binary grid alone would otherwise take the
+    # log-ratio iterations (compared alone vs batched in test_gpu_log_ratio.py)
+    g.set_option(binding.OPT_LOG_RATIO, 0)
     lpt = torch.as_tensor(np.asarray(lp, np.float32)).cuda()
     evt = torch.as_tensor(np.asarray(ev, np.float32)).cuda()
     m = g.new_msgs()
@@ -108,3 +111,31 @@ def test_autotune_and_cuda_graph_do_not_change_results(gpu):
             m = g.new_msgs()
             g.run_bp(lp, ev, 1.0, 0.5, 13, m)
             assert torch.equal(m, ref), (k, rep, before, after)
+
+
+@pytest.mark.parametrize("cuda_graph", [1, 0])
+def test_pass_timing(gpu, cuda_graph):
+    """pgm_set_profiling / pgm_pass_times: every period-th iteration's passes are timed,
+    inside the cached CUDA graph when graphs are on; results are unchanged."""
+    import torch
+    p = W.ising_grid(64, 80, 7)
+    for lr_min in (4, 0):  # log-ratio and edge-state iterations
+        g = gpu.Graph(p.graph)
+        g.set_option(gpu.OPT_CUDA_GRAPH, cuda_graph)
+        g.set_option(gpu.OPT_LOG_RATIO, lr_min)
+        lp = torch.as_tensor(p.log_pot).cuda()
+        ev = torch.as_tensor(p.evidence).cuda()
+        ref = g.new_msgs()
+        g.run_bp(lp, ev, 1.0, 0.5, 30, ref)
+        g.set_profiling(7)
+        for rep in range(3):  # replays of the same cached graph
+            m = g.new_msgs()
+            g.run_bp(lp, ev, 1.0, 0.5, 30, m)
+            assert torch.equal(m, ref)
+        var_ms, fac_ms, n_var, n_fac = g.pass_times()
+        per_call = 30 // 7  # iterations 6, 13, 20, 27
+        assert g.info["launches_per_iter"] == 2  # one variable and one factor launch
+        assert n_var == n_fac == 3 * per_call
+        assert var_ms > 0 and fac_ms > 0
+        assert g.pass_times()[2] == 0  # reset
+        g.set_profiling(0)
