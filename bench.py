@@ -415,9 +415,10 @@ def run_ours(args):
     # roofline of the dominant kernel: algorithmic bytes per launch / mean launch time
     V, VS, E = I["n_vars"], I["n_var_states"], I["n_edges"]
     n_cfg_total = 4 * I["n_factors"]
-    if lr:  # one log-ratio per edge for each message direction
-        fac_bytes = 4 * (2 * E + n_cfg_total + E)  # d read + d write + log-potentials + lam
-        var_bytes = 4 * (E + VS + E + E)           # d + evidence + lam write + incoming-edge index
+    if lr:  # one log-ratio per edge and direction, in variable order (4 slots per variable here)
+        S = 4 * V if I["max_degree"] <= 4 else E
+        fac_bytes = 4 * (E + E + 2 * E + n_cfg_total)  # slot index + lam gather + d read/write + log-potentials
+        var_bytes = 4 * (S + VS + S)                   # d + evidence + lam write (no index)
     else:
         fac_bytes = 4 * (2 * ES + n_cfg_total + E + VS)  # m_old + m_new + log-potentials + edge index + beliefs
         var_bytes = 4 * (ES + 2 * VS + E)               # messages + evidence + beliefs + incoming-edge index

@@ -60,6 +60,8 @@ struct pgm_graph {
     void *scratch_mem = nullptr;  // ping-pong message buffer, belief buffer, status word
     float *m_tmp = nullptr;
     float *b = nullptr;
+    float *lr_d = nullptr, *lr_lam = nullptr;  // Plan::lr: log-ratio arrays (lr_slots each)
+    int64_t lr_slots = 0;
     // pgm_infer_host buffers (allocated on first use)
     void *host_io_mem = nullptr;
     float *io_pot = nullptr, *io_ev = nullptr, *io_msgs = nullptr, *io_bel = nullptr;
@@ -135,6 +137,20 @@ int lanes_per_factor(int variant) {
         default: return 1;
     }
 }
+
+// Log-ratio iterations apply to a binary pairwise graph: every variable binary (edge e's
+// states at 2e), every factor a kPair2 factor, no high-degree variable.
+bool lr_eligible(const HostLayout &H) {
+    bool lr = H.all_binary && H.logic_groups.empty() && !H.enum_groups.empty() && H.ES == 2 * H.E &&
+              H.E % 2 == 0 && H.var_bucket[kVarBlock].empty();
+    for (const HostEnumGroup &hg : H.enum_groups) lr = lr && hg.variant == kPair2;
+    for (int kind = 0; kind < kNumVarKinds; ++kind)
+        if (kind != kVarBinary) lr = lr && H.var_bucket[kind].empty();
+    return lr && (H.vin_tab4.empty() ? H.E : 4 * H.V) <= INT32_MAX;
+}
+
+// Slots of each log-ratio array: 4 per variable with the 4-slot table, else one per edge.
+int64_t lr_slot_count(const HostLayout &H) { return H.vin_tab4.empty() ? H.E : 4 * H.V; }
 
 pgm_status build_plan(const HostLayout &H, pgm_graph *g, Packer &pk, std::vector<size_t> &seg_off,
                       std::vector<int> &seg_kind) {
@@ -238,13 +254,8 @@ pgm_status build_plan(const HostLayout &H, pgm_graph *g, Packer &pk, std::vector
                                              reinterpret_cast<const char *>(segs.data() + segs.size()));
         }
     }
-    // log-ratio iterations: a binary pairwise graph (every edge has 2 states at 2e)
-    bool lr = H.all_binary && H.logic_groups.empty() && !H.enum_groups.empty() && H.ES == 2 * H.E &&
-              H.E % 2 == 0 && H.var_bucket[kVarBlock].empty();
-    for (const HostEnumGroup &hg : H.enum_groups) lr = lr && hg.variant == kPair2;
-    for (int kind = 0; kind < kNumVarKinds; ++kind)
-        if (kind != kVarBinary) lr = lr && H.var_bucket[kind].empty();
-    P.lr = lr;
+    P.lr = lr_eligible(H);
+    P.lr_blocks = std::max(1, g->n_sm * 8);
     return PGM_OK;
 }
 
@@ -326,6 +337,23 @@ static pgm_status build_from_descs(const void *const *descs, int n, pgm_graph **
         delete g;
         return st;
     }
+    // log-ratio layout: slot k V + v of the k-th incoming edge of v (4 slots per
+    // variable), else the edge's CSR index
+    size_t o_lr_pos = 0;
+    if (g->P.lr) {
+        std::vector<int32_t> pos((size_t)H.E, -1);
+        if (!H.vin_tab4.empty()) {
+            for (int64_t v = 0; v < H.V; ++v)
+                for (int k = 0; k < 4; ++k) {
+                    const int32_t es = H.vin_tab4[4 * v + k];
+                    if (es >= 0) pos[es >> 1] = (int32_t)(k * H.V + v);
+                }
+        } else {
+            for (int64_t k = 0; k < H.E; ++k) pos[H.vin_es[k] >> 1] = (int32_t)k;
+        }
+        g->lr_slots = lr_slot_count(H);
+        o_lr_pos = pk.add(pos.data(), pos.size());
+    }
     g->ordered = ordered;
     g->alloc_stream = s;
     char *dmem = nullptr;
@@ -346,9 +374,10 @@ static pgm_status build_from_descs(const void *const *descs, int n, pgm_graph **
     size_t es_bytes = align_up(std::max<int64_t>(H.ES, 1) * sizeof(float), 256);
     size_t vs_bytes = align_up(std::max<int64_t>(H.VS, 1) * sizeof(float), 256);
     size_t hd_bytes = H.var_bucket[kVarBlock].empty() ? 0 : 2 * es_bytes;
+    const size_t lr_bytes = g->P.lr ? align_up((size_t)g->lr_slots * sizeof(float), 256) : 0;
+    const size_t scratch_bytes = es_bytes + vs_bytes + 256 + hd_bytes + 2 * lr_bytes;
     char *smem = nullptr;
-    ce = ordered ? cudaMallocAsync(&smem, es_bytes + vs_bytes + 256 + hd_bytes, s)
-                 : cudaMalloc(&smem, es_bytes + vs_bytes + 256 + hd_bytes);
+    ce = ordered ? cudaMallocAsync(&smem, scratch_bytes, s) : cudaMalloc(&smem, scratch_bytes);
     if (ce != cudaSuccess) {
         if (ordered) cudaFreeAsync(dmem, s);
         else cudaFree(dmem);
@@ -378,6 +407,11 @@ static pgm_status build_from_descs(const void *const *descs, int n, pgm_graph **
     G.vin_tab4 = H.vin_tab4.empty() ? nullptr : reinterpret_cast<const int4 *>(dmem + o_tab4);
     G.flags = flags;
     G.v2f_hd = hd_bytes ? reinterpret_cast<float *>(smem + es_bytes + vs_bytes + 256) : nullptr;
+    G.lr_pos = g->P.lr ? reinterpret_cast<const int32_t *>(dmem + o_lr_pos) : nullptr;
+    if (g->P.lr) {
+        g->lr_d = reinterpret_cast<float *>(smem + es_bytes + vs_bytes + 256 + hd_bytes);
+        g->lr_lam = reinterpret_cast<float *>(smem + es_bytes + vs_bytes + 256 + hd_bytes + lr_bytes);
+    }
     // attach device pointers of the launch lists / segments
     size_t vi = 0, fi = 0;
     int max_smem = 0;
@@ -406,7 +440,7 @@ static pgm_status build_from_descs(const void *const *descs, int n, pgm_graph **
     I.n_potentials = H.P;
     I.max_states = H.max_states;
     I.max_degree = H.max_degree;
-    I.device_bytes = (int64_t)(pk.host.size() + es_bytes + vs_bytes + 256 + hd_bytes);
+    I.device_bytes = (int64_t)(pk.host.size() + scratch_bytes);
     for (const VarLaunch &L : g->P.var) g->var_launches += (L.n > 0);
     for (const FactorLaunch &L : g->P.factor) g->factor_launches += (L.n_blocks > 0);
     I.launches_per_iter = g->var_launches + g->factor_launches;
@@ -478,6 +512,8 @@ pgm_status pgm_check_desc(const pgm_graph_desc *desc, pgm_info *info) {
     size_t idx = (H.vs_off.size() + H.vin_off.size() + H.vin_es.size() + H.edge_vs.size() +
                   H.paroff_pool.size() + nb + H.vin_tab4.size()) * sizeof(int32_t) + H.cfg_pool.size();
     size_t es_bytes = align_up(std::max<int64_t>(H.ES, 1) * sizeof(float), 256);
+    if (lr_eligible(H))  // the slot map and the two log-ratio arrays
+        idx += H.E * sizeof(int32_t) + 2 * align_up((size_t)lr_slot_count(H) * sizeof(float), 256);
     info->device_bytes = (int64_t)(idx + es_bytes + align_up(std::max<int64_t>(H.VS, 1) * sizeof(float), 256) +
                                    256 + (H.var_bucket[kVarBlock].empty() ? 0 : 2 * es_bytes));
     return PGM_OK;
@@ -513,9 +549,9 @@ pgm_status pgm_graph_info(const pgm_graph *g, pgm_info *info) {
 
 // Enqueue n_iters iterations (and the final copy back into msgs) on stream s.
 // On binary pairwise graphs (Plan::lr) runs long enough to repay the two conversions
-// iterate on log-ratios: msgs is packed into d = m_tmp[0, E), the variable pass writes
-// the variable-to-factor values to lam = m_tmp[E, 2E), the factor pass updates d in
-// place, and d is unpacked into msgs at the end.
+// iterate on log-ratios: msgs is packed into lr_d, the variable pass writes the
+// variable-to-factor values to lr_lam, the factor pass updates lr_d in place, and lr_d
+// is unpacked into msgs at the end.
 static bool log_ratio_run(const pgm_graph *g, int32_t n_iters) {
     return g->P.lr && g->log_ratio_min_iters > 0 && n_iters >= g->log_ratio_min_iters;
 }
@@ -525,10 +561,9 @@ static pgm_status enqueue_iterations(pgm_graph *g, const float *log_pot, const f
                                      bool profile) {
     float *cur = msgs, *nxt = g->m_tmp;
     const bool lr = log_ratio_run(g, n_iters);
-    const int32_t E = (int32_t)g->info.n_edges;
-    float *d = g->m_tmp, *lam = g->m_tmp + E;
+    float *d = g->lr_d, *lam = g->lr_lam;
     if (lr) {
-        cudaError_t e = launch_lr_pack(msgs, E, d, s);
+        cudaError_t e = launch_lr_pack(g->G, msgs, d, s);
         if (e != cudaSuccess) return cuda_fail(e, "log-ratio pack launch");
     }
     for (int it = 0; it < n_iters; ++it) {
@@ -561,7 +596,7 @@ static pgm_status enqueue_iterations(pgm_graph *g, const float *log_pot, const f
         if (!lr) std::swap(cur, nxt);
     }
     if (lr) {
-        cudaError_t e = launch_lr_unpack(d, E, msgs, s);
+        cudaError_t e = launch_lr_unpack(g->G, d, msgs, s);
         if (e != cudaSuccess) return cuda_fail(e, "log-ratio unpack launch");
     } else if (cur != msgs) {
         cudaError_t e = cudaMemcpyAsync(msgs, cur, (size_t)g->info.n_edge_states * sizeof(float),

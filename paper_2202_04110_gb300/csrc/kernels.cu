@@ -19,7 +19,7 @@
 // Binary pairwise graphs (every variable binary, every factor a 2 x 2 table) run a
 // log-ratio form of the same iteration: one float per edge for each message direction,
 // the variable pass writing exact leave-one-out variable-to-factor values and the factor
-// pass streaming them in factor order (k_var_tab4_lr / k_var_thread2_lr, k_pair2_lr).
+// pass streaming them in factor order (k_var_slot4_lr / k_var_csr_lr, k_pair2_lr).
 //
 // Numerics: messages and factor arithmetic in FP32. Variable-side sums are compensated
 // (float-float) and the beliefs the factor pass reads are stored relative to each
@@ -27,6 +27,7 @@
 // larger in magnitude than kExactThreshold takes its variable-to-factor values from an
 // explicit leave-one-out sum (v2f_slow_edge) instead of b - m; edges of variables with
 // more than kVarBlockDegree factors always do (computed by the block variable pass).
+#include <algorithm>
 #include <cstdint>
 
 #include <cuda_runtime.h>
@@ -1700,24 +1701,24 @@ __global__ void __launch_bounds__(128) k_adj_var(DevGraph G, const float *__rest
 // exactly 0 and the other <= 0, so d = m(1) - m(0) stores it in one float without loss:
 // m = (-d, 0) for d > 0, else (0, d); both directions are exact (a subtraction from 0, a
 // negation). Iterations on a graph whose variables are all binary and whose factors are
-// all 2 x 2 tables (F factors, E = 2F edges; edge e = 2f + j is slot j of factor f, its
-// states at 2e) keep two arrays of E floats, slot-major (slot 0 of every factor, then
-// slot 1: position lr_pos(e) = (e & 1) F + (e >> 1)):
+// all 2 x 2 tables (F factors, E = 2F edges; edge e = 2g + j is slot j of factor g, its
+// states at 2e) keep two arrays of S floats in variable order:
 //   d    the factor-to-variable messages as log-ratios;
 //   lam  the variable-to-factor values as log-ratios, lam = l(1) - l(0) with
 //        l(x) = e_v(x) + sum over the variable's other edges of m(x), the leave-one-out
 //        sum (no rounded b - m, so no threshold fallback is needed).
-// The variable pass reads d and writes lam; the factor pass streams lam, d and the
-// potentials in factor order (no gather) and updates d in place (a factor owns its two
-// edges). Slot-major storage makes the variable pass's accesses on a grid four
-// coalesced streams (a variable is slot 1 of the factor on its left / above and slot 0
-// of the one on its right / below). A leave-one-out pair that is -inf in both states
+// Position of an edge (G.lr_pos[e]): on graphs whose variables have at most 4 factors,
+// k V + v for the k-th incoming edge of variable v (S = 4V; the unused slots of d stay
+// 0, which adds nothing to a log-ratio sum, and their lam is never read); otherwise the
+// edge's index in the variables' CSR order (S = E). The variable pass streams d and
+// lam in variable order with no index (four coalesced streams on the 4-slot layout); the
+// factor pass streams lr_pos and the potentials in factor order and gathers / scatters
+// lam and d (L2-resident between the passes), updating d in place (an edge's slot
+// belongs to one factor). A leave-one-out pair that is -inf in both states
 // (contradictory evidence) is stored as the NaN pattern kLamBothNegInf; FP32 arithmetic
 // on this GPU returns the canonical NaN 0x7fffffff, never this pattern.
 
 constexpr uint32_t kLamBothNegInf = 0x7fc00001u;
-
-__device__ __forceinline__ int lr_pos(int e, int F) { return (e & 1) * F + (e >> 1); }
 
 __device__ __forceinline__ float2 lr_decode(float d) {
     return d > 0.f ? make_float2(-d, 0.f) : make_float2(0.f, d);
@@ -1749,7 +1750,8 @@ __device__ __forceinline__ FF ff_add_nc(FF a, float v) {
 // linear in the stored log-ratios, with D = (e(1) - e(0)) + sum_j d_j kept float-float
 // (the evidence difference exactly, by TwoSum), so lam_k is exact up to its final
 // rounding. lr_var_slow handles a variable with an infinite evidence entry or message
-// (hard constraints) by the per-state explicit sums l_k(x) instead.
+// (hard constraints) by the per-state explicit sums l_k(x) instead (d = 0 of an unused
+// slot decodes to (0, 0) and adds nothing there either).
 __device__ __noinline__ void lr_var_slow(float2 e, const float *dk, const int *pos, int n, float *lam) {
     for (int k = 0; k < n; ++k) {
         FF l0 = ff_make(e.x), l1 = ff_make(e.y);
@@ -1763,81 +1765,47 @@ __device__ __noinline__ void lr_var_slow(float2 e, const float *dk, const int *p
     }
 }
 
-// The log-ratios of one variable from its evidence e and the gathered messages dk at
-// slot-major positions pos (-1 = none, ascending).
-__device__ __forceinline__ void lr_var_tab4_item(float2 e, const int (&pos)[4], const float (&dk)[4],
-                                                 float *__restrict__ lam) {
-    const int deg = (pos[0] >= 0) + (pos[1] >= 0) + (pos[2] >= 0) + (pos[3] >= 0);
+// Variable pass, at most 4 factors per variable: thread per variable, slot k of variable
+// v at k V + v; four coalesced loads of d and four coalesced stores of lam, no index.
+__global__ void __launch_bounds__(256) k_var_slot4_lr(int V, const float *__restrict__ ev,
+                                                      const float *__restrict__ d, float *__restrict__ lam) {
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= V) return;
+    const float2 e = __ldcs(reinterpret_cast<const float2 *>(ev) + v);
+    float dk[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) dk[k] = __ldcg(d + (size_t)k * V + v);
     bool fin = isfinite(e.x) & isfinite(e.y);
 #pragma unroll
     for (int k = 0; k < 4; ++k) fin &= isfinite(dk[k]);
-    if (!fin) {
-        lr_var_slow(e, dk, pos, deg, lam);
-        return;
-    }
-    FF D = ff_add_nc(ff_make(e.y), -e.x);
+    if (fin) {
+        FF D = ff_add_nc(ff_make(e.y), -e.x);
 #pragma unroll
-    for (int k = 0; k < 4; ++k)
-        if (pos[k] >= 0) D = ff_add_nc(D, dk[k]);
-    float lk[4];
-    bool ok = true;
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        const FF l = ff_add_nc(D, -dk[k]);
-        lk[k] = l.hi + l.lo;
-        ok &= isfinite(lk[k]);
-    }
-    if (!ok) {  // an intermediate overflow (inputs near the FP32 range)
-        lr_var_slow(e, dk, pos, deg, lam);
-        return;
-    }
-#pragma unroll
-    for (int k = 0; k < 4; ++k)
-        if (pos[k] >= 0) lam[pos[k]] = lk[k];
-}
-
-// Variable pass, binary graphs whose variables all have at most 4 factors: one 16-byte
-// row of incoming edge-states per variable (-1 = none, ascending). A block covers
-// blockDim * ILP variables, each thread ILP of them, blockDim apart; all rows, then all
-// message gathers, are issued before the sums.
-template <int ILP>
-__global__ void __launch_bounds__(256) k_var_tab4_lr(DevGraph G, int n, int F, const float *__restrict__ ev,
-                                                     const float *__restrict__ d, float *__restrict__ lam) {
-    const int v0 = blockIdx.x * blockDim.x * ILP + threadIdx.x;
-    int4 t[ILP];
-    float2 e[ILP];
-#pragma unroll
-    for (int i = 0; i < ILP; ++i) {
-        const int v = v0 + i * blockDim.x;
-        if (v < n) {
-            t[i] = __ldcs(G.vin_tab4 + v);
-            e[i] = __ldcs(reinterpret_cast<const float2 *>(ev) + v);
-        } else {
-            t[i] = make_int4(-1, -1, -1, -1);
-            e[i] = make_float2(0.f, 0.f);
-        }
-    }
-    int pos[ILP][4];
-    float dk[ILP][4];
-#pragma unroll
-    for (int i = 0; i < ILP; ++i) {
-        const int es[4] = {t[i].x, t[i].y, t[i].z, t[i].w};
+        for (int k = 0; k < 4; ++k) D = ff_add_nc(D, dk[k]);
+        float lk[4];
+        bool ok = true;
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            pos[i][k] = es[k] >= 0 ? lr_pos(es[k] >> 1, F) : -1;
-            dk[i][k] = pos[i][k] >= 0 ? __ldg(d + pos[i][k]) : 0.f;
+            const FF l = ff_add_nc(D, -dk[k]);
+            lk[k] = l.hi + l.lo;
+            ok &= isfinite(lk[k]);
+        }
+        if (ok) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) lam[(size_t)k * V + v] = lk[k];
+            return;
         }
     }
-#pragma unroll
-    for (int i = 0; i < ILP; ++i)
-        if (v0 + i * (int)blockDim.x < n) lr_var_tab4_item(e[i], pos[i], dk[i], lam);
+    // an infinite entry, or an intermediate overflow (inputs near the FP32 range)
+    const int pos[4] = {v, V + v, 2 * V + v, 3 * V + v};
+    lr_var_slow(e, dk, pos, 4, lam);
 }
 
-// Variable pass, thread per binary variable with at most kVarBlockDegree factors (CSR),
-// same arithmetic: one pass for D, one for the edges.
-__global__ void __launch_bounds__(256) k_var_thread2_lr(DevGraph G, const int32_t *__restrict__ list, int n,
-                                                        int F, const float *__restrict__ ev,
-                                                        const float *__restrict__ d, float *__restrict__ lam) {
+// Variable pass, CSR layout (a variable's edges at vin_off[v] .. vin_off[v + 1] - 1, at
+// most kVarBlockDegree of them): thread per variable, one pass for D, one for the edges.
+__global__ void __launch_bounds__(256) k_var_csr_lr(DevGraph G, const int32_t *__restrict__ list, int n,
+                                                    const float *__restrict__ ev, const float *__restrict__ d,
+                                                    float *__restrict__ lam) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= n) return;
     const int v = list ? __ldg(list + t) : t;
@@ -1846,15 +1814,14 @@ __global__ void __launch_bounds__(256) k_var_thread2_lr(DevGraph G, const int32_
     bool fin = isfinite(e.x) & isfinite(e.y);
     FF D = ff_add(ff_make(e.y), -e.x);
     for (int k = k0; k < k1; ++k) {
-        const float dv = __ldg(d + lr_pos(__ldg(G.vin_es + k) >> 1, F));
+        const float dv = __ldcg(d + k);
         fin &= isfinite(dv);
         D = ff_add(D, dv);
     }
     if (fin) {
         for (int k = k0; k < k1; ++k) {
-            const int p = lr_pos(__ldg(G.vin_es + k) >> 1, F);
-            const FF l = ff_add(D, -__ldg(d + p));
-            lam[p] = l.hi + l.lo;
+            const FF l = ff_add(D, -__ldcg(d + k));
+            lam[k] = l.hi + l.lo;
         }
         return;
     }
@@ -1863,11 +1830,11 @@ __global__ void __launch_bounds__(256) k_var_thread2_lr(DevGraph G, const int32_
         FF l0 = ff_make(e.x), l1 = ff_make(e.y);
         for (int j = k0; j < k1; ++j) {
             if (j == k) continue;
-            const float2 r = lr_decode(__ldg(d + lr_pos(__ldg(G.vin_es + j) >> 1, F)));
+            const float2 r = lr_decode(__ldcg(d + j));
             l0 = ff_add(l0, r.x);
             l1 = ff_add(l1, r.y);
         }
-        lam[lr_pos(__ldg(G.vin_es + k) >> 1, F)] = lam_encode(l0, l1);
+        lam[k] = lam_encode(l0, l1);
     }
 }
 
@@ -1875,19 +1842,26 @@ __global__ void __launch_bounds__(256) k_var_thread2_lr(DevGraph G, const int32_
 //   max + T ln(1 + e^((min - max) / T)) = max + (T ln 2) log2(1 + 2^((min - max) k)),
 // k = log2(e) / T, on the SFU's base-2 exponential and logarithm (flush-to-zero forms;
 // the argument of log2 lies in [1, 2], the result's absolute error is below 3e-7 T).
-__device__ __forceinline__ float lse2_sfu(float a, float b, float k, float Tln2) {
+__device__ __forceinline__ float lse2_fast(float a, float b, float k, float Tln2) {
     const float mx = fmaxf(a, b), mn = fminf(a, b);
-    if (mx == kNegInf) return kNegInf;
     float p, l;
     asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(p) : "f"((mn - mx) * k));
     asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(l) : "f"(1.f + p));
     return fmaf(Tln2, l, mx);
 }
 
+// The same with the -inf case (both values -inf) returning -inf.
 template <bool MAXP>
 __device__ __forceinline__ float lse2_lr(float a, float b, float k, float Tln2) {
     if constexpr (MAXP) return fmaxf(a, b);
-    else return lse2_sfu(a, b, k, Tln2);
+    if (fmaxf(a, b) == kNegInf) return kNegInf;
+    return lse2_fast(a, b, k, Tln2);
+}
+
+template <bool MAXP>
+__device__ __forceinline__ float lse2_fast_t(float a, float b, float k, float Tln2) {
+    if constexpr (MAXP) return fmaxf(a, b);
+    else return lse2_fast(a, b, k, Tln2);
 }
 
 // The normalise-damp-normalise epilogue (finish_k) in log-ratio form: from the factor's
@@ -1927,117 +1901,119 @@ __device__ __noinline__ float2 pair2_lr_exact(const float *phi, float l0, float 
     return make_float2(lr_finish(a0, a1, mo0, damping, flags), lr_finish(c0, c1, mo1, damping, flags));
 }
 
-// The common case without guards. With o, mo the decoded new and stored messages (one
-// entry of each exactly 0), the damped pair t = damping mo + (1 - damping) o has
+// The segment of global factor g (segments in factor order, segment i starting at
+// factor segs[i].edge_base / 2).
+__device__ __forceinline__ int lr_seg_of(const EnumSeg *__restrict__ segs, int n_seg, int g) {
+    int lo = 0, hi = n_seg - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if ((__ldg(&segs[mid].edge_base) >> 1) <= g) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// The table of global factor g: its own 4 entries, or the segment's shared table.
+__device__ __forceinline__ float4 lr_table(const EnumSeg *__restrict__ segs, int n_seg,
+                                           const float *__restrict__ pot, int g) {
+    const EnumSeg *S = segs + lr_seg_of(segs, n_seg, g);
+    const int shared = __ldg(&S->shared);
+    const float *t = pot + __ldg(&S->pot_base) + (shared ? 0 : (size_t)4 * (g - (__ldg(&S->edge_base) >> 1)));
+    if ((reinterpret_cast<uintptr_t>(t) & 15u) == 0)
+        return shared ? __ldg(reinterpret_cast<const float4 *>(t)) : __ldcs(reinterpret_cast<const float4 *>(t));
+    return make_float4(__ldg(t), __ldg(t + 1), __ldg(t + 2), __ldg(t + 3));
+}
+
+// Factor pass, 2 x 2 tables, persistent: thread-stride loop over the global factors
+// g = 0 .. F-1 (edges 2g to its variable 0 and 2g + 1, at slots p = lr_pos[2g],
+// lr_pos[2g + 1] of lam and d; phi(x0, x1) at phi[2 x0 + x1]), software-pipelined: the
+// slots and the table of the next factor are loaded before the current factor's
+// gathers of lam and d and its arithmetic, so the index stream's latency overlaps the
+// gathers'. d is updated in place (a slot belongs to one factor).
+//
+// The common case runs without guards. With o, mo the decoded new and stored messages
+// (one entry of each exactly 0), the damped pair t = damping mo + (1 - damping) o has
 // log-ratio t(1) - t(0) = damping d_old + (1 - damping)(a(1) - a(0)), since
 // min(x, 0) + max(x, 0) = x; the final normalisation does not change it. Every input
 // that needs the guarded arithmetic (an LSE over two -inf values, an infinite stored
 // message, damping 0 against an infinite stored message) makes a result non-finite;
-// the caller tests that and a NaN lam, and then recomputes the factor with
-// pair2_lr_exact.
-__device__ __forceinline__ float lse2_fast(float a, float b, float k, float Tln2) {
-    const float mx = fmaxf(a, b), mn = fminf(a, b);
-    float p, l;
-    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(p) : "f"((mn - mx) * k));
-    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(l) : "f"(1.f + p));
-    return fmaf(Tln2, l, mx);
-}
-
+// that and a NaN lam (the contradiction pattern, which fmaxf / fminf would drop) send
+// the factor to pair2_lr_exact.
 template <bool MAXP>
-__device__ __forceinline__ float lse2_fast_t(float a, float b, float k, float Tln2) {
-    if constexpr (MAXP) return fmaxf(a, b);
-    else return lse2_fast(a, b, k, Tln2);
-}
-
-// Factor pass, 2 x 2 tables; global factor g = edge_base / 2 + f, its slot-0 values at
-// [g] and slot-1 values at [F + g] of lam and d; phi(x0, x1) at phi[2 x0 + x1]. Every
-// access is in factor order; d is updated in place. A block covers blockDim * ILP
-// factors of its segment, each thread ILP of them, blockDim apart, with all their loads
-// issued before any arithmetic (more bytes in flight per warp).
-template <bool MAXP, int ILP>
 __global__ void __launch_bounds__(256) k_pair2_lr(const EnumSeg *__restrict__ segs, int n_seg, int F,
-                                                  const float *__restrict__ pot, const float *__restrict__ lam,
-                                                  float *__restrict__ d, uint32_t *flags, float T, float k,
-                                                  float Tln2, float damping) {
-    __shared__ float tab[4];
-    const EnumSeg *S = segs + find_seg(segs, n_seg, blockIdx.x);
-    const int n_fac = __ldg(&S->n_fac), shared = __ldg(&S->shared), pot_base = __ldg(&S->pot_base);
-    if (shared) {  // uniform over the block (a block lies in one segment)
-        if (threadIdx.x < 4) tab[threadIdx.x] = __ldg(pot + pot_base + threadIdx.x);
-        __syncthreads();
-    }
-    const int f0 = (blockIdx.x - __ldg(&S->block_begin)) * blockDim.x * ILP + threadIdx.x;
-    const int gb = __ldg(&S->edge_base) >> 1;
-    float l0[ILP], l1[ILP], mo0[ILP], mo1[ILP], phi[ILP][4];
-#pragma unroll
-    for (int i = 0; i < ILP; ++i) {
-        const int f = f0 + i * blockDim.x;
-        if (f >= n_fac) continue;
-        const int g = gb + f;
-        l0[i] = __ldcs(lam + g);
-        l1[i] = __ldcs(lam + F + g);
-        mo0[i] = __ldcs(d + g);
-        mo1[i] = __ldcs(d + F + g);
-        if (shared) {
-#pragma unroll
-            for (int j = 0; j < 4; ++j) phi[i][j] = tab[j];
-        } else {
-            load_n_stream<4>(phi[i], pot + pot_base + (size_t)4 * f);
-        }
-    }
+                                                  const int2 *__restrict__ lr_pos2, const float *__restrict__ pot,
+                                                  const float *__restrict__ lam, float *__restrict__ d,
+                                                  uint32_t *flags, float k, float Tln2, float damping) {
+    const int stride = gridDim.x * blockDim.x;
+    int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= F) return;
+    int2 p = __ldcs(lr_pos2 + g);
+    float4 phi = lr_table(segs, n_seg, pot, g);
     const float w = 1.f - damping;
-#pragma unroll
-    for (int i = 0; i < ILP; ++i) {
-        const int f = f0 + i * blockDim.x;
-        if (f >= n_fac) continue;
-        const int g = gb + f;
-        const float2 v0 = lr_decode(l0[i]), v1 = lr_decode(l1[i]);
+    while (true) {
+        const int gn = g + stride;
+        int2 pn = p;
+        float4 phin = phi;
+        if (gn < F) {
+            pn = __ldcs(lr_pos2 + gn);
+            phin = lr_table(segs, n_seg, pot, gn);
+        }
+        const float l0 = __ldcg(lam + p.x), l1 = __ldcg(lam + p.y);
+        const float mo0 = __ldcg(d + p.x), mo1 = __ldcg(d + p.y);
+        const float2 v0 = lr_decode(l0), v1 = lr_decode(l1);
         // to variable 0: a(x0) = LSE over x1 of phi(x0, x1) + v1(x1); to variable 1: c(x1)
-        const float a0 = lse2_fast_t<MAXP>(phi[i][0] + v1.x, phi[i][1] + v1.y, k, Tln2);
-        const float a1 = lse2_fast_t<MAXP>(phi[i][2] + v1.x, phi[i][3] + v1.y, k, Tln2);
-        const float c0 = lse2_fast_t<MAXP>(phi[i][0] + v0.x, phi[i][2] + v0.y, k, Tln2);
-        const float c1 = lse2_fast_t<MAXP>(phi[i][1] + v0.x, phi[i][3] + v0.y, k, Tln2);
-        float2 dn = make_float2(fmaf(damping, mo0[i], w * (a1 - a0)), fmaf(damping, mo1[i], w * (c1 - c0)));
-        // (fmaxf / fminf drop a NaN operand, so a NaN lam -- the contradiction pattern --
-        // is tested directly)
-        if (!(isfinite(dn.x) && isfinite(dn.y) && l0[i] == l0[i] && l1[i] == l1[i]))
-            dn = pair2_lr_exact<MAXP>(phi[i], l0[i], l1[i], mo0[i], mo1[i], k, Tln2, damping, flags);
-        d[g] = dn.x;
-        d[F + g] = dn.y;
+        const float a0 = lse2_fast_t<MAXP>(phi.x + v1.x, phi.y + v1.y, k, Tln2);
+        const float a1 = lse2_fast_t<MAXP>(phi.z + v1.x, phi.w + v1.y, k, Tln2);
+        const float c0 = lse2_fast_t<MAXP>(phi.x + v0.x, phi.z + v0.y, k, Tln2);
+        const float c1 = lse2_fast_t<MAXP>(phi.y + v0.x, phi.w + v0.y, k, Tln2);
+        float2 dn = make_float2(fmaf(damping, mo0, w * (a1 - a0)), fmaf(damping, mo1, w * (c1 - c0)));
+        if (!(isfinite(dn.x) && isfinite(dn.y) && l0 == l0 && l1 == l1)) {
+            const float t4[4] = {phi.x, phi.y, phi.z, phi.w};
+            dn = pair2_lr_exact<MAXP>(t4, l0, l1, mo0, mo1, k, Tln2, damping, flags);
+        }
+        d[p.x] = dn.x;
+        d[p.y] = dn.y;
+        if (gn >= F) break;
+        g = gn;
+        p = pn;
+        phi = phin;
     }
 }
 
-// Pack (d[slot j of factor g] = m(1) - m(0) of edge 2g + j; exact for max-normalised
-// messages, else the normalised message's log-ratio, to which the next update is
-// invariant) and unpack (the edge's two entries = lr_decode of it). Thread per factor.
-template <bool ALIGNED>
-__global__ void __launch_bounds__(256) k_lr_pack(const float *__restrict__ m, int F, float *__restrict__ d) {
-    const int g = blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= F) return;
-    float q[4];
-    if constexpr (ALIGNED) {
-        const float4 v = __ldcs(reinterpret_cast<const float4 *>(m) + g);
-        q[0] = v.x; q[1] = v.y; q[2] = v.z; q[3] = v.w;
-    } else {
+// Pack: the log-ratios of msgs ([2E] edge-state layout) into d in variable order (exact
+// for max-normalised messages, else the normalised message's log-ratio, to which the
+// next update is invariant); unused slots get 0. Unpack: every edge's two entries
+// = lr_decode of its slot.
+__global__ void __launch_bounds__(256) k_lr_pack_slot4(DevGraph G, const float *__restrict__ m,
+                                                       float *__restrict__ d) {
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= G.V) return;
+    const int4 t = __ldg(G.vin_tab4 + v);
+    const int es[4] = {t.x, t.y, t.z, t.w};
 #pragma unroll
-        for (int i = 0; i < 4; ++i) q[i] = __ldcs(m + 4 * (size_t)g + i);
-    }
-    d[g] = lr_encode(q[0], q[1]);
-    d[F + g] = lr_encode(q[2], q[3]);
+    for (int k = 0; k < 4; ++k)
+        d[(size_t)k * G.V + v] = es[k] >= 0 ? lr_encode(__ldg(m + es[k]), __ldg(m + es[k] + 1)) : 0.f;
+}
+
+__global__ void __launch_bounds__(256) k_lr_pack_csr(DevGraph G, const float *__restrict__ m,
+                                                     float *__restrict__ d) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= G.E) return;
+    const int es = __ldg(G.vin_es + k);
+    d[k] = lr_encode(__ldg(m + es), __ldg(m + es + 1));
 }
 
 template <bool ALIGNED>
-__global__ void __launch_bounds__(256) k_lr_unpack(const float *__restrict__ d, int F, float *__restrict__ m) {
-    const int g = blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= F) return;
-    const float2 a = lr_decode(__ldcs(d + g)), b = lr_decode(__ldcs(d + F + g));
+__global__ void __launch_bounds__(256) k_lr_unpack(DevGraph G, const float *__restrict__ d,
+                                                   float *__restrict__ m) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= G.E) return;
+    const float2 q = lr_decode(__ldg(d + __ldg(G.lr_pos + e)));
     if constexpr (ALIGNED) {
-        reinterpret_cast<float4 *>(m)[g] = make_float4(a.x, a.y, b.x, b.y);
+        reinterpret_cast<float2 *>(m)[e] = q;
     } else {
-        m[4 * (size_t)g] = a.x;
-        m[4 * (size_t)g + 1] = a.y;
-        m[4 * (size_t)g + 2] = b.x;
-        m[4 * (size_t)g + 3] = b.y;
+        m[2 * (size_t)e] = q.x;
+        m[2 * (size_t)e + 1] = q.y;
     }
 }
 
@@ -2136,57 +2112,51 @@ static void factor_pass_t(const DevGraph &G, const Plan &P, const float *pot, co
     }
 }
 
-// Items per thread of the log-ratio kernels.
-constexpr int kLrIlp = 2;
-
 cudaError_t launch_lr_var_pass(const DevGraph &G, const Plan &P, const float *ev, const float *d, float *lam,
                                cudaStream_t s) {
-    const int F = G.E / 2;
     if (G.vin_tab4 != nullptr) {
-        k_var_tab4_lr<kLrIlp><<<(G.V + 255) / 256, 256 / kLrIlp, 0, s>>>(G, G.V, F, ev, d, lam);
+        k_var_slot4_lr<<<(G.V + 255) / 256, 256, 0, s>>>(G.V, ev, d, lam);
     } else {
         for (const VarLaunch &L : P.var)
-            if (L.n > 0) k_var_thread2_lr<<<L.n_blocks, L.threads, 0, s>>>(G, L.list, L.n, F, ev, d, lam);
+            if (L.n > 0) k_var_csr_lr<<<L.n_blocks, L.threads, 0, s>>>(G, L.list, L.n, ev, d, lam);
     }
     return cudaGetLastError();
 }
 
 cudaError_t launch_lr_factor_pass(const DevGraph &G, const Plan &P, const float *log_pot, const float *lam,
                                   float *d, float T, float damping, cudaStream_t s) {
-    const int F = G.E / 2;
-    // lse2_sfu constants: k = log2(e) / T, T ln 2
+    // lse2_fast constants: k = log2(e) / T, T ln 2
     const float k = T > 0.f ? (float)(1.4426950408889634 / (double)T) : 0.f;
     const float Tln2 = (float)((double)T * 0.6931471805599453);
-    for (const FactorLaunch &L : P.factor) {
+    const int2 *pos2 = reinterpret_cast<const int2 *>(G.lr_pos);
+    const int F = G.E / 2;
+    for (const FactorLaunch &L : P.factor) {  // the one kPair2 launch: every factor
         if (L.n_blocks == 0) continue;
         const EnumSeg *es = static_cast<const EnumSeg *>(L.segs);
-        // the planner's block ranges hold L.threads factors per block
-        const int threads = L.threads / kLrIlp;
+        // persistent: as many blocks of 256 as are resident at once (8 per SM), or fewer
+        const int blocks = std::min<int>(P.lr_blocks, (F + 255) / 256);
         if (T == 0.f)
-            k_pair2_lr<true, kLrIlp><<<L.n_blocks, threads, 0, s>>>(es, L.n_seg, F, log_pot, lam, d, G.flags, T, k,
-                                                                    Tln2, damping);
+            k_pair2_lr<true><<<blocks, 256, 0, s>>>(es, L.n_seg, F, pos2, log_pot, lam, d, G.flags, k, Tln2,
+                                                    damping);
         else
-            k_pair2_lr<false, kLrIlp><<<L.n_blocks, threads, 0, s>>>(es, L.n_seg, F, log_pot, lam, d, G.flags, T, k,
-                                                                     Tln2, damping);
+            k_pair2_lr<false><<<blocks, 256, 0, s>>>(es, L.n_seg, F, pos2, log_pot, lam, d, G.flags, k, Tln2,
+                                                     damping);
     }
     return cudaGetLastError();
 }
 
-cudaError_t launch_lr_pack(const float *m, int32_t E, float *d, cudaStream_t s) {
-    const int F = E / 2;
-    if (F <= 0) return cudaSuccess;
-    const int blocks = (F + 255) / 256;
-    if ((reinterpret_cast<uintptr_t>(m) & 15u) == 0) k_lr_pack<true><<<blocks, 256, 0, s>>>(m, F, d);
-    else k_lr_pack<false><<<blocks, 256, 0, s>>>(m, F, d);
+cudaError_t launch_lr_pack(const DevGraph &G, const float *m, float *d, cudaStream_t s) {
+    if (G.E <= 0) return cudaSuccess;
+    if (G.vin_tab4 != nullptr) k_lr_pack_slot4<<<(G.V + 255) / 256, 256, 0, s>>>(G, m, d);
+    else k_lr_pack_csr<<<(G.E + 255) / 256, 256, 0, s>>>(G, m, d);
     return cudaGetLastError();
 }
 
-cudaError_t launch_lr_unpack(const float *d, int32_t E, float *m, cudaStream_t s) {
-    const int F = E / 2;
-    if (F <= 0) return cudaSuccess;
-    const int blocks = (F + 255) / 256;
-    if ((reinterpret_cast<uintptr_t>(m) & 15u) == 0) k_lr_unpack<true><<<blocks, 256, 0, s>>>(d, F, m);
-    else k_lr_unpack<false><<<blocks, 256, 0, s>>>(d, F, m);
+cudaError_t launch_lr_unpack(const DevGraph &G, const float *d, float *m, cudaStream_t s) {
+    if (G.E <= 0) return cudaSuccess;
+    const int blocks = (G.E + 255) / 256;
+    if ((reinterpret_cast<uintptr_t>(m) & 7u) == 0) k_lr_unpack<true><<<blocks, 256, 0, s>>>(G, d, m);
+    else k_lr_unpack<false><<<blocks, 256, 0, s>>>(G, d, m);
     return cudaGetLastError();
 }
 

@@ -86,6 +86,8 @@ struct DevGraph {
     float *v2f_hd;           // [2 * ES] exact leave-one-out sums, float-float (hi, lo)
                              // pairs, for edges of high-degree variables (edge_vs = -1);
                              // null if there are none
+    const int32_t *lr_pos;   // [E] Plan::lr graphs: each edge's slot in the log-ratio
+                             // arrays (k V + v with vin_tab4, else its CSR index); else null
 };
 
 struct FactorLaunch {
@@ -126,6 +128,7 @@ struct Plan {
     // Binary pairwise graph (every variable binary, every factor a kPair2 factor, no
     // high-degree variable): iterations may keep one log-ratio per edge.
     bool lr = false;
+    int32_t lr_blocks = 1;  // persistent log-ratio factor pass: blocks of 256 (8 per SM)
 };
 
 // Host-side result of the graph compiler (compile.cpp).
@@ -170,17 +173,17 @@ cudaError_t launch_var_pass(const DevGraph &G, const Plan &P, const float *ev, c
 cudaError_t launch_factor_pass(const DevGraph &G, const Plan &P, const float *log_pot,
                                const float *b, const float *ev, const float *m_old,
                                float *m_new, float T, float damping, cudaStream_t s);
-// Log-ratio iteration of a Plan::lr graph (kernels.cu): d[E] the factor-to-variable
-// messages, lam[E] the variable-to-factor values, both one log-ratio per edge, stored
-// slot-major (slot 0 of every factor, then slot 1); the factor pass updates d in place.
+// Log-ratio iteration of a Plan::lr graph (kernels.cu): d the factor-to-variable
+// messages, lam the variable-to-factor values, one log-ratio per edge in variable order
+// (slots DevGraph::lr_pos; 4V of them with vin_tab4, else E); the factor pass updates d
+// in place.
 cudaError_t launch_lr_var_pass(const DevGraph &G, const Plan &P, const float *ev, const float *d, float *lam,
                                cudaStream_t s);
 cudaError_t launch_lr_factor_pass(const DevGraph &G, const Plan &P, const float *log_pot, const float *lam,
                                   float *d, float T, float damping, cudaStream_t s);
-// Log-ratio pack (from the [2E] edge-state layout) and unpack of a binary pairwise
-// graph's E = 2F edges.
-cudaError_t launch_lr_pack(const float *m, int32_t E, float *d, cudaStream_t s);
-cudaError_t launch_lr_unpack(const float *d, int32_t E, float *m, cudaStream_t s);
+// Log-ratio pack (from the [2E] edge-state layout; unused slots 0) and unpack.
+cudaError_t launch_lr_pack(const DevGraph &G, const float *m, float *d, cudaStream_t s);
+cudaError_t launch_lr_unpack(const DevGraph &G, const float *d, float *m, cudaStream_t s);
 // Adjoint launchers (kernels.cu).
 cudaError_t launch_adj_beliefs(const DevGraph &G, const float *ev, const float *m, const float *gnb, float *d_ev,
                                float *adj, cudaStream_t s);
