@@ -432,18 +432,27 @@ def run_ours(args):
     run_ms = [a.elapsed_time(b) for a, b in run_events]
     iter_run_s = statistics.mean(run_ms) / 1e3 / args.iters  # includes the run's pack / unpack
     iter_s = (var_ms + fac_ms) / 1e3 / max(n_fac, 1)
-    dominant = "k_pair2" if fac_ms >= var_ms else "variable_pass"
+    if lr:
+        fac_name, var_name = "k_pair2_lr", ("k_var_slot4_lr" if I["max_degree"] <= 4 else "k_var_csr_lr")
+    else:
+        fac_name, var_name = "k_pair2", "variable_pass"
+    fac_dom = fac_ms >= var_ms
+    dominant, other = (fac_name, var_name) if fac_dom else (var_name, fac_name)
+    dom_gbs, oth_gbs = (fac_gbs, var_gbs) if fac_dom else (var_gbs, fac_gbs)
+    dom_bytes, oth_bytes = (fac_bytes, var_bytes) if fac_dom else (var_bytes, fac_bytes)
+    dom_s, oth_s = (fac_avg_s, var_avg_s) if fac_dom else (var_avg_s, fac_avg_s)
     roof = {"bound": "hbm", "kernel": dominant,
-            "achieved": round(fac_gbs if dominant == "k_pair2" else var_gbs, 1),
+            "achieved": round(dom_gbs, 1),
             "peak": peak, "unit": "GB/s", "peak_source": f"{peak_src} HBM copy bandwidth",
-            "frac": round((fac_gbs if dominant == "k_pair2" else var_gbs) / peak, 4),
+            "frac": round(dom_gbs / peak, 4),
             "traffic": profiled_traffic(dominant, wl),
-            "algorithmic_bytes_per_launch": fac_bytes if dominant == "k_pair2" else var_bytes,
-            "mean_launch_us": round(1e6 * (fac_avg_s if dominant == "k_pair2" else var_avg_s), 2),
+            "algorithmic_bytes_per_launch": dom_bytes,
+            "mean_launch_us": round(1e6 * dom_s, 2),
             "other_kernels": {
-                "variable_pass": {"achieved": round(var_gbs, 1), "frac": round(var_gbs / peak, 4),
-                                  "algorithmic_bytes_per_launch": var_bytes,
-                                  "mean_launch_us": round(1e6 * var_avg_s, 2)}},
+                other: {"achieved": round(oth_gbs, 1), "frac": round(oth_gbs / peak, 4),
+                        "algorithmic_bytes_per_launch": oth_bytes,
+                        "mean_launch_us": round(1e6 * oth_s, 2),
+                        "traffic": profiled_traffic(other, wl)}},
             "kernel_timing": "CUDA events on the launching stream around the passes of every "
                              f"{min(PROFILE_PERIOD, args.iters)}th iteration of the timed runs (event nodes in their CUDA graphs)",
             "iteration": {"algorithmic_bytes": iter_bytes,
