@@ -18,6 +18,7 @@ the host cores on a bounded sample of the same workload.
 from __future__ import annotations
 
 import argparse
+import datetime
 import hashlib
 import json
 import os
@@ -40,7 +41,7 @@ PROFILE_PERIOD = 100  # per-pass CUDA events (graph event nodes) on every 100th 
 def parse_args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--side", type=int, default=1000)
@@ -109,21 +110,28 @@ def profiled_traffic(kernel: str, workload: str):
 class ClockSampler:
     """nvidia-smi samples during the timed region."""
 
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, gpu_index: int):
         self.gpu = gpu_index
         self.proc = None
+        self.window = None
 
     def start(self):
+        """Start sampling (every 20 ms); call before the warm-up so that sampling runs
+        when the timed region begins."""
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "20"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.proc = None
+
+    def mark(self, t0: float, t1: float):
+        """The timed region in host wall-clock seconds (time.time())."""
+        self.window = (t0, t1)
 
     def stop(self):
         if self.proc is None:
@@ -134,24 +142,24 @@ class ClockSampler:
         except subprocess.TimeoutExpired:
             self.proc.kill()
             out, _ = self.proc.communicate()
-        sm, mx, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        rows = []
         for line in out.strip().splitlines():
             parts = [p.strip() for p in line.split(",")]
-            if len(parts) < 9:
+            if len(parts) < 10:
                 continue
             try:
-                sm.append(float(parts[1]))
-                mx.append(float(parts[2]))
+                ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                rows.append((ts, float(parts[2]), float(parts[3]), parts[6:10]))
             except ValueError:
                 continue
-            for nm, val in zip(names, parts[5:9]):
-                if val.lower().startswith("active"):
-                    reasons.add(nm)
-        if not sm:
+        inside = [r for r in rows if self.window and self.window[0] <= r[0] <= self.window[1]]
+        used, where = (inside, "timed region") if inside else (rows, "whole run (no sample fell in the timed region)")
+        if not used:
             return None
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
-                "samples": len(sm)}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({nm for r in used for nm, val in zip(names, r[3]) if val.lower().startswith("active")})
+        return {"sm_mhz": statistics.median(r[1] for r in used), "sm_max_mhz": max(r[2] for r in used),
+                "reasons": reasons, "samples": len(used), "window": where}
 
 
 def aggregate_ranks(dist, local_ms: float, updates_per_rank: float, device=None):
@@ -373,6 +381,9 @@ def run_ours(args):
             g.beliefs(ev, msgs, True, out=bel)
             g.decode(ev, msgs, out=dec)
 
+    # clocks: nvidia-smi samples from before the warm-up on, kept inside the timed window
+    sampler = ClockSampler(torch.cuda.current_device())
+    sampler.start()
     # per-pass timing inside the timed runs: the captured CUDA graphs record events
     # around the variable and factor passes of every PROFILE_PERIOD-th iteration
     g.set_profiling(min(PROFILE_PERIOD, args.iters))
@@ -388,11 +399,10 @@ def run_ours(args):
     lr = lr_min > 0 and args.iters >= lr_min
     launches_per_step = len(temps) * (args.iters * I["launches_per_iter"] + 2 + (2 if lr else 0))
 
-    sampler = ClockSampler(torch.cuda.current_device())
     if dist is not None:
         dist.barrier()
     torch.cuda.synchronize()
-    sampler.start()
+    t_start = time.time()
     step_ms = []
     for _ in range(args.steps):
         flush.fill_(1.0)
@@ -403,6 +413,7 @@ def run_ours(args):
         e1.record(stream)
         step_ms.append((e0, e1))
     torch.cuda.synchronize()
+    sampler.mark(t_start, time.time())
     if dist is not None:
         dist.barrier()
     clocks = sampler.stop()
