@@ -561,7 +561,10 @@ static pgm_status enqueue_iterations(pgm_graph *g, const float *log_pot, const f
                                      bool profile) {
     float *cur = msgs, *nxt = g->m_tmp;
     const bool lr = log_ratio_run(g, n_iters);
+    // per-variable totals of the 4-slot layout in the belief buffer (VS = 2V floats on a
+    // binary graph), which log-ratio iterations do not otherwise use
     float *d = g->lr_d, *lam = g->lr_lam;
+    float2 *Dv = reinterpret_cast<float2 *>(g->b);
     if (lr) {
         cudaError_t e = launch_lr_pack(g->G, msgs, d, s);
         if (e != cudaSuccess) return cuda_fail(e, "log-ratio pack launch");
@@ -576,11 +579,11 @@ static pgm_status enqueue_iterations(pgm_graph *g, const float *log_pot, const f
             if (ps != PGM_OK) return ps;
             cudaEventRecordWithFlags(e0, s, rec_flags);
         }
-        cudaError_t e = lr ? launch_lr_var_pass(g->G, g->P, evidence, d, lam, s)
+        cudaError_t e = lr ? launch_lr_var_pass(g->G, g->P, evidence, d, Dv, lam, s)
                            : launch_var_pass(g->G, g->P, evidence, cur, g->b, kVarIter, nullptr, s);
         if (e != cudaSuccess) return cuda_fail(e, "variable pass launch");
         if (prof) cudaEventRecordWithFlags(e1, s, rec_flags);
-        e = lr ? launch_lr_factor_pass(g->G, g->P, log_pot, lam, d, T, damping, s)
+        e = lr ? launch_lr_factor_pass(g->G, g->P, log_pot, Dv, lam, d, T, damping, s)
                : launch_factor_pass(g->G, g->P, log_pot, g->b, evidence, cur, nxt, T, damping, s);
         if (e != cudaSuccess) return cuda_fail(e, "factor pass launch");
         if (prof) {

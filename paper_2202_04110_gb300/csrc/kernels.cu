@@ -1766,9 +1766,23 @@ __device__ __noinline__ void lr_var_slow(float2 e, const float *dk, const int *p
 }
 
 // Variable pass, at most 4 factors per variable: thread per variable, slot k of variable
-// v at k V + v; four coalesced loads of d and four coalesced stores of lam, no index.
+// v at k V + v; four coalesced loads of d and one store per variable, no index. It
+// writes the float-float total D = (e(1) - e(0)) + sum_k d_k (Dv[v] = (hi, lo)); the
+// factor pass forms each edge's lam = D - d_k itself, with the same arithmetic (it
+// reads d_k for the damping anyway), which halves the bytes this pass writes. A
+// variable whose lam would not come out finite this way (an infinite evidence entry or
+// message; an overflow) gets its four lam by the per-state explicit sums in lam, and
+// the pattern kDvSlow in Dv[v].x so that the factor pass reads them there.
+constexpr uint32_t kDvSlow = 0x7fc00002u;
+
+__device__ __forceinline__ float lr_lam_from_D(float2 D, float dk) {
+    const FF l = ff_add_nc(FF{D.x, D.y}, -dk);
+    return l.hi + l.lo;
+}
+
 __global__ void __launch_bounds__(256) k_var_slot4_lr(int V, const float *__restrict__ ev,
-                                                      const float *__restrict__ d, float *__restrict__ lam) {
+                                                      const float *__restrict__ d, float2 *__restrict__ Dv,
+                                                      float *__restrict__ lam) {
     const int v = blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= V) return;
     const float2 e = __ldcs(reinterpret_cast<const float2 *>(ev) + v);
@@ -1782,23 +1796,19 @@ __global__ void __launch_bounds__(256) k_var_slot4_lr(int V, const float *__rest
         FF D = ff_add_nc(ff_make(e.y), -e.x);
 #pragma unroll
         for (int k = 0; k < 4; ++k) D = ff_add_nc(D, dk[k]);
-        float lk[4];
+        const float2 Df = make_float2(D.hi, D.lo);
         bool ok = true;
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const FF l = ff_add_nc(D, -dk[k]);
-            lk[k] = l.hi + l.lo;
-            ok &= isfinite(lk[k]);
-        }
+        for (int k = 0; k < 4; ++k) ok &= isfinite(lr_lam_from_D(Df, dk[k]));
         if (ok) {
-#pragma unroll
-            for (int k = 0; k < 4; ++k) lam[(size_t)k * V + v] = lk[k];
+            Dv[v] = Df;
             return;
         }
     }
     // an infinite entry, or an intermediate overflow (inputs near the FP32 range)
     const int pos[4] = {v, V + v, 2 * V + v, 3 * V + v};
     lr_var_slow(e, dk, pos, 4, lam);
+    Dv[v] = make_float2(__uint_as_float(kDvSlow), 0.f);
 }
 
 // Variable pass, CSR layout (a variable's edges at vin_off[v] .. vin_off[v + 1] - 1, at
@@ -1926,7 +1936,8 @@ __device__ __forceinline__ float4 lr_table(const EnumSeg *__restrict__ segs, int
 
 // Factor pass, 2 x 2 tables, persistent: thread-stride loop over the global factors
 // g = 0 .. F-1 (edges 2g to its variable 0 and 2g + 1, at slots p = lr_pos[2g],
-// lr_pos[2g + 1] of lam and d; phi(x0, x1) at phi[2 x0 + x1]), software-pipelined: the
+// lr_pos[2g + 1] of lam and d; phi(x0, x1) at phi[2 x0 + x1]; FROM_D: the 4-slot layout,
+// lam formed from the variable's total Dv and d as in k_var_slot4_lr), software-pipelined: the
 // slots and the table of the next factor are loaded before the current factor's
 // gathers of lam and d and its arithmetic, so the index stream's latency overlaps the
 // gathers'. d is updated in place (a slot belongs to one factor).
@@ -1939,11 +1950,12 @@ __device__ __forceinline__ float4 lr_table(const EnumSeg *__restrict__ segs, int
 // message, damping 0 against an infinite stored message) makes a result non-finite;
 // that and a NaN lam (the contradiction pattern, which fmaxf / fminf would drop) send
 // the factor to pair2_lr_exact.
-template <bool MAXP>
-__global__ void __launch_bounds__(256) k_pair2_lr(const EnumSeg *__restrict__ segs, int n_seg, int F,
+template <bool MAXP, bool FROM_D>
+__global__ void __launch_bounds__(256) k_pair2_lr(const EnumSeg *__restrict__ segs, int n_seg, int F, int V,
                                                   const int2 *__restrict__ lr_pos2, const float *__restrict__ pot,
-                                                  const float *__restrict__ lam, float *__restrict__ d,
-                                                  uint32_t *flags, float k, float Tln2, float damping) {
+                                                  const float2 *__restrict__ Dv, const float *__restrict__ lam,
+                                                  float *__restrict__ d, uint32_t *flags, float k, float Tln2,
+                                                  float damping) {
     const int stride = gridDim.x * blockDim.x;
     int g = blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= F) return;
@@ -1958,8 +1970,19 @@ __global__ void __launch_bounds__(256) k_pair2_lr(const EnumSeg *__restrict__ se
             pn = __ldcs(lr_pos2 + gn);
             phin = lr_table(segs, n_seg, pot, gn);
         }
-        const float l0 = __ldcg(lam + p.x), l1 = __ldcg(lam + p.y);
         const float mo0 = __ldcg(d + p.x), mo1 = __ldcg(d + p.y);
+        float l0, l1;
+        if constexpr (FROM_D) {
+            // the slots' variables: slot k V + v, k = 0..3
+            const int v0 = p.x - V * ((p.x >= V) + (p.x >= 2 * V) + (p.x >= 3 * V));
+            const int v1 = p.y - V * ((p.y >= V) + (p.y >= 2 * V) + (p.y >= 3 * V));
+            const float2 D0 = __ldcg(Dv + v0), D1 = __ldcg(Dv + v1);
+            l0 = __float_as_uint(D0.x) == kDvSlow ? __ldcg(lam + p.x) : lr_lam_from_D(D0, mo0);
+            l1 = __float_as_uint(D1.x) == kDvSlow ? __ldcg(lam + p.y) : lr_lam_from_D(D1, mo1);
+        } else {
+            l0 = __ldcg(lam + p.x);
+            l1 = __ldcg(lam + p.y);
+        }
         const float2 v0 = lr_decode(l0), v1 = lr_decode(l1);
         // to variable 0: a(x0) = LSE over x1 of phi(x0, x1) + v1(x1); to variable 1: c(x1)
         const float a0 = lse2_fast_t<MAXP>(phi.x + v1.x, phi.y + v1.y, k, Tln2);
@@ -2112,10 +2135,10 @@ static void factor_pass_t(const DevGraph &G, const Plan &P, const float *pot, co
     }
 }
 
-cudaError_t launch_lr_var_pass(const DevGraph &G, const Plan &P, const float *ev, const float *d, float *lam,
-                               cudaStream_t s) {
+cudaError_t launch_lr_var_pass(const DevGraph &G, const Plan &P, const float *ev, const float *d, float2 *Dv,
+                               float *lam, cudaStream_t s) {
     if (G.vin_tab4 != nullptr) {
-        k_var_slot4_lr<<<(G.V + 255) / 256, 256, 0, s>>>(G.V, ev, d, lam);
+        k_var_slot4_lr<<<(G.V + 255) / 256, 256, 0, s>>>(G.V, ev, d, Dv, lam);
     } else {
         for (const VarLaunch &L : P.var)
             if (L.n > 0) k_var_csr_lr<<<L.n_blocks, L.threads, 0, s>>>(G, L.list, L.n, ev, d, lam);
@@ -2123,8 +2146,8 @@ cudaError_t launch_lr_var_pass(const DevGraph &G, const Plan &P, const float *ev
     return cudaGetLastError();
 }
 
-cudaError_t launch_lr_factor_pass(const DevGraph &G, const Plan &P, const float *log_pot, const float *lam,
-                                  float *d, float T, float damping, cudaStream_t s) {
+cudaError_t launch_lr_factor_pass(const DevGraph &G, const Plan &P, const float *log_pot, const float2 *Dv,
+                                  const float *lam, float *d, float T, float damping, cudaStream_t s) {
     // lse2_fast constants: k = log2(e) / T, T ln 2
     const float k = T > 0.f ? (float)(1.4426950408889634 / (double)T) : 0.f;
     const float Tln2 = (float)((double)T * 0.6931471805599453);
@@ -2135,12 +2158,22 @@ cudaError_t launch_lr_factor_pass(const DevGraph &G, const Plan &P, const float 
         const EnumSeg *es = static_cast<const EnumSeg *>(L.segs);
         // persistent: as many blocks of 256 as are resident at once (8 per SM), or fewer
         const int blocks = std::min<int>(P.lr_blocks, (F + 255) / 256);
-        if (T == 0.f)
-            k_pair2_lr<true><<<blocks, 256, 0, s>>>(es, L.n_seg, F, pos2, log_pot, lam, d, G.flags, k, Tln2,
-                                                    damping);
-        else
-            k_pair2_lr<false><<<blocks, 256, 0, s>>>(es, L.n_seg, F, pos2, log_pot, lam, d, G.flags, k, Tln2,
-                                                     damping);
+        const bool from_d = G.vin_tab4 != nullptr;
+        if (T == 0.f) {
+            if (from_d)
+                k_pair2_lr<true, true><<<blocks, 256, 0, s>>>(es, L.n_seg, F, G.V, pos2, log_pot, Dv, lam, d, G.flags,
+                                                              k, Tln2, damping);
+            else
+                k_pair2_lr<true, false><<<blocks, 256, 0, s>>>(es, L.n_seg, F, G.V, pos2, log_pot, Dv, lam, d,
+                                                               G.flags, k, Tln2, damping);
+        } else {
+            if (from_d)
+                k_pair2_lr<false, true><<<blocks, 256, 0, s>>>(es, L.n_seg, F, G.V, pos2, log_pot, Dv, lam, d,
+                                                               G.flags, k, Tln2, damping);
+            else
+                k_pair2_lr<false, false><<<blocks, 256, 0, s>>>(es, L.n_seg, F, G.V, pos2, log_pot, Dv, lam, d,
+                                                                G.flags, k, Tln2, damping);
+        }
     }
     return cudaGetLastError();
 }

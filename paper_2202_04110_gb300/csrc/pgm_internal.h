@@ -177,10 +177,13 @@ cudaError_t launch_factor_pass(const DevGraph &G, const Plan &P, const float *lo
 // messages, lam the variable-to-factor values, one log-ratio per edge in variable order
 // (slots DevGraph::lr_pos; 4V of them with vin_tab4, else E); the factor pass updates d
 // in place.
-cudaError_t launch_lr_var_pass(const DevGraph &G, const Plan &P, const float *ev, const float *d, float *lam,
-                               cudaStream_t s);
-cudaError_t launch_lr_factor_pass(const DevGraph &G, const Plan &P, const float *log_pot, const float *lam,
-                                  float *d, float T, float damping, cudaStream_t s);
+// On the 4-slot layout (vin_tab4) the variable pass writes each variable's float-float
+// total Dv[V] (lam only for variables that need the explicit sums) and the factor pass
+// forms lam from it; otherwise lam is written and read.
+cudaError_t launch_lr_var_pass(const DevGraph &G, const Plan &P, const float *ev, const float *d, float2 *Dv,
+                               float *lam, cudaStream_t s);
+cudaError_t launch_lr_factor_pass(const DevGraph &G, const Plan &P, const float *log_pot, const float2 *Dv,
+                                  const float *lam, float *d, float T, float damping, cudaStream_t s);
 // Log-ratio pack (from the [2E] edge-state layout; unused slots 0) and unpack.
 cudaError_t launch_lr_pack(const DevGraph &G, const float *m, float *d, cudaStream_t s);
 cudaError_t launch_lr_unpack(const DevGraph &G, const float *d, float *m, cudaStream_t s);
