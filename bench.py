@@ -426,13 +426,14 @@ def run_ours(args):
     # roofline of the dominant kernel: algorithmic bytes per launch / mean launch time
     V, VS, E = I["n_vars"], I["n_var_states"], I["n_edges"]
     n_cfg_total = 4 * I["n_factors"]
+    F = I["n_factors"]
     if lr and I["max_degree"] <= 4:  # log-ratios in 4 slots per variable; per-variable totals Dv
         S = 4 * V
-        fac_bytes = 4 * (E + 2 * E + n_cfg_total) + 8 * V  # slot index + d read/write + log-potentials + Dv
-        var_bytes = 4 * (S + VS) + 8 * V                   # d + evidence + Dv write (no index)
+        fac_bytes = 4 * (E + 2 * E + 3 * F) + 8 * V  # slot index + d read/write + table differences + Dv
+        var_bytes = 4 * (S + VS) + 8 * V             # d + evidence + Dv write (no index)
     elif lr:  # log-ratios in CSR order
-        fac_bytes = 4 * (E + E + 2 * E + n_cfg_total)  # slot index + lam gather + d read/write + log-potentials
-        var_bytes = 4 * (E + VS + E)                   # d + evidence + lam write
+        fac_bytes = 4 * (E + E + 2 * E + 3 * F)  # slot index + lam gather + d read/write + table differences
+        var_bytes = 4 * (E + VS + E)             # d + evidence + lam write
     else:
         fac_bytes = 4 * (2 * ES + n_cfg_total + E + VS)  # m_old + m_new + log-potentials + edge index + beliefs
         var_bytes = 4 * (ES + 2 * VS + E)               # messages + evidence + beliefs + incoming-edge index

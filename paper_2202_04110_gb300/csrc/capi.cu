@@ -61,6 +61,7 @@ struct pgm_graph {
     float *m_tmp = nullptr;
     float *b = nullptr;
     float *lr_d = nullptr, *lr_lam = nullptr;  // Plan::lr: log-ratio arrays (lr_slots each)
+    float *lr_prm = nullptr;                    // Plan::lr: table differences [3F] (per run)
     int64_t lr_slots = 0;
     // pgm_infer_host buffers (allocated on first use)
     void *host_io_mem = nullptr;
@@ -375,7 +376,8 @@ static pgm_status build_from_descs(const void *const *descs, int n, pgm_graph **
     size_t vs_bytes = align_up(std::max<int64_t>(H.VS, 1) * sizeof(float), 256);
     size_t hd_bytes = H.var_bucket[kVarBlock].empty() ? 0 : 2 * es_bytes;
     const size_t lr_bytes = g->P.lr ? align_up((size_t)g->lr_slots * sizeof(float), 256) : 0;
-    const size_t scratch_bytes = es_bytes + vs_bytes + 256 + hd_bytes + 2 * lr_bytes;
+    const size_t prm_bytes = g->P.lr ? align_up((size_t)3 * (H.E / 2) * sizeof(float), 256) : 0;
+    const size_t scratch_bytes = es_bytes + vs_bytes + 256 + hd_bytes + 2 * lr_bytes + prm_bytes;
     char *smem = nullptr;
     ce = ordered ? cudaMallocAsync(&smem, scratch_bytes, s) : cudaMalloc(&smem, scratch_bytes);
     if (ce != cudaSuccess) {
@@ -411,6 +413,7 @@ static pgm_status build_from_descs(const void *const *descs, int n, pgm_graph **
     if (g->P.lr) {
         g->lr_d = reinterpret_cast<float *>(smem + es_bytes + vs_bytes + 256 + hd_bytes);
         g->lr_lam = reinterpret_cast<float *>(smem + es_bytes + vs_bytes + 256 + hd_bytes + lr_bytes);
+        g->lr_prm = reinterpret_cast<float *>(smem + es_bytes + vs_bytes + 256 + hd_bytes + 2 * lr_bytes);
     }
     // attach device pointers of the launch lists / segments
     size_t vi = 0, fi = 0;
@@ -512,8 +515,9 @@ pgm_status pgm_check_desc(const pgm_graph_desc *desc, pgm_info *info) {
     size_t idx = (H.vs_off.size() + H.vin_off.size() + H.vin_es.size() + H.edge_vs.size() +
                   H.paroff_pool.size() + nb + H.vin_tab4.size()) * sizeof(int32_t) + H.cfg_pool.size();
     size_t es_bytes = align_up(std::max<int64_t>(H.ES, 1) * sizeof(float), 256);
-    if (lr_eligible(H))  // the slot map and the two log-ratio arrays
-        idx += H.E * sizeof(int32_t) + 2 * align_up((size_t)lr_slot_count(H) * sizeof(float), 256);
+    if (lr_eligible(H))  // the slot map, the two log-ratio arrays and the table differences
+        idx += H.E * sizeof(int32_t) + 2 * align_up((size_t)lr_slot_count(H) * sizeof(float), 256) +
+               align_up((size_t)3 * (H.E / 2) * sizeof(float), 256);
     info->device_bytes = (int64_t)(idx + es_bytes + align_up(std::max<int64_t>(H.VS, 1) * sizeof(float), 256) +
                                    256 + (H.var_bucket[kVarBlock].empty() ? 0 : 2 * es_bytes));
     return PGM_OK;
@@ -567,6 +571,7 @@ static pgm_status enqueue_iterations(pgm_graph *g, const float *log_pot, const f
     float2 *Dv = reinterpret_cast<float2 *>(g->b);
     if (lr) {
         cudaError_t e = launch_lr_pack(g->G, msgs, d, s);
+        if (e == cudaSuccess) e = launch_lr_params(g->G, g->P, log_pot, g->lr_prm, s);
         if (e != cudaSuccess) return cuda_fail(e, "log-ratio pack launch");
     }
     for (int it = 0; it < n_iters; ++it) {
@@ -583,7 +588,7 @@ static pgm_status enqueue_iterations(pgm_graph *g, const float *log_pot, const f
                            : launch_var_pass(g->G, g->P, evidence, cur, g->b, kVarIter, nullptr, s);
         if (e != cudaSuccess) return cuda_fail(e, "variable pass launch");
         if (prof) cudaEventRecordWithFlags(e1, s, rec_flags);
-        e = lr ? launch_lr_factor_pass(g->G, g->P, log_pot, Dv, lam, d, T, damping, s)
+        e = lr ? launch_lr_factor_pass(g->G, g->P, log_pot, g->lr_prm, Dv, lam, d, T, damping, s)
                : launch_factor_pass(g->G, g->P, log_pot, g->b, evidence, cur, nxt, T, damping, s);
         if (e != cudaSuccess) return cuda_fail(e, "factor pass launch");
         if (prof) {

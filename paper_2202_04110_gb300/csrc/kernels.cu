@@ -1934,41 +1934,76 @@ __device__ __forceinline__ float4 lr_table(const EnumSeg *__restrict__ segs, int
     return make_float4(__ldg(t), __ldg(t + 1), __ldg(t + 2), __ldg(t + 3));
 }
 
+// Per run: each factor's table as the three numbers the log-ratio update depends on,
+// c = phi(1,0) - phi(0,0), al = phi(1,1) - phi(1,0), be = phi(0,1) - phi(0,0), at
+// prm[g], prm[F + g], prm[2F + g]. A table with a non-finite entry gets c = NaN, which
+// sends its factor to the exact path (that reads the table itself).
+__global__ void __launch_bounds__(256) k_lr_params(const EnumSeg *__restrict__ segs, int n_seg, int F,
+                                                   const float *__restrict__ pot, float *__restrict__ prm) {
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= F) return;
+    const float4 t = lr_table(segs, n_seg, pot, g);
+    const bool fin = isfinite(t.x) & isfinite(t.y) & isfinite(t.z) & isfinite(t.w);
+    prm[g] = fin ? t.z - t.x : CUDART_NAN_F;
+    prm[F + g] = t.w - t.z;
+    prm[2 * (size_t)F + g] = t.y - t.x;
+}
+
+// sp_T(x) = T ln(1 + e^(x / T)) = max(x, 0) + (T ln 2) log2(1 + 2^(-|x| k)), k = log2(e) / T,
+// on the SFU's base-2 exponential and logarithm (flush-to-zero forms; the argument of
+// log2 lies in [1, 2], absolute error below 3e-7 T); max(x, 0) for T = 0.
+template <bool MAXP>
+__device__ __forceinline__ float softplus_t(float x, float k, float Tln2) {
+    if constexpr (MAXP) {
+        return fmaxf(x, 0.f);
+    } else {
+        float p, l;
+        asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(p) : "f"(-fabsf(x) * k));
+        asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(l) : "f"(1.f + p));
+        return fmaf(Tln2, l, fmaxf(x, 0.f));
+    }
+}
+
 // Factor pass, 2 x 2 tables, persistent: thread-stride loop over the global factors
 // g = 0 .. F-1 (edges 2g to its variable 0 and 2g + 1, at slots p = lr_pos[2g],
-// lr_pos[2g + 1] of lam and d; phi(x0, x1) at phi[2 x0 + x1]; FROM_D: the 4-slot layout,
-// lam formed from the variable's total Dv and d as in k_var_slot4_lr), software-pipelined: the
-// slots and the table of the next factor are loaded before the current factor's
-// gathers of lam and d and its arithmetic, so the index stream's latency overlaps the
-// gathers'. d is updated in place (a slot belongs to one factor).
+// lr_pos[2g + 1] of lam and d; FROM_D: the 4-slot layout, lam formed from the
+// variable's total Dv and d as in k_var_slot4_lr), software-pipelined: the slots and the
+// table numbers of the next factor are loaded before the current factor's gathers and
+// arithmetic, so the index stream's latency overlaps the gathers'. d is updated in place
+// (a slot belongs to one factor).
 //
-// The common case runs without guards. With o, mo the decoded new and stored messages
-// (one entry of each exactly 0), the damped pair t = damping mo + (1 - damping) o has
-// log-ratio t(1) - t(0) = damping d_old + (1 - damping)(a(1) - a(0)), since
-// min(x, 0) + max(x, 0) = x; the final normalisation does not change it. Every input
-// that needs the guarded arithmetic (an LSE over two -inf values, an infinite stored
-// message, damping 0 against an infinite stored message) makes a result non-finite;
-// that and a NaN lam (the contradiction pattern, which fmaxf / fminf would drop) send
-// the factor to pair2_lr_exact.
+// With the variable-to-factor log-ratios l0, l1 and the table numbers (k_lr_params),
+// LSE_T over the other variable's states gives the new log-ratios
+//   to variable 0: c  + sp_T(al + l1) - sp_T(be + l1),
+//   to variable 1: be + sp_T(al + c - be + l0) - sp_T(c + l0)   (al + c - be = phi(1,1) - phi(0,1)).
+// With o, mo the decoded new and stored messages (one entry of each exactly 0), the damped
+// pair t = damping mo + (1 - damping) o has log-ratio damping d_old + (1 - damping) dt,
+// since min(x, 0) + max(x, 0) = x; the final normalisation does not change it. Every
+// input that needs the guarded arithmetic (a non-finite table entry, an infinite
+// variable-to-factor value or stored message, damping 0 against an infinite stored
+// message) makes a result non-finite; that and a NaN lam (the contradiction pattern)
+// send the factor to pair2_lr_exact with its table.
 template <bool MAXP, bool FROM_D>
 __global__ void __launch_bounds__(256) k_pair2_lr(const EnumSeg *__restrict__ segs, int n_seg, int F, int V,
-                                                  const int2 *__restrict__ lr_pos2, const float *__restrict__ pot,
-                                                  const float2 *__restrict__ Dv, const float *__restrict__ lam,
-                                                  float *__restrict__ d, uint32_t *flags, float k, float Tln2,
-                                                  float damping) {
+                                                  const int2 *__restrict__ lr_pos2, const float *__restrict__ prm,
+                                                  const float *__restrict__ pot, const float2 *__restrict__ Dv,
+                                                  const float *__restrict__ lam, float *__restrict__ d,
+                                                  uint32_t *flags, float k, float Tln2, float damping) {
     const int stride = gridDim.x * blockDim.x;
     int g = blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= F) return;
     int2 p = __ldcs(lr_pos2 + g);
-    float4 phi = lr_table(segs, n_seg, pot, g);
+    float c = __ldcs(prm + g), al = __ldcs(prm + F + g), be = __ldcs(prm + 2 * (size_t)F + g);
     const float w = 1.f - damping;
     while (true) {
         const int gn = g + stride;
         int2 pn = p;
-        float4 phin = phi;
+        float cn = c, aln = al, ben = be;
         if (gn < F) {
             pn = __ldcs(lr_pos2 + gn);
-            phin = lr_table(segs, n_seg, pot, gn);
+            cn = __ldcs(prm + gn);
+            aln = __ldcs(prm + F + gn);
+            ben = __ldcs(prm + 2 * (size_t)F + gn);
         }
         const float mo0 = __ldcg(d + p.x), mo1 = __ldcg(d + p.y);
         float l0, l1;
@@ -1983,15 +2018,12 @@ __global__ void __launch_bounds__(256) k_pair2_lr(const EnumSeg *__restrict__ se
             l0 = __ldcg(lam + p.x);
             l1 = __ldcg(lam + p.y);
         }
-        const float2 v0 = lr_decode(l0), v1 = lr_decode(l1);
-        // to variable 0: a(x0) = LSE over x1 of phi(x0, x1) + v1(x1); to variable 1: c(x1)
-        const float a0 = lse2_fast_t<MAXP>(phi.x + v1.x, phi.y + v1.y, k, Tln2);
-        const float a1 = lse2_fast_t<MAXP>(phi.z + v1.x, phi.w + v1.y, k, Tln2);
-        const float c0 = lse2_fast_t<MAXP>(phi.x + v0.x, phi.z + v0.y, k, Tln2);
-        const float c1 = lse2_fast_t<MAXP>(phi.y + v0.x, phi.w + v0.y, k, Tln2);
-        float2 dn = make_float2(fmaf(damping, mo0, w * (a1 - a0)), fmaf(damping, mo1, w * (c1 - c0)));
+        const float dt0 = c + softplus_t<MAXP>(al + l1, k, Tln2) - softplus_t<MAXP>(be + l1, k, Tln2);
+        const float dt1 = be + softplus_t<MAXP>(al + c - be + l0, k, Tln2) - softplus_t<MAXP>(c + l0, k, Tln2);
+        float2 dn = make_float2(fmaf(damping, mo0, w * dt0), fmaf(damping, mo1, w * dt1));
         if (!(isfinite(dn.x) && isfinite(dn.y) && l0 == l0 && l1 == l1)) {
-            const float t4[4] = {phi.x, phi.y, phi.z, phi.w};
+            const float4 t = lr_table(segs, n_seg, pot, g);
+            const float t4[4] = {t.x, t.y, t.z, t.w};
             dn = pair2_lr_exact<MAXP>(t4, l0, l1, mo0, mo1, k, Tln2, damping, flags);
         }
         d[p.x] = dn.x;
@@ -1999,7 +2031,9 @@ __global__ void __launch_bounds__(256) k_pair2_lr(const EnumSeg *__restrict__ se
         if (gn >= F) break;
         g = gn;
         p = pn;
-        phi = phin;
+        c = cn;
+        al = aln;
+        be = ben;
     }
 }
 
@@ -2146,8 +2180,18 @@ cudaError_t launch_lr_var_pass(const DevGraph &G, const Plan &P, const float *ev
     return cudaGetLastError();
 }
 
-cudaError_t launch_lr_factor_pass(const DevGraph &G, const Plan &P, const float *log_pot, const float2 *Dv,
-                                  const float *lam, float *d, float T, float damping, cudaStream_t s) {
+cudaError_t launch_lr_params(const DevGraph &G, const Plan &P, const float *log_pot, float *prm, cudaStream_t s) {
+    const int F = G.E / 2;
+    for (const FactorLaunch &L : P.factor) {  // the one kPair2 launch: every factor
+        if (L.n_blocks == 0 || F == 0) continue;
+        k_lr_params<<<(F + 255) / 256, 256, 0, s>>>(static_cast<const EnumSeg *>(L.segs), L.n_seg, F, log_pot, prm);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lr_factor_pass(const DevGraph &G, const Plan &P, const float *log_pot, const float *prm,
+                                  const float2 *Dv, const float *lam, float *d, float T, float damping,
+                                  cudaStream_t s) {
     // lse2_fast constants: k = log2(e) / T, T ln 2
     const float k = T > 0.f ? (float)(1.4426950408889634 / (double)T) : 0.f;
     const float Tln2 = (float)((double)T * 0.6931471805599453);
@@ -2161,17 +2205,17 @@ cudaError_t launch_lr_factor_pass(const DevGraph &G, const Plan &P, const float 
         const bool from_d = G.vin_tab4 != nullptr;
         if (T == 0.f) {
             if (from_d)
-                k_pair2_lr<true, true><<<blocks, 256, 0, s>>>(es, L.n_seg, F, G.V, pos2, log_pot, Dv, lam, d, G.flags,
+                k_pair2_lr<true, true><<<blocks, 256, 0, s>>>(es, L.n_seg, F, G.V, pos2, prm, log_pot, Dv, lam, d, G.flags,
                                                               k, Tln2, damping);
             else
-                k_pair2_lr<true, false><<<blocks, 256, 0, s>>>(es, L.n_seg, F, G.V, pos2, log_pot, Dv, lam, d,
+                k_pair2_lr<true, false><<<blocks, 256, 0, s>>>(es, L.n_seg, F, G.V, pos2, prm, log_pot, Dv, lam, d,
                                                                G.flags, k, Tln2, damping);
         } else {
             if (from_d)
-                k_pair2_lr<false, true><<<blocks, 256, 0, s>>>(es, L.n_seg, F, G.V, pos2, log_pot, Dv, lam, d,
+                k_pair2_lr<false, true><<<blocks, 256, 0, s>>>(es, L.n_seg, F, G.V, pos2, prm, log_pot, Dv, lam, d,
                                                                G.flags, k, Tln2, damping);
             else
-                k_pair2_lr<false, false><<<blocks, 256, 0, s>>>(es, L.n_seg, F, G.V, pos2, log_pot, Dv, lam, d,
+                k_pair2_lr<false, false><<<blocks, 256, 0, s>>>(es, L.n_seg, F, G.V, pos2, prm, log_pot, Dv, lam, d,
                                                                 G.flags, k, Tln2, damping);
         }
     }

@@ -182,8 +182,11 @@ cudaError_t launch_factor_pass(const DevGraph &G, const Plan &P, const float *lo
 // forms lam from it; otherwise lam is written and read.
 cudaError_t launch_lr_var_pass(const DevGraph &G, const Plan &P, const float *ev, const float *d, float2 *Dv,
                                float *lam, cudaStream_t s);
-cudaError_t launch_lr_factor_pass(const DevGraph &G, const Plan &P, const float *log_pot, const float2 *Dv,
-                                  const float *lam, float *d, float T, float damping, cudaStream_t s);
+// Per run: each factor's table as the three differences the update depends on (prm[3F]).
+cudaError_t launch_lr_params(const DevGraph &G, const Plan &P, const float *log_pot, float *prm, cudaStream_t s);
+cudaError_t launch_lr_factor_pass(const DevGraph &G, const Plan &P, const float *log_pot, const float *prm,
+                                  const float2 *Dv, const float *lam, float *d, float T, float damping,
+                                  cudaStream_t s);
 // Log-ratio pack (from the [2E] edge-state layout; unused slots 0) and unpack.
 cudaError_t launch_lr_pack(const DevGraph &G, const float *m, float *d, cudaStream_t s);
 cudaError_t launch_lr_unpack(const DevGraph &G, const float *d, float *m, cudaStream_t s);
