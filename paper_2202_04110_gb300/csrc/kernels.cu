@@ -1720,6 +1720,16 @@ __global__ void __launch_bounds__(128) k_adj_var(DevGraph G, const float *__rest
 
 constexpr uint32_t kLamBothNegInf = 0x7fc00001u;
 
+// Programmatic dependent launch between the passes of a log-ratio run (the kernels are
+// launched with cudaLaunchAttributeProgrammaticStreamSerialization): each pass lets the
+// next one be scheduled as soon as all of its own blocks have started, loads only inputs
+// that are fixed for the run before pdl_wait(), and reads or writes the arrays the
+// passes exchange only after it. pdl_wait() returns once the previous kernel of the
+// stream has completed and its writes are visible (at once when there is none); as
+// that kernel waited the same way, every earlier one has completed too.
+__device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 __device__ __forceinline__ float2 lr_decode(float d) {
     return d > 0.f ? make_float2(-d, 0.f) : make_float2(0.f, d);
 }
@@ -1783,9 +1793,11 @@ __device__ __forceinline__ float lr_lam_from_D(float2 D, float dk) {
 __global__ void __launch_bounds__(256) k_var_slot4_lr(int V, const float *__restrict__ ev,
                                                       const float *__restrict__ d, float2 *__restrict__ Dv,
                                                       float *__restrict__ lam) {
+    pdl_launch_dependents();
     const int v = blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= V) return;
     const float2 e = __ldcs(reinterpret_cast<const float2 *>(ev) + v);
+    pdl_wait();  // d is the previous factor pass's output
     float dk[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) dk[k] = __ldcg(d + (size_t)k * V + v);
@@ -1816,11 +1828,13 @@ __global__ void __launch_bounds__(256) k_var_slot4_lr(int V, const float *__rest
 __global__ void __launch_bounds__(256) k_var_csr_lr(DevGraph G, const int32_t *__restrict__ list, int n,
                                                     const float *__restrict__ ev, const float *__restrict__ d,
                                                     float *__restrict__ lam) {
+    pdl_launch_dependents();
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= n) return;
     const int v = list ? __ldg(list + t) : t;
     const int k0 = __ldg(G.vin_off + v), k1 = __ldg(G.vin_off + v + 1);
     const float2 e = __ldg(reinterpret_cast<const float2 *>(ev) + v);  // all binary: states at 2v
+    pdl_wait();  // d is the previous factor pass's output
     bool fin = isfinite(e.x) & isfinite(e.y);
     FF D = ff_add(ff_make(e.y), -e.x);
     for (int k = k0; k < k1; ++k) {
@@ -1989,12 +2003,14 @@ __global__ void __launch_bounds__(256) k_pair2_lr(const EnumSeg *__restrict__ se
                                                   const float *__restrict__ pot, const float2 *__restrict__ Dv,
                                                   const float *__restrict__ lam, float *__restrict__ d,
                                                   uint32_t *flags, float k, float Tln2, float damping) {
+    pdl_launch_dependents();
     const int stride = gridDim.x * blockDim.x;
     int g = blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= F) return;
     int2 p = __ldcs(lr_pos2 + g);
     float c = __ldcs(prm + g), al = __ldcs(prm + F + g), be = __ldcs(prm + 2 * (size_t)F + g);
     const float w = 1.f - damping;
+    pdl_wait();  // Dv / lam are the variable pass's output
     while (true) {
         const int gn = g + stride;
         int2 pn = p;
@@ -2169,15 +2185,34 @@ static void factor_pass_t(const DevGraph &G, const Plan &P, const float *pot, co
     }
 }
 
+// A launch that may begin while the previous kernel of the stream finishes (the kernel
+// waits for it with pdl_wait before touching its output).
+template <typename... KArgs, typename... Args>
+static cudaError_t launch_pdl(void (*kernel)(KArgs...), int blocks, int threads, cudaStream_t s, Args... args) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3((unsigned)blocks);
+    cfg.blockDim = dim3((unsigned)threads);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 cudaError_t launch_lr_var_pass(const DevGraph &G, const Plan &P, const float *ev, const float *d, float2 *Dv,
                                float *lam, cudaStream_t s) {
+    cudaError_t e = cudaSuccess;
     if (G.vin_tab4 != nullptr) {
-        k_var_slot4_lr<<<(G.V + 255) / 256, 256, 0, s>>>(G.V, ev, d, Dv, lam);
+        e = launch_pdl(k_var_slot4_lr, (G.V + 255) / 256, 256, s, G.V, ev, d, Dv, lam);
     } else {
         for (const VarLaunch &L : P.var)
-            if (L.n > 0) k_var_csr_lr<<<L.n_blocks, L.threads, 0, s>>>(G, L.list, L.n, ev, d, lam);
+            if (L.n > 0 && e == cudaSuccess)
+                e = launch_pdl(k_var_csr_lr, L.n_blocks, L.threads, s, G, L.list, L.n, ev, d, lam);
     }
-    return cudaGetLastError();
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 cudaError_t launch_lr_params(const DevGraph &G, const Plan &P, const float *log_pot, float *prm, cudaStream_t s) {
@@ -2203,21 +2238,11 @@ cudaError_t launch_lr_factor_pass(const DevGraph &G, const Plan &P, const float 
         // persistent: as many blocks of 256 as are resident at once (8 per SM), or fewer
         const int blocks = std::min<int>(P.lr_blocks, (F + 255) / 256);
         const bool from_d = G.vin_tab4 != nullptr;
-        if (T == 0.f) {
-            if (from_d)
-                k_pair2_lr<true, true><<<blocks, 256, 0, s>>>(es, L.n_seg, F, G.V, pos2, prm, log_pot, Dv, lam, d, G.flags,
-                                                              k, Tln2, damping);
-            else
-                k_pair2_lr<true, false><<<blocks, 256, 0, s>>>(es, L.n_seg, F, G.V, pos2, prm, log_pot, Dv, lam, d,
-                                                               G.flags, k, Tln2, damping);
-        } else {
-            if (from_d)
-                k_pair2_lr<false, true><<<blocks, 256, 0, s>>>(es, L.n_seg, F, G.V, pos2, prm, log_pot, Dv, lam, d,
-                                                               G.flags, k, Tln2, damping);
-            else
-                k_pair2_lr<false, false><<<blocks, 256, 0, s>>>(es, L.n_seg, F, G.V, pos2, prm, log_pot, Dv, lam, d,
-                                                                G.flags, k, Tln2, damping);
-        }
+        auto kern = T == 0.f ? (from_d ? k_pair2_lr<true, true> : k_pair2_lr<true, false>)
+                             : (from_d ? k_pair2_lr<false, true> : k_pair2_lr<false, false>);
+        cudaError_t e = launch_pdl(kern, blocks, 256, s, es, L.n_seg, F, G.V, pos2, (const float *)prm, log_pot,
+                                   Dv, lam, d, G.flags, k, Tln2, damping);
+        if (e != cudaSuccess) return e;
     }
     return cudaGetLastError();
 }
