@@ -327,7 +327,8 @@ pgm_status pgm_get_option(const pgm_graph *g, int32_t option, int64_t *value);
 /*
  * Launch-shape autotuner: for every factor-pass launch of the graph (one per kernel
  * variant, covering all groups of that variant) times each thread-block shape the
- * kernel allows -- threads per block for the thread-per-factor kernels, warps per
+ * kernel allows, and for dense K-state pairwise launches (K = 4, 8, 16) both kernel
+ * forms (K lanes per factor, thread per factor) -- threads per block for the thread-per-factor kernels, warps per
  * block (factors per block) for the warp-per-factor logical kernel -- on the given
  * inputs, and keeps the fastest; likewise the block size of the thread-per-variable
  * pass. Allocates two temporary message buffers (freed before returning), blocks until
@@ -340,9 +341,11 @@ pgm_status pgm_autotune(pgm_graph *g, const float *log_pot, const float *evidenc
  * Launch i of one iteration (0 <= i < pgm_info.launches_per_iter): kind 0 = variable
  * pass (variant 0 thread per variable, 1 block per variable, 2 thread per binary
  * variable, 3..5 K = 4, 8, 16 lanes per variable, 6 padded 4-edge table),
- * kind 1 = factor pass (variant: 0..3 dense pairwise K = 2, 4, 8, 16; 4 listed
- * configurations; 5 OR/AND thread per factor; 6 OR/AND warp per factor); threads per
- * block and blocks. Any output pointer may be NULL.
+ * kind 1 = factor pass (variant: 0 dense pairwise K = 2; 1..3 dense pairwise K = 4, 8,
+ * 16 with K lanes per factor; 4 listed configurations; 5 OR/AND thread per factor; 6
+ * OR/AND warp per factor; 7..9 dense pairwise K = 4, 8, 16 with a thread per factor,
+ * the default form, which pgm_autotune may exchange with 1..3); threads per block and
+ * blocks. Any output pointer may be NULL.
  */
 pgm_status pgm_launch_info(const pgm_graph *g, int32_t i, int32_t *kind, int32_t *variant,
                            int32_t *threads, int32_t *n_blocks);

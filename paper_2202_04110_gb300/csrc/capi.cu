@@ -233,7 +233,7 @@ pgm_status build_plan(const HostLayout &H, pgm_graph *g, Packer &pk, std::vector
                                              reinterpret_cast<const char *>(segs.data() + segs.size()));
         } else {
             std::vector<EnumSeg> segs;
-            int threads = (variant == kEnumGeneric) ? 128 : 256;
+            int threads = (variant == kEnumGeneric || variant == kPairT16) ? 128 : 256;
             const int per_block = threads / lanes_per_factor(variant);
             int32_t blk = 0;
             for (const HostEnumGroup &hg : H.enum_groups) {
@@ -739,10 +739,27 @@ pgm_status pgm_run_bp(pgm_graph *g, const float *log_pot, const float *evidence,
     return enqueue_iterations(g, log_pot, evidence, T, damping, n_iters, msgs, s, true);
 }
 
+// The other kernel form for the same factors: dense K-state pairwise tables run either
+// with K lanes per factor (kPair4 / 8 / 16) or with a thread per factor (kPairT4 / 8 /
+// 16). -1 if there is none.
+static int alternative_form(int variant) {
+    switch (variant) {
+        case kPair4: return kPairT4;
+        case kPair8: return kPairT8;
+        case kPair16: return kPairT16;
+        case kPairT4: return kPair4;
+        case kPairT8: return kPair8;
+        case kPairT16: return kPair16;
+        default: return -1;
+    }
+}
+
 // Thread-block shapes a factor launch may use (within the kernels' launch bounds).
 static std::vector<int> shape_candidates(int variant) {
     switch (variant) {
         case kPair2: case kPair4: case kPair8: case kPair16: case kLogicSmall: return {64, 128, 256};
+        case kPairT4: case kPairT8: return {64, 128, 256};
+        case kPairT16: return {64, 128};
         case kEnumGeneric: return {32, 64, 128};
         case kLogicWarp: return {32, 64, 128};
         default: return {};
@@ -802,26 +819,35 @@ pgm_status pgm_autotune(pgm_graph *g, const float *log_pot, const float *evidenc
     enqueue_iterations(g, log_pot, evidence, T, damping, 1, m_in, s, false);
     launch_var_pass(g->G, g->P, evidence, m_in, g->b, kVarIter, nullptr, s);
     for (size_t li = 0; li < g->P.factor.size(); ++li) {
-        const int orig = g->P.factor[li].threads;
-        int best = orig;
+        const int orig_variant = g->P.factor[li].variant;
+        int best = g->P.factor[li].threads, best_variant = orig_variant;
         float best_ms = 1e30f;
-        for (int c : shape_candidates(g->P.factor[li].variant)) {
-            if (!replan_factor_launch(g, li, c, s)) continue;
-            Plan one;
-            one.factor.push_back(g->P.factor[li]);
-            launch_factor_pass(g->G, one, log_pot, g->b, evidence, m_in, m_out, T, damping, s);
-            cudaEventRecord(e0, s);
-            for (int r = 0; r < 5; ++r)
+        // the kernel forms that can run this launch's groups, each with its block shapes
+        std::vector<int> forms{orig_variant};
+        const int alt = alternative_form(orig_variant);
+        if (alt >= 0) forms.push_back(alt);
+        for (int variant : forms) {
+            g->P.factor[li].variant = variant;
+            for (int c : shape_candidates(variant)) {
+                if (!replan_factor_launch(g, li, c, s)) continue;
+                Plan one;
+                one.factor.push_back(g->P.factor[li]);
                 launch_factor_pass(g->G, one, log_pot, g->b, evidence, m_in, m_out, T, damping, s);
-            cudaEventRecord(e1, s);
-            cudaEventSynchronize(e1);
-            float ms = 0.f;
-            cudaEventElapsedTime(&ms, e0, e1);
-            if (cudaGetLastError() == cudaSuccess && ms < best_ms) {
-                best_ms = ms;
-                best = c;
+                cudaEventRecord(e0, s);
+                for (int r = 0; r < 5; ++r)
+                    launch_factor_pass(g->G, one, log_pot, g->b, evidence, m_in, m_out, T, damping, s);
+                cudaEventRecord(e1, s);
+                cudaEventSynchronize(e1);
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (cudaGetLastError() == cudaSuccess && ms < best_ms) {
+                    best_ms = ms;
+                    best = c;
+                    best_variant = variant;
+                }
             }
         }
+        g->P.factor[li].variant = best_variant;
         replan_factor_launch(g, li, best, s);
     }
     // thread-per-variable launches: block size

@@ -189,10 +189,12 @@ std::string compile_graph(const void *const *vdescs, int n_desc, HostLayout *L) 
             int K0 = s.K[0], K1 = g.arity > 1 ? s.K[1] : 0;
             hg.variant = kEnumGeneric;
             if (g.n_fac > 0 && is_dense_pair(g, K0, K1)) {
+                // K = 4, 8, 16: thread per factor by default (the autotuner may switch a
+                // launch to the K-lane form)
                 if (K0 == 2) hg.variant = kPair2;
-                else if (K0 == 4) hg.variant = kPair4;
-                else if (K0 == 8) hg.variant = kPair8;
-                else if (K0 == 16) hg.variant = kPair16;
+                else if (K0 == 4) hg.variant = kPairT4;
+                else if (K0 == 8) hg.variant = kPairT8;
+                else if (K0 == 16) hg.variant = kPairT16;
             }
             for (int64_t f = 0; f < g.n_fac; ++f)
                 for (int j = 0; j < g.arity; ++j) {

@@ -1178,6 +1178,118 @@ k_pair_group(DevGraph G, const EnumSeg *__restrict__ segs, int n_seg, int n_vblo
     }
 }
 
+// ---- K-state pairwise tables, thread per factor ------------------------------------
+
+// One direction of a K-state pairwise factor, thread-local: o(x) = LSE_T (or max) over y
+// of phi(x, y) + v(y) for the message to variable 0 (TR = false, rows of phi), or of
+// phi(y, x) + v(y) for the message to variable 1 (TR = true, columns). Linear form for a
+// shared table with E = exp((phi - tmax) / T) (tabE row-major E, tabET row-major E^T):
+// o(x) = T log(sum_y E(x, y) w(y)) + vmax + tmax with w(y) = exp((v(y) - vmax) / T), the
+// rows read as float4 (every thread of the block reads the same row: a broadcast).
+template <int K, bool MAXP, bool TR>
+__device__ __forceinline__ void pair_dir_thr(float (&v)[K], float (&o)[K], bool linear, const float *tabE,
+                                             const float *phi, bool phi_shared, float tmax, float T,
+                                             float invT) {
+    if (!MAXP && linear) {
+        float vmax = kNegInf;
+#pragma unroll
+        for (int y = 0; y < K; ++y) vmax = fmaxf(vmax, v[y]);
+        if (vmax == kNegInf) {
+#pragma unroll
+            for (int x = 0; x < K; ++x) o[x] = kNegInf;
+            return;
+        }
+#pragma unroll
+        for (int y = 0; y < K; ++y) v[y] = __expf((v[y] - vmax) * invT);  // w(y), in (0, 1]
+#pragma unroll
+        for (int x = 0; x < K; ++x) {
+            const float4 *row = reinterpret_cast<const float4 *>(tabE + x * K);
+            float s = 0.f;
+#pragma unroll
+            for (int j = 0; j < K / 4; ++j) {
+                const float4 a = row[j];
+                s = fmaf(a.x, v[4 * j], fmaf(a.y, v[4 * j + 1], fmaf(a.z, v[4 * j + 2], fmaf(a.w, v[4 * j + 3], s))));
+            }
+            o[x] = T * logf(s) + vmax + tmax;
+        }
+    } else {
+#pragma unroll
+        for (int x = 0; x < K; ++x) {
+            float z[K];
+#pragma unroll
+            for (int y = 0; y < K; ++y) {
+                const int i = TR ? y * K + x : x * K + y;
+                z[y] = (phi_shared ? phi[i] : __ldg(phi + i)) + v[y];
+            }
+            o[x] = lse_row<K, MAXP>(z, T, invT);
+        }
+    }
+}
+
+// Dense K-state pairwise tables (Potts, K = 4, 8, 16), thread per factor: the thread
+// keeps the factor's two stored messages and one variable-to-factor vector in registers
+// and forms the K x K table product itself, one direction at a time (no cross-lane
+// traffic, so the per-factor work is the product's K^2 multiply-adds plus 2K
+// exponentials and logarithms per direction). Shared tables are staged per block in
+// shared memory (with E and E^T for the linear form); per-factor tables are read from
+// the factor's own K*K entries. The rare cases (an edge of a high-degree variable, a
+// stored entry that is -inf or large) go to pair_factor_rare.
+template <int K, bool MAXP>
+__global__ void __launch_bounds__(K >= 16 ? 128 : 256)
+k_pair_thr(DevGraph G, const EnumSeg *__restrict__ segs, int n_seg, const float *__restrict__ pot,
+           const float *__restrict__ b, const float *__restrict__ ev, const float *__restrict__ m_old,
+           float *__restrict__ m_new, float T, float invT, float damping) {
+    __shared__ float tab[K * K];
+    __shared__ __align__(16) float tabE[MAXP ? 4 : K * K];
+    __shared__ __align__(16) float tabET[MAXP ? 4 : K * K];
+    __shared__ float tinfo[2];
+    const EnumSeg *S = segs + find_seg(segs, n_seg, blockIdx.x);
+    const int n_fac = __ldg(&S->n_fac), shared = __ldg(&S->shared), pot_base = __ldg(&S->pot_base);
+    bool linear = false;
+    if (shared) {  // uniform over the block (a block lies in one segment)
+        for (int i = threadIdx.x; i < K * K; i += blockDim.x) tab[i] = __ldg(pot + pot_base + i);
+        __syncthreads();
+        linear = prepare_linear_table<K, MAXP>(tab, tabE, tinfo, invT);
+        if (linear) {
+            for (int i = threadIdx.x; i < K * K; i += blockDim.x) tabET[(i % K) * K + i / K] = tabE[i];
+            __syncthreads();
+        }
+    }
+    const int f = (blockIdx.x - __ldg(&S->block_begin)) * blockDim.x + threadIdx.x;
+    if (f >= n_fac) return;
+    const int e = __ldg(&S->edge_base) + 2 * f;
+    const int es0 = __ldg(&S->es_base) + 2 * K * f, es1 = es0 + K;
+    const int vs0 = __ldg(G.edge_vs + e), vs1 = __ldg(G.edge_vs + e + 1);
+    const float *phi = shared ? tab : pot + pot_base + (size_t)f * (K * K);
+    float mo0[K], mo1[K];
+    load_n_stream<K>(mo0, m_old + es0);
+    load_n_stream<K>(mo1, m_old + es1);
+    bool rare = (vs0 < 0) | (vs1 < 0);
+#pragma unroll
+    for (int x = 0; x < K; ++x) rare |= needs_exact(mo0[x]) | needs_exact(mo1[x]);
+    if (rare) {
+        pair_factor_rare<K, MAXP>(G, shared ? tab : nullptr, pot + pot_base + (size_t)f * (K * K), b, ev, m_old,
+                                  m_new, vs0, vs1, es0, es1, T, invT, damping);
+        return;
+    }
+    const float tmax = linear ? tinfo[0] : 0.f;
+    float v[K], o[K];
+    // to variable 0: rows of phi against v1 = b1 - m1
+    load_n<K>(v, b + vs1);
+#pragma unroll
+    for (int y = 0; y < K; ++y) v[y] -= mo1[y];
+    pair_dir_thr<K, MAXP, false>(v, o, linear, tabE, phi, shared, tmax, T, invT);
+    finish_k<K>(o, mo0, damping, G.flags);
+    store_n<K>(m_new + es0, o);
+    // to variable 1: columns of phi against v0 = b0 - m0
+    load_n<K>(v, b + vs0);
+#pragma unroll
+    for (int y = 0; y < K; ++y) v[y] -= mo0[y];
+    pair_dir_thr<K, MAXP, true>(v, o, linear, tabET, phi, shared, tmax, T, invT);
+    finish_k<K>(o, mo1, damping, G.flags);
+    store_n<K>(m_new + es1, o);
+}
+
 // =====================================================================================
 // Factor pass: any listed-configuration factor, thread per factor
 // =====================================================================================
@@ -2169,6 +2281,15 @@ static void factor_pass_t(const DevGraph &G, const Plan &P, const float *pot, co
                 break;
             case kPair16:
                 k_pair_group<16, MAXP><<<min(L.n_blocks, L.max_blocks), L.threads, 0, s>>>(G, es, L.n_seg, L.n_blocks, pot, b, ev, m_old, m_new, T, invT, damping);
+                break;
+            case kPairT4:
+                k_pair_thr<4, MAXP><<<L.n_blocks, L.threads, 0, s>>>(G, es, L.n_seg, pot, b, ev, m_old, m_new, T, invT, damping);
+                break;
+            case kPairT8:
+                k_pair_thr<8, MAXP><<<L.n_blocks, L.threads, 0, s>>>(G, es, L.n_seg, pot, b, ev, m_old, m_new, T, invT, damping);
+                break;
+            case kPairT16:
+                k_pair_thr<16, MAXP><<<L.n_blocks, L.threads, 0, s>>>(G, es, L.n_seg, pot, b, ev, m_old, m_new, T, invT, damping);
                 break;
             case kEnumGeneric:
                 k_enum_generic<MAXP><<<L.n_blocks, L.threads, 0, s>>>(G, es, L.n_seg, pot, b, ev, m_old, m_new, T, invT, damping);

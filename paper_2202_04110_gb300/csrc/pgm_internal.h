@@ -36,7 +36,10 @@ enum FactorVariant : int32_t {
     kEnumGeneric = 4,  // any listed-configuration factor within the limits
     kLogicSmall = 5,   // OR / AND, fan-in <= kLogicSmallFan, thread per factor
     kLogicWarp = 6,    // OR / AND, any fan-in, warp per factor
-    kNumFactorVariants = 7
+    kPairT4 = 7,       // dense pairwise table, K = 4, 8, 16, thread per factor (the
+    kPairT8 = 8,       // alternative to the K-lane form kPair4 / 8 / 16; the autotuner
+    kPairT16 = 9,      // picks per launch)
+    kNumFactorVariants = 10
 };
 
 // One enumeration group as seen by a launch. Edges of factor f are
