@@ -5,8 +5,8 @@ import this package. It shares no code with the CUDA path: the arithmetic lives 
 ``lbp_oracle.c`` (plain C, double precision), this module only marshals numpy arrays.
 
 Functions follow PGMax (arXiv 2202.04110): flooding LBP with damping (Sec. 3),
-enumeration factors (Sec. 4.2), linear-time logical factors (Sec. 3), MAP decode
-(Sec. 4.1). ``lbp_oracle.c`` states each step.
+enumeration factors (Sec. 5.2), linear-time logical factors (Sec. 3), MAP decode
+(Sec. 5.1). ``lbp_oracle.c`` states each step.
 """
 from __future__ import annotations
 

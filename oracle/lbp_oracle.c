@@ -11,12 +11,12 @@
  *     every new factor-to-variable message of iteration t is computed from the
  *     messages of iteration t-1.
  *   - Enumeration factors given by their list of valid configurations and one
- *     log-potential per configuration (Sec. 4.2). Unlisted configurations have
+ *     log-potential per configuration (Sec. 5.2). Unlisted configurations have
  *     potential -inf.
  *   - Logical OR / AND factors with message updates linear in the fan-in (Sec. 3).
  *   - Temperature T on the factor log-sum-exp: T = 1 is sum-product, T = 0 is the
- *     max-product limit used for MAP (Sec. 4.1).
- *   - MAP decode: per-variable argmax of the beliefs (Sec. 4.1), lowest state on ties.
+ *     max-product limit used for MAP (Sec. 5.1).
+ *   - MAP decode: per-variable argmax of the beliefs (Sec. 5.1), lowest state on ties.
  *
  * Steps of one iteration, in this order:
  *   (i)   variable to factor: m_{v->f}(x) = e_v(x) + sum_{g in N(v), g != f} m_{g->v}(x),
@@ -568,7 +568,7 @@ static int argmax_k(const double *m, int K) {
 /*
  * Gradient of L = sum_v sum_x g[v,x] * nb[v,x], nb = b - LSE_1(b), the normalised
  * log-beliefs after n_iters flooding iterations from zero messages, with respect to the
- * log-potentials and the evidence (the "grad" of Sec. 4.3: LBP inside a differentiable
+ * log-potentials and the evidence (the "grad" of Sec. 5.3: LBP inside a differentiable
  * system). T > 0 and enumeration factors only (returns -2 for logical factors).
  * Reverse-mode chain rule through each forward step, in reverse order:
  *   beliefs   nb = b - LSE(b):         db = g - softmax(b) * sum(g)

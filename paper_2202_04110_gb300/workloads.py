@@ -4,9 +4,9 @@ This module only builds graph structure and draws random numbers; it holds none 
 the belief-propagation arithmetic. The CUDA path and the FP64 oracle both consume
 what it produces, so a workload is bit-identical on both sides.
 
-Graph model (PGMax's model specification layer, Sec. 3 "Package features": discrete
+Graph model (PGMax's model specification layer, Sec. 3, the package features: discrete
 variables with a varying number of states, arbitrary topology, enumeration factors
-given by their list of valid configurations, Sec. 4.2; logical factors, Sec. 3):
+given by their list of valid configurations, Sec. 5.2; logical factors, Sec. 3):
 
 * ``num_states[v]``: number of states K_v of variable v.
 * Enumeration group: factors that share an arity and a configuration list.
@@ -203,7 +203,7 @@ def deconvolution(seed: int, n_feat: int = 5, feat_side: int = 6, s_side: int = 
                   prior: float = -2.0, T: float = 0.0, damping: float = 0.5,
                   n_iters: int = 1000) -> Problem:
     """2D binary deconvolution with logical factors (the PGMax example notebook of
-    Sec. 4.2, after Lazaro-Gredilla et al. 2021).
+    Sec. 5.2, after Lazaro-Gredilla et al. 2021).
 
     Variables, numbered in this order: features W[k, dy, dx], activations
     S[n, k, py, px], one AND variable z per (n, k, p, d) with z = AND(W[k, d], S[n, k, p]),

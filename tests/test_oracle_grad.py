@@ -1,4 +1,4 @@
-"""Pins for the oracle's adjoint (gradient of normalised log-beliefs, Sec. 4.3 "grad"):
+"""Pins for the oracle's adjoint (gradient of normalised log-beliefs; Sec. 5.3 on using LBP inside differentiable programs):
 central finite differences of the oracle's own pinned forward pass, in FP64, on every
 coordinate of small graphs, plus the shift invariances the gradient must satisfy
 (normalised beliefs do not change when a constant is added to one variable's evidence or

@@ -10,7 +10,7 @@
   enumeration over all parent configurations, for T in {0, 0.5, 1}.
 * Special cases: one parent copies the child's log-odds and vice versa; no parents
   forces the child to 0 (OR) or 1 (AND); a 2-variable Ising pair has a closed form.
-* MAP decode on random 30-unit RBMs (the protocol of Sec. 4.1) never beats the
+* MAP decode on random 30-unit RBMs (the protocol of Sec. 5.1) never beats the
   brute-force MAP and is checked against it.
 """
 import numpy as np
@@ -173,7 +173,7 @@ def test_sizes_of_workloads():
 
 
 def test_rbm_map_protocol():
-    """Sec. 4.1 protocol: 20 random 30-unit RBMs (15 visible + 15 hidden), 200
+    """Sec. 5.1 protocol: 20 random 30-unit RBMs (15 visible + 15 hidden), 200
     max-product iterations with damping 0.5, MAP quality = log-potential of the decoded
     configuration, ground truth by enumeration. The decode can never beat the brute-force
     MAP; how often it recovers it depends on the RBM distribution, which the paper does
