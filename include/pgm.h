@@ -5,11 +5,11 @@
  * the method of PGMax (arXiv 2202.04110): discrete variables with varying numbers of
  * states and factor graphs of arbitrary topology (Sec. 3, "Easy specification of
  * general factor graphs"), enumeration factors listed by their valid configurations
- * (Sec. 4.2), logical factors with message updates linear in the fan-in (Sec. 3),
+ * (Sec. 5.2), logical factors with message updates linear in the fan-in (Sec. 3),
  * parallel message updates with damping (Sec. 3, after Pretti 2005), all messages kept
  * in flat arrays updated by gather/scatter (Sec. 4 "A fully flat array-based LBP
  * implementation"), LBP as a pure function of explicit message state (Sec. 3,
- * Sec. 4.3), MAP decoding (Sec. 4.1).
+ * Sec. 5.3), MAP decoding (Sec. 5.1).
  *
  * Conventions for every call:
  *  - Return value: PGM_OK (0) or a negative pgm_status. pgm_last_error() returns a
@@ -69,7 +69,7 @@ typedef int32_t pgm_status;
 typedef struct pgm_graph pgm_graph;
 
 /*
- * Enumeration factors (Sec. 4.2: "explicitly enumerating the valid configurations").
+ * Enumeration factors (Sec. 5.2: a factor given by the list of its valid configurations).
  * All factors of a group share arity, configuration list and the state counts of their
  * j-th neighbours. Configurations that are not listed have log-potential -inf.
  */
@@ -83,7 +83,7 @@ typedef struct {
 } pgm_enum_group;
 
 /*
- * Logical factors (Sec. 3: "logical factors with linear message updates"): child =
+ * Logical factors (Sec. 3: logical factors whose updates are linear in the fan-in): child =
  * OP(parents) over binary variables, log-potential 0 on valid configurations and -inf
  * otherwise. A factor may have zero parents (OR of nothing is 0, AND of nothing is 1).
  */
@@ -147,7 +147,7 @@ pgm_status pgm_build(const pgm_graph_desc *desc, pgm_graph **out);
 pgm_status pgm_check_desc(const pgm_graph_desc *desc, pgm_info *info);
 
 /*
- * Batch of many graphs (Sec. 4.3: processing batches of models in parallel). Compiles n
+ * Batch of many graphs (Sec. 5.3: processing batches of models in parallel). Compiles n
  * descriptions into one graph whose flat arrays hold the members one after the other:
  * member i's variables, evidence, beliefs, edges, messages and log-potentials are
  * contiguous ranges (pgm_batch_member) laid out exactly as pgm_build lays out that
@@ -196,7 +196,7 @@ pgm_status pgm_beliefs(pgm_graph *g, const float *evidence, const float *msgs, f
                        int32_t normalise, void *stream);
 
 /*
- * MAP decode (Sec. 4.1): out[v] = argmax_x b_v(x), lowest state on exact ties
+ * MAP decode (Sec. 5.1): out[v] = argmax_x b_v(x), lowest state on exact ties
  * (device out [n_vars] int32).
  */
 pgm_status pgm_decode(pgm_graph *g, const float *evidence, const float *msgs, int32_t *out,
@@ -233,7 +233,7 @@ pgm_status pgm_pass_times(pgm_graph *g, double *var_ms, double *factor_ms, int64
                           int64_t *n_factor);
 
 /*
- * Gradient (Sec. 4.3: LBP as part of an end-to-end differentiable system): the
+ * Gradient (Sec. 5.3: LBP as part of an end-to-end differentiable system): the
  * vector-Jacobian product of the normalised log-beliefs after n_iters iterations from
  * zero messages (pgm_run_bp then pgm_beliefs(normalise = 1)) with the cotangent
  * d_beliefs [n_var_states], i.e. the gradient of L = sum(d_beliefs * (b - LSE_1(b)))
@@ -289,6 +289,29 @@ pgm_status pgm_device_flags(pgm_graph *g, uint32_t *flags, int32_t clear, void *
 pgm_status pgm_grid2_run_bp_noalloc(int32_t rows, int32_t cols, const float *log_pot,
                                     const float *evidence, float T, float damping,
                                     int32_t n_iters, float *msgs, void *stream);
+
+/*
+ * n_samples runs of one graph with different inputs, as n_samples calls of pgm_run_bp:
+ * sample s uses evidence[s * n_var_states ...], msgs[s * n_edge_states ...] (in/out,
+ * the pgm_run_bp layout for each sample), and log_pot[s * n_potentials ...] if
+ * pot_per_sample, else the one log_pot for every sample (Sec. 5.3 names batches of
+ * samples processed in parallel as a use of the pure-function design). On a graph that takes log-ratio iterations
+ * (PGM_OPT_LOG_RATIO) with at most 4 factors per variable, the samples run together in
+ * chunks: one variable pass and one factor pass per iteration over a chunk's samples,
+ * with the sample index innermost, so the graph's index arrays (and a shared table set)
+ * are read once per iteration for the chunk; results equal those of the single-sample
+ * runs. A chunk holds as many samples as keep the arrays exchanged between the passes
+ * (about 32 bytes per variable and sample, plus 12 per factor and sample for
+ * per-sample tables) within half the L2; where one sample alone exceeds that (e.g. a
+ * 1000 x 1000 grid), and on other graphs, the samples run one after another as
+ * pgm_run_bp. The first call with a larger chunk than before allocates device buffers
+ * (about 72 bytes per variable and sample on a grid), synchronising the device; they
+ * are kept until pgm_free. Stream-ordered otherwise.
+ * PGM_EINVAL for n_samples < 1 or the pgm_run_bp argument errors.
+ */
+pgm_status pgm_run_bp_multi(pgm_graph *g, int32_t n_samples, const float *log_pot, int32_t pot_per_sample,
+                            const float *evidence, float T, float damping, int32_t n_iters, float *msgs,
+                            void *stream);
 
 /*
  * Options of a graph. PGM_OPT_CUDA_GRAPH (default 1): pgm_run_bp with n_iters >= 2

@@ -23,7 +23,7 @@ FLAG_NAN = 2
 # Every symbol include/pgm.h declares.
 EXPORTED = ["pgm_build", "pgm_build_batch", "pgm_batch_member", "pgm_check_desc", "pgm_free", "pgm_graph_info", "pgm_run_bp", "pgm_beliefs",
             "pgm_decode", "pgm_infer_host", "pgm_set_profiling", "pgm_pass_times",
-            "pgm_device_flags", "pgm_grid2_run_bp_noalloc", "pgm_set_option", "pgm_get_option", "pgm_autotune",
+            "pgm_device_flags", "pgm_grid2_run_bp_noalloc", "pgm_run_bp_multi", "pgm_set_option", "pgm_get_option", "pgm_autotune",
             "pgm_launch_info", "pgm_grad", "pgm_serve_create", "pgm_serve_submit", "pgm_serve_poll",
             "pgm_serve_wait", "pgm_serve_stats", "pgm_serve_destroy", "pgm_last_error"]
 OPT_CUDA_GRAPH = 1
@@ -105,6 +105,8 @@ def load_library(path: str | None = None):
     lib.pgm_graph_info.argtypes = [vp, ctypes.POINTER(InfoC)]
     lib.pgm_run_bp.restype = i32
     lib.pgm_run_bp.argtypes = [vp, vp, vp, f32, f32, i32, vp, vp]
+    lib.pgm_run_bp_multi.restype = i32
+    lib.pgm_run_bp_multi.argtypes = [vp, i32, vp, i32, vp, f32, f32, i32, vp, vp]
     lib.pgm_beliefs.restype = i32
     lib.pgm_beliefs.argtypes = [vp, vp, vp, vp, i32, vp]
     lib.pgm_decode.restype = i32
@@ -255,6 +257,23 @@ class Graph:
     def new_msgs(self):
         import torch
         return torch.zeros(max(self.info["n_edge_states"], 1), dtype=torch.float32, device="cuda")[: self.info["n_edge_states"]]
+
+    def run_bp_multi(self, log_pot, evidence, T: float, damping: float, n_iters: int, msgs, stream=None):
+        """In-place, for S samples at once (pgm_run_bp_multi): evidence [S, n_var_states],
+        msgs [S, n_edge_states]; log_pot [n_potentials] (shared) or [S, n_potentials]."""
+        import torch
+        I = self.info
+        S = int(evidence.shape[0]) if evidence.dim() == 2 else 1
+        per_sample = log_pot is not None and log_pot.dim() == 2
+        if I["n_potentials"]:
+            lp = _dptr(log_pot, torch.float32, I["n_potentials"] * (S if per_sample else 1), "log_pot")
+        else:
+            lp = 0
+        check(load_library().pgm_run_bp_multi(
+            self._h, S, lp, int(per_sample), _dptr(evidence, torch.float32, S * I["n_var_states"], "evidence"),
+            float(T), float(damping), int(n_iters), _dptr(msgs, torch.float32, S * I["n_edge_states"], "msgs"),
+            _stream_ptr(stream)))
+        return msgs
 
     def run_bp(self, log_pot, evidence, T: float, damping: float, n_iters: int, msgs, stream=None):
         """In-place: msgs <- n_iters LBP iterations from msgs (pgm_run_bp)."""

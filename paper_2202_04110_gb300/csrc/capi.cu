@@ -62,6 +62,11 @@ struct pgm_graph {
     float *b = nullptr;
     float *lr_d = nullptr, *lr_lam = nullptr;  // Plan::lr: log-ratio arrays (lr_slots each)
     float *lr_prm = nullptr;                    // Plan::lr: table differences [3F] (per run)
+    // pgm_run_bp_multi buffers for up to ms_cap samples (allocated on first use)
+    void *ms_mem = nullptr;
+    int32_t ms_cap = 0;
+    float2 *ms_ev = nullptr, *ms_Dv = nullptr;
+    float *ms_d = nullptr, *ms_lam = nullptr, *ms_prm = nullptr;
     int64_t lr_slots = 0;
     // pgm_infer_host buffers (allocated on first use)
     void *host_io_mem = nullptr;
@@ -539,6 +544,7 @@ void pgm_free(pgm_graph *g) {
     if (g->index_mem) cudaFree(g->index_mem);
     if (g->scratch_mem) cudaFree(g->scratch_mem);
     if (g->host_io_mem) cudaFree(g->host_io_mem);
+    if (g->ms_mem) cudaFree(g->ms_mem);
     for (cudaEvent_t e : g->events) cudaEventDestroy(e);
     drop_cached_runs(g);
     if (g->capture_stream) cudaStreamDestroy(g->capture_stream);
@@ -714,6 +720,93 @@ static void drop_cached_runs(pgm_graph *g) {
         destroy_run(r);
     }
     g->runs.clear();
+}
+
+// pgm_run_bp_multi's buffers for S samples: transposed evidence (V S float2), packed
+// messages and flagged-variable lam (4V S each), per-variable totals (V S float2), table
+// differences (3F S: room for per-sample tables).
+static pgm_status ms_reserve(pgm_graph *g, int32_t S) {
+    if (g->ms_cap >= S) return PGM_OK;
+    const size_t V = (size_t)g->info.n_vars, F = (size_t)g->info.n_edges / 2;
+    const size_t b_ev = align_up(V * S * sizeof(float2), 256), b_d = align_up(4 * V * S * sizeof(float), 256);
+    const size_t b_prm = align_up(3 * F * S * sizeof(float), 256);
+    if (g->ms_mem) {
+        cudaError_t e = cudaDeviceSynchronize();  // the old buffers may still be in use
+        if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceSynchronize");
+        cudaFree(g->ms_mem);
+        g->ms_mem = nullptr;
+        g->ms_cap = 0;
+    }
+    char *mem = nullptr;
+    if (cudaMalloc(&mem, 2 * b_ev + 2 * b_d + b_prm) != cudaSuccess)
+        return fail(PGM_ENOMEM, "cudaMalloc(multi-sample buffers)");
+    g->ms_mem = mem;
+    g->ms_cap = S;
+    g->ms_ev = reinterpret_cast<float2 *>(mem);
+    g->ms_Dv = reinterpret_cast<float2 *>(mem + b_ev);
+    g->ms_d = reinterpret_cast<float *>(mem + 2 * b_ev);
+    g->ms_lam = reinterpret_cast<float *>(mem + 2 * b_ev + b_d);
+    g->ms_prm = reinterpret_cast<float *>(mem + 2 * b_ev + 2 * b_d);
+    return PGM_OK;
+}
+
+pgm_status pgm_run_bp_multi(pgm_graph *g, int32_t n_samples, const float *log_pot, int32_t pot_per_sample,
+                            const float *evidence, float T, float damping, int32_t n_iters, float *msgs,
+                            void *stream) {
+    if (n_samples < 1) return fail(PGM_EINVAL, "n_samples must be >= 1");
+    pgm_status st = check_run_args(g, log_pot, evidence, T, damping, n_iters, msgs);
+    if (st != PGM_OK) return st;
+    if (n_iters == 0 || g->info.n_edge_states == 0) return PGM_OK;
+    const int64_t VS = g->info.n_var_states, ES = g->info.n_edge_states, P = g->info.n_potentials;
+    const bool ms = log_ratio_run(g, n_iters) && g->G.vin_tab4 != nullptr &&
+                    4 * (int64_t)g->info.n_vars * n_samples <= INT32_MAX;
+    if (!ms) {  // each sample on its own (same kernels, no shared index traffic)
+        for (int32_t s = 0; s < n_samples; ++s) {
+            st = pgm_run_bp(g, log_pot + (pot_per_sample ? (size_t)s * P : 0), evidence + (size_t)s * VS, T,
+                            damping, n_iters, msgs + (size_t)s * ES, stream);
+            if (st != PGM_OK) return st;
+        }
+        return PGM_OK;
+    }
+    DeviceGuard dg(g->device);
+    if (!dg.ok) return fail(PGM_ECUDA, "cudaSetDevice failed");
+    // Samples run together in chunks whose per-iteration exchange arrays (messages and
+    // per-variable totals, plus their table differences and evidence) fit in half the
+    // L2, so that the factor pass finds them there; a sample that alone needs more runs
+    // on its own, as pgm_run_bp (which keeps one sample's arrays in L2).
+    int l2 = 0;
+    if (cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, g->device) != cudaSuccess || l2 <= 0) l2 = 64 << 20;
+    const int64_t V = g->info.n_vars, F = g->info.n_edges / 2;
+    const int64_t per_sample = 4 * 4 * V + 8 * V + 8 * V + (pot_per_sample ? 12 * F : 0);
+    const int32_t chunk = (int32_t)std::min<int64_t>(n_samples, (int64_t)l2 / 2 / std::max<int64_t>(per_sample, 1));
+    if (chunk <= 1) {
+        for (int32_t smp = 0; smp < n_samples; ++smp) {
+            st = pgm_run_bp(g, log_pot + (pot_per_sample ? (size_t)smp * P : 0), evidence + (size_t)smp * VS, T,
+                            damping, n_iters, msgs + (size_t)smp * ES, stream);
+            if (st != PGM_OK) return st;
+        }
+        return PGM_OK;
+    }
+    st = ms_reserve(g, chunk);
+    if (st != PGM_OK) return st;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    for (int32_t s0 = 0; s0 < n_samples; s0 += chunk) {
+        const int S = std::min(chunk, n_samples - s0);
+        const int Sp = pot_per_sample ? S : 1;
+        const float *lp = log_pot + (pot_per_sample ? (size_t)s0 * P : 0);
+        const float *ev = evidence + (size_t)s0 * VS;
+        float *m = msgs + (size_t)s0 * ES;
+        cudaError_t e = launch_ms_prepare(g->G, g->P, S, Sp, P, lp, ev, m, g->ms_ev, g->ms_d, g->ms_prm, s);
+        if (e != cudaSuccess) return cuda_fail(e, "multi-sample prepare launch");
+        for (int it = 0; it < n_iters; ++it) {
+            e = launch_ms_iteration(g->G, g->P, S, Sp, P, lp, g->ms_prm, g->ms_ev, g->ms_d, g->ms_Dv, g->ms_lam, T,
+                                    damping, s);
+            if (e != cudaSuccess) return cuda_fail(e, "multi-sample iteration launch");
+        }
+        e = launch_ms_unpack(g->G, S, g->ms_d, m, s);
+        if (e != cudaSuccess) return cuda_fail(e, "multi-sample unpack launch");
+    }
+    return PGM_OK;
 }
 
 pgm_status pgm_run_bp(pgm_graph *g, const float *log_pot, const float *evidence, float T,

@@ -2,8 +2,8 @@
 //
 // Method (PGMax, arXiv 2202.04110): log-space loopy belief propagation with parallel
 // updates and damping (Sec. 3), enumeration factors over listed configurations
-// (Sec. 4.2), OR / AND factors with updates linear in the fan-in (Sec. 3), flat
-// message arrays updated by gather / scatter (Sec. 4), MAP decode (Sec. 4.1).
+// (Sec. 5.2), OR / AND factors with updates linear in the fan-in (Sec. 3), flat
+// message arrays updated by gather / scatter (Sec. 4), MAP decode (Sec. 5.1).
 //
 // One iteration is two passes over HBM-resident flat arrays:
 //   variable pass  b_v = e_v + sum_{f in N(v)} m_{f->v}            (k_var_*)
@@ -2202,6 +2202,150 @@ __global__ void __launch_bounds__(256) k_lr_unpack(DevGraph G, const float *__re
     }
 }
 
+// =====================================================================================
+// Many evidence / potential sets on one binary pairwise graph (pgm_run_bp_multi)
+// =====================================================================================
+//
+// S samples share the graph's structure (4-slot log-ratio layout). The arrays put the
+// sample index innermost: slot p of sample s at p S + s, variable v of sample s at
+// v S + s, table numbers of factor g at g Sp + s (Sp = S for per-sample tables, else 1
+// and shared). Thread (item) t = i S + s works on sample s of variable / factor i, so
+// consecutive threads read consecutive samples (coalesced) and the S threads of one
+// factor share its slot pair and, with a shared table, its table numbers. The
+// per-sample arithmetic is that of the single-sample kernels, step for step.
+
+// Per run: the evidence pairs in variable-major, sample-minor order (ev_s[v S + s]).
+__global__ void __launch_bounds__(256) k_ms_evidence(int V, int S, int64_t VS, const float *__restrict__ ev,
+                                                     float2 *__restrict__ ev_s) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)V * S) return;
+    const int v = (int)(t / S), s = (int)(t - (int64_t)v * S);
+    const float *e = ev + (size_t)s * VS + 2 * (size_t)v;
+    ev_s[t] = make_float2(__ldg(e), __ldg(e + 1));
+}
+
+// Per run: the log-ratios of each sample's messages ([S][2E] edge-state layout) into
+// slot-major, sample-minor d; unused slots 0 (as k_lr_pack_slot4).
+__global__ void __launch_bounds__(256) k_ms_pack(DevGraph G, int S, const float *__restrict__ m,
+                                                 float *__restrict__ d) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)G.V * S) return;
+    const int v = (int)(t / S), s = (int)(t - (int64_t)v * S);
+    const int4 q = __ldg(G.vin_tab4 + v);
+    const int es[4] = {q.x, q.y, q.z, q.w};
+    const float *ms = m + (size_t)s * G.ES;
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+        d[((size_t)k * G.V + v) * S + s] = es[k] >= 0 ? lr_encode(__ldg(ms + es[k]), __ldg(ms + es[k] + 1)) : 0.f;
+}
+
+// Per run: each sample's messages back into the [S][2E] edge-state layout.
+__global__ void __launch_bounds__(256) k_ms_unpack(DevGraph G, int S, const float *__restrict__ d,
+                                                   float *__restrict__ m) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)G.E * S) return;
+    const int s = (int)(t / G.E), e = (int)(t - (int64_t)s * G.E);
+    const float2 q = lr_decode(__ldg(d + (size_t)__ldg(G.lr_pos + e) * S + s));
+    float *ms = m + (size_t)s * G.ES + 2 * (size_t)e;
+    ms[0] = q.x;
+    ms[1] = q.y;
+}
+
+// Per run: table differences (k_lr_params) of each of the Sp table sets (pot + sp P),
+// at prm[g Sp + sp], prm[F Sp + g Sp + sp], prm[2 F Sp + g Sp + sp].
+__global__ void __launch_bounds__(256) k_ms_params(const EnumSeg *__restrict__ segs, int n_seg, int F, int Sp,
+                                                   int64_t P, const float *__restrict__ pot,
+                                                   float *__restrict__ prm) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t n = (int64_t)F * Sp;
+    if (t >= n) return;
+    const int g = (int)(t / Sp), sp = (int)(t - (int64_t)g * Sp);
+    const float4 q = lr_table(segs, n_seg, pot + (size_t)sp * P, g);
+    const bool fin = isfinite(q.x) & isfinite(q.y) & isfinite(q.z) & isfinite(q.w);
+    prm[t] = fin ? q.z - q.x : CUDART_NAN_F;
+    prm[n + t] = q.w - q.z;
+    prm[2 * n + t] = q.y - q.x;
+}
+
+// Variable pass (k_var_slot4_lr per sample): item t = v S + s.
+__global__ void __launch_bounds__(256) k_ms_var(int V, int S, const float2 *__restrict__ ev_s,
+                                                const float *__restrict__ d, float2 *__restrict__ Dv,
+                                                float *__restrict__ lam) {
+    pdl_launch_dependents();
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)V * S) return;
+    const float2 e = __ldcs(ev_s + t);
+    const size_t plane = (size_t)V * S;  // one slot index k across all variables and samples
+    pdl_wait();  // d is the previous factor pass's output
+    float dk[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) dk[k] = __ldcg(d + k * plane + t);
+    bool fin = isfinite(e.x) & isfinite(e.y);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) fin &= isfinite(dk[k]);
+    if (fin) {
+        FF D = ff_add_nc(ff_make(e.y), -e.x);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) D = ff_add_nc(D, dk[k]);
+        const float2 Df = make_float2(D.hi, D.lo);
+        bool ok = true;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) ok &= isfinite(lr_lam_from_D(Df, dk[k]));
+        if (ok) {
+            Dv[t] = Df;
+            return;
+        }
+    }
+    const int pos[4] = {(int)t, (int)(plane + t), (int)(2 * plane + t), (int)(3 * plane + t)};
+    lr_var_slow(e, dk, pos, 4, lam);
+    Dv[t] = make_float2(__uint_as_float(kDvSlow), 0.f);
+}
+
+// Factor pass (k_pair2_lr<MAXP, FROM_D> per sample): item t = g S + s, grid-stride.
+// The S items of factor g read its slot pair (one 8-byte load, the same address) and,
+// with Sp = 1, its table numbers; lam / d / Dv are gathered per sample at p S + s and
+// v S + s.
+template <bool MAXP>
+__global__ void __launch_bounds__(256) k_ms_pair(const EnumSeg *__restrict__ segs, int n_seg, int F, int V, int S,
+                                                 int Sp, int64_t P, const int2 *__restrict__ lr_pos2,
+                                                 const float *__restrict__ prm, const float *__restrict__ pot,
+                                                 const float2 *__restrict__ Dv, const float *__restrict__ lam,
+                                                 float *__restrict__ d, uint32_t *flags, float k, float Tln2,
+                                                 float damping) {
+    pdl_launch_dependents();
+    const int64_t n = (int64_t)F * S, np = (int64_t)F * Sp;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const float w = 1.f - damping;
+    bool waited = false;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += stride) {
+        const int g = (int)(t / S), s = (int)(t - (int64_t)g * S);
+        const int2 p = __ldg(lr_pos2 + g);
+        const int64_t q = (int64_t)g * Sp + (Sp > 1 ? s : 0);
+        const float c = __ldg(prm + q), al = __ldg(prm + np + q), be = __ldg(prm + 2 * np + q);
+        if (!waited) {
+            pdl_wait();  // Dv / lam are the variable pass's output
+            waited = true;
+        }
+        const size_t px = (size_t)p.x * S + s, py = (size_t)p.y * S + s;
+        const float mo0 = __ldcg(d + px), mo1 = __ldcg(d + py);
+        const int v0 = p.x - V * ((p.x >= V) + (p.x >= 2 * V) + (p.x >= 3 * V));
+        const int v1 = p.y - V * ((p.y >= V) + (p.y >= 2 * V) + (p.y >= 3 * V));
+        const float2 D0 = __ldcg(Dv + (size_t)v0 * S + s), D1 = __ldcg(Dv + (size_t)v1 * S + s);
+        const float l0 = __float_as_uint(D0.x) == kDvSlow ? __ldcg(lam + px) : lr_lam_from_D(D0, mo0);
+        const float l1 = __float_as_uint(D1.x) == kDvSlow ? __ldcg(lam + py) : lr_lam_from_D(D1, mo1);
+        const float dt0 = c + softplus_t<MAXP>(al + l1, k, Tln2) - softplus_t<MAXP>(be + l1, k, Tln2);
+        const float dt1 = be + softplus_t<MAXP>(al + c - be + l0, k, Tln2) - softplus_t<MAXP>(c + l0, k, Tln2);
+        float2 dn = make_float2(fmaf(damping, mo0, w * dt0), fmaf(damping, mo1, w * dt1));
+        if (!(isfinite(dn.x) && isfinite(dn.y) && l0 == l0 && l1 == l1)) {
+            const float4 tq = lr_table(segs, n_seg, pot + (Sp > 1 ? (size_t)s * P : 0), g);
+            const float t4[4] = {tq.x, tq.y, tq.z, tq.w};
+            dn = pair2_lr_exact<MAXP>(t4, l0, l1, mo0, mo1, k, Tln2, damping, flags);
+        }
+        d[px] = dn.x;
+        d[py] = dn.y;
+    }
+}
+
 }  // namespace
 
 // =====================================================================================
@@ -2365,6 +2509,46 @@ cudaError_t launch_lr_factor_pass(const DevGraph &G, const Plan &P, const float 
                                    Dv, lam, d, G.flags, k, Tln2, damping);
         if (e != cudaSuccess) return e;
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ms_prepare(const DevGraph &G, const Plan &P, int S, int Sp, int64_t n_pot,
+                              const float *log_pot, const float *ev, const float *msgs, float2 *ev_s, float *d,
+                              float *prm, cudaStream_t s) {
+    const int64_t nv = (int64_t)G.V * S, F = G.E / 2;
+    k_ms_evidence<<<(unsigned)((nv + 255) / 256), 256, 0, s>>>(G.V, S, G.VS, ev, ev_s);
+    k_ms_pack<<<(unsigned)((nv + 255) / 256), 256, 0, s>>>(G, S, msgs, d);
+    for (const FactorLaunch &L : P.factor)  // the one kPair2 launch: every factor
+        if (L.n_blocks > 0 && F > 0)
+            k_ms_params<<<(unsigned)((F * Sp + 255) / 256), 256, 0, s>>>(static_cast<const EnumSeg *>(L.segs),
+                                                                        L.n_seg, (int)F, Sp, n_pot, log_pot, prm);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ms_iteration(const DevGraph &G, const Plan &P, int S, int Sp, int64_t n_pot,
+                                const float *log_pot, const float *prm, const float2 *ev_s, float *d, float2 *Dv,
+                                float *lam, float T, float damping, cudaStream_t s) {
+    const int64_t nv = (int64_t)G.V * S, F = G.E / 2;
+    cudaError_t e = launch_pdl(k_ms_var, (int)((nv + 255) / 256), 256, s, G.V, S, ev_s, (const float *)d, Dv, lam);
+    if (e != cudaSuccess) return e;
+    const float k = T > 0.f ? (float)(1.4426950408889634 / (double)T) : 0.f;
+    const float Tln2 = (float)((double)T * 0.6931471805599453);
+    const int2 *pos2 = reinterpret_cast<const int2 *>(G.lr_pos);
+    for (const FactorLaunch &L : P.factor) {
+        if (L.n_blocks == 0) continue;
+        const EnumSeg *es = static_cast<const EnumSeg *>(L.segs);
+        const int blocks = (int)std::min<int64_t>(P.lr_blocks, (F * S + 255) / 256);
+        auto kern = T == 0.f ? k_ms_pair<true> : k_ms_pair<false>;
+        e = launch_pdl(kern, blocks, 256, s, es, L.n_seg, (int)F, G.V, S, Sp, n_pot, pos2, prm, log_pot,
+                       (const float2 *)Dv, (const float *)lam, d, G.flags, k, Tln2, damping);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ms_unpack(const DevGraph &G, int S, const float *d, float *msgs, cudaStream_t s) {
+    const int64_t n = (int64_t)G.E * S;
+    if (n > 0) k_ms_unpack<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(G, S, d, msgs);
     return cudaGetLastError();
 }
 

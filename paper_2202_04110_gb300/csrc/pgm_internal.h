@@ -190,6 +190,17 @@ cudaError_t launch_lr_params(const DevGraph &G, const Plan &P, const float *log_
 cudaError_t launch_lr_factor_pass(const DevGraph &G, const Plan &P, const float *log_pot, const float *prm,
                                   const float2 *Dv, const float *lam, float *d, float T, float damping,
                                   cudaStream_t s);
+// Many samples of one 4-slot log-ratio graph (sample index innermost; Sp = S for
+// per-sample potentials, else 1): per run, the transposed evidence ev_s[V S], packed
+// messages d[4V S] and table differences prm[3 F Sp]; per iteration, the variable pass
+// (Dv[V S], lam[4V S] for flagged variables) and the factor pass; at the end, unpack.
+cudaError_t launch_ms_prepare(const DevGraph &G, const Plan &P, int S, int Sp, int64_t n_pot,
+                              const float *log_pot, const float *ev, const float *msgs, float2 *ev_s, float *d,
+                              float *prm, cudaStream_t s);
+cudaError_t launch_ms_iteration(const DevGraph &G, const Plan &P, int S, int Sp, int64_t n_pot,
+                                const float *log_pot, const float *prm, const float2 *ev_s, float *d, float2 *Dv,
+                                float *lam, float T, float damping, cudaStream_t s);
+cudaError_t launch_ms_unpack(const DevGraph &G, int S, const float *d, float *msgs, cudaStream_t s);
 // Log-ratio pack (from the [2E] edge-state layout; unused slots 0) and unpack.
 cudaError_t launch_lr_pack(const DevGraph &G, const float *m, float *d, cudaStream_t s);
 cudaError_t launch_lr_unpack(const DevGraph &G, const float *d, float *m, cudaStream_t s);
