@@ -324,11 +324,19 @@ def measure_multi(args, binding, W, torch, dev):
     t_single = timed(run_singles, 3)
     same = all(torch.equal(msgs[s_], singles[s_]) for s_ in range(S))
     upd = S * args.iters * ES
+    # perturb-and-max-product: S samples (Gumbel-perturbed evidence, T=0, same iterations)
+    u = rng.uniform(1e-12, 1.0, (S, g.info["n_var_states"]))
+    noise = torch.as_tensor((-np.log(-np.log(u))).astype(np.float32)).to(dev)
+    ev0 = ev[0].contiguous()
+    t_pmp = timed(lambda: g.pmp_sample(lp, ev0, noise, 0.5, args.iters), 3)
     return {"workload": f"ising{side}x{side}, {S} evidence sets (h ~ N(0,1)), shared couplings, "
                         f"T=1, damping 0.5, {args.iters} iterations",
             "samples": S, "multi": upd / t_multi, "one_by_one": upd / t_single, "unit": UNIT,
             "multi_ms_per_call": 1e3 * t_multi, "one_by_one_ms": 1e3 * t_single,
-            "speedup": t_single / t_multi, "bitwise_equal_to_single_runs": bool(same)}
+            "speedup": t_single / t_multi, "bitwise_equal_to_single_runs": bool(same),
+            "pmp_samples_per_s": S / t_pmp,
+            "pmp": f"{S} perturb-and-max-product samples per call (Gumbel-perturbed evidence, T=0, "
+                   f"{args.iters} iterations, MAP decode), pgm_pmp_sample"}
 
 
 def serve_run(binding, templates, descs, arrivals, slots, budget):

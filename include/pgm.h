@@ -314,6 +314,22 @@ pgm_status pgm_run_bp_multi(pgm_graph *g, int32_t n_samples, const float *log_po
                             void *stream);
 
 /*
+ * Perturb-and-max-product samples (the sampler of the binary-deconvolution example of
+ * Sec. 5.2, after Lazaro-Gredilla et al. 2021): for each sample s, max-product (T = 0)
+ * LBP for n_iters iterations from zero messages on the model whose evidence is
+ * evidence + noise[s * n_var_states ...] (the caller draws the perturbations, e.g. Gumbel
+ * noise), then the MAP decode of that model into samples[s * n_vars ...]. msgs
+ * [n_samples * n_edge_states] is caller-owned working memory and holds each sample's
+ * final messages on return. Runs the samples through pgm_run_bp_multi. The first call
+ * with more samples than before allocates the perturbed-evidence buffer (n_samples *
+ * n_var_states floats), synchronising the device; it is kept until pgm_free.
+ * PGM_EINVAL for n_samples < 1, NULL noise / samples or the pgm_run_bp argument errors.
+ */
+pgm_status pgm_pmp_sample(pgm_graph *g, int32_t n_samples, const float *log_pot, const float *evidence,
+                          const float *noise, float damping, int32_t n_iters, float *msgs, int32_t *samples,
+                          void *stream);
+
+/*
  * Options of a graph. PGM_OPT_CUDA_GRAPH (default 1): pgm_run_bp with n_iters >= 2
  * (and per-pass profiling off) records the whole call -- every kernel of every
  * iteration and the final copy -- as a CUDA graph the first time it sees a given

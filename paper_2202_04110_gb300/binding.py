@@ -23,7 +23,7 @@ FLAG_NAN = 2
 # Every symbol include/pgm.h declares.
 EXPORTED = ["pgm_build", "pgm_build_batch", "pgm_batch_member", "pgm_check_desc", "pgm_free", "pgm_graph_info", "pgm_run_bp", "pgm_beliefs",
             "pgm_decode", "pgm_infer_host", "pgm_set_profiling", "pgm_pass_times",
-            "pgm_device_flags", "pgm_grid2_run_bp_noalloc", "pgm_run_bp_multi", "pgm_set_option", "pgm_get_option", "pgm_autotune",
+            "pgm_device_flags", "pgm_grid2_run_bp_noalloc", "pgm_run_bp_multi", "pgm_pmp_sample", "pgm_set_option", "pgm_get_option", "pgm_autotune",
             "pgm_launch_info", "pgm_grad", "pgm_serve_create", "pgm_serve_submit", "pgm_serve_poll",
             "pgm_serve_wait", "pgm_serve_stats", "pgm_serve_destroy", "pgm_last_error"]
 OPT_CUDA_GRAPH = 1
@@ -107,6 +107,8 @@ def load_library(path: str | None = None):
     lib.pgm_run_bp.argtypes = [vp, vp, vp, f32, f32, i32, vp, vp]
     lib.pgm_run_bp_multi.restype = i32
     lib.pgm_run_bp_multi.argtypes = [vp, i32, vp, i32, vp, f32, f32, i32, vp, vp]
+    lib.pgm_pmp_sample.restype = i32
+    lib.pgm_pmp_sample.argtypes = [vp, i32, vp, vp, vp, f32, i32, vp, vp, vp]
     lib.pgm_beliefs.restype = i32
     lib.pgm_beliefs.argtypes = [vp, vp, vp, vp, i32, vp]
     lib.pgm_decode.restype = i32
@@ -274,6 +276,22 @@ class Graph:
             float(T), float(damping), int(n_iters), _dptr(msgs, torch.float32, S * I["n_edge_states"], "msgs"),
             _stream_ptr(stream)))
         return msgs
+
+    def pmp_sample(self, log_pot, evidence, noise, damping: float, n_iters: int, stream=None):
+        """Perturb-and-max-product samples (pgm_pmp_sample): noise [S, n_var_states].
+        Returns (samples [S, n_vars] int32, messages [S, n_edge_states])."""
+        import torch
+        I = self.info
+        S = int(noise.shape[0])
+        msgs = torch.empty(S, I["n_edge_states"], dtype=torch.float32, device=noise.device)
+        out = torch.empty(S, I["n_vars"], dtype=torch.int32, device=noise.device)
+        lp = _dptr(log_pot, torch.float32, I["n_potentials"], "log_pot") if I["n_potentials"] else 0
+        check(load_library().pgm_pmp_sample(
+            self._h, S, lp, _dptr(evidence, torch.float32, I["n_var_states"], "evidence"),
+            _dptr(noise, torch.float32, S * I["n_var_states"], "noise"), float(damping), int(n_iters),
+            _dptr(msgs, torch.float32, S * I["n_edge_states"], "msgs"), _dptr(out, torch.int32, S * I["n_vars"], "samples"),
+            _stream_ptr(stream)))
+        return out, msgs
 
     def run_bp(self, log_pot, evidence, T: float, damping: float, n_iters: int, msgs, stream=None):
         """In-place: msgs <- n_iters LBP iterations from msgs (pgm_run_bp)."""

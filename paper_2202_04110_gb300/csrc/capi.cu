@@ -67,6 +67,9 @@ struct pgm_graph {
     int32_t ms_cap = 0;
     float2 *ms_ev = nullptr, *ms_Dv = nullptr;
     float *ms_d = nullptr, *ms_lam = nullptr, *ms_prm = nullptr;
+    // pgm_pmp_sample: perturbed evidence for up to pmp_cap samples (allocated on first use)
+    float *pmp_ev = nullptr;
+    int32_t pmp_cap = 0;
     int64_t lr_slots = 0;
     // pgm_infer_host buffers (allocated on first use)
     void *host_io_mem = nullptr;
@@ -545,6 +548,7 @@ void pgm_free(pgm_graph *g) {
     if (g->scratch_mem) cudaFree(g->scratch_mem);
     if (g->host_io_mem) cudaFree(g->host_io_mem);
     if (g->ms_mem) cudaFree(g->ms_mem);
+    if (g->pmp_ev) cudaFree(g->pmp_ev);
     for (cudaEvent_t e : g->events) cudaEventDestroy(e);
     drop_cached_runs(g);
     if (g->capture_stream) cudaStreamDestroy(g->capture_stream);
@@ -805,6 +809,44 @@ pgm_status pgm_run_bp_multi(pgm_graph *g, int32_t n_samples, const float *log_po
         }
         e = launch_ms_unpack(g->G, S, g->ms_d, m, s);
         if (e != cudaSuccess) return cuda_fail(e, "multi-sample unpack launch");
+    }
+    return PGM_OK;
+}
+
+pgm_status pgm_pmp_sample(pgm_graph *g, int32_t n_samples, const float *log_pot, const float *evidence,
+                          const float *noise, float damping, int32_t n_iters, float *msgs, int32_t *samples,
+                          void *stream) {
+    if (n_samples < 1) return fail(PGM_EINVAL, "n_samples must be >= 1");
+    if (!noise || !samples) return fail(PGM_EINVAL, "noise / samples is NULL");
+    pgm_status st = check_run_args(g, log_pot, evidence, 0.f, damping, n_iters, msgs);
+    if (st != PGM_OK) return st;
+    DeviceGuard dg(g->device);
+    if (!dg.ok) return fail(PGM_ECUDA, "cudaSetDevice failed");
+    const int64_t VS = g->info.n_var_states, ES = g->info.n_edge_states, V = g->info.n_vars;
+    if (g->pmp_cap < n_samples) {
+        if (g->pmp_ev) {
+            cudaError_t e = cudaDeviceSynchronize();  // the old buffer may still be in use
+            if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceSynchronize");
+            cudaFree(g->pmp_ev);
+            g->pmp_ev = nullptr;
+            g->pmp_cap = 0;
+        }
+        if (cudaMalloc(&g->pmp_ev, (size_t)VS * n_samples * sizeof(float)) != cudaSuccess) {
+            g->pmp_ev = nullptr;
+            return fail(PGM_ENOMEM, "cudaMalloc(perturbed evidence)");
+        }
+        g->pmp_cap = n_samples;
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e = launch_pmp_perturb(VS, n_samples, evidence, noise, g->pmp_ev, s);
+    if (e == cudaSuccess && ES > 0) e = cudaMemsetAsync(msgs, 0, (size_t)ES * n_samples * sizeof(float), s);
+    if (e != cudaSuccess) return cuda_fail(e, "perturb-and-max-product set-up");
+    st = pgm_run_bp_multi(g, n_samples, log_pot, 0, g->pmp_ev, 0.f, damping, n_iters, msgs, stream);
+    if (st != PGM_OK) return st;
+    for (int32_t smp = 0; smp < n_samples; ++smp) {
+        e = launch_var_pass(g->G, g->P, g->pmp_ev + (size_t)smp * VS, msgs + (size_t)smp * ES, nullptr, kVarDecode,
+                            samples + (size_t)smp * V, s);
+        if (e != cudaSuccess) return cuda_fail(e, "decode launch");
     }
     return PGM_OK;
 }

@@ -2346,6 +2346,14 @@ __global__ void __launch_bounds__(256) k_ms_pair(const EnumSeg *__restrict__ seg
     }
 }
 
+// Perturb-and-max-product: sample s's evidence = evidence + noise[s] (all samples).
+__global__ void __launch_bounds__(256) k_pmp_perturb(int64_t VS, int S, const float *__restrict__ ev,
+                                                     const float *__restrict__ noise, float *__restrict__ out) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= VS * S) return;
+    out[t] = __ldg(ev + t % VS) + __ldg(noise + t);
+}
+
 }  // namespace
 
 // =====================================================================================
@@ -2543,6 +2551,12 @@ cudaError_t launch_ms_iteration(const DevGraph &G, const Plan &P, int S, int Sp,
                        (const float2 *)Dv, (const float *)lam, d, G.flags, k, Tln2, damping);
         if (e != cudaSuccess) return e;
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pmp_perturb(int64_t VS, int S, const float *ev, const float *noise, float *out, cudaStream_t s) {
+    const int64_t n = VS * S;
+    if (n > 0) k_pmp_perturb<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(VS, S, ev, noise, out);
     return cudaGetLastError();
 }
 

@@ -201,6 +201,8 @@ cudaError_t launch_ms_iteration(const DevGraph &G, const Plan &P, int S, int Sp,
                                 const float *log_pot, const float *prm, const float2 *ev_s, float *d, float2 *Dv,
                                 float *lam, float T, float damping, cudaStream_t s);
 cudaError_t launch_ms_unpack(const DevGraph &G, int S, const float *d, float *msgs, cudaStream_t s);
+// out[s VS + i] = ev[i] + noise[s VS + i] (perturb-and-max-product evidence).
+cudaError_t launch_pmp_perturb(int64_t VS, int S, const float *ev, const float *noise, float *out, cudaStream_t s);
 // Log-ratio pack (from the [2E] edge-state layout; unused slots 0) and unpack.
 cudaError_t launch_lr_pack(const DevGraph &G, const float *m, float *d, cudaStream_t s);
 cudaError_t launch_lr_unpack(const DevGraph &G, const float *d, float *m, cudaStream_t s);
