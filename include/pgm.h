@@ -314,6 +314,23 @@ pgm_status pgm_run_bp_multi(pgm_graph *g, int32_t n_samples, const float *log_po
                             void *stream);
 
 /*
+ * pgm_run_bp with an early exit: up to max_iters iterations in chunks of check_every;
+ * the last iteration of each chunk is checked, residual = max over edge-states of
+ * |m_t - m_{t-1}| (messages are max-normalised, so this is scale-free; equal infinite
+ * entries count 0), and the run stops after the first chunk whose residual is <= tol.
+ * *iters_done (may be NULL) = iterations run, *residual (may be NULL) = the last
+ * residual checked (NaN if none was, i.e. max_iters = 0). The messages are those of
+ * chunked pgm_run_bp calls (chunk - 1 iterations, then 1), so on a graph with
+ * log-ratio iterations they can differ by rounding from one pgm_run_bp of the same
+ * length. Blocking: synchronises the stream after each chunk. The first call allocates
+ * an [n_edge_states] buffer and a pinned word, kept until pgm_free. PGM_EINVAL for
+ * check_every < 1, tol < 0 or NaN, or the pgm_run_bp argument errors.
+ */
+pgm_status pgm_run_bp_until(pgm_graph *g, const float *log_pot, const float *evidence, float T, float damping,
+                            int32_t max_iters, float tol, int32_t check_every, float *msgs, int32_t *iters_done,
+                            float *residual, void *stream);
+
+/*
  * Perturb-and-max-product samples (the sampler of the binary-deconvolution example of
  * Sec. 5.2, after Lazaro-Gredilla et al. 2021): for each sample s, max-product (T = 0)
  * LBP for n_iters iterations from zero messages on the model whose evidence is

@@ -67,6 +67,11 @@ struct pgm_graph {
     int32_t ms_cap = 0;
     float2 *ms_ev = nullptr, *ms_Dv = nullptr;
     float *ms_d = nullptr, *ms_lam = nullptr, *ms_prm = nullptr;
+    // pgm_run_bp_until: the messages before a chunk's last iteration [ES] and the residual
+    // word (device), its host copy (pinned); allocated on first use
+    float *until_prev = nullptr;
+    unsigned *until_res = nullptr;
+    unsigned *until_res_host = nullptr;
     // pgm_pmp_sample: perturbed evidence for up to pmp_cap samples (allocated on first use)
     float *pmp_ev = nullptr;
     int32_t pmp_cap = 0;
@@ -307,6 +312,9 @@ pgm_status check_run_args(pgm_graph *g, const float *log_pot, const float *evide
 }
 
 }  // namespace
+
+// Host-side quiet NaN (the residual before any check).
+static const float CUDART_NAN_F_HOST = __builtin_nanf("");
 
 extern "C" {
 
@@ -549,6 +557,8 @@ void pgm_free(pgm_graph *g) {
     if (g->host_io_mem) cudaFree(g->host_io_mem);
     if (g->ms_mem) cudaFree(g->ms_mem);
     if (g->pmp_ev) cudaFree(g->pmp_ev);
+    if (g->until_prev) cudaFree(g->until_prev);
+    if (g->until_res_host) cudaFreeHost(g->until_res_host);
     for (cudaEvent_t e : g->events) cudaEventDestroy(e);
     drop_cached_runs(g);
     if (g->capture_stream) cudaStreamDestroy(g->capture_stream);
@@ -810,6 +820,64 @@ pgm_status pgm_run_bp_multi(pgm_graph *g, int32_t n_samples, const float *log_po
         e = launch_ms_unpack(g->G, S, g->ms_d, m, s);
         if (e != cudaSuccess) return cuda_fail(e, "multi-sample unpack launch");
     }
+    return PGM_OK;
+}
+
+pgm_status pgm_run_bp_until(pgm_graph *g, const float *log_pot, const float *evidence, float T, float damping,
+                            int32_t max_iters, float tol, int32_t check_every, float *msgs, int32_t *iters_done,
+                            float *residual, void *stream) {
+    if (iters_done) *iters_done = 0;
+    if (residual) *residual = CUDART_NAN_F_HOST;
+    pgm_status st = check_run_args(g, log_pot, evidence, T, damping, max_iters, msgs);
+    if (st != PGM_OK) return st;
+    if (check_every < 1) return fail(PGM_EINVAL, "check_every must be >= 1");
+    if (!(tol >= 0.f)) return fail(PGM_EINVAL, "tol must be >= 0");
+    const int64_t ES = g->info.n_edge_states;
+    if (max_iters == 0 || ES == 0) {
+        if (residual && ES == 0) *residual = 0.f;
+        return PGM_OK;
+    }
+    DeviceGuard dg(g->device);
+    if (!dg.ok) return fail(PGM_ECUDA, "cudaSetDevice failed");
+    if (!g->until_prev) {
+        char *mem = nullptr;
+        if (cudaMalloc(&mem, align_up((size_t)ES * sizeof(float), 256) + 256) != cudaSuccess)
+            return fail(PGM_ENOMEM, "cudaMalloc(residual buffers)");
+        g->until_prev = reinterpret_cast<float *>(mem);
+        g->until_res = reinterpret_cast<unsigned *>(mem + align_up((size_t)ES * sizeof(float), 256));
+        if (cudaMallocHost(&g->until_res_host, sizeof(unsigned)) != cudaSuccess) {
+            cudaFree(g->until_prev);
+            g->until_prev = nullptr;
+            g->until_res = nullptr;
+            g->until_res_host = nullptr;
+            return fail(PGM_ENOMEM, "cudaMallocHost(residual word)");
+        }
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int32_t done = 0;
+    float res = CUDART_NAN_F_HOST;
+    while (done < max_iters) {
+        const int32_t n = std::min(check_every, max_iters - done);
+        if (n > 1) {
+            st = pgm_run_bp(g, log_pot, evidence, T, damping, n - 1, msgs, stream);
+            if (st != PGM_OK) return st;
+        }
+        cudaError_t e = cudaMemcpyAsync(g->until_prev, msgs, (size_t)ES * sizeof(float), cudaMemcpyDeviceToDevice, s);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(messages)");
+        st = pgm_run_bp(g, log_pot, evidence, T, damping, 1, msgs, stream);
+        if (st != PGM_OK) return st;
+        e = cudaMemsetAsync(g->until_res, 0, sizeof(unsigned), s);
+        if (e == cudaSuccess) e = launch_residual(ES, msgs, g->until_prev, g->until_res, g->n_sm, s);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(g->until_res_host, g->until_res, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return cuda_fail(e, "residual");
+        std::memcpy(&res, g->until_res_host, sizeof res);
+        done += n;
+        if (res <= tol) break;
+    }
+    if (iters_done) *iters_done = done;
+    if (residual) *residual = res;
     return PGM_OK;
 }
 

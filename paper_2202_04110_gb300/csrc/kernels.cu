@@ -2354,6 +2354,25 @@ __global__ void __launch_bounds__(256) k_pmp_perturb(int64_t VS, int S, const fl
     out[t] = __ldg(ev + t % VS) + __ldg(noise + t);
 }
 
+// Residual of one iteration: *out = max over i of |a[i] - b[i]| (NaN if any difference is
+// NaN; an entry -inf in both counts 0). Non-negative floats order as their bit patterns,
+// so the block maxima combine with an integer atomicMax on *out (zeroed by the caller).
+__global__ void __launch_bounds__(256) k_residual(int64_t n, const float *__restrict__ a,
+                                                  const float *__restrict__ b, unsigned *__restrict__ out) {
+    float mx = 0.f;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float x = __ldg(a + i), y = __ldg(b + i);
+        const float dlt = (x == y) ? 0.f : fabsf(x - y);  // equal infinities: 0
+        mx = (dlt != dlt || mx != mx) ? CUDART_NAN_F : fmaxf(mx, dlt);
+    }
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+        const float o = __shfl_xor_sync(0xffffffffu, mx, d);
+        mx = (o != o || mx != mx) ? CUDART_NAN_F : fmaxf(mx, o);
+    }
+    if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(mx));  // NaN (0x7fc00000) ranks above +inf
+}
+
 }  // namespace
 
 // =====================================================================================
@@ -2551,6 +2570,14 @@ cudaError_t launch_ms_iteration(const DevGraph &G, const Plan &P, int S, int Sp,
                        (const float2 *)Dv, (const float *)lam, d, G.flags, k, Tln2, damping);
         if (e != cudaSuccess) return e;
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_residual(int64_t n, const float *a, const float *b, unsigned *out, int n_sm, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    const int64_t want = (n + 255) / 256;
+    const int blocks = (int)std::min<int64_t>(want, (int64_t)n_sm * 8);
+    k_residual<<<blocks, 256, 0, s>>>(n, a, b, out);
     return cudaGetLastError();
 }
 

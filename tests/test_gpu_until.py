@@ -1,0 +1,85 @@
+"""Runs with an early exit (pgm_run_bp_until).
+
+The run stops after the first checked iteration whose residual max |m_t - m_{t-1}| is
+<= tol. The reported residual is recomputed here from an independent replay (t - 1
+iterations, a copy, one more iteration); the messages equal those of the same
+iterations run with pgm_run_bp, and track the FP64 oracle.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2202_04110_gb300 import workloads as W
+from tests._parity import assert_beliefs_close
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2202_04110_gb300 import build
+    build.build()
+    from paper_2202_04110_gb300 import binding
+    return binding
+
+
+def _t(a):
+    import torch
+    return torch.as_tensor(np.asarray(a, np.float32)).cuda()
+
+
+def test_early_exit_residual_and_messages(gpu):
+    p = W.potts_grid(20, 4, 2, T=1.0)  # edge-state iterations: chunking changes nothing
+    g = gpu.Graph(p.graph)
+    lp, ev = _t(p.log_pot), _t(p.evidence)
+    m = g.new_msgs()
+    done, res = g.run_bp_until(lp, ev, 1.0, 0.5, 400, 1e-5, 10, m)
+    assert done % 10 == 0 and 10 <= done < 400 and 0.0 <= res <= 1e-5
+    # the residual of the last checked iteration, recomputed
+    r = g.new_msgs()
+    g.run_bp(lp, ev, 1.0, 0.5, done - 1, r)
+    prev = r.cpu().numpy()
+    g.run_bp(lp, ev, 1.0, 0.5, 1, r)
+    assert np.array_equal(r.cpu().numpy(), m.cpu().numpy())
+    d = np.abs(r.cpu().numpy().astype(np.float64) - prev)
+    assert np.float32(d.max()) == np.float32(res)
+    # the previous check had not converged
+    if done == 10:
+        return
+    q = g.new_msgs()
+    g.run_bp(lp, ev, 1.0, 0.5, done - 11, q)
+    prev = q.cpu().numpy()
+    g.run_bp(lp, ev, 1.0, 0.5, 1, q)
+    assert np.abs(q.cpu().numpy() - prev).max() > 1e-5
+
+
+def test_early_exit_log_ratio_graph_tracks_oracle(gpu):
+    p = W.ising_grid(40, 50, 9, T=1.0)
+    g = gpu.Graph(p.graph)
+    m = g.new_msgs()
+    done, res = g.run_bp_until(_t(p.log_pot), _t(p.evidence), 1.0, 0.5, 300, 1e-6, 25, m)
+    assert done < 300 and res <= 1e-6
+    om, _ = oracle.run_bp(p.graph, p.log_pot, p.evidence, 1.0, 0.5, done)
+    _, onb, _, _ = oracle.beliefs(p.graph, p.evidence, om)
+    nb = g.beliefs(_t(p.evidence), m, True).cpu().numpy()
+    assert_beliefs_close(nb, onb, what=f"ising after {done} iterations")
+
+
+def test_no_convergence_and_arguments(gpu):
+    p = W.ising_grid(12, 12, 4, T=0.0)
+    g = gpu.Graph(p.graph)
+    lp, ev = _t(p.log_pot), _t(p.evidence)
+    m = g.new_msgs()
+    done, res = g.run_bp_until(lp, ev, 0.0, 0.5, 37, 0.0, 8, m)  # tol 0: runs to the end unless exact
+    assert done == 37 or res == 0.0
+    m = g.new_msgs()
+    assert g.run_bp_until(lp, ev, 1.0, 0.5, 0, 1e-3, 5, m)[0] == 0
+    assert math.isnan(g.run_bp_until(lp, ev, 1.0, 0.5, 0, 1e-3, 5, m)[1])
+    for bad in ((1e-3, 0), (-1.0, 5), (float("nan"), 5)):
+        with pytest.raises(gpu.PgmError):
+            g.run_bp_until(lp, ev, 1.0, 0.5, 10, bad[0], bad[1], m)
