@@ -88,22 +88,36 @@ def measured_peaks():
     return FALLBACK_HBM_GBS, "fallback"
 
 
-def kernel_source_hash() -> str:
-    with open(os.path.join(ROOT, "paper_2202_04110_gb300", "csrc", "kernels.cu"), "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()[:16]
+LR_KERNELS = ("k_pair2_lr", "k_var_slot4_lr", "k_var_csr_lr")
+
+
+def kernel_source_hash(kernel: str) -> str:
+    """sha256 (16 hex digits) of the source a kernel is built from: for the log-ratio
+    kernels, kernels.cu's helper prelude (before the first section), its log-ratio
+    section and the log-ratio launchers; for the others, the whole of kernels.cu."""
+    with open(os.path.join(ROOT, "paper_2202_04110_gb300", "csrc", "kernels.cu")) as f:
+        src = f.read()
+    if kernel in LR_KERNELS:
+        first = src.index("// =====")
+        a = src.index("// Binary pairwise graphs: log-ratio messages (Plan::lr)")
+        b = src.index("// Many evidence / potential sets on one binary pairwise graph")
+        c = src.index("static cudaError_t launch_pdl(")
+        d = src.index("cudaError_t launch_ms_prepare(")
+        src = src[:first] + src[a:b] + src[c:d]
+    return hashlib.sha256(src.encode()).hexdigest()[:16]
 
 
 def profiled_traffic(kernel: str, workload: str):
-    """dram bytes per launch recorded from an ncu capture in profiles/, if the kernel
-    source has not changed since."""
+    """dram bytes per launch recorded from an ncu capture in profiles/, if the kernel's
+    source (kernel_source_hash) has not changed since."""
     path = os.path.join(ROOT, "profiles", f"{kernel}_{workload}.md")
     try:
         txt = open(path).read()
     except OSError:
         return None
     m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", txt)
-    h = re.search(r"kernels_cu_sha256_16:\s*([0-9a-f]+)", txt)
-    if not m or not h or h.group(1) != kernel_source_hash():
+    h = re.search(r"source_sha256_16:\s*([0-9a-f]+)", txt)
+    if not m or not h or h.group(1) != kernel_source_hash(kernel):
         return None
     return float(m.group(1))
 
