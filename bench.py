@@ -466,11 +466,11 @@ def run_ours(args):
     g.pass_times()  # reset
     ES = I["n_edge_states"]
     updates_per_step = len(temps) * args.iters * ES
-    # log-ratio iterations (binary pairwise graph): one number per edge during the run,
-    # packed from / unpacked to msgs by one launch each
+    # log-ratio iterations (binary pairwise graph): one number per edge during the run;
+    # per run one pack, one table-differences and one unpack launch
     lr_min = g.get_option(binding.OPT_LOG_RATIO)
     lr = lr_min > 0 and args.iters >= lr_min
-    launches_per_step = len(temps) * (args.iters * I["launches_per_iter"] + 2 + (2 if lr else 0))
+    launches_per_step = len(temps) * (args.iters * I["launches_per_iter"] + 2 + (3 if lr else 0))
 
     if dist is not None:
         dist.barrier()
