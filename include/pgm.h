@@ -368,8 +368,8 @@ pgm_status pgm_pmp_sample(pgm_graph *g, int32_t n_samples, const float *log_pot,
  * the start (messages that are not max-normalised are normalised, which the update
  * does not see) and written back in the [n_edge_states] layout at the end. The
  * iteration is the same; results differ from the option-off path by rounding only.
- * Negative values: PGM_EINVAL. pgm_launch_info / launches_per_iter do not count the 2
- * conversion launches per run.
+ * Negative values: PGM_EINVAL. pgm_launch_info / launches_per_iter do not count the 3
+ * launches per run around the iterations (pack, table differences, unpack).
  */
 #define PGM_OPT_LOG_RATIO 2
 pgm_status pgm_set_option(pgm_graph *g, int32_t option, int64_t value);
