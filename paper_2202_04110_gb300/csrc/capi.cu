@@ -129,13 +129,13 @@ struct Packer {
     }
 };
 
-// Lanes that work on one variable: K for the K-lane kernels, else 1 (per block for
-// kVarBlock).
+// Lanes that work on one variable: K / 4 for the K-state group kernels (4 states per
+// lane), else 1 (per block for kVarBlock).
 int var_lanes(int kind) {
     switch (kind) {
-        case kVarGroup4: return 4;
-        case kVarGroup8: return 8;
-        case kVarGroup16: return 16;
+        case kVarGroup4: return 1;  // K / 4 lanes per variable, 4 states each
+        case kVarGroup8: return 2;
+        case kVarGroup16: return 4;
         default: return 1;
     }
 }

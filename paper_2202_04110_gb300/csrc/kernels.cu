@@ -545,54 +545,112 @@ __global__ void __launch_bounds__(256) k_var_tab4(DevGraph G, int n, const float
     }
 }
 
-// K lanes per variable (K = 4, 8, 16): lane x sums state x over the incoming edges
-// (coalesced across the group), float-float, ascending edge order; the best state is
-// found across the group (exact comparison, lowest state on ties).
+// K/4 lanes per variable (K = 4, 8, 16): lane l owns states 4l .. 4l+3 and sums them
+// over the incoming edges (16-byte loads where the offsets allow; a group's lanes read
+// 4K contiguous bytes per edge), float-float, ascending edge order; the best state is
+// found across the group (the largest rounded sum, lowest state on ties).
+template <int K>
+__device__ __forceinline__ void group_argmax_vec(float v, int idx, float &mx, int &arg) {
+    constexpr int L = K / 4;
+    mx = v;
+    arg = idx;
+#pragma unroll
+    for (int d = L / 2; d > 0; d >>= 1) {
+        const float ov = __shfl_xor_sync(0xffffffffu, mx, d, L);
+        const int oi = __shfl_xor_sync(0xffffffffu, arg, d, L);
+        if (ov > mx || (ov == mx && oi < arg)) {
+            mx = ov;
+            arg = oi;
+        }
+    }
+}
+
+template <int K>
+__device__ __forceinline__ float group_sum_vec(float v) {
+    constexpr int L = K / 4;
+#pragma unroll
+    for (int d = L / 2; d > 0; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d, L);
+    return v;
+}
+
 template <int K, int MODE>
 __global__ void __launch_bounds__(256) k_var_group(DevGraph G, const int32_t *__restrict__ list, int n,
                                                    const float *__restrict__ ev, const float *__restrict__ m,
                                                    float *__restrict__ out, int32_t *__restrict__ dec) {
-    const int x = threadIdx.x & (K - 1);
-    const int t_raw = (blockIdx.x * blockDim.x + threadIdx.x) / K;
+    constexpr int L = K / 4;
+    const int l = threadIdx.x & (L - 1);
+    const int t_raw = (blockIdx.x * blockDim.x + threadIdx.x) / L;
     const bool valid = t_raw < n;
     const int t = valid ? t_raw : n - 1;
     const int v = list ? __ldg(list + t) : t;
     const int vs = __ldg(G.vs_off + v);
     const int k0 = __ldg(G.vin_off + v), k1 = __ldg(G.vin_off + v + 1);
-    FF s = ff_make(__ldg(ev + vs + x));
-    for (int k = k0; k < k1; ++k) s = ff_add(s, __ldg(m + __ldg(G.vin_es + k) + x));
+    float e4[4];
+    load_n<4>(e4, ev + vs + 4 * l);
+    FF s[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) s[j] = ff_make(e4[j]);
+    for (int k = k0; k < k1; ++k) {
+        float q[4];
+        load_n<4>(q, m + __ldg(G.vin_es + k) + 4 * l);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) s[j] = ff_add(s[j], q[j]);
+    }
     // best state: the largest rounded sum, lowest state among equal ones (states whose
     // float-float sums differ by less than one FP32 ulp count as tied)
-    const float rs = s.hi + s.lo;
-    float mx = rs;
+    float rs[4];
+    float lmx = kNegInf;  // NaN states never win; all -inf (or NaN): the lowest state
+    int larg = 4 * l;
 #pragma unroll
-    for (int d = K / 2; d > 0; d >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, d, K));
-    const unsigned gshift = (threadIdx.x & 31) & ~(K - 1);
-    const unsigned at_max = (__ballot_sync(0xffffffffu, rs == mx) >> gshift) & ((1u << K) - 1u);
-    const int arg = at_max ? __ffs(at_max) - 1 : 0;
-    const FF best{__shfl_sync(0xffffffffu, s.hi, arg, K), __shfl_sync(0xffffffffu, s.lo, arg, K)};
+    for (int j = 0; j < 4; ++j) {
+        rs[j] = s[j].hi + s[j].lo;
+        if (rs[j] > lmx) {
+            lmx = rs[j];
+            larg = 4 * l + j;
+        }
+    }
+    float mx;
+    int arg;
+    group_argmax_vec<K>(lmx, larg, mx, arg);
     if constexpr (MODE == kVarDecode) {
-        if (valid && x == 0) dec[v] = arg;
+        if (valid && l == 0) dec[v] = arg;
         return;
     }
     if constexpr (MODE == kVarBeliefs) {
-        if (valid) out[vs + x] = s.hi + s.lo;
+        if (valid) store_n<4>(out + vs + 4 * l, rs);
         return;
     }
+    // the best state's float-float sum, from the lane that owns it
+    const int jb = arg & 3;
+    const float bh = jb == 0 ? s[0].hi : jb == 1 ? s[1].hi : jb == 2 ? s[2].hi : s[3].hi;
+    const float bl = jb == 0 ? s[0].lo : jb == 1 ? s[1].lo : jb == 2 ? s[2].lo : s[3].lo;
+    const FF best{__shfl_sync(0xffffffffu, bh, arg >> 2, L), __shfl_sync(0xffffffffu, bl, arg >> 2, L)};
     const bool dead = best.hi == kNegInf;  // every state -inf
-    const float r = dead ? kNegInf : (x == arg ? 0.f : ff_diff(s, best));
-    if constexpr (MODE == kVarIter) {
-        if (valid) out[vs + x] = r;
-    } else {
-        float acc = (x == arg || dead) ? 0.f : expf(r);
+    float r[4];
 #pragma unroll
-        for (int d = K / 2; d > 0; d >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, d, K);
-        const bool nan = __any_sync(0xffffffffu, s.hi != s.hi);
-        if (valid && x == 0) {
+    for (int j = 0; j < 4; ++j) r[j] = dead ? kNegInf : (4 * l + j == arg ? 0.f : ff_diff(s[j], best));
+    if constexpr (MODE == kVarIter) {
+        if (valid) store_n<4>(out + vs + 4 * l, r);
+    } else {
+        float acc = 0.f;  // sum over the other states of e^r (the best state adds 1)
+        bool nan = false;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            if (!(4 * l + j == arg || dead)) acc += expf(r[j]);
+            nan |= (s[j].hi != s[j].hi);
+        }
+        acc = group_sum_vec<K>(acc);
+        nan = __any_sync(0xffffffffu, nan);
+        if (valid && l == 0) {
             if (dead) atomicOr(G.flags, kFlagContradiction);
             if (nan) atomicOr(G.flags, kFlagNaN);
         }
-        if (valid) out[vs + x] = dead ? kNegInf : r - log1pf(acc);
+        if (valid) {
+            const float z = log1pf(acc);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) r[j] = dead ? kNegInf : r[j] - z;
+            store_n<4>(out + vs + 4 * l, r);
+        }
     }
 }
 

@@ -110,7 +110,7 @@ enum VarKind : int32_t {
     kVarGeneric = 0,  // thread per variable, any K
     kVarBlock = 1,    // block per variable, degree > kVarBlockDegree
     kVarBinary = 2,   // thread per binary variable (float2 loads)
-    kVarGroup4 = 3,   // K lanes per variable, K = 4, 8, 16
+    kVarGroup4 = 3,   // K / 4 lanes per variable (4 states each), K = 4, 8, 16
     kVarGroup8 = 4,
     kVarGroup16 = 5,
     kNumVarKinds = 6
