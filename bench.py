@@ -51,6 +51,8 @@ def parse_args():
     ap.add_argument("--no-batch", action="store_true", help="skip the batched vs per-graph measurement")
     ap.add_argument("--batch-grids", type=int, default=256)
     ap.add_argument("--no-multi", action="store_true", help="skip the multi-evidence measurement")
+    ap.add_argument("--batch-probe", type=int, default=0,
+                    help="only run the batched workload for N iterations (3 runs, no CUDA graphs; for ncu)")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
     ap.add_argument("--serve-rate", type=float, default=2000.0, help="mean Poisson arrival rate (requests/s)")
     ap.add_argument("--serve-duration", type=float, default=1.0, help="seconds of arrivals per serving run")
@@ -607,9 +609,33 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def batch_probe(args):
+    """A short, uncaptured run of the batched workload for ncu captures of its kernels:
+    two warm-up runs and one measured run of `--batch-probe` iterations each, CUDA graphs
+    off (one launch per kernel per pass). Prints one JSON line with the launch shapes."""
+    import torch
+    from paper_2202_04110_gb300 import binding, build
+    from paper_2202_04110_gb300 import workloads as W
+    build.build()
+    batch, members = W.potts_rbm_batch(seed=0, n_grids=args.batch_grids, n_iters=100)
+    lp = torch.as_tensor(batch.log_pot).cuda()
+    ev = torch.as_tensor(batch.evidence).cuda()
+    g = binding.Graph([m.graph for m in members])
+    g.set_option(binding.OPT_CUDA_GRAPH, 0)
+    m = g.new_msgs()
+    for _ in range(3):
+        m.zero_()
+        g.run_bp(lp, ev, 1.0, 0.5, args.batch_probe, m)
+    torch.cuda.synchronize()
+    print(json.dumps({"batch_probe": args.batch_probe, "launches_per_iter": g.info["launches_per_iter"],
+                      "launch_shapes": g.launches()}))
+
+
 def main():
     args = parse_args()
-    if args.impl == "reference":
+    if args.batch_probe:
+        batch_probe(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)
