@@ -51,6 +51,7 @@ def parse_args():
     ap.add_argument("--no-batch", action="store_true", help="skip the batched vs per-graph measurement")
     ap.add_argument("--batch-grids", type=int, default=256)
     ap.add_argument("--no-multi", action="store_true", help="skip the multi-evidence measurement")
+    ap.add_argument("--no-grad", action="store_true", help="skip the gradient measurement")
     ap.add_argument("--batch-probe", type=int, default=0,
                     help="only run the batched workload for N iterations (3 runs, no CUDA graphs; for ncu)")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
@@ -355,6 +356,50 @@ def measure_multi(args, binding, W, torch, dev):
                    f"{args.iters} iterations, MAP decode), pgm_pmp_sample"}
 
 
+def measure_grad(args, binding, W, torch, dev):
+    """The gradient of the serving + gradient configuration: L = sum(g * normalised
+    log-beliefs) after 100 sum-product iterations (damping 0.5) of a 64x64 Ising grid,
+    w.r.t. the log-potentials and the evidence (pgm_grad, reverse mode through the
+    unrolled iterations, a message checkpoint every 10 iterations), against the forward
+    run alone (pgm_run_bp + normalised beliefs)."""
+    import numpy as np
+    p = W.ising_grid(64, 64, 0, T=1.0, n_iters=100)
+    g = binding.Graph(p.graph)
+    lp = torch.as_tensor(p.log_pot).to(dev)
+    ev = torch.as_tensor(p.evidence).to(dev)
+    gnb = torch.as_tensor(np.random.default_rng(1).standard_normal(p.graph.n_var_states).astype(np.float32)).to(dev)
+    msgs = g.new_msgs()
+    stream = torch.cuda.current_stream()
+
+    def forward():
+        msgs.zero_()
+        g.run_bp(lp, ev, 1.0, 0.5, 100, msgs)
+        g.beliefs(ev, msgs, True)
+
+    def backward():
+        g.grad(lp, ev, 1.0, 0.5, 100, 10, gnb)
+
+    def timed(fn, reps):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    t_fwd = timed(forward, 20)
+    t_grad = timed(backward, 20)
+    return {"workload": "ising64x64, T=1, damping 0.5, 100 iterations, checkpoint every 10, "
+                        "cotangent N(0,1) on the normalised log-beliefs",
+            "grad_ms": t_grad, "forward_ms": t_fwd, "grad_over_forward": t_grad / t_fwd,
+            "call": "pgm_grad (forward with checkpoints + reverse pass)"}
+
+
 def serve_run(binding, templates, descs, arrivals, slots, budget):
     """Submit `arrivals` on schedule to a server with `slots` in-flight requests; wait
     for all; latencies (s) and throughput (updates/s over first submission to last
@@ -594,6 +639,8 @@ def run_ours(args):
         line["batched"] = measure_batched(args, binding, W, torch, dev)
     if not args.no_multi:
         line["multi_evidence"] = measure_multi(args, binding, W, torch, dev)
+    if not args.no_grad:
+        line["gradient"] = measure_grad(args, binding, W, torch, dev)
     if not args.no_serve and world == 1:
         line["serving"] = measure_serving(args, binding, W)
 

@@ -242,7 +242,11 @@ pgm_status pgm_pass_times(pgm_graph *g, double *var_ms, double *factor_ms, int64
  * unrolled iterations: the forward keeps a checkpoint of the messages every ckpt_every
  * iterations and the reverse pass recomputes each segment from its checkpoint
  * (device scratch of (ceil(n_iters / ckpt_every) + min(ckpt_every, n_iters) + 6) x
- * n_edge_states floats, stream-ordered allocation freed before the call's work ends).
+ * n_edge_states floats). With PGM_OPT_CUDA_GRAPH on (default) the scratch is kept with
+ * the graph (grown when a call needs more, which synchronises the device) and the whole
+ * call is recorded as a CUDA graph on first use of an argument tuple (up to 4 kept) and
+ * replayed on the caller's stream; with it off, the scratch is a stream-ordered
+ * allocation freed before the call's work ends.
  * Gradients of log-potentials shared by a group are summed over its factors in
  * arbitrary order (atomic adds); everything else is deterministic.
  * Errors: PGM_ENOTSUP for T = 0 (max-product is not differentiable) or graphs with

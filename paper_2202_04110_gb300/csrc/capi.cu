@@ -112,6 +112,18 @@ struct pgm_graph {
     int32_t log_ratio_min_iters = 4;  // PGM_OPT_LOG_RATIO
     cudaStream_t capture_stream = nullptr;
     std::vector<CachedRun> runs;
+    // pgm_grad as CUDA graphs (PGM_OPT_CUDA_GRAPH): persistent work buffers and the
+    // recorded calls, keyed by their arguments
+    void *grad_mem = nullptr;
+    size_t grad_bytes = 0;
+    struct CachedGrad {
+        const float *log_pot, *evidence, *d_beliefs;
+        float *d_log_pot, *d_evidence;
+        uint32_t T_bits, damping_bits;
+        int32_t n_iters, ckpt_every;
+        cudaGraphExec_t exec;
+    };
+    std::vector<CachedGrad> grads;
     uint64_t use_clock = 0;
 };
 
@@ -556,6 +568,7 @@ void pgm_free(pgm_graph *g) {
     if (g->scratch_mem) cudaFree(g->scratch_mem);
     if (g->host_io_mem) cudaFree(g->host_io_mem);
     if (g->ms_mem) cudaFree(g->ms_mem);
+    if (g->grad_mem) cudaFree(g->grad_mem);
     if (g->pmp_ev) cudaFree(g->pmp_ev);
     if (g->until_prev) cudaFree(g->until_prev);
     if (g->until_res_host) cudaFreeHost(g->until_res_host);
@@ -728,7 +741,10 @@ static pgm_status cached_run(pgm_graph *g, const float *log_pot, const float *ev
     return PGM_OK;
 }
 
+static void drop_cached_grads(pgm_graph *g);
+
 static void drop_cached_runs(pgm_graph *g) {
+    drop_cached_grads(g);
     for (auto &r : g->runs) {
         collect_run_times(g, r);
         destroy_run(r);
@@ -1117,29 +1133,24 @@ static pgm_status one_iteration(pgm_graph *g, const float *log_pot, const float 
     return PGM_OK;
 }
 
-pgm_status pgm_grad(pgm_graph *g, const float *log_pot, const float *evidence, float T, float damping,
-                    int32_t n_iters, int32_t ckpt_every, const float *d_beliefs, float *d_log_pot,
-                    float *d_evidence, void *stream) {
-    if (!g) return fail(PGM_EINVAL, "graph is NULL");
-    if (!(T > 0.f) || !std::isfinite(T))
-        return fail(T == 0.f ? PGM_ENOTSUP : PGM_EINVAL, "pgm_grad needs a finite T > 0 (max-product has no gradient)");
-    if (g->has_logic) return fail(PGM_ENOTSUP, "pgm_grad supports enumeration factors only");
-    if (!(damping >= 0.f && damping < 1.f)) return fail(PGM_EINVAL, "damping must be in [0, 1)");
-    if (n_iters < 0 || ckpt_every < 1) return fail(PGM_EINVAL, "n_iters >= 0 and ckpt_every >= 1 required");
-    if (!evidence || !d_beliefs || !d_evidence || (g->info.n_potentials > 0 && (!log_pot || !d_log_pot)))
-        return fail(PGM_EINVAL, "NULL argument");
-    DeviceGuard dg(g->device);
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
+// Work buffers of a gradient: checkpoints, one segment of recomputed states, two message
+// buffers, two adjoint buffers, the variable-to-factor adjoint, the damping adjoint.
+static size_t grad_work_bytes(const pgm_graph *g, int32_t n_iters, int32_t ckpt_every) {
     const int64_t ES = std::max<int64_t>(g->info.n_edge_states, 1);
     const size_t esb = align_up((size_t)ES * sizeof(float), 256);
     const int n_ck = n_iters > 0 ? (n_iters + ckpt_every - 1) / ckpt_every : 0;
     const int seg_len = std::min(ckpt_every, std::max(n_iters, 1));
-    // checkpoints, one segment of recomputed states, two message buffers, two adjoint
-    // buffers, the variable-to-factor adjoint
-    const size_t total = esb * ((size_t)n_ck + (size_t)seg_len + 6);
-    char *mem = nullptr;
-    cudaError_t e = cudaMallocAsync(&mem, total, s);
-    if (e != cudaSuccess) return fail(PGM_ENOMEM, std::string("cudaMallocAsync(grad): ") + cudaGetErrorString(e));
+    return esb * ((size_t)n_ck + (size_t)seg_len + 6);
+}
+
+// Enqueues the whole gradient on s, with its work buffers at mem.
+static pgm_status enqueue_grad(pgm_graph *g, const float *log_pot, const float *evidence, float T, float damping,
+                               int32_t n_iters, int32_t ckpt_every, const float *d_beliefs, float *d_log_pot,
+                               float *d_evidence, char *mem, cudaStream_t s) {
+    const int64_t ES = std::max<int64_t>(g->info.n_edge_states, 1);
+    const size_t esb = align_up((size_t)ES * sizeof(float), 256);
+    const int n_ck = n_iters > 0 ? (n_iters + ckpt_every - 1) / ckpt_every : 0;
+    const int seg_len = std::min(ckpt_every, std::max(n_iters, 1));
     auto buf = [&](size_t i) { return reinterpret_cast<float *>(mem + i * esb); };
     float *ck = buf(0), *rec = buf(n_ck), *mA = buf(n_ck + seg_len), *mB = buf(n_ck + seg_len + 1);
     float *adjA = buf(n_ck + seg_len + 2), *adjB = buf(n_ck + seg_len + 3), *dv = buf(n_ck + seg_len + 4);
@@ -1147,6 +1158,7 @@ pgm_status pgm_grad(pgm_graph *g, const float *log_pot, const float *evidence, f
     auto ckp = [&](int i) { return ck + (size_t)i * (esb / sizeof(float)); };
     auto recp = [&](int i) { return rec + (size_t)i * (esb / sizeof(float)); };
     pgm_status st = PGM_OK;
+    cudaError_t e = cudaSuccess;
     if (g->info.n_potentials > 0) e = cudaMemsetAsync(d_log_pot, 0, (size_t)g->info.n_potentials * sizeof(float), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(mA, 0, esb, s);
     if (e != cudaSuccess) st = cuda_fail(e, "cudaMemsetAsync(grad)");
@@ -1182,8 +1194,88 @@ pgm_status pgm_grad(pgm_graph *g, const float *log_pot, const float *evidence, f
             std::swap(adjA, adjB);
         }
     }
-    cudaFreeAsync(mem, s);
     return st;
+}
+
+static void drop_cached_grads(pgm_graph *g) {
+    for (auto &c : g->grads) cudaGraphExecDestroy(c.exec);
+    g->grads.clear();
+}
+
+pgm_status pgm_grad(pgm_graph *g, const float *log_pot, const float *evidence, float T, float damping,
+                    int32_t n_iters, int32_t ckpt_every, const float *d_beliefs, float *d_log_pot,
+                    float *d_evidence, void *stream) {
+    if (!g) return fail(PGM_EINVAL, "graph is NULL");
+    if (!(T > 0.f) || !std::isfinite(T))
+        return fail(T == 0.f ? PGM_ENOTSUP : PGM_EINVAL, "pgm_grad needs a finite T > 0 (max-product has no gradient)");
+    if (g->has_logic) return fail(PGM_ENOTSUP, "pgm_grad supports enumeration factors only");
+    if (!(damping >= 0.f && damping < 1.f)) return fail(PGM_EINVAL, "damping must be in [0, 1)");
+    if (n_iters < 0 || ckpt_every < 1) return fail(PGM_EINVAL, "n_iters >= 0 and ckpt_every >= 1 required");
+    if (!evidence || !d_beliefs || !d_evidence || (g->info.n_potentials > 0 && (!log_pot || !d_log_pot)))
+        return fail(PGM_EINVAL, "NULL argument");
+    DeviceGuard dg(g->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const size_t total = grad_work_bytes(g, n_iters, ckpt_every);
+    if (!g->use_cuda_graph || g->ordered) {  // stream-ordered work buffers, direct launches
+        char *mem = nullptr;
+        cudaError_t e = cudaMallocAsync(&mem, total, s);
+        if (e != cudaSuccess) return fail(PGM_ENOMEM, std::string("cudaMallocAsync(grad): ") + cudaGetErrorString(e));
+        pgm_status st = enqueue_grad(g, log_pot, evidence, T, damping, n_iters, ckpt_every, d_beliefs, d_log_pot,
+                                     d_evidence, mem, s);
+        cudaFreeAsync(mem, s);
+        return st;
+    }
+    // CUDA graph of the whole call on persistent work buffers (grown when needed)
+    if (g->grad_bytes < total) {
+        cudaError_t e = cudaDeviceSynchronize();  // the old buffers may be in use by a replay
+        if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceSynchronize");
+        drop_cached_grads(g);
+        if (g->grad_mem) cudaFree(g->grad_mem);
+        g->grad_mem = nullptr;
+        g->grad_bytes = 0;
+        if (cudaMalloc(&g->grad_mem, total) != cudaSuccess) {
+            g->grad_mem = nullptr;
+            return fail(PGM_ENOMEM, "cudaMalloc(grad)");
+        }
+        g->grad_bytes = total;
+    }
+    uint32_t tb, db;
+    std::memcpy(&tb, &T, sizeof tb);
+    std::memcpy(&db, &damping, sizeof db);
+    cudaGraphExec_t exec = nullptr;
+    for (auto &c : g->grads)
+        if (c.log_pot == log_pot && c.evidence == evidence && c.d_beliefs == d_beliefs && c.d_log_pot == d_log_pot &&
+            c.d_evidence == d_evidence && c.T_bits == tb && c.damping_bits == db && c.n_iters == n_iters &&
+            c.ckpt_every == ckpt_every)
+            exec = c.exec;
+    if (!exec) {
+        if (!g->capture_stream) {
+            cudaError_t e = cudaStreamCreateWithFlags(&g->capture_stream, cudaStreamNonBlocking);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaStreamCreate");
+        }
+        cudaError_t e = cudaStreamBeginCapture(g->capture_stream, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamBeginCapture");
+        pgm_status st = enqueue_grad(g, log_pot, evidence, T, damping, n_iters, ckpt_every, d_beliefs, d_log_pot,
+                                     d_evidence, static_cast<char *>(g->grad_mem), g->capture_stream);
+        cudaGraph_t graph = nullptr;
+        e = cudaStreamEndCapture(g->capture_stream, &graph);
+        if (st != PGM_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return st;
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+        e = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+        if (g->grads.size() >= 4) {
+            cudaGraphExecDestroy(g->grads.front().exec);
+            g->grads.erase(g->grads.begin());
+        }
+        g->grads.push_back({log_pot, evidence, d_beliefs, d_log_pot, d_evidence, tb, db, n_iters, ckpt_every, exec});
+    }
+    cudaError_t e = cudaGraphLaunch(exec, s);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
+    return PGM_OK;
 }
 
 pgm_status pgm_set_option(pgm_graph *g, int32_t option, int64_t value) {
