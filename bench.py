@@ -400,6 +400,31 @@ def measure_grad(args, binding, W, torch, dev):
             "call": "pgm_grad (forward with checkpoints + reverse pass)"}
 
 
+def measure_until(args, binding, W, torch, dev):
+    """Early-exit runs (pgm_run_bp_until) on a 64x64 Ising grid, T=1, damping 0.5, up to
+    400 iterations, residual checked every 10, tol 1e-6: the device loop (CUDA graph with a
+    conditional while node) vs the host-checked chunks (CUDA graphs off)."""
+    p = W.ising_grid(64, 64, 0, T=1.0)
+    lp = torch.as_tensor(p.log_pot).to(dev)
+    ev = torch.as_tensor(p.evidence).to(dev)
+    out = {"workload": "ising64x64, T=1, damping 0.5, max 400 iterations, check every 10, tol 1e-6"}
+    for name, graphs in (("device_loop", 1), ("host_checked", 0)):
+        g = binding.Graph(p.graph)
+        g.set_option(binding.OPT_CUDA_GRAPH, graphs)
+        m = g.new_msgs()
+        for _ in range(3):
+            m.zero_()
+            done, res = g.run_bp_until(lp, ev, 1.0, 0.5, 400, 1e-6, 10, m)
+        t0 = time.perf_counter()
+        for _ in range(10):
+            m.zero_()
+            done, res = g.run_bp_until(lp, ev, 1.0, 0.5, 400, 1e-6, 10, m)
+        out[name + "_ms"] = (time.perf_counter() - t0) / 10 * 1e3
+        out["iterations"] = done
+    out["speedup"] = out["host_checked_ms"] / out["device_loop_ms"]
+    return out
+
+
 def serve_run(binding, templates, descs, arrivals, slots, budget):
     """Submit `arrivals` on schedule to a server with `slots` in-flight requests; wait
     for all; latencies (s) and throughput (updates/s over first submission to last
@@ -641,6 +666,7 @@ def run_ours(args):
         line["multi_evidence"] = measure_multi(args, binding, W, torch, dev)
     if not args.no_grad:
         line["gradient"] = measure_grad(args, binding, W, torch, dev)
+        line["early_exit"] = measure_until(args, binding, W, torch, dev)
     if not args.no_serve and world == 1:
         line["serving"] = measure_serving(args, binding, W)
 

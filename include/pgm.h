@@ -326,8 +326,12 @@ pgm_status pgm_run_bp_multi(pgm_graph *g, int32_t n_samples, const float *log_po
  * residual checked (NaN if none was, i.e. max_iters = 0). The messages are those of
  * chunked pgm_run_bp calls (chunk - 1 iterations, then 1), so on a graph with
  * log-ratio iterations they can differ by rounding from one pgm_run_bp of the same
- * length. Blocking: synchronises the stream after each chunk. The first call allocates
- * an [n_edge_states] buffer and a pinned word, kept until pgm_free. PGM_EINVAL for
+ * length. With PGM_OPT_CUDA_GRAPH on, the full chunks run as one CUDA graph whose
+ * conditional while node repeats a chunk on the device while its residual is above tol
+ * (recorded once per argument tuple, up to 4 kept): the call synchronises the stream
+ * once, plus once for a last chunk shorter than check_every; with it off, after each
+ * chunk. Blocking. The first call allocates an [n_edge_states] buffer and two pinned
+ * words, kept until pgm_free. PGM_EINVAL for
  * check_every < 1, tol < 0 or NaN, or the pgm_run_bp argument errors.
  */
 pgm_status pgm_run_bp_until(pgm_graph *g, const float *log_pot, const float *evidence, float T, float damping,

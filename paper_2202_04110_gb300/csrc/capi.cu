@@ -70,8 +70,17 @@ struct pgm_graph {
     // pgm_run_bp_until: the messages before a chunk's last iteration [ES] and the residual
     // word (device), its host copy (pinned); allocated on first use
     float *until_prev = nullptr;
-    unsigned *until_res = nullptr;
-    unsigned *until_res_host = nullptr;
+    unsigned *until_res = nullptr;       // residual bits; the next word counts iterations done
+    unsigned *until_res_host = nullptr;  // 2 words
+    // device-side early-exit runs (conditional while node), keyed by their arguments
+    struct CachedUntil {
+        const float *log_pot, *evidence;
+        float *msgs;
+        uint32_t T_bits, damping_bits, tol_bits;
+        int32_t check_every, limit;
+        cudaGraphExec_t exec;
+    };
+    std::vector<CachedUntil> untils;
     // pgm_pmp_sample: perturbed evidence for up to pmp_cap samples (allocated on first use)
     float *pmp_ev = nullptr;
     int32_t pmp_cap = 0;
@@ -743,8 +752,14 @@ static pgm_status cached_run(pgm_graph *g, const float *log_pot, const float *ev
 
 static void drop_cached_grads(pgm_graph *g);
 
+static void drop_cached_untils(pgm_graph *g) {
+    for (auto &u : g->untils) cudaGraphExecDestroy(u.exec);
+    g->untils.clear();
+}
+
 static void drop_cached_runs(pgm_graph *g) {
     drop_cached_grads(g);
+    drop_cached_untils(g);
     for (auto &r : g->runs) {
         collect_run_times(g, r);
         destroy_run(r);
@@ -839,6 +854,92 @@ pgm_status pgm_run_bp_multi(pgm_graph *g, int32_t n_samples, const float *log_po
     return PGM_OK;
 }
 
+// The graph of the full chunks of an early-exit run: the iteration counter set to 0,
+// then a conditional while node whose body runs one chunk (check_every - 1 iterations, a
+// copy of the messages, one more iteration, the residual) and k_until_control, which
+// continues the loop while the residual is above tol (or NaN) and fewer than limit
+// iterations are done (so the loop ends after at most limit / check_every trips).
+static pgm_status cached_until(pgm_graph *g, const float *log_pot, const float *evidence, float T, float damping,
+                               int32_t check_every, int32_t limit, float tol, float *msgs, cudaGraphExec_t *out) {
+    uint32_t tb, db, lb;
+    std::memcpy(&tb, &T, sizeof tb);
+    std::memcpy(&db, &damping, sizeof db);
+    std::memcpy(&lb, &tol, sizeof lb);
+    for (auto &u : g->untils)
+        if (u.log_pot == log_pot && u.evidence == evidence && u.msgs == msgs && u.T_bits == tb &&
+            u.damping_bits == db && u.tol_bits == lb && u.check_every == check_every && u.limit == limit) {
+            *out = u.exec;
+            return PGM_OK;
+        }
+    if (!g->capture_stream) {
+        cudaError_t e = cudaStreamCreateWithFlags(&g->capture_stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamCreate");
+    }
+    const int64_t ES = g->info.n_edge_states;
+    int *done = reinterpret_cast<int *>(g->until_res + 1);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaGraphCreate(&graph, 0);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphCreate");
+    auto failed = [&](cudaError_t err, const char *what) {
+        cudaGraphDestroy(graph);
+        return cuda_fail(err, what);
+    };
+    cudaGraphConditionalHandle h;
+    e = cudaGraphConditionalHandleCreate(&h, graph, 1, cudaGraphCondAssignDefault);
+    if (e != cudaSuccess) return failed(e, "cudaGraphConditionalHandleCreate");
+    cudaMemsetParams mp{};
+    mp.dst = done;
+    mp.value = 0;
+    mp.elementSize = sizeof(int);
+    mp.width = 1;
+    mp.height = 1;
+    cudaGraphNode_t n_init = nullptr, n_loop = nullptr;
+    e = cudaGraphAddMemsetNode(&n_init, graph, nullptr, 0, &mp);
+    if (e != cudaSuccess) return failed(e, "cudaGraphAddMemsetNode");
+    cudaGraphNodeParams cp{};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    e = cudaGraphAddNode(&n_loop, graph, &n_init, nullptr, 1, &cp);
+    if (e != cudaSuccess) return failed(e, "cudaGraphAddNode(while)");
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    cudaStream_t cs = g->capture_stream;
+    e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return failed(e, "cudaStreamBeginCaptureToGraph");
+    pgm_status st = PGM_OK;
+    if (check_every > 1) st = enqueue_iterations(g, log_pot, evidence, T, damping, check_every - 1, msgs, cs, false);
+    if (st == PGM_OK) {
+        e = cudaMemcpyAsync(g->until_prev, msgs, (size_t)ES * sizeof(float), cudaMemcpyDeviceToDevice, cs);
+        if (e != cudaSuccess) st = cuda_fail(e, "cudaMemcpyAsync(messages)");
+    }
+    if (st == PGM_OK) st = enqueue_iterations(g, log_pot, evidence, T, damping, 1, msgs, cs, false);
+    if (st == PGM_OK) {
+        e = cudaMemsetAsync(g->until_res, 0, sizeof(unsigned), cs);
+        if (e == cudaSuccess) e = launch_residual(ES, msgs, g->until_prev, g->until_res, g->n_sm, cs);
+        if (e == cudaSuccess) e = launch_until_control(h, g->until_res, done, check_every, limit, tol, cs);
+        if (e != cudaSuccess) st = cuda_fail(e, "early-exit body");
+    }
+    cudaGraph_t captured = nullptr;
+    e = cudaStreamEndCapture(cs, &captured);
+    if (st != PGM_OK) {
+        cudaGraphDestroy(graph);
+        return st;
+    }
+    if (e != cudaSuccess) return failed(e, "cudaStreamEndCapture");
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate(early exit)");
+    if (g->untils.size() >= 4) {
+        cudaGraphExecDestroy(g->untils.front().exec);
+        g->untils.erase(g->untils.begin());
+    }
+    g->untils.push_back({log_pot, evidence, msgs, tb, db, lb, check_every, limit, exec});
+    *out = exec;
+    return PGM_OK;
+}
+
 pgm_status pgm_run_bp_until(pgm_graph *g, const float *log_pot, const float *evidence, float T, float damping,
                             int32_t max_iters, float tol, int32_t check_every, float *msgs, int32_t *iters_done,
                             float *residual, void *stream) {
@@ -861,7 +962,7 @@ pgm_status pgm_run_bp_until(pgm_graph *g, const float *log_pot, const float *evi
             return fail(PGM_ENOMEM, "cudaMalloc(residual buffers)");
         g->until_prev = reinterpret_cast<float *>(mem);
         g->until_res = reinterpret_cast<unsigned *>(mem + align_up((size_t)ES * sizeof(float), 256));
-        if (cudaMallocHost(&g->until_res_host, sizeof(unsigned)) != cudaSuccess) {
+        if (cudaMallocHost(&g->until_res_host, 2 * sizeof(unsigned)) != cudaSuccess) {
             cudaFree(g->until_prev);
             g->until_prev = nullptr;
             g->until_res = nullptr;
@@ -872,6 +973,26 @@ pgm_status pgm_run_bp_until(pgm_graph *g, const float *log_pot, const float *evi
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     int32_t done = 0;
     float res = CUDART_NAN_F_HOST;
+    // With CUDA graphs on, the full chunks run as one graph whose conditional while node
+    // repeats a chunk while its residual is above tol: no host round trip per chunk.
+    const int32_t limit = (max_iters / check_every) * check_every;
+    if (g->use_cuda_graph && !g->ordered && limit > 0) {
+        cudaGraphExec_t exec = nullptr;
+        st = cached_until(g, log_pot, evidence, T, damping, check_every, limit, tol, msgs, &exec);
+        if (st != PGM_OK) return st;
+        cudaError_t e = cudaGraphLaunch(exec, s);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(g->until_res_host, g->until_res, 2 * sizeof(unsigned), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return cuda_fail(e, "early-exit graph");
+        std::memcpy(&res, g->until_res_host, sizeof res);
+        done = (int32_t)g->until_res_host[1];
+        if (res <= tol || done >= max_iters) {
+            if (iters_done) *iters_done = done;
+            if (residual) *residual = res;
+            return PGM_OK;
+        }
+    }
     while (done < max_iters) {
         const int32_t n = std::min(check_every, max_iters - done);
         if (n > 1) {

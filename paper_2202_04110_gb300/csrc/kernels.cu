@@ -2431,6 +2431,18 @@ __global__ void __launch_bounds__(256) k_residual(int64_t n, const float *__rest
     if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(mx));  // NaN (0x7fc00000) ranks above +inf
 }
 
+// The loop control of a device-side early-exit run (the body of a conditional while
+// node): after a trip of n iterations, done += n; the loop goes on while the trip's
+// residual (bits in *res) is above tol or NaN and fewer than limit iterations are done.
+__global__ void k_until_control(cudaGraphConditionalHandle h, const unsigned *__restrict__ res,
+                                int *__restrict__ done, int n, int limit, float tol) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const int d = *done + n;
+    *done = d;
+    const float r = __uint_as_float(*res);
+    cudaGraphSetConditional(h, ((r > tol) || (r != r)) && d < limit ? 1u : 0u);
+}
+
 }  // namespace
 
 // =====================================================================================
@@ -2636,6 +2648,12 @@ cudaError_t launch_residual(int64_t n, const float *a, const float *b, unsigned 
     const int64_t want = (n + 255) / 256;
     const int blocks = (int)std::min<int64_t>(want, (int64_t)n_sm * 8);
     k_residual<<<blocks, 256, 0, s>>>(n, a, b, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_until_control(cudaGraphConditionalHandle h, const unsigned *res, int *done, int n, int limit,
+                                 float tol, cudaStream_t s) {
+    k_until_control<<<1, 32, 0, s>>>(h, res, done, n, limit, tol);
     return cudaGetLastError();
 }
 

@@ -203,6 +203,10 @@ cudaError_t launch_ms_iteration(const DevGraph &G, const Plan &P, int S, int Sp,
 cudaError_t launch_ms_unpack(const DevGraph &G, int S, const float *d, float *msgs, cudaStream_t s);
 // *out (zeroed by the caller; a float as its bit pattern) = max(*out, max_i |a[i] - b[i]|).
 cudaError_t launch_residual(int64_t n, const float *a, const float *b, unsigned *out, int n_sm, cudaStream_t s);
+// Early-exit loop control (a kernel in a conditional while body): *done += n; continue
+// while the residual bits in *res are above tol (or NaN) and *done < limit.
+cudaError_t launch_until_control(cudaGraphConditionalHandle h, const unsigned *res, int *done, int n, int limit,
+                                 float tol, cudaStream_t s);
 // out[s VS + i] = ev[i] + noise[s VS + i] (perturb-and-max-product evidence).
 cudaError_t launch_pmp_perturb(int64_t VS, int S, const float *ev, const float *noise, float *out, cudaStream_t s);
 // Log-ratio pack (from the [2E] edge-state layout; unused slots 0) and unpack.

@@ -83,3 +83,27 @@ def test_no_convergence_and_arguments(gpu):
     for bad in ((1e-3, 0), (-1.0, 5), (float("nan"), 5)):
         with pytest.raises(gpu.PgmError):
             g.run_bp_until(lp, ev, 1.0, 0.5, 10, bad[0], bad[1], m)
+
+
+@pytest.mark.parametrize("which", ["potts", "ising"])
+def test_device_loop_equals_host_checked(gpu, which):
+    """With CUDA graphs on, the full chunks run in a conditional while node (no host round
+    trip per chunk); with them off, the host checks each chunk. Same iterations, same
+    residual, bitwise the same messages; also when max_iters leaves a shorter last chunk
+    and when the loop runs to its limit."""
+    p = W.potts_grid(20, 4, 2, T=1.0) if which == "potts" else W.ising_grid(40, 50, 9, T=1.0)
+    lp, ev = _t(p.log_pot), _t(p.evidence)
+    for max_iters, tol, ck in ((400, 1e-5, 10), (47, 1e-5, 10), (33, 0.0, 8), (7, 1e-3, 10)):
+        out = []
+        for graphs in (1, 0):
+            g = gpu.Graph(p.graph)
+            g.set_option(gpu.OPT_CUDA_GRAPH, graphs)
+            m = g.new_msgs()
+            done, res = g.run_bp_until(lp, ev, 1.0, 0.5, max_iters, tol, ck, m)
+            m2 = g.new_msgs()  # a second call replays the cached graph
+            done2, res2 = g.run_bp_until(lp, ev, 1.0, 0.5, max_iters, tol, ck, m2)
+            assert (done2, np.float32(res2)) == (done, np.float32(res))
+            assert np.array_equal(m.cpu().numpy(), m2.cpu().numpy())
+            out.append((done, np.float32(res), m.cpu().numpy()))
+        assert out[0][0] == out[1][0] and out[0][1] == out[1][1], (which, max_iters, out[0][:2], out[1][:2])
+        assert np.array_equal(out[0][2], out[1][2])
