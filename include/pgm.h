@@ -64,7 +64,9 @@ typedef int32_t pgm_status;
 /* Limits of this build (checked by pgm_build). */
 #define PGM_MAX_STATES 256        /* states per variable */
 #define PGM_MAX_ENUM_ARITY 8      /* neighbours of an enumeration factor */
-#define PGM_MAX_ENUM_STATE_SUM 64 /* sum of K over one enumeration factor's neighbours */
+#define PGM_MAX_ENUM_STATE_SUM 2048 /* sum of K over one enumeration factor's neighbours
+                                      (above 64: pgm_grad returns PGM_ENOTSUP) */
+#define PGM_MAX_ENUM_LIST 1073741824 /* n_cfg * arity of one enumeration group */
 
 typedef struct pgm_graph pgm_graph;
 
@@ -380,11 +382,23 @@ pgm_status pgm_pmp_sample(pgm_graph *g, int32_t n_samples, const float *log_pot,
  * launches per run around the iterations (pack, table differences, unpack).
  */
 #define PGM_OPT_LOG_RATIO 2
+/*
+ * PGM_OPT_ENUM_BLOCK (default 0): listed-configuration groups (factors that are not
+ * dense pairwise tables) run with a thread per factor when their state sum is at most
+ * 64 and their list at most 256 configurations, else with a block per run of factors
+ * that stages the group's configuration table in shared memory. 1 moves the
+ * thread-per-factor launch to the block form as well (0 moves it back), with one thread
+ * per output state so that both give the same bits. Blocking (synchronises the device,
+ * re-plans the launch, drops the cached CUDA graphs); values other than 0 and 1:
+ * PGM_EINVAL.
+ */
+#define PGM_OPT_ENUM_BLOCK 3
 pgm_status pgm_set_option(pgm_graph *g, int32_t option, int64_t value);
 /*
- * The option's effective value in *value: for PGM_OPT_CUDA_GRAPH the setting; for
- * PGM_OPT_LOG_RATIO the setting if the graph qualifies, else 0. PGM_EINVAL for
- * a NULL argument or an unknown option. No device work.
+ * The option's effective value in *value: for PGM_OPT_CUDA_GRAPH and
+ * PGM_OPT_ENUM_BLOCK the setting; for PGM_OPT_LOG_RATIO the setting if the graph
+ * qualifies, else 0. PGM_EINVAL for a NULL argument or an unknown option. No device
+ * work.
  */
 pgm_status pgm_get_option(const pgm_graph *g, int32_t option, int64_t *value);
 
@@ -392,7 +406,9 @@ pgm_status pgm_get_option(const pgm_graph *g, int32_t option, int64_t *value);
  * Launch-shape autotuner: for every factor-pass launch of the graph (one per kernel
  * variant, covering all groups of that variant) times each thread-block shape the
  * kernel allows, and for dense K-state pairwise launches (K = 4, 8, 16) both kernel
- * forms (K lanes per factor, thread per factor) -- threads per block for the thread-per-factor kernels, warps per
+ * forms (K lanes per factor, thread per factor), for listed-configuration launches both
+ * forms (thread per factor, block per run of factors; the former only where every group
+ * fits it) -- threads per block for the thread-per-factor kernels, warps per
  * block (factors per block) for the warp-per-factor logical kernel -- on the given
  * inputs, and keeps the fastest; likewise the block size of the thread-per-variable
  * pass. Allocates two temporary message buffers (freed before returning), blocks until
@@ -408,8 +424,9 @@ pgm_status pgm_autotune(pgm_graph *g, const float *log_pot, const float *evidenc
  * kind 1 = factor pass (variant: 0 dense pairwise K = 2; 1..3 dense pairwise K = 4, 8,
  * 16 with K lanes per factor; 4 listed configurations; 5 OR/AND thread per factor; 6
  * OR/AND warp per factor; 7..9 dense pairwise K = 4, 8, 16 with a thread per factor,
- * the default form, which pgm_autotune may exchange with 1..3); threads per block and
- * blocks. Any output pointer may be NULL.
+ * the default form, which pgm_autotune may exchange with 1..3; 10 listed configurations
+ * with a block per run of factors); threads per block and blocks. Any output pointer
+ * may be NULL.
  */
 pgm_status pgm_launch_info(const pgm_graph *g, int32_t i, int32_t *kind, int32_t *variant,
                            int32_t *threads, int32_t *n_blocks);

@@ -28,6 +28,7 @@ EXPORTED = ["pgm_build", "pgm_build_batch", "pgm_batch_member", "pgm_check_desc"
             "pgm_serve_wait", "pgm_serve_stats", "pgm_serve_destroy", "pgm_last_error"]
 OPT_CUDA_GRAPH = 1
 OPT_LOG_RATIO = 2
+OPT_ENUM_BLOCK = 3
 
 
 class PgmError(RuntimeError):

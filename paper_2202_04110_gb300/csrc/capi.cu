@@ -99,6 +99,8 @@ struct pgm_graph {
     FactorLaunch adj_launch{};      // pgm_grad: every enumeration group, thread per factor
     size_t adj_seg_off = (size_t)-1;
     bool has_logic = false;
+    bool has_large_enum = false;
+    int32_t enum_block = 0;       // PGM_OPT_ENUM_BLOCK  // an enumeration group with a state sum above kMaxStateSum
     std::vector<std::vector<char>> factor_segs_host;  // host copy of each factor launch's segments
     // CUDA graphs of whole pgm_run_bp calls, keyed by their arguments (LRU)
     struct CachedRun {
@@ -187,6 +189,33 @@ bool lr_eligible(const HostLayout &H) {
 // Slots of each log-ratio array: 4 per variable with the 4-slot table, else one per edge.
 int64_t lr_slot_count(const HostLayout &H) { return H.vin_tab4.empty() ? H.E : 4 * H.V; }
 
+// Block-per-factor enumeration launch (kEnumBlock), any block size: each segment's
+// factors per block (about 4 blocks per SM for a large group) and threads per output
+// state (enough to fill a 256-thread block, at most the mean list length, more for long lists;
+// one with `one_lane`, which keeps the thread-per-factor kernel's summation order, so
+// that groups moved from that kernel give the same bits); block ranges; the dynamic
+// shared memory (two state-sum arrays plus the staged table).
+static int32_t plan_enum_block(EnumSeg *segs, int n_seg, int n_sm, bool one_lane, int32_t *smem) {
+    int32_t blk = 0;
+    *smem = 0;
+    for (int i = 0; i < n_seg; ++i) {
+        EnumSeg &sg = segs[i];
+        const int64_t target = (int64_t)n_sm * 4;
+        sg.fpb = (int32_t)std::max<int64_t>(1, sg.n_fac / std::max<int64_t>(target, 1));
+        const int64_t mean = (int64_t)sg.arity * sg.n_cfg / std::max(sg.es_per_fac, 1);
+        int lanes = 1;
+        // (a property of the group, not of the block size: results do not depend on the shape)
+        while (!one_lane && lanes < 32 && 2 * lanes <= mean && (int64_t)sg.es_per_fac * 2 * lanes <= kEnumBlockThreads)
+            lanes *= 2;
+        while (!one_lane && lanes < 32 && mean > 8 * lanes) lanes *= 2;
+        sg.lanes = lanes;
+        sg.block_begin = blk;
+        blk += (sg.n_fac + sg.fpb - 1) / sg.fpb;
+        *smem = std::max(*smem, ((8 * sg.es_per_fac + 15) & ~15) + sg.table_bytes);
+    }
+    return blk;
+}
+
 pgm_status build_plan(const HostLayout &H, pgm_graph *g, Packer &pk, std::vector<size_t> &seg_off,
                       std::vector<int> &seg_kind) {
     // variable pass: one launch per non-empty bucket of variables
@@ -222,6 +251,7 @@ pgm_status build_plan(const HostLayout &H, pgm_graph *g, Packer &pk, std::vector
         g->adj_launch.threads = 128;
         g->adj_seg_off = segs.empty() ? (size_t)-1 : pk.add(segs.data(), segs.size());
         g->has_logic = !H.logic_groups.empty();
+        for (const HostEnumGroup &hg : H.enum_groups) g->has_large_enum |= hg.seg.es_per_fac > kMaxStateSum;
     }
     // factor pass: one launch per variant, all groups of that variant as segments
     for (int variant = 0; variant < kNumFactorVariants; ++variant) {
@@ -260,6 +290,7 @@ pgm_status build_plan(const HostLayout &H, pgm_graph *g, Packer &pk, std::vector
             L.threads = threads;
             L.smem = (int32_t)smem;
             L.max_fan = mf;
+            L.base_variant = variant;
             P.factor.push_back(L);
             seg_off.push_back(pk.add(segs.data(), segs.size()));
             seg_kind.push_back(variant);
@@ -278,10 +309,13 @@ pgm_status build_plan(const HostLayout &H, pgm_graph *g, Packer &pk, std::vector
                 segs.push_back(s);
             }
             if (segs.empty()) continue;
+            if (variant == kEnumBlock)
+                blk = plan_enum_block(segs.data(), (int)segs.size(), g->n_sm, false, &L.smem);
             L.n_seg = (int32_t)segs.size();
             L.n_blocks = blk;
             L.threads = threads;
             L.max_blocks = g->n_sm * 8;
+            L.base_variant = variant;
             P.factor.push_back(L);
             seg_off.push_back(pk.add(segs.data(), segs.size()));
             seg_kind.push_back(variant);
@@ -367,6 +401,7 @@ static pgm_status build_from_descs(const void *const *descs, int n, pgm_graph **
     size_t o_edge_vs = pk.add(H.edge_vs.data(), H.edge_vs.size());
     size_t o_cfg = pk.add(H.cfg_pool.data(), H.cfg_pool.size());
     size_t o_po = pk.add(H.paroff_pool.data(), H.paroff_pool.size());
+    size_t o_bs = pk.add(H.bs_pool.data(), H.bs_pool.size());
     size_t o_tab4 = H.vin_tab4.empty() ? 0 : pk.add(H.vin_tab4.data(), H.vin_tab4.size());
     std::vector<size_t> seg_off;
     std::vector<int> seg_kind;
@@ -443,6 +478,7 @@ static pgm_status build_from_descs(const void *const *descs, int n, pgm_graph **
     G.edge_vs = reinterpret_cast<const int32_t *>(dmem + o_edge_vs);
     G.cfg_pool = reinterpret_cast<const uint8_t *>(dmem + o_cfg);
     G.paroff_pool = reinterpret_cast<const int32_t *>(dmem + o_po);
+    G.bs_pool = reinterpret_cast<const int32_t *>(dmem + o_bs);
     G.vin_tab4 = H.vin_tab4.empty() ? nullptr : reinterpret_cast<const int4 *>(dmem + o_tab4);
     G.flags = flags;
     G.v2f_hd = hd_bytes ? reinterpret_cast<float *>(smem + es_bytes + vs_bytes + 256) : nullptr;
@@ -550,7 +586,8 @@ pgm_status pgm_check_desc(const pgm_graph_desc *desc, pgm_info *info) {
     size_t nb = 0;
     for (int kk = 0; kk < kNumVarKinds; ++kk) nb += H.var_bucket_identity[kk] ? 0 : H.var_bucket[kk].size();
     size_t idx = (H.vs_off.size() + H.vin_off.size() + H.vin_es.size() + H.edge_vs.size() +
-                  H.paroff_pool.size() + nb + H.vin_tab4.size()) * sizeof(int32_t) + H.cfg_pool.size();
+                  H.paroff_pool.size() + H.bs_pool.size() + nb + H.vin_tab4.size()) * sizeof(int32_t) +
+                 H.cfg_pool.size();
     size_t es_bytes = align_up(std::max<int64_t>(H.ES, 1) * sizeof(float), 256);
     if (lr_eligible(H))  // the slot map, the two log-ratio arrays and the table differences
         idx += H.E * sizeof(int32_t) + 2 * align_up((size_t)lr_slot_count(H) * sizeof(float), 256) +
@@ -1090,6 +1127,8 @@ static int alternative_form(int variant) {
         case kPairT4: return kPair4;
         case kPairT8: return kPair8;
         case kPairT16: return kPair16;
+        case kEnumGeneric: return kEnumBlock;
+        case kEnumBlock: return kEnumGeneric;  // when every group fits (checked by the caller)
         default: return -1;
     }
 }
@@ -1101,6 +1140,7 @@ static std::vector<int> shape_candidates(int variant) {
         case kPairT4: case kPairT8: return {64, 128, 256};
         case kPairT16: return {64, 128};
         case kEnumGeneric: return {32, 64, 128};
+        case kEnumBlock: return {128, 256};
         case kLogicWarp: return {32, 64, 128};
         default: return {};
     }
@@ -1125,9 +1165,16 @@ static bool replan_factor_launch(pgm_graph *g, size_t li, int threads, cudaStrea
             segs[i].block_begin = blk;
             blk += (segs[i].n_fac + per_block - 1) / per_block;
         }
+    } else if (L.variant == kEnumBlock) {
+        int32_t sm = 0;
+        blk = plan_enum_block(reinterpret_cast<EnumSeg *>(host.data()), L.n_seg, g->n_sm,
+                              L.base_variant == kEnumGeneric, &sm);
+        smem = (size_t)sm;
+        if (prepare_kernels(sm) != cudaSuccess) return false;
     } else {
         EnumSeg *segs = reinterpret_cast<EnumSeg *>(host.data());
         for (int i = 0; i < L.n_seg; ++i) {
+            if (L.variant == kEnumGeneric && segs[i].es_per_fac > kMaxStateSum) return false;
             segs[i].block_begin = blk;
             blk += (segs[i].n_fac + per_block - 1) / per_block;
         }
@@ -1330,6 +1377,8 @@ pgm_status pgm_grad(pgm_graph *g, const float *log_pot, const float *evidence, f
     if (!(T > 0.f) || !std::isfinite(T))
         return fail(T == 0.f ? PGM_ENOTSUP : PGM_EINVAL, "pgm_grad needs a finite T > 0 (max-product has no gradient)");
     if (g->has_logic) return fail(PGM_ENOTSUP, "pgm_grad supports enumeration factors only");
+    if (g->has_large_enum)
+        return fail(PGM_ENOTSUP, "pgm_grad supports enumeration factors with a state sum of at most 64");
     if (!(damping >= 0.f && damping < 1.f)) return fail(PGM_EINVAL, "damping must be in [0, 1)");
     if (n_iters < 0 || ckpt_every < 1) return fail(PGM_EINVAL, "n_iters >= 0 and ckpt_every >= 1 required");
     if (!evidence || !d_beliefs || !d_evidence || (g->info.n_potentials > 0 && (!log_pot || !d_log_pot)))
@@ -1411,6 +1460,29 @@ pgm_status pgm_set_option(pgm_graph *g, int32_t option, int64_t value) {
             if (value != g->log_ratio_min_iters) drop_cached_runs(g);
             g->log_ratio_min_iters = (int32_t)value;
             return PGM_OK;
+        case PGM_OPT_ENUM_BLOCK: {
+            if (value != 0 && value != 1) return fail(PGM_EINVAL, "PGM_OPT_ENUM_BLOCK must be 0 or 1");
+            DeviceGuard dg(g->device);
+            cudaError_t e = cudaDeviceSynchronize();  // a replay may be reading the segments
+            if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceSynchronize");
+            drop_cached_runs(g);
+            for (size_t li = 0; li < g->P.factor.size(); ++li) {
+                FactorLaunch &L = g->P.factor[li];
+                if (L.base_variant != kEnumGeneric) continue;
+                const int want = value ? kEnumBlock : kEnumGeneric;
+                if (L.variant == want) continue;
+                const int old_variant = L.variant;
+                L.variant = want;
+                if (!replan_factor_launch(g, li, want == kEnumBlock ? 256 : 128, nullptr)) {
+                    L.variant = old_variant;
+                    return fail(PGM_ECUDA, "re-planning an enumeration launch failed");
+                }
+            }
+            e = cudaDeviceSynchronize();
+            if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceSynchronize");
+            g->enum_block = (int32_t)value;
+            return PGM_OK;
+        }
         default:
             return fail(PGM_EINVAL, "unknown option");
     }
@@ -1424,6 +1496,9 @@ pgm_status pgm_get_option(const pgm_graph *g, int32_t option, int64_t *value) {
             return PGM_OK;
         case PGM_OPT_LOG_RATIO:
             *value = g->P.lr ? g->log_ratio_min_iters : 0;
+            return PGM_OK;
+        case PGM_OPT_ENUM_BLOCK:
+            *value = g->enum_block;
             return PGM_OK;
         default:
             return fail(PGM_EINVAL, "unknown option");

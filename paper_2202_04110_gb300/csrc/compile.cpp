@@ -8,10 +8,13 @@
 //   vin_off/vin_es  CSR from each variable to the first edge-state of each incoming
 //                   edge, in ascending edge order (deterministic summation order)
 //   cfg_pool      uint8 configuration tables of the enumeration groups
+//   bs_pool       the same configurations listed by output edge-state (the gather
+//                 order of the block-per-factor form)
 //   paroff_pool   par_off arrays of the logical groups
 //   per-group segment records with the kernel variant chosen for the group
 //   degree buckets of the variables (thread- or block-per-variable)
 #include <algorithm>
+#include <climits>
 #include <cstdio>
 #include <limits>
 #include <string>
@@ -98,7 +101,9 @@ std::string compile_graph(const void *const *vdescs, int n_desc, HostLayout *L) 
                 if (v0 < 0 || v0 >= Vm) return fmt("enum group %lld: variable %lld out of range", gi, v0);
                 ksum += K[vo + v0];
             }
-            if (ksum > kMaxStateSum) return fmt("enum group %lld: state sum %lld exceeds 64", gi, ksum);
+            if (ksum > kEnumBlockStateSum) return fmt("enum group %lld: state sum %lld exceeds 2048", gi, ksum);
+            if ((int64_t)g.n_cfg * g.arity > (int64_t)1 << 30)
+                return fmt("enum group %lld: n_cfg * arity %lld exceeds 2^30", gi, (int64_t)g.n_cfg * g.arity);
             for (int64_t f = 0; f < g.n_fac; ++f)
                 for (int j = 0; j < g.arity; ++j) {
                     int32_t v = g.vars[f * g.arity + j];
@@ -177,6 +182,9 @@ std::string compile_graph(const void *const *vdescs, int n_desc, HostLayout *L) 
             s.shared = g.shared_potentials ? 1 : 0;
             s.n_cfg = g.n_cfg;
             s.arity = g.arity;
+            L->cfg_pool.resize((L->cfg_pool.size() + 15) & ~(size_t)15, 0);
+            if (L->cfg_pool.size() + (size_t)g.n_cfg * g.arity > (size_t)INT32_MAX)
+                return "configuration tables exceed 2^31 bytes";
             s.cfg_base = (int32_t)L->cfg_pool.size();
             int32_t off = 0;
             for (int j = 0; j < g.arity; ++j) {
@@ -185,9 +193,9 @@ std::string compile_graph(const void *const *vdescs, int n_desc, HostLayout *L) 
                 off += s.K[j];
             }
             s.es_per_fac = off;
-            for (int c = 0; c < g.n_cfg * g.arity; ++c) L->cfg_pool.push_back((uint8_t)g.cfg[c]);
+            for (int64_t c = 0; c < (int64_t)g.n_cfg * g.arity; ++c) L->cfg_pool.push_back((uint8_t)g.cfg[c]);
             int K0 = s.K[0], K1 = g.arity > 1 ? s.K[1] : 0;
-            hg.variant = kEnumGeneric;
+            hg.variant = (off > kMaxStateSum || g.n_cfg > kEnumGenericMaxCfg) ? kEnumBlock : kEnumGeneric;
             if (g.n_fac > 0 && is_dense_pair(g, K0, K1)) {
                 // K = 4, 8, 16: thread per factor by default (the autotuner may switch a
                 // launch to the K-lane form)
@@ -195,6 +203,33 @@ std::string compile_graph(const void *const *vdescs, int n_desc, HostLayout *L) 
                 else if (K0 == 4) hg.variant = kPairT4;
                 else if (K0 == 8) hg.variant = kPairT8;
                 else if (K0 == 16) hg.variant = kPairT16;
+            }
+            s.bs_base = -1;
+            s.fpb = 1;
+            s.lanes = 1;
+            s.table_bytes = 0;
+            if (g.n_fac > 0 && (hg.variant == kEnumGeneric || hg.variant == kEnumBlock)) {
+                // configuration lists by output state: for neighbour j and state x, the
+                // configurations with state x at j (the block form's gather order)
+                // (offsets block padded to a multiple of 4 entries, the whole padded to 4)
+                const int64_t nl = (int64_t)g.arity * g.n_cfg, ob = (off + 1 + 3) & ~3;
+                const size_t len = (size_t)((ob + nl + 3) & ~(int64_t)3);
+                if (L->bs_pool.size() + len > (size_t)INT32_MAX) return "configuration lists exceed 2^31 entries";
+                s.bs_base = (int32_t)L->bs_pool.size();
+                L->bs_pool.resize(L->bs_pool.size() + len, 0);
+                int32_t *bo = L->bs_pool.data() + s.bs_base, *bl = bo + ob;
+                for (int j = 0; j < g.arity; ++j)
+                    for (int c = 0; c < g.n_cfg; ++c) bo[s.Koff[j] + g.cfg[(int64_t)c * g.arity + j] + 1]++;
+                for (int o = 0; o < off; ++o) bo[o + 1] += bo[o];
+                std::vector<int32_t> fill(bo, bo + off);
+                for (int j = 0; j < g.arity; ++j)
+                    for (int c = 0; c < g.n_cfg; ++c) bl[fill[s.Koff[j] + g.cfg[(int64_t)c * g.arity + j]]++] = c;
+                // threads per output state from the mean list length (about 8 configs each)
+                const int64_t mean = nl / std::max<int32_t>(off, 1);
+                while (s.lanes < 32 && mean > 8 * s.lanes) s.lanes *= 2;
+                const int64_t tb = (((int64_t)g.n_cfg * g.arity + 15) & ~15) + (int64_t)len * 4 +
+                                   (g.shared_potentials ? (int64_t)g.n_cfg * 4 : 0);
+                s.table_bytes = tb <= kEnumTableSmem ? (int32_t)tb : 0;
             }
             for (int64_t f = 0; f < g.n_fac; ++f)
                 for (int j = 0; j < g.arity; ++j) {
@@ -245,6 +280,7 @@ std::string compile_graph(const void *const *vdescs, int n_desc, HostLayout *L) 
         mem.n_potentials = pot - mem.pot_off;
         L->members.push_back(mem);
     }
+    L->cfg_pool.resize((L->cfg_pool.size() + 15) & ~(size_t)15, 0);  // 16-byte copies stay inside
 
     // ---- variable -> incoming edge-state CSR (ascending edge id)
     L->vin_off.assign(V + 1, 0);

@@ -28,6 +28,7 @@
 // explicit leave-one-out sum (v2f_slow_edge) instead of b - m; edges of variables with
 // more than kVarBlockDegree factors always do (computed by the block variable pass).
 #include <algorithm>
+#include <atomic>
 #include <cstdint>
 
 #include <cuda_runtime.h>
@@ -1434,6 +1435,180 @@ k_enum_generic(DevGraph G, const EnumSeg *__restrict__ segs, int n_seg, const fl
 }
 
 // =====================================================================================
+// Factor pass: large listed-configuration factors, a block per run of factors
+// =====================================================================================
+
+// Factors given by a long list of valid configurations or with many states (Sec. 5.2:
+// RCN's non-standard pairwise factors are specified this way), beyond the thread-per-factor
+// kernel's kMaxStateSum. A block takes fpb consecutive factors of one group. The group's
+// table (each configuration's states, the configurations listed by output edge-state, a
+// shared log-potential table) is staged once per block in shared memory when it fits
+// (table_bytes > 0), else read in place. Per factor:
+//   (1) a warp per edge writes the edge's variable-to-factor values to shared memory;
+//   (2) `lanes` threads per output edge-state (j, x) walk the configurations with state
+//       x at neighbour j; each value is the log-potential plus the other neighbours'
+//       variable-to-factor values, reduced by max (T = 0) or a running log-sum-exp
+//       (T > 0); the lanes of an output combine by shuffles;
+//   (3) a warp per edge normalises, damps and normalises the edge's message.
+// Every output sums its terms in neighbour order and, with one lane, reduces its
+// configurations in ascending order, as the thread-per-factor kernel does: the two then
+// give the same bits (with several lanes, T > 0 differs by rounding).
+template <bool MAXP>
+__global__ void __launch_bounds__(kEnumBlockThreads)
+k_enum_block(DevGraph G, const EnumSeg *__restrict__ segs, int n_seg, const float *__restrict__ pot,
+             const float *__restrict__ b, const float *__restrict__ ev, const float *__restrict__ m_old,
+             float *__restrict__ m_new, float T, float invT, float damping) {
+    extern __shared__ __align__(16) unsigned char eb_smem[];
+    __shared__ int sK[kMaxArity], sKo[kMaxArity];
+    const EnumSeg *S = segs + find_seg(segs, n_seg, blockIdx.x);
+    const int a = __ldg(&S->arity), nc = __ldg(&S->n_cfg), ksum = __ldg(&S->es_per_fac);
+    const int fpb = __ldg(&S->fpb), L = __ldg(&S->lanes), tb = __ldg(&S->table_bytes);
+    const int n_fac = __ldg(&S->n_fac), shared = __ldg(&S->shared);
+    const int f0 = (blockIdx.x - __ldg(&S->block_begin)) * fpb;
+    const int f1 = min(n_fac, f0 + fpb);
+    if (threadIdx.x < a) {
+        sK[threadIdx.x] = __ldg(&S->K[threadIdx.x]);
+        sKo[threadIdx.x] = __ldg(&S->Koff[threadIdx.x]);
+    }
+    float *v2f = reinterpret_cast<float *>(eb_smem);  // [ksum]
+    float *out = v2f + ksum;                        // [ksum]
+    const int cfg_bytes = (nc * a + 15) & ~15;
+    const int ob = (ksum + 1 + 3) & ~3;              // offsets block, then the lists
+    const int bs_len = (ob + a * nc + 3) & ~3;
+    const uint8_t *cfg = G.cfg_pool + __ldg(&S->cfg_base);
+    const int32_t *bs = G.bs_pool + __ldg(&S->bs_base);
+    const float *phi_g = pot + __ldg(&S->pot_base);
+    const float *phi_tab = phi_g;
+    if (tb > 0) {  // 16-byte aligned sources (pool layout) and destinations
+        unsigned char *t = eb_smem + ((8 * ksum + 15) & ~15);
+        const uint4 *c_src = reinterpret_cast<const uint4 *>(cfg);
+        uint4 *c_dst = reinterpret_cast<uint4 *>(t);
+        for (int i = threadIdx.x; i < cfg_bytes / 16; i += blockDim.x) c_dst[i] = __ldg(c_src + i);
+        int32_t *tbs = reinterpret_cast<int32_t *>(t + cfg_bytes);
+        const int4 *b_src = reinterpret_cast<const int4 *>(bs);
+        int4 *b_dst = reinterpret_cast<int4 *>(tbs);
+        for (int i = threadIdx.x; i < bs_len / 4; i += blockDim.x) b_dst[i] = __ldg(b_src + i);
+        if (shared) {
+            float *tphi = reinterpret_cast<float *>(tbs + bs_len);
+            for (int i = threadIdx.x; i < nc; i += blockDim.x) tphi[i] = __ldg(phi_g + i);
+            phi_tab = tphi;
+        }
+        cfg = t;
+        bs = tbs;
+    }
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    const int ng = blockDim.x / L, gi = threadIdx.x / L, gl = threadIdx.x - gi * L;
+    const int32_t *lst = bs + ob;
+    const float w = 1.f - damping;
+    for (int f = f0; f < f1; ++f) {
+        const int es_f = __ldg(&S->es_base) + f * ksum;
+        const int e_f = __ldg(&S->edge_base) + f * a;
+        // (1) variable-to-factor values, a warp per edge (see k_enum_generic)
+        for (int j = warp; j < a; j += nw) {
+            const int vs = __ldg(G.edge_vs + e_f + j), es = es_f + sKo[j], K = sK[j];
+            float *vj = v2f + sKo[j];
+            if (vs < 0) {
+                if (lane == 0) {
+                    float2 hmx = make_float2(-CUDART_INF_F, 0.f);
+                    for (int x = 0; x < K; ++x) {
+                        const float2 q = hd_pair(G, es, x);
+                        if (x == 0 || hd_gt(q, hmx)) hmx = q;
+                    }
+                    for (int x = 0; x < K; ++x)
+                        vj[x] = hmx.x == -CUDART_INF_F ? -CUDART_INF_F : hd_rel(hd_pair(G, es, x), hmx);
+                }
+            } else {
+                bool exact = false;
+                for (int x = lane; x < K; x += 32) exact |= needs_exact(__ldg(m_old + es + x));
+                if (__any_sync(0xffffffffu, exact)) {
+                    if (lane == 0) v2f_slow_edge(G, ev, m_old, vs, es, K, vj);
+                } else {
+                    for (int x = lane; x < K; x += 32) vj[x] = __ldg(b + vs + x) - __ldg(m_old + es + x);
+                }
+            }
+        }
+        __syncthreads();
+        // (2) every output edge-state over its configurations
+        const float *phi = shared ? phi_tab : phi_g + (size_t)f * nc;
+        for (int base = 0; base < ksum; base += ng) {
+            const int o = base + gi;
+            float mx = kNegInf, sm = 0.f;
+            if (o < ksum) {
+                int j = 0;
+                for (int k = 1; k < a; ++k)
+                    if (o >= sKo[k]) j = k;
+                const int i1 = bs[o + 1];
+                for (int i = bs[o] + gl; i < i1; i += L) {
+                    const int c = lst[i];
+                    const uint8_t *cc = cfg + c * a;
+                    float val = phi[c];
+                    for (int k = 0; k < a; ++k)
+                        if (k != j) val += v2f[sKo[k] + cc[k]];
+                    if (MAXP) {
+                        mx = fmaxf(mx, val);
+                    } else if (val > mx) {
+                        sm = sm * expf((mx - val) * invT) + 1.f;
+                        mx = val;
+                    } else if (val > kNegInf) {
+                        sm += expf((val - mx) * invT);
+                    }
+                }
+            }
+            for (int d = 1; d < L; d <<= 1) {  // L a power of two; whole warps take part
+                const float m2 = __shfl_xor_sync(0xffffffffu, mx, d);
+                if (MAXP) {
+                    mx = fmaxf(mx, m2);
+                } else {
+                    const float s2 = __shfl_xor_sync(0xffffffffu, sm, d);
+                    const float mn = fmaxf(mx, m2);
+                    if (mn != kNegInf) {
+                        sm = (mx == kNegInf ? 0.f : sm * expf((mx - mn) * invT)) +
+                             (m2 == kNegInf ? 0.f : s2 * expf((m2 - mn) * invT));
+                        mx = mn;
+                    }
+                }
+            }
+            if (o < ksum && gl == 0) out[o] = (MAXP || mx == kNegInf) ? mx : mx + T * logf(sm);
+        }
+        __syncthreads();
+        // (3) normalise, damp, normalise; a warp per edge, up to 8 states per lane
+        for (int j = warp; j < a; j += nw) {
+            const int K = sK[j], es = es_f + sKo[j];
+            const float *t = out + sKo[j];
+            float v[kMaxStates / 32];
+            float mx = kNegInf;
+#pragma unroll
+            for (int r = 0; r < kMaxStates / 32; ++r) {
+                const int x = lane + 32 * r;
+                v[r] = x < K ? t[x] : kNegInf;
+                if (v[r] > mx) mx = v[r];
+            }
+            for (int d = 16; d > 0; d >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, d));
+            if (mx == kNegInf && lane == 0) atomicOr(G.flags, kFlagContradiction);
+            float mx2 = kNegInf;
+#pragma unroll
+            for (int r = 0; r < kMaxStates / 32; ++r) {
+                const int x = lane + 32 * r;
+                if (x < K) {
+                    float y = mx == kNegInf ? 0.f : v[r] - mx;
+                    if (damping != 0.f) y = damping * __ldg(m_old + es + x) + w * y;
+                    v[r] = y;
+                    if (y > mx2) mx2 = y;
+                }
+            }
+            for (int d = 16; d > 0; d >>= 1) mx2 = fmaxf(mx2, __shfl_xor_sync(0xffffffffu, mx2, d));
+            if (mx2 == kNegInf && lane == 0) atomicOr(G.flags, kFlagContradiction);
+#pragma unroll
+            for (int r = 0; r < kMaxStates / 32; ++r) {
+                const int x = lane + 32 * r;
+                if (x < K) m_new[es + x] = mx2 == kNegInf ? 0.f : v[r] - mx2;
+            }
+        }
+    }
+}
+
+// =====================================================================================
 // Factor pass: logical OR / AND
 // =====================================================================================
 
@@ -2449,14 +2624,31 @@ __global__ void k_until_control(cudaGraphConditionalHandle h, const unsigned *__
 // Launchers
 // =====================================================================================
 
+// The kernels with dynamic shared memory may take up to the device's opt-in maximum
+// (set once per device; a smaller limit set later would break other graphs' launches).
 cudaError_t prepare_kernels(int max_smem_bytes) {
-    cudaError_t e = cudaSuccess;
-    if (max_smem_bytes > 48 * 1024) {
-        e = cudaFuncSetAttribute(k_logic_warp<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem_bytes);
-        if (e != cudaSuccess) return e;
-        e = cudaFuncSetAttribute(k_logic_warp<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem_bytes);
-    }
-    return e;
+    static std::atomic<int> done[64];
+    if (max_smem_bytes <= 48 * 1024) return cudaSuccess;
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev >= 0 && dev < 64 && done[dev].load()) return cudaSuccess;
+    if ((e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess) return e;
+    // each kernel: the opt-in maximum less its static shared memory
+    auto allow = [&](const void *fn) -> cudaError_t {
+        cudaFuncAttributes fa{};
+        cudaError_t r = cudaFuncGetAttributes(&fa, fn);
+        if (r != cudaSuccess) return r;
+        const int dyn = optin - (int)fa.sharedSizeBytes;
+        if (max_smem_bytes > dyn) return cudaErrorInvalidValue;
+        return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
+    };
+    if ((e = allow((const void *)k_logic_warp<true>)) != cudaSuccess) return e;
+    if ((e = allow((const void *)k_logic_warp<false>)) != cudaSuccess) return e;
+    if ((e = allow((const void *)k_enum_block<true>)) != cudaSuccess) return e;
+    if ((e = allow((const void *)k_enum_block<false>)) != cudaSuccess) return e;
+    if (dev >= 0 && dev < 64) done[dev].store(1);
+    return cudaSuccess;
 }
 
 template <int MODE>
@@ -2534,6 +2726,9 @@ static void factor_pass_t(const DevGraph &G, const Plan &P, const float *pot, co
                 break;
             case kEnumGeneric:
                 k_enum_generic<MAXP><<<L.n_blocks, L.threads, 0, s>>>(G, es, L.n_seg, pot, b, ev, m_old, m_new, T, invT, damping);
+                break;
+            case kEnumBlock:
+                k_enum_block<MAXP><<<L.n_blocks, L.threads, L.smem, s>>>(G, es, L.n_seg, pot, b, ev, m_old, m_new, T, invT, damping);
                 break;
             case kLogicSmall:
                 k_logic_small<MAXP><<<L.n_blocks, L.threads, 0, s>>>(G, ls, L.n_seg, b, ev, m_old, m_new, T, invT, damping);

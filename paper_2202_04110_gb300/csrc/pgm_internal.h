@@ -18,7 +18,11 @@
 namespace pgm {
 
 constexpr int kMaxArity = 8;
-constexpr int kMaxStateSum = 64;
+constexpr int kMaxStateSum = 64;          // thread-per-factor enumeration kernels
+constexpr int kEnumBlockStateSum = 2048;  // block-per-factor form (kMaxArity x kMaxStates)
+constexpr int kEnumGenericMaxCfg = 256;   // longer configuration lists use the block form
+constexpr int kEnumBlockThreads = 256;
+constexpr int kEnumTableSmem = 160 * 1024;  // largest configuration table staged per block
 constexpr int kMaxStates = 256;
 constexpr int kVarBlockDegree = 64;  // variables with more factors use a block each
 constexpr int kVarBlockThreads = 256;
@@ -39,7 +43,9 @@ enum FactorVariant : int32_t {
     kPairT4 = 7,       // dense pairwise table, K = 4, 8, 16, thread per factor (the
     kPairT8 = 8,       // alternative to the K-lane form kPair4 / 8 / 16; the autotuner
     kPairT16 = 9,      // picks per launch)
-    kNumFactorVariants = 10
+    kEnumBlock = 10,   // listed-configuration factors with a state sum above kMaxStateSum or
+                       // a list longer than kEnumGenericMaxCfg: a block per run of factors
+    kNumFactorVariants = 11
 };
 
 // One enumeration group as seen by a launch. Edges of factor f are
@@ -57,6 +63,14 @@ struct EnumSeg {
     int32_t cfg_base;     // offset of the group's [n_cfg * arity] table in the uint8 pool
     int32_t K[kMaxArity];
     int32_t Koff[kMaxArity];
+    // block form (kEnumBlock) only:
+    int32_t bs_base;      // offset in DevGraph::bs_pool of the group's lists by output
+                          // state: es_per_fac + 1 offsets, then arity * n_cfg config ids
+                          // (for each neighbour j and state x, the configs with state x
+                          // at j, ascending); -1 if the group has none
+    int32_t fpb;          // factors per block (set by the planner)
+    int32_t lanes;        // threads per output state (1, 2, .., 32)
+    int32_t table_bytes;  // bytes of the table staged in shared memory (0: read in place)
 };
 
 // One logical group as seen by a launch. Factor f owns edges
@@ -89,6 +103,7 @@ struct DevGraph {
     float *v2f_hd;           // [2 * ES] exact leave-one-out sums, float-float (hi, lo)
                              // pairs, for edges of high-degree variables (edge_vs = -1);
                              // null if there are none
+    const int32_t *bs_pool;  // configuration lists by output state (EnumSeg::bs_base)
     const int32_t *lr_pos;   // [E] Plan::lr graphs: each edge's slot in the log-ratio
                              // arrays (k V + v with vin_tab4, else its CSR index); else null
 };
@@ -103,6 +118,7 @@ struct FactorLaunch {
     int32_t max_fan;   // logical warp launches: largest fan-in
     int32_t max_blocks;  // K-lane pairwise launches: physical blocks (each walks a range
                          // of the n_blocks chunks)
+    int32_t base_variant;  // the variant the compiler chose (before options and autotuning)
 };
 
 // Variable-pass kernel variants (buckets of variables).
@@ -155,8 +171,9 @@ struct HostLayout {
     int64_t V = 0, VS = 0, E = 0, ES = 0, F = 0, P = 0;
     int32_t max_states = 0, max_degree = 0;
     std::vector<int32_t> vs_off, vin_off, vin_es, edge_vs;
-    std::vector<uint8_t> cfg_pool;
+    std::vector<uint8_t> cfg_pool;    // each group's table starts on a 16-byte boundary
     std::vector<int32_t> paroff_pool;
+    std::vector<int32_t> bs_pool;     // each group's lists start on a 16-byte boundary
     std::vector<HostEnumGroup> enum_groups;
     std::vector<HostLogicGroup> logic_groups;
     std::vector<int32_t> var_bucket[kNumVarKinds];  // variables of each VarKind, ascending

@@ -253,6 +253,58 @@ def deconvolution(seed: int, n_feat: int = 5, feat_side: int = 6, s_side: int = 
     return Problem("deconv", g, np.zeros(0, np.float32), ev.ravel(), T, damping, n_iters)
 
 
+def pool_offsets(radius: int) -> np.ndarray:
+    """The (2 radius + 1)^2 states of a pool variable: 2-D offsets (dy, dx), row-major."""
+    r = np.arange(-radius, radius + 1)
+    dy, dx = np.meshgrid(r, r, indexing="ij")
+    return np.stack([dy.ravel(), dx.ravel()], axis=1)
+
+
+def pool_grid(side: int, radius: int, slack: int, seed: int, T: float = 0.0, damping: float = 0.5,
+              n_iters: int = 50, shared: bool = True) -> Problem:
+    """Grid of pool variables shaped like a recursive cortical network's (Sec. 5.2):
+    each variable has K = (2 radius + 1)^2 states, one per 2-D offset of its feature
+    within the pool; a lateral pairwise factor joins 4-neighbours and lists only the
+    offset pairs that differ by at most `slack` in each coordinate (a sparse list of
+    configurations, e.g. 361 of 49 x 49 for radius 3, slack 1). Log-potentials N(0, 1)
+    per listed configuration (one table for the grid, or one per factor with
+    shared=False); evidence N(0, 1) per state."""
+    rng = np.random.default_rng(seed)
+    off = pool_offsets(radius)
+    K = off.shape[0]
+    d = np.abs(off[:, None, :] - off[None, :, :]).max(axis=2)
+    a, b = np.nonzero(d <= slack)
+    cfg = np.stack([a, b], axis=1).astype(np.int32)
+    pairs = grid_pairs(side, side)
+    n_pot = cfg.shape[0] if shared else cfg.shape[0] * pairs.shape[0]
+    pot = rng.standard_normal(n_pot).astype(np.float32)
+    ev = rng.standard_normal(side * side * K).astype(np.float32)
+    g = FactorGraph(np.full(side * side, K, np.int32), [EnumGroup(cfg, pairs, shared)], [])
+    return Problem(f"pool{side}x{side}K{K}s{slack}", g, pot, ev, T, damping, n_iters)
+
+
+def random_enum_factors(seed: int, n_vars: int, K: int, arity: int, n_fac: int, n_cfg: int,
+                        shared: bool = True, T: float = 1.0, damping: float = 0.5,
+                        n_iters: int = 20, scale: float = 1.0) -> Problem:
+    """n_fac factors of `arity` distinct variables drawn at random among n_vars K-state
+    variables, sharing one random list of n_cfg distinct configurations (at most K^arity);
+    log-potentials and evidence N(0, scale^2)."""
+    rng = np.random.default_rng(seed)
+    total = K ** arity
+    n_cfg = min(n_cfg, total)
+    if total <= 1 << 22:
+        codes = np.sort(rng.choice(total, size=n_cfg, replace=False))
+    else:
+        codes = np.unique(rng.integers(0, total, size=2 * n_cfg))[:n_cfg]
+    cfg = np.stack([(codes // K ** (arity - 1 - j)) % K for j in range(arity)], axis=1).astype(np.int32)
+    vars_ = np.stack([rng.choice(n_vars, size=arity, replace=False) for _ in range(n_fac)]).astype(np.int32)
+    n_pot = cfg.shape[0] if shared else cfg.shape[0] * n_fac
+    pot = (scale * rng.standard_normal(n_pot)).astype(np.float32)
+    ev = (scale * rng.standard_normal(n_vars * K)).astype(np.float32)
+    g = FactorGraph(np.full(n_vars, K, np.int32), [EnumGroup(cfg, vars_, shared)], [])
+    return Problem(f"enum{arity}xK{K}c{cfg.shape[0]}", g, pot, ev, T, damping, n_iters)
+
+
 def union(problems: list[Problem], name: str = "batch") -> Problem:
     """Disjoint union of several graphs: variables, groups, log-potentials and evidence
     concatenated in order. All members must share T and damping; the iteration count

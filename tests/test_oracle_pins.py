@@ -10,6 +10,8 @@
   enumeration over all parent configurations, for T in {0, 0.5, 1}.
 * Special cases: one parent copies the child's log-odds and vice versa; no parents
   forces the child to 0 (OR) or 1 (AND); a 2-variable Ising pair has a closed form.
+* Large sparse configuration lists (40-state chain, pairs within 3 listed): the
+  beliefs equal the forward-backward (max-)marginals of the chain.
 * MAP decode on random 30-unit RBMs (the protocol of Sec. 5.1) never beats the
   brute-force MAP and is checked against it.
 """
@@ -194,3 +196,53 @@ def test_rbm_map_protocol():
         assert got <= best + 1e-9
         recovered += bool(np.isclose(got, best, atol=1e-9))
     assert recovered >= 10
+
+
+def _chain_forward_backward(K, cfg, phis, ev, T):
+    """Exact (max-)marginals of a chain x_0 - x_1 - ... by the forward-backward
+    recursions (Rabiner 1989), in log space: phis[i] is the [K, K] table of the factor
+    between x_i and x_{i+1} (-inf where a configuration is not listed), ev[i] the
+    evidence of x_i. LSE for T = 1, max for T = 0. Returns unnormalised [n, K] scores."""
+    def red(z, axis):
+        if T == 0.0:
+            return z.max(axis=axis)
+        return B.lse(z, axis=axis)
+    n = len(ev)
+    alpha = [ev[0]]
+    for i in range(n - 1):
+        alpha.append(ev[i + 1] + red(alpha[i][:, None] + phis[i], 0))
+    beta = [np.zeros(K)] * n
+    for i in range(n - 2, -1, -1):
+        beta[i] = red(phis[i] + (ev[i + 1] + beta[i + 1])[None, :], 1)
+    return np.stack([alpha[i] + beta[i] for i in range(n)])
+
+
+@pytest.mark.parametrize("T", [1.0, 0.0])
+@pytest.mark.parametrize("shared", [True, False])
+def test_large_sparse_factor_chain_exact(T, shared):
+    """A chain of 40-state variables whose pairwise factors list only the pairs within 3
+    of each other (a large, sparse configuration list, as in Sec. 5.2): LBP is exact on
+    the chain, so the oracle's beliefs equal the forward-backward (max-)marginals."""
+    K, n = 40, 7
+    rng = np.random.default_rng(5)
+    a, b = np.nonzero(np.abs(np.arange(K)[:, None] - np.arange(K)[None, :]) <= 3)
+    cfg = np.stack([a, b], axis=1).astype(np.int32)
+    pairs = np.stack([np.arange(n - 1), np.arange(1, n)], axis=1).astype(np.int32)
+    n_pot = cfg.shape[0] * (1 if shared else n - 1)
+    lp = rng.standard_normal(n_pot)
+    ev = rng.standard_normal((n, K))
+    g = W.FactorGraph(np.full(n, K, np.int32), [W.EnumGroup(cfg, pairs, shared)], [])
+    phis = []
+    for i in range(n - 1):
+        t = np.full((K, K), -np.inf)
+        t[cfg[:, 0], cfg[:, 1]] = lp if shared else lp[i * cfg.shape[0]:(i + 1) * cfg.shape[0]]
+        phis.append(t)
+    exact = _chain_forward_backward(K, cfg, phis, ev, T)
+    msgs, fl = oracle.run_bp(g, lp, ev.ravel(), T, 0.0, n + 1)
+    _, nb, dec, fl2 = oracle.beliefs(g, ev.ravel(), msgs)
+    assert fl == 0 and fl2 == 0
+    nb = nb.reshape(n, K)
+    for v in range(n):  # defined up to one constant per variable
+        np.testing.assert_allclose(nb[v] - nb[v].max(), exact[v] - exact[v].max(), atol=1e-10)
+    if T == 0.0:
+        np.testing.assert_array_equal(dec, exact.argmax(axis=1))
