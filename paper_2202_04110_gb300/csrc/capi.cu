@@ -189,29 +189,33 @@ bool lr_eligible(const HostLayout &H) {
 // Slots of each log-ratio array: 4 per variable with the 4-slot table, else one per edge.
 int64_t lr_slot_count(const HostLayout &H) { return H.vin_tab4.empty() ? H.E : 4 * H.V; }
 
-// Block-per-factor enumeration launch (kEnumBlock), any block size: each segment's
-// factors per block (about 4 blocks per SM for a large group) and threads per output
-// state (enough to fill a 256-thread block, at most the mean list length, more for long lists;
+// Block-per-factor enumeration launch (kEnumBlock) with `threads` threads: each segment's
+// factors per block (about 8 blocks per SM for a large group) and threads per output
+// state (enough to fill the factor's team, at most the mean list length, more for long lists;
 // one with `one_lane`, which keeps the thread-per-factor kernel's summation order, so
 // that groups moved from that kernel give the same bits); block ranges; the dynamic
-// shared memory (two state-sum arrays plus the staged table).
-static int32_t plan_enum_block(EnumSeg *segs, int n_seg, int n_sm, bool one_lane, int32_t *smem) {
+// shared memory.
+static int32_t plan_enum_block(EnumSeg *segs, int n_seg, int threads, int n_sm, bool one_lane, int32_t *smem) {
     int32_t blk = 0;
     *smem = 0;
     for (int i = 0; i < n_seg; ++i) {
         EnumSeg &sg = segs[i];
-        const int64_t target = (int64_t)n_sm * 4;
+        const int64_t target = (int64_t)n_sm * 8;
         sg.fpb = (int32_t)std::max<int64_t>(1, sg.n_fac / std::max<int64_t>(target, 1));
         const int64_t mean = (int64_t)sg.arity * sg.n_cfg / std::max(sg.es_per_fac, 1);
         int lanes = 1;
-        // (a property of the group, not of the block size: results do not depend on the shape)
-        while (!one_lane && lanes < 32 && 2 * lanes <= mean && (int64_t)sg.es_per_fac * 2 * lanes <= kEnumBlockThreads)
+        // (a property of the group, not of the block size: results do not depend on the
+        // shape; a team is a warp up to kEnumWarpStateSum, else a 256-thread block)
+        const int team = sg.es_per_fac <= kEnumWarpStateSum ? 32 : kEnumBlockThreads;
+        while (!one_lane && lanes < 32 && 2 * lanes <= mean && (int64_t)sg.es_per_fac * 2 * lanes <= team)
             lanes *= 2;
         while (!one_lane && lanes < 32 && mean > 8 * lanes) lanes *= 2;
         sg.lanes = lanes;
         sg.block_begin = blk;
         blk += (sg.n_fac + sg.fpb - 1) / sg.fpb;
-        *smem = std::max(*smem, ((8 * sg.es_per_fac + 15) & ~15) + sg.table_bytes);
+        // three state-sum arrays per team (a warp, or the block), then the staged table
+        const int teams = sg.es_per_fac <= kEnumWarpStateSum ? threads / 32 : 1;
+        *smem = std::max(*smem, ((12 * sg.es_per_fac * teams + 15) & ~15) + sg.table_bytes);
     }
     return blk;
 }
@@ -310,7 +314,7 @@ pgm_status build_plan(const HostLayout &H, pgm_graph *g, Packer &pk, std::vector
             }
             if (segs.empty()) continue;
             if (variant == kEnumBlock)
-                blk = plan_enum_block(segs.data(), (int)segs.size(), g->n_sm, false, &L.smem);
+                blk = plan_enum_block(segs.data(), (int)segs.size(), threads, g->n_sm, false, &L.smem);
             L.n_seg = (int32_t)segs.size();
             L.n_blocks = blk;
             L.threads = threads;
@@ -402,6 +406,7 @@ static pgm_status build_from_descs(const void *const *descs, int n, pgm_graph **
     size_t o_cfg = pk.add(H.cfg_pool.data(), H.cfg_pool.size());
     size_t o_po = pk.add(H.paroff_pool.data(), H.paroff_pool.size());
     size_t o_bs = pk.add(H.bs_pool.data(), H.bs_pool.size());
+    size_t o_ev = H.edge_var.empty() ? 0 : pk.add(H.edge_var.data(), H.edge_var.size());
     size_t o_tab4 = H.vin_tab4.empty() ? 0 : pk.add(H.vin_tab4.data(), H.vin_tab4.size());
     std::vector<size_t> seg_off;
     std::vector<int> seg_kind;
@@ -479,6 +484,7 @@ static pgm_status build_from_descs(const void *const *descs, int n, pgm_graph **
     G.cfg_pool = reinterpret_cast<const uint8_t *>(dmem + o_cfg);
     G.paroff_pool = reinterpret_cast<const int32_t *>(dmem + o_po);
     G.bs_pool = reinterpret_cast<const int32_t *>(dmem + o_bs);
+    G.edge_var = H.edge_var.empty() ? nullptr : reinterpret_cast<const int32_t *>(dmem + o_ev);
     G.vin_tab4 = H.vin_tab4.empty() ? nullptr : reinterpret_cast<const int4 *>(dmem + o_tab4);
     G.flags = flags;
     G.v2f_hd = hd_bytes ? reinterpret_cast<float *>(smem + es_bytes + vs_bytes + 256) : nullptr;
@@ -586,7 +592,8 @@ pgm_status pgm_check_desc(const pgm_graph_desc *desc, pgm_info *info) {
     size_t nb = 0;
     for (int kk = 0; kk < kNumVarKinds; ++kk) nb += H.var_bucket_identity[kk] ? 0 : H.var_bucket[kk].size();
     size_t idx = (H.vs_off.size() + H.vin_off.size() + H.vin_es.size() + H.edge_vs.size() +
-                  H.paroff_pool.size() + H.bs_pool.size() + nb + H.vin_tab4.size()) * sizeof(int32_t) +
+                  H.paroff_pool.size() + H.bs_pool.size() + H.edge_var.size() + nb + H.vin_tab4.size()) *
+                     sizeof(int32_t) +
                  H.cfg_pool.size();
     size_t es_bytes = align_up(std::max<int64_t>(H.ES, 1) * sizeof(float), 256);
     if (lr_eligible(H))  // the slot map, the two log-ratio arrays and the table differences
@@ -1167,7 +1174,7 @@ static bool replan_factor_launch(pgm_graph *g, size_t li, int threads, cudaStrea
         }
     } else if (L.variant == kEnumBlock) {
         int32_t sm = 0;
-        blk = plan_enum_block(reinterpret_cast<EnumSeg *>(host.data()), L.n_seg, g->n_sm,
+        blk = plan_enum_block(reinterpret_cast<EnumSeg *>(host.data()), L.n_seg, threads, g->n_sm,
                               L.base_variant == kEnumGeneric, &sm);
         smem = (size_t)sm;
         if (prepare_kernels(sm) != cudaSuccess) return false;

@@ -208,6 +208,7 @@ std::string compile_graph(const void *const *vdescs, int n_desc, HostLayout *L) 
             s.fpb = 1;
             s.lanes = 1;
             s.table_bytes = 0;
+            s.packed = 0;
             if (g.n_fac > 0 && (hg.variant == kEnumGeneric || hg.variant == kEnumBlock)) {
                 // configuration lists by output state: for neighbour j and state x, the
                 // configurations with state x at j (the block form's gather order)
@@ -222,8 +223,16 @@ std::string compile_graph(const void *const *vdescs, int n_desc, HostLayout *L) 
                     for (int c = 0; c < g.n_cfg; ++c) bo[s.Koff[j] + g.cfg[(int64_t)c * g.arity + j] + 1]++;
                 for (int o = 0; o < off; ++o) bo[o + 1] += bo[o];
                 std::vector<int32_t> fill(bo, bo + off);
+                // pairwise groups with fewer than 2^20 configurations: each entry also
+                // carries the other neighbour's state offset (the state sum is <= 2048)
+                s.packed = (g.arity == 2 && g.n_cfg < (1 << 20)) ? 1 : 0;
                 for (int j = 0; j < g.arity; ++j)
-                    for (int c = 0; c < g.n_cfg; ++c) bl[fill[s.Koff[j] + g.cfg[(int64_t)c * g.arity + j]]++] = c;
+                    for (int c = 0; c < g.n_cfg; ++c) {
+                        const int64_t r = (int64_t)c * g.arity;
+                        int32_t ent = c;
+                        if (s.packed) ent = (c << 11) | (s.Koff[1 - j] + g.cfg[r + 1 - j]);
+                        bl[fill[s.Koff[j] + g.cfg[r + j]]++] = ent;
+                    }
                 // threads per output state from the mean list length (about 8 configs each)
                 const int64_t mean = nl / std::max<int32_t>(off, 1);
                 while (s.lanes < 32 && mean > 8 * s.lanes) s.lanes *= 2;
@@ -325,6 +334,12 @@ std::string compile_graph(const void *const *vdescs, int n_desc, HostLayout *L) 
         int32_t v = edge_var[i];
         if (L->vin_off[v + 1] - L->vin_off[v] > kVarBlockDegree) L->edge_vs[i] = -1;
     }
+
+    // each edge's variable, for the block-per-factor kernel's explicit sums
+    L->edge_var.clear();
+    bool listed = false;
+    for (const HostEnumGroup &hg : L->enum_groups) listed |= hg.seg.bs_base >= 0;
+    if (listed) L->edge_var = edge_var;
 
     L->all_binary = (kmax == 2);
     for (int64_t v = 0; v < V && L->all_binary; ++v)

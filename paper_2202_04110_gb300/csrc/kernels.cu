@@ -201,6 +201,22 @@ __device__ __noinline__ void v2f_slow_edge(const DevGraph G, const float *__rest
 
 __device__ __forceinline__ bool needs_exact(float mv) { return !(fabsf(mv) <= kExactThreshold); }
 
+// v2f_slow_edge for the edge of variable v, the states spread over the lanes of a warp
+// (same sums, same bits).
+__device__ __noinline__ void v2f_slow_edge_warp(const DevGraph G, const float *__restrict__ ev,
+                                                const float *__restrict__ m, int v, int vs, int es, int K,
+                                                float *out, int lane) {
+    const int k0 = G.vin_off[v], k1 = G.vin_off[v + 1];
+    for (int x = lane; x < K; x += 32) {
+        FF s = ff_make(ev[vs + x]);
+        for (int k = k0; k < k1; ++k) {
+            const int e2 = G.vin_es[k];
+            if (e2 != es) s = ff_add(s, m[e2 + x]);
+        }
+        out[x] = s.hi + s.lo;
+    }
+}
+
 // Exact leave-one-out values of a high-degree variable's edge, stored as float-float
 // (hi, lo) pairs in G.v2f_hd, shifted so that the edge's largest state is 0 (factor
 // updates are invariant to a per-edge constant) and rounded once to FP32.
@@ -1435,20 +1451,25 @@ k_enum_generic(DevGraph G, const EnumSeg *__restrict__ segs, int n_seg, const fl
 }
 
 // =====================================================================================
-// Factor pass: large listed-configuration factors, a block per run of factors
+// Factor pass: large listed-configuration factors, a team per factor
 // =====================================================================================
 
 // Factors given by a long list of valid configurations or with many states (Sec. 5.2:
 // RCN's non-standard pairwise factors are specified this way), beyond the thread-per-factor
-// kernel's kMaxStateSum. A block takes fpb consecutive factors of one group. The group's
-// table (each configuration's states, the configurations listed by output edge-state, a
-// shared log-potential table) is staged once per block in shared memory when it fits
-// (table_bytes > 0), else read in place. Per factor:
-//   (1) a warp per edge writes the edge's variable-to-factor values to shared memory;
+// kernel's kMaxStateSum. A block takes fpb consecutive factors of one group; a team -- a
+// warp when the state sum is at most kEnumWarpStateSum (so a 256-thread block has 8
+// factors in flight and no block-wide barrier), else the whole block -- takes one factor
+// at a time. The group's table (each configuration's states, the configurations listed
+// by output edge-state, a shared log-potential table) is staged once per block in shared
+// memory when it fits (table_bytes > 0), else read in place. Per factor:
+//   (1) a thread per edge-state writes b - m to the team's shared arrays (keeping m for
+//       step 3); an edge with an entry that needs the explicit sums, or of a high-degree
+//       variable, is then redone by a warp;
 //   (2) `lanes` threads per output edge-state (j, x) walk the configurations with state
 //       x at neighbour j; each value is the log-potential plus the other neighbours'
 //       variable-to-factor values, reduced by max (T = 0) or a running log-sum-exp
-//       (T > 0); the lanes of an output combine by shuffles;
+//       (T > 0); the lanes of an output combine by shuffles; a pairwise group's list
+//       entries carry the other neighbour's state offset with the configuration id;
 //   (3) a warp per edge normalises, damps and normalises the edge's message.
 // Every output sums its terms in neighbour order and, with one lane, reduces its
 // configurations in ascending order, as the thread-per-factor kernel does: the two then
@@ -1460,27 +1481,35 @@ k_enum_block(DevGraph G, const EnumSeg *__restrict__ segs, int n_seg, const floa
              float *__restrict__ m_new, float T, float invT, float damping) {
     extern __shared__ __align__(16) unsigned char eb_smem[];
     __shared__ int sK[kMaxArity], sKo[kMaxArity];
+    __shared__ int s_fix[kEnumBlockThreads / 32][kMaxArity];
     const EnumSeg *S = segs + find_seg(segs, n_seg, blockIdx.x);
     const int a = __ldg(&S->arity), nc = __ldg(&S->n_cfg), ksum = __ldg(&S->es_per_fac);
     const int fpb = __ldg(&S->fpb), L = __ldg(&S->lanes), tb = __ldg(&S->table_bytes);
-    const int n_fac = __ldg(&S->n_fac), shared = __ldg(&S->shared);
+    const int n_fac = __ldg(&S->n_fac), shared = __ldg(&S->shared), packed = __ldg(&S->packed);
     const int f0 = (blockIdx.x - __ldg(&S->block_begin)) * fpb;
     const int f1 = min(n_fac, f0 + fpb);
     if (threadIdx.x < a) {
         sK[threadIdx.x] = __ldg(&S->K[threadIdx.x]);
         sKo[threadIdx.x] = __ldg(&S->Koff[threadIdx.x]);
     }
-    float *v2f = reinterpret_cast<float *>(eb_smem);  // [ksum]
-    float *out = v2f + ksum;                        // [ksum]
+    // teams (uniform over the block)
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    const bool wteam = ksum <= kEnumWarpStateSum;
+    const int tsize = wteam ? 32 : (int)blockDim.x, trank = wteam ? lane : (int)threadIdx.x;
+    const int team = wteam ? warp : 0, n_teams = wteam ? nw : 1;
+    const int ej0 = wteam ? 0 : warp, ejs = wteam ? 1 : nw;  // the edges a warp takes
+    float *v2f = reinterpret_cast<float *>(eb_smem) + (size_t)team * 3 * ksum;  // [ksum]
+    float *out = v2f + ksum;                                                  // [ksum]
+    float *smo = out + ksum;                                                  // [ksum]
     const int cfg_bytes = (nc * a + 15) & ~15;
-    const int ob = (ksum + 1 + 3) & ~3;              // offsets block, then the lists
+    const int ob = (ksum + 1 + 3) & ~3;  // offsets block, then the lists
     const int bs_len = (ob + a * nc + 3) & ~3;
     const uint8_t *cfg = G.cfg_pool + __ldg(&S->cfg_base);
     const int32_t *bs = G.bs_pool + __ldg(&S->bs_base);
     const float *phi_g = pot + __ldg(&S->pot_base);
     const float *phi_tab = phi_g;
     if (tb > 0) {  // 16-byte aligned sources (pool layout) and destinations
-        unsigned char *t = eb_smem + ((8 * ksum + 15) & ~15);
+        unsigned char *t = eb_smem + ((12 * ksum * n_teams + 15) & ~15);
         const uint4 *c_src = reinterpret_cast<const uint4 *>(cfg);
         uint4 *c_dst = reinterpret_cast<uint4 *>(t);
         for (int i = threadIdx.x; i < cfg_bytes / 16; i += blockDim.x) c_dst[i] = __ldg(c_src + i);
@@ -1496,45 +1525,95 @@ k_enum_block(DevGraph G, const EnumSeg *__restrict__ segs, int n_seg, const floa
         cfg = t;
         bs = tbs;
     }
-    __syncthreads();
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    const int ng = blockDim.x / L, gi = threadIdx.x / L, gl = threadIdx.x - gi * L;
+    __syncthreads();  // the last block-wide barrier when teams are warps
+    auto team_sync = [&]() {
+        if (wteam) __syncwarp();
+        else __syncthreads();
+    };
+    const int ng = tsize / L, gi = trank / L, gl = trank - gi * L;
     const int32_t *lst = bs + ob;
     const float w = 1.f - damping;
-    for (int f = f0; f < f1; ++f) {
+    for (int f = f0 + team; f < f1; f += n_teams) {
         const int es_f = __ldg(&S->es_base) + f * ksum;
         const int e_f = __ldg(&S->edge_base) + f * a;
-        // (1) variable-to-factor values, a warp per edge (see k_enum_generic)
-        for (int j = warp; j < a; j += nw) {
+        // (1) variable-to-factor values (as in k_enum_generic)
+        if (trank < a) s_fix[team][trank] = 0;
+        team_sync();
+        for (int t = trank; t < ksum; t += tsize) {
+            int j = 0;
+            for (int k = 1; k < a; ++k)
+                if (t >= sKo[k]) j = k;
+            const int vs = __ldg(G.edge_vs + e_f + j);
+            const float mo = __ldg(m_old + es_f + t);
+            smo[t] = mo;
+            if (vs < 0 || needs_exact(mo)) s_fix[team][j] = 1;  // benign race: all write 1
+            else v2f[t] = __ldg(b + vs + t - sKo[j]) - mo;
+        }
+        team_sync();
+        for (int j = ej0; j < a; j += ejs) {
+            if (!s_fix[team][j]) continue;  // warp-uniform
             const int vs = __ldg(G.edge_vs + e_f + j), es = es_f + sKo[j], K = sK[j];
             float *vj = v2f + sKo[j];
-            if (vs < 0) {
-                if (lane == 0) {
-                    float2 hmx = make_float2(-CUDART_INF_F, 0.f);
-                    for (int x = 0; x < K; ++x) {
-                        const float2 q = hd_pair(G, es, x);
-                        if (x == 0 || hd_gt(q, hmx)) hmx = q;
-                    }
-                    for (int x = 0; x < K; ++x)
-                        vj[x] = hmx.x == -CUDART_INF_F ? -CUDART_INF_F : hd_rel(hd_pair(G, es, x), hmx);
-                }
-            } else {
-                bool exact = false;
-                for (int x = lane; x < K; x += 32) exact |= needs_exact(__ldg(m_old + es + x));
-                if (__any_sync(0xffffffffu, exact)) {
-                    if (lane == 0) v2f_slow_edge(G, ev, m_old, vs, es, K, vj);
-                } else {
-                    for (int x = lane; x < K; x += 32) vj[x] = __ldg(b + vs + x) - __ldg(m_old + es + x);
+            if (vs >= 0) {
+                v2f_slow_edge_warp(G, ev, m_old, __ldg(G.edge_var + e_f + j), vs, es, K, vj, lane);
+                continue;
+            }
+            // the largest state (first of equals), then every state relative to it
+            float2 hmx = make_float2(-CUDART_INF_F, 0.f);
+            int hx = K;
+            for (int x = lane; x < K; x += 32) {
+                const float2 q = hd_pair(G, es, x);
+                if (hx == K || hd_gt(q, hmx)) {
+                    hmx = q;
+                    hx = x;
                 }
             }
+            for (int d = 16; d > 0; d >>= 1) {
+                const float2 q = make_float2(__shfl_xor_sync(0xffffffffu, hmx.x, d),
+                                             __shfl_xor_sync(0xffffffffu, hmx.y, d));
+                const int qx = __shfl_xor_sync(0xffffffffu, hx, d);
+                const bool take = qx < K && (hx == K || hd_gt(q, hmx) || (!hd_gt(hmx, q) && qx < hx));
+                if (take) {
+                    hmx = q;
+                    hx = qx;
+                }
+            }
+            for (int x = lane; x < K; x += 32)
+                vj[x] = hmx.x == -CUDART_INF_F ? -CUDART_INF_F : hd_rel(hd_pair(G, es, x), hmx);
         }
-        __syncthreads();
+        team_sync();
         // (2) every output edge-state over its configurations
         const float *phi = shared ? phi_tab : phi_g + (size_t)f * nc;
         for (int base = 0; base < ksum; base += ng) {
             const int o = base + gi;
             float mx = kNegInf, sm = 0.f;
-            if (o < ksum) {
+            if (o < ksum && packed) {
+                // pairwise: entry = (configuration << 11) | the other neighbour's
+                // state offset; at T = 0 two independent max chains
+                const int i1 = bs[o + 1];
+                int i = bs[o] + gl;
+                if (MAXP) {
+                    float mb = kNegInf;
+                    for (; i + L < i1; i += 2 * L) {
+                        const int e0 = lst[i], e1 = lst[i + L];
+                        mx = fmaxf(mx, phi[e0 >> 11] + v2f[e0 & 2047]);
+                        mb = fmaxf(mb, phi[e1 >> 11] + v2f[e1 & 2047]);
+                    }
+                    mx = fmaxf(mx, mb);
+                }
+                for (; i < i1; i += L) {
+                    const int e = lst[i];
+                    const float val = phi[e >> 11] + v2f[e & 2047];
+                    if (MAXP) {
+                        mx = fmaxf(mx, val);
+                    } else if (val > mx) {
+                        sm = sm * expf((mx - val) * invT) + 1.f;
+                        mx = val;
+                    } else if (val > kNegInf) {
+                        sm += expf((val - mx) * invT);
+                    }
+                }
+            } else if (o < ksum) {
                 int j = 0;
                 for (int k = 1; k < a; ++k)
                     if (o >= sKo[k]) j = k;
@@ -1571,11 +1650,11 @@ k_enum_block(DevGraph G, const EnumSeg *__restrict__ segs, int n_seg, const floa
             }
             if (o < ksum && gl == 0) out[o] = (MAXP || mx == kNegInf) ? mx : mx + T * logf(sm);
         }
-        __syncthreads();
+        team_sync();
         // (3) normalise, damp, normalise; a warp per edge, up to 8 states per lane
-        for (int j = warp; j < a; j += nw) {
+        for (int j = ej0; j < a; j += ejs) {
             const int K = sK[j], es = es_f + sKo[j];
-            const float *t = out + sKo[j];
+            const float *t = out + sKo[j], *mo = smo + sKo[j];
             float v[kMaxStates / 32];
             float mx = kNegInf;
 #pragma unroll
@@ -1592,7 +1671,7 @@ k_enum_block(DevGraph G, const EnumSeg *__restrict__ segs, int n_seg, const floa
                 const int x = lane + 32 * r;
                 if (x < K) {
                     float y = mx == kNegInf ? 0.f : v[r] - mx;
-                    if (damping != 0.f) y = damping * __ldg(m_old + es + x) + w * y;
+                    if (damping != 0.f) y = damping * mo[x] + w * y;
                     v[r] = y;
                     if (y > mx2) mx2 = y;
                 }

@@ -22,6 +22,7 @@ constexpr int kMaxStateSum = 64;          // thread-per-factor enumeration kerne
 constexpr int kEnumBlockStateSum = 2048;  // block-per-factor form (kMaxArity x kMaxStates)
 constexpr int kEnumGenericMaxCfg = 256;   // longer configuration lists use the block form
 constexpr int kEnumBlockThreads = 256;
+constexpr int kEnumWarpStateSum = 256;  // block form: a warp per factor up to this state sum
 constexpr int kEnumTableSmem = 160 * 1024;  // largest configuration table staged per block
 constexpr int kMaxStates = 256;
 constexpr int kVarBlockDegree = 64;  // variables with more factors use a block each
@@ -71,6 +72,7 @@ struct EnumSeg {
     int32_t fpb;          // factors per block (set by the planner)
     int32_t lanes;        // threads per output state (1, 2, .., 32)
     int32_t table_bytes;  // bytes of the table staged in shared memory (0: read in place)
+    int32_t packed;       // 1: pairwise, list entries (c << 11) | (Koff[other] + state)
 };
 
 // One logical group as seen by a launch. Factor f owns edges
@@ -104,6 +106,7 @@ struct DevGraph {
                              // pairs, for edges of high-degree variables (edge_vs = -1);
                              // null if there are none
     const int32_t *bs_pool;  // configuration lists by output state (EnumSeg::bs_base)
+    const int32_t *edge_var; // [E] each edge's variable (graphs with such lists), else null
     const int32_t *lr_pos;   // [E] Plan::lr graphs: each edge's slot in the log-ratio
                              // arrays (k V + v with vin_tab4, else its CSR index); else null
 };
@@ -171,6 +174,7 @@ struct HostLayout {
     int64_t V = 0, VS = 0, E = 0, ES = 0, F = 0, P = 0;
     int32_t max_states = 0, max_degree = 0;
     std::vector<int32_t> vs_off, vin_off, vin_es, edge_vs;
+    std::vector<int32_t> edge_var;  // [E] when a group has lists by output state, else empty
     std::vector<uint8_t> cfg_pool;    // each group's table starts on a 16-byte boundary
     std::vector<int32_t> paroff_pool;
     std::vector<int32_t> bs_pool;     // each group's lists start on a 16-byte boundary
