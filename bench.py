@@ -52,6 +52,9 @@ def parse_args():
     ap.add_argument("--batch-grids", type=int, default=256)
     ap.add_argument("--no-multi", action="store_true", help="skip the multi-evidence measurement")
     ap.add_argument("--no-grad", action="store_true", help="skip the gradient measurement")
+    ap.add_argument("--pool-probe", default="",
+                    help="SIDE,RADIUS,SLACK: a short uncaptured run of a pool grid (large listed-"
+                         "configuration factors, T=0) for ncu captures of its kernels")
     ap.add_argument("--batch-probe", type=int, default=0,
                     help="only run the batched workload for N iterations (3 runs, no CUDA graphs; for ncu)")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
@@ -756,9 +759,34 @@ def batch_probe(args):
                       "launch_shapes": g.launches()}))
 
 
+def pool_probe(args):
+    """A short, uncaptured run of a pool grid (`--pool-probe SIDE,RADIUS,SLACK`, T=0,
+    damping 0.5) for ncu captures of the block-form enumeration kernel: three runs of 10
+    iterations, CUDA graphs off. Prints one JSON line with the launch shapes."""
+    import torch
+    from paper_2202_04110_gb300 import binding, build
+    from paper_2202_04110_gb300 import workloads as W
+    build.build()
+    side, radius, slack = (int(x) for x in args.pool_probe.split(","))
+    p = W.pool_grid(side, radius, slack, 0, T=0.0, n_iters=10)
+    lp = torch.as_tensor(p.log_pot).cuda()
+    ev = torch.as_tensor(p.evidence).cuda()
+    g = binding.Graph(p.graph)
+    g.set_option(binding.OPT_CUDA_GRAPH, 0)
+    m = g.new_msgs()
+    for _ in range(3):
+        m.zero_()
+        g.run_bp(lp, ev, 0.0, 0.5, 10, m)
+    torch.cuda.synchronize()
+    print(json.dumps({"pool_probe": args.pool_probe, "n_factors": g.info["n_factors"],
+                      "n_edge_states": g.info["n_edge_states"], "launch_shapes": g.launches()}))
+
+
 def main():
     args = parse_args()
-    if args.batch_probe:
+    if args.pool_probe:
+        pool_probe(args)
+    elif args.batch_probe:
         batch_probe(args)
     elif args.impl == "reference":
         run_reference(args)

@@ -153,12 +153,13 @@ struct Packer {
 };
 
 // Lanes that work on one variable: K / 4 for the K-state group kernels (4 states per
-// lane), else 1 (per block for kVarBlock).
+// lane), a warp for kVarWarp, else 1 (per block for kVarBlock).
 int var_lanes(int kind) {
     switch (kind) {
         case kVarGroup4: return 1;  // K / 4 lanes per variable, 4 states each
         case kVarGroup8: return 2;
         case kVarGroup16: return 4;
+        case kVarWarp: return 32;
         default: return 1;
     }
 }
@@ -211,6 +212,7 @@ static int32_t plan_enum_block(EnumSeg *segs, int n_seg, int threads, int n_sm, 
             lanes *= 2;
         while (!one_lane && lanes < 32 && mean > 8 * lanes) lanes *= 2;
         sg.lanes = lanes;
+        sg.ordered = one_lane ? 1 : 0;
         sg.block_begin = blk;
         blk += (sg.n_fac + sg.fpb - 1) / sg.fpb;
         // three state-sum arrays per team (a warp, or the block), then the staged table
@@ -454,7 +456,8 @@ static pgm_status build_from_descs(const void *const *descs, int n, pgm_graph **
     size_t hd_bytes = H.var_bucket[kVarBlock].empty() ? 0 : 2 * es_bytes;
     const size_t lr_bytes = g->P.lr ? align_up((size_t)g->lr_slots * sizeof(float), 256) : 0;
     const size_t prm_bytes = g->P.lr ? align_up((size_t)3 * (H.E / 2) * sizeof(float), 256) : 0;
-    const size_t scratch_bytes = es_bytes + vs_bytes + 256 + hd_bytes + 2 * lr_bytes + prm_bytes;
+    const size_t blo_bytes = H.var_bucket[kVarWarp].empty() ? 0 : vs_bytes;
+    const size_t scratch_bytes = es_bytes + vs_bytes + 256 + hd_bytes + 2 * lr_bytes + prm_bytes + blo_bytes;
     char *smem = nullptr;
     ce = ordered ? cudaMallocAsync(&smem, scratch_bytes, s) : cudaMalloc(&smem, scratch_bytes);
     if (ce != cudaSuccess) {
@@ -489,6 +492,9 @@ static pgm_status build_from_descs(const void *const *descs, int n, pgm_graph **
     G.flags = flags;
     G.v2f_hd = hd_bytes ? reinterpret_cast<float *>(smem + es_bytes + vs_bytes + 256) : nullptr;
     G.lr_pos = g->P.lr ? reinterpret_cast<const int32_t *>(dmem + o_lr_pos) : nullptr;
+    G.b_lo = blo_bytes ? reinterpret_cast<float *>(smem + es_bytes + vs_bytes + 256 + hd_bytes + 2 * lr_bytes +
+                                                    prm_bytes)
+                       : nullptr;
     if (g->P.lr) {
         g->lr_d = reinterpret_cast<float *>(smem + es_bytes + vs_bytes + 256 + hd_bytes);
         g->lr_lam = reinterpret_cast<float *>(smem + es_bytes + vs_bytes + 256 + hd_bytes + lr_bytes);
@@ -599,8 +605,9 @@ pgm_status pgm_check_desc(const pgm_graph_desc *desc, pgm_info *info) {
     if (lr_eligible(H))  // the slot map, the two log-ratio arrays and the table differences
         idx += H.E * sizeof(int32_t) + 2 * align_up((size_t)lr_slot_count(H) * sizeof(float), 256) +
                align_up((size_t)3 * (H.E / 2) * sizeof(float), 256);
-    info->device_bytes = (int64_t)(idx + es_bytes + align_up(std::max<int64_t>(H.VS, 1) * sizeof(float), 256) +
-                                   256 + (H.var_bucket[kVarBlock].empty() ? 0 : 2 * es_bytes));
+    const size_t vs_bytes = align_up(std::max<int64_t>(H.VS, 1) * sizeof(float), 256);
+    info->device_bytes = (int64_t)(idx + es_bytes + vs_bytes + 256 + (H.var_bucket[kVarBlock].empty() ? 0 : 2 * es_bytes) +
+                                   (H.var_bucket[kVarWarp].empty() ? 0 : vs_bytes));
     return PGM_OK;
 }
 
@@ -1286,7 +1293,7 @@ pgm_status pgm_launch_info(const pgm_graph *g, int32_t i, int32_t *kind, int32_t
     if (i < nv) {
         const VarLaunch &L = g->P.var[i];
         if (kind) *kind = 0;
-        if (variant) *variant = g->G.vin_tab4 ? 6 : L.kind;
+        if (variant) *variant = g->G.vin_tab4 ? 6 : (L.kind == kVarWarp ? 7 : L.kind);
         if (threads) *threads = L.kind == kVarBlock ? kVarBlockThreads : (g->G.vin_tab4 ? 256 : L.threads);
         if (n_blocks) *n_blocks = g->G.vin_tab4 ? (int32_t)((g->info.n_vars + 255) / 256) : L.n_blocks;
     } else {

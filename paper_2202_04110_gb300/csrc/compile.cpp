@@ -209,6 +209,7 @@ std::string compile_graph(const void *const *vdescs, int n_desc, HostLayout *L) 
             s.lanes = 1;
             s.table_bytes = 0;
             s.packed = 0;
+            s.ordered = 0;
             if (g.n_fac > 0 && (hg.variant == kEnumGeneric || hg.variant == kEnumBlock)) {
                 // configuration lists by output state: for neighbour j and state x, the
                 // configurations with state x at j (the block form's gather order)
@@ -324,6 +325,8 @@ std::string compile_graph(const void *const *vdescs, int n_desc, HostLayout *L) 
             kind = kVarGroup8;
         } else if (K[v] == 16) {
             kind = kVarGroup16;
+        } else if (K[v] > 16) {
+            kind = kVarWarp;
         } else {
             kind = kVarGeneric;
         }

@@ -28,7 +28,6 @@
 // explicit leave-one-out sum (v2f_slow_edge) instead of b - m; edges of variables with
 // more than kVarBlockDegree factors always do (computed by the block variable pass).
 #include <algorithm>
-#include <atomic>
 #include <cstdint>
 
 #include <cuda_runtime.h>
@@ -200,22 +199,6 @@ __device__ __noinline__ void v2f_slow_edge(const DevGraph G, const float *__rest
 }
 
 __device__ __forceinline__ bool needs_exact(float mv) { return !(fabsf(mv) <= kExactThreshold); }
-
-// v2f_slow_edge for the edge of variable v, the states spread over the lanes of a warp
-// (same sums, same bits).
-__device__ __noinline__ void v2f_slow_edge_warp(const DevGraph G, const float *__restrict__ ev,
-                                                const float *__restrict__ m, int v, int vs, int es, int K,
-                                                float *out, int lane) {
-    const int k0 = G.vin_off[v], k1 = G.vin_off[v + 1];
-    for (int x = lane; x < K; x += 32) {
-        FF s = ff_make(ev[vs + x]);
-        for (int k = k0; k < k1; ++k) {
-            const int e2 = G.vin_es[k];
-            if (e2 != es) s = ff_add(s, m[e2 + x]);
-        }
-        out[x] = s.hi + s.lo;
-    }
-}
 
 // Exact leave-one-out values of a high-degree variable's edge, stored as float-float
 // (hi, lo) pairs in G.v2f_hd, shifted so that the edge's largest state is 0 (factor
@@ -506,6 +489,111 @@ __global__ void __launch_bounds__(256) k_var_thread(DevGraph G, const int32_t *_
                 for (int x = 0; x < K; ++x) out[vs + x] -= z;
             }
         }
+    }
+}
+
+// Warp per variable with more than 16 states (and at most kVarBlockDegree factors): lane
+// l takes states l, l + 32, ..; each state's float-float sum adds the evidence and the
+// incoming messages in ascending edge order, as k_var_thread does, and the best state is
+// the first of the largest, so beliefs, decodes and the iteration's values have the same
+// bits (normalised beliefs sum e^r in another order). The iteration also writes b_lo,
+// the rounding residual of each value, so that a factor can form b - m without the
+// cancellation a large message would cause.
+template <int MODE>
+__global__ void __launch_bounds__(256) k_var_warp(DevGraph G, const int32_t *__restrict__ list, int n,
+                                                  const float *__restrict__ ev, const float *__restrict__ m,
+                                                  float *__restrict__ out, int32_t *__restrict__ dec) {
+    const int w = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+    if (w >= n) return;  // warp-uniform
+    const int v = list ? __ldg(list + w) : w;
+    const int k0 = __ldg(G.vin_off + v), k1 = __ldg(G.vin_off + v + 1);
+    const int vs = __ldg(G.vs_off + v), K = __ldg(G.vs_off + v + 1) - vs;
+    constexpr int R = kMaxStates / 32;
+    FF s[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int x = lane + 32 * r;
+        s[r] = ff_make(x < K ? __ldg(ev + vs + x) : kNegInf);
+    }
+    for (int k = k0; k < k1; ++k) {
+        const int es = __ldg(G.vin_es + k);
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int x = lane + 32 * r;
+            if (x < K) s[r] = ff_add(s[r], __ldg(m + es + x));
+        }
+    }
+    FF best = ff_make(kNegInf);
+    int arg = K;
+    bool nan = false;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int x = lane + 32 * r;
+        if (x < K) {
+            nan |= (s[r].hi != s[r].hi);
+            if (arg == K || ff_gt(s[r], best)) {
+                best = s[r];
+                arg = x;
+            }
+        }
+    }
+    for (int d = 16; d > 0; d >>= 1) {  // first of the largest over the warp
+        FF q;
+        q.hi = __shfl_xor_sync(0xffffffffu, best.hi, d);
+        q.lo = __shfl_xor_sync(0xffffffffu, best.lo, d);
+        const int qa = __shfl_xor_sync(0xffffffffu, arg, d);
+        if (qa < K && (arg == K || ff_gt(q, best) || (!ff_gt(best, q) && qa < arg))) {
+            best = q;
+            arg = qa;
+        }
+    }
+    nan = __any_sync(0xffffffffu, nan);
+    if constexpr (MODE == kVarDecode) {
+        if (lane == 0) dec[v] = arg;
+        return;
+    }
+    if constexpr (MODE == kVarBeliefs) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int x = lane + 32 * r;
+            if (x < K) out[vs + x] = s[r].hi + s[r].lo;
+        }
+        return;
+    }
+    if (best.hi == kNegInf) {
+        if (MODE == kVarNormalised && lane == 0) atomicOr(G.flags, kFlagContradiction);
+        for (int x = lane; x < K; x += 32) out[vs + x] = kNegInf;
+        return;
+    }
+    if (nan && MODE == kVarNormalised && lane == 0) atomicOr(G.flags, kFlagNaN);
+    float rr[R];
+    float acc = 0.f;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int x = lane + 32 * r;
+        rr[r] = (x == arg) ? 0.f : ff_diff(s[r], best);
+        if (MODE == kVarNormalised && x < K && x != arg) acc += expf(rr[r]);
+        if (MODE == kVarIter && x < K && G.b_lo != nullptr) {
+            // s - best as a float-float (two-sum of the high parts plus the low parts),
+            // less the rounded value rr: the part of the difference rr dropped
+            float lo = 0.f;
+            if (x != arg && isfinite(s[r].hi) && isfinite(best.hi)) {
+                const float th = s[r].hi - best.hi, bb = th - s[r].hi;
+                const float te = (s[r].hi - (th - bb)) + (-best.hi - bb);
+                lo = (th - rr[r]) + (te + (s[r].lo - best.lo));
+            }
+            G.b_lo[vs + x] = lo;
+        }
+    }
+    float z = 0.f;
+    if constexpr (MODE == kVarNormalised) {
+        for (int d = 16; d > 0; d >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, d);
+        z = log1pf(acc);
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int x = lane + 32 * r;
+        if (x < K) out[vs + x] = rr[r] - z;
     }
 }
 
@@ -1397,16 +1485,20 @@ k_enum_generic(DevGraph G, const EnumSeg *__restrict__ segs, int n_seg, const fl
                 if (x == 0 || hd_gt(q, hmx)) hmx = q;
             }
         bool exact = false;
+        const bool lo = G.b_lo != nullptr && Kj[j] > 16;  // a variable of the warp pass
         for (int x = 0; x < Kj[j]; ++x) {
             const float mv = __ldg(m_old + es + x);
             mo[Ko[j] + x] = mv;
-            exact |= needs_exact(mv);
+            exact |= lo ? !isfinite(mv) : needs_exact(mv);
         }
         if (vs < 0) {
             for (int x = 0; x < Kj[j]; ++x)
                 v2f[Ko[j] + x] = hmx.x == -CUDART_INF_F ? -CUDART_INF_F : hd_rel(hd_pair(G, es, x), hmx);
         } else if (exact) {
             v2f_slow_edge(G, ev, m_old, vs, es, Kj[j], v2f + Ko[j]);
+        } else if (lo) {
+            for (int x = 0; x < Kj[j]; ++x)
+                v2f[Ko[j] + x] = (__ldg(b + vs + x) - mo[Ko[j] + x]) + __ldg(G.b_lo + vs + x);
         } else {
             for (int x = 0; x < Kj[j]; ++x) v2f[Ko[j] + x] = __ldg(b + vs + x) - mo[Ko[j] + x];
         }
@@ -1462,18 +1554,34 @@ k_enum_generic(DevGraph G, const EnumSeg *__restrict__ segs, int n_seg, const fl
 // at a time. The group's table (each configuration's states, the configurations listed
 // by output edge-state, a shared log-potential table) is staged once per block in shared
 // memory when it fits (table_bytes > 0), else read in place. Per factor:
-//   (1) a thread per edge-state writes b - m to the team's shared arrays (keeping m for
-//       step 3); an edge with an entry that needs the explicit sums, or of a high-degree
-//       variable, is then redone by a warp;
+//   (1) a thread per edge-state writes b - m (plus b_lo for variables with more than 16
+//       states) to the team's shared arrays, keeping m for step 3; an edge with an entry
+//       that needs the explicit sums, or of a high-degree variable, is redone by a warp;
 //   (2) `lanes` threads per output edge-state (j, x) walk the configurations with state
 //       x at neighbour j; each value is the log-potential plus the other neighbours'
 //       variable-to-factor values, reduced by max (T = 0) or a running log-sum-exp
 //       (T > 0); the lanes of an output combine by shuffles; a pairwise group's list
 //       entries carry the other neighbour's state offset with the configuration id;
 //   (3) a warp per edge normalises, damps and normalises the edge's message.
-// Every output sums its terms in neighbour order and, with one lane, reduces its
-// configurations in ascending order, as the thread-per-factor kernel does: the two then
-// give the same bits (with several lanes, T > 0 differs by rounding).
+// Every output sums its terms in neighbour order; a group with `ordered` set (one lane per
+// output) reduces its configurations in ascending order, as the thread-per-factor kernel
+// does, and the two give the same bits; otherwise T > 0 differs by rounding.
+// v2f_slow_edge for the edge of variable v, the states spread over the lanes of a warp
+// (same sums, same bits).
+__device__ __noinline__ void v2f_slow_edge_warp(const DevGraph G, const float *__restrict__ ev,
+                                                const float *__restrict__ m, int v, int vs, int es, int K,
+                                                float *out, int lane) {
+    const int k0 = G.vin_off[v], k1 = G.vin_off[v + 1];
+    for (int x = lane; x < K; x += 32) {
+        FF s = ff_make(ev[vs + x]);
+        for (int k = k0; k < k1; ++k) {
+            const int e2 = G.vin_es[k];
+            if (e2 != es) s = ff_add(s, m[e2 + x]);
+        }
+        out[x] = s.hi + s.lo;
+    }
+}
+
 template <bool MAXP>
 __global__ void __launch_bounds__(kEnumBlockThreads)
 k_enum_block(DevGraph G, const EnumSeg *__restrict__ segs, int n_seg, const float *__restrict__ pot,
@@ -1486,6 +1594,7 @@ k_enum_block(DevGraph G, const EnumSeg *__restrict__ segs, int n_seg, const floa
     const int a = __ldg(&S->arity), nc = __ldg(&S->n_cfg), ksum = __ldg(&S->es_per_fac);
     const int fpb = __ldg(&S->fpb), L = __ldg(&S->lanes), tb = __ldg(&S->table_bytes);
     const int n_fac = __ldg(&S->n_fac), shared = __ldg(&S->shared), packed = __ldg(&S->packed);
+    const int ordered = __ldg(&S->ordered);
     const int f0 = (blockIdx.x - __ldg(&S->block_begin)) * fpb;
     const int f1 = min(n_fac, f0 + fpb);
     if (threadIdx.x < a) {
@@ -1546,7 +1655,9 @@ k_enum_block(DevGraph G, const EnumSeg *__restrict__ segs, int n_seg, const floa
             const int vs = __ldg(G.edge_vs + e_f + j);
             const float mo = __ldg(m_old + es_f + t);
             smo[t] = mo;
-            if (vs < 0 || needs_exact(mo)) s_fix[team][j] = 1;  // benign race: all write 1
+            const bool lo = G.b_lo != nullptr && sK[j] > 16;  // (as in k_enum_generic)
+            if (vs < 0 || (lo ? !isfinite(mo) : needs_exact(mo))) s_fix[team][j] = 1;  // benign race
+            else if (lo) v2f[t] = (__ldg(b + vs + t - sKo[j]) - mo) + __ldg(G.b_lo + vs + t - sKo[j]);
             else v2f[t] = __ldg(b + vs + t - sKo[j]) - mo;
         }
         team_sync();
@@ -1589,17 +1700,44 @@ k_enum_block(DevGraph G, const EnumSeg *__restrict__ segs, int n_seg, const floa
             float mx = kNegInf, sm = 0.f;
             if (o < ksum && packed) {
                 // pairwise: entry = (configuration << 11) | the other neighbour's
-                // state offset; at T = 0 two independent max chains
+                // state offset; at T = 0 four independent max chains; at T > 0 two
+                // log-sum-exp chains unless the group keeps the ascending order
                 const int i1 = bs[o + 1];
                 int i = bs[o] + gl;
                 if (MAXP) {
-                    float mb = kNegInf;
+                    float m1 = kNegInf, m2 = kNegInf, m3 = kNegInf;
+                    for (; i + 3 * L < i1; i += 4 * L) {
+                        const int e0 = lst[i], e1 = lst[i + L], e2 = lst[i + 2 * L], e3 = lst[i + 3 * L];
+                        mx = fmaxf(mx, phi[e0 >> 11] + v2f[e0 & 2047]);
+                        m1 = fmaxf(m1, phi[e1 >> 11] + v2f[e1 & 2047]);
+                        m2 = fmaxf(m2, phi[e2 >> 11] + v2f[e2 & 2047]);
+                        m3 = fmaxf(m3, phi[e3 >> 11] + v2f[e3 & 2047]);
+                    }
+                    mx = fmaxf(fmaxf(mx, m1), fmaxf(m2, m3));
+                } else if (!ordered) {
+                    float mb = kNegInf, sb = 0.f;
                     for (; i + L < i1; i += 2 * L) {
                         const int e0 = lst[i], e1 = lst[i + L];
-                        mx = fmaxf(mx, phi[e0 >> 11] + v2f[e0 & 2047]);
-                        mb = fmaxf(mb, phi[e1 >> 11] + v2f[e1 & 2047]);
+                        const float va = phi[e0 >> 11] + v2f[e0 & 2047], vb = phi[e1 >> 11] + v2f[e1 & 2047];
+                        if (va > mx) {
+                            sm = sm * expf((mx - va) * invT) + 1.f;
+                            mx = va;
+                        } else if (va > kNegInf) {
+                            sm += expf((va - mx) * invT);
+                        }
+                        if (vb > mb) {
+                            sb = sb * expf((mb - vb) * invT) + 1.f;
+                            mb = vb;
+                        } else if (vb > kNegInf) {
+                            sb += expf((vb - mb) * invT);
+                        }
                     }
-                    mx = fmaxf(mx, mb);
+                    const float mn = fmaxf(mx, mb);
+                    if (mn != kNegInf) {
+                        sm = (mx == kNegInf ? 0.f : sm * expf((mx - mn) * invT)) +
+                             (mb == kNegInf ? 0.f : sb * expf((mb - mn) * invT));
+                        mx = mn;
+                    }
                 }
                 for (; i < i1; i += L) {
                     const int e = lst[i];
@@ -2704,14 +2842,15 @@ __global__ void k_until_control(cudaGraphConditionalHandle h, const unsigned *__
 // =====================================================================================
 
 // The kernels with dynamic shared memory may take up to the device's opt-in maximum
-// (set once per device; a smaller limit set later would break other graphs' launches).
+// (set once per device; a smaller limit set later would break other graphs' launches;
+// two threads that race here both set the same values).
 cudaError_t prepare_kernels(int max_smem_bytes) {
-    static std::atomic<int> done[64];
+    static volatile int done[64];
     if (max_smem_bytes <= 48 * 1024) return cudaSuccess;
     int dev = 0, optin = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
-    if (dev >= 0 && dev < 64 && done[dev].load()) return cudaSuccess;
+    if (dev >= 0 && dev < 64 && done[dev]) return cudaSuccess;
     if ((e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess) return e;
     // each kernel: the opt-in maximum less its static shared memory
     auto allow = [&](const void *fn) -> cudaError_t {
@@ -2726,7 +2865,7 @@ cudaError_t prepare_kernels(int max_smem_bytes) {
     if ((e = allow((const void *)k_logic_warp<false>)) != cudaSuccess) return e;
     if ((e = allow((const void *)k_enum_block<true>)) != cudaSuccess) return e;
     if ((e = allow((const void *)k_enum_block<false>)) != cudaSuccess) return e;
-    if (dev >= 0 && dev < 64) done[dev].store(1);
+    if (dev >= 0 && dev < 64) done[dev] = 1;
     return cudaSuccess;
 }
 
@@ -2755,6 +2894,9 @@ static void var_pass_mode(const DevGraph &G, const Plan &P, const float *ev, con
                 break;
             case kVarGroup16:
                 k_var_group<16, MODE><<<L.n_blocks, L.threads, 0, s>>>(G, L.list, L.n, ev, m, out, dec);
+                break;
+            case kVarWarp:
+                k_var_warp<MODE><<<L.n_blocks, L.threads, 0, s>>>(G, L.list, L.n, ev, m, out, dec);
                 break;
             default:
                 k_var_thread<0, MODE><<<L.n_blocks, L.threads, 0, s>>>(G, L.list, L.n, 0, ev, m, out, dec);

@@ -73,6 +73,7 @@ struct EnumSeg {
     int32_t lanes;        // threads per output state (1, 2, .., 32)
     int32_t table_bytes;  // bytes of the table staged in shared memory (0: read in place)
     int32_t packed;       // 1: pairwise, list entries (c << 11) | (Koff[other] + state)
+    int32_t ordered;      // 1: reduce each output's configurations in ascending order
 };
 
 // One logical group as seen by a launch. Factor f owns edges
@@ -107,6 +108,9 @@ struct DevGraph {
                              // null if there are none
     const int32_t *bs_pool;  // configuration lists by output state (EnumSeg::bs_base)
     const int32_t *edge_var; // [E] each edge's variable (graphs with such lists), else null
+    float *b_lo;             // [VS] for variables of the warp pass (K > 16): what the
+                             // iteration's beliefs b lost to rounding (b + b_lo is the
+                             // float-float value); null if there are none
     const int32_t *lr_pos;   // [E] Plan::lr graphs: each edge's slot in the log-ratio
                              // arrays (k V + v with vin_tab4, else its CSR index); else null
 };
@@ -132,7 +136,8 @@ enum VarKind : int32_t {
     kVarGroup4 = 3,   // K / 4 lanes per variable (4 states each), K = 4, 8, 16
     kVarGroup8 = 4,
     kVarGroup16 = 5,
-    kNumVarKinds = 6
+    kVarWarp = 6,     // warp per variable, K > 16 (pgm_launch_info reports 7)
+    kNumVarKinds = 7
 };
 
 struct VarLaunch {
