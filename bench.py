@@ -479,10 +479,11 @@ def measure_until(args, binding, W, torch, dev):
     return out
 
 
-def serve_run(binding, templates, descs, arrivals, slots, budget):
+def serve_run(binding, templates, descs, arrivals, slots, budget, tol=None):
     """Submit `arrivals` on schedule to a server with `slots` in-flight requests; wait
     for all; latencies (s) and throughput (updates/s over first submission to last
-    completion)."""
+    completion). With `tol`, each request may stop early (residual checked every 10
+    iterations; its iteration count is the limit)."""
     srv = binding.Server(memory_budget_bytes=budget, max_in_flight=slots)
     ids = []
     t0 = time.perf_counter()
@@ -491,7 +492,7 @@ def serve_run(binding, templates, descs, arrivals, slots, budget):
         if t_arr > now:
             time.sleep(t_arr - now)
         p = templates[ti]
-        ids.append(srv.submit(p.graph, p.log_pot, p.evidence, p.T, 0.5, iters, desc=descs[ti]))
+        ids.append(srv.submit(p.graph, p.log_pot, p.evidence, p.T, 0.5, iters, desc=descs[ti], tol=tol))
     t_sub = time.perf_counter() - t0
     lat = []
     for i in ids:
@@ -526,12 +527,20 @@ def measure_serving(args, binding, W):
     arr = W.poisson_arrivals(1, rate, dur, len(templates))
     out["continuous"] = serve_run(binding, templates, descs, arr, args.serve_slots, budget)
     out["fifo"] = serve_run(binding, templates, descs, arr, 1, budget)
+    # f4: the same arrivals, each request stopping once its residual is <= 1e-4
+    out["continuous_early_exit"] = serve_run(binding, templates, descs, arr, args.serve_slots, budget, tol=1e-4)
+    out["continuous_early_exit"]["tol"] = 1e-4
     out["sweep"] = []
     for f in (0.25, 0.5):
         a = W.poisson_arrivals(2, rate * f, dur, len(templates))
         r = serve_run(binding, templates, descs, a, args.serve_slots, budget)
         r["rate_req_s"] = rate * f
         out["sweep"].append(r)
+        if f == 0.25:  # below saturation: latency is service time, which early exit shortens
+            r = serve_run(binding, templates, descs, a, args.serve_slots, budget, tol=1e-4)
+            r["rate_req_s"] = rate * f
+            r["tol"] = 1e-4
+            out["sweep"].append(r)
     return out
 
 

@@ -476,6 +476,19 @@ pgm_status pgm_serve_submit(pgm_server *s, const pgm_graph_desc *desc, const flo
                             int64_t *id);
 
 /*
+ * pgm_serve_submit with an early exit: the request runs as pgm_run_bp_until (up to
+ * max_iters iterations, stopping after the first checked iteration whose residual
+ * max |m_t - m_{t-1}| is <= tol, checked every check_every iterations), so a request
+ * that converges early frees its slot and memory early. Results equal pgm_run_bp_until
+ * of the same request alone (the residual checks are host-side on the serving streams);
+ * pgm_server_stats.updates_done counts the iterations actually run. Errors as
+ * pgm_serve_submit, plus PGM_EINVAL for check_every < 1 or tol < 0 / NaN.
+ */
+pgm_status pgm_serve_submit_until(pgm_server *s, const pgm_graph_desc *desc, const float *log_pot,
+                                  const float *evidence, float T, float damping, int32_t max_iters,
+                                  float tol, int32_t check_every, int64_t *id);
+
+/*
  * Result of request `id`: PGM_EBUSY while it is queued or running; otherwise copies the
  * normalised log-beliefs [n_var_states] and decode [n_vars] into the host buffers (each
  * may be NULL), writes the latency in seconds, forgets the request and returns its

@@ -24,7 +24,7 @@ FLAG_NAN = 2
 EXPORTED = ["pgm_build", "pgm_build_batch", "pgm_batch_member", "pgm_check_desc", "pgm_free", "pgm_graph_info", "pgm_run_bp", "pgm_beliefs",
             "pgm_decode", "pgm_infer_host", "pgm_set_profiling", "pgm_pass_times",
             "pgm_device_flags", "pgm_grid2_run_bp_noalloc", "pgm_run_bp_multi", "pgm_pmp_sample", "pgm_run_bp_until", "pgm_set_option", "pgm_get_option", "pgm_autotune",
-            "pgm_launch_info", "pgm_grad", "pgm_serve_create", "pgm_serve_submit", "pgm_serve_poll",
+            "pgm_launch_info", "pgm_grad", "pgm_serve_create", "pgm_serve_submit", "pgm_serve_submit_until", "pgm_serve_poll",
             "pgm_serve_wait", "pgm_serve_stats", "pgm_serve_destroy", "pgm_last_error"]
 OPT_CUDA_GRAPH = 1
 OPT_LOG_RATIO = 2
@@ -137,6 +137,9 @@ def load_library(path: str | None = None):
     lib.pgm_serve_create.argtypes = [ctypes.POINTER(ServerConfigC), ctypes.POINTER(vp)]
     lib.pgm_serve_submit.restype = i32
     lib.pgm_serve_submit.argtypes = [vp, ctypes.POINTER(GraphDescC), vp, vp, f32, f32, i32, ctypes.POINTER(ctypes.c_int64)]
+    lib.pgm_serve_submit_until.restype = i32
+    lib.pgm_serve_submit_until.argtypes = [vp, ctypes.POINTER(GraphDescC), vp, vp, f32, f32, i32, f32, i32,
+                                           ctypes.POINTER(ctypes.c_int64)]
     lib.pgm_serve_poll.restype = i32
     lib.pgm_serve_poll.argtypes = [vp, ctypes.c_int64, vp, vp, ctypes.POINTER(ctypes.c_double)]
     lib.pgm_serve_wait.restype = i32
@@ -498,16 +501,25 @@ class Server:
         self._h = h
         self._shapes = {}
 
-    def submit(self, fg, log_pot, evidence, T: float, damping: float, n_iters: int, desc=None) -> int:
+    def submit(self, fg, log_pot, evidence, T: float, damping: float, n_iters: int, desc=None,
+               tol=None, check_every: int = 10) -> int:
         """Queue a request. `desc` may be a (desc, keepalive) pair from marshal_desc(fg),
-        reused across submissions of the same graph."""
+        reused across submissions of the same graph. With `tol`, the request stops early
+        (pgm_serve_submit_until: n_iters is the limit, the residual is checked every
+        `check_every` iterations)."""
         desc, keep = desc if desc is not None else marshal_desc(fg)
         lp = np.ascontiguousarray(log_pot, np.float32)
         ev = np.ascontiguousarray(evidence, np.float32)
         rid = ctypes.c_int64()
-        check(load_library().pgm_serve_submit(self._h, ctypes.byref(desc), lp.ctypes.data if lp.size else None,
-                                              ev.ctypes.data, float(T), float(damping), int(n_iters),
-                                              ctypes.byref(rid)))
+        lib = load_library()
+        lpp = lp.ctypes.data if lp.size else None
+        if tol is None:
+            check(lib.pgm_serve_submit(self._h, ctypes.byref(desc), lpp, ev.ctypes.data, float(T), float(damping),
+                                       int(n_iters), ctypes.byref(rid)))
+        else:
+            check(lib.pgm_serve_submit_until(self._h, ctypes.byref(desc), lpp, ev.ctypes.data, float(T),
+                                             float(damping), int(n_iters), float(tol), int(check_every),
+                                             ctypes.byref(rid)))
         del keep
         self._shapes[rid.value] = (fg.n_var_states, fg.n_vars)
         return rid.value

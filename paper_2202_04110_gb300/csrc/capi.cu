@@ -71,7 +71,8 @@ struct pgm_graph {
     // word (device), its host copy (pinned); allocated on first use
     float *until_prev = nullptr;
     unsigned *until_res = nullptr;       // residual bits; the next word counts iterations done
-    unsigned *until_res_host = nullptr;  // 2 words
+    unsigned *until_res_host = nullptr;  // 2 words (pinned; stream-ordered graphs: until_words)
+    unsigned until_words[2] = {0, 0};
     // device-side early-exit runs (conditional while node), keyed by their arguments
     struct CachedUntil {
         const float *log_pot, *evidence;
@@ -620,7 +621,10 @@ void pgm_free(pgm_graph *g) {
         if (g->index_mem) cudaFreeAsync(g->index_mem, g->alloc_stream);
         if (g->scratch_mem) cudaFreeAsync(g->scratch_mem, g->alloc_stream);
         if (g->host_io_mem) cudaFreeAsync(g->host_io_mem, g->alloc_stream);
+        if (g->until_prev) cudaFreeAsync(g->until_prev, g->alloc_stream);
         g->index_mem = g->scratch_mem = g->host_io_mem = nullptr;
+        g->until_prev = nullptr;
+        g->until_res_host = nullptr;  // until_words
     } else {
         cudaDeviceSynchronize();
     }
@@ -1007,6 +1011,14 @@ pgm_status pgm_run_bp_until(pgm_graph *g, const float *log_pot, const float *evi
     }
     DeviceGuard dg(g->device);
     if (!dg.ok) return fail(PGM_ECUDA, "cudaSetDevice failed");
+    if (!g->until_prev && g->ordered) {  // stream-ordered, no pinned word (the serving loop)
+        char *mem = nullptr;
+        if (cudaMallocAsync(&mem, align_up((size_t)ES * sizeof(float), 256) + 256, g->alloc_stream) != cudaSuccess)
+            return fail(PGM_ENOMEM, "cudaMallocAsync(residual buffers)");
+        g->until_prev = reinterpret_cast<float *>(mem);
+        g->until_res = reinterpret_cast<unsigned *>(mem + align_up((size_t)ES * sizeof(float), 256));
+        g->until_res_host = g->until_words;
+    }
     if (!g->until_prev) {
         char *mem = nullptr;
         if (cudaMalloc(&mem, align_up((size_t)ES * sizeof(float), 256) + 256) != cudaSuccess)

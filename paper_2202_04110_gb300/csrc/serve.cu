@@ -96,7 +96,9 @@ struct Request {
     DescCopy d;
     std::vector<float> log_pot, evidence;
     float T = 1.f, damping = 0.f;
-    int32_t n_iters = 0;
+    int32_t n_iters = 0;        // iterations (the limit when check_every > 0)
+    float tol = 0.f;            // early exit: residual tolerance
+    int32_t check_every = 0;    // early exit: residual checked every check_every iterations; 0 = off
     Clock::time_point t_submit, t_done;
     int32_t state = kPending;
     pgm_status status = PGM_OK;
@@ -159,7 +161,7 @@ pgm_status run_request(Request &r, cudaStream_t st, std::string &err) {
     }
     pgm_info I{};
     pgm_graph_info(g, &I);
-    r.updates = I.n_edge_states * (int64_t)r.n_iters;
+    r.updates = I.n_edge_states * (int64_t)r.n_iters;  // (early exit: iterations run)
     char *mem = nullptr;
     auto up = [](int64_t n) { return (size_t)((std::max<int64_t>(n, 1) * 4 + 255) / 256 * 256); };
     const size_t b_lp = up(I.n_potentials), b_vs = up(I.n_var_states), b_es = up(I.n_edge_states), b_v = up(I.n_vars);
@@ -178,7 +180,14 @@ pgm_status run_request(Request &r, cudaStream_t st, std::string &err) {
         e = cudaMemcpyAsync(ev, r.evidence.data(), I.n_var_states * sizeof(float), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess && I.n_edge_states > 0) e = cudaMemsetAsync(msgs, 0, I.n_edge_states * sizeof(float), st);
     rc = (e == cudaSuccess) ? PGM_OK : PGM_ECUDA;
-    if (rc == PGM_OK) rc = pgm_run_bp(g, lp, ev, r.T, r.damping, r.n_iters, msgs, st);
+    if (rc == PGM_OK && r.check_every > 0) {
+        int32_t done = 0;
+        float res = 0.f;
+        rc = pgm_run_bp_until(g, lp, ev, r.T, r.damping, r.n_iters, r.tol, r.check_every, msgs, &done, &res, st);
+        r.updates = I.n_edge_states * (int64_t)done;
+    } else if (rc == PGM_OK) {
+        rc = pgm_run_bp(g, lp, ev, r.T, r.damping, r.n_iters, msgs, st);
+    }
     if (rc == PGM_OK) rc = pgm_beliefs(g, ev, msgs, bel, 1, st);
     if (rc == PGM_OK) rc = pgm_decode(g, ev, msgs, dec, st);
     if (rc == PGM_OK) {
@@ -196,9 +205,11 @@ pgm_status run_request(Request &r, cudaStream_t st, std::string &err) {
     return rc;
 }
 
-// Device bytes a request holds while in flight (graph + its input/output buffers).
-int64_t request_bytes(const pgm_info &I) {
-    return I.device_bytes + 4 * (I.n_potentials + 2 * I.n_var_states + I.n_edge_states + I.n_vars) + 2048;
+// Device bytes a request holds while in flight (graph + its input/output buffers, and
+// with an early exit the residual buffers of pgm_run_bp_until).
+int64_t request_bytes(const pgm_info &I, bool until) {
+    return I.device_bytes + 4 * (I.n_potentials + 2 * I.n_var_states + I.n_edge_states + I.n_vars) + 2048 +
+           (until ? 4 * I.n_edge_states + 512 : 0);
 }
 
 void worker_loop(pgm_server *s, int w) {
@@ -222,7 +233,7 @@ void worker_loop(pgm_server *s, int w) {
         pgm_status rc = pgm_check_desc(&r->d.desc, &I);
         int64_t need = 0;
         if (rc == PGM_OK) {
-            need = request_bytes(I);
+            need = request_bytes(I, r->check_every > 0);
             if (need > s->cfg.memory_budget_bytes) rc = PGM_ENOMEM;
         }
         if (rc != PGM_OK) {
@@ -280,8 +291,8 @@ pgm_status pgm_serve_create(const pgm_server_config *cfg, pgm_server **out) {
     return PGM_OK;
 }
 
-pgm_status pgm_serve_submit(pgm_server *s, const pgm_graph_desc *desc, const float *log_pot,
-                            const float *evidence, float T, float damping, int32_t n_iters, int64_t *id) {
+static pgm_status submit(pgm_server *s, const pgm_graph_desc *desc, const float *log_pot, const float *evidence,
+                         float T, float damping, int32_t n_iters, float tol, int32_t check_every, int64_t *id) {
     if (!s || !id) return pgm::set_last_error(PGM_EINVAL, "NULL argument");
     if (!(T >= 0.f) || !std::isfinite(T)) return pgm::set_last_error(PGM_EINVAL, "T must be finite and >= 0");
     if (!(damping >= 0.f && damping < 1.f)) return pgm::set_last_error(PGM_EINVAL, "damping must be in [0, 1)");
@@ -295,6 +306,8 @@ pgm_status pgm_serve_submit(pgm_server *s, const pgm_graph_desc *desc, const flo
     r->T = T;
     r->damping = damping;
     r->n_iters = n_iters;
+    r->tol = tol;
+    r->check_every = check_every;
     std::lock_guard<std::mutex> lk(s->mu);
     if ((int64_t)s->pending.size() >= s->cfg.max_pending)
         return pgm::set_last_error(PGM_EBUSY, "the pending queue is full");
@@ -307,6 +320,19 @@ pgm_status pgm_serve_submit(pgm_server *s, const pgm_graph_desc *desc, const flo
     *id = r->id;
     s->cv_work.notify_one();
     return PGM_OK;
+}
+
+pgm_status pgm_serve_submit(pgm_server *s, const pgm_graph_desc *desc, const float *log_pot,
+                            const float *evidence, float T, float damping, int32_t n_iters, int64_t *id) {
+    return submit(s, desc, log_pot, evidence, T, damping, n_iters, 0.f, 0, id);
+}
+
+pgm_status pgm_serve_submit_until(pgm_server *s, const pgm_graph_desc *desc, const float *log_pot,
+                                  const float *evidence, float T, float damping, int32_t max_iters, float tol,
+                                  int32_t check_every, int64_t *id) {
+    if (check_every < 1) return pgm::set_last_error(PGM_EINVAL, "check_every must be >= 1");
+    if (!(tol >= 0.f)) return pgm::set_last_error(PGM_EINVAL, "tol must be >= 0");
+    return submit(s, desc, log_pot, evidence, T, damping, max_iters, tol, check_every, id);
 }
 
 static pgm_status take_result(pgm_server *s, std::unordered_map<int64_t, std::shared_ptr<Request>>::iterator it,

@@ -113,3 +113,45 @@ def test_bounded_wait_times_out(gpu):
     assert ei.value.status == -6  # PGM_ETIMEDOUT, the request keeps running
     assert srv.wait(i, 120.0) is not None
     srv.close()
+
+
+def _alone_until(binding, p, T, it, tol, ck):
+    import torch
+    g = binding.Graph(p.graph)
+    lp = torch.as_tensor(np.asarray(p.log_pot, np.float32)).cuda()
+    ev = torch.as_tensor(np.asarray(p.evidence, np.float32)).cuda()
+    m = g.new_msgs()
+    done, _ = g.run_bp_until(lp, ev, T, 0.5, it, tol, ck, m)
+    return g.beliefs(ev, m, True).cpu().numpy(), g.decode(ev, m).cpu().numpy(), done, g.info["n_edge_states"]
+
+
+@pytest.mark.parametrize("slots", [4, 1])
+def test_early_exit_requests_equal_alone(gpu, slots):
+    """Requests with a residual tolerance (pgm_serve_submit_until) stop early; each result
+    equals pgm_run_bp_until of the same request alone, and the server counts only the
+    iterations run."""
+    reqs = _requests(n=18, seed=3)
+    tol, ck = 1e-4, 10
+    srv = gpu.Server(memory_budget_bytes=48 << 20, max_in_flight=slots)
+    ids = [srv.submit(p.graph, p.log_pot, p.evidence, T, 0.5, 4 * it, tol=tol, check_every=ck) for p, T, it in reqs]
+    results = [srv.wait(i, 120.0) for i in ids]
+    st = srv.stats()
+    srv.close()
+    assert st["completed"] == len(reqs) and st["failed"] == 0
+    assert st["peak_bytes"] <= 48 << 20
+    upd, full = 0, 0
+    for (p, T, it), (bel, dec, lat) in zip(reqs, results):
+        b1, d1, done, ES = _alone_until(gpu, p, T, 4 * it, tol, ck)
+        np.testing.assert_array_equal(bel, b1, err_msg=p.name)
+        np.testing.assert_array_equal(dec, d1, err_msg=p.name)
+        upd += done * ES
+        full += 4 * it * ES
+    assert st["updates_done"] == upd
+    assert upd < full  # some requests converged before their limit
+    with pytest.raises(gpu.PgmError):
+        srv2 = gpu.Server(memory_budget_bytes=1 << 20, max_in_flight=1)
+        try:
+            p = reqs[0][0]
+            srv2.submit(p.graph, p.log_pot, p.evidence, 1.0, 0.5, 10, tol=1e-3, check_every=0)
+        finally:
+            srv2.close()
