@@ -52,6 +52,7 @@ def parse_args():
     ap.add_argument("--batch-grids", type=int, default=256)
     ap.add_argument("--no-multi", action="store_true", help="skip the multi-evidence measurement")
     ap.add_argument("--no-grad", action="store_true", help="skip the gradient measurement")
+    ap.add_argument("--no-until", action="store_true", help="skip the batch's per-member early exit")
     ap.add_argument("--pool-probe", default="",
                     help="SIDE,RADIUS,SLACK: a short uncaptured run of a pool grid (large listed-"
                          "configuration factors, T=0) for ncu captures of its kernels")
@@ -290,15 +291,36 @@ def measure_batched(args, binding, W, torch, dev):
             mi.zero_()
             g.run_bp(lpi, evi, 1.0, 0.5, iters, mi)
 
+    import numpy as np
     t_single = timed(run_singles, 2)
     upd = ES * iters
     launches = [dict(zip(("kind", "variant", "threads", "blocks"), x)) for x in gb.launches()]
+    # f4 inside the batch: each member stops once its own residual is <= 1e-4 (checked
+    # every 10 iterations, at most `iters`), the stopped members' factors are skipped
+    out_ee = {}
+    if not args.no_until:
+        res_holder = {}
+
+        def run_members():
+            mb.zero_()
+            res_holder["done"], _ = gb.run_bp_until_members(lp, ev, 1.0, 0.5, iters, 1e-4, 10, mb)
+
+        t_members = timed(run_members, 3)
+        done = res_holder["done"]
+        member_es = np.array([gb.member(i)["n_edge_states"] for i in range(len(members))], np.int64)
+        out_ee = {"early_exit_members": {
+            "tol": 1e-4, "check_every": 10, "max_iters": iters, "ms_per_run": 1e3 * t_members,
+            "speedup_vs_fixed": t_batched / t_members,
+            "members_stopped_early": int((done < iters).sum()),
+            "edge_state_updates_run_fraction": float((done * member_es).sum() / (iters * member_es.sum())),
+            "call": "pgm_run_bp_until_members (edge-state iterations, conditional while node)"}}
     return {"workload": f"{args.batch_grids} Potts grids (side U{{16..256}}, K in {{2,4,8,16}}) + RBM 784x500, "
                         f"T=1, damping 0.5, {iters} iterations",
             "graphs": len(members), "edge_states": ES,
             "batched": upd / t_batched, "per_graph": upd / t_single, "unit": UNIT,
             "batched_ms_per_run": 1e3 * t_batched, "per_graph_ms_per_run": 1e3 * t_single,
-            "speedup": t_single / t_batched, "autotune_s": round(tune_s, 2), "launch_shapes": launches}
+            "speedup": t_single / t_batched, "autotune_s": round(tune_s, 2), "launch_shapes": launches,
+            **out_ee}
 
 
 def measure_multi(args, binding, W, torch, dev):

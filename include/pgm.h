@@ -357,6 +357,26 @@ pgm_status pgm_pmp_sample(pgm_graph *g, int32_t n_samples, const float *log_pot,
                           void *stream);
 
 /*
+ * Early exit per member of a batch (pgm_build_batch; a single graph is a batch of one):
+ * every member runs until the first checked iteration whose residual over its own
+ * messages, max |m_t - m_{t-1}|, is <= tol (checked every check_every iterations), or
+ * max_iters; from then on the factor pass skips the stopped member's factors and leaves
+ * its messages at that iteration, while the other members go on. iters_done[m] and
+ * residual[m] (host arrays [n_members]) are each member's iterations and last checked
+ * residual (NaN before any check; 0 iterations and residual 0 for a member without
+ * edges). A member's messages equal pgm_run_bp_until of that member alone with
+ * PGM_OPT_LOG_RATIO 0: the run uses the edge-state iteration throughout. With
+ * PGM_OPT_CUDA_GRAPH on, the full chunks run as one CUDA graph whose conditional while
+ * node repeats a chunk while a member is active (recorded once per argument tuple, up to
+ * 4 kept with those of pgm_run_bp_until); the rest is checked by the host. Blocking. The
+ * first call allocates 4 (n_edge_states + 5 n_members) bytes, kept until pgm_free.
+ * PGM_EINVAL for check_every < 1, tol < 0 or NaN, NULL outputs, and as pgm_run_bp.
+ */
+pgm_status pgm_run_bp_until_members(pgm_graph *g, const float *log_pot, const float *evidence, float T,
+                                    float damping, int32_t max_iters, float tol, int32_t check_every,
+                                    float *msgs, int32_t *iters_done, float *residual, void *stream);
+
+/*
  * Options of a graph. PGM_OPT_CUDA_GRAPH (default 1): pgm_run_bp with n_iters >= 2
  * (and per-pass profiling off) records the whole call -- every kernel of every
  * iteration and the final copy -- as a CUDA graph the first time it sees a given

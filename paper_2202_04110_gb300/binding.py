@@ -23,7 +23,7 @@ FLAG_NAN = 2
 # Every symbol include/pgm.h declares.
 EXPORTED = ["pgm_build", "pgm_build_batch", "pgm_batch_member", "pgm_check_desc", "pgm_free", "pgm_graph_info", "pgm_run_bp", "pgm_beliefs",
             "pgm_decode", "pgm_infer_host", "pgm_set_profiling", "pgm_pass_times",
-            "pgm_device_flags", "pgm_grid2_run_bp_noalloc", "pgm_run_bp_multi", "pgm_pmp_sample", "pgm_run_bp_until", "pgm_set_option", "pgm_get_option", "pgm_autotune",
+            "pgm_device_flags", "pgm_grid2_run_bp_noalloc", "pgm_run_bp_multi", "pgm_pmp_sample", "pgm_run_bp_until", "pgm_run_bp_until_members", "pgm_set_option", "pgm_get_option", "pgm_autotune",
             "pgm_launch_info", "pgm_grad", "pgm_serve_create", "pgm_serve_submit", "pgm_serve_submit_until", "pgm_serve_poll",
             "pgm_serve_wait", "pgm_serve_stats", "pgm_serve_destroy", "pgm_last_error"]
 OPT_CUDA_GRAPH = 1
@@ -110,6 +110,8 @@ def load_library(path: str | None = None):
     lib.pgm_run_bp_multi.argtypes = [vp, i32, vp, i32, vp, f32, f32, i32, vp, vp]
     lib.pgm_run_bp_until.restype = i32
     lib.pgm_run_bp_until.argtypes = [vp, vp, vp, f32, f32, i32, f32, i32, vp, vp, vp, vp]
+    lib.pgm_run_bp_until_members.restype = i32
+    lib.pgm_run_bp_until_members.argtypes = [vp, vp, vp, f32, f32, i32, f32, i32, vp, vp, vp, vp]
     lib.pgm_pmp_sample.restype = i32
     lib.pgm_pmp_sample.argtypes = [vp, i32, vp, vp, vp, f32, i32, vp, vp, vp]
     lib.pgm_beliefs.restype = i32
@@ -295,6 +297,22 @@ class Graph:
             int(max_iters), float(tol), int(check_every), _dptr(msgs, torch.float32, I["n_edge_states"], "msgs"),
             ctypes.byref(done), ctypes.byref(res), _stream_ptr(stream)))
         return done.value, res.value
+
+    def run_bp_until_members(self, log_pot, evidence, T: float, damping: float, max_iters: int, tol: float,
+                             check_every: int, msgs, stream=None):
+        """In-place early exit per batch member (pgm_run_bp_until_members). Returns
+        (iterations run [n_members], last residual [n_members]) as numpy arrays."""
+        import torch
+        I = self.info
+        n = I["n_members"]
+        done = np.zeros(n, np.int32)
+        res = np.zeros(n, np.float32)
+        lp = _dptr(log_pot, torch.float32, I["n_potentials"], "log_pot") if I["n_potentials"] else 0
+        check(load_library().pgm_run_bp_until_members(
+            self._h, lp, _dptr(evidence, torch.float32, I["n_var_states"], "evidence"), float(T), float(damping),
+            int(max_iters), float(tol), int(check_every), _dptr(msgs, torch.float32, I["n_edge_states"], "msgs"),
+            done.ctypes.data, res.ctypes.data, _stream_ptr(stream)))
+        return done, res
 
     def pmp_sample(self, log_pot, evidence, noise, damping: float, n_iters: int, stream=None):
         """Perturb-and-max-product samples (pgm_pmp_sample): noise [S, n_var_states].

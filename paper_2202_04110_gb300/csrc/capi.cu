@@ -79,9 +79,19 @@ struct pgm_graph {
         float *msgs;
         uint32_t T_bits, damping_bits, tol_bits;
         int32_t check_every, limit;
+        bool members;  // pgm_run_bp_until_members
         cudaGraphExec_t exec;
     };
     std::vector<CachedUntil> untils;
+    // pgm_run_bp_until_members (allocated on first use): member edge-state offsets [n+1],
+    // frozen words, residual words, iterations and residuals [n each], loop state [3]
+    // (iterations done, go on, a member active), the previous messages [n_edge_states]
+    char *mu_mem = nullptr;
+    int32_t *mu_off = nullptr, *mu_frozen = nullptr, *mu_iters = nullptr;
+    unsigned *mu_res = nullptr;
+    float *mu_resid = nullptr, *mu_prev = nullptr;
+    int *mu_state = nullptr;
+    bool force_es = false;  // edge-state iterations only (the members' early exit)
     // pgm_pmp_sample: perturbed evidence for up to pmp_cap samples (allocated on first use)
     float *pmp_ev = nullptr;
     int32_t pmp_cap = 0;
@@ -636,6 +646,7 @@ void pgm_free(pgm_graph *g) {
     if (g->pmp_ev) cudaFree(g->pmp_ev);
     if (g->until_prev) cudaFree(g->until_prev);
     if (g->until_res_host) cudaFreeHost(g->until_res_host);
+    if (g->mu_mem) cudaFree(g->mu_mem);
     for (cudaEvent_t e : g->events) cudaEventDestroy(e);
     drop_cached_runs(g);
     if (g->capture_stream) cudaStreamDestroy(g->capture_stream);
@@ -654,7 +665,7 @@ pgm_status pgm_graph_info(const pgm_graph *g, pgm_info *info) {
 // variable-to-factor values to lr_lam, the factor pass updates lr_d in place, and lr_d
 // is unpacked into msgs at the end.
 static bool log_ratio_run(const pgm_graph *g, int32_t n_iters) {
-    return g->P.lr && g->log_ratio_min_iters > 0 && n_iters >= g->log_ratio_min_iters;
+    return g->P.lr && !g->force_es && g->log_ratio_min_iters > 0 && n_iters >= g->log_ratio_min_iters;
 }
 
 static pgm_status enqueue_iterations(pgm_graph *g, const float *log_pot, const float *evidence, float T,
@@ -909,9 +920,29 @@ pgm_status pgm_run_bp_multi(pgm_graph *g, int32_t n_samples, const float *log_po
     return PGM_OK;
 }
 
+// One chunk of an early-exit run: n iterations, the last one's messages in msgs and the
+// one before in *prev. An even number of edge-state iterations ends its ping-pong in msgs
+// with the previous iteration still in the scratch buffer (no copy); otherwise n - 1
+// iterations, a copy of the messages into prev_buf, and one more.
+static pgm_status enqueue_chunk(pgm_graph *g, const float *log_pot, const float *evidence, float T, float damping,
+                                int32_t n, float *msgs, float *prev_buf, const float **prev, cudaStream_t s) {
+    if (n % 2 == 0 && !log_ratio_run(g, n)) {
+        *prev = g->m_tmp;
+        return enqueue_iterations(g, log_pot, evidence, T, damping, n, msgs, s, false);
+    }
+    *prev = prev_buf;
+    pgm_status st = PGM_OK;
+    if (n > 1) st = enqueue_iterations(g, log_pot, evidence, T, damping, n - 1, msgs, s, false);
+    if (st != PGM_OK) return st;
+    cudaError_t e = cudaMemcpyAsync(prev_buf, msgs, (size_t)g->info.n_edge_states * sizeof(float),
+                                    cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(messages)");
+    return enqueue_iterations(g, log_pot, evidence, T, damping, 1, msgs, s, false);
+}
+
 // The graph of the full chunks of an early-exit run: the iteration counter set to 0,
-// then a conditional while node whose body runs one chunk (check_every - 1 iterations, a
-// copy of the messages, one more iteration, the residual) and k_until_control, which
+// then a conditional while node whose body runs one chunk (enqueue_chunk, the residual)
+// and k_until_control, which
 // continues the loop while the residual is above tol (or NaN) and fewer than limit
 // iterations are done (so the loop ends after at most limit / check_every trips).
 static pgm_status cached_until(pgm_graph *g, const float *log_pot, const float *evidence, float T, float damping,
@@ -921,7 +952,7 @@ static pgm_status cached_until(pgm_graph *g, const float *log_pot, const float *
     std::memcpy(&db, &damping, sizeof db);
     std::memcpy(&lb, &tol, sizeof lb);
     for (auto &u : g->untils)
-        if (u.log_pot == log_pot && u.evidence == evidence && u.msgs == msgs && u.T_bits == tb &&
+        if (!u.members && u.log_pot == log_pot && u.evidence == evidence && u.msgs == msgs && u.T_bits == tb &&
             u.damping_bits == db && u.tol_bits == lb && u.check_every == check_every && u.limit == limit) {
             *out = u.exec;
             return PGM_OK;
@@ -962,16 +993,11 @@ static pgm_status cached_until(pgm_graph *g, const float *log_pot, const float *
     cudaStream_t cs = g->capture_stream;
     e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return failed(e, "cudaStreamBeginCaptureToGraph");
-    pgm_status st = PGM_OK;
-    if (check_every > 1) st = enqueue_iterations(g, log_pot, evidence, T, damping, check_every - 1, msgs, cs, false);
-    if (st == PGM_OK) {
-        e = cudaMemcpyAsync(g->until_prev, msgs, (size_t)ES * sizeof(float), cudaMemcpyDeviceToDevice, cs);
-        if (e != cudaSuccess) st = cuda_fail(e, "cudaMemcpyAsync(messages)");
-    }
-    if (st == PGM_OK) st = enqueue_iterations(g, log_pot, evidence, T, damping, 1, msgs, cs, false);
+    const float *prev = nullptr;
+    pgm_status st = enqueue_chunk(g, log_pot, evidence, T, damping, check_every, msgs, g->until_prev, &prev, cs);
     if (st == PGM_OK) {
         e = cudaMemsetAsync(g->until_res, 0, sizeof(unsigned), cs);
-        if (e == cudaSuccess) e = launch_residual(ES, msgs, g->until_prev, g->until_res, g->n_sm, cs);
+        if (e == cudaSuccess) e = launch_residual(ES, msgs, prev, g->until_res, g->n_sm, cs);
         if (e == cudaSuccess) e = launch_until_control(h, g->until_res, done, check_every, limit, tol, cs);
         if (e != cudaSuccess) st = cuda_fail(e, "early-exit body");
     }
@@ -990,7 +1016,7 @@ static pgm_status cached_until(pgm_graph *g, const float *log_pot, const float *
         cudaGraphExecDestroy(g->untils.front().exec);
         g->untils.erase(g->untils.begin());
     }
-    g->untils.push_back({log_pot, evidence, msgs, tb, db, lb, check_every, limit, exec});
+    g->untils.push_back({log_pot, evidence, msgs, tb, db, lb, check_every, limit, false, exec});
     *out = exec;
     return PGM_OK;
 }
@@ -1058,16 +1084,11 @@ pgm_status pgm_run_bp_until(pgm_graph *g, const float *log_pot, const float *evi
     }
     while (done < max_iters) {
         const int32_t n = std::min(check_every, max_iters - done);
-        if (n > 1) {
-            st = pgm_run_bp(g, log_pot, evidence, T, damping, n - 1, msgs, stream);
-            if (st != PGM_OK) return st;
-        }
-        cudaError_t e = cudaMemcpyAsync(g->until_prev, msgs, (size_t)ES * sizeof(float), cudaMemcpyDeviceToDevice, s);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(messages)");
-        st = pgm_run_bp(g, log_pot, evidence, T, damping, 1, msgs, stream);
+        const float *prev = nullptr;
+        st = enqueue_chunk(g, log_pot, evidence, T, damping, n, msgs, g->until_prev, &prev, s);
         if (st != PGM_OK) return st;
-        e = cudaMemsetAsync(g->until_res, 0, sizeof(unsigned), s);
-        if (e == cudaSuccess) e = launch_residual(ES, msgs, g->until_prev, g->until_res, g->n_sm, s);
+        cudaError_t e = cudaMemsetAsync(g->until_res, 0, sizeof(unsigned), s);
+        if (e == cudaSuccess) e = launch_residual(ES, msgs, prev, g->until_res, g->n_sm, s);
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(g->until_res_host, g->until_res, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -1078,6 +1099,166 @@ pgm_status pgm_run_bp_until(pgm_graph *g, const float *log_pot, const float *evi
     }
     if (iters_done) *iters_done = done;
     if (residual) *residual = res;
+    return PGM_OK;
+}
+
+// The graph of the full chunks of a members' early-exit run: a conditional while node
+// whose body runs one chunk (enqueue_chunk), the per-member residuals, the loop control (which freezes converged
+// members and ends the loop when none is active or limit iterations are done) and the
+// copy of newly frozen members' messages to the other ping-pong buffer. The caller
+// resets the members' state before each launch.
+static pgm_status cached_until_members(pgm_graph *g, const float *log_pot, const float *evidence, float T,
+                                       float damping, int32_t check_every, int32_t limit, float tol, float *msgs,
+                                       cudaGraphExec_t *out) {
+    uint32_t tb, db, lb;
+    std::memcpy(&tb, &T, sizeof tb);
+    std::memcpy(&db, &damping, sizeof db);
+    std::memcpy(&lb, &tol, sizeof lb);
+    for (auto &u : g->untils)
+        if (u.members && u.log_pot == log_pot && u.evidence == evidence && u.msgs == msgs && u.T_bits == tb &&
+            u.damping_bits == db && u.tol_bits == lb && u.check_every == check_every && u.limit == limit) {
+            *out = u.exec;
+            return PGM_OK;
+        }
+    if (!g->capture_stream) {
+        cudaError_t e = cudaStreamCreateWithFlags(&g->capture_stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamCreate");
+    }
+    const int64_t ES = g->info.n_edge_states;
+    const int nm = (int)g->members.size();
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaGraphCreate(&graph, 0);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphCreate");
+    auto failed = [&](cudaError_t err, const char *what) {
+        cudaGraphDestroy(graph);
+        return cuda_fail(err, what);
+    };
+    cudaGraphConditionalHandle h;
+    e = cudaGraphConditionalHandleCreate(&h, graph, 1, cudaGraphCondAssignDefault);
+    if (e != cudaSuccess) return failed(e, "cudaGraphConditionalHandleCreate");
+    cudaGraphNodeParams cp{};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t n_loop = nullptr;
+    e = cudaGraphAddNode(&n_loop, graph, nullptr, nullptr, 0, &cp);
+    if (e != cudaSuccess) return failed(e, "cudaGraphAddNode(while)");
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    cudaStream_t cs = g->capture_stream;
+    e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return failed(e, "cudaStreamBeginCaptureToGraph");
+    const float *prev = nullptr;
+    pgm_status st = enqueue_chunk(g, log_pot, evidence, T, damping, check_every, msgs, g->mu_prev, &prev, cs);
+    if (st == PGM_OK) {
+        e = launch_residual_members(ES, msgs, prev, g->mu_off, nm, g->mu_frozen, g->mu_res, g->n_sm, cs);
+        if (e == cudaSuccess)
+            e = launch_until_control_members(h, true, g->mu_res, g->mu_frozen, g->mu_iters, g->mu_resid, nm,
+                                             g->mu_state, check_every, limit, tol, cs);
+        if (e == cudaSuccess) e = launch_freeze_copy(g->mu_frozen, g->mu_off, nm, msgs, g->m_tmp, g->n_sm, cs);
+        if (e != cudaSuccess) st = cuda_fail(e, "members' early-exit body");
+    }
+    cudaGraph_t captured = nullptr;
+    e = cudaStreamEndCapture(cs, &captured);
+    if (st != PGM_OK) {
+        cudaGraphDestroy(graph);
+        return st;
+    }
+    if (e != cudaSuccess) return failed(e, "cudaStreamEndCapture");
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate(members' early exit)");
+    if (g->untils.size() >= 4) {
+        cudaGraphExecDestroy(g->untils.front().exec);
+        g->untils.erase(g->untils.begin());
+    }
+    g->untils.push_back({log_pot, evidence, msgs, tb, db, lb, check_every, limit, true, exec});
+    *out = exec;
+    return PGM_OK;
+}
+
+pgm_status pgm_run_bp_until_members(pgm_graph *g, const float *log_pot, const float *evidence, float T,
+                                    float damping, int32_t max_iters, float tol, int32_t check_every, float *msgs,
+                                    int32_t *iters_done, float *residual, void *stream) {
+    pgm_status st = check_run_args(g, log_pot, evidence, T, damping, max_iters, msgs);
+    if (st != PGM_OK) return st;
+    if (!iters_done || !residual) return fail(PGM_EINVAL, "iters_done / residual is NULL");
+    if (check_every < 1) return fail(PGM_EINVAL, "check_every must be >= 1");
+    if (!(tol >= 0.f)) return fail(PGM_EINVAL, "tol must be >= 0");
+    const int nm = (int)g->members.size();
+    const int64_t ES = g->info.n_edge_states;
+    for (int m = 0; m < nm; ++m) {
+        iters_done[m] = 0;
+        residual[m] = (max_iters == 0 && g->members[m].n_edge_states > 0) ? CUDART_NAN_F_HOST : 0.f;
+    }
+    if (max_iters == 0 || ES == 0) return PGM_OK;
+    DeviceGuard dg(g->device);
+    if (!dg.ok) return fail(PGM_ECUDA, "cudaSetDevice failed");
+    if (!g->mu_mem) {
+        const size_t a4 = align_up((size_t)(nm + 1) * sizeof(int32_t), 256);
+        const size_t total = 5 * a4 + 256 + align_up((size_t)ES * sizeof(float), 256);
+        char *mem = nullptr;
+        if (cudaMalloc(&mem, total) != cudaSuccess) return fail(PGM_ENOMEM, "cudaMalloc(members' early-exit state)");
+        std::vector<int32_t> off(nm + 1);
+        for (int m = 0; m < nm; ++m) off[m] = (int32_t)g->members[m].es_off;
+        off[nm] = (int32_t)ES;
+        if (cudaMemcpy(mem, off.data(), off.size() * sizeof(int32_t), cudaMemcpyHostToDevice) != cudaSuccess) {
+            cudaFree(mem);
+            return fail(PGM_ECUDA, "cudaMemcpy(member offsets)");
+        }
+        g->mu_mem = mem;
+        g->mu_off = reinterpret_cast<int32_t *>(mem);
+        g->mu_frozen = reinterpret_cast<int32_t *>(mem + a4);
+        g->mu_res = reinterpret_cast<unsigned *>(mem + 2 * a4);
+        g->mu_iters = reinterpret_cast<int32_t *>(mem + 3 * a4);
+        g->mu_resid = reinterpret_cast<float *>(mem + 4 * a4);
+        g->mu_state = reinterpret_cast<int *>(mem + 5 * a4);
+        g->mu_prev = reinterpret_cast<float *>(mem + 5 * a4 + 256);
+        if (cudaMemset(g->mu_frozen, 0, (size_t)nm * sizeof(int32_t)) != cudaSuccess)
+            return fail(PGM_ECUDA, "cudaMemset(frozen)");
+        g->G.frozen = g->mu_frozen;  // launches from now on check it (zero outside these runs)
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    struct ForceEs {  // edge-state iterations for the whole call
+        pgm_graph *g;
+        ~ForceEs() { g->force_es = false; }
+    } force{g};
+    g->force_es = true;
+    cudaError_t e = launch_until_members_init(g->mu_frozen, g->mu_res, g->mu_iters, g->mu_resid, g->mu_off, nm,
+                                              g->mu_state, s);
+    if (e != cudaSuccess) return cuda_fail(e, "members' early-exit reset");
+    int state[3] = {0, 1, 1};  // iterations done, go on, a member active
+    const int32_t limit = (max_iters / check_every) * check_every;
+    if (g->use_cuda_graph && !g->ordered && limit > 0) {
+        cudaGraphExec_t exec = nullptr;
+        st = cached_until_members(g, log_pot, evidence, T, damping, check_every, limit, tol, msgs, &exec);
+        if (st != PGM_OK) return st;
+        e = cudaGraphLaunch(exec, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(state, g->mu_state, sizeof state, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return cuda_fail(e, "members' early-exit graph");
+    }
+    // the rest (all of it with CUDA graphs off): chunks checked by the host
+    while (state[0] < max_iters && state[2]) {
+        const int32_t n = std::min(check_every, max_iters - state[0]);
+        const float *prev = nullptr;
+        st = enqueue_chunk(g, log_pot, evidence, T, damping, n, msgs, g->mu_prev, &prev, s);
+        if (st != PGM_OK) return st;
+        e = launch_residual_members(ES, msgs, prev, g->mu_off, nm, g->mu_frozen, g->mu_res, g->n_sm, s);
+        if (e == cudaSuccess)
+            e = launch_until_control_members(0, false, g->mu_res, g->mu_frozen, g->mu_iters, g->mu_resid, nm,
+                                             g->mu_state, n, max_iters, tol, s);
+        if (e == cudaSuccess) e = launch_freeze_copy(g->mu_frozen, g->mu_off, nm, msgs, g->m_tmp, g->n_sm, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(state, g->mu_state, sizeof state, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return cuda_fail(e, "members' early exit");
+    }
+    e = cudaMemcpyAsync(iters_done, g->mu_iters, (size_t)nm * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(residual, g->mu_resid, (size_t)nm * sizeof(float), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(g->mu_frozen, 0, (size_t)nm * sizeof(int32_t), s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "members' early-exit results");
     return PGM_OK;
 }
 

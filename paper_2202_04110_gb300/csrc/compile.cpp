@@ -210,6 +210,7 @@ std::string compile_graph(const void *const *vdescs, int n_desc, HostLayout *L) 
             s.table_bytes = 0;
             s.packed = 0;
             s.ordered = 0;
+            s.member = m;
             if (g.n_fac > 0 && (hg.variant == kEnumGeneric || hg.variant == kEnumBlock)) {
                 // configuration lists by output state: for neighbour j and state x, the
                 // configurations with state x at j (the block form's gather order)
@@ -262,6 +263,7 @@ std::string compile_graph(const void *const *vdescs, int n_desc, HostLayout *L) 
             s.edge_base = (int32_t)e;
             s.es_base = (int32_t)es;
             s.paroff_base = (int32_t)L->paroff_pool.size();
+            s.member = m;
             int32_t mf = 0;
             for (int64_t f = 0; f <= g.n_fac; ++f) L->paroff_pool.push_back(g.par_off[f]);
             for (int64_t f = 0; f < g.n_fac; ++f) {

@@ -916,6 +916,12 @@ __global__ void __launch_bounds__(kVarBlockThreads) k_var_block(DevGraph G, cons
 // Factor pass: dense pairwise tables (Ising, RBM, Potts), thread per factor
 // =====================================================================================
 
+// A batch member whose early exit has frozen it: the factor pass leaves its messages
+// alone (a block, or a chunk of the persistent kernel, lies in one member's group).
+__device__ __forceinline__ bool member_frozen(const DevGraph &G, int member) {
+    return G.frozen != nullptr && __ldg(G.frozen + member) != 0;
+}
+
 // The factor-to-variable update of one dense pairwise factor from its two
 // variable-to-factor vectors v0, v1 and stored messages mo0, mo1; writes the damped,
 // normalised messages.
@@ -1049,6 +1055,7 @@ k_pair(DevGraph G, const EnumSeg *__restrict__ segs, int n_seg, const float *__r
     __shared__ float tabE[K >= 4 ? K * K : 1];
     __shared__ float tinfo[2];
     const EnumSeg *S = segs + find_seg(segs, n_seg, blockIdx.x);
+    if (member_frozen(G, S->member)) return;  // the whole block
     const int n_fac = __ldg(&S->n_fac), shared = __ldg(&S->shared), pot_base = __ldg(&S->pot_base);
     bool linear = false;
     if (shared) {
@@ -1270,6 +1277,7 @@ k_pair_group(DevGraph G, const EnumSeg *__restrict__ segs, int n_seg, int n_vblo
         const float bb0 = fast0 ? __ldg(b + vs0 + x) : 0.f;
         const float bb1 = fast1 ? __ldg(b + vs1 + x) : 0.f;
         if (vb + 1 < vb_end) fetch(vb + 1, nsi, nvs0, nvs1, nmo0, nmo1);
+        if (member_frozen(G, S->member)) continue;  // uniform across the block
         if (si != cur) {  // uniform across the block
             cur = si;
             shared = __ldg(&S->shared) != 0;
@@ -1407,6 +1415,7 @@ k_pair_thr(DevGraph G, const EnumSeg *__restrict__ segs, int n_seg, const float 
     __shared__ __align__(16) float tabET[MAXP ? 4 : K * K];
     __shared__ float tinfo[2];
     const EnumSeg *S = segs + find_seg(segs, n_seg, blockIdx.x);
+    if (member_frozen(G, S->member)) return;  // the whole block
     const int n_fac = __ldg(&S->n_fac), shared = __ldg(&S->shared), pot_base = __ldg(&S->pot_base);
     bool linear = false;
     if (shared) {  // uniform over the block (a block lies in one segment)
@@ -1464,6 +1473,7 @@ k_enum_generic(DevGraph G, const EnumSeg *__restrict__ segs, int n_seg, const fl
                const float *__restrict__ m_old, float *__restrict__ m_new, float T, float invT,
                float damping) {
     const EnumSeg *S = segs + find_seg(segs, n_seg, blockIdx.x);
+    if (member_frozen(G, S->member)) return;
     const int f = (blockIdx.x - __ldg(&S->block_begin)) * blockDim.x + threadIdx.x;
     if (f >= __ldg(&S->n_fac)) return;
     const int a = __ldg(&S->arity), nc = __ldg(&S->n_cfg), ksum = __ldg(&S->es_per_fac);
@@ -1591,6 +1601,7 @@ k_enum_block(DevGraph G, const EnumSeg *__restrict__ segs, int n_seg, const floa
     __shared__ int sK[kMaxArity], sKo[kMaxArity];
     __shared__ int s_fix[kEnumBlockThreads / 32][kMaxArity];
     const EnumSeg *S = segs + find_seg(segs, n_seg, blockIdx.x);
+    if (member_frozen(G, S->member)) return;  // the whole block
     const int a = __ldg(&S->arity), nc = __ldg(&S->n_cfg), ksum = __ldg(&S->es_per_fac);
     const int fpb = __ldg(&S->fpb), L = __ldg(&S->lanes), tb = __ldg(&S->table_bytes);
     const int n_fac = __ldg(&S->n_fac), shared = __ldg(&S->shared), packed = __ldg(&S->packed);
@@ -1880,6 +1891,7 @@ k_logic_small(DevGraph G, const LogicSeg *__restrict__ segs, int n_seg, const fl
               const float *__restrict__ ev, const float *__restrict__ m_old,
               float *__restrict__ m_new, float T, float invT, float damping) {
     const LogicSeg *S = segs + find_seg(segs, n_seg, blockIdx.x);
+    if (member_frozen(G, S->member)) return;
     const int f = (blockIdx.x - __ldg(&S->block_begin)) * blockDim.x + threadIdx.x;
     if (f >= __ldg(&S->n_fac)) return;
     const int *po = G.paroff_pool + __ldg(&S->paroff_base);
@@ -1989,6 +2001,7 @@ k_logic_warp(DevGraph G, const LogicSeg *__restrict__ segs, int n_seg, const flo
     extern __shared__ float smem[];
     const int warps = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const LogicSeg *S = segs + find_seg(segs, n_seg, blockIdx.x);
+    if (member_frozen(G, S->member)) return;
     const int f = (blockIdx.x - __ldg(&S->block_begin)) * warps + warp;
     if (f >= __ldg(&S->n_fac)) return;
     float *sx = smem + (size_t)warp * 3 * cap;  // log-odds x_j (times sgn)
@@ -2823,6 +2836,110 @@ __global__ void __launch_bounds__(256) k_residual(int64_t n, const float *__rest
     if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(mx));  // NaN (0x7fc00000) ranks above +inf
 }
 
+// ---- per-member early exit of a batch ---------------------------------------------------
+
+// Reset of a batched early-exit run: members with no edge-states are frozen from the
+// start (0 iterations, residual 0), the others active; state[0] (iterations done) = 0.
+__global__ void k_until_members_init(int32_t *__restrict__ frozen, unsigned *__restrict__ res,
+                                     int32_t *__restrict__ iters, float *__restrict__ resid,
+                                     const int32_t *__restrict__ off, int n_members, int *__restrict__ state) {
+    for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < n_members; m += gridDim.x * blockDim.x) {
+        const bool empty = __ldg(off + m + 1) == __ldg(off + m);
+        frozen[m] = empty ? 1 : 0;
+        res[m] = 0u;
+        iters[m] = 0;
+        resid[m] = empty ? 0.f : CUDART_NAN_F;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) state[0] = 0;
+}
+
+// res[m] = max(res[m], max over member m's edge-states off[m]..off[m+1] of |a - b|), as
+// k_residual, for members not frozen. A warp takes a contiguous run of edge-states
+// (lanes interleaved, so loads coalesce); a lane adds its running maximum to the
+// member's word when its member changes and at the end.
+__global__ void __launch_bounds__(256) k_residual_members(int64_t n, const float *__restrict__ a,
+                                                          const float *__restrict__ b,
+                                                          const int32_t *__restrict__ off, int n_members,
+                                                          const int32_t *__restrict__ frozen,
+                                                          unsigned *__restrict__ res) {
+    const int64_t n_warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    const int64_t chunk = (((n + n_warps - 1) / n_warps) + 31) & ~(int64_t)31;
+    const int64_t i1 = min(n, (w + 1) * chunk);
+    int64_t i = w * chunk + lane;
+    if (i >= i1) return;
+    int lo = 0, hi = n_members - 1;  // the member holding edge-state i: last m with off[m] <= i
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(off + mid) <= i) lo = mid;
+        else hi = mid - 1;
+    }
+    int m = lo;
+    int64_t end = __ldg(off + m + 1);
+    float mx = 0.f;
+    for (; i < i1; i += 32) {
+        if (i >= end) {
+            if (!__ldg(frozen + m)) atomicMax(res + m, __float_as_uint(mx));
+            mx = 0.f;
+            do {
+                ++m;
+                end = __ldg(off + m + 1);
+            } while (i >= end);
+        }
+        const float x = __ldg(a + i), y = __ldg(b + i);
+        const float dlt = (x == y) ? 0.f : fabsf(x - y);
+        mx = (dlt != dlt || mx != mx) ? CUDART_NAN_F : fmaxf(mx, dlt);
+    }
+    if (!__ldg(frozen + m)) atomicMax(res + m, __float_as_uint(mx));
+}
+
+// Loop control of a batched early-exit run after a trip of n iterations (one block):
+// state[0] += n; a member frozen last trip (2) becomes 1; an active member records its
+// iterations and residual, and freezes (2: its messages are copied next) when the
+// residual is <= tol; its residual word is reset for the next trip. state[1] = whether
+// to go on: a member is active and fewer than limit iterations are done (also the
+// condition of the while node when set_condition); state[2] = a member is active.
+__global__ void __launch_bounds__(256) k_until_control_members(cudaGraphConditionalHandle h, bool set_condition,
+                                                               unsigned *__restrict__ res, int32_t *__restrict__ frozen,
+                                                               int32_t *__restrict__ iters, float *__restrict__ resid,
+                                                               int n_members, int *__restrict__ state, int n,
+                                                               int limit, float tol) {
+    const int d = state[0] + n;
+    int active = 0;
+    for (int m = threadIdx.x; m < n_members; m += blockDim.x) {
+        const int f = frozen[m];
+        if (f == 2) frozen[m] = 1;
+        if (f != 0) continue;
+        const float r = __uint_as_float(res[m]);
+        res[m] = 0u;
+        iters[m] = d;
+        resid[m] = r;
+        if (r <= tol) frozen[m] = 2;  // (false for NaN)
+        else active = 1;
+    }
+    active = __syncthreads_or(active);
+    if (threadIdx.x == 0) {
+        state[0] = d;
+        const int go = active && d < limit;
+        state[1] = go;
+        state[2] = active;
+        if (set_condition) cudaGraphSetConditional(h, go ? 1u : 0u);
+    }
+}
+
+// Members frozen at the last control (2): their messages a copied to the other
+// ping-pong buffer b, so that both hold the iteration the member stopped at.
+__global__ void __launch_bounds__(256) k_freeze_copy(const int32_t *__restrict__ frozen, const int32_t *__restrict__ off,
+                                                     int n_members, const float *__restrict__ a, float *__restrict__ b) {
+    for (int m = 0; m < n_members; ++m) {
+        if (__ldg(frozen + m) != 2) continue;
+        const int64_t s0 = __ldg(off + m), s1 = __ldg(off + m + 1);
+        for (int64_t i = s0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < s1; i += (int64_t)gridDim.x * blockDim.x)
+            b[i] = a[i];
+    }
+}
+
 // The loop control of a device-side early-exit run (the body of a conditional while
 // node): after a trip of n iterations, done += n; the loop goes on while the trip's
 // residual (bits in *res) is above tol or NaN and fewer than limit iterations are done.
@@ -3056,6 +3173,35 @@ cudaError_t launch_ms_iteration(const DevGraph &G, const Plan &P, int S, int Sp,
                        (const float2 *)Dv, (const float *)lam, d, G.flags, k, Tln2, damping);
         if (e != cudaSuccess) return e;
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_until_members_init(int32_t *frozen, unsigned *res, int32_t *iters, float *resid,
+                                      const int32_t *off, int n_members, int *state, cudaStream_t s) {
+    k_until_members_init<<<std::max(1, std::min((n_members + 255) / 256, 1024)), 256, 0, s>>>(frozen, res, iters, resid,
+                                                                                              off, n_members, state);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_residual_members(int64_t n, const float *a, const float *b, const int32_t *off, int n_members,
+                                    const int32_t *frozen, unsigned *res, int n_sm, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    const int blocks = (int)std::min<int64_t>((n + 255) / 256, (int64_t)n_sm * 8);
+    k_residual_members<<<blocks, 256, 0, s>>>(n, a, b, off, n_members, frozen, res);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_until_control_members(cudaGraphConditionalHandle h, bool set_condition, unsigned *res,
+                                         int32_t *frozen, int32_t *iters, float *resid, int n_members, int *state,
+                                         int n, int limit, float tol, cudaStream_t s) {
+    k_until_control_members<<<1, 256, 0, s>>>(h, set_condition, res, frozen, iters, resid, n_members, state, n, limit,
+                                              tol);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_freeze_copy(const int32_t *frozen, const int32_t *off, int n_members, const float *a, float *b,
+                               int n_sm, cudaStream_t s) {
+    k_freeze_copy<<<n_sm * 4, 256, 0, s>>>(frozen, off, n_members, a, b);
     return cudaGetLastError();
 }
 

@@ -74,6 +74,7 @@ struct EnumSeg {
     int32_t table_bytes;  // bytes of the table staged in shared memory (0: read in place)
     int32_t packed;       // 1: pairwise, list entries (c << 11) | (Koff[other] + state)
     int32_t ordered;      // 1: reduce each output's configurations in ascending order
+    int32_t member;       // the batch member the group belongs to
 };
 
 // One logical group as seen by a launch. Factor f owns edges
@@ -87,7 +88,7 @@ struct LogicSeg {
     int32_t es_base;
     int32_t paroff_base;  // offset of the group's par_off[n_fac + 1] in the pool
     int32_t max_fan;
-    int32_t pad;
+    int32_t member;       // the batch member the group belongs to
 };
 
 // Device-side view of a graph's index arrays (all int32, device memory).
@@ -108,6 +109,9 @@ struct DevGraph {
                              // null if there are none
     const int32_t *bs_pool;  // configuration lists by output state (EnumSeg::bs_base)
     const int32_t *edge_var; // [E] each edge's variable (graphs with such lists), else null
+    const int32_t *frozen;   // [n_members] batches: nonzero = the factor pass skips the
+                             // member (per-member early exit; zero outside such runs);
+                             // null for single graphs and until first needed
     float *b_lo;             // [VS] for variables of the warp pass (K > 16): what the
                              // iteration's beliefs b lost to rounding (b + b_lo is the
                              // float-float value); null if there are none
@@ -233,6 +237,19 @@ cudaError_t launch_residual(int64_t n, const float *a, const float *b, unsigned 
 // while the residual bits in *res are above tol (or NaN) and *done < limit.
 cudaError_t launch_until_control(cudaGraphConditionalHandle h, const unsigned *res, int *done, int n, int limit,
                                  float tol, cudaStream_t s);
+// Per-member early exit of a batch (member edge-state ranges off[n_members + 1]):
+// state reset; residuals of the members not frozen (res[m] = max(res[m], max |a - b|));
+// loop control after a trip of n iterations (frozen members' words: 2 = frozen this
+// trip, its messages to be copied to the other buffer; 1 = frozen); the copy.
+cudaError_t launch_until_members_init(int32_t *frozen, unsigned *res, int32_t *iters, float *resid,
+                                      const int32_t *off, int n_members, int *state, cudaStream_t s);
+cudaError_t launch_residual_members(int64_t n, const float *a, const float *b, const int32_t *off, int n_members,
+                                    const int32_t *frozen, unsigned *res, int n_sm, cudaStream_t s);
+cudaError_t launch_until_control_members(cudaGraphConditionalHandle h, bool set_condition, unsigned *res,
+                                         int32_t *frozen, int32_t *iters, float *resid, int n_members, int *state,
+                                         int n, int limit, float tol, cudaStream_t s);
+cudaError_t launch_freeze_copy(const int32_t *frozen, const int32_t *off, int n_members, const float *a, float *b,
+                               int n_sm, cudaStream_t s);
 // out[s VS + i] = ev[i] + noise[s VS + i] (perturb-and-max-product evidence).
 cudaError_t launch_pmp_perturb(int64_t VS, int S, const float *ev, const float *noise, float *out, cudaStream_t s);
 // Log-ratio pack (from the [2E] edge-state layout; unused slots 0) and unpack.

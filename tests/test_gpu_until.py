@@ -107,3 +107,64 @@ def test_device_loop_equals_host_checked(gpu, which):
             out.append((done, np.float32(res), m.cpu().numpy()))
         assert out[0][0] == out[1][0] and out[0][1] == out[1][1], (which, max_iters, out[0][:2], out[1][:2])
         assert np.array_equal(out[0][2], out[1][2])
+
+
+def _members():
+    ms = [W.ising_grid(20, 30, 1, T=1.0), W.potts_grid(16, 4, 2, T=1.0), W.ising_grid(9, 9, 3, T=1.0),
+          W.potts_grid(12, 8, 4, T=1.0), W.rbm(12, 9, 5, T=1.0)]
+    g, lp, ev = W.random_graph(6, n_vars=12, max_K=3, n_pair=14, n_triple=2)
+    ms.append(W.Problem("random", g, lp, ev, 1.0, 0.5, 10))
+    return ms
+
+
+@pytest.mark.parametrize("graphs", [1, 0])
+@pytest.mark.parametrize("case", [(300, 1e-5, 10), (57, 1e-4, 8), (40, 0.0, 10)])
+def test_members_stop_on_their_own(gpu, graphs, case):
+    """pgm_run_bp_until_members on a batch: every member's iterations, residual and
+    messages equal pgm_run_bp_until of that member alone (log-ratio iterations off), so
+    a stopped member keeps its messages while the others go on."""
+    import torch
+    max_iters, tol, ck = case
+    ms = _members()
+    T = 1.0
+    bg = gpu.Graph([p.graph for p in ms])
+    bg.set_option(gpu.OPT_CUDA_GRAPH, graphs)
+    lp = _t(np.concatenate([p.log_pot for p in ms]))
+    ev = _t(np.concatenate([p.evidence for p in ms]))
+    for rep in range(2):  # the second call replays the cached graph
+        m = bg.new_msgs()
+        done, res = bg.run_bp_until_members(lp, ev, T, 0.5, max_iters, tol, ck, m)
+        mm = m.cpu().numpy()
+        for k, p in enumerate(ms):
+            g = gpu.Graph(p.graph)
+            g.set_option(gpu.OPT_LOG_RATIO, 0)
+            a = g.new_msgs()
+            d1, r1 = g.run_bp_until(_t(p.log_pot), _t(p.evidence), T, 0.5, max_iters, tol, ck, a)
+            info = bg.member(k)
+            assert (done[k], np.float32(res[k])) == (d1, np.float32(r1)), (k, p.name, done[k], res[k], d1, r1)
+            assert np.array_equal(mm[info["es_off"]:info["es_off"] + info["n_edge_states"]], a.cpu().numpy()), p.name
+    if tol > 0 and max_iters == 300:
+        assert len(set(done.tolist())) > 1  # members stopped at different iterations
+    # a normal run afterwards skips nothing
+    m1 = bg.new_msgs()
+    bg.run_bp(lp, ev, T, 0.5, 7, m1)
+    for k, p in enumerate(ms):
+        g = gpu.Graph(p.graph)
+        g.set_option(gpu.OPT_LOG_RATIO, 0)  # the batch is not a binary pairwise graph
+        a = g.new_msgs()
+        g.run_bp(_t(p.log_pot), _t(p.evidence), T, 0.5, 7, a)
+        info = bg.member(k)
+        assert np.array_equal(m1.cpu().numpy()[info["es_off"]:info["es_off"] + info["n_edge_states"]], a.cpu().numpy())
+
+
+def test_members_arguments(gpu):
+    ms = _members()[:2]
+    bg = gpu.Graph([p.graph for p in ms])
+    lp = _t(np.concatenate([p.log_pot for p in ms]))
+    ev = _t(np.concatenate([p.evidence for p in ms]))
+    m = bg.new_msgs()
+    done, res = bg.run_bp_until_members(lp, ev, 1.0, 0.5, 0, 1e-3, 5, m)
+    assert (done == 0).all() and np.isnan(res).all()
+    for bad in ((1e-3, 0), (-1.0, 5), (float("nan"), 5)):
+        with pytest.raises(gpu.PgmError):
+            bg.run_bp_until_members(lp, ev, 1.0, 0.5, 10, bad[0], bad[1], m)
