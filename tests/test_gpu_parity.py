@@ -289,3 +289,17 @@ def test_random_loopy_stepwise(gpu, T):
         g, lp, ev = W.random_graph(seed, n_vars=40, max_K=4, n_pair=70, n_triple=6, n_or=5, n_and=5,
                                    sparse=True, shared=(seed % 2 == 1))
         _check_stepwise(gpu, g, lp, ev, T, 0.5, [0, 5, 11], f"random seed={seed}")
+
+
+def test_check_desc_device_bytes_match_build(gpu):
+    """pgm_check_desc's device-memory figure (what the serving loop admits by) equals
+    pgm_build's within the 256-byte alignment of each sub-array, for every layout: the
+    log-ratio grid, K-state grids, high-degree variables (RBM), logical factors, and large
+    listed-configuration factors (lists by output state, per-edge variables, residuals)."""
+    cases = [W.ising_grid(30, 40, 1).graph, W.potts_grid(20, 8, 2).graph, W.rbm(100, 80, 3).graph,
+             W.deconvolution(4, n_img=2).graph, W.pool_grid(8, 3, 1, 5).graph,
+             W.random_enum_factors(6, 30, 48, 2, 20, 2304).graph]
+    for fg in cases:
+        est = gpu.check_desc(fg)["device_bytes"]
+        built = gpu.Graph(fg).info["device_bytes"]
+        assert est <= built <= est + 24 * 256, (est, built)
