@@ -309,10 +309,14 @@ pgm_status pgm_grid2_run_bp_noalloc(int32_t rows, int32_t cols, const float *log
  * runs. A chunk holds as many samples as keep the arrays exchanged between the passes
  * (about 32 bytes per variable and sample, plus 12 per factor and sample for
  * per-sample tables) within half the L2; where one sample alone exceeds that (e.g. a
- * 1000 x 1000 grid), and on other graphs, the samples run one after another as
- * pgm_run_bp. The first call with a larger chunk than before allocates device buffers
- * (about 72 bytes per variable and sample on a grid), synchronising the device; they
- * are kept until pgm_free. Stream-ordered otherwise.
+ * 1000 x 1000 grid), the samples run one after another as pgm_run_bp. On every other
+ * graph the samples run side by side as the second grid dimension of each edge-state
+ * launch (one variable pass and one factor pass per iteration for a chunk, the index
+ * arrays shared), in chunks whose per-sample scratch (a message buffer, beliefs, and the
+ * graph's leave-one-out and residual buffers if it has them) stays within 1 GiB;
+ * results equal those of the single-sample runs. The first call with a larger chunk
+ * than before allocates device buffers, synchronising the device; they are kept until
+ * pgm_free. Stream-ordered otherwise.
  * PGM_EINVAL for n_samples < 1 or the pgm_run_bp argument errors.
  */
 pgm_status pgm_run_bp_multi(pgm_graph *g, int32_t n_samples, const float *log_pot, int32_t pot_per_sample,

@@ -87,6 +87,9 @@ struct pgm_graph {
     // frozen words, residual words, iterations and residuals [n each], loop state [3]
     // (iterations done, go on, a member active), the previous messages [n_edge_states]
     char *mu_mem = nullptr;
+    // pgm_run_bp_multi on graphs without the joint log-ratio path: per-sample scratch
+    char *mse_mem = nullptr;
+    size_t mse_bytes = 0;
     int32_t *mu_off = nullptr, *mu_frozen = nullptr, *mu_iters = nullptr;
     unsigned *mu_res = nullptr;
     float *mu_resid = nullptr, *mu_prev = nullptr;
@@ -647,6 +650,7 @@ void pgm_free(pgm_graph *g) {
     if (g->until_prev) cudaFree(g->until_prev);
     if (g->until_res_host) cudaFreeHost(g->until_res_host);
     if (g->mu_mem) cudaFree(g->mu_mem);
+    if (g->mse_mem) cudaFree(g->mse_mem);
     for (cudaEvent_t e : g->events) cudaEventDestroy(e);
     drop_cached_runs(g);
     if (g->capture_stream) cudaStreamDestroy(g->capture_stream);
@@ -861,6 +865,62 @@ static pgm_status ms_reserve(pgm_graph *g, int32_t S) {
     return PGM_OK;
 }
 
+// Edge-state iterations of many samples of one graph, the samples as the y dimension of
+// every launch: they share the index arrays; each has its own ping-pong partner of its
+// messages, beliefs and, where the graph uses them, exact leave-one-out and belief-residual
+// scratch. Samples run in chunks whose scratch is at most 1 GiB (and at most 65,535).
+static pgm_status run_multi_es(pgm_graph *g, int32_t n_samples, const float *log_pot, int32_t pot_per_sample,
+                               const float *evidence, float T, float damping, int32_t n_iters, float *msgs,
+                               void *stream) {
+    const int64_t VS = g->info.n_var_states, ES = g->info.n_edge_states, P = g->info.n_potentials;
+    const int64_t hd = g->G.v2f_hd ? 2 * ES : 0, blo = g->G.b_lo ? VS : 0;
+    const int64_t per = 4 * (ES + VS + hd + blo);
+    const int64_t chunk = std::min<int64_t>({(int64_t)n_samples, 65535, std::max<int64_t>(1, ((int64_t)1 << 30) / per)});
+    if (chunk <= 1) {
+        for (int32_t smp = 0; smp < n_samples; ++smp) {
+            pgm_status st = pgm_run_bp(g, log_pot + (pot_per_sample ? (size_t)smp * P : 0),
+                                       evidence + (size_t)smp * VS, T, damping, n_iters, msgs + (size_t)smp * ES, stream);
+            if (st != PGM_OK) return st;
+        }
+        return PGM_OK;
+    }
+    const size_t r_mt = align_up((size_t)(chunk * ES) * 4, 256), r_b = align_up((size_t)(chunk * VS) * 4, 256);
+    const size_t r_hd = align_up((size_t)(chunk * hd) * 4, 256), r_lo = align_up((size_t)(chunk * blo) * 4, 256);
+    const size_t need = r_mt + r_b + r_hd + r_lo;
+    if (g->mse_bytes < need) {
+        if (g->mse_mem) cudaFree(g->mse_mem);  // (synchronises the device: no launch still uses it)
+        g->mse_mem = nullptr;
+        g->mse_bytes = 0;
+        if (cudaMalloc(&g->mse_mem, need) != cudaSuccess) return fail(PGM_ENOMEM, "cudaMalloc(multi-sample scratch)");
+        g->mse_bytes = need;
+    }
+    float *mt = reinterpret_cast<float *>(g->mse_mem), *bb = reinterpret_cast<float *>(g->mse_mem + r_mt);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    for (int64_t s0 = 0; s0 < n_samples; s0 += chunk) {
+        const int S = (int)std::min<int64_t>(chunk, n_samples - s0);
+        DevGraph Gs = g->G;
+        Gs.s_es = ES;
+        Gs.s_vs = VS;
+        Gs.s_pot = pot_per_sample ? P : 0;
+        Gs.v2f_hd = hd ? reinterpret_cast<float *>(g->mse_mem + r_mt + r_b) : nullptr;
+        Gs.b_lo = blo ? reinterpret_cast<float *>(g->mse_mem + r_mt + r_b + r_hd) : nullptr;
+        const float *lp = log_pot + (pot_per_sample ? (size_t)s0 * P : 0);
+        const float *ev = evidence + (size_t)s0 * VS;
+        float *m0 = msgs + (size_t)s0 * ES, *cur = m0, *nxt = mt;
+        for (int it = 0; it < n_iters; ++it) {
+            cudaError_t e = launch_var_pass(Gs, g->P, ev, cur, bb, kVarIter, nullptr, s, S);
+            if (e == cudaSuccess) e = launch_factor_pass(Gs, g->P, lp, bb, ev, cur, nxt, T, damping, s, S);
+            if (e != cudaSuccess) return cuda_fail(e, "multi-sample pass launch");
+            std::swap(cur, nxt);
+        }
+        if (cur != m0) {
+            cudaError_t e = cudaMemcpyAsync(m0, cur, (size_t)S * ES * sizeof(float), cudaMemcpyDeviceToDevice, s);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(multi-sample messages)");
+        }
+    }
+    return PGM_OK;
+}
+
 pgm_status pgm_run_bp_multi(pgm_graph *g, int32_t n_samples, const float *log_pot, int32_t pot_per_sample,
                             const float *evidence, float T, float damping, int32_t n_iters, float *msgs,
                             void *stream) {
@@ -871,16 +931,10 @@ pgm_status pgm_run_bp_multi(pgm_graph *g, int32_t n_samples, const float *log_po
     const int64_t VS = g->info.n_var_states, ES = g->info.n_edge_states, P = g->info.n_potentials;
     const bool ms = log_ratio_run(g, n_iters) && g->G.vin_tab4 != nullptr &&
                     4 * (int64_t)g->info.n_vars * n_samples <= INT32_MAX;
-    if (!ms) {  // each sample on its own (same kernels, no shared index traffic)
-        for (int32_t s = 0; s < n_samples; ++s) {
-            st = pgm_run_bp(g, log_pot + (pot_per_sample ? (size_t)s * P : 0), evidence + (size_t)s * VS, T,
-                            damping, n_iters, msgs + (size_t)s * ES, stream);
-            if (st != PGM_OK) return st;
-        }
-        return PGM_OK;
-    }
     DeviceGuard dg(g->device);
     if (!dg.ok) return fail(PGM_ECUDA, "cudaSetDevice failed");
+    if (!ms)  // any other graph: edge-state iterations with the samples side by side
+        return run_multi_es(g, n_samples, log_pot, pot_per_sample, evidence, T, damping, n_iters, msgs, stream);
     // Samples run together in chunks whose per-iteration exchange arrays (messages and
     // per-variable totals, plus their table differences and evidence) fit in half the
     // L2, so that the factor pass finds them there; a sample that alone needs more runs

@@ -397,6 +397,20 @@ __device__ __forceinline__ float lse_row(const float (&z)[K], float T, float inv
 // Variable pass
 // =====================================================================================
 
+// Multi-sample launches (pgm_run_bp_multi on graphs without the joint log-ratio path):
+// gridDim.y samples share the index arrays; a block works on sample blockIdx.y, whose
+// messages, beliefs, evidence and log-potentials lie at the DevGraph strides (0 for an
+// ordinary launch) and whose scratch (exact leave-one-out sums, belief residuals) is the
+// sample's slice.
+__device__ __forceinline__ int64_t sample_select(DevGraph &G) {
+    const int64_t smp = blockIdx.y;
+    if (smp != 0) {
+        if (G.v2f_hd) G.v2f_hd += smp * 2 * G.s_es;
+        if (G.b_lo) G.b_lo += smp * G.s_vs;
+    }
+    return smp;
+}
+
 // Thread per variable (degree <= kVarBlockDegree). Sums are compensated (float-float)
 // in ascending edge order. KFIX = 2: every variable binary (states at 2v, edge-states
 // even, float2 loads).
@@ -406,6 +420,13 @@ __global__ void __launch_bounds__(256) k_var_thread(DevGraph G, const int32_t *_
                                                     const float *__restrict__ m,
                                                     float *__restrict__ out,
                                                     int32_t *__restrict__ dec) {
+    {  // multi-sample launches: this block's sample
+        const int64_t smp = sample_select(G);
+        ev += smp * G.s_vs;
+        m += smp * G.s_es;
+        out += smp * G.s_vs;
+        if (dec) dec += smp * G.V;
+    }
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= n) return;
     const int v = list ? __ldg(list + t) : t;
@@ -503,6 +524,13 @@ template <int MODE>
 __global__ void __launch_bounds__(256) k_var_warp(DevGraph G, const int32_t *__restrict__ list, int n,
                                                   const float *__restrict__ ev, const float *__restrict__ m,
                                                   float *__restrict__ out, int32_t *__restrict__ dec) {
+    {  // multi-sample launches: this block's sample
+        const int64_t smp = sample_select(G);
+        ev += smp * G.s_vs;
+        m += smp * G.s_es;
+        out += smp * G.s_vs;
+        if (dec) dec += smp * G.V;
+    }
     const int w = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
     if (w >= n) return;  // warp-uniform
     const int v = list ? __ldg(list + w) : w;
@@ -604,6 +632,13 @@ template <int MODE>
 __global__ void __launch_bounds__(256) k_var_tab4(DevGraph G, int n, const float *__restrict__ ev,
                                                   const float *__restrict__ m, float *__restrict__ out,
                                                   int32_t *__restrict__ dec) {
+    {  // multi-sample launches: this block's sample
+        const int64_t smp = sample_select(G);
+        ev += smp * G.s_vs;
+        m += smp * G.s_es;
+        out += smp * G.s_vs;
+        if (dec) dec += smp * G.V;
+    }
     const int v = blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= n) return;
     const int4 t = __ldcs(G.vin_tab4 + v);
@@ -682,6 +717,13 @@ template <int K, int MODE>
 __global__ void __launch_bounds__(256) k_var_group(DevGraph G, const int32_t *__restrict__ list, int n,
                                                    const float *__restrict__ ev, const float *__restrict__ m,
                                                    float *__restrict__ out, int32_t *__restrict__ dec) {
+    {  // multi-sample launches: this block's sample
+        const int64_t smp = sample_select(G);
+        ev += smp * G.s_vs;
+        m += smp * G.s_es;
+        out += smp * G.s_vs;
+        if (dec) dec += smp * G.V;
+    }
     constexpr int L = K / 4;
     const int l = threadIdx.x & (L - 1);
     const int t_raw = (blockIdx.x * blockDim.x + threadIdx.x) / L;
@@ -814,6 +856,13 @@ __global__ void __launch_bounds__(kVarBlockThreads) k_var_block(DevGraph G, cons
                                                                 const float *__restrict__ m,
                                                                 float *__restrict__ out,
                                                                 int32_t *__restrict__ dec) {
+    {  // multi-sample launches: this block's sample
+        const int64_t smp = sample_select(G);
+        ev += smp * G.s_vs;
+        m += smp * G.s_es;
+        out += smp * G.s_vs;
+        if (dec) dec += smp * G.V;
+    }
     __shared__ float sh[64];
     __shared__ FF tile_tot[kVarMaxTiles];
     __shared__ FF sb[kMaxStates];
@@ -1051,6 +1100,14 @@ __global__ void __launch_bounds__(K >= 16 ? 128 : 256, K == 2 ? 8 : 1)
 k_pair(DevGraph G, const EnumSeg *__restrict__ segs, int n_seg, const float *__restrict__ pot,
        const float *__restrict__ b, const float *__restrict__ ev, const float *__restrict__ m_old,
        float *__restrict__ m_new, float T, float invT, float damping) {
+    {  // multi-sample launches: this block's sample
+        const int64_t smp = sample_select(G);
+        pot += smp * G.s_pot;
+        b += smp * G.s_vs;
+        ev += smp * G.s_vs;
+        m_old += smp * G.s_es;
+        m_new += smp * G.s_es;
+    }
     __shared__ float tab[K * K];
     __shared__ float tabE[K >= 4 ? K * K : 1];
     __shared__ float tinfo[2];
@@ -1237,6 +1294,14 @@ __global__ void __launch_bounds__(256, 4)
 k_pair_group(DevGraph G, const EnumSeg *__restrict__ segs, int n_seg, int n_vblocks, const float *__restrict__ pot,
              const float *__restrict__ b, const float *__restrict__ ev, const float *__restrict__ m_old,
              float *__restrict__ m_new, float T, float invT, float damping) {
+    {  // multi-sample launches: this block's sample
+        const int64_t smp = sample_select(G);
+        pot += smp * G.s_pot;
+        b += smp * G.s_vs;
+        ev += smp * G.s_vs;
+        m_old += smp * G.s_es;
+        m_new += smp * G.s_es;
+    }
     __shared__ float tab[K * K], tabT[K * K];
     __shared__ __align__(16) float tabE[MAXP ? 4 : K * kRowPad<K>];
     __shared__ __align__(16) float tabET[MAXP ? 4 : K * kRowPad<K>];
@@ -1410,6 +1475,14 @@ __global__ void __launch_bounds__(K >= 16 ? 128 : 256)
 k_pair_thr(DevGraph G, const EnumSeg *__restrict__ segs, int n_seg, const float *__restrict__ pot,
            const float *__restrict__ b, const float *__restrict__ ev, const float *__restrict__ m_old,
            float *__restrict__ m_new, float T, float invT, float damping) {
+    {  // multi-sample launches: this block's sample
+        const int64_t smp = sample_select(G);
+        pot += smp * G.s_pot;
+        b += smp * G.s_vs;
+        ev += smp * G.s_vs;
+        m_old += smp * G.s_es;
+        m_new += smp * G.s_es;
+    }
     __shared__ float tab[K * K];
     __shared__ __align__(16) float tabE[MAXP ? 4 : K * K];
     __shared__ __align__(16) float tabET[MAXP ? 4 : K * K];
@@ -1472,6 +1545,14 @@ k_enum_generic(DevGraph G, const EnumSeg *__restrict__ segs, int n_seg, const fl
                const float *__restrict__ b, const float *__restrict__ ev,
                const float *__restrict__ m_old, float *__restrict__ m_new, float T, float invT,
                float damping) {
+    {  // multi-sample launches: this block's sample
+        const int64_t smp = sample_select(G);
+        pot += smp * G.s_pot;
+        b += smp * G.s_vs;
+        ev += smp * G.s_vs;
+        m_old += smp * G.s_es;
+        m_new += smp * G.s_es;
+    }
     const EnumSeg *S = segs + find_seg(segs, n_seg, blockIdx.x);
     if (member_frozen(G, S->member)) return;
     const int f = (blockIdx.x - __ldg(&S->block_begin)) * blockDim.x + threadIdx.x;
@@ -1597,6 +1678,14 @@ __global__ void __launch_bounds__(kEnumBlockThreads)
 k_enum_block(DevGraph G, const EnumSeg *__restrict__ segs, int n_seg, const float *__restrict__ pot,
              const float *__restrict__ b, const float *__restrict__ ev, const float *__restrict__ m_old,
              float *__restrict__ m_new, float T, float invT, float damping) {
+    {  // multi-sample launches: this block's sample
+        const int64_t smp = sample_select(G);
+        pot += smp * G.s_pot;
+        b += smp * G.s_vs;
+        ev += smp * G.s_vs;
+        m_old += smp * G.s_es;
+        m_new += smp * G.s_es;
+    }
     extern __shared__ __align__(16) unsigned char eb_smem[];
     __shared__ int sK[kMaxArity], sKo[kMaxArity];
     __shared__ int s_fix[kEnumBlockThreads / 32][kMaxArity];
@@ -1890,6 +1979,13 @@ __global__ void __launch_bounds__(256)
 k_logic_small(DevGraph G, const LogicSeg *__restrict__ segs, int n_seg, const float *__restrict__ b,
               const float *__restrict__ ev, const float *__restrict__ m_old,
               float *__restrict__ m_new, float T, float invT, float damping) {
+    {  // multi-sample launches: this block's sample
+        const int64_t smp = sample_select(G);
+        b += smp * G.s_vs;
+        ev += smp * G.s_vs;
+        m_old += smp * G.s_es;
+        m_new += smp * G.s_es;
+    }
     const LogicSeg *S = segs + find_seg(segs, n_seg, blockIdx.x);
     if (member_frozen(G, S->member)) return;
     const int f = (blockIdx.x - __ldg(&S->block_begin)) * blockDim.x + threadIdx.x;
@@ -1998,6 +2094,13 @@ __global__ void __launch_bounds__(128)
 k_logic_warp(DevGraph G, const LogicSeg *__restrict__ segs, int n_seg, const float *__restrict__ b,
              const float *__restrict__ ev, const float *__restrict__ m_old,
              float *__restrict__ m_new, float T, float invT, float damping, int cap) {
+    {  // multi-sample launches: this block's sample
+        const int64_t smp = sample_select(G);
+        b += smp * G.s_vs;
+        ev += smp * G.s_vs;
+        m_old += smp * G.s_es;
+        m_new += smp * G.s_es;
+    }
     extern __shared__ float smem[];
     const int warps = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const LogicSeg *S = segs + find_seg(segs, n_seg, blockIdx.x);
@@ -2988,53 +3091,53 @@ cudaError_t prepare_kernels(int max_smem_bytes) {
 
 template <int MODE>
 static void var_pass_mode(const DevGraph &G, const Plan &P, const float *ev, const float *m,
-                          float *out, int32_t *dec, cudaStream_t s) {
+                          float *out, int32_t *dec, cudaStream_t s, int S) {
     if (G.vin_tab4 != nullptr) {
         const int n = G.V;
-        k_var_tab4<MODE><<<(n + 255) / 256, 256, 0, s>>>(G, n, ev, m, out, dec);
+        k_var_tab4<MODE><<<dim3((n + 255) / 256, S), 256, 0, s>>>(G, n, ev, m, out, dec);
         return;
     }
     for (const VarLaunch &L : P.var) {
         if (L.n == 0) continue;
         switch (L.kind) {
             case kVarBlock:
-                k_var_block<MODE><<<L.n, kVarBlockThreads, 0, s>>>(G, L.list, ev, m, out, dec);
+                k_var_block<MODE><<<dim3(L.n, S), kVarBlockThreads, 0, s>>>(G, L.list, ev, m, out, dec);
                 break;
             case kVarBinary:
-                k_var_thread<2, MODE><<<L.n_blocks, L.threads, 0, s>>>(G, L.list, L.n, L.dense_binary, ev, m, out, dec);
+                k_var_thread<2, MODE><<<dim3(L.n_blocks, S), L.threads, 0, s>>>(G, L.list, L.n, L.dense_binary, ev, m, out, dec);
                 break;
             case kVarGroup4:
-                k_var_group<4, MODE><<<L.n_blocks, L.threads, 0, s>>>(G, L.list, L.n, ev, m, out, dec);
+                k_var_group<4, MODE><<<dim3(L.n_blocks, S), L.threads, 0, s>>>(G, L.list, L.n, ev, m, out, dec);
                 break;
             case kVarGroup8:
-                k_var_group<8, MODE><<<L.n_blocks, L.threads, 0, s>>>(G, L.list, L.n, ev, m, out, dec);
+                k_var_group<8, MODE><<<dim3(L.n_blocks, S), L.threads, 0, s>>>(G, L.list, L.n, ev, m, out, dec);
                 break;
             case kVarGroup16:
-                k_var_group<16, MODE><<<L.n_blocks, L.threads, 0, s>>>(G, L.list, L.n, ev, m, out, dec);
+                k_var_group<16, MODE><<<dim3(L.n_blocks, S), L.threads, 0, s>>>(G, L.list, L.n, ev, m, out, dec);
                 break;
             case kVarWarp:
-                k_var_warp<MODE><<<L.n_blocks, L.threads, 0, s>>>(G, L.list, L.n, ev, m, out, dec);
+                k_var_warp<MODE><<<dim3(L.n_blocks, S), L.threads, 0, s>>>(G, L.list, L.n, ev, m, out, dec);
                 break;
             default:
-                k_var_thread<0, MODE><<<L.n_blocks, L.threads, 0, s>>>(G, L.list, L.n, 0, ev, m, out, dec);
+                k_var_thread<0, MODE><<<dim3(L.n_blocks, S), L.threads, 0, s>>>(G, L.list, L.n, 0, ev, m, out, dec);
                 break;
         }
     }
 }
 
 cudaError_t launch_var_pass(const DevGraph &G, const Plan &P, const float *ev, const float *m,
-                            float *b, int mode, int32_t *decode, cudaStream_t s) {
-    if (mode == kVarIter) var_pass_mode<kVarIter>(G, P, ev, m, b, decode, s);
-    else if (mode == kVarBeliefs) var_pass_mode<kVarBeliefs>(G, P, ev, m, b, decode, s);
-    else if (mode == kVarNormalised) var_pass_mode<kVarNormalised>(G, P, ev, m, b, decode, s);
-    else var_pass_mode<kVarDecode>(G, P, ev, m, b, decode, s);
+                            float *b, int mode, int32_t *decode, cudaStream_t s, int S) {
+    if (mode == kVarIter) var_pass_mode<kVarIter>(G, P, ev, m, b, decode, s, S);
+    else if (mode == kVarBeliefs) var_pass_mode<kVarBeliefs>(G, P, ev, m, b, decode, s, S);
+    else if (mode == kVarNormalised) var_pass_mode<kVarNormalised>(G, P, ev, m, b, decode, s, S);
+    else var_pass_mode<kVarDecode>(G, P, ev, m, b, decode, s, S);
     return cudaGetLastError();
 }
 
 template <bool MAXP>
 static void factor_pass_t(const DevGraph &G, const Plan &P, const float *pot, const float *b,
                           const float *ev, const float *m_old, float *m_new, float T, float damping,
-                          cudaStream_t s) {
+                          cudaStream_t s, int S) {
     const float invT = MAXP ? 0.f : 1.f / T;
     for (const FactorLaunch &L : P.factor) {
         if (L.n_blocks == 0) continue;
@@ -3042,37 +3145,37 @@ static void factor_pass_t(const DevGraph &G, const Plan &P, const float *pot, co
         const LogicSeg *ls = static_cast<const LogicSeg *>(L.segs);
         switch (L.variant) {
             case kPair2:
-                k_pair<2, MAXP><<<L.n_blocks, L.threads, 0, s>>>(G, es, L.n_seg, pot, b, ev, m_old, m_new, T, invT, damping);
+                k_pair<2, MAXP><<<dim3(L.n_blocks, S), L.threads, 0, s>>>(G, es, L.n_seg, pot, b, ev, m_old, m_new, T, invT, damping);
                 break;
             case kPair4:
-                k_pair_group<4, MAXP><<<min(L.n_blocks, L.max_blocks), L.threads, 0, s>>>(G, es, L.n_seg, L.n_blocks, pot, b, ev, m_old, m_new, T, invT, damping);
+                k_pair_group<4, MAXP><<<dim3(min(L.n_blocks, L.max_blocks), S), L.threads, 0, s>>>(G, es, L.n_seg, L.n_blocks, pot, b, ev, m_old, m_new, T, invT, damping);
                 break;
             case kPair8:
-                k_pair_group<8, MAXP><<<min(L.n_blocks, L.max_blocks), L.threads, 0, s>>>(G, es, L.n_seg, L.n_blocks, pot, b, ev, m_old, m_new, T, invT, damping);
+                k_pair_group<8, MAXP><<<dim3(min(L.n_blocks, L.max_blocks), S), L.threads, 0, s>>>(G, es, L.n_seg, L.n_blocks, pot, b, ev, m_old, m_new, T, invT, damping);
                 break;
             case kPair16:
-                k_pair_group<16, MAXP><<<min(L.n_blocks, L.max_blocks), L.threads, 0, s>>>(G, es, L.n_seg, L.n_blocks, pot, b, ev, m_old, m_new, T, invT, damping);
+                k_pair_group<16, MAXP><<<dim3(min(L.n_blocks, L.max_blocks), S), L.threads, 0, s>>>(G, es, L.n_seg, L.n_blocks, pot, b, ev, m_old, m_new, T, invT, damping);
                 break;
             case kPairT4:
-                k_pair_thr<4, MAXP><<<L.n_blocks, L.threads, 0, s>>>(G, es, L.n_seg, pot, b, ev, m_old, m_new, T, invT, damping);
+                k_pair_thr<4, MAXP><<<dim3(L.n_blocks, S), L.threads, 0, s>>>(G, es, L.n_seg, pot, b, ev, m_old, m_new, T, invT, damping);
                 break;
             case kPairT8:
-                k_pair_thr<8, MAXP><<<L.n_blocks, L.threads, 0, s>>>(G, es, L.n_seg, pot, b, ev, m_old, m_new, T, invT, damping);
+                k_pair_thr<8, MAXP><<<dim3(L.n_blocks, S), L.threads, 0, s>>>(G, es, L.n_seg, pot, b, ev, m_old, m_new, T, invT, damping);
                 break;
             case kPairT16:
-                k_pair_thr<16, MAXP><<<L.n_blocks, L.threads, 0, s>>>(G, es, L.n_seg, pot, b, ev, m_old, m_new, T, invT, damping);
+                k_pair_thr<16, MAXP><<<dim3(L.n_blocks, S), L.threads, 0, s>>>(G, es, L.n_seg, pot, b, ev, m_old, m_new, T, invT, damping);
                 break;
             case kEnumGeneric:
-                k_enum_generic<MAXP><<<L.n_blocks, L.threads, 0, s>>>(G, es, L.n_seg, pot, b, ev, m_old, m_new, T, invT, damping);
+                k_enum_generic<MAXP><<<dim3(L.n_blocks, S), L.threads, 0, s>>>(G, es, L.n_seg, pot, b, ev, m_old, m_new, T, invT, damping);
                 break;
             case kEnumBlock:
-                k_enum_block<MAXP><<<L.n_blocks, L.threads, L.smem, s>>>(G, es, L.n_seg, pot, b, ev, m_old, m_new, T, invT, damping);
+                k_enum_block<MAXP><<<dim3(L.n_blocks, S), L.threads, L.smem, s>>>(G, es, L.n_seg, pot, b, ev, m_old, m_new, T, invT, damping);
                 break;
             case kLogicSmall:
-                k_logic_small<MAXP><<<L.n_blocks, L.threads, 0, s>>>(G, ls, L.n_seg, b, ev, m_old, m_new, T, invT, damping);
+                k_logic_small<MAXP><<<dim3(L.n_blocks, S), L.threads, 0, s>>>(G, ls, L.n_seg, b, ev, m_old, m_new, T, invT, damping);
                 break;
             case kLogicWarp:
-                k_logic_warp<MAXP><<<L.n_blocks, L.threads, L.smem, s>>>(G, ls, L.n_seg, b, ev, m_old, m_new, T, invT, damping, L.max_fan);
+                k_logic_warp<MAXP><<<dim3(L.n_blocks, S), L.threads, L.smem, s>>>(G, ls, L.n_seg, b, ev, m_old, m_new, T, invT, damping, L.max_fan);
                 break;
             default:
                 break;
@@ -3248,9 +3351,9 @@ cudaError_t launch_lr_unpack(const DevGraph &G, const float *d, float *m, cudaSt
 
 cudaError_t launch_factor_pass(const DevGraph &G, const Plan &P, const float *log_pot,
                                const float *b, const float *ev, const float *m_old,
-                               float *m_new, float T, float damping, cudaStream_t s) {
-    if (T == 0.f) factor_pass_t<true>(G, P, log_pot, b, ev, m_old, m_new, T, damping, s);
-    else factor_pass_t<false>(G, P, log_pot, b, ev, m_old, m_new, T, damping, s);
+                               float *m_new, float T, float damping, cudaStream_t s, int S) {
+    if (T == 0.f) factor_pass_t<true>(G, P, log_pot, b, ev, m_old, m_new, T, damping, s, S);
+    else factor_pass_t<false>(G, P, log_pot, b, ev, m_old, m_new, T, damping, s, S);
     return cudaGetLastError();
 }
 

@@ -109,6 +109,9 @@ struct DevGraph {
                              // null if there are none
     const int32_t *bs_pool;  // configuration lists by output state (EnumSeg::bs_base)
     const int32_t *edge_var; // [E] each edge's variable (graphs with such lists), else null
+    int64_t s_es, s_vs, s_pot;  // multi-sample launches (gridDim.y samples): per-sample
+                                // strides of messages, evidence and beliefs, and
+                                // log-potentials (0 if shared); 0 for ordinary launches
     const int32_t *frozen;   // [n_members] batches: nonzero = the factor pass skips the
                              // member (per-member early exit; zero outside such runs);
                              // null for single graphs and until first needed
@@ -201,11 +204,12 @@ struct HostLayout {
 std::string compile_graph(const void *const *descs, int n_desc, HostLayout *out);
 
 // Kernel launchers (kernels.cu). Each returns cudaGetLastError() of its launches.
+// (n_samples > 1: samples as the launches' y dimension, at the strides of G)
 cudaError_t launch_var_pass(const DevGraph &G, const Plan &P, const float *ev, const float *m,
-                            float *b, int mode, int32_t *decode, cudaStream_t s);
+                            float *b, int mode, int32_t *decode, cudaStream_t s, int n_samples = 1);
 cudaError_t launch_factor_pass(const DevGraph &G, const Plan &P, const float *log_pot,
                                const float *b, const float *ev, const float *m_old,
-                               float *m_new, float T, float damping, cudaStream_t s);
+                               float *m_new, float T, float damping, cudaStream_t s, int n_samples = 1);
 // Log-ratio iteration of a Plan::lr graph (kernels.cu): d the factor-to-variable
 // messages, lam the variable-to-factor values, one log-ratio per edge in variable order
 // (slots DevGraph::lr_pos; 4V of them with vin_tab4, else E); the factor pass updates d

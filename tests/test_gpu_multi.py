@@ -121,13 +121,41 @@ def test_growing_sample_count_and_short_runs(gpu):
         gpu.check(gpu.load_library().pgm_run_bp_multi(g.handle, 0, None, 0, None, 1.0, 0.5, 1, None, None))
 
 
-def test_other_graphs_run_sample_by_sample(gpu):
-    p = W.potts_grid(12, 4, 1, T=1.0)
+def _other(name):
+    if name == "potts4":
+        return W.potts_grid(12, 4, 1, T=1.0)
+    if name == "potts16":
+        return W.potts_grid(10, 16, 2, T=1.0)
+    if name == "rbm":  # visible variables of degree 150: block-per-variable pass, exact sums
+        return W.rbm(40, 150, 3)
+    if name == "deconv":  # OR / AND factors, degree up to 200
+        return W.deconvolution(4, n_img=1, n_iters=10)
+    if name == "pool":  # 49-state variables (warp pass, residuals), block-form factors
+        return W.pool_grid(6, 3, 1, 5, T=1.0)
+    g, lp, ev = W.random_graph(9, n_vars=14, max_K=4, n_pair=16, n_triple=3, n_or=2, n_and=2)
+    return W.Problem("random", g, lp, ev, 1.0, 0.5, 10)
+
+
+@pytest.mark.parametrize("T", [1.0, 0.0])
+@pytest.mark.parametrize("per_sample_pot", [False, True])
+@pytest.mark.parametrize("name", ["potts4", "potts16", "rbm", "deconv", "pool", "random"])
+def test_other_graphs_samples_side_by_side(gpu, name, per_sample_pot, T):
+    """Graphs without the joint log-ratio path run their samples as the second grid
+    dimension of every edge-state launch; each sample's messages are bitwise those of
+    pgm_run_bp on that sample alone."""
+    p = _other(name)
+    S = 5
     rng = np.random.default_rng(3)
-    ev = rng.standard_normal((3, p.graph.n_var_states)).astype(np.float32)
-    lp = p.log_pot.astype(np.float32)
-    _, mm = _multi(gpu, p.graph, lp, ev, 1.0, 15)
-    _same(mm, _single(gpu, p.graph, lp, ev, 1.0, 15))
+    ev = (np.asarray(p.evidence, np.float32)[None, :] +
+          rng.standard_normal((S, p.graph.n_var_states)).astype(np.float32))
+    if per_sample_pot and p.graph.n_potentials > 0:
+        lp = (np.asarray(p.log_pot, np.float32)[None, :] +
+              0.3 * rng.standard_normal((S, p.graph.n_potentials)).astype(np.float32))
+    else:
+        lp = np.asarray(p.log_pot, np.float32)
+    for it in (7, 8):  # odd and even: the result in the scratch buffer or in place
+        _, mm = _multi(gpu, p.graph, lp, ev, T, it)
+        _same(mm, _single(gpu, p.graph, lp, ev, T, it))
 
 
 def test_chunks_of_samples(gpu):
