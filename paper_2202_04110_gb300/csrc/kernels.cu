@@ -397,8 +397,9 @@ __device__ __forceinline__ float lse_row(const float (&z)[K], float T, float inv
 // Variable pass
 // =====================================================================================
 
-// Multi-sample launches (pgm_run_bp_multi on graphs without the joint log-ratio path):
-// gridDim.y samples share the index arrays; a block works on sample blockIdx.y, whose
+// Multi-sample launches (pgm_run_bp_multi on graphs without the joint log-ratio path;
+// the kernels' MS instantiations): gridDim.y samples share the index arrays; a block
+// works on sample blockIdx.y, whose
 // messages, beliefs, evidence and log-potentials lie at the DevGraph strides (0 for an
 // ordinary launch) and whose scratch (exact leave-one-out sums, belief residuals) is the
 // sample's slice.
@@ -414,13 +415,13 @@ __device__ __forceinline__ int64_t sample_select(DevGraph &G) {
 // Thread per variable (degree <= kVarBlockDegree). Sums are compensated (float-float)
 // in ascending edge order. KFIX = 2: every variable binary (states at 2v, edge-states
 // even, float2 loads).
-template <int KFIX, int MODE>
+template <int KFIX, int MODE, bool MS = false>
 __global__ void __launch_bounds__(256) k_var_thread(DevGraph G, const int32_t *__restrict__ list, int n,
                                                     int dense_binary, const float *__restrict__ ev,
                                                     const float *__restrict__ m,
                                                     float *__restrict__ out,
                                                     int32_t *__restrict__ dec) {
-    {  // multi-sample launches: this block's sample
+    if constexpr (MS) {  // multi-sample launches: this block's sample
         const int64_t smp = sample_select(G);
         ev += smp * G.s_vs;
         m += smp * G.s_es;
@@ -520,11 +521,11 @@ __global__ void __launch_bounds__(256) k_var_thread(DevGraph G, const int32_t *_
 // bits (normalised beliefs sum e^r in another order). The iteration also writes b_lo,
 // the rounding residual of each value, so that a factor can form b - m without the
 // cancellation a large message would cause.
-template <int MODE>
+template <int MODE, bool MS = false>
 __global__ void __launch_bounds__(256) k_var_warp(DevGraph G, const int32_t *__restrict__ list, int n,
                                                   const float *__restrict__ ev, const float *__restrict__ m,
                                                   float *__restrict__ out, int32_t *__restrict__ dec) {
-    {  // multi-sample launches: this block's sample
+    if constexpr (MS) {  // multi-sample launches: this block's sample
         const int64_t smp = sample_select(G);
         ev += smp * G.s_vs;
         m += smp * G.s_es;
@@ -628,11 +629,11 @@ __global__ void __launch_bounds__(256) k_var_warp(DevGraph G, const int32_t *__r
 // Thread per variable for binary graphs whose variables all have at most 4 factors:
 // one 16-byte row of incoming edge-states per variable (-1 = none), all four message
 // gathers issued before the compensated sums (in ascending edge order, as the CSR path).
-template <int MODE>
+template <int MODE, bool MS = false>
 __global__ void __launch_bounds__(256) k_var_tab4(DevGraph G, int n, const float *__restrict__ ev,
                                                   const float *__restrict__ m, float *__restrict__ out,
                                                   int32_t *__restrict__ dec) {
-    {  // multi-sample launches: this block's sample
+    if constexpr (MS) {  // multi-sample launches: this block's sample
         const int64_t smp = sample_select(G);
         ev += smp * G.s_vs;
         m += smp * G.s_es;
@@ -713,11 +714,11 @@ __device__ __forceinline__ float group_sum_vec(float v) {
     return v;
 }
 
-template <int K, int MODE>
+template <int K, int MODE, bool MS = false>
 __global__ void __launch_bounds__(256) k_var_group(DevGraph G, const int32_t *__restrict__ list, int n,
                                                    const float *__restrict__ ev, const float *__restrict__ m,
                                                    float *__restrict__ out, int32_t *__restrict__ dec) {
-    {  // multi-sample launches: this block's sample
+    if constexpr (MS) {  // multi-sample launches: this block's sample
         const int64_t smp = sample_select(G);
         ev += smp * G.s_vs;
         m += smp * G.s_es;
@@ -850,13 +851,13 @@ __device__ __forceinline__ FF block_sum(FF v, float *sh) {
 // (kVarIter) the block also writes, for every incoming edge-state, the exact
 // leave-one-out sum e_v(x) + sum_{other edges} m(x), as prefix + suffix (no subtraction),
 // to G.v2f_hd as a (hi, lo) pair; the factor kernels read it for these edges.
-template <int MODE>
+template <int MODE, bool MS = false>
 __global__ void __launch_bounds__(kVarBlockThreads) k_var_block(DevGraph G, const int32_t *__restrict__ list,
                                                                 const float *__restrict__ ev,
                                                                 const float *__restrict__ m,
                                                                 float *__restrict__ out,
                                                                 int32_t *__restrict__ dec) {
-    {  // multi-sample launches: this block's sample
+    if constexpr (MS) {  // multi-sample launches: this block's sample
         const int64_t smp = sample_select(G);
         ev += smp * G.s_vs;
         m += smp * G.s_es;
@@ -1095,12 +1096,12 @@ __device__ __noinline__ void pair_factor_rare(const DevGraph G, const float *phi
 }
 
 // Dense pairwise tables (Ising, RBM, Potts): thread per factor.
-template <int K, bool MAXP>
+template <int K, bool MAXP, bool MS = false>
 __global__ void __launch_bounds__(K >= 16 ? 128 : 256, K == 2 ? 8 : 1)
 k_pair(DevGraph G, const EnumSeg *__restrict__ segs, int n_seg, const float *__restrict__ pot,
        const float *__restrict__ b, const float *__restrict__ ev, const float *__restrict__ m_old,
        float *__restrict__ m_new, float T, float invT, float damping) {
-    {  // multi-sample launches: this block's sample
+    if constexpr (MS) {  // multi-sample launches: this block's sample
         const int64_t smp = sample_select(G);
         pot += smp * G.s_pot;
         b += smp * G.s_vs;
@@ -1289,12 +1290,12 @@ __device__ __forceinline__ void group_tables(const float *__restrict__ phi, floa
 // the segments' block ranges); each physical block walks a contiguous range of chunks
 // and rebuilds its shared-memory tables only when the chunk's group changes, so the
 // per-table work is paid once per block rather than once per chunk.
-template <int K, bool MAXP>
+template <int K, bool MAXP, bool MS = false>
 __global__ void __launch_bounds__(256, 4)
 k_pair_group(DevGraph G, const EnumSeg *__restrict__ segs, int n_seg, int n_vblocks, const float *__restrict__ pot,
              const float *__restrict__ b, const float *__restrict__ ev, const float *__restrict__ m_old,
              float *__restrict__ m_new, float T, float invT, float damping) {
-    {  // multi-sample launches: this block's sample
+    if constexpr (MS) {  // multi-sample launches: this block's sample
         const int64_t smp = sample_select(G);
         pot += smp * G.s_pot;
         b += smp * G.s_vs;
@@ -1470,12 +1471,12 @@ __device__ __forceinline__ void pair_dir_thr(float (&v)[K], float (&o)[K], bool 
 // shared memory (with E and E^T for the linear form); per-factor tables are read from
 // the factor's own K*K entries. The rare cases (an edge of a high-degree variable, a
 // stored entry that is -inf or large) go to pair_factor_rare.
-template <int K, bool MAXP>
+template <int K, bool MAXP, bool MS = false>
 __global__ void __launch_bounds__(K >= 16 ? 128 : 256)
 k_pair_thr(DevGraph G, const EnumSeg *__restrict__ segs, int n_seg, const float *__restrict__ pot,
            const float *__restrict__ b, const float *__restrict__ ev, const float *__restrict__ m_old,
            float *__restrict__ m_new, float T, float invT, float damping) {
-    {  // multi-sample launches: this block's sample
+    if constexpr (MS) {  // multi-sample launches: this block's sample
         const int64_t smp = sample_select(G);
         pot += smp * G.s_pot;
         b += smp * G.s_vs;
@@ -1539,13 +1540,13 @@ k_pair_thr(DevGraph G, const EnumSeg *__restrict__ segs, int n_seg, const float 
 // Factor pass: any listed-configuration factor, thread per factor
 // =====================================================================================
 
-template <bool MAXP>
+template <bool MAXP, bool MS = false>
 __global__ void __launch_bounds__(128)
 k_enum_generic(DevGraph G, const EnumSeg *__restrict__ segs, int n_seg, const float *__restrict__ pot,
                const float *__restrict__ b, const float *__restrict__ ev,
                const float *__restrict__ m_old, float *__restrict__ m_new, float T, float invT,
                float damping) {
-    {  // multi-sample launches: this block's sample
+    if constexpr (MS) {  // multi-sample launches: this block's sample
         const int64_t smp = sample_select(G);
         pot += smp * G.s_pot;
         b += smp * G.s_vs;
@@ -1673,12 +1674,12 @@ __device__ __noinline__ void v2f_slow_edge_warp(const DevGraph G, const float *_
     }
 }
 
-template <bool MAXP>
+template <bool MAXP, bool MS = false>
 __global__ void __launch_bounds__(kEnumBlockThreads)
 k_enum_block(DevGraph G, const EnumSeg *__restrict__ segs, int n_seg, const float *__restrict__ pot,
              const float *__restrict__ b, const float *__restrict__ ev, const float *__restrict__ m_old,
              float *__restrict__ m_new, float T, float invT, float damping) {
-    {  // multi-sample launches: this block's sample
+    if constexpr (MS) {  // multi-sample launches: this block's sample
         const int64_t smp = sample_select(G);
         pot += smp * G.s_pot;
         b += smp * G.s_vs;
@@ -1974,12 +1975,12 @@ __device__ __forceinline__ float edge_logodds(const DevGraph &G, const float *ev
 }
 
 // Thread per factor, fan-in <= kLogicSmallFan; leave-one-out sums written out directly.
-template <bool MAXP>
+template <bool MAXP, bool MS = false>
 __global__ void __launch_bounds__(256)
 k_logic_small(DevGraph G, const LogicSeg *__restrict__ segs, int n_seg, const float *__restrict__ b,
               const float *__restrict__ ev, const float *__restrict__ m_old,
               float *__restrict__ m_new, float T, float invT, float damping) {
-    {  // multi-sample launches: this block's sample
+    if constexpr (MS) {  // multi-sample launches: this block's sample
         const int64_t smp = sample_select(G);
         b += smp * G.s_vs;
         ev += smp * G.s_vs;
@@ -2089,12 +2090,12 @@ __device__ __forceinline__ ScanEl shfl_el(ScanEl v, int src) {
 // Warp per factor, any fan-in. Leave-one-out sums as exclusive prefix (first pass) and
 // exclusive suffix (second pass) warp scans over rounds of 32 parents; the log-odds
 // and the prefix of each parent are staged in shared memory (3 floats per parent).
-template <bool MAXP>
+template <bool MAXP, bool MS = false>
 __global__ void __launch_bounds__(128)
 k_logic_warp(DevGraph G, const LogicSeg *__restrict__ segs, int n_seg, const float *__restrict__ b,
              const float *__restrict__ ev, const float *__restrict__ m_old,
              float *__restrict__ m_new, float T, float invT, float damping, int cap) {
-    {  // multi-sample launches: this block's sample
+    if constexpr (MS) {  // multi-sample launches: this block's sample
         const int64_t smp = sample_select(G);
         b += smp * G.s_vs;
         ev += smp * G.s_vs;
@@ -3085,41 +3086,45 @@ cudaError_t prepare_kernels(int max_smem_bytes) {
     if ((e = allow((const void *)k_logic_warp<false>)) != cudaSuccess) return e;
     if ((e = allow((const void *)k_enum_block<true>)) != cudaSuccess) return e;
     if ((e = allow((const void *)k_enum_block<false>)) != cudaSuccess) return e;
+    if ((e = allow((const void *)k_logic_warp<true, true>)) != cudaSuccess) return e;
+    if ((e = allow((const void *)k_logic_warp<false, true>)) != cudaSuccess) return e;
+    if ((e = allow((const void *)k_enum_block<true, true>)) != cudaSuccess) return e;
+    if ((e = allow((const void *)k_enum_block<false, true>)) != cudaSuccess) return e;
     if (dev >= 0 && dev < 64) done[dev] = 1;
     return cudaSuccess;
 }
 
-template <int MODE>
+template <int MODE, bool MS>
 static void var_pass_mode(const DevGraph &G, const Plan &P, const float *ev, const float *m,
                           float *out, int32_t *dec, cudaStream_t s, int S) {
     if (G.vin_tab4 != nullptr) {
         const int n = G.V;
-        k_var_tab4<MODE><<<dim3((n + 255) / 256, S), 256, 0, s>>>(G, n, ev, m, out, dec);
+        k_var_tab4<MODE, MS><<<dim3((n + 255) / 256, S), 256, 0, s>>>(G, n, ev, m, out, dec);
         return;
     }
     for (const VarLaunch &L : P.var) {
         if (L.n == 0) continue;
         switch (L.kind) {
             case kVarBlock:
-                k_var_block<MODE><<<dim3(L.n, S), kVarBlockThreads, 0, s>>>(G, L.list, ev, m, out, dec);
+                k_var_block<MODE, MS><<<dim3(L.n, S), kVarBlockThreads, 0, s>>>(G, L.list, ev, m, out, dec);
                 break;
             case kVarBinary:
-                k_var_thread<2, MODE><<<dim3(L.n_blocks, S), L.threads, 0, s>>>(G, L.list, L.n, L.dense_binary, ev, m, out, dec);
+                k_var_thread<2, MODE, MS><<<dim3(L.n_blocks, S), L.threads, 0, s>>>(G, L.list, L.n, L.dense_binary, ev, m, out, dec);
                 break;
             case kVarGroup4:
-                k_var_group<4, MODE><<<dim3(L.n_blocks, S), L.threads, 0, s>>>(G, L.list, L.n, ev, m, out, dec);
+                k_var_group<4, MODE, MS><<<dim3(L.n_blocks, S), L.threads, 0, s>>>(G, L.list, L.n, ev, m, out, dec);
                 break;
             case kVarGroup8:
-                k_var_group<8, MODE><<<dim3(L.n_blocks, S), L.threads, 0, s>>>(G, L.list, L.n, ev, m, out, dec);
+                k_var_group<8, MODE, MS><<<dim3(L.n_blocks, S), L.threads, 0, s>>>(G, L.list, L.n, ev, m, out, dec);
                 break;
             case kVarGroup16:
-                k_var_group<16, MODE><<<dim3(L.n_blocks, S), L.threads, 0, s>>>(G, L.list, L.n, ev, m, out, dec);
+                k_var_group<16, MODE, MS><<<dim3(L.n_blocks, S), L.threads, 0, s>>>(G, L.list, L.n, ev, m, out, dec);
                 break;
             case kVarWarp:
-                k_var_warp<MODE><<<dim3(L.n_blocks, S), L.threads, 0, s>>>(G, L.list, L.n, ev, m, out, dec);
+                k_var_warp<MODE, MS><<<dim3(L.n_blocks, S), L.threads, 0, s>>>(G, L.list, L.n, ev, m, out, dec);
                 break;
             default:
-                k_var_thread<0, MODE><<<dim3(L.n_blocks, S), L.threads, 0, s>>>(G, L.list, L.n, 0, ev, m, out, dec);
+                k_var_thread<0, MODE, MS><<<dim3(L.n_blocks, S), L.threads, 0, s>>>(G, L.list, L.n, 0, ev, m, out, dec);
                 break;
         }
     }
@@ -3127,14 +3132,15 @@ static void var_pass_mode(const DevGraph &G, const Plan &P, const float *ev, con
 
 cudaError_t launch_var_pass(const DevGraph &G, const Plan &P, const float *ev, const float *m,
                             float *b, int mode, int32_t *decode, cudaStream_t s, int S) {
-    if (mode == kVarIter) var_pass_mode<kVarIter>(G, P, ev, m, b, decode, s, S);
-    else if (mode == kVarBeliefs) var_pass_mode<kVarBeliefs>(G, P, ev, m, b, decode, s, S);
-    else if (mode == kVarNormalised) var_pass_mode<kVarNormalised>(G, P, ev, m, b, decode, s, S);
-    else var_pass_mode<kVarDecode>(G, P, ev, m, b, decode, s, S);
+    if (mode == kVarIter && S > 1) var_pass_mode<kVarIter, true>(G, P, ev, m, b, decode, s, S);
+    else if (mode == kVarIter) var_pass_mode<kVarIter, false>(G, P, ev, m, b, decode, s, 1);
+    else if (mode == kVarBeliefs) var_pass_mode<kVarBeliefs, false>(G, P, ev, m, b, decode, s, 1);
+    else if (mode == kVarNormalised) var_pass_mode<kVarNormalised, false>(G, P, ev, m, b, decode, s, 1);
+    else var_pass_mode<kVarDecode, false>(G, P, ev, m, b, decode, s, 1);
     return cudaGetLastError();
 }
 
-template <bool MAXP>
+template <bool MAXP, bool MS>
 static void factor_pass_t(const DevGraph &G, const Plan &P, const float *pot, const float *b,
                           const float *ev, const float *m_old, float *m_new, float T, float damping,
                           cudaStream_t s, int S) {
@@ -3145,37 +3151,37 @@ static void factor_pass_t(const DevGraph &G, const Plan &P, const float *pot, co
         const LogicSeg *ls = static_cast<const LogicSeg *>(L.segs);
         switch (L.variant) {
             case kPair2:
-                k_pair<2, MAXP><<<dim3(L.n_blocks, S), L.threads, 0, s>>>(G, es, L.n_seg, pot, b, ev, m_old, m_new, T, invT, damping);
+                k_pair<2, MAXP, MS><<<dim3(L.n_blocks, S), L.threads, 0, s>>>(G, es, L.n_seg, pot, b, ev, m_old, m_new, T, invT, damping);
                 break;
             case kPair4:
-                k_pair_group<4, MAXP><<<dim3(min(L.n_blocks, L.max_blocks), S), L.threads, 0, s>>>(G, es, L.n_seg, L.n_blocks, pot, b, ev, m_old, m_new, T, invT, damping);
+                k_pair_group<4, MAXP, MS><<<dim3(min(L.n_blocks, L.max_blocks), S), L.threads, 0, s>>>(G, es, L.n_seg, L.n_blocks, pot, b, ev, m_old, m_new, T, invT, damping);
                 break;
             case kPair8:
-                k_pair_group<8, MAXP><<<dim3(min(L.n_blocks, L.max_blocks), S), L.threads, 0, s>>>(G, es, L.n_seg, L.n_blocks, pot, b, ev, m_old, m_new, T, invT, damping);
+                k_pair_group<8, MAXP, MS><<<dim3(min(L.n_blocks, L.max_blocks), S), L.threads, 0, s>>>(G, es, L.n_seg, L.n_blocks, pot, b, ev, m_old, m_new, T, invT, damping);
                 break;
             case kPair16:
-                k_pair_group<16, MAXP><<<dim3(min(L.n_blocks, L.max_blocks), S), L.threads, 0, s>>>(G, es, L.n_seg, L.n_blocks, pot, b, ev, m_old, m_new, T, invT, damping);
+                k_pair_group<16, MAXP, MS><<<dim3(min(L.n_blocks, L.max_blocks), S), L.threads, 0, s>>>(G, es, L.n_seg, L.n_blocks, pot, b, ev, m_old, m_new, T, invT, damping);
                 break;
             case kPairT4:
-                k_pair_thr<4, MAXP><<<dim3(L.n_blocks, S), L.threads, 0, s>>>(G, es, L.n_seg, pot, b, ev, m_old, m_new, T, invT, damping);
+                k_pair_thr<4, MAXP, MS><<<dim3(L.n_blocks, S), L.threads, 0, s>>>(G, es, L.n_seg, pot, b, ev, m_old, m_new, T, invT, damping);
                 break;
             case kPairT8:
-                k_pair_thr<8, MAXP><<<dim3(L.n_blocks, S), L.threads, 0, s>>>(G, es, L.n_seg, pot, b, ev, m_old, m_new, T, invT, damping);
+                k_pair_thr<8, MAXP, MS><<<dim3(L.n_blocks, S), L.threads, 0, s>>>(G, es, L.n_seg, pot, b, ev, m_old, m_new, T, invT, damping);
                 break;
             case kPairT16:
-                k_pair_thr<16, MAXP><<<dim3(L.n_blocks, S), L.threads, 0, s>>>(G, es, L.n_seg, pot, b, ev, m_old, m_new, T, invT, damping);
+                k_pair_thr<16, MAXP, MS><<<dim3(L.n_blocks, S), L.threads, 0, s>>>(G, es, L.n_seg, pot, b, ev, m_old, m_new, T, invT, damping);
                 break;
             case kEnumGeneric:
-                k_enum_generic<MAXP><<<dim3(L.n_blocks, S), L.threads, 0, s>>>(G, es, L.n_seg, pot, b, ev, m_old, m_new, T, invT, damping);
+                k_enum_generic<MAXP, MS><<<dim3(L.n_blocks, S), L.threads, 0, s>>>(G, es, L.n_seg, pot, b, ev, m_old, m_new, T, invT, damping);
                 break;
             case kEnumBlock:
-                k_enum_block<MAXP><<<dim3(L.n_blocks, S), L.threads, L.smem, s>>>(G, es, L.n_seg, pot, b, ev, m_old, m_new, T, invT, damping);
+                k_enum_block<MAXP, MS><<<dim3(L.n_blocks, S), L.threads, L.smem, s>>>(G, es, L.n_seg, pot, b, ev, m_old, m_new, T, invT, damping);
                 break;
             case kLogicSmall:
-                k_logic_small<MAXP><<<dim3(L.n_blocks, S), L.threads, 0, s>>>(G, ls, L.n_seg, b, ev, m_old, m_new, T, invT, damping);
+                k_logic_small<MAXP, MS><<<dim3(L.n_blocks, S), L.threads, 0, s>>>(G, ls, L.n_seg, b, ev, m_old, m_new, T, invT, damping);
                 break;
             case kLogicWarp:
-                k_logic_warp<MAXP><<<dim3(L.n_blocks, S), L.threads, L.smem, s>>>(G, ls, L.n_seg, b, ev, m_old, m_new, T, invT, damping, L.max_fan);
+                k_logic_warp<MAXP, MS><<<dim3(L.n_blocks, S), L.threads, L.smem, s>>>(G, ls, L.n_seg, b, ev, m_old, m_new, T, invT, damping, L.max_fan);
                 break;
             default:
                 break;
@@ -3352,8 +3358,13 @@ cudaError_t launch_lr_unpack(const DevGraph &G, const float *d, float *m, cudaSt
 cudaError_t launch_factor_pass(const DevGraph &G, const Plan &P, const float *log_pot,
                                const float *b, const float *ev, const float *m_old,
                                float *m_new, float T, float damping, cudaStream_t s, int S) {
-    if (T == 0.f) factor_pass_t<true>(G, P, log_pot, b, ev, m_old, m_new, T, damping, s, S);
-    else factor_pass_t<false>(G, P, log_pot, b, ev, m_old, m_new, T, damping, s, S);
+    if (S > 1) {  // the multi-sample instantiations
+        if (T == 0.f) factor_pass_t<true, true>(G, P, log_pot, b, ev, m_old, m_new, T, damping, s, S);
+        else factor_pass_t<false, true>(G, P, log_pot, b, ev, m_old, m_new, T, damping, s, S);
+    } else {
+        if (T == 0.f) factor_pass_t<true, false>(G, P, log_pot, b, ev, m_old, m_new, T, damping, s, 1);
+        else factor_pass_t<false, false>(G, P, log_pot, b, ev, m_old, m_new, T, damping, s, 1);
+    }
     return cudaGetLastError();
 }
 
