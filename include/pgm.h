@@ -64,8 +64,7 @@ typedef int32_t pgm_status;
 /* Limits of this build (checked by pgm_build). */
 #define PGM_MAX_STATES 256        /* states per variable */
 #define PGM_MAX_ENUM_ARITY 8      /* neighbours of an enumeration factor */
-#define PGM_MAX_ENUM_STATE_SUM 2048 /* sum of K over one enumeration factor's neighbours
-                                      (above 64: pgm_grad returns PGM_ENOTSUP) */
+#define PGM_MAX_ENUM_STATE_SUM 2048 /* sum of K over one enumeration factor's neighbours */
 #define PGM_MAX_ENUM_LIST 1073741824 /* n_cfg * arity of one enumeration group */
 
 typedef struct pgm_graph pgm_graph;
@@ -250,7 +249,9 @@ pgm_status pgm_pass_times(pgm_graph *g, double *var_ms, double *factor_ms, int64
  * replayed on the caller's stream; with it off, the scratch is a stream-ordered
  * allocation freed before the call's work ends.
  * Gradients of log-potentials shared by a group are summed over its factors in
- * arbitrary order (atomic adds); everything else is deterministic.
+ * arbitrary order (atomic adds), and for factors with a state sum above 64 (computed
+ * in the block form, a warp or block per factor) so are those of per-factor tables and
+ * of the variable-to-factor values; everything else is deterministic.
  * Errors: PGM_ENOTSUP for T = 0 (max-product is not differentiable) or graphs with
  * logical factors; PGM_EINVAL for a non-finite or negative T, damping outside [0, 1),
  * n_iters < 0, ckpt_every < 1, NULL pointers.

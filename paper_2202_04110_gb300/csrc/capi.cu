@@ -110,11 +110,12 @@ struct pgm_graph {
     int64_t prof_var_launches = 0, prof_factor_launches = 0;
     int32_t var_launches = 0, factor_launches = 0;
     std::vector<HostMember> members;
-    FactorLaunch adj_launch{};      // pgm_grad: every enumeration group, thread per factor
+    FactorLaunch adj_launch{};      // pgm_grad: enumeration groups of state sum <= 64, thread per factor
     size_t adj_seg_off = (size_t)-1;
+    FactorLaunch adj_block_launch{};  // pgm_grad: the larger groups, block form (k_adj_block)
+    size_t adj_block_seg_off = (size_t)-1;
     bool has_logic = false;
-    bool has_large_enum = false;
-    int32_t enum_block = 0;       // PGM_OPT_ENUM_BLOCK  // an enumeration group with a state sum above kMaxStateSum
+    int32_t enum_block = 0;  // PGM_OPT_ENUM_BLOCK
     std::vector<std::vector<char>> factor_segs_host;  // host copy of each factor launch's segments
     // CUDA graphs of whole pgm_run_bp calls, keyed by their arguments (LRU)
     struct CachedRun {
@@ -254,12 +255,17 @@ pgm_status build_plan(const HostLayout &H, pgm_graph *g, Packer &pk, std::vector
         seg_off.push_back(H.var_bucket_identity[kind] ? (size_t)-1 : pk.add(bucket.data(), bucket.size()));
         seg_kind.push_back(-1);
     }
-    // adjoint factor launch: every enumeration group, thread per factor
+    // adjoint factor launches: enumeration groups with a state sum up to kMaxStateSum,
+    // thread per factor; larger ones in the team layout of the block form
     {
-        std::vector<EnumSeg> segs;
+        std::vector<EnumSeg> segs, bsegs;
         int32_t blk = 0;
         for (const HostEnumGroup &hg : H.enum_groups) {
             EnumSeg s = hg.seg;
+            if (s.es_per_fac > kMaxStateSum) {
+                bsegs.push_back(s);
+                continue;
+            }
             s.block_begin = blk;
             blk += (s.n_fac + 127) / 128;
             segs.push_back(s);
@@ -270,8 +276,21 @@ pgm_status build_plan(const HostLayout &H, pgm_graph *g, Packer &pk, std::vector
         g->adj_launch.n_blocks = blk;
         g->adj_launch.threads = 128;
         g->adj_seg_off = segs.empty() ? (size_t)-1 : pk.add(segs.data(), segs.size());
+        g->adj_block_launch = FactorLaunch{};
+        g->adj_block_launch.variant = kEnumBlock;
+        if (!bsegs.empty()) {
+            int32_t unused = 0;
+            g->adj_block_launch.n_blocks =
+                plan_enum_block(bsegs.data(), (int)bsegs.size(), kEnumBlockThreads, g->n_sm, false, &unused);
+            int32_t sm = 0;  // four state-sum arrays per team
+            for (const EnumSeg &sg : bsegs)
+                sm = std::max(sm, 16 * sg.es_per_fac * (sg.es_per_fac <= kEnumWarpStateSum ? kEnumBlockThreads / 32 : 1));
+            g->adj_block_launch.smem = sm;
+            g->adj_block_launch.n_seg = (int32_t)bsegs.size();
+            g->adj_block_launch.threads = kEnumBlockThreads;
+            g->adj_block_seg_off = pk.add(bsegs.data(), bsegs.size());
+        }
         g->has_logic = !H.logic_groups.empty();
-        for (const HostEnumGroup &hg : H.enum_groups) g->has_large_enum |= hg.seg.es_per_fac > kMaxStateSum;
     }
     // factor pass: one launch per variant, all groups of that variant as segments
     for (int variant = 0; variant < kNumFactorVariants; ++variant) {
@@ -528,6 +547,7 @@ static pgm_status build_from_descs(const void *const *descs, int n, pgm_graph **
         }
     }
     if (g->adj_seg_off != (size_t)-1) g->adj_launch.segs = dmem + g->adj_seg_off;
+    if (g->adj_block_seg_off != (size_t)-1) g->adj_block_launch.segs = dmem + g->adj_block_seg_off;
     ce = prepare_kernels(max_smem);
     if (ce != cudaSuccess) {
         pgm_free(g);
@@ -1618,6 +1638,9 @@ static pgm_status enqueue_grad(pgm_graph *g, const float *log_pot, const float *
             if (e == cudaSuccess)
                 e = launch_adj_factor(g->G, g->adj_launch, log_pot, g->b, evidence, m_prev, adjA, dv, ddamp,
                                       d_log_pot, T, damping, s);
+            if (e == cudaSuccess)
+                e = launch_adj_factor(g->G, g->adj_block_launch, log_pot, g->b, evidence, m_prev, adjA, dv, ddamp,
+                                      d_log_pot, T, damping, s);
             if (e == cudaSuccess) e = launch_adj_var(g->G, ddamp, dv, adjB, d_evidence, s);
             if (e != cudaSuccess) st = cuda_fail(e, "adjoint step launch");
             std::swap(adjA, adjB);
@@ -1638,8 +1661,6 @@ pgm_status pgm_grad(pgm_graph *g, const float *log_pot, const float *evidence, f
     if (!(T > 0.f) || !std::isfinite(T))
         return fail(T == 0.f ? PGM_ENOTSUP : PGM_EINVAL, "pgm_grad needs a finite T > 0 (max-product has no gradient)");
     if (g->has_logic) return fail(PGM_ENOTSUP, "pgm_grad supports enumeration factors only");
-    if (g->has_large_enum)
-        return fail(PGM_ENOTSUP, "pgm_grad supports enumeration factors with a state sum of at most 64");
     if (!(damping >= 0.f && damping < 1.f)) return fail(PGM_EINVAL, "damping must be in [0, 1)");
     if (n_iters < 0 || ckpt_every < 1) return fail(PGM_EINVAL, "n_iters >= 0 and ckpt_every >= 1 required");
     if (!evidence || !d_beliefs || !d_evidence || (g->info.n_potentials > 0 && (!log_pot || !d_log_pot)))

@@ -1674,6 +1674,72 @@ __device__ __noinline__ void v2f_slow_edge_warp(const DevGraph G, const float *_
     }
 }
 
+// A barrier over a factor's team: the warp, or the whole block.
+__device__ __forceinline__ void team_barrier(bool wteam) {
+    if (wteam) __syncwarp();
+    else __syncthreads();
+}
+
+// Step (1) of the team kernels (k_enum_block, k_adj_block): the factor's variable-to-factor
+// values into v2f[ksum] (and its stored messages into smo[ksum] if not null), as
+// k_enum_generic forms them: b - m by a thread per edge-state (plus the belief residual
+// for variables of more than 16 states); an edge with an entry that needs the explicit
+// leave-one-out sums, or of a high-degree variable, is then redone by a warp. fix[a]:
+// the team's flags. Ends with a team barrier.
+__device__ __forceinline__ void enum_team_v2f(const DevGraph &G, const float *__restrict__ b,
+                                              const float *__restrict__ ev, const float *__restrict__ m_old,
+                                              int e_f, int es_f, int a, int ksum, const int *sK, const int *sKo,
+                                              float *v2f, float *smo, int *fix, bool wteam, int trank, int tsize,
+                                              int ej0, int ejs, int lane) {
+    if (trank < a) fix[trank] = 0;
+    team_barrier(wteam);
+    for (int t = trank; t < ksum; t += tsize) {
+        int j = 0;
+        for (int k = 1; k < a; ++k)
+            if (t >= sKo[k]) j = k;
+        const int vs = __ldg(G.edge_vs + e_f + j);
+        const float mo = __ldg(m_old + es_f + t);
+        if (smo) smo[t] = mo;
+        const bool lo = G.b_lo != nullptr && sK[j] > 16;  // (as in k_enum_generic)
+        if (vs < 0 || (lo ? !isfinite(mo) : needs_exact(mo))) fix[j] = 1;  // benign race: all write 1
+        else if (lo) v2f[t] = (__ldg(b + vs + t - sKo[j]) - mo) + __ldg(G.b_lo + vs + t - sKo[j]);
+        else v2f[t] = __ldg(b + vs + t - sKo[j]) - mo;
+    }
+    team_barrier(wteam);
+    for (int j = ej0; j < a; j += ejs) {
+        if (!fix[j]) continue;  // warp-uniform
+        const int vs = __ldg(G.edge_vs + e_f + j), es = es_f + sKo[j], K = sK[j];
+        float *vj = v2f + sKo[j];
+        if (vs >= 0) {
+            v2f_slow_edge_warp(G, ev, m_old, __ldg(G.edge_var + e_f + j), vs, es, K, vj, lane);
+            continue;
+        }
+        // the largest state (first of equals), then every state relative to it
+        float2 hmx = make_float2(-CUDART_INF_F, 0.f);
+        int hx = K;
+        for (int x = lane; x < K; x += 32) {
+            const float2 q = hd_pair(G, es, x);
+            if (hx == K || hd_gt(q, hmx)) {
+                hmx = q;
+                hx = x;
+            }
+        }
+        for (int d = 16; d > 0; d >>= 1) {
+            const float2 q = make_float2(__shfl_xor_sync(0xffffffffu, hmx.x, d),
+                                         __shfl_xor_sync(0xffffffffu, hmx.y, d));
+            const int qx = __shfl_xor_sync(0xffffffffu, hx, d);
+            const bool take = qx < K && (hx == K || hd_gt(q, hmx) || (!hd_gt(hmx, q) && qx < hx));
+            if (take) {
+                hmx = q;
+                hx = qx;
+            }
+        }
+        for (int x = lane; x < K; x += 32)
+            vj[x] = hmx.x == -CUDART_INF_F ? -CUDART_INF_F : hd_rel(hd_pair(G, es, x), hmx);
+    }
+    team_barrier(wteam);
+}
+
 template <bool MAXP, bool MS = false>
 __global__ void __launch_bounds__(kEnumBlockThreads)
 k_enum_block(DevGraph G, const EnumSeg *__restrict__ segs, int n_seg, const float *__restrict__ pot,
@@ -1736,64 +1802,15 @@ k_enum_block(DevGraph G, const EnumSeg *__restrict__ segs, int n_seg, const floa
         bs = tbs;
     }
     __syncthreads();  // the last block-wide barrier when teams are warps
-    auto team_sync = [&]() {
-        if (wteam) __syncwarp();
-        else __syncthreads();
-    };
     const int ng = tsize / L, gi = trank / L, gl = trank - gi * L;
     const int32_t *lst = bs + ob;
     const float w = 1.f - damping;
     for (int f = f0 + team; f < f1; f += n_teams) {
         const int es_f = __ldg(&S->es_base) + f * ksum;
         const int e_f = __ldg(&S->edge_base) + f * a;
-        // (1) variable-to-factor values (as in k_enum_generic)
-        if (trank < a) s_fix[team][trank] = 0;
-        team_sync();
-        for (int t = trank; t < ksum; t += tsize) {
-            int j = 0;
-            for (int k = 1; k < a; ++k)
-                if (t >= sKo[k]) j = k;
-            const int vs = __ldg(G.edge_vs + e_f + j);
-            const float mo = __ldg(m_old + es_f + t);
-            smo[t] = mo;
-            const bool lo = G.b_lo != nullptr && sK[j] > 16;  // (as in k_enum_generic)
-            if (vs < 0 || (lo ? !isfinite(mo) : needs_exact(mo))) s_fix[team][j] = 1;  // benign race
-            else if (lo) v2f[t] = (__ldg(b + vs + t - sKo[j]) - mo) + __ldg(G.b_lo + vs + t - sKo[j]);
-            else v2f[t] = __ldg(b + vs + t - sKo[j]) - mo;
-        }
-        team_sync();
-        for (int j = ej0; j < a; j += ejs) {
-            if (!s_fix[team][j]) continue;  // warp-uniform
-            const int vs = __ldg(G.edge_vs + e_f + j), es = es_f + sKo[j], K = sK[j];
-            float *vj = v2f + sKo[j];
-            if (vs >= 0) {
-                v2f_slow_edge_warp(G, ev, m_old, __ldg(G.edge_var + e_f + j), vs, es, K, vj, lane);
-                continue;
-            }
-            // the largest state (first of equals), then every state relative to it
-            float2 hmx = make_float2(-CUDART_INF_F, 0.f);
-            int hx = K;
-            for (int x = lane; x < K; x += 32) {
-                const float2 q = hd_pair(G, es, x);
-                if (hx == K || hd_gt(q, hmx)) {
-                    hmx = q;
-                    hx = x;
-                }
-            }
-            for (int d = 16; d > 0; d >>= 1) {
-                const float2 q = make_float2(__shfl_xor_sync(0xffffffffu, hmx.x, d),
-                                             __shfl_xor_sync(0xffffffffu, hmx.y, d));
-                const int qx = __shfl_xor_sync(0xffffffffu, hx, d);
-                const bool take = qx < K && (hx == K || hd_gt(q, hmx) || (!hd_gt(hmx, q) && qx < hx));
-                if (take) {
-                    hmx = q;
-                    hx = qx;
-                }
-            }
-            for (int x = lane; x < K; x += 32)
-                vj[x] = hmx.x == -CUDART_INF_F ? -CUDART_INF_F : hd_rel(hd_pair(G, es, x), hmx);
-        }
-        team_sync();
+        // (1) variable-to-factor values
+        enum_team_v2f(G, b, ev, m_old, e_f, es_f, a, ksum, sK, sKo, v2f, smo, s_fix[team], wteam, trank, tsize,
+                      ej0, ejs, lane);
         // (2) every output edge-state over its configurations
         const float *phi = shared ? phi_tab : phi_g + (size_t)f * nc;
         for (int base = 0; base < ksum; base += ng) {
@@ -1889,7 +1906,7 @@ k_enum_block(DevGraph G, const EnumSeg *__restrict__ segs, int n_seg, const floa
             }
             if (o < ksum && gl == 0) out[o] = (MAXP || mx == kNegInf) ? mx : mx + T * logf(sm);
         }
-        team_sync();
+        team_barrier(wteam);
         // (3) normalise, damp, normalise; a warp per edge, up to 8 states per lane
         for (int j = ej0; j < a; j += ejs) {
             const int K = sK[j], es = es_f + sKo[j];
@@ -2349,6 +2366,165 @@ k_adj_factor(DevGraph G, const EnumSeg *__restrict__ segs, int n_seg, const floa
         else dphi[c] += dc;
     }
     for (int i = 0; i < ksum; ++i) dv2f[es_f + i] = dv[i];
+}
+
+// k_adj_factor for listed-configuration groups with a state sum above kMaxStateSum, with
+// the team layout of k_enum_block (a warp per factor up to kEnumWarpStateSum, else the
+// block; fpb factors per block; configuration tables read in place). Per factor: the
+// variable-to-factor values (enum_team_v2f); each output's forward value lm = LSE_T over
+// its configurations (ascending, as k_adj_factor); a warp per edge reverses
+// normalise - damp - normalise into gam and ddamp; each output then walks its
+// configurations again and adds gam e^((s - lm) / T) to the configuration's
+// log-potential gradient (global atomics) and to the other neighbours' variable-to-factor
+// adjoints (shared-memory atomics), which are written to dv2f at the end.
+__global__ void __launch_bounds__(kEnumBlockThreads)
+k_adj_block(DevGraph G, const EnumSeg *__restrict__ segs, int n_seg, const float *__restrict__ pot,
+            const float *__restrict__ b, const float *__restrict__ ev, const float *__restrict__ m_old,
+            const float *__restrict__ adj, float *__restrict__ dv2f, float *__restrict__ ddamp,
+            float *__restrict__ d_pot, float T, float invT, float damping) {
+    extern __shared__ __align__(16) float ab_smem[];
+    __shared__ int sK[kMaxArity], sKo[kMaxArity];
+    __shared__ int s_fix[kEnumBlockThreads / 32][kMaxArity];
+    const EnumSeg *S = segs + find_seg(segs, n_seg, blockIdx.x);
+    const int a = __ldg(&S->arity), nc = __ldg(&S->n_cfg), ksum = __ldg(&S->es_per_fac);
+    const int fpb = __ldg(&S->fpb), n_fac = __ldg(&S->n_fac), shared = __ldg(&S->shared);
+    const int packed = __ldg(&S->packed);
+    const int f0 = (blockIdx.x - __ldg(&S->block_begin)) * fpb;
+    const int f1 = min(n_fac, f0 + fpb);
+    if (threadIdx.x < a) {
+        sK[threadIdx.x] = __ldg(&S->K[threadIdx.x]);
+        sKo[threadIdx.x] = __ldg(&S->Koff[threadIdx.x]);
+    }
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    const bool wteam = ksum <= kEnumWarpStateSum;
+    const int tsize = wteam ? 32 : (int)blockDim.x, trank = wteam ? lane : (int)threadIdx.x;
+    const int team = wteam ? warp : 0, n_teams = wteam ? nw : 1;
+    const int ej0 = wteam ? 0 : warp, ejs = wteam ? 1 : nw;
+    float *v2f = ab_smem + (size_t)team * 4 * ksum, *lm = v2f + ksum, *gam = lm + ksum, *dv = gam + ksum;
+    const uint8_t *cfg = G.cfg_pool + __ldg(&S->cfg_base);
+    const int32_t *bs = G.bs_pool + __ldg(&S->bs_base);
+    const int32_t *lst = bs + ((ksum + 1 + 3) & ~3);
+    const float w1 = (damping != 0.f) ? 1.f - damping : 1.f;
+    for (int f = f0 + team; f < f1; f += n_teams) {
+        const int es_f = __ldg(&S->es_base) + f * ksum;
+        const int e_f = __ldg(&S->edge_base) + f * a;
+        const float *phi = pot + __ldg(&S->pot_base) + (shared ? 0 : (size_t)f * nc);
+        float *dphi = d_pot + __ldg(&S->pot_base) + (shared ? 0 : (size_t)f * nc);
+        enum_team_v2f(G, b, ev, m_old, e_f, es_f, a, ksum, sK, sKo, v2f, nullptr, s_fix[team], wteam, trank, tsize,
+                      ej0, ejs, lane);
+        // the value s of configuration c seen from output o = (j, x): phi + the other
+        // neighbours' variable-to-factor values (for pairwise lists, entry = c << 11 | offset)
+        auto value = [&](int o, int j, int ent, int &c) -> float {
+            if (packed) {
+                c = ent >> 11;
+                return __ldg(phi + c) + v2f[ent & 2047];
+            }
+            c = ent;
+            const uint8_t *cc = cfg + (size_t)c * a;
+            float sv = __ldg(phi + c);
+            for (int k = 0; k < a; ++k)
+                if (k != j) sv += v2f[sKo[k] + __ldg(cc + k)];
+            return sv;
+        };
+        // (2) forward values of the outputs
+        for (int o = trank; o < ksum; o += tsize) {
+            int j = 0;
+            for (int k = 1; k < a; ++k)
+                if (o >= sKo[k]) j = k;
+            float mx = kNegInf, sm = 0.f;
+            for (int i = __ldg(bs + o); i < __ldg(bs + o + 1); ++i) {
+                int c;
+                const float sv = value(o, j, __ldg(lst + i), c);
+                if (sv > mx) {
+                    sm = sm * expf((mx - sv) * invT) + 1.f;
+                    mx = sv;
+                } else if (sv > kNegInf) {
+                    sm += expf((sv - mx) * invT);
+                }
+            }
+            lm[o] = mx == kNegInf ? mx : mx + T * logf(sm);
+            dv[o] = 0.f;
+        }
+        team_barrier(wteam);
+        // (3) reverse of normalise - damp - normalise, a warp per edge
+        for (int j = ej0; j < a; j += ejs) {
+            const int K = sK[j], o = sKo[j], es = es_f + o;
+            float b1 = kNegInf;  // first argmax of lm over the edge
+            int a1 = K;
+            for (int x = lane; x < K; x += 32)
+                if (a1 == K || lm[o + x] > b1) {
+                    b1 = lm[o + x];
+                    a1 = x;
+                }
+            for (int d = 16; d > 0; d >>= 1) {
+                const float qb = __shfl_xor_sync(0xffffffffu, b1, d);
+                const int qa = __shfl_xor_sync(0xffffffffu, a1, d);
+                if (qa < K && (a1 == K || qb > b1 || (!(b1 > qb) && qa < a1))) {
+                    b1 = qb;
+                    a1 = qa;
+                }
+            }
+            const float mx = b1;
+            float b2 = kNegInf, sa = 0.f;  // first argmax of the damped value; sum of adj
+            int a2 = K;
+            for (int x = lane; x < K; x += 32) {
+                const float n = (mx == kNegInf) ? 0.f : lm[o + x] - mx;
+                const float dd = (damping != 0.f) ? damping * __ldg(m_old + es + x) + w1 * n : n;
+                if (a2 == K || dd > b2) {
+                    b2 = dd;
+                    a2 = x;
+                }
+                sa += __ldg(adj + es + x);
+            }
+            for (int d = 16; d > 0; d >>= 1) {
+                const float qb = __shfl_xor_sync(0xffffffffu, b2, d);
+                const int qa = __shfl_xor_sync(0xffffffffu, a2, d);
+                if (qa < K && (a2 == K || qb > b2 || (!(b2 > qb) && qa < a2))) {
+                    b2 = qb;
+                    a2 = qa;
+                }
+                sa += __shfl_xor_sync(0xffffffffu, sa, d);
+            }
+            float sn = 0.f;
+            for (int x = lane; x < K; x += 32) {
+                const float dd = __ldg(adj + es + x) - (x == a2 ? sa : 0.f);
+                ddamp[es + x] = damping * dd;
+                gam[o + x] = w1 * dd;
+                sn += gam[o + x];
+            }
+            for (int d = 16; d > 0; d >>= 1) sn += __shfl_xor_sync(0xffffffffu, sn, d);
+            __syncwarp();
+            if (lane == 0) gam[o + a1] -= sn;
+        }
+        team_barrier(wteam);
+        // (4) back through the log-sum-exp: log-potentials and variable-to-factor values
+        for (int o = trank; o < ksum; o += tsize) {
+            if (lm[o] == kNegInf) continue;
+            int j = 0;
+            for (int k = 1; k < a; ++k)
+                if (o >= sKo[k]) j = k;
+            const float go = gam[o], lo = lm[o];
+            for (int i = __ldg(bs + o); i < __ldg(bs + o + 1); ++i) {
+                const int ent = __ldg(lst + i);
+                int c;
+                const float sv = value(o, j, ent, c);
+                if (sv == kNegInf) continue;
+                const float w = go * expf((sv - lo) * invT);
+                atomicAdd(dphi + c, w);
+                if (packed) {
+                    atomicAdd(dv + (ent & 2047), w);
+                } else {
+                    const uint8_t *cc = cfg + (size_t)c * a;
+                    for (int k = 0; k < a; ++k)
+                        if (k != j) atomicAdd(dv + sKo[k] + __ldg(cc + k), w);
+                }
+            }
+        }
+        team_barrier(wteam);
+        for (int t = trank; t < ksum; t += tsize) dv2f[es_f + t] = dv[t];
+        team_barrier(wteam);  // v2f / lm / dv are reused by the team's next factor
+    }
 }
 
 // Variable step in reverse, thread per variable: db(x) = sum over incoming edges of
@@ -3382,8 +3558,12 @@ cudaError_t launch_adj_factor(const DevGraph &G, const FactorLaunch &L, const fl
                               const float *ev, const float *m_old, const float *adj, float *dv2f, float *ddamp,
                               float *d_pot, float T, float damping, cudaStream_t s) {
     if (L.n_blocks == 0) return cudaSuccess;
-    k_adj_factor<<<L.n_blocks, L.threads, 0, s>>>(G, static_cast<const EnumSeg *>(L.segs), L.n_seg, pot, b, ev,
-                                                  m_old, adj, dv2f, ddamp, d_pot, T, 1.f / T, damping);
+    if (L.variant == kEnumBlock)
+        k_adj_block<<<L.n_blocks, L.threads, L.smem, s>>>(G, static_cast<const EnumSeg *>(L.segs), L.n_seg, pot, b, ev,
+                                                          m_old, adj, dv2f, ddamp, d_pot, T, 1.f / T, damping);
+    else
+        k_adj_factor<<<L.n_blocks, L.threads, 0, s>>>(G, static_cast<const EnumSeg *>(L.segs), L.n_seg, pot, b, ev,
+                                                      m_old, adj, dv2f, ddamp, d_pot, T, 1.f / T, damping);
     return cudaGetLastError();
 }
 

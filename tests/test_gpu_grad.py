@@ -135,3 +135,21 @@ def test_autograd_function(gpu):
     assert torch.equal(lp.grad, d_lp) and torch.equal(ev.grad, d_ev)
     olp, oev = oracle.grad(p.graph, p.log_pot, p.evidence, 1.0, 0.5, 15, g.cpu().numpy())
     _close(lp.grad.cpu().numpy().astype(np.float64), olp, "autograd d log_pot")
+
+
+@pytest.mark.parametrize("shared", [True, False])
+def test_large_factor_gradient_vs_oracle(gpu, shared):
+    """Listed-configuration factors with a state sum above 64 (a pool grid of 49-state
+    variables, 361 listed pairs per factor: the block-form adjoint, packed lists) and an
+    8-ary group over 16-state variables (generic lists), with a few small pairwise
+    factors in the same graph (the thread-per-factor adjoint): T=1, 12 iterations,
+    checkpoint every 5, against the FP64 oracle's adjoint."""
+    a = W.pool_grid(4, 3, 1, 7, T=1.0, shared=shared)
+    b = W.random_enum_factors(8, 40, 16, 8, 6, 1500, shared=shared, scale=0.5)
+    c = W.ising_grid(4, 5, 9, T=1.0)
+    p = W.union([a, b, c])
+    g = np.random.default_rng(13).standard_normal(p.graph.n_var_states)
+    dlp, dev = _gpu_grad(gpu, p.graph, p.log_pot, p.evidence, 1.0, 0.5, 12, 5, g)
+    olp, oev = oracle.grad(p.graph, p.log_pot, p.evidence, 1.0, 0.5, 12, g)
+    _close(dlp, olp, "d log_pot")
+    _close(dev, oev, "d evidence")

@@ -156,11 +156,3 @@ def test_batch_members_bit_identical(gpu):
         _, ma, _, _ = _run(gpu, p, 1.0, 15)
         info = bg.member(k)
         assert np.array_equal(mm[info["es_off"]:info["es_off"] + info["n_edge_states"]], ma)
-
-
-def test_grad_not_supported_on_large_factors(gpu):
-    p = W.pool_grid(3, 3, 1, 1, T=1.0)
-    g = gpu.Graph(p.graph)
-    with pytest.raises(gpu.PgmError) as ei:
-        g.grad(_t(p.log_pot), _t(p.evidence), 1.0, 0.5, 5, 1, _t(np.ones(p.graph.n_var_states)))
-    assert ei.value.status == -4  # PGM_ENOTSUP
