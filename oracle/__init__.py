@@ -203,7 +203,8 @@ def logic_update(kind: int, v2f: np.ndarray, T: float, brute: bool = False) -> n
 
 def grad(graph, log_pot, evidence, T: float, damping: float, n_iters: int, g_nb):
     """Gradient of L = sum(g_nb * normalised log-beliefs) after n_iters iterations from
-    zero messages, w.r.t. (log-potentials, evidence). T > 0, enumeration factors only."""
+    zero messages, w.r.t. (log-potentials, evidence). T > 0; logical factors of fan-in
+    at most 20 (their adjoint enumerates the valid configurations)."""
     lib = _load()
     m = _Marshalled(graph)
     lp = np.ascontiguousarray(log_pot, np.float64)
@@ -216,7 +217,7 @@ def grad(graph, log_pot, evidence, T: float, damping: float, n_iters: int, g_nb)
     rc = lib.og_grad(ctypes.byref(m.g), _ptr(lp), _ptr(ev), float(T), float(damping), int(n_iters),
                      _ptr(gn), _ptr(dlp), _ptr(dev))
     if rc == -2:
-        raise ValueError("oracle grad: logical factors are not supported")
+        raise ValueError("oracle grad: a logical factor has more than 20 parents")
     if rc != 0:
         raise ValueError("oracle grad: invalid T, damping or n_iters")
     return dlp[:graph.n_potentials], dev

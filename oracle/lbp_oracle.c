@@ -569,7 +569,7 @@ static int argmax_k(const double *m, int K) {
  * Gradient of L = sum_v sum_x g[v,x] * nb[v,x], nb = b - LSE_1(b), the normalised
  * log-beliefs after n_iters flooding iterations from zero messages, with respect to the
  * log-potentials and the evidence (the "grad" of Sec. 5.3: LBP inside a differentiable
- * system). T > 0 and enumeration factors only (returns -2 for logical factors).
+ * system). T > 0; logical factors of fan-in at most 20 (returns -2 for larger ones).
  * Reverse-mode chain rule through each forward step, in reverse order:
  *   beliefs   nb = b - LSE(b):         db = g - softmax(b) * sum(g)
  *   b = e + sum m:                     de += db, dm_{g->v} += db
@@ -578,13 +578,19 @@ static int argmax_k(const double *m, int K) {
  *   normalise n = mt - mt[argmax]:     dmt = dn - (sum dn) * onehot(argmax)
  *   factor mt_i(x) = T log sum_{c: c_i = x} exp(s_{-i}(c) / T), s_{-i}(c) = phi(c) + sum_{j != i} v_j(c_j):
  *       with p = exp((s_{-i}(c) - mt_i(c_i)) / T):  dphi(c) += dmt_i(c_i) p,  dv_j(c_j) += dmt_i(c_i) p (j != i)
+ *   logical factor: the same softmax rule over its valid configurations (parents' states
+ *       p, child c = OR(p) or AND(p), log-potential 0), the outgoing 2-vectors taken as
+ *       their enumerated LSE values (logic_brute; the closed form's normalised output
+ *       differs from them by a constant per edge, which the normalisation removes)
  *   leave-one-out v_{f->v} = e_v + sum_{g != f} m_{g->v}:  de += dv,  dm_{g->v} += dv (g != f)
  * All intermediate message states are kept (small graphs).
  */
 int og_grad(const og_graph *g, const double *log_pot, const double *evidence, double T, double damping,
             int n_iters, const double *g_nb, double *d_log_pot, double *d_evidence) {
     if (!(T > 0.0) || damping < 0.0 || damping >= 1.0 || n_iters < 0) return -1;
-    if (g->n_logic > 0) return -2;
+    for (int k = 0; k < g->n_logic; ++k)
+        for (int64_t f = 0; f < g->l_nfac[k]; ++f)
+            if (g->l_paroff[k][f + 1] - g->l_paroff[k][f] > 20) return -2;
     og_layout L;
     layout_build(g, &L);
     const int64_t ES = L.ES, VS = L.VS;
@@ -605,6 +611,12 @@ int og_grad(const og_graph *g, const double *log_pot, const double *evidence, do
         var_to_factor(g, &L, evidence, mo, v2f);
         for (int k = 0; k < g->n_enum; ++k)
             for (int64_t f = 0; f < g->e_nfac[k]; ++f) enum_factor(g, &L, k, f, log_pot, T, v2f, mt, vals);
+        for (int k = 0; k < g->n_logic; ++k)
+            for (int64_t f = 0; f < g->l_nfac[k]; ++f) {
+                const int32_t *po = g->l_paroff[k];
+                int64_t s0 = L.es_off[L.logic_edge0[k] + po[f] + f];
+                logic_closed(g->l_kind[k], po[f + 1] - po[f], v2f + s0, T, mt + s0);
+            }
         for (int64_t e = 0; e < L.E; ++e) {
             int K = (int)(L.es_off[e + 1] - L.es_off[e]);
             damp_normalise(mt + L.es_off[e], mo + L.es_off[e], K, damping, &fl);
@@ -639,6 +651,12 @@ int og_grad(const og_graph *g, const double *log_pot, const double *evidence, do
         var_to_factor(g, &L, evidence, mo, v2f);
         for (int k = 0; k < g->n_enum; ++k)
             for (int64_t f = 0; f < g->e_nfac[k]; ++f) enum_factor(g, &L, k, f, log_pot, T, v2f, mt, vals);
+        for (int k = 0; k < g->n_logic; ++k)
+            for (int64_t f = 0; f < g->l_nfac[k]; ++f) {
+                const int32_t *po = g->l_paroff[k];
+                int64_t s0 = L.es_off[L.logic_edge0[k] + po[f] + f];
+                logic_closed(g->l_kind[k], po[f + 1] - po[f], v2f + s0, T, mt + s0);
+            }
         for (int64_t i = 0; i < ES; ++i) {
             dm_prev[i] = 0.0;
             dv[i] = 0.0;
@@ -686,6 +704,35 @@ int og_grad(const og_graph *g, const double *log_pot, const double *evidence, do
                             if (j != i) dv[L.es_off[e0 + j] + cfg[c * a + j]] += w;
                     }
                 }
+            }
+        }
+        /* logical factors backward: softmax over the valid configurations */
+        for (int k = 0; k < g->n_logic; ++k) {
+            const int32_t *po = g->l_paroff[k];
+            for (int64_t f = 0; f < g->l_nfac[k]; ++f) {
+                int n = po[f + 1] - po[f];
+                int64_t s0 = L.es_off[L.logic_edge0[k] + po[f] + f];
+                double *raw = (double *)malloc(sizeof(double) * (size_t)(2 * (n + 1)));
+                logic_brute(g->l_kind[k], n, v2f + s0, T, raw);
+                for (int64_t p = 0; p < ((int64_t)1 << n); ++p) {
+                    int any = 0, all = 1;
+                    for (int j = 0; j < n; ++j) {
+                        any |= (int)((p >> j) & 1);
+                        all &= (int)((p >> j) & 1);
+                    }
+                    int c = (g->l_kind[k] == OG_OR) ? any : all;
+                    for (int i = 0; i <= n; ++i) {
+                        int xi = (i < n) ? (int)((p >> i) & 1) : c;
+                        double sv = 0.0;
+                        for (int j = 0; j <= n; ++j)
+                            if (j != i) sv += v2f[s0 + 2 * j + ((j < n) ? (int)((p >> j) & 1) : c)];
+                        if (sv == -INFINITY || raw[2 * i + xi] == -INFINITY) continue;
+                        double w = dm[s0 + 2 * i + xi] * exp((sv - raw[2 * i + xi]) / T);
+                        for (int j = 0; j <= n; ++j)
+                            if (j != i) dv[s0 + 2 * j + ((j < n) ? (int)((p >> j) & 1) : c)] += w;
+                    }
+                }
+                free(raw);
             }
         }
         /* leave-one-out backward: v_{f->v} = e_v + sum_{g != f} m_{g->v} */

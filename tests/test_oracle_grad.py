@@ -1,6 +1,6 @@
 """Pins for the oracle's adjoint (gradient of normalised log-beliefs; Sec. 5.3 on using LBP inside differentiable programs):
 central finite differences of the oracle's own pinned forward pass, in FP64, on every
-coordinate of small graphs, plus the shift invariances the gradient must satisfy
+coordinate of small graphs (including logical OR / AND factors), plus the shift invariances the gradient must satisfy
 (normalised beliefs do not change when a constant is added to one variable's evidence or
 to one factor's log-potentials, so those gradients sum to zero)."""
 import numpy as np
@@ -37,6 +37,11 @@ def _cases():
         out.append((f"random{seed}", g, lp, ev))
     p = W.potts_grid(3, 3, 4, T=1.0)
     out.append(("potts3x3K3", p.graph, p.log_pot, p.evidence))
+    # logical OR / AND factors (fan-in 1..4) among pairwise and triple factors (seeds
+    # whose runs have no structural zero: a -inf belief makes the loss undefined)
+    for seed in (4, 5, 9):
+        g, lp, ev = W.random_graph(seed, n_vars=8, max_K=2, n_pair=5, n_triple=1, n_or=2, n_and=2)
+        out.append((f"logic{seed}", g, lp, ev))
     return out
 
 
@@ -71,7 +76,9 @@ def test_grad_shift_invariances(case):
         off += grp.n_potentials
 
 
-def test_grad_rejects_logical_and_max_product():
+def test_grad_rejects_wide_logical_and_max_product():
+    """The oracle's logical adjoint enumerates parent configurations: fan-in above 20
+    (the deconvolution's OR factors reach 180) is refused, as is max-product."""
     p = W.deconvolution(1, n_img=1, n_iters=3)
     with pytest.raises(ValueError):
         oracle.grad(p.graph, p.log_pot, p.evidence, 1.0, 0.5, 3, np.zeros(p.graph.n_var_states))
