@@ -252,8 +252,11 @@ pgm_status pgm_pass_times(pgm_graph *g, double *var_ms, double *factor_ms, int64
  * arbitrary order (atomic adds), and for factors with a state sum above 64 (computed
  * in the block form, a warp or block per factor) so are those of per-factor tables and
  * of the variable-to-factor values; everything else is deterministic.
- * Errors: PGM_ENOTSUP for T = 0 (max-product is not differentiable) or graphs with
- * logical factors; PGM_EINVAL for a non-finite or negative T, damping outside [0, 1),
+ * Logical OR / AND factors are differentiated through their closed forms (linear in the
+ * fan-in); a factor whose incoming log-odds include an infinite one (a hard constraint)
+ * passes no gradient to its variable-to-factor values.
+ * Errors: PGM_ENOTSUP for T = 0 (max-product is not differentiable); PGM_EINVAL for a
+ * non-finite or negative T, damping outside [0, 1),
  * n_iters < 0, ckpt_every < 1, NULL pointers.
  */
 pgm_status pgm_grad(pgm_graph *g, const float *log_pot, const float *evidence, float T, float damping,

@@ -114,7 +114,8 @@ struct pgm_graph {
     size_t adj_seg_off = (size_t)-1;
     FactorLaunch adj_block_launch{};  // pgm_grad: the larger groups, block form (k_adj_block)
     size_t adj_block_seg_off = (size_t)-1;
-    bool has_logic = false;
+    FactorLaunch adj_logic_launch{};  // pgm_grad: logical groups, thread per factor (k_adj_logic)
+    size_t adj_logic_seg_off = (size_t)-1;
     int32_t enum_block = 0;  // PGM_OPT_ENUM_BLOCK
     std::vector<std::vector<char>> factor_segs_host;  // host copy of each factor launch's segments
     // CUDA graphs of whole pgm_run_bp calls, keyed by their arguments (LRU)
@@ -290,7 +291,21 @@ pgm_status build_plan(const HostLayout &H, pgm_graph *g, Packer &pk, std::vector
             g->adj_block_launch.threads = kEnumBlockThreads;
             g->adj_block_seg_off = pk.add(bsegs.data(), bsegs.size());
         }
-        g->has_logic = !H.logic_groups.empty();
+        // logical groups: thread per factor
+        std::vector<LogicSeg> lsegs;
+        int32_t lblk = 0;
+        for (const HostLogicGroup &hg : H.logic_groups) {
+            LogicSeg ls = hg.seg;
+            ls.block_begin = lblk;
+            lblk += (ls.n_fac + 127) / 128;
+            lsegs.push_back(ls);
+        }
+        g->adj_logic_launch = FactorLaunch{};
+        g->adj_logic_launch.variant = kLogicSmall;
+        g->adj_logic_launch.n_seg = (int32_t)lsegs.size();
+        g->adj_logic_launch.n_blocks = lblk;
+        g->adj_logic_launch.threads = 128;
+        g->adj_logic_seg_off = lsegs.empty() ? (size_t)-1 : pk.add(lsegs.data(), lsegs.size());
     }
     // factor pass: one launch per variant, all groups of that variant as segments
     for (int variant = 0; variant < kNumFactorVariants; ++variant) {
@@ -548,6 +563,7 @@ static pgm_status build_from_descs(const void *const *descs, int n, pgm_graph **
     }
     if (g->adj_seg_off != (size_t)-1) g->adj_launch.segs = dmem + g->adj_seg_off;
     if (g->adj_block_seg_off != (size_t)-1) g->adj_block_launch.segs = dmem + g->adj_block_seg_off;
+    if (g->adj_logic_seg_off != (size_t)-1) g->adj_logic_launch.segs = dmem + g->adj_logic_seg_off;
     ce = prepare_kernels(max_smem);
     if (ce != cudaSuccess) {
         pgm_free(g);
@@ -1641,6 +1657,8 @@ static pgm_status enqueue_grad(pgm_graph *g, const float *log_pot, const float *
             if (e == cudaSuccess)
                 e = launch_adj_factor(g->G, g->adj_block_launch, log_pot, g->b, evidence, m_prev, adjA, dv, ddamp,
                                       d_log_pot, T, damping, s);
+            if (e == cudaSuccess)
+                e = launch_adj_logic(g->G, g->adj_logic_launch, g->b, evidence, m_prev, adjA, dv, ddamp, T, damping, s);
             if (e == cudaSuccess) e = launch_adj_var(g->G, ddamp, dv, adjB, d_evidence, s);
             if (e != cudaSuccess) st = cuda_fail(e, "adjoint step launch");
             std::swap(adjA, adjB);
@@ -1660,7 +1678,6 @@ pgm_status pgm_grad(pgm_graph *g, const float *log_pot, const float *evidence, f
     if (!g) return fail(PGM_EINVAL, "graph is NULL");
     if (!(T > 0.f) || !std::isfinite(T))
         return fail(T == 0.f ? PGM_ENOTSUP : PGM_EINVAL, "pgm_grad needs a finite T > 0 (max-product has no gradient)");
-    if (g->has_logic) return fail(PGM_ENOTSUP, "pgm_grad supports enumeration factors only");
     if (!(damping >= 0.f && damping < 1.f)) return fail(PGM_EINVAL, "damping must be in [0, 1)");
     if (n_iters < 0 || ckpt_every < 1) return fail(PGM_EINVAL, "n_iters >= 0 and ckpt_every >= 1 required");
     if (!evidence || !d_beliefs || !d_evidence || (g->info.n_potentials > 0 && (!log_pot || !d_log_pot)))

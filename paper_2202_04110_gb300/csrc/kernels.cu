@@ -2527,6 +2527,135 @@ k_adj_block(DevGraph G, const EnumSeg *__restrict__ segs, int n_seg, const float
     }
 }
 
+// Reverse of write_logic_edge (t = [-o, 0] or [0, o], then normalise - damp - normalise)
+// for one binary edge: mo the old message, ad the adjoint of the new one; writes the
+// damping term to ddamp_es[2] and returns the adjoint of o.
+__device__ __forceinline__ double logic_edge_reverse(float o, float2 mo, float2 ad, float damping, float *ddamp_es) {
+    const float t0 = o >= 0.f ? -o : 0.f, t1 = o >= 0.f ? 0.f : o;
+    const int a1 = (t1 > t0) ? 1 : 0;  // first argmax
+    const float tm = a1 ? t1 : t0;
+    const float w1 = (damping != 0.f) ? 1.f - damping : 1.f;
+    const float d0 = (damping != 0.f) ? damping * mo.x + w1 * (t0 - tm) : t0 - tm;
+    const float d1 = (damping != 0.f) ? damping * mo.y + w1 * (t1 - tm) : t1 - tm;
+    const int a2 = (d1 > d0) ? 1 : 0;
+    const float sa = ad.x + ad.y;
+    const float dd0 = ad.x - (a2 == 0 ? sa : 0.f), dd1 = ad.y - (a2 == 1 ? sa : 0.f);
+    ddamp_es[0] = damping * dd0;
+    ddamp_es[1] = damping * dd1;
+    float g0 = w1 * dd0, g1 = w1 * dd1;
+    const float sn = g0 + g1;
+    if (a1 == 0) g0 -= sn;
+    else g1 -= sn;
+    return o >= 0.f ? -(double)g0 : (double)g1;
+}
+
+// Adjoint of the logical OR / AND update (T > 0), thread per factor, in the OR frame
+// (AND: inputs and outputs negated). With s_j = sp_T(x_j), A = sum_j s_j, A_-i = A - s_i,
+// q = A_-i / T, D_i = log(expm1(q) + e^(-x_c / T)) and cotangents g_i (to parent i) and
+// g_c (to the child) on the outgoing log-odds:
+//   d out_i / d x_c = e^(-x_c / T - D_i),
+//   d out_i / d A_-i = 1 - e^(q - D_i) = expm1(-x_c / T) e^(-D_i),
+//   d out_c / d A = L'(A) = e^(A / T) / expm1(A / T),   d s_j / d x_j = sigmoid(x_j / T),
+// so dx_c = sum_i g_i e^(-x_c/T - D_i) and dx_j = sigmoid(x_j / T) (g_c L'(A) + H - h_j),
+// h_i = g_i d out_i / d A_-i, H = sum_i h_i: linear in the fan-in. The damping term of
+// every edge is written as for enumeration factors; a factor with an infinite log-odds
+// passes no gradient to its variable-to-factor values.
+__global__ void __launch_bounds__(128)
+k_adj_logic(DevGraph G, const LogicSeg *__restrict__ segs, int n_seg, const float *__restrict__ b,
+            const float *__restrict__ ev, const float *__restrict__ m_old, const float *__restrict__ adj,
+            float *__restrict__ dv2f, float *__restrict__ ddamp, float T, float damping) {
+    const LogicSeg *S = segs + find_seg(segs, n_seg, blockIdx.x);
+    const int f = (blockIdx.x - __ldg(&S->block_begin)) * blockDim.x + threadIdx.x;
+    if (f >= __ldg(&S->n_fac)) return;
+    const int *po = G.paroff_pool + __ldg(&S->paroff_base);
+    const int p0 = __ldg(po + f), n = __ldg(po + f + 1) - p0;
+    const int edge_base = __ldg(&S->edge_base), es_base = __ldg(&S->es_base);
+    const int e0 = edge_base + p0 + f;
+    auto es_of = [&](int k) { return es_base + 2 * (e0 + k - edge_base); };
+    const float sgn = __ldg(&S->kind) == 1 ? -1.f : 1.f;
+    const double Td = T, invT = 1.0 / Td;
+    auto t_of = [&](float x) { return x == kNegInf ? -CUDART_INF : log_softplus_d((double)x * invT); };
+    auto adj2 = [&](int es) { return make_float2(__ldg(adj + es), __ldg(adj + es + 1)); };
+    // pass 0: child log-odds, log of A / T
+    float2 moc;
+    const float xc = edge_logodds(G, ev, b, m_old, e0 + n, es_of(n), sgn, moc);
+    bool finite = isfinite(xc);
+    double la = -CUDART_INF;
+    for (int k = 0; k < n; ++k) {
+        float2 mo;
+        const float x = edge_logodds(G, ev, b, m_old, e0 + k, es_of(k), sgn, mo);
+        finite &= isfinite(x);
+        la = lse2_d(la, t_of(x));
+    }
+    const double lm1 = log_expm1_from_log_d(la);
+    // the child edge
+    const double gc = sgn * logic_edge_reverse(sgn * (float)(Td * lm1), moc, adj2(es_of(n)), damping,
+                                               ddamp + es_of(n));
+    finite &= n > 0 && la != -CUDART_INF;
+    const double lc = -(double)xc * invT;
+    // pass 1: each parent's output and damping term; dx_c; h_i (kept in FP64 in the
+    // parent's two dv2f words meanwhile). h_i grows like 1 / q when the other parents are
+    // off, so the largest h is kept apart (hm, index km) from the sum of the others (Hx),
+    // and H - h_j never subtracts it.
+    double dxc = 0.0, Hx = 0.0, hm = 0.0;
+    int km = -1;
+    for (int i = 0; i < n; ++i) {
+        float2 mo;
+        const float xi = edge_logodds(G, ev, b, m_old, e0 + i, es_of(i), sgn, mo);
+        const double ti = t_of(xi);
+        double li;  // log(A_-i / T)
+        if (ti == -CUDART_INF) {
+            li = la;
+        } else if (ti - la < -0.7) {
+            li = la + log(-expm1(ti - la));
+        } else {  // parent i carries most of A: the explicit leave-one-out sum
+            li = -CUDART_INF;
+            for (int j = 0; j < n; ++j) {
+                if (j == i) continue;
+                float2 mj;
+                li = lse2_d(li, t_of(edge_logodds(G, ev, b, m_old, e0 + j, es_of(j), sgn, mj)));
+            }
+        }
+        const double gi = sgn * logic_edge_reverse(sgn * or_parent_soft(li, xc, Td), mo, adj2(es_of(i)), damping,
+                                                   ddamp + es_of(i));
+        double hi = 0.0;
+        if (finite) {
+            const double D = lse2_d(log_expm1_from_log_d(li), lc);
+            dxc += gi * exp(lc - D);
+            hi = gi * expm1(lc) * exp(-D);
+            if (km < 0 || fabs(hi) > fabs(hm)) {
+                if (km >= 0) Hx += hm;
+                hm = hi;
+                km = i;
+            } else {
+                Hx += hi;
+            }
+        }
+        reinterpret_cast<double *>(dv2f + es_of(i))[0] = hi;  // (es_of is even: 8-byte aligned)
+    }
+    if (!finite) {
+        for (int k = 0; k <= n; ++k) {
+            dv2f[es_of(k)] = 0.f;
+            dv2f[es_of(k) + 1] = 0.f;
+        }
+        return;
+    }
+    // pass 2: the parents' adjoints, then the child's (x = sgn (a1 - a0))
+    const double cA = gc * exp(exp(la) - lm1);  // g_c L'(A)
+    for (int j = 0; j < n; ++j) {
+        float2 mo;
+        const float xj = edge_logodds(G, ev, b, m_old, e0 + j, es_of(j), sgn, mo);
+        const double sj = 1.0 / (1.0 + exp(-(double)xj * invT));
+        const double hj = reinterpret_cast<const double *>(dv2f + es_of(j))[0];
+        const double Hj = (j == km) ? Hx : hm + (Hx - hj);  // H - h_j
+        const double dxj = sj * (cA + Hj);
+        dv2f[es_of(j)] = (float)(-sgn * dxj);
+        dv2f[es_of(j) + 1] = (float)(sgn * dxj);
+    }
+    dv2f[es_of(n)] = (float)(-sgn * dxc);
+    dv2f[es_of(n) + 1] = (float)(sgn * dxc);
+}
+
 // Variable step in reverse, thread per variable: db(x) = sum over incoming edges of
 // dv2f(x); d_evidence += db; adjoint of message m_{t-1} on each incoming edge =
 // ddamp - dv2f + db (ddamp: the damping term from k_adj_factor).
@@ -3564,6 +3693,15 @@ cudaError_t launch_adj_factor(const DevGraph &G, const FactorLaunch &L, const fl
     else
         k_adj_factor<<<L.n_blocks, L.threads, 0, s>>>(G, static_cast<const EnumSeg *>(L.segs), L.n_seg, pot, b, ev,
                                                       m_old, adj, dv2f, ddamp, d_pot, T, 1.f / T, damping);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adj_logic(const DevGraph &G, const FactorLaunch &L, const float *b, const float *ev,
+                             const float *m_old, const float *adj, float *dv2f, float *ddamp, float T, float damping,
+                             cudaStream_t s) {
+    if (L.n_blocks == 0) return cudaSuccess;
+    k_adj_logic<<<L.n_blocks, L.threads, 0, s>>>(G, static_cast<const LogicSeg *>(L.segs), L.n_seg, b, ev, m_old, adj,
+                                                 dv2f, ddamp, T, damping);
     return cudaGetLastError();
 }
 

@@ -265,6 +265,9 @@ cudaError_t launch_adj_beliefs(const DevGraph &G, const float *ev, const float *
 cudaError_t launch_adj_factor(const DevGraph &G, const FactorLaunch &L, const float *pot, const float *b,
                               const float *ev, const float *m_old, const float *adj, float *dv2f, float *ddamp,
                               float *d_pot, float T, float damping, cudaStream_t s);
+cudaError_t launch_adj_logic(const DevGraph &G, const FactorLaunch &L, const float *b, const float *ev,
+                             const float *m_old, const float *adj, float *dv2f, float *ddamp, float T, float damping,
+                             cudaStream_t s);
 cudaError_t launch_adj_var(const DevGraph &G, const float *ddamp, const float *dv2f, float *adj_prev, float *d_ev,
                            cudaStream_t s);
 // Configure kernel attributes (large dynamic shared memory) once per process/device.
