@@ -155,3 +155,19 @@ def test_early_exit_requests_equal_alone(gpu, slots):
             srv2.submit(p.graph, p.log_pot, p.evidence, 1.0, 0.5, 10, tol=1e-3, check_every=0)
         finally:
             srv2.close()
+
+
+def test_large_factor_requests_equal_alone(gpu):
+    """Requests with large listed-configuration factors (pool grids of 49 and 121 states:
+    the block-form factor kernel, the warp variable pass and its belief residuals) served
+    alongside Ising grids: each result equals the request run alone."""
+    reqs = [(W.pool_grid(6, 3, 1, 31, T=0.0), 0.0, 20), (W.ising_grid(20, 25, 32), 1.0, 30),
+            (W.pool_grid(4, 5, 2, 33, T=1.0), 1.0, 15), (W.pool_grid(5, 3, 1, 34, T=1.0, shared=False), 1.0, 12)]
+    srv = gpu.Server(memory_budget_bytes=256 << 20, max_in_flight=3)
+    ids = [srv.submit(p.graph, p.log_pot, p.evidence, T, 0.5, it) for p, T, it in reqs]
+    results = [srv.wait(i, 120.0) for i in ids]
+    srv.close()
+    for (p, T, it), (bel, dec, _) in zip(reqs, results):
+        b1, d1 = _alone(gpu, p, T, it)
+        np.testing.assert_array_equal(bel, b1, err_msg=p.name)
+        np.testing.assert_array_equal(dec, d1, err_msg=p.name)

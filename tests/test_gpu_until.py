@@ -114,6 +114,7 @@ def _members():
           W.potts_grid(12, 8, 4, T=1.0), W.rbm(12, 9, 5, T=1.0)]
     g, lp, ev = W.random_graph(6, n_vars=12, max_K=3, n_pair=14, n_triple=2)
     ms.append(W.Problem("random", g, lp, ev, 1.0, 0.5, 10))
+    ms.append(W.pool_grid(5, 3, 1, 8, T=1.0))  # block-form factors, warp variable pass
     return ms
 
 
