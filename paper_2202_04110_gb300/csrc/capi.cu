@@ -207,7 +207,7 @@ bool lr_eligible(const HostLayout &H) {
 int64_t lr_slot_count(const HostLayout &H) { return H.vin_tab4.empty() ? H.E : 4 * H.V; }
 
 // Block-per-factor enumeration launch (kEnumBlock) with `threads` threads: each segment's
-// factors per block (about 8 blocks per SM for a large group) and threads per output
+// factors per block (one wave of resident blocks for a large group) and threads per output
 // state (enough to fill the factor's team, at most the mean list length, more for long lists;
 // one with `one_lane`, which keeps the thread-per-factor kernel's summation order, so
 // that groups moved from that kernel give the same bits); block ranges; the dynamic
@@ -215,10 +215,17 @@ int64_t lr_slot_count(const HostLayout &H) { return H.vin_tab4.empty() ? H.E : 4
 static int32_t plan_enum_block(EnumSeg *segs, int n_seg, int threads, int n_sm, bool one_lane, int32_t *smem) {
     int32_t blk = 0;
     *smem = 0;
+    for (int i = 0; i < n_seg; ++i) {  // the launch's shared memory first (it sets the occupancy)
+        const EnumSeg &sg = segs[i];
+        const int teams = sg.es_per_fac <= kEnumWarpStateSum ? threads / 32 : 1;
+        *smem = std::max(*smem, ((12 * sg.es_per_fac * teams + 15) & ~15) + sg.table_bytes);
+    }
+    // one wave: as many blocks as are resident at once, spread over the segments
+    const int64_t wave = (int64_t)n_sm * enum_block_resident(threads, *smem);
     for (int i = 0; i < n_seg; ++i) {
         EnumSeg &sg = segs[i];
-        const int64_t target = (int64_t)n_sm * 8;
-        sg.fpb = (int32_t)std::max<int64_t>(1, sg.n_fac / std::max<int64_t>(target, 1));
+        const int64_t target = std::max<int64_t>(1, wave);
+        sg.fpb = (int32_t)std::max<int64_t>(1, (sg.n_fac + target - 1) / target);
         const int64_t mean = (int64_t)sg.arity * sg.n_cfg / std::max(sg.es_per_fac, 1);
         int lanes = 1;
         // (a property of the group, not of the block size: results do not depend on the
@@ -231,9 +238,6 @@ static int32_t plan_enum_block(EnumSeg *segs, int n_seg, int threads, int n_sm, 
         sg.ordered = one_lane ? 1 : 0;
         sg.block_begin = blk;
         blk += (sg.n_fac + sg.fpb - 1) / sg.fpb;
-        // three state-sum arrays per team (a warp, or the block), then the staged table
-        const int teams = sg.es_per_fac <= kEnumWarpStateSum ? threads / 32 : 1;
-        *smem = std::max(*smem, ((12 * sg.es_per_fac * teams + 15) & ~15) + sg.table_bytes);
     }
     return blk;
 }

@@ -3367,6 +3367,22 @@ __global__ void k_until_control(cudaGraphConditionalHandle h, const unsigned *__
 // Launchers
 // =====================================================================================
 
+cudaError_t prepare_kernels(int max_smem_bytes);
+
+// Blocks of k_enum_block resident on one SM at `threads` threads and `smem` bytes of
+// dynamic shared memory: the smaller count of its max-product and sum-product forms
+// (at least 1).
+int enum_block_resident(int threads, int smem) {
+    if (smem > 48 * 1024 && prepare_kernels(smem) != cudaSuccess) return 1;
+    int a = 0, b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_enum_block<true, false>, threads, (size_t)smem) !=
+            cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_enum_block<false, false>, threads, (size_t)smem) !=
+            cudaSuccess)
+        return 1;
+    return std::max(1, std::min(a, b));
+}
+
 // The kernels with dynamic shared memory may take up to the device's opt-in maximum
 // (set once per device; a smaller limit set later would break other graphs' launches;
 // two threads that race here both set the same values).

@@ -270,6 +270,8 @@ cudaError_t launch_adj_logic(const DevGraph &G, const FactorLaunch &L, const flo
                              cudaStream_t s);
 cudaError_t launch_adj_var(const DevGraph &G, const float *ddamp, const float *dv2f, float *adj_prev, float *d_ev,
                            cudaStream_t s);
+// Resident blocks per SM of the block-form enumeration kernel for a launch shape.
+int enum_block_resident(int threads, int smem);
 // Configure kernel attributes (large dynamic shared memory) once per process/device.
 cudaError_t prepare_kernels(int max_smem_bytes);
 
