@@ -98,3 +98,23 @@ def test_product_path_has_no_oracle_import():
                 src = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in src and "from oracle" not in src, f
                 assert "lbp_oracle" not in src, f
+
+
+def test_large_enumeration_groups_accepted(lib):
+    """State sums above 64 (up to 8 neighbours x 256 states) and long configuration lists
+    compile on the host (the block-form kernels take them); sizes are exact."""
+    K = 256
+    cfg = np.stack([np.arange(K), (np.arange(K) + 1) % K], axis=1).astype(np.int32)
+    fg = W.FactorGraph(np.full(3, K, np.int32), [W.EnumGroup(cfg, np.array([[0, 1], [1, 2]], np.int32))])
+    info = B.check_desc(fg)
+    assert info["n_edge_states"] == 2 * 2 * K and info["n_potentials"] == 2 * K
+    big = np.zeros((3, 8), np.int32)
+    big[1] = 255
+    big[2] = np.arange(8)
+    fg8 = W.FactorGraph(np.full(8, K, np.int32), [W.EnumGroup(big, np.arange(8, dtype=np.int32)[None], True)])
+    info = B.check_desc(fg8)
+    assert info["n_edge_states"] == 8 * K and info["n_potentials"] == 3
+    p = W.pool_grid(16, 5, 2, 0)
+    info = B.check_desc(p.graph)
+    assert info["n_edge_states"] == 2 * (2 * 16 * 15) * 121
+    assert info["n_potentials"] == 2401
