@@ -517,6 +517,20 @@ pgm_status pgm_serve_submit_until(pgm_server *s, const pgm_graph_desc *desc, con
                                   float tol, int32_t check_every, int64_t *id);
 
 /*
+ * pgm_serve_submit (check_every = 0) or pgm_serve_submit_until (check_every >= 1, tol)
+ * without copies: the description (with every array it points to), log_pot and
+ * evidence are borrowed, and must stay valid and unchanged until pgm_serve_poll /
+ * pgm_serve_wait has returned the request's result (or pgm_serve_destroy has
+ * returned). For callers that submit many requests of a few graph structures at a
+ * high rate (copying a large grid's description and evidence at every submission
+ * bounds the submission rate). The description is validated by the worker that admits
+ * the request (errors reported by pgm_serve_poll / pgm_serve_wait).
+ */
+pgm_status pgm_serve_submit_borrowed(pgm_server *s, const pgm_graph_desc *desc, const float *log_pot,
+                                     const float *evidence, float T, float damping, int32_t max_iters,
+                                     float tol, int32_t check_every, int64_t *id);
+
+/*
  * Result of request `id`: PGM_EBUSY while it is queued or running; otherwise copies the
  * normalised log-beliefs [n_var_states] and decode [n_vars] into the host buffers (each
  * may be NULL), writes the latency in seconds, forgets the request and returns its

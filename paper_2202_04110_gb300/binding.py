@@ -24,7 +24,7 @@ FLAG_NAN = 2
 EXPORTED = ["pgm_build", "pgm_build_batch", "pgm_batch_member", "pgm_check_desc", "pgm_free", "pgm_graph_info", "pgm_run_bp", "pgm_beliefs",
             "pgm_decode", "pgm_infer_host", "pgm_set_profiling", "pgm_pass_times",
             "pgm_device_flags", "pgm_grid2_run_bp_noalloc", "pgm_run_bp_multi", "pgm_pmp_sample", "pgm_run_bp_until", "pgm_run_bp_until_members", "pgm_set_option", "pgm_get_option", "pgm_autotune",
-            "pgm_launch_info", "pgm_grad", "pgm_serve_create", "pgm_serve_submit", "pgm_serve_submit_until", "pgm_serve_poll",
+            "pgm_launch_info", "pgm_grad", "pgm_serve_create", "pgm_serve_submit", "pgm_serve_submit_until", "pgm_serve_submit_borrowed", "pgm_serve_poll",
             "pgm_serve_wait", "pgm_serve_stats", "pgm_serve_destroy", "pgm_last_error"]
 OPT_CUDA_GRAPH = 1
 OPT_LOG_RATIO = 2
@@ -142,6 +142,9 @@ def load_library(path: str | None = None):
     lib.pgm_serve_submit_until.restype = i32
     lib.pgm_serve_submit_until.argtypes = [vp, ctypes.POINTER(GraphDescC), vp, vp, f32, f32, i32, f32, i32,
                                            ctypes.POINTER(ctypes.c_int64)]
+    lib.pgm_serve_submit_borrowed.restype = i32
+    lib.pgm_serve_submit_borrowed.argtypes = [vp, ctypes.POINTER(GraphDescC), vp, vp, f32, f32, i32, f32, i32,
+                                              ctypes.POINTER(ctypes.c_int64)]
     lib.pgm_serve_poll.restype = i32
     lib.pgm_serve_poll.argtypes = [vp, ctypes.c_int64, vp, vp, ctypes.POINTER(ctypes.c_double)]
     lib.pgm_serve_wait.restype = i32
@@ -518,20 +521,28 @@ class Server:
         check(lib.pgm_serve_create(ctypes.byref(cfg), ctypes.byref(h)))
         self._h = h
         self._shapes = {}
+        self._borrowed = {}  # request id -> what a borrowed submission points into
 
     def submit(self, fg, log_pot, evidence, T: float, damping: float, n_iters: int, desc=None,
-               tol=None, check_every: int = 10) -> int:
+               tol=None, check_every: int = 10, borrow: bool = False) -> int:
         """Queue a request. `desc` may be a (desc, keepalive) pair from marshal_desc(fg),
         reused across submissions of the same graph. With `tol`, the request stops early
         (pgm_serve_submit_until: n_iters is the limit, the residual is checked every
-        `check_every` iterations)."""
+        `check_every` iterations). With `borrow`, nothing is copied
+        (pgm_serve_submit_borrowed): the server keeps references to the description and
+        arrays until the result is taken."""
         desc, keep = desc if desc is not None else marshal_desc(fg)
         lp = np.ascontiguousarray(log_pot, np.float32)
         ev = np.ascontiguousarray(evidence, np.float32)
         rid = ctypes.c_int64()
         lib = load_library()
         lpp = lp.ctypes.data if lp.size else None
-        if tol is None:
+        if borrow:
+            check(lib.pgm_serve_submit_borrowed(self._h, ctypes.byref(desc), lpp, ev.ctypes.data, float(T),
+                                                float(damping), int(n_iters), 0.0 if tol is None else float(tol),
+                                                0 if tol is None else int(check_every), ctypes.byref(rid)))
+            self._borrowed[rid.value] = (desc, keep, lp, ev)  # alive until the result is taken
+        elif tol is None:
             check(lib.pgm_serve_submit(self._h, ctypes.byref(desc), lpp, ev.ctypes.data, float(T), float(damping),
                                        int(n_iters), ctypes.byref(rid)))
         else:
@@ -552,6 +563,7 @@ class Server:
             return None
         if st != -6:  # a timed-out request is still pending
             self._shapes.pop(rid, None)
+            self._borrowed.pop(rid, None)
         check(st)
         return bel, dec, lat.value
 
@@ -571,6 +583,8 @@ class Server:
         if getattr(self, "_h", None) is not None and self._h.value:
             load_library().pgm_serve_destroy(self._h)
             self._h = ctypes.c_void_p()
+        if hasattr(self, "_borrowed"):
+            self._borrowed.clear()  # the server no longer reads them
 
     def __del__(self):
         try:

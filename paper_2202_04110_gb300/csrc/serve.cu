@@ -98,6 +98,12 @@ struct Request {
     float T = 1.f, damping = 0.f;
     int32_t n_iters = 0;        // iterations (the limit when check_every > 0)
     float tol = 0.f;            // early exit: residual tolerance
+    // borrowed requests (pgm_serve_submit_borrowed): the caller's description and arrays
+    const pgm_graph_desc *b_desc = nullptr;
+    const float *b_lp = nullptr, *b_ev = nullptr;
+    const pgm_graph_desc *desc() const { return b_desc ? b_desc : &d.desc; }
+    const float *lp() const { return b_desc ? b_lp : log_pot.data(); }
+    const float *ev() const { return b_desc ? b_ev : evidence.data(); }
     int32_t check_every = 0;    // early exit: residual checked every check_every iterations; 0 = off
     Clock::time_point t_submit, t_done;
     int32_t state = kPending;
@@ -154,7 +160,7 @@ void finish(pgm_server *s, const std::shared_ptr<Request> &r, pgm_status st, con
 // One request on one slot's stream. Returns the status; `err` gets the message.
 pgm_status run_request(Request &r, cudaStream_t st, std::string &err) {
     pgm_graph *g = nullptr;
-    pgm_status rc = pgm::build_graph_on_stream(&r.d.desc, st, &g);
+    pgm_status rc = pgm::build_graph_on_stream(r.desc(), st, &g);
     if (rc != PGM_OK) {
         err = pgm_last_error();
         return rc;
@@ -175,9 +181,9 @@ pgm_status run_request(Request &r, cudaStream_t st, std::string &err) {
     float *bel = reinterpret_cast<float *>(mem + b_lp + b_vs), *msgs = reinterpret_cast<float *>(mem + b_lp + 2 * b_vs);
     int32_t *dec = reinterpret_cast<int32_t *>(mem + b_lp + 2 * b_vs + b_es);
     if (I.n_potentials > 0)
-        e = cudaMemcpyAsync(lp, r.log_pot.data(), I.n_potentials * sizeof(float), cudaMemcpyHostToDevice, st);
+        e = cudaMemcpyAsync(lp, r.lp(), I.n_potentials * sizeof(float), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(ev, r.evidence.data(), I.n_var_states * sizeof(float), cudaMemcpyHostToDevice, st);
+        e = cudaMemcpyAsync(ev, r.ev(), I.n_var_states * sizeof(float), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess && I.n_edge_states > 0) e = cudaMemsetAsync(msgs, 0, I.n_edge_states * sizeof(float), st);
     rc = (e == cudaSuccess) ? PGM_OK : PGM_ECUDA;
     if (rc == PGM_OK && r.check_every > 0) {
@@ -230,8 +236,10 @@ void worker_loop(pgm_server *s, int w) {
         }
         // size check on the host (the compile is repeated by the build)
         pgm_info I{};
-        pgm_status rc = pgm_check_desc(&r->d.desc, &I);
+        pgm_status rc = pgm_check_desc(r->desc(), &I);
         int64_t need = 0;
+        if (rc == PGM_OK && r->b_desc && I.n_potentials > 0 && !r->b_lp)
+            rc = pgm::set_last_error(PGM_EINVAL, "log_pot is NULL");
         if (rc == PGM_OK) {
             need = request_bytes(I, r->check_every > 0);
             if (need > s->cfg.memory_budget_bytes) rc = PGM_ENOMEM;
@@ -292,17 +300,25 @@ pgm_status pgm_serve_create(const pgm_server_config *cfg, pgm_server **out) {
 }
 
 static pgm_status submit(pgm_server *s, const pgm_graph_desc *desc, const float *log_pot, const float *evidence,
-                         float T, float damping, int32_t n_iters, float tol, int32_t check_every, int64_t *id) {
+                         float T, float damping, int32_t n_iters, float tol, int32_t check_every, bool borrowed,
+                         int64_t *id) {
     if (!s || !id) return pgm::set_last_error(PGM_EINVAL, "NULL argument");
     if (!(T >= 0.f) || !std::isfinite(T)) return pgm::set_last_error(PGM_EINVAL, "T must be finite and >= 0");
     if (!(damping >= 0.f && damping < 1.f)) return pgm::set_last_error(PGM_EINVAL, "damping must be in [0, 1)");
     if (n_iters < 0 || !evidence) return pgm::set_last_error(PGM_EINVAL, "invalid n_iters or NULL evidence");
     auto r = std::make_shared<Request>();
-    std::string err = r->d.copy_from(desc);
-    if (!err.empty()) return pgm::set_last_error(PGM_EINVAL, err);
-    if (r->d.n_potentials > 0 && !log_pot) return pgm::set_last_error(PGM_EINVAL, "log_pot is NULL");
-    r->log_pot.assign(log_pot ? log_pot : evidence, log_pot ? log_pot + r->d.n_potentials : evidence);
-    r->evidence.assign(evidence, evidence + r->d.n_var_states);
+    if (borrowed) {  // checked by the worker that admits it
+        if (!desc) return pgm::set_last_error(PGM_EINVAL, "invalid description");
+        r->b_desc = desc;
+        r->b_lp = log_pot;
+        r->b_ev = evidence;
+    } else {
+        std::string err = r->d.copy_from(desc);
+        if (!err.empty()) return pgm::set_last_error(PGM_EINVAL, err);
+        if (r->d.n_potentials > 0 && !log_pot) return pgm::set_last_error(PGM_EINVAL, "log_pot is NULL");
+        r->log_pot.assign(log_pot ? log_pot : evidence, log_pot ? log_pot + r->d.n_potentials : evidence);
+        r->evidence.assign(evidence, evidence + r->d.n_var_states);
+    }
     r->T = T;
     r->damping = damping;
     r->n_iters = n_iters;
@@ -324,7 +340,15 @@ static pgm_status submit(pgm_server *s, const pgm_graph_desc *desc, const float 
 
 pgm_status pgm_serve_submit(pgm_server *s, const pgm_graph_desc *desc, const float *log_pot,
                             const float *evidence, float T, float damping, int32_t n_iters, int64_t *id) {
-    return submit(s, desc, log_pot, evidence, T, damping, n_iters, 0.f, 0, id);
+    return submit(s, desc, log_pot, evidence, T, damping, n_iters, 0.f, 0, false, id);
+}
+
+pgm_status pgm_serve_submit_borrowed(pgm_server *s, const pgm_graph_desc *desc, const float *log_pot,
+                                     const float *evidence, float T, float damping, int32_t max_iters, float tol,
+                                     int32_t check_every, int64_t *id) {
+    if (check_every < 0) return pgm::set_last_error(PGM_EINVAL, "check_every must be >= 0");
+    if (check_every > 0 && !(tol >= 0.f)) return pgm::set_last_error(PGM_EINVAL, "tol must be >= 0");
+    return submit(s, desc, log_pot, evidence, T, damping, max_iters, tol, check_every, true, id);
 }
 
 pgm_status pgm_serve_submit_until(pgm_server *s, const pgm_graph_desc *desc, const float *log_pot,
@@ -332,7 +356,7 @@ pgm_status pgm_serve_submit_until(pgm_server *s, const pgm_graph_desc *desc, con
                                   int32_t check_every, int64_t *id) {
     if (check_every < 1) return pgm::set_last_error(PGM_EINVAL, "check_every must be >= 1");
     if (!(tol >= 0.f)) return pgm::set_last_error(PGM_EINVAL, "tol must be >= 0");
-    return submit(s, desc, log_pot, evidence, T, damping, max_iters, tol, check_every, id);
+    return submit(s, desc, log_pot, evidence, T, damping, max_iters, tol, check_every, false, id);
 }
 
 static pgm_status take_result(pgm_server *s, std::unordered_map<int64_t, std::shared_ptr<Request>>::iterator it,

@@ -171,3 +171,29 @@ def test_large_factor_requests_equal_alone(gpu):
         b1, d1 = _alone(gpu, p, T, it)
         np.testing.assert_array_equal(bel, b1, err_msg=p.name)
         np.testing.assert_array_equal(dec, d1, err_msg=p.name)
+
+
+@pytest.mark.parametrize("tol", [None, 1e-4])
+def test_borrowed_requests_equal_copied(gpu, tol):
+    """pgm_serve_submit_borrowed (no copies at submission) gives the results of the
+    copying submissions, with and without an early exit; a borrowed request with a bad
+    description fails on its own."""
+    reqs = _requests(n=12, seed=5)
+    out = []
+    for borrow in (False, True):
+        srv = gpu.Server(memory_budget_bytes=64 << 20, max_in_flight=4)
+        keep = [(np.asarray(p.log_pot, np.float32), np.asarray(p.evidence, np.float32)) for p, _, _ in reqs]
+        ids = [srv.submit(p.graph, lp, ev, T, 0.5, it, tol=tol, borrow=borrow)
+               for (p, T, it), (lp, ev) in zip(reqs, keep)]
+        out.append([srv.wait(i, 120.0) for i in ids])
+        srv.close()
+    for (b0, d0, _), (b1, d1, _) in zip(out[0], out[1]):
+        np.testing.assert_array_equal(b0, b1)
+        np.testing.assert_array_equal(d0, d1)
+    srv = gpu.Server(memory_budget_bytes=1 << 20, max_in_flight=1)
+    bad = W.FactorGraph(np.array([2, 2], np.int32), [W.EnumGroup(W.PAIR2_CFG.copy(), np.array([[0, 5]], np.int32))])
+    i_bad = srv.submit(bad, np.zeros(4, np.float32), np.zeros(4, np.float32), 1.0, 0.5, 5, borrow=True)
+    with pytest.raises(gpu.PgmError) as ei:
+        srv.wait(i_bad, 60.0)
+    assert ei.value.status == -1
+    srv.close()
