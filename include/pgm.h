@@ -7,8 +7,8 @@
  * general factor graphs"), enumeration factors listed by their valid configurations
  * (Sec. 5.2), logical factors with message updates linear in the fan-in (Sec. 3),
  * parallel message updates with damping (Sec. 3, after Pretti 2005), all messages kept
- * in flat arrays updated by gather/scatter (Sec. 4 "A fully flat array-based LBP
- * implementation"), LBP as a pure function of explicit message state (Sec. 3,
+ * in flat arrays updated by gather/scatter (Sec. 4, the flat-array implementation),
+ * LBP as a pure function of explicit message state (Sec. 3,
  * Sec. 5.3), MAP decoding (Sec. 5.1).
  *
  * Conventions for every call:

@@ -1639,7 +1639,7 @@ k_enum_generic(DevGraph G, const EnumSeg *__restrict__ segs, int n_seg, const fl
 // =====================================================================================
 
 // Factors given by a long list of valid configurations or with many states (Sec. 5.2:
-// RCN's non-standard pairwise factors are specified this way), beyond the thread-per-factor
+// the irregular pairwise factors of RCN are given this way), beyond the thread-per-factor
 // kernel's kMaxStateSum. A block takes fpb consecutive factors of one group; a team -- a
 // warp when the state sum is at most kEnumWarpStateSum (so a 256-thread block has 8
 // factors in flight and no block-wide barrier), else the whole block -- takes one factor

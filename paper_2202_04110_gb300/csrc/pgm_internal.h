@@ -1,6 +1,6 @@
 // Internal layout of a compiled factor graph (host compiler <-> kernels).
 //
-// The flat layout follows PGMax's fully flat array design (arXiv 2202.04110, Sec. 4):
+// The flat layout follows PGMax's flat-array design (arXiv 2202.04110, Sec. 4):
 // every factor-to-variable message lives in one 1-D array indexed by edge-state, and
 // the compiler keeps the global indices of variable states and factor configurations.
 // Only factor-to-variable messages are stored; variable-to-factor messages are
