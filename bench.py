@@ -822,11 +822,13 @@ def run_ours(args):
                        "d2h_bytes_per_step": len(temps) * 4 * (VS + V),
                        "call": "pgm_infer_host (pinned host buffers, blocking)"}
 
-    if not args.no_batch:
+    # the further sections are single-GPU measurements: run at N = 1 only (at N > 1 the
+    # line reports the replicas' headline)
+    if not args.no_batch and world == 1:
         line["batched"] = measure_batched(args, binding, W, torch, dev)
-    if not args.no_multi:
+    if not args.no_multi and world == 1:
         line["multi_evidence"] = measure_multi(args, binding, W, torch, dev)
-    if not args.no_grad:
+    if not args.no_grad and world == 1:
         line["gradient"] = measure_grad(args, binding, W, torch, dev)
         line["early_exit"] = measure_until(args, binding, W, torch, dev)
         line["large_factors"] = measure_large_enum(args, binding, W, torch, dev)
