@@ -53,6 +53,8 @@ def parse_args():
     ap.add_argument("--batch-grids", type=int, default=256)
     ap.add_argument("--no-multi", action="store_true", help="skip the multi-evidence measurement")
     ap.add_argument("--no-grad", action="store_true", help="skip the gradient measurement")
+    ap.add_argument("--no-deconv", action="store_true",
+                    help="skip the deconvolution (1000 iterations) and 10x10 latency sections")
     ap.add_argument("--no-until", action="store_true", help="skip the batch's per-member early exit")
     ap.add_argument("--pool-probe", default="",
                     help="SIDE,RADIUS,SLACK: a short uncaptured run of a pool grid (large listed-"
@@ -315,9 +317,28 @@ def measure_batched(args, binding, W, torch, dev):
             "members_stopped_early": int((done < iters).sum()),
             "edge_state_updates_run_fraction": float((done * member_es).sum() / (iters * member_es.sum())),
             "call": "pgm_run_bp_until_members (edge-state iterations, conditional while node)"}}
+    peak, _ = measured_peaks()
+    it_bytes = sec8d_bytes(batch.graph)
+    out_cpu = {}
+    if not args.no_cpu_baseline:
+        # the FP64 oracle on a seeded subset: the first 16 grids of the batch and the RBM
+        import oracle
+        oracle.build()
+        sub = W.union(members[:16] + [members[-1]], name="subset")
+        n_cpu = 3
+        t0 = time.perf_counter()
+        oracle.run_bp(sub.graph, sub.log_pot, sub.evidence, 1.0, 0.5, n_cpu)
+        dt = time.perf_counter() - t0
+        out_cpu = {"cpu_baseline": {"value": n_cpu * sub.graph.n_edge_states / dt, "unit": UNIT,
+                                    "cores": oracle.num_threads(), "kind": "oracle",
+                                    "sample": f"{n_cpu} iterations of the first 16 Potts grids and the RBM "
+                                              f"({sub.graph.n_edge_states} edge-states), FP64, {dt:.1f} s"}}
     return {"workload": f"{args.batch_grids} Potts grids (side U{{16..256}}, K in {{2,4,8,16}}) + RBM 784x500, "
                         f"T=1, damping 0.5, {iters} iterations",
             "graphs": len(members), "edge_states": ES,
+            "iteration_sec8d_bytes": it_bytes,
+            "batched_iteration_frac": round(it_bytes / (t_batched / iters) / 1e9 / peak, 4),
+            **out_cpu,
             "batched": upd / t_batched, "per_graph": upd / t_single, "unit": UNIT,
             "batched_ms_per_run": 1e3 * t_batched, "per_graph_ms_per_run": 1e3 * t_single,
             "speedup": t_single / t_batched, "autotune_s": round(tune_s, 2), "launch_shapes": launches,
@@ -499,6 +520,171 @@ def measure_large_enum(args, binding, W, torch, dev):
                     "factor_pass_ms": f_ms, "var_pass_ms": tv / max(nv, 1),
                     "factor_pass_gbs": fac_bytes / (f_ms * 1e-3) / 1e9,
                     "launches": g.launches()})
+    return out
+
+
+def sec8d_bytes(fg, factor_groups=None):
+    """The per-iteration minimum traffic of the method for a factor graph: 8 ES (read and
+    write every factor-to-variable message) + 4 sum n_cfg (per-factor log-potentials; a
+    shared table counts once) + 4 VS (evidence) + 4 E (edge index). With `factor_groups`
+    (indices into enum_groups + logic_groups), the factor-side share of those groups
+    only: their 8 ES + 4 n_cfg + 4 E."""
+    import numpy as np
+    k = fg.num_states.astype(np.int64)
+    groups = [("enum", g) for g in fg.enum_groups] + [("logic", g) for g in fg.logic_groups]
+    sel = range(len(groups)) if factor_groups is None else factor_groups
+    total = 0
+    for i in sel:
+        kind, g = groups[i]
+        if kind == "enum":
+            es, e = int(k[g.vars].sum()), g.n_fac * g.arity
+            total += 8 * es + 4 * e + 4 * (g.n_cfg if g.shared else g.n_cfg * g.n_fac)
+        else:
+            e = int(g.par_off[-1]) + g.n_fac
+            total += 8 * 2 * e + 4 * e
+    if factor_groups is None:
+        total += 4 * int(k.sum())
+    return total
+
+
+def measure_deconv(args, binding, W, torch, dev):
+    """Binary deconvolution with logical factors (the paper's Sec. 5.2 example; synthetic
+    stand-in for its notebook data): 5 features 6x6, activations 10x10, 100 images 15x15,
+    1,800,000 AND factors (fan-in 2) and 22,500 OR factors (fan-in 5..180), max-product T=0,
+    damping 0.5, 1000 iterations from zero messages. Whole runs timed with CUDA events;
+    per-launch times from in-graph events on every 50th iteration of one run; the FP64
+    oracle timed on the host cores on a 10-iteration sample of the same graph."""
+    import numpy as np
+    n_it = 1000
+    p = W.deconvolution(0, n_iters=n_it)
+    fg = p.graph
+    g = binding.Graph(fg)
+    I = g.info
+    ev = torch.as_tensor(p.evidence).to(dev)
+    m = g.new_msgs()
+    stream = torch.cuda.current_stream()
+    for _ in range(2):
+        m.zero_()
+        g.run_bp(None, ev, 0.0, 0.5, n_it, m)
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(3):
+        m.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        g.run_bp(None, ev, 0.0, 0.5, n_it, m)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1) / 1e3)
+    t = statistics.median(times)
+    period = 50
+    g.set_profiling(period)
+    m.zero_()
+    g.run_bp(None, ev, 0.0, 0.5, n_it, m)
+    torch.cuda.synchronize()
+    lt = g.launch_times()
+    g.set_profiling(0)
+    launches = g.launches()
+    peak, _ = measured_peaks()
+    # the workload's parts: W (degree 10,000: block-per-variable pass), the AND group
+    # (thread per factor) and the OR group (warp per factor)
+    ks = fg.num_states.astype(np.int64)
+    deg = np.zeros(fg.n_vars, np.int64)
+    for lg_ in fg.logic_groups:
+        np.add.at(deg, lg_.parents, 1)
+        np.add.at(deg, lg_.child, 1)
+    hi = deg > 64
+    # implementation bytes per launch (two-pass design): block variable pass reads K d
+    # messages and writes 2 K d float-float leave-one-out values; a logical factor reads
+    # its old messages, the beliefs of its edges and their index, and writes its messages
+    n_hi_es = int((ks[hi] * deg[hi]).sum())
+    and_g, or_g = fg.logic_groups[0], fg.logic_groups[1]
+    e_and = int(and_g.par_off[-1]) + and_g.n_fac
+    e_or = int(or_g.par_off[-1]) + or_g.n_fac
+    impl = {"k_var_block": 12 * n_hi_es + 8 * int(ks[hi].sum()),
+            "k_logic_small": 4 * (4 * e_and + 2 * e_and + e_and),
+            "k_logic_warp": 4 * (4 * e_or + 2 * e_or + e_or)}
+    s8d = {"k_logic_small": sec8d_bytes(fg, [0]), "k_logic_warp": sec8d_bytes(fg, [1]),
+           "k_var_block": 4 * int(ks[hi].sum())}
+    names = {(0, 1): "k_var_block", (0, 2): "k_var_thread<2>", (0, 0): "k_var_thread",
+             (1, 5): "k_logic_small", (1, 6): "k_logic_warp"}
+    per = {}
+    for (kind, variant, threads, blocks), (ms, cnt) in zip(launches, lt):
+        name = names.get((kind, variant), f"kind{kind}_variant{variant}")
+        if cnt == 0:
+            continue
+        us = 1e3 * ms / cnt
+        d = {"mean_launch_us": round(us, 2), "threads": threads, "blocks": blocks}
+        if name in impl:
+            d["algorithmic_bytes_per_launch"] = impl[name]
+            d["achieved_gbs"] = round(impl[name] / (us * 1e-6) / 1e9, 1)
+            d["frac"] = round(impl[name] / (us * 1e-6) / 1e9 / peak, 4)
+            d["sec8d_share_bytes"] = s8d[name]
+            d["sec8d_frac"] = round(s8d[name] / (us * 1e-6) / 1e9 / peak, 4)
+        per[name] = d
+    it_s = t / n_it
+    it_bytes = sec8d_bytes(fg)
+    ES = I["n_edge_states"]
+    out = {"workload": "deconvolution: 5 features 6x6, S 10x10, 100 images 15x15 (W 180, S 50,000, AND 1,800,000, "
+                       "X 22,500 variables; 1,800,000 AND + 22,500 OR factors), T=0, damping 0.5, 1000 iterations",
+           "edge_states": ES, "value": n_it * ES / t, "unit": UNIT, "ms_per_run": round(1e3 * t, 3),
+           "iteration_us": round(1e6 * it_s, 2), "iteration_sec8d_bytes": it_bytes,
+           "iteration_achieved_gbs": round(it_bytes / it_s / 1e9, 1),
+           "iteration_frac": round(it_bytes / it_s / 1e9 / peak, 4),
+           "kernels": per,
+           "kernel_timing": f"CUDA events around each launch of every {period}th iteration of one run "
+                            "(event nodes in its CUDA graph); an event pair includes the launch's latency"}
+    if not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        n_cpu = 10
+        t0 = time.perf_counter()
+        oracle.run_bp(fg, p.log_pot, p.evidence, 0.0, 0.5, n_cpu)
+        dt = time.perf_counter() - t0
+        out["cpu_baseline"] = {"value": n_cpu * ES / dt, "unit": UNIT, "cores": oracle.num_threads(),
+                               "kind": "oracle", "sample": f"{n_cpu} iterations of the full graph, FP64, {dt:.1f} s"}
+    del m, g
+    return out
+
+
+def measure_small(args, binding, W, torch, dev):
+    """Per-iteration latency of the 10x10 Ising grid (180 factors, 720 edge-states), T=1,
+    damping 0.5, 50 iterations: CUDA events around 200 back-to-back pgm_run_bp calls (one
+    CUDA graph replay each), and the FP64 oracle's time for the same run on the host."""
+    p = W.ising_small(0)
+    g = binding.Graph(p.graph)
+    lp = torch.as_tensor(p.log_pot).to(dev)
+    ev = torch.as_tensor(p.evidence).to(dev)
+    m = g.new_msgs()
+    stream = torch.cuda.current_stream()
+    for _ in range(10):
+        g.run_bp(lp, ev, 1.0, 0.5, p.n_iters, m)
+    torch.cuda.synchronize()
+    reps = 200
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        g.run_bp(lp, ev, 1.0, 0.5, p.n_iters, m)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) / 1e3 / reps
+    out = {"workload": "ising10x10, T=1, damping 0.5, 50 iterations", "us_per_run": round(1e6 * t, 2),
+           "us_per_iteration": round(1e6 * t / p.n_iters, 3),
+           "value": p.n_iters * g.info["n_edge_states"] / t, "unit": UNIT,
+           "launches_per_run": p.n_iters * g.info["launches_per_iter"] + 3}
+    if not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        t0 = time.perf_counter()
+        n_rep = 0
+        while n_rep < 200 and time.perf_counter() - t0 < 2.0:
+            oracle.run_bp(p.graph, p.log_pot, p.evidence, 1.0, 0.5, p.n_iters)
+            n_rep += 1
+        dt = (time.perf_counter() - t0) / n_rep
+        out["cpu_baseline"] = {"us_per_run": round(1e6 * dt, 2), "cores": oracle.num_threads(), "kind": "oracle",
+                               "sample": f"{n_rep} runs of the full workload (FP64)"}
     return out
 
 
@@ -742,6 +928,13 @@ def run_ours(args):
     else:
         fac_bytes = 4 * (2 * ES + n_cfg_total + E + VS)  # m_old + m_new + log-potentials + edge index + beliefs
         var_bytes = 4 * (ES + 2 * VS + E)               # messages + evidence + beliefs + incoming-edge index
+    # the method's minimum traffic per iteration (8 ES + 4 sum n_cfg + 4 VS + 4 E), split
+    # into the factor pass's share (its messages, log-potentials and edge index) and the
+    # variable pass's (evidence); the bytes the implementation above moves are reported
+    # beside it (the log-ratio encoding keeps one number per edge and direction)
+    impl_fac_bytes, impl_var_bytes = fac_bytes, var_bytes
+    fac_bytes = sec8d_bytes(p.graph, [0])
+    var_bytes = 4 * VS
     fac_avg_s = fac_ms / 1e3 / max(n_fac, 1)
     var_avg_s = var_ms / 1e3 / max(n_var, 1)
     peak, peak_src = measured_peaks()
@@ -760,6 +953,7 @@ def run_ours(args):
     dominant, other = (fac_name, var_name) if fac_dom else (var_name, fac_name)
     dom_gbs, oth_gbs = (fac_gbs, var_gbs) if fac_dom else (var_gbs, fac_gbs)
     dom_bytes, oth_bytes = (fac_bytes, var_bytes) if fac_dom else (var_bytes, fac_bytes)
+    dom_impl, oth_impl = (impl_fac_bytes, impl_var_bytes) if fac_dom else (impl_var_bytes, impl_fac_bytes)
     dom_s, oth_s = (fac_avg_s, var_avg_s) if fac_dom else (var_avg_s, fac_avg_s)
     roof = {"bound": "hbm", "kernel": dominant,
             "achieved": round(dom_gbs, 1),
@@ -767,16 +961,23 @@ def run_ours(args):
             "frac": round(dom_gbs / peak, 4),
             "traffic": profiled_traffic(dominant, wl),
             "algorithmic_bytes_per_launch": dom_bytes,
+            "algorithmic_bytes": "the factor pass's share of the per-iteration minimum 8 ES + 4 sum n_cfg + "
+                                 "4 VS + 4 E (8 ES + 4 sum n_cfg + 4 E); the variable pass's share is 4 VS",
+            "implementation_bytes_per_launch": dom_impl,
+            "implementation_frac": round(dom_impl / dom_s / 1e9 / peak, 4),
             "mean_launch_us": round(1e6 * dom_s, 2),
             "other_kernels": {
                 other: {"achieved": round(oth_gbs, 1), "frac": round(oth_gbs / peak, 4),
                         "algorithmic_bytes_per_launch": oth_bytes,
+                        "implementation_bytes_per_launch": oth_impl,
+                        "implementation_frac": round(oth_impl / oth_s / 1e9 / peak, 4),
                         "mean_launch_us": round(1e6 * oth_s, 2),
                         "traffic": profiled_traffic(other, wl)}},
             "kernel_timing": "CUDA events on the launching stream around the passes of every "
                              f"{min(PROFILE_PERIOD, args.iters)}th iteration of the timed runs (event nodes in their CUDA graphs)",
             "nominal_peak": NOMINAL_HBM_GBS, "frac_of_nominal": round(dom_gbs / NOMINAL_HBM_GBS, 4),
             "iteration": {"algorithmic_bytes": iter_bytes,
+                          "implementation_bytes": impl_fac_bytes + impl_var_bytes,
                           "mean_us": round(1e6 * iter_run_s, 2),
                           "achieved": round(iter_bytes / iter_run_s / 1e9, 1),
                           "frac": round(iter_bytes / iter_run_s / 1e9 / peak, 4),
@@ -828,6 +1029,9 @@ def run_ours(args):
         line["batched"] = measure_batched(args, binding, W, torch, dev)
     if not args.no_multi and world == 1:
         line["multi_evidence"] = measure_multi(args, binding, W, torch, dev)
+    if not args.no_deconv and world == 1:
+        line["deconvolution"] = measure_deconv(args, binding, W, torch, dev)
+        line["small_grid"] = measure_small(args, binding, W, torch, dev)
     if not args.no_grad and world == 1:
         line["gradient"] = measure_grad(args, binding, W, torch, dev)
         line["early_exit"] = measure_until(args, binding, W, torch, dev)

@@ -232,6 +232,17 @@ pgm_status pgm_infer_host(pgm_graph *g, const float *log_pot, const float *evide
 pgm_status pgm_set_profiling(pgm_graph *g, int32_t period);
 pgm_status pgm_pass_times(pgm_graph *g, double *var_ms, double *factor_ms, int64_t *n_var,
                           int64_t *n_factor);
+/*
+ * The same sampled iterations, per launch: with profiling on, each sampled iteration
+ * records an event before its first launch and one after each launch, so launch i of
+ * the iteration (in the order of pgm_launch_info for edge-state iterations; for log-ratio
+ * iterations the variable pass, then the factor pass) is timed from the end of launch
+ * i - 1. ms[i] (host [n]) = the summed durations of launch position i, count[i] = how
+ * many were sampled; *n_positions (may be NULL) = positions recorded. Synchronises and
+ * resets the times like pgm_pass_times (the two calls share one set of totals).
+ * PGM_EINVAL for a NULL graph, n < 0 or NULL arrays with n > 0.
+ */
+pgm_status pgm_launch_times(pgm_graph *g, int32_t n, double *ms, int64_t *count, int32_t *n_positions);
 
 /*
  * Gradient (Sec. 5.3: LBP as part of an end-to-end differentiable system): the
@@ -287,18 +298,28 @@ pgm_status pgm_device_flags(pgm_graph *g, uint32_t *flags, int32_t clear, void *
  *   neighbour); evidence is [2 * rows * cols]. All pointers are device memory owned by
  *   the caller (log_pot and msgs 16-byte aligned, evidence 8-byte aligned); msgs is
  *   in/out as in pgm_run_bp, whose iteration this is.
- *   Limit: 4 * n_factors + 2 * rows * cols <= PGM_NOALLOC_SCRATCH_FLOATS (for example a
- *   632 x 632 grid); larger grids return PGM_EINVAL with the sizes in pgm_last_error().
+ *   Limit: 4 * n_factors + 2 * rows * cols <= PGM_NOALLOC_SCRATCH_FLOATS, with
+ *   n_factors = 2 * rows * cols - rows - cols (the largest square grid is 648 x 648);
+ *   larger grids return PGM_EINVAL with the sizes in pgm_last_error().
  *   The first call on a device looks up the array's device address
  *   (cudaGetSymbolAddress) with that device current; make that first call before any
  *   stream capture. Every call on a device shares the one array, so calls whose work
  *   overlaps on the GPU (different streams, or different host threads) race and corrupt
- *   each other's results: serialise them.
+ *   each other's results: serialise them. Each call clears the array's status word and
+ *   then raises PGM_FLAG_CONTRADICTION in it when a message has both states at -inf (the
+ *   message becomes 0, as in pgm_run_bp); pgm_grid2_noalloc_flags reads it.
  */
 #define PGM_NOALLOC_SCRATCH_FLOATS 4194304
 pgm_status pgm_grid2_run_bp_noalloc(int32_t rows, int32_t cols, const float *log_pot,
                                     const float *evidence, float T, float damping,
                                     int32_t n_iters, float *msgs, void *stream);
+/*
+ * The status word of the last pgm_grid2_run_bp_noalloc call on the current device (its
+ * PGM_FLAG_* bits; 0 before any call): synchronises `stream`, copies the word into
+ * *flags (host) and, with clear = 1, zeroes it. Allocates nothing. PGM_EINVAL for NULL
+ * flags, PGM_ECUDA if the array's address cannot be looked up or a copy fails.
+ */
+pgm_status pgm_grid2_noalloc_flags(uint32_t *flags, int32_t clear, void *stream);
 
 /*
  * n_samples runs of one graph with different inputs, as n_samples calls of pgm_run_bp:

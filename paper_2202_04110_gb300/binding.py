@@ -22,8 +22,8 @@ FLAG_NAN = 2
 
 # Every symbol include/pgm.h declares.
 EXPORTED = ["pgm_build", "pgm_build_batch", "pgm_batch_member", "pgm_check_desc", "pgm_free", "pgm_graph_info", "pgm_run_bp", "pgm_beliefs",
-            "pgm_decode", "pgm_infer_host", "pgm_set_profiling", "pgm_pass_times",
-            "pgm_device_flags", "pgm_grid2_run_bp_noalloc", "pgm_run_bp_multi", "pgm_pmp_sample", "pgm_run_bp_until", "pgm_run_bp_until_members", "pgm_set_option", "pgm_get_option", "pgm_autotune",
+            "pgm_decode", "pgm_infer_host", "pgm_set_profiling", "pgm_pass_times", "pgm_launch_times",
+            "pgm_device_flags", "pgm_grid2_run_bp_noalloc", "pgm_grid2_noalloc_flags", "pgm_run_bp_multi", "pgm_pmp_sample", "pgm_run_bp_until", "pgm_run_bp_until_members", "pgm_set_option", "pgm_get_option", "pgm_autotune",
             "pgm_launch_info", "pgm_grad", "pgm_serve_create", "pgm_serve_submit", "pgm_serve_submit_until", "pgm_serve_submit_borrowed", "pgm_serve_poll",
             "pgm_serve_wait", "pgm_serve_stats", "pgm_serve_destroy", "pgm_last_error"]
 OPT_CUDA_GRAPH = 1
@@ -125,10 +125,14 @@ def load_library(path: str | None = None):
     lib.pgm_pass_times.restype = i32
     lib.pgm_pass_times.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                                    ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
+    lib.pgm_launch_times.restype = i32
+    lib.pgm_launch_times.argtypes = [vp, i32, vp, vp, ctypes.POINTER(i32)]
     lib.pgm_device_flags.restype = i32
     lib.pgm_device_flags.argtypes = [vp, ctypes.POINTER(ctypes.c_uint32), i32, vp]
     lib.pgm_grid2_run_bp_noalloc.restype = i32
     lib.pgm_grid2_run_bp_noalloc.argtypes = [i32, i32, vp, vp, f32, f32, i32, vp, vp]
+    lib.pgm_grid2_noalloc_flags.restype = i32
+    lib.pgm_grid2_noalloc_flags.argtypes = [ctypes.POINTER(ctypes.c_uint32), i32, vp]
     lib.pgm_autotune.restype = i32
     lib.pgm_autotune.argtypes = [vp, vp, vp, f32, f32, vp]
     lib.pgm_launch_info.restype = i32
@@ -436,6 +440,16 @@ class Graph:
         check(load_library().pgm_pass_times(self._h, ctypes.byref(tv), ctypes.byref(tf), ctypes.byref(nv), ctypes.byref(nf)))
         return tv.value, tf.value, nv.value, nf.value
 
+    def launch_times(self, n: int = 32):
+        """[(summed ms, sampled launches)] per launch position of the sampled iterations
+        since the last call (pgm_launch_times), from CUDA events on the launching stream."""
+        ms = np.zeros(max(n, 1), np.float64)
+        cnt = np.zeros(max(n, 1), np.int64)
+        npos = ctypes.c_int32(0)
+        check(load_library().pgm_launch_times(self._h, int(n), ms.ctypes.data, cnt.ctypes.data, ctypes.byref(npos)))
+        k = min(int(npos.value), n)
+        return [(float(ms[i]), int(cnt[i])) for i in range(k)]
+
     def flags(self, clear: bool = False, stream=None) -> int:
         f = ctypes.c_uint32(0)
         check(load_library().pgm_device_flags(self._h, ctypes.byref(f), int(bool(clear)), _stream_ptr(stream)))
@@ -456,6 +470,14 @@ def grid2_run_bp_noalloc(rows: int, cols: int, log_pot, evidence, T: float, damp
         _dptr(evidence, torch.float32, 2 * rows * cols, "evidence"), float(T), float(damping),
         int(n_iters), _dptr(msgs, torch.float32, 4 * F, "msgs") if F else 0, _stream_ptr(stream)))
     return msgs
+
+
+def grid2_noalloc_flags(clear: bool = False, stream=None) -> int:
+    """pgm_grid2_noalloc_flags: the PGM_FLAG_* bits of the last allocation-free grid call
+    on the current device (synchronises the stream)."""
+    f = ctypes.c_uint32(0)
+    check(load_library().pgm_grid2_noalloc_flags(ctypes.byref(f), int(bool(clear)), _stream_ptr(stream)))
+    return int(f.value)
 
 
 def infer(problem, n_iters: int | None = None, T: float | None = None, graph: Graph | None = None):

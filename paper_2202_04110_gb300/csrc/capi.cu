@@ -48,6 +48,13 @@ size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 int32_t pgm::set_last_error(int32_t code, const std::string &msg) { return fail(code, msg); }
 
+// One sampled iteration of per-launch timing: its first event, then one event after each
+// of its nv variable-pass and nf factor-pass launches.
+struct ProfGroup {
+    uint32_t first;
+    uint16_t nv, nf;
+};
+
 struct pgm_graph {
     int device = 0;
     int n_sm = 1;
@@ -103,11 +110,14 @@ struct pgm_graph {
     void *host_io_mem = nullptr;
     float *io_pot = nullptr, *io_ev = nullptr, *io_msgs = nullptr, *io_bel = nullptr;
     int32_t *io_dec = nullptr;
-    // per-pass event timing
+    // per-launch event timing
     int32_t profiling = 0;  // sampling period in iterations, 0 = off
     std::vector<cudaEvent_t> events;
     size_t events_used = 0;
+    std::vector<ProfGroup> prof_groups;  // sampled iterations of direct launches
     int64_t prof_var_launches = 0, prof_factor_launches = 0;
+    std::vector<double> launch_ms;       // summed event time per launch position
+    std::vector<int64_t> launch_n;       // sampled launches per position
     int32_t var_launches = 0, factor_launches = 0;
     std::vector<HostMember> members;
     FactorLaunch adj_launch{};      // pgm_grad: enumeration groups of state sum <= 64, thread per factor
@@ -124,17 +134,17 @@ struct pgm_graph {
         float *msgs;
         uint32_t T_bits, damping_bits;
         int32_t n_iters;
-        int32_t prof_period;             // per-pass timing captured in the graph (0 = none)
+        int32_t prof_period;             // per-launch timing captured in the graph (0 = none)
         cudaGraphExec_t exec;
         uint64_t last_use;
-        std::vector<cudaEvent_t> ev;     // event triples recorded by each replay
-        int64_t nv = 0, nf = 0;          // sampled launches per replay
+        std::vector<cudaEvent_t> ev;     // events recorded by each replay
+        std::vector<ProfGroup> groups;   // the sampled iterations among them
         bool pending = false;            // a replay whose times are not collected yet
     };
-    // capture in progress: where take_events puts the graph's events
+    // capture in progress: where take_event puts the graph's events
     std::vector<cudaEvent_t> *capture_events = nullptr;
-    int64_t capture_nv = 0, capture_nf = 0;
-    double graph_var_ms = 0.0, graph_factor_ms = 0.0;  // collected from replays
+    std::vector<ProfGroup> *capture_groups = nullptr;
+    double graph_var_ms = 0.0, graph_factor_ms = 0.0;  // summed over the sampled passes
     int32_t use_cuda_graph = 1;
     int32_t log_ratio_min_iters = 4;  // PGM_OPT_LOG_RATIO
     cudaStream_t capture_stream = nullptr;
@@ -386,29 +396,48 @@ pgm_status build_plan(const HostLayout &H, pgm_graph *g, Packer &pk, std::vector
     return PGM_OK;
 }
 
-pgm_status take_events(pgm_graph *g, cudaEvent_t *a, cudaEvent_t *b, cudaEvent_t *c) {
-    if (g->capture_events) {  // new events owned by the graph being captured
-        cudaEvent_t ev[3];
-        for (int i = 0; i < 3; ++i) {
-            cudaError_t e = cudaEventCreate(&ev[i]);
-            if (e != cudaSuccess) return cuda_fail(e, "cudaEventCreate");
-            g->capture_events->push_back(ev[i]);
-        }
-        *a = ev[0];
-        *b = ev[1];
-        *c = ev[2];
+// The next timing event: a new event owned by the graph being captured, or the next one
+// of the graph's pool for direct launches.
+pgm_status take_event(pgm_graph *g, cudaEvent_t *out) {
+    if (g->capture_events) {
+        cudaEvent_t ev;
+        cudaError_t e = cudaEventCreate(&ev);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaEventCreate");
+        g->capture_events->push_back(ev);
+        *out = ev;
         return PGM_OK;
     }
-    while (g->events.size() < g->events_used + 3) {
+    if (g->events.size() <= g->events_used) {
         cudaEvent_t ev;
         cudaError_t e = cudaEventCreate(&ev);
         if (e != cudaSuccess) return cuda_fail(e, "cudaEventCreate");
         g->events.push_back(ev);
     }
-    *a = g->events[g->events_used];
-    *b = g->events[g->events_used + 1];
-    *c = g->events[g->events_used + 2];
-    g->events_used += 3;
+    *out = g->events[g->events_used++];
+    return PGM_OK;
+}
+
+// Adds the durations of recorded sampled iterations to the graph's per-launch totals
+// (waits for each iteration's last event).
+pgm_status accumulate_groups(pgm_graph *g, const std::vector<cudaEvent_t> &ev, const std::vector<ProfGroup> &groups) {
+    for (const ProfGroup &grp : groups) {
+        const int n = grp.nv + grp.nf;
+        cudaError_t e = cudaEventSynchronize(ev[grp.first + n]);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaEventSynchronize");
+        if ((int)g->launch_ms.size() < n) {
+            g->launch_ms.resize(n, 0.0);
+            g->launch_n.resize(n, 0);
+        }
+        for (int i = 0; i < n; ++i) {
+            float dt = 0.f;
+            cudaEventElapsedTime(&dt, ev[grp.first + i], ev[grp.first + i + 1]);
+            g->launch_ms[i] += dt;
+            g->launch_n[i] += 1;
+            (i < grp.nv ? g->graph_var_ms : g->graph_factor_ms) += dt;
+        }
+        g->prof_var_launches += grp.nv;
+        g->prof_factor_launches += grp.nf;
+    }
     return PGM_OK;
 }
 
@@ -726,32 +755,49 @@ static pgm_status enqueue_iterations(pgm_graph *g, const float *log_pot, const f
         if (e == cudaSuccess) e = launch_lr_params(g->G, g->P, log_pot, g->lr_prm, s);
         if (e != cudaSuccess) return cuda_fail(e, "log-ratio pack launch");
     }
+    // per-launch timing: an event before the iteration and one after each launch
+    struct HookCtx {
+        pgm_graph *g;
+        cudaStream_t s;
+        unsigned flags;
+        int count;
+        pgm_status st;
+    };
+    auto after_launch = [](void *p) {
+        HookCtx *c = static_cast<HookCtx *>(p);
+        ++c->count;
+        if (c->st != PGM_OK) return;
+        cudaEvent_t ev = nullptr;
+        c->st = take_event(c->g, &ev);
+        if (c->st == PGM_OK) cudaEventRecordWithFlags(ev, c->s, c->flags);
+    };
     for (int it = 0; it < n_iters; ++it) {
-        cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr;
         const bool prof = profile && g->profiling > 0 && (it % g->profiling) == g->profiling - 1;
         // inside a stream capture the records become event nodes of the graph
-        const unsigned rec_flags = g->capture_events ? cudaEventRecordExternal : cudaEventRecordDefault;
+        HookCtx ctx{g, s, g->capture_events ? (unsigned)cudaEventRecordExternal : (unsigned)cudaEventRecordDefault, 0,
+                    PGM_OK};
+        const LaunchHook hook{after_launch, &ctx};
+        ProfGroup grp{};
         if (prof) {
-            pgm_status ps = take_events(g, &e0, &e1, &e2);
+            grp.first = (uint32_t)(g->capture_events ? g->capture_events->size() : g->events_used);
+            cudaEvent_t e0 = nullptr;
+            pgm_status ps = take_event(g, &e0);
             if (ps != PGM_OK) return ps;
-            cudaEventRecordWithFlags(e0, s, rec_flags);
+            cudaEventRecordWithFlags(e0, s, ctx.flags);
         }
-        cudaError_t e = lr ? launch_lr_var_pass(g->G, g->P, evidence, d, Dv, lam, s)
-                           : launch_var_pass(g->G, g->P, evidence, cur, g->b, kVarIter, nullptr, s);
+        const LaunchHook *h = prof ? &hook : nullptr;
+        cudaError_t e = lr ? launch_lr_var_pass(g->G, g->P, evidence, d, Dv, lam, s, h)
+                           : launch_var_pass(g->G, g->P, evidence, cur, g->b, kVarIter, nullptr, s, 1, h);
         if (e != cudaSuccess) return cuda_fail(e, "variable pass launch");
-        if (prof) cudaEventRecordWithFlags(e1, s, rec_flags);
-        e = lr ? launch_lr_factor_pass(g->G, g->P, log_pot, g->lr_prm, Dv, lam, d, T, damping, s)
-               : launch_factor_pass(g->G, g->P, log_pot, g->b, evidence, cur, nxt, T, damping, s);
+        grp.nv = (uint16_t)ctx.count;
+        ctx.count = 0;
+        e = lr ? launch_lr_factor_pass(g->G, g->P, log_pot, g->lr_prm, Dv, lam, d, T, damping, s, h)
+               : launch_factor_pass(g->G, g->P, log_pot, g->b, evidence, cur, nxt, T, damping, s, 1, h);
         if (e != cudaSuccess) return cuda_fail(e, "factor pass launch");
+        grp.nf = (uint16_t)ctx.count;
         if (prof) {
-            cudaEventRecordWithFlags(e2, s, rec_flags);
-            if (g->capture_events) {
-                g->capture_nv += g->var_launches;
-                g->capture_nf += g->factor_launches;
-            } else {
-                g->prof_var_launches += g->var_launches;
-                g->prof_factor_launches += g->factor_launches;
-            }
+            if (ctx.st != PGM_OK) return ctx.st;
+            (g->capture_groups ? *g->capture_groups : g->prof_groups).push_back(grp);
         }
         if (!lr) std::swap(cur, nxt);
     }
@@ -777,18 +823,7 @@ static uint32_t float_bits(float x) {
 static pgm_status collect_run_times(pgm_graph *g, pgm_graph::CachedRun &r) {
     if (!r.pending) return PGM_OK;
     r.pending = false;
-    for (size_t k = 0; k + 3 <= r.ev.size(); k += 3) {
-        cudaError_t e = cudaEventSynchronize(r.ev[k + 2]);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaEventSynchronize");
-        float a = 0.f, b = 0.f;
-        cudaEventElapsedTime(&a, r.ev[k], r.ev[k + 1]);
-        cudaEventElapsedTime(&b, r.ev[k + 1], r.ev[k + 2]);
-        g->graph_var_ms += a;
-        g->graph_factor_ms += b;
-    }
-    g->prof_var_launches += r.nv;
-    g->prof_factor_launches += r.nf;
-    return PGM_OK;
+    return accumulate_groups(g, r.ev, r.groups);
 }
 
 static void destroy_run(pgm_graph::CachedRun &r) {
@@ -818,11 +853,13 @@ static pgm_status cached_run(pgm_graph *g, const float *log_pot, const float *ev
     cudaError_t e = cudaStreamBeginCapture(g->capture_stream, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamBeginCapture");
     std::vector<cudaEvent_t> events;
+    std::vector<ProfGroup> groups;
     g->capture_events = &events;
-    g->capture_nv = g->capture_nf = 0;
+    g->capture_groups = &groups;
     pgm_status st = enqueue_iterations(g, log_pot, evidence, T, damping, n_iters, msgs, g->capture_stream,
                                        g->profiling > 0);
     g->capture_events = nullptr;
+    g->capture_groups = nullptr;
     cudaGraph_t graph = nullptr;
     e = cudaStreamEndCapture(g->capture_stream, &graph);
     auto drop_events = [&]() {
@@ -852,8 +889,7 @@ static pgm_status cached_run(pgm_graph *g, const float *log_pot, const float *ev
     }
     pgm_graph::CachedRun r{log_pot, evidence, msgs, tb, db, n_iters, g->profiling, exec, ++g->use_clock};
     r.ev = std::move(events);
-    r.nv = g->capture_nv;
-    r.nf = g->capture_nf;
+    r.groups = std::move(groups);
     g->runs.push_back(std::move(r));
     *out = exec;
     *run = &g->runs.back();
@@ -1411,7 +1447,7 @@ pgm_status pgm_run_bp(pgm_graph *g, const float *log_pot, const float *evidence,
         if (st != PGM_OK) return st;
         cudaError_t e = cudaGraphLaunch(exec, s);
         if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
-        run->pending = !run->ev.empty();
+        run->pending = !run->groups.empty();
         return PGM_OK;
     }
     return enqueue_iterations(g, log_pot, evidence, T, damping, n_iters, msgs, s, true);
@@ -1888,31 +1924,52 @@ pgm_status pgm_set_profiling(pgm_graph *g, int32_t period) {
     return PGM_OK;
 }
 
-pgm_status pgm_pass_times(pgm_graph *g, double *var_ms, double *factor_ms, int64_t *n_var,
-                          int64_t *n_factor) {
-    if (!g) return fail(PGM_EINVAL, "graph is NULL");
-    DeviceGuard dg(g->device);
+// Moves every recorded sampled iteration (cached-graph replays and direct launches) into
+// the per-launch totals.
+static pgm_status collect_all_times(pgm_graph *g) {
     for (auto &r : g->runs) {
         pgm_status st = collect_run_times(g, r);
         if (st != PGM_OK) return st;
     }
-    double tv = g->graph_var_ms, tf = g->graph_factor_ms;
+    pgm_status st = accumulate_groups(g, g->events, g->prof_groups);
+    g->prof_groups.clear();
+    g->events_used = 0;
+    return st;
+}
+
+static void reset_times(pgm_graph *g) {
+    g->launch_ms.clear();
+    g->launch_n.clear();
     g->graph_var_ms = g->graph_factor_ms = 0.0;
-    for (size_t k = 0; k + 3 <= g->events_used; k += 3) {
-        cudaError_t e = cudaEventSynchronize(g->events[k + 2]);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaEventSynchronize");
-        float a = 0.f, b = 0.f;
-        cudaEventElapsedTime(&a, g->events[k], g->events[k + 1]);
-        cudaEventElapsedTime(&b, g->events[k + 1], g->events[k + 2]);
-        tv += a;
-        tf += b;
-    }
-    if (var_ms) *var_ms = tv;
-    if (factor_ms) *factor_ms = tf;
+    g->prof_var_launches = g->prof_factor_launches = 0;
+}
+
+pgm_status pgm_pass_times(pgm_graph *g, double *var_ms, double *factor_ms, int64_t *n_var,
+                          int64_t *n_factor) {
+    if (!g) return fail(PGM_EINVAL, "graph is NULL");
+    DeviceGuard dg(g->device);
+    pgm_status st = collect_all_times(g);
+    if (st != PGM_OK) return st;
+    if (var_ms) *var_ms = g->graph_var_ms;
+    if (factor_ms) *factor_ms = g->graph_factor_ms;
     if (n_var) *n_var = g->prof_var_launches;
     if (n_factor) *n_factor = g->prof_factor_launches;
-    g->events_used = 0;
-    g->prof_var_launches = g->prof_factor_launches = 0;
+    reset_times(g);
+    return PGM_OK;
+}
+
+pgm_status pgm_launch_times(pgm_graph *g, int32_t n, double *ms, int64_t *count, int32_t *n_positions) {
+    if (!g || n < 0 || (n > 0 && (!ms || !count))) return fail(PGM_EINVAL, "NULL argument or n < 0");
+    DeviceGuard dg(g->device);
+    pgm_status st = collect_all_times(g);
+    if (st != PGM_OK) return st;
+    const int np = (int)g->launch_ms.size();
+    for (int i = 0; i < n; ++i) {
+        ms[i] = i < np ? g->launch_ms[i] : 0.0;
+        count[i] = i < np ? g->launch_n[i] : 0;
+    }
+    if (n_positions) *n_positions = np;
+    reset_times(g);
     return PGM_OK;
 }
 

@@ -3417,10 +3417,11 @@ cudaError_t prepare_kernels(int max_smem_bytes) {
 
 template <int MODE, bool MS>
 static void var_pass_mode(const DevGraph &G, const Plan &P, const float *ev, const float *m,
-                          float *out, int32_t *dec, cudaStream_t s, int S) {
+                          float *out, int32_t *dec, cudaStream_t s, int S, const LaunchHook *hook) {
     if (G.vin_tab4 != nullptr) {
         const int n = G.V;
         k_var_tab4<MODE, MS><<<dim3((n + 255) / 256, S), 256, 0, s>>>(G, n, ev, m, out, dec);
+        if (hook) hook->after(hook->ctx);
         return;
     }
     for (const VarLaunch &L : P.var) {
@@ -3448,23 +3449,24 @@ static void var_pass_mode(const DevGraph &G, const Plan &P, const float *ev, con
                 k_var_thread<0, MODE, MS><<<dim3(L.n_blocks, S), L.threads, 0, s>>>(G, L.list, L.n, 0, ev, m, out, dec);
                 break;
         }
+        if (hook) hook->after(hook->ctx);
     }
 }
 
 cudaError_t launch_var_pass(const DevGraph &G, const Plan &P, const float *ev, const float *m,
-                            float *b, int mode, int32_t *decode, cudaStream_t s, int S) {
-    if (mode == kVarIter && S > 1) var_pass_mode<kVarIter, true>(G, P, ev, m, b, decode, s, S);
-    else if (mode == kVarIter) var_pass_mode<kVarIter, false>(G, P, ev, m, b, decode, s, 1);
-    else if (mode == kVarBeliefs) var_pass_mode<kVarBeliefs, false>(G, P, ev, m, b, decode, s, 1);
-    else if (mode == kVarNormalised) var_pass_mode<kVarNormalised, false>(G, P, ev, m, b, decode, s, 1);
-    else var_pass_mode<kVarDecode, false>(G, P, ev, m, b, decode, s, 1);
+                            float *b, int mode, int32_t *decode, cudaStream_t s, int S, const LaunchHook *hook) {
+    if (mode == kVarIter && S > 1) var_pass_mode<kVarIter, true>(G, P, ev, m, b, decode, s, S, hook);
+    else if (mode == kVarIter) var_pass_mode<kVarIter, false>(G, P, ev, m, b, decode, s, 1, hook);
+    else if (mode == kVarBeliefs) var_pass_mode<kVarBeliefs, false>(G, P, ev, m, b, decode, s, 1, hook);
+    else if (mode == kVarNormalised) var_pass_mode<kVarNormalised, false>(G, P, ev, m, b, decode, s, 1, hook);
+    else var_pass_mode<kVarDecode, false>(G, P, ev, m, b, decode, s, 1, hook);
     return cudaGetLastError();
 }
 
 template <bool MAXP, bool MS>
 static void factor_pass_t(const DevGraph &G, const Plan &P, const float *pot, const float *b,
                           const float *ev, const float *m_old, float *m_new, float T, float damping,
-                          cudaStream_t s, int S) {
+                          cudaStream_t s, int S, const LaunchHook *hook) {
     const float invT = MAXP ? 0.f : 1.f / T;
     for (const FactorLaunch &L : P.factor) {
         if (L.n_blocks == 0) continue;
@@ -3507,6 +3509,7 @@ static void factor_pass_t(const DevGraph &G, const Plan &P, const float *pot, co
             default:
                 break;
         }
+        if (hook) hook->after(hook->ctx);
     }
 }
 
@@ -3528,14 +3531,17 @@ static cudaError_t launch_pdl(void (*kernel)(KArgs...), int blocks, int threads,
 }
 
 cudaError_t launch_lr_var_pass(const DevGraph &G, const Plan &P, const float *ev, const float *d, float2 *Dv,
-                               float *lam, cudaStream_t s) {
+                               float *lam, cudaStream_t s, const LaunchHook *hook) {
     cudaError_t e = cudaSuccess;
     if (G.vin_tab4 != nullptr) {
         e = launch_pdl(k_var_slot4_lr, (G.V + 255) / 256, 256, s, G.V, ev, d, Dv, lam);
+        if (hook && e == cudaSuccess) hook->after(hook->ctx);
     } else {
         for (const VarLaunch &L : P.var)
-            if (L.n > 0 && e == cudaSuccess)
+            if (L.n > 0 && e == cudaSuccess) {
                 e = launch_pdl(k_var_csr_lr, L.n_blocks, L.threads, s, G, L.list, L.n, ev, d, lam);
+                if (hook && e == cudaSuccess) hook->after(hook->ctx);
+            }
     }
     return e != cudaSuccess ? e : cudaGetLastError();
 }
@@ -3551,7 +3557,7 @@ cudaError_t launch_lr_params(const DevGraph &G, const Plan &P, const float *log_
 
 cudaError_t launch_lr_factor_pass(const DevGraph &G, const Plan &P, const float *log_pot, const float *prm,
                                   const float2 *Dv, const float *lam, float *d, float T, float damping,
-                                  cudaStream_t s) {
+                                  cudaStream_t s, const LaunchHook *hook) {
     // lse2_fast constants: k = log2(e) / T, T ln 2
     const float k = T > 0.f ? (float)(1.4426950408889634 / (double)T) : 0.f;
     const float Tln2 = (float)((double)T * 0.6931471805599453);
@@ -3568,6 +3574,7 @@ cudaError_t launch_lr_factor_pass(const DevGraph &G, const Plan &P, const float 
         cudaError_t e = launch_pdl(kern, blocks, 256, s, es, L.n_seg, F, G.V, pos2, (const float *)prm, log_pot,
                                    Dv, lam, d, G.flags, k, Tln2, damping);
         if (e != cudaSuccess) return e;
+        if (hook) hook->after(hook->ctx);
     }
     return cudaGetLastError();
 }
@@ -3678,13 +3685,14 @@ cudaError_t launch_lr_unpack(const DevGraph &G, const float *d, float *m, cudaSt
 
 cudaError_t launch_factor_pass(const DevGraph &G, const Plan &P, const float *log_pot,
                                const float *b, const float *ev, const float *m_old,
-                               float *m_new, float T, float damping, cudaStream_t s, int S) {
+                               float *m_new, float T, float damping, cudaStream_t s, int S,
+                               const LaunchHook *hook) {
     if (S > 1) {  // the multi-sample instantiations
-        if (T == 0.f) factor_pass_t<true, true>(G, P, log_pot, b, ev, m_old, m_new, T, damping, s, S);
-        else factor_pass_t<false, true>(G, P, log_pot, b, ev, m_old, m_new, T, damping, s, S);
+        if (T == 0.f) factor_pass_t<true, true>(G, P, log_pot, b, ev, m_old, m_new, T, damping, s, S, hook);
+        else factor_pass_t<false, true>(G, P, log_pot, b, ev, m_old, m_new, T, damping, s, S, hook);
     } else {
-        if (T == 0.f) factor_pass_t<true, false>(G, P, log_pot, b, ev, m_old, m_new, T, damping, s, 1);
-        else factor_pass_t<false, false>(G, P, log_pot, b, ev, m_old, m_new, T, damping, s, 1);
+        if (T == 0.f) factor_pass_t<true, false>(G, P, log_pot, b, ev, m_old, m_new, T, damping, s, 1, hook);
+        else factor_pass_t<false, false>(G, P, log_pot, b, ev, m_old, m_new, T, damping, s, 1, hook);
     }
     return cudaGetLastError();
 }

@@ -122,9 +122,9 @@ __device__ __forceinline__ float lse_pair(float a, float b, float T, float invT)
 
 __device__ __forceinline__ void norm2(float &a, float &b, unsigned *status) {
     const float mx = fmaxf(a, b);
-    if (mx == ninf()) {
+    if (mx == ninf()) {  // a contradiction: the message becomes 0 and the status records it
         a = b = 0.f;
-        atomicOr(status, 1u);
+        atomicOr(status, PGM_FLAG_CONTRADICTION);
         return;
     }
     a -= mx;
@@ -224,8 +224,9 @@ extern "C" pgm_status pgm_grid2_run_bp_noalloc(int32_t rows, int32_t cols, const
     unsigned *status = reinterpret_cast<unsigned *>(scratch);
     float *m_tmp = scratch + kStatusFloats;
     float *b = m_tmp + ES;
-    // the status word is the only scratch that must start at zero; the message buffer
-    // and the beliefs are fully written before they are read
+    // the status word is the only scratch that must start at zero (it then holds this
+    // call's PGM_FLAG_* bits, read with pgm_grid2_noalloc_flags); the message buffer and
+    // the beliefs are fully written before they are read
     e = cudaMemsetAsync(status, 0, sizeof(unsigned), s);
     if (e != cudaSuccess) return pgm::set_last_error(PGM_ECUDA, std::string("cudaMemsetAsync: ") + cudaGetErrorString(e));
     const float invT = T > 0.f ? 1.f / T : 0.f;
@@ -246,6 +247,24 @@ extern "C" pgm_status pgm_grid2_run_bp_noalloc(int32_t rows, int32_t cols, const
     if (cur != msgs) {
         e = cudaMemcpyAsync(msgs, cur, (size_t)ES * sizeof(float), cudaMemcpyDeviceToDevice, s);
         if (e != cudaSuccess) return pgm::set_last_error(PGM_ECUDA, std::string("cudaMemcpyAsync: ") + cudaGetErrorString(e));
+    }
+    return PGM_OK;
+}
+
+extern "C" pgm_status pgm_grid2_noalloc_flags(uint32_t *flags, int32_t clear, void *stream) {
+    if (!flags) return pgm::set_last_error(PGM_EINVAL, "flags is NULL");
+    float *scratch = nullptr;
+    cudaError_t e = scratch_for_current_device(&scratch);
+    if (e != cudaSuccess)
+        return pgm::set_last_error(PGM_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return pgm::set_last_error(PGM_ECUDA, std::string("cudaStreamSynchronize: ") + cudaGetErrorString(e));
+    e = cudaMemcpy(flags, scratch, sizeof(uint32_t), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return pgm::set_last_error(PGM_ECUDA, std::string("cudaMemcpy: ") + cudaGetErrorString(e));
+    if (clear) {
+        e = cudaMemset(scratch, 0, sizeof(uint32_t));
+        if (e != cudaSuccess) return pgm::set_last_error(PGM_ECUDA, std::string("cudaMemset: ") + cudaGetErrorString(e));
     }
     return PGM_OK;
 }

@@ -203,13 +203,21 @@ struct HostLayout {
 // arrays hold the members one after the other. Returns "" on success, else an error.
 std::string compile_graph(const void *const *descs, int n_desc, HostLayout *out);
 
+// Called by a pass launcher after each of its kernel launches (per-launch event timing).
+struct LaunchHook {
+    void (*after)(void *ctx);
+    void *ctx;
+};
+
 // Kernel launchers (kernels.cu). Each returns cudaGetLastError() of its launches.
 // (n_samples > 1: samples as the launches' y dimension, at the strides of G)
 cudaError_t launch_var_pass(const DevGraph &G, const Plan &P, const float *ev, const float *m,
-                            float *b, int mode, int32_t *decode, cudaStream_t s, int n_samples = 1);
+                            float *b, int mode, int32_t *decode, cudaStream_t s, int n_samples = 1,
+                            const LaunchHook *hook = nullptr);
 cudaError_t launch_factor_pass(const DevGraph &G, const Plan &P, const float *log_pot,
                                const float *b, const float *ev, const float *m_old,
-                               float *m_new, float T, float damping, cudaStream_t s, int n_samples = 1);
+                               float *m_new, float T, float damping, cudaStream_t s, int n_samples = 1,
+                               const LaunchHook *hook = nullptr);
 // Log-ratio iteration of a Plan::lr graph (kernels.cu): d the factor-to-variable
 // messages, lam the variable-to-factor values, one log-ratio per edge in variable order
 // (slots DevGraph::lr_pos; 4V of them with vin_tab4, else E); the factor pass updates d
@@ -218,12 +226,12 @@ cudaError_t launch_factor_pass(const DevGraph &G, const Plan &P, const float *lo
 // total Dv[V] (lam only for variables that need the explicit sums) and the factor pass
 // forms lam from it; otherwise lam is written and read.
 cudaError_t launch_lr_var_pass(const DevGraph &G, const Plan &P, const float *ev, const float *d, float2 *Dv,
-                               float *lam, cudaStream_t s);
+                               float *lam, cudaStream_t s, const LaunchHook *hook = nullptr);
 // Per run: each factor's table as the three differences the update depends on (prm[3F]).
 cudaError_t launch_lr_params(const DevGraph &G, const Plan &P, const float *log_pot, float *prm, cudaStream_t s);
 cudaError_t launch_lr_factor_pass(const DevGraph &G, const Plan &P, const float *log_pot, const float *prm,
                                   const float2 *Dv, const float *lam, float *d, float T, float damping,
-                                  cudaStream_t s);
+                                  cudaStream_t s, const LaunchHook *hook = nullptr);
 // Many samples of one 4-slot log-ratio graph (sample index innermost; Sp = S for
 // per-sample potentials, else 1): per run, the transposed evidence ev_s[V S], packed
 // messages d[4V S] and table differences prm[3 F Sp]; per iteration, the variable pass

@@ -107,3 +107,39 @@ def _argmax(nb, vs):
     for v in range(len(vs) - 1):
         out[v] = int(np.argmax(nb[vs[v]:vs[v + 1]]))
     return out
+
+
+def horizon_stats(gpu_nb, gpu_dec, nb0, spread, unstable, num_states, tie=TIE):
+    """Figures of a long run against the oracle and its ensemble: |gpu - oracle| (max,
+    99th percentile, median), the ensemble spread (max, median, fraction above 1e-4), the
+    fraction of entries the GPU moves by more than 1e-4, and how many variables the GPU
+    decodes differently from the FP64 oracle -- split into ensemble-unstable ones (the
+    nearby FP64 runs disagree among themselves), oracle ties and stable ones."""
+    g = np.asarray(gpu_nb, np.float64)
+    fin = np.isfinite(nb0)
+    with np.errstate(invalid="ignore"):
+        err = np.abs(g - nb0)[fin]
+    spr = spread[fin]
+    vs = np.concatenate([[0], np.cumsum(num_states)])
+    am = _argmax(nb0, vs)
+    dec = np.asarray(gpu_dec)
+    diff = np.flatnonzero(dec != am)
+    n_unst = n_tie = n_stable = 0
+    for v in diff:
+        b = nb0[vs[v]:vs[v + 1]]
+        d = int(dec[v])
+        if unstable[v]:
+            n_unst += 1
+        elif 0 <= d < b.size and b[d] >= b.max() - tie:
+            n_tie += 1
+        else:
+            n_stable += 1
+    q = lambda a, f: float(np.quantile(a, f)) if a.size else 0.0
+    return {"err_max": float(err.max()) if err.size else 0.0, "err_p99": q(err, 0.99), "err_median": q(err, 0.5),
+            "err_frac_above_1e-4": float((err > 1e-4).mean()) if err.size else 0.0,
+            "spread_max": float(spr.max()) if spr.size else 0.0, "spread_p99": q(spr, 0.99),
+            "spread_median": q(spr, 0.5), "spread_frac_above_1e-4": float((spr > 1e-4).mean()) if spr.size else 0.0,
+            "ratio_max": float(np.max(err / (1e-4 + spr))) if err.size else 0.0,
+            "decode_diff": int(diff.size), "decode_diff_unstable": n_unst, "decode_diff_tie": n_tie,
+            "decode_diff_stable": n_stable, "unstable_vars": int(np.asarray(unstable).sum()),
+            "n_vars": int(len(num_states))}

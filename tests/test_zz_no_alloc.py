@@ -1,4 +1,5 @@
-"""The allocation-free grid entry point (pgm_grid2_run_bp_noalloc) against pgm_run_bp.
+"""The allocation-free grid entry point (pgm_grid2_run_bp_noalloc) against pgm_run_bp and
+the FP64 oracle.
 
 Some callers cannot allocate device memory (a process whose device memory is owned and
 budgeted by a host framework, or code that must not call cudaMalloc after start-up);
@@ -9,7 +10,9 @@ every other test; it must pass alone in a fresh process and after the other test
 import numpy as np
 import pytest
 
+import oracle
 from paper_2202_04110_gb300 import workloads as W
+from tests._parity import assert_beliefs_close
 
 pytestmark = pytest.mark.gpu
 
@@ -35,6 +38,12 @@ def _reference(binding, p, T, n_iters):
     return g, lp, ev, m
 
 
+def _oracle_nb(p, T, n_iters):
+    om, ofl = oracle.run_bp(p.graph, p.log_pot, p.evidence, T, p.damping, n_iters)
+    _, onb, _, ofl2 = oracle.beliefs(p.graph, p.evidence, om)
+    return onb, ofl | ofl2
+
+
 @pytest.mark.parametrize("shape,T,n_iters", [((37, 53), 1.0, 25), ((64, 1), 0.0, 12), ((200, 300), 1.0, 31)])
 def test_noalloc_matches_run_bp_twice(gpu, shape, T, n_iters):
     import torch
@@ -42,15 +51,89 @@ def test_noalloc_matches_run_bp_twice(gpu, shape, T, n_iters):
     p = W.ising_grid(rows, cols, seed=rows + cols, T=T, n_iters=n_iters)
     g, lp, ev, m_ref = _reference(gpu, p, T, n_iters)
     nb_ref = g.beliefs(ev, m_ref, True)
+    onb, _ = _oracle_nb(p, T, n_iters)
     for call in range(2):  # the second call reuses the static scratch the first one left behind
         m = torch.zeros_like(m_ref)
         gpu.grid2_run_bp_noalloc(rows, cols, lp, ev, T, p.damping, n_iters, m)
         torch.cuda.synchronize()
         np.testing.assert_allclose(m.cpu().numpy(), m_ref.cpu().numpy(), atol=1e-4, rtol=0,
                                    err_msg=f"messages, call {call}")
-        nb = g.beliefs(ev, m, True)
-        np.testing.assert_allclose(nb.cpu().numpy(), nb_ref.cpu().numpy(), atol=1e-4, rtol=0,
-                                   err_msg=f"beliefs, call {call}")
+        nb = g.beliefs(ev, m, True).cpu().numpy()
+        np.testing.assert_allclose(nb, nb_ref.cpu().numpy(), atol=1e-4, rtol=0, err_msg=f"beliefs, call {call}")
+        assert_beliefs_close(nb, onb, what=f"noalloc vs oracle, call {call}")
+        assert gpu.grid2_noalloc_flags(clear=True) == 0
+
+
+def _hard_grid(rows, cols, seed, scale):
+    """An Ising grid with couplings scale * U[-1, 1] and fields scale * N(0, 1), a fifth
+    of the cells clamped by hard evidence (one state at -inf). With scale > 128 the
+    stored messages exceed the kernels' threshold for b - m, so every factor takes its
+    variable-to-factor values from explicit leave-one-out sums."""
+    p = W.ising_grid(rows, cols, seed=seed, T=1.0)
+    rng = np.random.default_rng(seed + 1)
+    lp = (p.log_pot * scale).astype(np.float32)
+    ev = (p.evidence * scale).reshape(-1, 2)
+    clamp = rng.random(rows * cols) < 0.2
+    state = rng.integers(0, 2, rows * cols)
+    ev[clamp, 1 - state[clamp]] = -np.inf
+    p.log_pot = lp
+    p.evidence = ev.astype(np.float32).ravel()
+    return p
+
+
+@pytest.mark.parametrize("T", [0.0, 1.0])
+@pytest.mark.parametrize("scale", [1.0, 300.0])
+def test_noalloc_hard_evidence_and_large_messages(gpu, T, scale):
+    """-inf evidence on a fifth of the cells; with scale 300 the messages exceed 128, the
+    recompute branch of the factor kernel. Against pgm_run_bp and the oracle, twice."""
+    import torch
+    rows, cols, n_iters = 29, 31, 20
+    p = _hard_grid(rows, cols, 11, scale)
+    g, lp, ev, m_ref = _reference(gpu, p, T, n_iters)
+    nb_ref = g.beliefs(ev, m_ref, True).cpu().numpy()
+    onb, ofl = _oracle_nb(p, T, n_iters)
+    for call in range(2):
+        m = torch.zeros_like(m_ref)
+        gpu.grid2_run_bp_noalloc(rows, cols, lp, ev, T, 0.5, n_iters, m)
+        nb = g.beliefs(ev, m, True).cpu().numpy()
+        assert_beliefs_close(nb, nb_ref, what=f"noalloc vs pgm_run_bp, call {call}")
+        assert_beliefs_close(nb, onb, what=f"noalloc vs oracle, call {call}")
+        assert gpu.grid2_noalloc_flags(clear=True) == (ofl & oracle.FLAG_CONTRADICTION), call
+
+
+def test_noalloc_contradiction_flag(gpu):
+    """A 3 x 3 grid whose centre is forced to 0 by its upper neighbour and to 1 by its left
+    neighbour (hard evidence and hard equality couplings): the centre's message towards its
+    right neighbour has both states at -inf, a contradiction that pgm_run_bp, the oracle and
+    the allocation-free call all report."""
+    import torch
+    p = W.ising_grid(3, 3, seed=0, T=1.0)
+    pairs = p.graph.enum_groups[0].vars
+    lp = np.tile(np.array([0.0, 0.3, -0.2, 0.1], np.float32), (pairs.shape[0], 1))
+    eq = np.array([0.0, -np.inf, -np.inf, 0.0], np.float32)
+    for f, (a, b) in enumerate(pairs):
+        if (a, b) in ((1, 4), (3, 4)):
+            lp[f] = eq
+    ev = np.zeros((9, 2), np.float32)
+    ev[1] = [0.0, -np.inf]   # (0, 1) forced to 0
+    ev[3] = [-np.inf, 0.0]   # (1, 0) forced to 1
+    p.log_pot, p.evidence = lp.ravel(), ev.ravel()
+    g, lp_d, ev_d, m_ref = _reference(gpu, p, 1.0, 6)
+    assert g.flags(clear=True) & gpu.FLAG_CONTRADICTION
+    onb, ofl = _oracle_nb(p, 1.0, 6)
+    assert ofl & oracle.FLAG_CONTRADICTION
+    gpu.grid2_noalloc_flags(clear=True)
+    m = torch.zeros_like(m_ref)
+    gpu.grid2_run_bp_noalloc(3, 3, lp_d, ev_d, 1.0, 0.5, 6, m)
+    assert gpu.grid2_noalloc_flags() & gpu.FLAG_CONTRADICTION
+    np.testing.assert_array_equal(np.isneginf(m.cpu().numpy()), np.isneginf(m_ref.cpu().numpy()))
+    fin = np.isfinite(m_ref.cpu().numpy())
+    np.testing.assert_allclose(m.cpu().numpy()[fin], m_ref.cpu().numpy()[fin], atol=1e-4, rtol=0)
+    # the next call starts from a clear status word
+    p2 = W.ising_grid(3, 3, seed=1, T=1.0)
+    gpu.grid2_run_bp_noalloc(3, 3, torch.as_tensor(p2.log_pot).cuda(), torch.as_tensor(p2.evidence).cuda(),
+                             1.0, 0.5, 6, torch.zeros_like(m_ref))
+    assert gpu.grid2_noalloc_flags(clear=True) == 0
 
 
 def test_noalloc_warm_start_and_odd_counts(gpu):
@@ -63,11 +146,18 @@ def test_noalloc_warm_start_and_odd_counts(gpu):
     np.testing.assert_allclose(m.cpu().numpy(), m_ref.cpu().numpy(), atol=1e-4, rtol=0)
 
 
-def test_noalloc_rejects_oversized_grid(gpu):
+def test_noalloc_size_limit(gpu):
+    """4 * (2 r c - r - c) + 2 r c <= 4,194,304 floats: 648 x 648 (4,193,856) runs and
+    matches pgm_run_bp; 649 x 649 (4,206,818) is rejected."""
     import torch
-    rows = cols = 700  # 4 * 978,600 factors + 2 * 490,000 variables > 4,194,304 floats
-    ev = torch.zeros(2 * rows * cols, device="cuda")
+    p = W.ising_grid(648, 648, seed=5, T=1.0, n_iters=4)
+    g, lp, ev, m_ref = _reference(gpu, p, 1.0, 4)
+    m = torch.zeros_like(m_ref)
+    gpu.grid2_run_bp_noalloc(648, 648, lp, ev, 1.0, 0.5, 4, m)
+    np.testing.assert_allclose(m.cpu().numpy(), m_ref.cpu().numpy(), atol=1e-4, rtol=0)
+    rows = cols = 649
     F = rows * (cols - 1) + (rows - 1) * cols
+    ev = torch.zeros(2 * rows * cols, device="cuda")
     lp = torch.zeros(4 * F, device="cuda")
     m = torch.zeros(4 * F, device="cuda")
     with pytest.raises(gpu.PgmError) as ei:
