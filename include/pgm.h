@@ -442,6 +442,16 @@ pgm_status pgm_run_bp_until_members(pgm_graph *g, const float *log_pot, const fl
  * PGM_EINVAL.
  */
 #define PGM_OPT_ENUM_BLOCK 3
+/*
+ * PGM_OPT_PAIR_FORM (default 0): the kernel form of dense K-state pairwise groups (K = 4,
+ * 8, 16). 0 the compiler's choice (K = 4 and tables per factor: a thread per factor; K =
+ * 8 and 16 with a table shared by the group: K / 4 lanes per factor, four states each),
+ * 1 a thread per factor, 2 K lanes per factor, 3 K / 4 lanes where the compiler chose it
+ * (else a thread per factor). The thread and K / 4-lane forms give the same bits.
+ * Blocking like PGM_OPT_ENUM_BLOCK; pgm_autotune may change the forms afterwards.
+ * Values outside 0..3: PGM_EINVAL.
+ */
+#define PGM_OPT_PAIR_FORM 4
 pgm_status pgm_set_option(pgm_graph *g, int32_t option, int64_t value);
 /*
  * The option's effective value in *value: for PGM_OPT_CUDA_GRAPH and
@@ -454,8 +464,9 @@ pgm_status pgm_get_option(const pgm_graph *g, int32_t option, int64_t *value);
 /*
  * Launch-shape autotuner: for every factor-pass launch of the graph (one per kernel
  * variant, covering all groups of that variant) times each thread-block shape the
- * kernel allows, and for dense K-state pairwise launches (K = 4, 8, 16) both kernel
- * forms (K lanes per factor, thread per factor), for listed-configuration launches both
+ * kernel allows, and for dense K-state pairwise launches (K = 4, 8, 16) every kernel
+ * form (K lanes per factor, thread per factor, and for shared tables K / 4 lanes per
+ * factor), for listed-configuration launches both
  * forms (thread per factor, block per run of factors; the former only where every group
  * fits it) -- threads per block for the thread-per-factor kernels, warps per
  * block (factors per block) for the warp-per-factor logical kernel -- on the given
@@ -474,9 +485,10 @@ pgm_status pgm_autotune(pgm_graph *g, const float *log_pot, const float *evidenc
  * kind 1 = factor pass (variant: 0 dense pairwise K = 2; 1..3 dense pairwise K = 4, 8,
  * 16 with K lanes per factor; 4 listed configurations; 5 OR/AND thread per factor; 6
  * OR/AND warp per factor; 7..9 dense pairwise K = 4, 8, 16 with a thread per factor,
- * the default form, which pgm_autotune may exchange with 1..3; 10 listed configurations
- * with a block per run of factors); threads per block and blocks. Any output pointer
- * may be NULL.
+ * the default form for K = 4 and per-factor tables, which pgm_autotune may exchange with
+ * 1..3; 10 listed configurations with a block per run of factors; 11, 12 dense pairwise
+ * K = 8, 16 with K / 4 lanes per factor, the default form for shared tables); threads
+ * per block and blocks. Any output pointer may be NULL.
  */
 pgm_status pgm_launch_info(const pgm_graph *g, int32_t i, int32_t *kind, int32_t *variant,
                            int32_t *threads, int32_t *n_blocks);

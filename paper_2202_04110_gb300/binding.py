@@ -29,6 +29,7 @@ EXPORTED = ["pgm_build", "pgm_build_batch", "pgm_batch_member", "pgm_check_desc"
 OPT_CUDA_GRAPH = 1
 OPT_LOG_RATIO = 2
 OPT_ENUM_BLOCK = 3
+OPT_PAIR_FORM = 4
 
 
 class PgmError(RuntimeError):

@@ -127,6 +127,7 @@ struct pgm_graph {
     FactorLaunch adj_logic_launch{};  // pgm_grad: logical groups, thread per factor (k_adj_logic)
     size_t adj_logic_seg_off = (size_t)-1;
     int32_t enum_block = 0;  // PGM_OPT_ENUM_BLOCK
+    int32_t pair_form = 0;   // PGM_OPT_PAIR_FORM
     std::vector<std::vector<char>> factor_segs_host;  // host copy of each factor launch's segments
     // CUDA graphs of whole pgm_run_bp calls, keyed by their arguments (LRU)
     struct CachedRun {
@@ -197,6 +198,8 @@ int lanes_per_factor(int variant) {
         case kPair4: return 4;
         case kPair8: return 8;
         case kPair16: return 16;
+        case kPairQ8: return 2;
+        case kPairQ16: return 4;
         case kLogicWarp: return 32;
         default: return 1;
     }
@@ -1453,20 +1456,18 @@ pgm_status pgm_run_bp(pgm_graph *g, const float *log_pot, const float *evidence,
     return enqueue_iterations(g, log_pot, evidence, T, damping, n_iters, msgs, s, true);
 }
 
-// The other kernel form for the same factors: dense K-state pairwise tables run either
-// with K lanes per factor (kPair4 / 8 / 16) or with a thread per factor (kPairT4 / 8 /
-// 16). -1 if there is none.
-static int alternative_form(int variant) {
-    switch (variant) {
-        case kPair4: return kPairT4;
-        case kPair8: return kPairT8;
-        case kPair16: return kPairT16;
-        case kPairT4: return kPair4;
-        case kPairT8: return kPair8;
-        case kPairT16: return kPair16;
-        case kEnumGeneric: return kEnumBlock;
-        case kEnumBlock: return kEnumGeneric;  // when every group fits (checked by the caller)
-        default: return -1;
+// The other kernel forms for the same factors: dense K-state pairwise tables run with K
+// lanes per factor (kPair4 / 8 / 16), a thread per factor (kPairT4 / 8 / 16) or, for
+// tables shared by the group, K / 4 lanes per factor (kPairQ8 / 16).
+static std::vector<int> alternative_forms(int base_variant, bool all_shared) {
+    switch (base_variant) {
+        case kPair4: case kPairT4: return {kPairT4, kPair4};
+        case kPair8: case kPairT8: case kPairQ8:
+            return all_shared ? std::vector<int>{kPairQ8, kPairT8, kPair8} : std::vector<int>{kPairT8, kPair8};
+        case kPair16: case kPairT16: case kPairQ16:
+            return all_shared ? std::vector<int>{kPairQ16, kPairT16, kPair16} : std::vector<int>{kPairT16, kPair16};
+        case kEnumGeneric: case kEnumBlock: return {kEnumGeneric, kEnumBlock};  // the former where every group fits
+        default: return {base_variant};
     }
 }
 
@@ -1476,6 +1477,7 @@ static std::vector<int> shape_candidates(int variant) {
         case kPair2: case kPair4: case kPair8: case kPair16: case kLogicSmall: return {64, 128, 256};
         case kPairT4: case kPairT8: return {64, 128, 256};
         case kPairT16: return {64, 128};
+        case kPairQ8: case kPairQ16: return {64, 128, 256};
         case kEnumGeneric: return {32, 64, 128};
         case kEnumBlock: return {128, 256};
         case kLogicWarp: return {32, 64, 128};
@@ -1547,9 +1549,15 @@ pgm_status pgm_autotune(pgm_graph *g, const float *log_pot, const float *evidenc
         int best = g->P.factor[li].threads, best_variant = orig_variant;
         float best_ms = 1e30f;
         // the kernel forms that can run this launch's groups, each with its block shapes
-        std::vector<int> forms{orig_variant};
-        const int alt = alternative_form(orig_variant);
-        if (alt >= 0) forms.push_back(alt);
+        bool all_shared = true;
+        {
+            const FactorLaunch &L0 = g->P.factor[li];
+            if (L0.variant != kLogicSmall && L0.variant != kLogicWarp) {
+                const EnumSeg *segs = reinterpret_cast<const EnumSeg *>(g->factor_segs_host[li].data());
+                for (int i = 0; i < L0.n_seg; ++i) all_shared = all_shared && segs[i].shared != 0;
+            }
+        }
+        const std::vector<int> forms = alternative_forms(g->P.factor[li].base_variant, all_shared);
         for (int variant : forms) {
             g->P.factor[li].variant = variant;
             for (int c : shape_candidates(variant)) {
@@ -1822,6 +1830,39 @@ pgm_status pgm_set_option(pgm_graph *g, int32_t option, int64_t value) {
             g->enum_block = (int32_t)value;
             return PGM_OK;
         }
+        case PGM_OPT_PAIR_FORM: {
+            if (value < 0 || value > 3) return fail(PGM_EINVAL, "PGM_OPT_PAIR_FORM must be 0..3");
+            DeviceGuard dg(g->device);
+            cudaError_t e = cudaDeviceSynchronize();  // a replay may be reading the segments
+            if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceSynchronize");
+            drop_cached_runs(g);
+            for (size_t li = 0; li < g->P.factor.size(); ++li) {
+                FactorLaunch &L = g->P.factor[li];
+                const int base = L.base_variant;
+                int K = 0;
+                if (base == kPairT4 || base == kPair4) K = 4;
+                else if (base == kPairT8 || base == kPairQ8 || base == kPair8) K = 8;
+                else if (base == kPairT16 || base == kPairQ16 || base == kPair16) K = 16;
+                if (K == 0) continue;
+                const int thr = K == 4 ? kPairT4 : K == 8 ? kPairT8 : kPairT16;
+                const int lanes = K == 4 ? kPair4 : K == 8 ? kPair8 : kPair16;
+                const int quad = K == 8 ? kPairQ8 : K == 16 ? kPairQ16 : thr;
+                // the K / 4-lane form runs shared tables only (the compiler's choice for them)
+                const int want = value == 0 ? base : value == 1 ? thr : value == 2 ? lanes
+                                                   : (base == kPairQ8 || base == kPairQ16 ? quad : thr);
+                if (L.variant == want) continue;
+                const int old_variant = L.variant;
+                L.variant = want;
+                if (!replan_factor_launch(g, li, want == kPairT16 ? 128 : 256, nullptr)) {
+                    L.variant = old_variant;
+                    return fail(PGM_ECUDA, "re-planning a pairwise launch failed");
+                }
+            }
+            e = cudaDeviceSynchronize();
+            if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceSynchronize");
+            g->pair_form = (int32_t)value;
+            return PGM_OK;
+        }
         default:
             return fail(PGM_EINVAL, "unknown option");
     }
@@ -1838,6 +1879,9 @@ pgm_status pgm_get_option(const pgm_graph *g, int32_t option, int64_t *value) {
             return PGM_OK;
         case PGM_OPT_ENUM_BLOCK:
             *value = g->enum_block;
+            return PGM_OK;
+        case PGM_OPT_PAIR_FORM:
+            *value = g->pair_form;
             return PGM_OK;
         default:
             return fail(PGM_EINVAL, "unknown option");

@@ -1536,6 +1536,222 @@ k_pair_thr(DevGraph G, const EnumSeg *__restrict__ segs, int n_seg, const float 
     store_n<K>(m_new + es1, o);
 }
 
+// ---- K / 4 lanes per factor, four consecutive states each (K = 8, 16, shared tables) ----
+//
+// The factor's L = K / 4 lanes form an aligned group of a warp: lane q loads the states
+// 4q..4q+3 of both stored messages and both beliefs (16-byte loads; the group reads each
+// vector as one contiguous run) and computes the outputs of those four states in both
+// directions. The input vector of a direction is exchanged through the group's slot of
+// shared memory, and each output state's row of the table (padded rows, conflict-free
+// float4 reads) is dotted with it. Per factor this spreads the thread form's work over L
+// lanes with a quarter of its registers, so four times as many factors are in flight per
+// SM. The arithmetic is the thread form's, term for term and in the same order (the
+// table rows in the same float4 chunks, the maxima exact), so both forms give the same
+// bits. The rare cases (an edge of a high-degree variable, a stored entry that is -inf
+// or large) go to pair_factor_rare on the group's first lane.
+
+template <int K>
+constexpr int kQRow = K + 4;  // padded row stride of the shared tables (floats)
+
+// Four consecutive floats: one 16-byte access when aligned (a batch member's arrays
+// start wherever the previous member's end), else four.
+__device__ __forceinline__ float4 ld4(const float *p, bool stream) {
+    if ((reinterpret_cast<uintptr_t>(p) & 15u) == 0)
+        return stream ? __ldcs(reinterpret_cast<const float4 *>(p)) : __ldg(reinterpret_cast<const float4 *>(p));
+    return make_float4(__ldg(p), __ldg(p + 1), __ldg(p + 2), __ldg(p + 3));
+}
+
+__device__ __forceinline__ void st4(float *p, float4 v) {
+    if ((reinterpret_cast<uintptr_t>(p) & 15u) == 0) {
+        *reinterpret_cast<float4 *>(p) = v;
+        return;
+    }
+    p[0] = v.x;
+    p[1] = v.y;
+    p[2] = v.z;
+    p[3] = v.w;
+}
+
+template <int L>
+__device__ __forceinline__ float quad_max(float v) {
+#pragma unroll
+    for (int d = L / 2; d > 0; d >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, d, L));
+    return v;
+}
+
+// normalise the group's K values (four per lane) by their maximum; all -inf becomes 0
+template <int L>
+__device__ __forceinline__ void quad_normalise(float4 &t, uint32_t *flags, bool lead) {
+    const float mx = quad_max<L>(fmaxf(fmaxf(t.x, t.y), fmaxf(t.z, t.w)));
+    if (mx == kNegInf) {
+        t = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (lead) atomicOr(flags, kFlagContradiction);
+        return;
+    }
+    t.x -= mx;
+    t.y -= mx;
+    t.z -= mx;
+    t.w -= mx;
+}
+
+// One direction: the outputs of states 4q..4q+3 from the input vector v (this lane's
+// four states) against the rows of `rows` (a padded K x K table: E or E^T for the linear
+// form, phi or phi^T otherwise). xs is the group's exchange slot (K floats).
+template <int K, bool MAXP>
+__device__ __forceinline__ float4 quad_dir(float4 v, bool linear, const float *rows, float *xs, int q, float tmax,
+                                          float T, float invT) {
+    constexpr int L = K / 4;
+    float4 o;
+    if (!MAXP && linear) {
+        const float vm = quad_max<L>(fmaxf(fmaxf(v.x, v.y), fmaxf(v.z, v.w)));
+        // all -inf: w = 0 and every output -inf, as in the thread form
+        const float vmax = vm;
+        float4 w;
+        if (vmax == kNegInf) {
+            w = make_float4(0.f, 0.f, 0.f, 0.f);
+        } else {
+            w = make_float4(__expf((v.x - vmax) * invT), __expf((v.y - vmax) * invT), __expf((v.z - vmax) * invT),
+                            __expf((v.w - vmax) * invT));
+        }
+        reinterpret_cast<float4 *>(xs)[q] = w;
+        __syncwarp();
+        float wa[K];
+#pragma unroll
+        for (int j = 0; j < K / 4; ++j) {
+            const float4 a = reinterpret_cast<const float4 *>(xs)[j];
+            wa[4 * j] = a.x; wa[4 * j + 1] = a.y; wa[4 * j + 2] = a.z; wa[4 * j + 3] = a.w;
+        }
+        __syncwarp();
+        float out[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const float4 *row = reinterpret_cast<const float4 *>(rows + (4 * q + i) * kQRow<K>);
+            float s = 0.f;
+#pragma unroll
+            for (int j = 0; j < K / 4; ++j) {
+                const float4 a = row[j];
+                s = fmaf(a.x, wa[4 * j], fmaf(a.y, wa[4 * j + 1], fmaf(a.z, wa[4 * j + 2], fmaf(a.w, wa[4 * j + 3], s))));
+            }
+            out[i] = vmax == kNegInf ? kNegInf : T * logf(s) + vmax + tmax;
+        }
+        o = make_float4(out[0], out[1], out[2], out[3]);
+    } else {
+        reinterpret_cast<float4 *>(xs)[q] = v;
+        __syncwarp();
+        float va[K];
+#pragma unroll
+        for (int j = 0; j < K / 4; ++j) {
+            const float4 a = reinterpret_cast<const float4 *>(xs)[j];
+            va[4 * j] = a.x; va[4 * j + 1] = a.y; va[4 * j + 2] = a.z; va[4 * j + 3] = a.w;
+        }
+        __syncwarp();
+        float out[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const float *row = rows + (4 * q + i) * kQRow<K>;
+            float z[K];
+#pragma unroll
+            for (int y = 0; y < K; ++y) z[y] = row[y] + va[y];
+            out[i] = lse_row<K, MAXP>(z, T, invT);
+        }
+        o = make_float4(out[0], out[1], out[2], out[3]);
+    }
+    return o;
+}
+
+template <int K, bool MAXP, bool MS = false>
+__global__ void __launch_bounds__(256, 4)
+k_pair_quad(DevGraph G, const EnumSeg *__restrict__ segs, int n_seg, const float *__restrict__ pot,
+            const float *__restrict__ b, const float *__restrict__ ev, const float *__restrict__ m_old,
+            float *__restrict__ m_new, float T, float invT, float damping) {
+    static_assert(K == 8 || K == 16, "four states per lane, K / 4 lanes per factor");
+    constexpr int L = K / 4;
+    if constexpr (MS) {  // multi-sample launches: this block's sample
+        const int64_t smp = sample_select(G);
+        pot += smp * G.s_pot;
+        b += smp * G.s_vs;
+        ev += smp * G.s_vs;
+        m_old += smp * G.s_es;
+        m_new += smp * G.s_es;
+    }
+    __shared__ float tab[K * K];                          // phi, row-major (the rare path)
+    __shared__ __align__(16) float rows0[K * kQRow<K>];   // E (linear) or phi, padded rows
+    __shared__ __align__(16) float rows1[K * kQRow<K>];   // E^T or phi^T
+    __shared__ __align__(16) float xchg[256 * 4];
+    __shared__ float tinfo[2];
+    const EnumSeg *S = segs + find_seg(segs, n_seg, blockIdx.x);
+    if (member_frozen(G, S->member)) return;  // the whole block
+    const int n_fac = __ldg(&S->n_fac), pot_base = __ldg(&S->pot_base);
+    // the group's shared table (quad groups are planned for shared tables only)
+    for (int i = threadIdx.x; i < K * K; i += blockDim.x) tab[i] = __ldg(pot + pot_base + i);
+    __syncthreads();
+    const bool linear = prepare_linear_table<K, MAXP>(tab, rows0, tinfo, invT);  // rows0 = E, unpadded
+    // pad: E (or phi) rows to kQRow, and the transposes (blocks of at least 64 threads)
+    {
+        constexpr int kPer = (K * K + 63) / 64;
+        float e[kPer];
+#pragma unroll
+        for (int k = 0; k < kPer; ++k) {
+            const int i = threadIdx.x + k * blockDim.x;
+            e[k] = i < K * K ? (linear ? rows0[i] : tab[i]) : 0.f;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < kPer; ++k) {
+            const int i = threadIdx.x + k * blockDim.x;
+            if (i < K * K) {
+                const int r = i / K, c = i % K;
+                rows0[r * kQRow<K> + c] = e[k];
+                rows1[c * kQRow<K> + r] = e[k];
+            }
+        }
+        __syncthreads();
+    }
+    const float tmax = linear ? tinfo[0] : 0.f;
+    const int q = threadIdx.x & (L - 1);
+    const int fi = (blockIdx.x - __ldg(&S->block_begin)) * (blockDim.x / L) + (threadIdx.x / L);
+    const bool valid = fi < n_fac;
+    const int f = valid ? fi : n_fac - 1;  // idle lanes shadow the last factor, store nothing
+    const int e = __ldg(&S->edge_base) + 2 * f;
+    const int es0 = __ldg(&S->es_base) + 2 * K * f, es1 = es0 + K;
+    const int vs0 = __ldg(G.edge_vs + e), vs1 = __ldg(G.edge_vs + e + 1);
+    const float4 mo0 = ld4(m_old + es0 + 4 * q, true);
+    const float4 mo1 = ld4(m_old + es1 + 4 * q, true);
+    const bool rare_lane = (vs0 < 0) | (vs1 < 0) | needs_exact(mo0.x) | needs_exact(mo0.y) | needs_exact(mo0.z) |
+                           needs_exact(mo0.w) | needs_exact(mo1.x) | needs_exact(mo1.y) | needs_exact(mo1.z) |
+                           needs_exact(mo1.w);
+    const unsigned lane = threadIdx.x & 31;
+    const unsigned gbits = ((1u << L) - 1u) << (lane & ~(unsigned)(L - 1));
+    const bool rare = (__ballot_sync(0xffffffffu, rare_lane) & gbits) != 0u;
+    float *xs = xchg + (threadIdx.x & ~(L - 1)) * 4;
+    // the common path runs on every lane (the exchanges are warp-synchronous); a rare
+    // group's results are discarded
+    const float4 b1 = ld4(b + max(vs1, 0) + 4 * q, false);
+    float4 v = make_float4(b1.x - mo1.x, b1.y - mo1.y, b1.z - mo1.z, b1.w - mo1.w);
+    float4 o0 = quad_dir<K, MAXP>(v, linear, rows0, xs, q, tmax, T, invT);
+    const float4 b0 = ld4(b + max(vs0, 0) + 4 * q, false);
+    v = make_float4(b0.x - mo0.x, b0.y - mo0.y, b0.z - mo0.z, b0.w - mo0.w);
+    float4 o1 = quad_dir<K, MAXP>(v, linear, rows1, xs, q, tmax, T, invT);
+    const bool lead = q == 0 && valid && !rare;
+    quad_normalise<L>(o0, G.flags, lead);
+    quad_normalise<L>(o1, G.flags, lead);
+    if (damping != 0.f) {
+        const float w = 1.f - damping;
+        o0 = make_float4(damping * mo0.x + w * o0.x, damping * mo0.y + w * o0.y, damping * mo0.z + w * o0.z,
+                         damping * mo0.w + w * o0.w);
+        o1 = make_float4(damping * mo1.x + w * o1.x, damping * mo1.y + w * o1.y, damping * mo1.z + w * o1.z,
+                         damping * mo1.w + w * o1.w);
+    }
+    quad_normalise<L>(o0, G.flags, lead);
+    quad_normalise<L>(o1, G.flags, lead);
+    if (valid && !rare) {
+        st4(m_new + es0 + 4 * q, o0);
+        st4(m_new + es1 + 4 * q, o1);
+    }
+    if (valid && rare && q == 0)
+        pair_factor_rare<K, MAXP>(G, tab, pot + pot_base, b, ev, m_old, m_new, vs0, vs1, es0, es1, T, invT, damping);
+}
+
 // =====================================================================================
 // Factor pass: any listed-configuration factor, thread per factor
 // =====================================================================================
@@ -3493,6 +3709,12 @@ static void factor_pass_t(const DevGraph &G, const Plan &P, const float *pot, co
                 break;
             case kPairT16:
                 k_pair_thr<16, MAXP, MS><<<dim3(L.n_blocks, S), L.threads, 0, s>>>(G, es, L.n_seg, pot, b, ev, m_old, m_new, T, invT, damping);
+                break;
+            case kPairQ8:
+                k_pair_quad<8, MAXP, MS><<<dim3(L.n_blocks, S), L.threads, 0, s>>>(G, es, L.n_seg, pot, b, ev, m_old, m_new, T, invT, damping);
+                break;
+            case kPairQ16:
+                k_pair_quad<16, MAXP, MS><<<dim3(L.n_blocks, S), L.threads, 0, s>>>(G, es, L.n_seg, pot, b, ev, m_old, m_new, T, invT, damping);
                 break;
             case kEnumGeneric:
                 k_enum_generic<MAXP, MS><<<dim3(L.n_blocks, S), L.threads, 0, s>>>(G, es, L.n_seg, pot, b, ev, m_old, m_new, T, invT, damping);

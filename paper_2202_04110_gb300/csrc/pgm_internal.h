@@ -46,7 +46,9 @@ enum FactorVariant : int32_t {
     kPairT16 = 9,      // picks per launch)
     kEnumBlock = 10,   // listed-configuration factors with a state sum above kMaxStateSum or
                        // a list longer than kEnumGenericMaxCfg: a block per run of factors
-    kNumFactorVariants = 11
+    kPairQ8 = 11,      // dense pairwise table shared by the group, K = 8, 16: K / 4 lanes per
+    kPairQ16 = 12,     // factor, four states each (the default form for shared tables)
+    kNumFactorVariants = 13
 };
 
 // One enumeration group as seen by a launch. Edges of factor f are

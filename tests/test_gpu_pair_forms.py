@@ -1,0 +1,118 @@
+"""Dense K-state pairwise factors (Potts, Sec. 5.2's enumeration factors over full
+tables): the kernel forms of the factor pass give the same results.
+
+The K / 4-lane form (four states per lane, the default for tables shared by a group)
+and the thread-per-factor form run the same arithmetic in the same order, so their
+messages are bitwise equal: with the linear-domain form of a shared table (range within
+60 T), with the exact form (a table range above 60 T), at T = 0, with hard evidence (the
+rare path), in batches whose members start at any offset, and for many samples at once.
+Both are held to the FP64 oracle as well.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2202_04110_gb300 import workloads as W
+from tests._parity import assert_beliefs_close, assert_decode_ok
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2202_04110_gb300 import build
+    build.build()
+    from paper_2202_04110_gb300 import binding
+    return binding
+
+
+def _run_form(binding, graph, lp, ev, T, n_iters, form, damping=0.5, samples=0):
+    import torch
+    g = binding.Graph(graph)
+    g.set_option(binding.OPT_PAIR_FORM, form)
+    lpt = torch.as_tensor(np.asarray(lp, np.float32)).cuda()
+    if samples:
+        evt = torch.as_tensor(np.asarray(ev, np.float32)).cuda()
+        m = torch.zeros(samples, g.info["n_edge_states"], device="cuda")
+        g.run_bp_multi(lpt, evt, T, damping, n_iters, m)
+        return g, m.cpu().numpy()
+    evt = torch.as_tensor(np.asarray(ev, np.float32)).cuda()
+    m = g.new_msgs()
+    g.run_bp(lpt, evt, T, damping, n_iters, m)
+    return g, m.cpu().numpy()
+
+
+def _hard(p, frac, seed):
+    """Clamp a fraction of the variables to one state with -inf evidence."""
+    rng = np.random.default_rng(seed)
+    K = int(p.graph.num_states[0])
+    ev = p.evidence.reshape(-1, K).copy()
+    rows = np.flatnonzero(rng.random(ev.shape[0]) < frac)
+    keep = rng.integers(0, K, rows.size)
+    ev[rows] = -np.inf
+    ev[rows, keep] = 0.0
+    p.evidence = ev.ravel()
+    return p
+
+
+@pytest.mark.parametrize("K", [8, 16])
+@pytest.mark.parametrize("T", [1.0, 0.0, 0.4])
+@pytest.mark.parametrize("case", ["plain", "wide_table", "hard"])
+def test_quad_equals_thread_form(gpu, K, T, case):
+    side = 37
+    w = 40.0 if case == "wide_table" else None  # range 80 > 60 T: the exact (non-linear) form
+    p = W.potts_grid(side, K, seed=K + 3, T=T, n_iters=15, w=w)
+    if case == "hard":
+        p = _hard(p, 0.1, 5)
+    g_q, m_q = _run_form(gpu, p.graph, p.log_pot, p.evidence, T, 15, 0)
+    assert gpu.OPT_PAIR_FORM and g_q.launches()[-1][1] == (11 if K == 8 else 12)
+    _, m_t = _run_form(gpu, p.graph, p.log_pot, p.evidence, T, 15, 1)
+    assert np.array_equal(m_q, m_t, equal_nan=True), f"max diff {np.nanmax(np.abs(m_q - m_t))}"
+    om, _ = oracle.run_bp(p.graph, p.log_pot, p.evidence, T, 0.5, 15)
+    _, onb, _, _ = oracle.beliefs(p.graph, p.evidence, om)
+    import torch
+    evt = torch.as_tensor(p.evidence).cuda()
+    mt = torch.as_tensor(m_q).cuda()
+    nb = g_q.beliefs(evt, mt, True).cpu().numpy()
+    dec = g_q.decode(evt, mt).cpu().numpy()
+    assert_beliefs_close(nb, onb, what=f"K={K} T={T} {case}")
+    assert_decode_ok(dec, onb, p.graph.num_states, what=f"K={K} T={T} {case}")
+
+
+def test_quad_in_batch_at_any_offset(gpu):
+    """Members of 2, 4 and 8 states before the 16-state grids put their messages and
+    beliefs at offsets that are not multiples of four floats; the batched run equals the
+    thread form and each member alone."""
+    ms = [W.potts_grid(13, 2, 1, T=1.0), W.potts_grid(17, 16, 2, T=1.0), W.potts_grid(11, 4, 3, T=1.0),
+          W.potts_grid(9, 8, 4, T=1.0), W.ising_grid(3, 5, 5, T=1.0), W.potts_grid(21, 16, 6, T=1.0)]
+    batch = W.union(ms)
+    graphs = [p.graph for p in ms]
+    g_q, m_q = _run_form(gpu, graphs, batch.log_pot, batch.evidence, 1.0, 12, 0)
+    _, m_t = _run_form(gpu, graphs, batch.log_pot, batch.evidence, 1.0, 12, 1)
+    assert np.array_equal(m_q, m_t)
+    for i, p in enumerate(ms):
+        off = g_q.member(i)
+        g1 = gpu.Graph(p.graph)
+        g1.set_option(gpu.OPT_LOG_RATIO, 0)
+        import torch
+        m1 = g1.new_msgs()
+        g1.run_bp(torch.as_tensor(p.log_pot).cuda(), torch.as_tensor(p.evidence).cuda(), 1.0, 0.5, 12, m1)
+        seg = m_q[off["es_off"]: off["es_off"] + off["n_edge_states"]]
+        assert np.array_equal(seg, m1.cpu().numpy()), p.name
+
+
+@pytest.mark.parametrize("T", [1.0, 0.0])
+def test_quad_multi_sample(gpu, T):
+    p = W.potts_grid(29, 16, 9, T=T, n_iters=10)
+    S = 5
+    rng = np.random.default_rng(3)
+    ev = (p.evidence[None, :] + rng.standard_normal((S, p.evidence.size))).astype(np.float32)
+    _, mq = _run_form(gpu, p.graph, p.log_pot, ev, T, 10, 0, samples=S)
+    _, mt = _run_form(gpu, p.graph, p.log_pot, ev, T, 10, 1, samples=S)
+    assert np.array_equal(mq, mt)
+    for s in range(S):
+        _, m1 = _run_form(gpu, p.graph, p.log_pot, ev[s], T, 10, 0)
+        assert np.array_equal(mq[s], m1), s

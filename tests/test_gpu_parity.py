@@ -25,8 +25,8 @@ import pytest
 
 import oracle
 from paper_2202_04110_gb300 import workloads as W
-from tests._parity import (assert_beliefs_close, assert_decode_ok, assert_within_envelope,
-                           horizon_stats, oracle_envelope)
+from tests._parity import (assert_beliefs_close, assert_decode_ok, assert_like_members, assert_within_envelope,
+                           horizon_stats, oracle_envelope, oracle_members)
 
 pytestmark = pytest.mark.gpu
 
@@ -267,20 +267,41 @@ def test_ising_1000x1000_max_product_stepwise(gpu):
     _check_stepwise(gpu, p.graph, p.log_pot, p.evidence, 0.0, p.damping, [0, 60, 150, 199], "ising1000 T=0")
 
 
+def _check_members(binding, graph, log_pot, evidence, T, damping, n_iters, what, k=2):
+    """A long run against the FP64 oracle and its ensemble of nearby FP64 runs (FP32
+    storage, ~8-ulp input perturbations): the GPU must deviate from the oracle run like a
+    member does (assert_like_members); the figures of the GPU and of each member are
+    printed."""
+    _, _, nb, dec, _ = _gpu_infer(binding, graph, log_pot, evidence, T, damping, n_iters)
+    nb0, dec0, members = oracle_members(oracle, graph, log_pot, evidence, T, damping, n_iters, k=k)
+    fmt = lambda f: " ".join(f"{a}={b:.4g}" if isinstance(b, float) else f"{a}={b}" for a, b in f.items())
+    from tests._parity import deviation_figures
+    fg = deviation_figures(nb, dec, nb0, dec0, graph.num_states)
+    print(f"MEMBERS {what}: gpu {fmt(fg)}")
+    for i, (nbm, decm) in enumerate(members):
+        print(f"MEMBERS {what}: member{i} {fmt(deviation_figures(nbm, decm, nb0, dec0, graph.num_states))}")
+    assert_like_members(nb, dec, nb0, dec0, members, graph.num_states, what=what)
+
+
 def test_ising_1000x1000_max_product_envelope(gpu):
-    """T=0 on the full grid, all 200 iterations, against the oracle's perturbation envelope
-    (its figures are printed: errors, spread, decode differences by kind)."""
+    """T=0 on the full grid, all 200 iterations: every entry within 1e-4 + 10x the
+    per-entry spread of the oracle's ensemble (the factor each run needs is printed),
+    decodes equal wherever the ensemble agrees, and the run deviates from the FP64 oracle
+    like an ensemble member."""
     p = W.ising_large(0, T=0.0)
     _check_envelope(gpu, p.graph, p.log_pot, p.evidence, 0.0, p.damping, p.n_iters, "ising1000 T=0", report=True)
+    _check_members(gpu, p.graph, p.log_pot, p.evidence, 0.0, p.damping, p.n_iters, "ising1000 T=0")
 
 
-def test_deconvolution_full_size_envelope(gpu):
+def test_deconvolution_full_size_members(gpu):
     """The full deconvolution workload over its whole horizon (max-product, damping 0.5,
-    1000 iterations) against the oracle and an ensemble of two nearby FP64 runs (FP32
-    message storage, evidence perturbed by ~8 FP32 ulps): every entry within the
-    envelope, decodes equal wherever the ensemble agrees; figures printed."""
+    1000 iterations). The run is chaotic: FP32 message storage alone moves half of the FP64
+    oracle's log-beliefs by more than 1e-4 (by hundreds at the 99th percentile) and flips
+    thousands of decodes, so no per-entry bound exists; the GPU run must deviate from the
+    oracle like the ensemble's members do (quantiles of the deviation and the number of
+    differently decoded variables within 3x the largest member's)."""
     p = W.deconvolution(0, n_iters=1000)
-    _check_envelope(gpu, p.graph, p.log_pot, p.evidence, 0.0, 0.5, 1000, "deconv full 1000 it", k=1, report=True)
+    _check_members(gpu, p.graph, p.log_pot, p.evidence, 0.0, 0.5, 1000, "deconv full 1000 it", k=2)
 
 
 def test_deconvolution_full_size_strict(gpu):
