@@ -159,6 +159,24 @@ pgm_status pgm_check_desc(const pgm_graph_desc *desc, pgm_info *info);
  */
 pgm_status pgm_build_batch(const pgm_graph_desc *const *descs, int32_t n, pgm_graph **out);
 
+/*
+ * A batch (pgm_build_batch; a single graph is a batch of one) with its own T, damping
+ * and iteration count for every member (Sec. 5.3 batches of models; each member as a
+ * pgm_run_bp call of its own): T, damping, n_iters are host arrays [n_members]; member m
+ * runs n_iters[m] iterations at T[m] and damping[m] from its messages in msgs (in/out,
+ * warm starts as in pgm_run_bp). Every iteration is one variable pass and one factor
+ * pass over all members still running -- two factor launches per kernel variant when
+ * the batch mixes max-product (T = 0) with other members --, and a member leaves the
+ * factor pass once its count is reached. A member's messages equal pgm_run_bp of that
+ * member alone with its parameters and PGM_OPT_LOG_RATIO 0 (the edge-state iteration is
+ * used throughout). Blocking. The first call allocates 20 n_members bytes and the
+ * members' early-exit state of pgm_run_bp_until_members, kept until pgm_free.
+ * Errors: PGM_EINVAL for NULL arrays or pointers, a T[m] negative or not finite, a
+ * damping[m] outside [0, 1), an n_iters[m] < 0 (the message names the member).
+ */
+pgm_status pgm_run_bp_batch(pgm_graph *g, const float *log_pot, const float *evidence, const float *T,
+                            const float *damping, const int32_t *n_iters, float *msgs, void *stream);
+
 /* Offsets of member i (0 <= i < pgm_info.n_members) of a batch. */
 pgm_status pgm_batch_member(const pgm_graph *g, int32_t i, pgm_member *m);
 

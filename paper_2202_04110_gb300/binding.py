@@ -23,7 +23,7 @@ FLAG_NAN = 2
 # Every symbol include/pgm.h declares.
 EXPORTED = ["pgm_build", "pgm_build_batch", "pgm_batch_member", "pgm_check_desc", "pgm_free", "pgm_graph_info", "pgm_run_bp", "pgm_beliefs",
             "pgm_decode", "pgm_infer_host", "pgm_set_profiling", "pgm_pass_times", "pgm_launch_times",
-            "pgm_device_flags", "pgm_grid2_run_bp_noalloc", "pgm_grid2_noalloc_flags", "pgm_run_bp_multi", "pgm_pmp_sample", "pgm_run_bp_until", "pgm_run_bp_until_members", "pgm_set_option", "pgm_get_option", "pgm_autotune",
+            "pgm_device_flags", "pgm_grid2_run_bp_noalloc", "pgm_grid2_noalloc_flags", "pgm_run_bp_multi", "pgm_pmp_sample", "pgm_run_bp_until", "pgm_run_bp_until_members", "pgm_run_bp_batch", "pgm_set_option", "pgm_get_option", "pgm_autotune",
             "pgm_launch_info", "pgm_grad", "pgm_serve_create", "pgm_serve_submit", "pgm_serve_submit_until", "pgm_serve_submit_borrowed", "pgm_serve_poll",
             "pgm_serve_wait", "pgm_serve_stats", "pgm_serve_destroy", "pgm_last_error"]
 OPT_CUDA_GRAPH = 1
@@ -113,6 +113,8 @@ def load_library(path: str | None = None):
     lib.pgm_run_bp_until.argtypes = [vp, vp, vp, f32, f32, i32, f32, i32, vp, vp, vp, vp]
     lib.pgm_run_bp_until_members.restype = i32
     lib.pgm_run_bp_until_members.argtypes = [vp, vp, vp, f32, f32, i32, f32, i32, vp, vp, vp, vp]
+    lib.pgm_run_bp_batch.restype = i32
+    lib.pgm_run_bp_batch.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp]
     lib.pgm_pmp_sample.restype = i32
     lib.pgm_pmp_sample.argtypes = [vp, i32, vp, vp, vp, f32, i32, vp, vp, vp]
     lib.pgm_beliefs.restype = i32
@@ -321,6 +323,23 @@ class Graph:
             int(max_iters), float(tol), int(check_every), _dptr(msgs, torch.float32, I["n_edge_states"], "msgs"),
             done.ctypes.data, res.ctypes.data, _stream_ptr(stream)))
         return done, res
+
+    def run_bp_batch(self, log_pot, evidence, T, damping, n_iters, msgs, stream=None):
+        """In-place batch run with per-member parameters (pgm_run_bp_batch): T, damping and
+        n_iters are sequences of length n_members."""
+        import torch
+        I = self.info
+        n = I["n_members"]
+        Ta = np.ascontiguousarray(T, np.float32)
+        da = np.ascontiguousarray(damping, np.float32)
+        na = np.ascontiguousarray(n_iters, np.int32)
+        if Ta.size != n or da.size != n or na.size != n:
+            raise ValueError(f"T, damping and n_iters need {n} entries (one per member)")
+        lp = _dptr(log_pot, torch.float32, I["n_potentials"], "log_pot") if I["n_potentials"] else 0
+        check(load_library().pgm_run_bp_batch(
+            self._h, lp, _dptr(evidence, torch.float32, I["n_var_states"], "evidence"), Ta.ctypes.data, da.ctypes.data,
+            na.ctypes.data, _dptr(msgs, torch.float32, I["n_edge_states"], "msgs"), _stream_ptr(stream)))
+        return msgs
 
     def pmp_sample(self, log_pot, evidence, noise, damping: float, n_iters: int, stream=None):
         """Perturb-and-max-product samples (pgm_pmp_sample): noise [S, n_var_states].

@@ -94,6 +94,11 @@ struct pgm_graph {
     // frozen words, residual words, iterations and residuals [n each], loop state [3]
     // (iterations done, go on, a member active), the previous messages [n_edge_states]
     char *mu_mem = nullptr;
+    // pgm_run_bp_batch (allocated on first use): per-member (T, 1 / T, damping, 0) and
+    // iteration counts
+    char *bm_mem = nullptr;
+    float *bm_prm = nullptr;
+    int32_t *bm_iters = nullptr;
     // pgm_run_bp_multi on graphs without the joint log-ratio path: per-sample scratch
     char *mse_mem = nullptr;
     size_t mse_bytes = 0;
@@ -722,6 +727,7 @@ void pgm_free(pgm_graph *g) {
     if (g->until_prev) cudaFree(g->until_prev);
     if (g->until_res_host) cudaFreeHost(g->until_res_host);
     if (g->mu_mem) cudaFree(g->mu_mem);
+    if (g->bm_mem) cudaFree(g->bm_mem);
     if (g->mse_mem) cudaFree(g->mse_mem);
     for (cudaEvent_t e : g->events) cudaEventDestroy(e);
     drop_cached_runs(g);
@@ -1311,23 +1317,13 @@ static pgm_status cached_until_members(pgm_graph *g, const float *log_pot, const
     return PGM_OK;
 }
 
-pgm_status pgm_run_bp_until_members(pgm_graph *g, const float *log_pot, const float *evidence, float T,
-                                    float damping, int32_t max_iters, float tol, int32_t check_every, float *msgs,
-                                    int32_t *iters_done, float *residual, void *stream) {
-    pgm_status st = check_run_args(g, log_pot, evidence, T, damping, max_iters, msgs);
-    if (st != PGM_OK) return st;
-    if (!iters_done || !residual) return fail(PGM_EINVAL, "iters_done / residual is NULL");
-    if (check_every < 1) return fail(PGM_EINVAL, "check_every must be >= 1");
-    if (!(tol >= 0.f)) return fail(PGM_EINVAL, "tol must be >= 0");
+// Device state of the per-member runs of a batch (allocated on first use, kept until
+// pgm_free): member edge-state offsets, frozen words (zero outside such runs; every
+// factor launch checks them from then on), residual words, iterations, residuals, loop
+// state and a previous-messages buffer.
+static pgm_status ensure_member_state(pgm_graph *g) {
     const int nm = (int)g->members.size();
     const int64_t ES = g->info.n_edge_states;
-    for (int m = 0; m < nm; ++m) {
-        iters_done[m] = 0;
-        residual[m] = (max_iters == 0 && g->members[m].n_edge_states > 0) ? CUDART_NAN_F_HOST : 0.f;
-    }
-    if (max_iters == 0 || ES == 0) return PGM_OK;
-    DeviceGuard dg(g->device);
-    if (!dg.ok) return fail(PGM_ECUDA, "cudaSetDevice failed");
     if (!g->mu_mem) {
         const size_t a4 = align_up((size_t)(nm + 1) * sizeof(int32_t), 256);
         const size_t total = 5 * a4 + 256 + align_up((size_t)ES * sizeof(float), 256);
@@ -1352,6 +1348,28 @@ pgm_status pgm_run_bp_until_members(pgm_graph *g, const float *log_pot, const fl
             return fail(PGM_ECUDA, "cudaMemset(frozen)");
         g->G.frozen = g->mu_frozen;  // launches from now on check it (zero outside these runs)
     }
+    return PGM_OK;
+}
+
+pgm_status pgm_run_bp_until_members(pgm_graph *g, const float *log_pot, const float *evidence, float T,
+                                    float damping, int32_t max_iters, float tol, int32_t check_every, float *msgs,
+                                    int32_t *iters_done, float *residual, void *stream) {
+    pgm_status st = check_run_args(g, log_pot, evidence, T, damping, max_iters, msgs);
+    if (st != PGM_OK) return st;
+    if (!iters_done || !residual) return fail(PGM_EINVAL, "iters_done / residual is NULL");
+    if (check_every < 1) return fail(PGM_EINVAL, "check_every must be >= 1");
+    if (!(tol >= 0.f)) return fail(PGM_EINVAL, "tol must be >= 0");
+    const int nm = (int)g->members.size();
+    const int64_t ES = g->info.n_edge_states;
+    for (int m = 0; m < nm; ++m) {
+        iters_done[m] = 0;
+        residual[m] = (max_iters == 0 && g->members[m].n_edge_states > 0) ? CUDART_NAN_F_HOST : 0.f;
+    }
+    if (max_iters == 0 || ES == 0) return PGM_OK;
+    DeviceGuard dg(g->device);
+    if (!dg.ok) return fail(PGM_ECUDA, "cudaSetDevice failed");
+    st = ensure_member_state(g);
+    if (st != PGM_OK) return st;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     struct ForceEs {  // edge-state iterations for the whole call
         pgm_graph *g;
@@ -1392,6 +1410,84 @@ pgm_status pgm_run_bp_until_members(pgm_graph *g, const float *log_pot, const fl
     if (e == cudaSuccess) e = cudaMemsetAsync(g->mu_frozen, 0, (size_t)nm * sizeof(int32_t), s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(e, "members' early-exit results");
+    return PGM_OK;
+}
+
+pgm_status pgm_run_bp_batch(pgm_graph *g, const float *log_pot, const float *evidence, const float *T,
+                            const float *damping, const int32_t *n_iters, float *msgs, void *stream) {
+    pgm_status st = check_run_args(g, log_pot, evidence, 1.f, 0.f, 0, msgs);
+    if (st != PGM_OK) return st;
+    if (!T || !damping || !n_iters) return fail(PGM_EINVAL, "T / damping / n_iters is NULL");
+    const int nm = (int)g->members.size();
+    const int64_t ES = g->info.n_edge_states;
+    std::vector<float> prm(4 * (size_t)nm, 0.f);
+    int32_t max_it = 0;
+    bool any_max = false, any_sum = false, finish_at_zero = false;
+    for (int m = 0; m < nm; ++m) {
+        if (!(T[m] >= 0.f) || T[m] == __builtin_inff())
+            return fail(PGM_EINVAL, "T[" + std::to_string(m) + "] must be finite and >= 0");
+        if (!(damping[m] >= 0.f && damping[m] < 1.f))
+            return fail(PGM_EINVAL, "damping[" + std::to_string(m) + "] must be in [0, 1)");
+        if (n_iters[m] < 0) return fail(PGM_EINVAL, "n_iters[" + std::to_string(m) + "] must be >= 0");
+        prm[4 * m] = T[m];
+        prm[4 * m + 1] = T[m] > 0.f ? 1.f / T[m] : 0.f;
+        prm[4 * m + 2] = damping[m];
+        if (g->members[m].n_edge_states == 0) continue;
+        if (n_iters[m] == 0) {
+            finish_at_zero = true;
+            continue;
+        }
+        max_it = std::max(max_it, n_iters[m]);
+        (T[m] == 0.f ? any_max : any_sum) = true;
+    }
+    if (max_it == 0 || ES == 0) return PGM_OK;
+    DeviceGuard dg(g->device);
+    if (!dg.ok) return fail(PGM_ECUDA, "cudaSetDevice failed");
+    st = ensure_member_state(g);
+    if (st != PGM_OK) return st;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (!g->bm_mem) {
+        const size_t a = align_up((size_t)nm * 4 * sizeof(float), 256);
+        if (cudaMalloc(&g->bm_mem, a + align_up((size_t)nm * sizeof(int32_t), 256)) != cudaSuccess) {
+            g->bm_mem = nullptr;
+            return fail(PGM_ENOMEM, "cudaMalloc(per-member parameters)");
+        }
+        g->bm_prm = reinterpret_cast<float *>(g->bm_mem);
+        g->bm_iters = reinterpret_cast<int32_t *>(g->bm_mem + a);
+    }
+    // pageable sources: each copy has taken its data when the call returns
+    std::vector<int32_t> frozen(nm), iters(n_iters, n_iters + nm);
+    for (int m = 0; m < nm; ++m) frozen[m] = (n_iters[m] == 0 || g->members[m].n_edge_states == 0) ? 1 : 0;
+    cudaError_t e = cudaMemcpyAsync(g->bm_prm, prm.data(), prm.size() * sizeof(float), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(g->bm_iters, iters.data(), iters.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(g->mu_frozen, frozen.data(), frozen.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return cuda_fail(e, "per-member parameters upload");
+    DevGraph G2 = g->G;
+    G2.mem_prm = g->bm_prm;
+    G2.frozen = g->mu_frozen;
+    float *cur = msgs, *nxt = g->m_tmp;
+    // members that run no iteration: both buffers hold their messages
+    if (finish_at_zero) e = launch_batch_freeze(g->bm_iters, 0, nm, g->mu_off, g->mu_frozen, cur, nxt, g->n_sm, s);
+    std::vector<char> ends((size_t)max_it + 1, 0);
+    for (int m = 0; m < nm; ++m)
+        if (n_iters[m] > 0 && g->members[m].n_edge_states > 0) ends[n_iters[m]] = 1;
+    for (int32_t it = 0; it < max_it && e == cudaSuccess; ++it) {
+        e = launch_var_pass(G2, g->P, evidence, cur, g->b, kVarIter, nullptr, s);
+        // one launch per kind of member: max-product (T = 0) and the others
+        if (e == cudaSuccess && any_max) e = launch_factor_pass(G2, g->P, log_pot, g->b, evidence, cur, nxt, 0.f, 0.f, s);
+        if (e == cudaSuccess && any_sum) e = launch_factor_pass(G2, g->P, log_pot, g->b, evidence, cur, nxt, 1.f, 0.f, s);
+        std::swap(cur, nxt);
+        if (e == cudaSuccess && ends[it + 1] && it + 1 < max_it)
+            e = launch_batch_freeze(g->bm_iters, it + 1, nm, g->mu_off, g->mu_frozen, cur, nxt, g->n_sm, s);
+    }
+    if (e == cudaSuccess && cur != msgs)
+        e = cudaMemcpyAsync(msgs, cur, (size_t)ES * sizeof(float), cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(g->mu_frozen, 0, (size_t)nm * sizeof(int32_t), s);
+    // the host vectors above are the copies' sources: keep them until the copies are done
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "batch run with per-member parameters");
     return PGM_OK;
 }
 

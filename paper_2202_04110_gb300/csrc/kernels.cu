@@ -972,6 +972,22 @@ __device__ __forceinline__ bool member_frozen(const DevGraph &G, int member) {
     return G.frozen != nullptr && __ldg(G.frozen + member) != 0;
 }
 
+// A batch run with parameters per member (pgm_run_bp_batch): the member's T, 1 / T and
+// damping replace the launch's, and the launch of the other kind (max-product or not)
+// skips it. Also true for a frozen member.
+template <bool MAXP>
+__device__ __forceinline__ bool member_skip(const DevGraph &G, int member, float &T, float &invT, float &damping) {
+    if (member_frozen(G, member)) return true;
+    if (G.mem_prm != nullptr) {
+        const float4 p = __ldg(reinterpret_cast<const float4 *>(G.mem_prm) + member);
+        if ((p.x == 0.f) != MAXP) return true;
+        T = p.x;
+        invT = p.y;
+        damping = p.z;
+    }
+    return false;
+}
+
 // The factor-to-variable update of one dense pairwise factor from its two
 // variable-to-factor vectors v0, v1 and stored messages mo0, mo1; writes the damped,
 // normalised messages.
@@ -1113,7 +1129,7 @@ k_pair(DevGraph G, const EnumSeg *__restrict__ segs, int n_seg, const float *__r
     __shared__ float tabE[K >= 4 ? K * K : 1];
     __shared__ float tinfo[2];
     const EnumSeg *S = segs + find_seg(segs, n_seg, blockIdx.x);
-    if (member_frozen(G, S->member)) return;  // the whole block
+    if (member_skip<MAXP>(G, S->member, T, invT, damping)) return;  // the whole block
     const int n_fac = __ldg(&S->n_fac), shared = __ldg(&S->shared), pot_base = __ldg(&S->pot_base);
     bool linear = false;
     if (shared) {
@@ -1343,7 +1359,7 @@ k_pair_group(DevGraph G, const EnumSeg *__restrict__ segs, int n_seg, int n_vblo
         const float bb0 = fast0 ? __ldg(b + vs0 + x) : 0.f;
         const float bb1 = fast1 ? __ldg(b + vs1 + x) : 0.f;
         if (vb + 1 < vb_end) fetch(vb + 1, nsi, nvs0, nvs1, nmo0, nmo1);
-        if (member_frozen(G, S->member)) continue;  // uniform across the block
+        if (member_skip<MAXP>(G, S->member, T, invT, damping)) continue;  // uniform across the block
         if (si != cur) {  // uniform across the block
             cur = si;
             shared = __ldg(&S->shared) != 0;
@@ -1489,7 +1505,7 @@ k_pair_thr(DevGraph G, const EnumSeg *__restrict__ segs, int n_seg, const float 
     __shared__ __align__(16) float tabET[MAXP ? 4 : K * K];
     __shared__ float tinfo[2];
     const EnumSeg *S = segs + find_seg(segs, n_seg, blockIdx.x);
-    if (member_frozen(G, S->member)) return;  // the whole block
+    if (member_skip<MAXP>(G, S->member, T, invT, damping)) return;  // the whole block
     const int n_fac = __ldg(&S->n_fac), shared = __ldg(&S->shared), pot_base = __ldg(&S->pot_base);
     bool linear = false;
     if (shared) {  // uniform over the block (a block lies in one segment)
@@ -1680,7 +1696,7 @@ k_pair_quad(DevGraph G, const EnumSeg *__restrict__ segs, int n_seg, const float
     __shared__ __align__(16) float xchg[256 * 4];
     __shared__ float tinfo[2];
     const EnumSeg *S = segs + find_seg(segs, n_seg, blockIdx.x);
-    if (member_frozen(G, S->member)) return;  // the whole block
+    if (member_skip<MAXP>(G, S->member, T, invT, damping)) return;  // the whole block
     const int n_fac = __ldg(&S->n_fac), pot_base = __ldg(&S->pot_base);
     // the group's shared table (quad groups are planned for shared tables only)
     for (int i = threadIdx.x; i < K * K; i += blockDim.x) tab[i] = __ldg(pot + pot_base + i);
@@ -1771,7 +1787,7 @@ k_enum_generic(DevGraph G, const EnumSeg *__restrict__ segs, int n_seg, const fl
         m_new += smp * G.s_es;
     }
     const EnumSeg *S = segs + find_seg(segs, n_seg, blockIdx.x);
-    if (member_frozen(G, S->member)) return;
+    if (member_skip<MAXP>(G, S->member, T, invT, damping)) return;
     const int f = (blockIdx.x - __ldg(&S->block_begin)) * blockDim.x + threadIdx.x;
     if (f >= __ldg(&S->n_fac)) return;
     const int a = __ldg(&S->arity), nc = __ldg(&S->n_cfg), ksum = __ldg(&S->es_per_fac);
@@ -1973,7 +1989,7 @@ k_enum_block(DevGraph G, const EnumSeg *__restrict__ segs, int n_seg, const floa
     __shared__ int sK[kMaxArity], sKo[kMaxArity];
     __shared__ int s_fix[kEnumBlockThreads / 32][kMaxArity];
     const EnumSeg *S = segs + find_seg(segs, n_seg, blockIdx.x);
-    if (member_frozen(G, S->member)) return;  // the whole block
+    if (member_skip<MAXP>(G, S->member, T, invT, damping)) return;  // the whole block
     const int a = __ldg(&S->arity), nc = __ldg(&S->n_cfg), ksum = __ldg(&S->es_per_fac);
     const int fpb = __ldg(&S->fpb), L = __ldg(&S->lanes), tb = __ldg(&S->table_bytes);
     const int n_fac = __ldg(&S->n_fac), shared = __ldg(&S->shared), packed = __ldg(&S->packed);
@@ -2221,7 +2237,7 @@ k_logic_small(DevGraph G, const LogicSeg *__restrict__ segs, int n_seg, const fl
         m_new += smp * G.s_es;
     }
     const LogicSeg *S = segs + find_seg(segs, n_seg, blockIdx.x);
-    if (member_frozen(G, S->member)) return;
+    if (member_skip<MAXP>(G, S->member, T, invT, damping)) return;
     const int f = (blockIdx.x - __ldg(&S->block_begin)) * blockDim.x + threadIdx.x;
     if (f >= __ldg(&S->n_fac)) return;
     const int *po = G.paroff_pool + __ldg(&S->paroff_base);
@@ -2338,7 +2354,7 @@ k_logic_warp(DevGraph G, const LogicSeg *__restrict__ segs, int n_seg, const flo
     extern __shared__ float smem[];
     const int warps = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const LogicSeg *S = segs + find_seg(segs, n_seg, blockIdx.x);
-    if (member_frozen(G, S->member)) return;
+    if (member_skip<MAXP>(G, S->member, T, invT, damping)) return;
     const int f = (blockIdx.x - __ldg(&S->block_begin)) * warps + warp;
     if (f >= __ldg(&S->n_fac)) return;
     float *sx = smem + (size_t)warp * 3 * cap;  // log-odds x_j (times sgn)
@@ -3568,6 +3584,22 @@ __global__ void __launch_bounds__(256) k_freeze_copy(const int32_t *__restrict__
 // The loop control of a device-side early-exit run (the body of a conditional while
 // node): after a trip of n iterations, done += n; the loop goes on while the trip's
 // residual (bits in *res) is above tol or NaN and fewer than limit iterations are done.
+// Batch run with iteration counts per member: after `it` iterations, the members whose
+// count is `it` stop (frozen; the factor pass skips them) and their messages are copied
+// from the buffer that holds iteration `it` (a) to the other one (b), so that both hold
+// their last iteration whichever buffer the run ends in.
+__global__ void __launch_bounds__(256) k_batch_freeze(const int32_t *__restrict__ n_iters, int it, int n_members,
+                                                      const int32_t *__restrict__ off, int32_t *__restrict__ frozen,
+                                                      const float *__restrict__ a, float *__restrict__ b) {
+    for (int m = 0; m < n_members; ++m) {
+        if (__ldg(n_iters + m) != it) continue;
+        if (blockIdx.x == 0 && threadIdx.x == 0) frozen[m] = 1;
+        const int64_t s0 = __ldg(off + m), s1 = __ldg(off + m + 1);
+        for (int64_t i = s0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < s1; i += (int64_t)gridDim.x * blockDim.x)
+            b[i] = a[i];
+    }
+}
+
 __global__ void k_until_control(cudaGraphConditionalHandle h, const unsigned *__restrict__ res,
                                 int *__restrict__ done, int n, int limit, float tol) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
@@ -3861,6 +3893,12 @@ cudaError_t launch_until_control_members(cudaGraphConditionalHandle h, bool set_
 cudaError_t launch_freeze_copy(const int32_t *frozen, const int32_t *off, int n_members, const float *a, float *b,
                                int n_sm, cudaStream_t s) {
     k_freeze_copy<<<n_sm * 4, 256, 0, s>>>(frozen, off, n_members, a, b);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_freeze(const int32_t *n_iters, int it, int n_members, const int32_t *off, int32_t *frozen,
+                                const float *a, float *b, int n_sm, cudaStream_t s) {
+    k_batch_freeze<<<n_sm * 4, 256, 0, s>>>(n_iters, it, n_members, off, frozen, a, b);
     return cudaGetLastError();
 }
 

@@ -122,6 +122,8 @@ struct DevGraph {
                              // float-float value); null if there are none
     const int32_t *lr_pos;   // [E] Plan::lr graphs: each edge's slot in the log-ratio
                              // arrays (k V + v with vin_tab4, else its CSR index); else null
+    const float *mem_prm;    // [4 n_members] batch runs with parameters per member: each
+                             // member's (T, 1 / T, damping, 0); null otherwise
 };
 
 struct FactorLaunch {
@@ -264,6 +266,10 @@ cudaError_t launch_until_control_members(cudaGraphConditionalHandle h, bool set_
                                          int n, int limit, float tol, cudaStream_t s);
 cudaError_t launch_freeze_copy(const int32_t *frozen, const int32_t *off, int n_members, const float *a, float *b,
                                int n_sm, cudaStream_t s);
+// Batch runs with iteration counts per member: members whose count is `it` are frozen
+// and their message ranges (off[n_members + 1]) copied from a to b.
+cudaError_t launch_batch_freeze(const int32_t *n_iters, int it, int n_members, const int32_t *off, int32_t *frozen,
+                                const float *a, float *b, int n_sm, cudaStream_t s);
 // out[s VS + i] = ev[i] + noise[s VS + i] (perturb-and-max-product evidence).
 cudaError_t launch_pmp_perturb(int64_t VS, int S, const float *ev, const float *noise, float *out, cudaStream_t s);
 // Log-ratio pack (from the [2E] edge-state layout; unused slots 0) and unpack.

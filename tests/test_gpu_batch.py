@@ -139,3 +139,72 @@ def test_pass_timing(gpu, cuda_graph):
         assert var_ms > 0 and fac_ms > 0
         assert g.pass_times()[2] == 0  # reset
         g.set_profiling(0)
+
+
+def _alone(binding, p, T, damping, n_iters):
+    import torch
+    g = binding.Graph(p.graph)
+    g.set_option(binding.OPT_LOG_RATIO, 0)
+    m = g.new_msgs()
+    g.run_bp(torch.as_tensor(p.log_pot).cuda(), torch.as_tensor(p.evidence).cuda(), T, damping, n_iters, m)
+    return m.cpu().numpy()
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_batch_per_member_parameters(gpu, seed):
+    """pgm_run_bp_batch: every member with its own T (0, 0.5 or 1), damping (0, 0.3, 0.5)
+    and iteration count (0..12) in one batched run; each member's messages equal the
+    member run alone with its parameters, bitwise, and its beliefs match the oracle."""
+    import torch
+    members = _mixed_members()
+    rng = np.random.default_rng(seed)
+    n = len(members)
+    Ts = rng.choice([0.0, 0.5, 1.0], n).astype(np.float32)
+    ds = rng.choice([0.0, 0.3, 0.5], n).astype(np.float32)
+    its = rng.integers(0, 13, n).astype(np.int32)
+    its[0] = 0
+    its[-1] = 12
+    batch = W.union(members)
+    gb = gpu.Graph([p.graph for p in members])
+    lp = torch.as_tensor(batch.log_pot).cuda()
+    ev = torch.as_tensor(batch.evidence).cuda()
+    m = gb.new_msgs()
+    gb.run_bp_batch(lp, ev, Ts, ds, its, m)
+    mb = m.cpu().numpy()
+    for i, p in enumerate(members):
+        off = gb.member(i)
+        seg = mb[off["es_off"]: off["es_off"] + off["n_edge_states"]]
+        ref = _alone(gpu, p, float(Ts[i]), float(ds[i]), int(its[i]))
+        assert np.array_equal(seg, ref), (p.name, Ts[i], ds[i], its[i])
+        om, _ = oracle.run_bp(p.graph, p.log_pot, p.evidence, float(Ts[i]), float(ds[i]), int(its[i]))
+        _, onb, _, _ = oracle.beliefs(p.graph, p.evidence, om)
+        g1 = gpu.Graph(p.graph)
+        nb = g1.beliefs(torch.as_tensor(p.evidence).cuda(), torch.as_tensor(seg).cuda(), True).cpu().numpy()
+        assert_beliefs_close(nb, onb, what=f"{p.name} T={Ts[i]} d={ds[i]} it={its[i]}")
+
+
+def test_batch_per_member_warm_start_and_errors(gpu):
+    """Two calls continue where the first stopped (warm start per member); bad
+    per-member values are rejected with the member named."""
+    import torch
+    members = _mixed_members()[:4]
+    batch = W.union(members)
+    gb = gpu.Graph([p.graph for p in members])
+    lp = torch.as_tensor(batch.log_pot).cuda()
+    ev = torch.as_tensor(batch.evidence).cuda()
+    Ts = np.array([1.0, 0.0, 1.0, 0.0], np.float32)
+    ds = np.full(4, 0.5, np.float32)
+    a = gb.new_msgs()
+    gb.run_bp_batch(lp, ev, Ts, ds, np.array([2, 3, 0, 5], np.int32), a)
+    gb.run_bp_batch(lp, ev, Ts, ds, np.array([4, 2, 6, 1], np.int32), a)
+    b = gb.new_msgs()
+    gb.run_bp_batch(lp, ev, Ts, ds, np.array([6, 5, 6, 6], np.int32), b)
+    # a member's iterations split over two calls equal one run of the sum (ping-pong
+    # buffers hold the same values; results are bitwise equal)
+    assert torch.equal(a, b)
+    for bad_T, bad_d, bad_n, word in ((-1.0, 0.5, 3, "T[2]"), (1.0, 1.0, 3, "damping[2]"), (1.0, 0.5, -1, "n_iters[2]")):
+        T2, d2, n2 = Ts.copy(), ds.copy(), np.array([1, 1, 1, 1], np.int32)
+        T2[2], d2[2], n2[2] = bad_T, bad_d, bad_n
+        with pytest.raises(gpu.PgmError) as ei:
+            gb.run_bp_batch(lp, ev, T2, d2, n2, a)
+        assert ei.value.status == -1 and word in str(ei.value)
