@@ -1569,23 +1569,38 @@ k_pair_thr(DevGraph G, const EnumSeg *__restrict__ segs, int n_seg, const float 
 template <int K>
 constexpr int kQRow = K + 4;  // padded row stride of the shared tables (floats)
 
-// Four consecutive floats: one 16-byte access when aligned (a batch member's arrays
-// start wherever the previous member's end), else four.
+// Four consecutive floats of global memory: one 16-byte access when the address is
+// 16-byte aligned (a batch member's arrays start wherever the previous member's end),
+// else four 4-byte accesses. Written as PTX so that each branch issues exactly these
+// accesses (the compiler may not merge the 4-byte ones into wider ones).
 __device__ __forceinline__ float4 ld4(const float *p, bool stream) {
-    if ((reinterpret_cast<uintptr_t>(p) & 15u) == 0)
-        return stream ? __ldcs(reinterpret_cast<const float4 *>(p)) : __ldg(reinterpret_cast<const float4 *>(p));
-    return make_float4(__ldg(p), __ldg(p + 1), __ldg(p + 2), __ldg(p + 3));
+    float4 v;
+    if ((reinterpret_cast<uintptr_t>(p) & 15u) == 0) {
+        if (stream)
+            asm volatile("ld.global.cs.v4.f32 {%0, %1, %2, %3}, [%4];"
+                         : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "l"(p));
+        else
+            asm volatile("ld.global.nc.v4.f32 {%0, %1, %2, %3}, [%4];"
+                         : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "l"(p));
+        return v;
+    }
+    asm volatile("ld.global.nc.f32 %0, [%1];" : "=f"(v.x) : "l"(p));
+    asm volatile("ld.global.nc.f32 %0, [%1];" : "=f"(v.y) : "l"(p + 1));
+    asm volatile("ld.global.nc.f32 %0, [%1];" : "=f"(v.z) : "l"(p + 2));
+    asm volatile("ld.global.nc.f32 %0, [%1];" : "=f"(v.w) : "l"(p + 3));
+    return v;
 }
 
 __device__ __forceinline__ void st4(float *p, float4 v) {
     if ((reinterpret_cast<uintptr_t>(p) & 15u) == 0) {
-        *reinterpret_cast<float4 *>(p) = v;
+        asm volatile("st.global.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w)
+                     : "memory");
         return;
     }
-    p[0] = v.x;
-    p[1] = v.y;
-    p[2] = v.z;
-    p[3] = v.w;
+    asm volatile("st.global.f32 [%0], %1;" ::"l"(p), "f"(v.x) : "memory");
+    asm volatile("st.global.f32 [%0], %1;" ::"l"(p + 1), "f"(v.y) : "memory");
+    asm volatile("st.global.f32 [%0], %1;" ::"l"(p + 2), "f"(v.z) : "memory");
+    asm volatile("st.global.f32 [%0], %1;" ::"l"(p + 3), "f"(v.w) : "memory");
 }
 
 template <int L>
