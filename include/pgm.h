@@ -60,6 +60,7 @@ typedef int32_t pgm_status;
 /* Bits of the device status word (pgm_device_flags). */
 #define PGM_FLAG_CONTRADICTION 1u /* a message or belief had every state at -inf */
 #define PGM_FLAG_NAN 2u           /* a NaN reached a belief */
+#define PGM_FLAG_INDEX 4u         /* checked mode: an index array entry out of range (pgm_checked_report) */
 
 /* Limits of this build (checked by pgm_build). */
 #define PGM_MAX_STATES 256        /* states per variable */
@@ -299,6 +300,28 @@ pgm_status pgm_grad(pgm_graph *g, const float *log_pot, const float *evidence, f
 pgm_status pgm_device_flags(pgm_graph *g, uint32_t *flags, int32_t clear, void *stream);
 
 /*
+ * Checked mode: the first index-array violation found on this graph (*array = -1 if
+ * none): the array (0 vs_off, 1 vin_off, 2 vin_es, 3 edge_vs, 4 edge_var, 5 vin_tab4,
+ * 6 lr_pos, 7 paroff_pool, 8 cfg_pool, 9 configuration lists, 10 enumeration group
+ * records, 11 logical group records, 12 variable lists), the entry's position (the
+ * record's index for 10 and 11) and its value (-1 where none is read back). Host only.
+ */
+pgm_status pgm_checked_report(const pgm_graph *g, int32_t *array, int64_t *position, int64_t *value);
+
+/*
+ * Host only, no GPU: compiles a description and runs the checked-mode range checks on
+ * the host copies of its index arrays (the same rules as the device checks), after
+ * writing corrupt_value into entry corrupt_pos of array corrupt_array (ids as in
+ * pgm_checked_report; for the records 10 / 11 the value replaces the record's first
+ * edge-state / parent-offset base; for 12 the first variable list) when corrupt_array
+ * >= 0. *bad_array, *bad_pos = the first violation in array order, -1 if none. For tests
+ * of the checks on hosts without a GPU. PGM_EINVAL for a bad description or a corrupt
+ * position outside the array.
+ */
+pgm_status pgm_audit_desc(const pgm_graph_desc *desc, int32_t corrupt_array, int64_t corrupt_pos,
+                          int64_t corrupt_value, int32_t *bad_array, int64_t *bad_pos);
+
+/*
  * Allocation-free LBP on a rows x cols grid of binary variables with one pairwise factor
  * per pair of 4-neighbours. The paper has no counterpart: this entry point exists for
  * callers that cannot allocate device memory -- a process whose device memory is owned
@@ -470,6 +493,22 @@ pgm_status pgm_run_bp_until_members(pgm_graph *g, const float *log_pot, const fl
  * Values outside 0..3: PGM_EINVAL.
  */
 #define PGM_OPT_PAIR_FORM 4
+/*
+ * PGM_OPT_CHECKED (default 0): 1 turns on checked mode. Every call that launches kernels
+ * on the graph (pgm_run_bp and the runs built on it, pgm_beliefs, pgm_decode, pgm_grad,
+ * pgm_autotune, pgm_infer_host) first range-checks, on the device, every entry of the
+ * graph's index arrays -- the per-variable state offsets and incoming-edge lists, each
+ * edge's variable state, the padded incoming-edge table, the log-ratio slot map, the
+ * logical groups' parent offsets, the configuration tables and lists by output state,
+ * the group records of every launch and the variable lists of the variable pass --
+ * against the range the kernels assume (these arrays are where every gathered index of
+ * Sec. 4's flat layout comes from), and waits for the result. On a violation it raises
+ * PGM_FLAG_INDEX in the status word (pgm_device_flags), keeps the array, position and
+ * value for pgm_checked_report, and returns PGM_EINVAL without launching anything that
+ * reads the arrays; nothing traps. The checks synchronise the stream on every call.
+ * Values other than 0 and 1: PGM_EINVAL.
+ */
+#define PGM_OPT_CHECKED 5
 pgm_status pgm_set_option(pgm_graph *g, int32_t option, int64_t value);
 /*
  * The option's effective value in *value: for PGM_OPT_CUDA_GRAPH and

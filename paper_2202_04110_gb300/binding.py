@@ -19,17 +19,19 @@ STATUS_NAMES = {-1: "PGM_EINVAL", -2: "PGM_ENOMEM", -3: "PGM_ECUDA", -4: "PGM_EN
                 -5: "PGM_EBUSY", -6: "PGM_ETIMEDOUT"}
 FLAG_CONTRADICTION = 1
 FLAG_NAN = 2
+FLAG_INDEX = 4
 
 # Every symbol include/pgm.h declares.
 EXPORTED = ["pgm_build", "pgm_build_batch", "pgm_batch_member", "pgm_check_desc", "pgm_free", "pgm_graph_info", "pgm_run_bp", "pgm_beliefs",
             "pgm_decode", "pgm_infer_host", "pgm_set_profiling", "pgm_pass_times", "pgm_launch_times",
-            "pgm_device_flags", "pgm_grid2_run_bp_noalloc", "pgm_grid2_noalloc_flags", "pgm_run_bp_multi", "pgm_pmp_sample", "pgm_run_bp_until", "pgm_run_bp_until_members", "pgm_run_bp_batch", "pgm_set_option", "pgm_get_option", "pgm_autotune",
+            "pgm_device_flags", "pgm_checked_report", "pgm_audit_desc", "pgm_grid2_run_bp_noalloc", "pgm_grid2_noalloc_flags", "pgm_run_bp_multi", "pgm_pmp_sample", "pgm_run_bp_until", "pgm_run_bp_until_members", "pgm_run_bp_batch", "pgm_set_option", "pgm_get_option", "pgm_autotune",
             "pgm_launch_info", "pgm_grad", "pgm_serve_create", "pgm_serve_submit", "pgm_serve_submit_until", "pgm_serve_submit_borrowed", "pgm_serve_poll",
             "pgm_serve_wait", "pgm_serve_stats", "pgm_serve_destroy", "pgm_last_error"]
 OPT_CUDA_GRAPH = 1
 OPT_LOG_RATIO = 2
 OPT_ENUM_BLOCK = 3
 OPT_PAIR_FORM = 4
+OPT_CHECKED = 5
 
 
 class PgmError(RuntimeError):
@@ -128,6 +130,11 @@ def load_library(path: str | None = None):
     lib.pgm_pass_times.restype = i32
     lib.pgm_pass_times.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                                    ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
+    lib.pgm_checked_report.restype = i32
+    lib.pgm_checked_report.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
+    lib.pgm_audit_desc.restype = i32
+    lib.pgm_audit_desc.argtypes = [ctypes.POINTER(GraphDescC), i32, ctypes.c_int64, ctypes.c_int64, ctypes.POINTER(i32),
+                                   ctypes.POINTER(ctypes.c_int64)]
     lib.pgm_launch_times.restype = i32
     lib.pgm_launch_times.argtypes = [vp, i32, vp, vp, ctypes.POINTER(i32)]
     lib.pgm_device_flags.restype = i32
@@ -470,6 +477,12 @@ class Graph:
         k = min(int(npos.value), n)
         return [(float(ms[i]), int(cnt[i])) for i in range(k)]
 
+    def checked_report(self):
+        """(array id, position, value) of the first checked-mode violation, array -1 if none."""
+        a, pos, val = ctypes.c_int32(), ctypes.c_int64(), ctypes.c_int64()
+        check(load_library().pgm_checked_report(self._h, ctypes.byref(a), ctypes.byref(pos), ctypes.byref(val)))
+        return a.value, pos.value, val.value
+
     def flags(self, clear: bool = False, stream=None) -> int:
         f = ctypes.c_uint32(0)
         check(load_library().pgm_device_flags(self._h, ctypes.byref(f), int(bool(clear)), _stream_ptr(stream)))
@@ -490,6 +503,18 @@ def grid2_run_bp_noalloc(rows: int, cols: int, log_pot, evidence, T: float, damp
         _dptr(evidence, torch.float32, 2 * rows * cols, "evidence"), float(T), float(damping),
         int(n_iters), _dptr(msgs, torch.float32, 4 * F, "msgs") if F else 0, _stream_ptr(stream)))
     return msgs
+
+
+def audit_desc(fg, corrupt_array: int = -1, corrupt_pos: int = 0, corrupt_value: int = 0):
+    """pgm_audit_desc: the checked-mode range checks run on the host copies of a
+    description's index arrays (optionally after corrupting one entry). Returns (array,
+    position) of the first violation, (-1, -1) if none. No GPU needed."""
+    desc, keep = marshal_desc(fg)
+    a, pos = ctypes.c_int32(), ctypes.c_int64()
+    check(load_library().pgm_audit_desc(ctypes.byref(desc), int(corrupt_array), int(corrupt_pos), int(corrupt_value),
+                                        ctypes.byref(a), ctypes.byref(pos)))
+    del keep
+    return a.value, pos.value
 
 
 def grid2_noalloc_flags(clear: bool = False, stream=None) -> int:

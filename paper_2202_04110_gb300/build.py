@@ -15,8 +15,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD_DIR = os.path.join(HERE, "_build")
 LIB_PATH = os.path.join(HERE, "libpgm.so")
-SOURCES = ["compile.cpp", "kernels.cu", "capi.cu", "noalloc.cu", "serve.cu"]
-HEADERS = [os.path.join(CSRC, "pgm_internal.h"), os.path.join(ROOT, "include", "pgm.h")]
+SOURCES = ["compile.cpp", "kernels.cu", "capi.cu", "noalloc.cu", "serve.cu", "audit.cu"]
+HEADERS = [os.path.join(CSRC, "pgm_internal.h"), os.path.join(CSRC, "audit.h"), os.path.join(ROOT, "include", "pgm.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -10,6 +10,10 @@
 #pragma once
 
 #include <cstdint>
+#include <utility>
+#include <vector>
+
+#include <cuda_runtime.h>
 
 #include "pgm_internal.h"
 
@@ -105,5 +109,16 @@ __host__ __device__ __forceinline__ bool audit_bs_ok(const EnumSeg &s, int64_t i
     if (s.packed) return x >= 0 && (x >> 11) < s.n_cfg && (x & 2047) < s.es_per_fac;
     return x >= 0 && x < s.n_cfg;
 }
+
+// audit.cu: the audit on the host (first violation in array-id order, -1 if none) and
+// on the device (enqueued on s, waits; raises PGM_FLAG_INDEX in *flags on a violation;
+// `work` is a device buffer of audit_work_bytes(flat.size()) bytes).
+const char *audit_array_name(int id);
+void audit_host(const std::vector<AuditArray> &flat, const std::vector<EnumSeg> &esegs,
+                const std::vector<LogicSeg> &lsegs, const AuditSizes &z, int32_t *bad_array, int64_t *bad_pos);
+size_t audit_work_bytes(size_t n_flat);
+cudaError_t audit_device(const std::vector<AuditArray> &flat, const std::vector<std::pair<const void *, int>> &enum_launches,
+                         const std::vector<std::pair<const void *, int>> &logic_launches, const AuditSizes &z,
+                         uint32_t *flags, char *work, cudaStream_t s, int32_t *bad_array, int64_t *bad_pos);
 
 }  // namespace pgm

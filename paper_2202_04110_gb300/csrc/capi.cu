@@ -5,11 +5,13 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include <cuda_runtime.h>
 
 #include "../../include/pgm.h"
+#include "audit.h"
 #include "pgm_internal.h"
 
 using namespace pgm;
@@ -133,6 +135,13 @@ struct pgm_graph {
     size_t adj_logic_seg_off = (size_t)-1;
     int32_t enum_block = 0;  // PGM_OPT_ENUM_BLOCK
     int32_t pair_form = 0;   // PGM_OPT_PAIR_FORM
+    // checked mode (PGM_OPT_CHECKED): the audit's work buffer (allocated on first use),
+    // the pools' sizes, the last violation found
+    int32_t checked = 0;
+    char *audit_mem = nullptr;
+    int64_t cfg_size = 0, bs_size = 0, paroff_size = 0;
+    int32_t bad_array = -1;
+    int64_t bad_pos = -1, bad_value = 0;
     std::vector<std::vector<char>> factor_segs_host;  // host copy of each factor launch's segments
     // CUDA graphs of whole pgm_run_bp calls, keyed by their arguments (LRU)
     struct CachedRun {
@@ -223,6 +232,20 @@ bool lr_eligible(const HostLayout &H) {
 
 // Slots of each log-ratio array: 4 per variable with the 4-slot table, else one per edge.
 int64_t lr_slot_count(const HostLayout &H) { return H.vin_tab4.empty() ? H.E : 4 * H.V; }
+
+std::vector<int32_t> lr_slot_map(const HostLayout &H) {
+    std::vector<int32_t> pos((size_t)H.E, -1);
+    if (!H.vin_tab4.empty()) {
+        for (int64_t v = 0; v < H.V; ++v)
+            for (int k = 0; k < 4; ++k) {
+                const int32_t es = H.vin_tab4[4 * v + k];
+                if (es >= 0) pos[es >> 1] = (int32_t)(k * H.V + v);
+            }
+    } else {
+        for (int64_t k = 0; k < H.E; ++k) pos[H.vin_es[k] >> 1] = (int32_t)k;
+    }
+    return pos;
+}
 
 // Block-per-factor enumeration launch (kEnumBlock) with `threads` threads: each segment's
 // factors per block (one wave of resident blocks for a large group) and threads per output
@@ -449,6 +472,88 @@ pgm_status accumulate_groups(pgm_graph *g, const std::vector<cudaEvent_t> &ev, c
     return PGM_OK;
 }
 
+// Checked mode: the graph's flat index arrays (device pointers) and their ranges.
+std::vector<AuditArray> device_audit_arrays(const pgm_graph *g) {
+    const DevGraph &G = g->G;
+    const int64_t V = G.V, VS = G.VS, E = G.E, ES = G.ES;
+    std::vector<AuditArray> a;
+    auto add = [&](const int32_t *p, int64_t n, int64_t lo, int64_t hi, bool neg, int id) {
+        if (p && n > 0) a.push_back(AuditArray{p, n, lo, hi, neg ? 1 : 0, id});
+    };
+    add(G.vs_off, V + 1, 0, VS + 1, false, kAuditVsOff);
+    add(G.vin_off, V + 1, 0, E + 1, false, kAuditVinOff);
+    add(G.vin_es, E, 0, ES, false, kAuditVinEs);
+    add(G.edge_vs, E, 0, VS, true, kAuditEdgeVs);
+    add(G.edge_var, E, 0, V, false, kAuditEdgeVar);
+    add(reinterpret_cast<const int32_t *>(G.vin_tab4), 4 * V, 0, ES, true, kAuditTab4);
+    add(G.lr_pos, E, 0, g->lr_slots, false, kAuditLrPos);
+    add(G.paroff_pool, g->paroff_size, 0, E + 1, false, kAuditParOff);
+    for (const VarLaunch &L : g->P.var) add(L.list, L.n, 0, V, false, kAuditVarList);
+    return a;
+}
+
+// Checked mode (PGM_OPT_CHECKED): before a call's kernels, the device audit of every
+// index array and group record; a violation is recorded and ends the call with
+// PGM_EINVAL before any LBP kernel reads the bad index.
+pgm_status checked_gate(pgm_graph *g, void *stream) {
+    if (!g->checked) return PGM_OK;
+    DeviceGuard dg(g->device);
+    const std::vector<AuditArray> flat = device_audit_arrays(g);
+    const size_t need = audit_work_bytes(flat.size());
+    if (!g->audit_mem && cudaMalloc(&g->audit_mem, need) != cudaSuccess) {
+        g->audit_mem = nullptr;
+        return fail(PGM_ENOMEM, "cudaMalloc(index audit)");
+    }
+    std::vector<std::pair<const void *, int>> enums, logics;
+    auto add_launch = [&](const FactorLaunch &L) {
+        if (!L.segs || L.n_seg <= 0) return;
+        if (L.variant == kLogicSmall || L.variant == kLogicWarp) logics.emplace_back(L.segs, L.n_seg);
+        else enums.emplace_back(L.segs, L.n_seg);
+    };
+    for (const FactorLaunch &L : g->P.factor) add_launch(L);
+    if (g->adj_launch.segs) enums.emplace_back(g->adj_launch.segs, g->adj_launch.n_seg);
+    if (g->adj_block_launch.segs) enums.emplace_back(g->adj_block_launch.segs, g->adj_block_launch.n_seg);
+    if (g->adj_logic_launch.segs) logics.emplace_back(g->adj_logic_launch.segs, g->adj_logic_launch.n_seg);
+    const DevGraph &G = g->G;
+    const AuditSizes z{G.V, G.VS, G.E, G.ES, g->info.n_potentials, g->cfg_size, g->bs_size, g->paroff_size,
+                       G.cfg_pool, G.bs_pool, G.paroff_pool};
+    int32_t bad = -1;
+    int64_t pos = -1;
+    cudaError_t e = audit_device(flat, enums, logics, z, G.flags, g->audit_mem, static_cast<cudaStream_t>(stream),
+                                 &bad, &pos);
+    if (e != cudaSuccess) return cuda_fail(e, "index audit");
+    if (bad < 0) return PGM_OK;
+    // the offending entry's value, read back for the report
+    int64_t value = -1;
+    for (const AuditArray &a : flat)
+        if (a.id == bad) {
+            int32_t v = 0;
+            const AuditArray *hit = &a;
+            if (bad == kAuditVarList) {  // several lists share the id: the first one holding pos
+                hit = nullptr;
+                for (const AuditArray &b : flat)
+                    if (b.id == bad && pos < b.n) {
+                        hit = &b;
+                        break;
+                    }
+            }
+            if (hit && cudaMemcpy(&v, hit->p + pos, sizeof v, cudaMemcpyDeviceToHost) == cudaSuccess) value = v;
+            break;
+        }
+    if (bad == kAuditCfg) {
+        uint8_t v = 0;
+        if (cudaMemcpy(&v, G.cfg_pool + pos, 1, cudaMemcpyDeviceToHost) == cudaSuccess) value = v;
+    } else if (bad == kAuditBs) {
+        int32_t v = 0;
+        if (cudaMemcpy(&v, G.bs_pool + pos, sizeof v, cudaMemcpyDeviceToHost) == cudaSuccess) value = v;
+    }
+    g->bad_array = bad;
+    g->bad_pos = pos;
+    g->bad_value = value;
+    return fail(PGM_EINVAL, std::string("checked mode: ") + audit_array_name(bad) + " entry " + std::to_string(pos) +
+                                " (value " + std::to_string(value) + ") is out of range; nothing was run");
+}
+
 pgm_status check_run_args(pgm_graph *g, const float *log_pot, const float *evidence, float T,
                           float damping, int32_t n_iters, const float *msgs) {
     if (!g) return fail(PGM_EINVAL, "graph is NULL");
@@ -510,16 +615,7 @@ static pgm_status build_from_descs(const void *const *descs, int n, pgm_graph **
     // variable), else the edge's CSR index
     size_t o_lr_pos = 0;
     if (g->P.lr) {
-        std::vector<int32_t> pos((size_t)H.E, -1);
-        if (!H.vin_tab4.empty()) {
-            for (int64_t v = 0; v < H.V; ++v)
-                for (int k = 0; k < 4; ++k) {
-                    const int32_t es = H.vin_tab4[4 * v + k];
-                    if (es >= 0) pos[es >> 1] = (int32_t)(k * H.V + v);
-                }
-        } else {
-            for (int64_t k = 0; k < H.E; ++k) pos[H.vin_es[k] >> 1] = (int32_t)k;
-        }
+        const std::vector<int32_t> pos = lr_slot_map(H);
         g->lr_slots = lr_slot_count(H);
         o_lr_pos = pk.add(pos.data(), pos.size());
     }
@@ -625,6 +721,9 @@ static pgm_status build_from_descs(const void *const *descs, int n, pgm_graph **
     I.launches_per_iter = g->var_launches + g->factor_launches;
     I.n_members = (int32_t)H.members.size();
     g->members = H.members;
+    g->cfg_size = (int64_t)H.cfg_pool.size();
+    g->bs_size = (int64_t)H.bs_pool.size();
+    g->paroff_size = (int64_t)H.paroff_pool.size();
     *out = g;
     return PGM_OK;
 }
@@ -728,6 +827,7 @@ void pgm_free(pgm_graph *g) {
     if (g->until_res_host) cudaFreeHost(g->until_res_host);
     if (g->mu_mem) cudaFree(g->mu_mem);
     if (g->bm_mem) cudaFree(g->bm_mem);
+    if (g->audit_mem) cudaFree(g->audit_mem);
     if (g->mse_mem) cudaFree(g->mse_mem);
     for (cudaEvent_t e : g->events) cudaEventDestroy(e);
     drop_cached_runs(g);
@@ -1012,6 +1112,7 @@ pgm_status pgm_run_bp_multi(pgm_graph *g, int32_t n_samples, const float *log_po
     if (n_samples < 1) return fail(PGM_EINVAL, "n_samples must be >= 1");
     pgm_status st = check_run_args(g, log_pot, evidence, T, damping, n_iters, msgs);
     if (st != PGM_OK) return st;
+    if ((st = checked_gate(g, stream)) != PGM_OK) return st;
     if (n_iters == 0 || g->info.n_edge_states == 0) return PGM_OK;
     const int64_t VS = g->info.n_var_states, ES = g->info.n_edge_states, P = g->info.n_potentials;
     const bool ms = log_ratio_run(g, n_iters) && g->G.vin_tab4 != nullptr &&
@@ -1169,6 +1270,7 @@ pgm_status pgm_run_bp_until(pgm_graph *g, const float *log_pot, const float *evi
     if (st != PGM_OK) return st;
     if (check_every < 1) return fail(PGM_EINVAL, "check_every must be >= 1");
     if (!(tol >= 0.f)) return fail(PGM_EINVAL, "tol must be >= 0");
+    if ((st = checked_gate(g, stream)) != PGM_OK) return st;
     const int64_t ES = g->info.n_edge_states;
     if (max_iters == 0 || ES == 0) {
         if (residual && ES == 0) *residual = 0.f;
@@ -1359,6 +1461,7 @@ pgm_status pgm_run_bp_until_members(pgm_graph *g, const float *log_pot, const fl
     if (!iters_done || !residual) return fail(PGM_EINVAL, "iters_done / residual is NULL");
     if (check_every < 1) return fail(PGM_EINVAL, "check_every must be >= 1");
     if (!(tol >= 0.f)) return fail(PGM_EINVAL, "tol must be >= 0");
+    if ((st = checked_gate(g, stream)) != PGM_OK) return st;
     const int nm = (int)g->members.size();
     const int64_t ES = g->info.n_edge_states;
     for (int m = 0; m < nm; ++m) {
@@ -1417,6 +1520,7 @@ pgm_status pgm_run_bp_batch(pgm_graph *g, const float *log_pot, const float *evi
                             const float *damping, const int32_t *n_iters, float *msgs, void *stream) {
     pgm_status st = check_run_args(g, log_pot, evidence, 1.f, 0.f, 0, msgs);
     if (st != PGM_OK) return st;
+    if ((st = checked_gate(g, stream)) != PGM_OK) return st;
     if (!T || !damping || !n_iters) return fail(PGM_EINVAL, "T / damping / n_iters is NULL");
     const int nm = (int)g->members.size();
     const int64_t ES = g->info.n_edge_states;
@@ -1533,6 +1637,7 @@ pgm_status pgm_run_bp(pgm_graph *g, const float *log_pot, const float *evidence,
                       float damping, int32_t n_iters, float *msgs, void *stream) {
     pgm_status st = check_run_args(g, log_pot, evidence, T, damping, n_iters, msgs);
     if (st != PGM_OK) return st;
+    if ((st = checked_gate(g, stream)) != PGM_OK) return st;
     if (n_iters == 0 || g->info.n_edge_states == 0) return PGM_OK;
     DeviceGuard dg(g->device);
     if (!dg.ok) return fail(PGM_ECUDA, "cudaSetDevice failed");
@@ -1626,6 +1731,7 @@ pgm_status pgm_autotune(pgm_graph *g, const float *log_pot, const float *evidenc
                         float damping, void *stream) {
     pgm_status st = check_run_args(g, log_pot, evidence, T, damping, 1, g ? g->m_tmp : nullptr);
     if (st != PGM_OK) return st;
+    if ((st = checked_gate(g, stream)) != PGM_OK) return st;
     if (g->info.n_edge_states == 0) return PGM_OK;
     DeviceGuard dg(g->device);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -1826,6 +1932,7 @@ pgm_status pgm_grad(pgm_graph *g, const float *log_pot, const float *evidence, f
     if (n_iters < 0 || ckpt_every < 1) return fail(PGM_EINVAL, "n_iters >= 0 and ckpt_every >= 1 required");
     if (!evidence || !d_beliefs || !d_evidence || (g->info.n_potentials > 0 && (!log_pot || !d_log_pot)))
         return fail(PGM_EINVAL, "NULL argument");
+    if (pgm_status st = checked_gate(g, stream); st != PGM_OK) return st;
     DeviceGuard dg(g->device);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const size_t total = grad_work_bytes(g, n_iters, ckpt_every);
@@ -1926,6 +2033,10 @@ pgm_status pgm_set_option(pgm_graph *g, int32_t option, int64_t value) {
             g->enum_block = (int32_t)value;
             return PGM_OK;
         }
+        case PGM_OPT_CHECKED:
+            if (value != 0 && value != 1) return fail(PGM_EINVAL, "PGM_OPT_CHECKED must be 0 or 1");
+            g->checked = (int32_t)value;
+            return PGM_OK;
         case PGM_OPT_PAIR_FORM: {
             if (value < 0 || value > 3) return fail(PGM_EINVAL, "PGM_OPT_PAIR_FORM must be 0..3");
             DeviceGuard dg(g->device);
@@ -1979,6 +2090,9 @@ pgm_status pgm_get_option(const pgm_graph *g, int32_t option, int64_t *value) {
         case PGM_OPT_PAIR_FORM:
             *value = g->pair_form;
             return PGM_OK;
+        case PGM_OPT_CHECKED:
+            *value = g->checked;
+            return PGM_OK;
         default:
             return fail(PGM_EINVAL, "unknown option");
     }
@@ -1988,6 +2102,7 @@ pgm_status pgm_beliefs(pgm_graph *g, const float *evidence, const float *msgs, f
                        int32_t normalise, void *stream) {
     if (!g || !evidence || !out) return fail(PGM_EINVAL, "NULL argument");
     if (!msgs && g->info.n_edge_states > 0) return fail(PGM_EINVAL, "msgs is NULL");
+    if (pgm_status st = checked_gate(g, stream); st != PGM_OK) return st;
     DeviceGuard dg(g->device);
     cudaError_t e = launch_var_pass(g->G, g->P, evidence, msgs, out,
                                     normalise ? kVarNormalised : kVarBeliefs, nullptr,
@@ -2000,6 +2115,7 @@ pgm_status pgm_decode(pgm_graph *g, const float *evidence, const float *msgs, in
                       void *stream) {
     if (!g || !evidence || !out) return fail(PGM_EINVAL, "NULL argument");
     if (!msgs && g->info.n_edge_states > 0) return fail(PGM_EINVAL, "msgs is NULL");
+    if (pgm_status st = checked_gate(g, stream); st != PGM_OK) return st;
     DeviceGuard dg(g->device);
     cudaError_t e = launch_var_pass(g->G, g->P, evidence, msgs, nullptr, kVarDecode, out,
                                     static_cast<cudaStream_t>(stream));
@@ -2012,6 +2128,7 @@ pgm_status pgm_infer_host(pgm_graph *g, const float *log_pot, const float *evide
                           void *stream) {
     if (!g || !evidence) return fail(PGM_EINVAL, "NULL argument");
     if (!log_pot && g->info.n_potentials > 0) return fail(PGM_EINVAL, "log_pot is NULL");
+    if (pgm_status st = checked_gate(g, stream); st != PGM_OK) return st;
     DeviceGuard dg(g->device);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const pgm_info &I = g->info;
@@ -2110,6 +2227,85 @@ pgm_status pgm_launch_times(pgm_graph *g, int32_t n, double *ms, int64_t *count,
     }
     if (n_positions) *n_positions = np;
     reset_times(g);
+    return PGM_OK;
+}
+
+pgm_status pgm_checked_report(const pgm_graph *g, int32_t *array, int64_t *position, int64_t *value) {
+    if (!g || !array || !position || !value) return fail(PGM_EINVAL, "NULL argument");
+    *array = g->bad_array;
+    *position = g->bad_pos;
+    *value = g->bad_array >= 0 ? g->bad_value : 0;
+    return PGM_OK;
+}
+
+pgm_status pgm_audit_desc(const pgm_graph_desc *desc, int32_t corrupt_array, int64_t corrupt_pos,
+                          int64_t corrupt_value, int32_t *bad_array, int64_t *bad_pos) {
+    g_last_error.clear();
+    if (!bad_array || !bad_pos) return fail(PGM_EINVAL, "NULL argument");
+    HostLayout H;
+    const void *one = desc;
+    std::string err = compile_graph(&one, 1, &H);
+    if (!err.empty()) return fail(PGM_EINVAL, err);
+    std::vector<int32_t> lr = lr_eligible(H) ? lr_slot_map(H) : std::vector<int32_t>{};
+    std::vector<EnumSeg> esegs;
+    std::vector<LogicSeg> lsegs;
+    for (const HostEnumGroup &hg : H.enum_groups) esegs.push_back(hg.seg);
+    for (const HostLogicGroup &hg : H.logic_groups) lsegs.push_back(hg.seg);
+    std::vector<std::vector<int32_t>> lists;
+    for (int k = 0; k < kNumVarKinds; ++k)
+        if (!H.var_bucket[k].empty() && !H.var_bucket_identity[k]) lists.push_back(H.var_bucket[k]);
+    // the test's corruption of one entry (corrupt_array < 0: none)
+    if (corrupt_array >= 0) {
+        auto poke = [&](auto &vec, const char *name) -> pgm_status {
+            if (corrupt_pos < 0 || corrupt_pos >= (int64_t)vec.size())
+                return fail(PGM_EINVAL, std::string("corrupt_pos outside ") + name);
+            vec[(size_t)corrupt_pos] = (typename std::decay_t<decltype(vec)>::value_type)corrupt_value;
+            return PGM_OK;
+        };
+        pgm_status st = PGM_OK;
+        switch (corrupt_array) {
+            case kAuditVsOff: st = poke(H.vs_off, "vs_off"); break;
+            case kAuditVinOff: st = poke(H.vin_off, "vin_off"); break;
+            case kAuditVinEs: st = poke(H.vin_es, "vin_es"); break;
+            case kAuditEdgeVs: st = poke(H.edge_vs, "edge_vs"); break;
+            case kAuditEdgeVar: st = poke(H.edge_var, "edge_var"); break;
+            case kAuditTab4: st = poke(H.vin_tab4, "vin_tab4"); break;
+            case kAuditLrPos: st = poke(lr, "lr_pos"); break;
+            case kAuditParOff: st = poke(H.paroff_pool, "paroff_pool"); break;
+            case kAuditCfg: st = poke(H.cfg_pool, "cfg_pool"); break;
+            case kAuditBs: st = poke(H.bs_pool, "bs_pool"); break;
+            case kAuditEnumSeg:
+                if (corrupt_pos < 0 || corrupt_pos >= (int64_t)esegs.size()) return fail(PGM_EINVAL, "no such record");
+                esegs[(size_t)corrupt_pos].es_base = (int32_t)corrupt_value;
+                break;
+            case kAuditLogicSeg:
+                if (corrupt_pos < 0 || corrupt_pos >= (int64_t)lsegs.size()) return fail(PGM_EINVAL, "no such record");
+                lsegs[(size_t)corrupt_pos].paroff_base = (int32_t)corrupt_value;
+                break;
+            case kAuditVarList:
+                if (lists.empty()) return fail(PGM_EINVAL, "the graph has no variable lists");
+                st = poke(lists[0], "variable lists");
+                break;
+            default: return fail(PGM_EINVAL, "unknown array id");
+        }
+        if (st != PGM_OK) return st;
+    }
+    std::vector<AuditArray> flat;
+    auto add = [&](const int32_t *p, int64_t n, int64_t lo, int64_t hi, bool neg, int id) {
+        if (n > 0) flat.push_back(AuditArray{p, n, lo, hi, neg ? 1 : 0, id});
+    };
+    add(H.vs_off.data(), H.V + 1, 0, H.VS + 1, false, kAuditVsOff);
+    add(H.vin_off.data(), H.V + 1, 0, H.E + 1, false, kAuditVinOff);
+    add(H.vin_es.data(), (int64_t)H.vin_es.size(), 0, H.ES, false, kAuditVinEs);
+    add(H.edge_vs.data(), (int64_t)H.edge_vs.size(), 0, H.VS, true, kAuditEdgeVs);
+    add(H.edge_var.data(), (int64_t)H.edge_var.size(), 0, H.V, false, kAuditEdgeVar);
+    add(H.vin_tab4.data(), (int64_t)H.vin_tab4.size(), 0, H.ES, true, kAuditTab4);
+    add(lr.data(), (int64_t)lr.size(), 0, lr_slot_count(H), false, kAuditLrPos);
+    add(H.paroff_pool.data(), (int64_t)H.paroff_pool.size(), 0, H.E + 1, false, kAuditParOff);
+    for (const auto &l : lists) add(l.data(), (int64_t)l.size(), 0, H.V, false, kAuditVarList);
+    const AuditSizes z{H.V, H.VS, H.E, H.ES, H.P, (int64_t)H.cfg_pool.size(), (int64_t)H.bs_pool.size(),
+                       (int64_t)H.paroff_pool.size(), H.cfg_pool.data(), H.bs_pool.data(), H.paroff_pool.data()};
+    audit_host(flat, esegs, lsegs, z, bad_array, bad_pos);
     return PGM_OK;
 }
 
