@@ -556,10 +556,11 @@ pgm_status pgm_launch_info(const pgm_graph *g, int32_t i, int32_t *kind, int32_t
  * copied at submission), T, damping and an iteration count; its result is the
  * normalised log-beliefs and the MAP decode after n_iters iterations from zero messages
  * (pgm_run_bp + pgm_beliefs + pgm_decode). Requests queue in arrival order; up to
- * max_in_flight of them are on the GPU at once, each on its own stream, and the one at
- * the head of the queue is admitted as soon as a slot is free and its device memory
- * (compiled graph, scratch, inputs, outputs; stream-ordered allocations) fits
- * memory_budget_bytes together with the requests in flight. Kernels of in-flight
+ * max_in_flight of them are on the GPU at once, each on its own stream. A free worker
+ * takes the head of the queue and compiles its graph on the host (once; the workers
+ * compile in parallel), and requests are admitted in arrival order, each as soon as its
+ * device memory (compiled graph, scratch, inputs, outputs; stream-ordered allocations)
+ * fits memory_budget_bytes together with the requests in flight. Kernels of in-flight
  * requests overlap on the device; a request's messages stay resident until it
  * finishes; max_in_flight = 1 runs one request at a time in arrival order. Results are
  * those of the same request run alone. Latency = submission to results in host memory.
@@ -578,6 +579,11 @@ typedef struct {
     int64_t bytes_in_use, peak_bytes; /* device memory accounted to requests in flight */
     int64_t updates_done;             /* edge-state message updates of completed requests */
     double span_s;                    /* first submission to last completion, seconds */
+    /* where completed requests spent their latency, seconds summed over them: in the
+     * queue until a worker took them, compiling the graph on the host, waiting for
+     * admission (their turn in arrival order and device memory), and on the device
+     * (build and upload, iterations, read-back, free) */
+    double queue_s, compile_s, admit_s, run_s;
 } pgm_server_stats;
 
 /* Create a server on the current device (starts max_in_flight worker threads). */

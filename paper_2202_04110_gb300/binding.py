@@ -73,7 +73,8 @@ class ServerConfigC(ctypes.Structure):
 
 class ServerStatsC(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int64) for n in ("submitted", "completed", "failed", "pending", "in_flight",
-                                              "bytes_in_use", "peak_bytes", "updates_done")] + [("span_s", ctypes.c_double)]
+                                              "bytes_in_use", "peak_bytes", "updates_done")] + \
+               [(n, ctypes.c_double) for n in ("span_s", "queue_s", "compile_s", "admit_s", "run_s")]
 
 
 class MemberC(ctypes.Structure):

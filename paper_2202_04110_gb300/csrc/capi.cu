@@ -577,6 +577,8 @@ const char *pgm_last_error(void) { return g_last_error.c_str(); }
 
 // Build a graph. With `ordered`, every allocation, copy and free of the graph is
 // stream-ordered on `s` (no device-wide synchronisation; used by the serving loop).
+static pgm_status build_from_layout(const HostLayout &H, pgm_graph **out, cudaStream_t s, bool ordered);
+
 static pgm_status build_from_descs(const void *const *descs, int n, pgm_graph **out, cudaStream_t s = nullptr,
                                    bool ordered = false) {
     g_last_error.clear();
@@ -585,6 +587,13 @@ static pgm_status build_from_descs(const void *const *descs, int n, pgm_graph **
     HostLayout H;
     std::string err = compile_graph(descs, n, &H);
     if (!err.empty()) return fail(PGM_EINVAL, err);
+    return build_from_layout(H, out, s, ordered);
+}
+
+// Build a graph from a compiled layout (the device part of pgm_build).
+static pgm_status build_from_layout(const HostLayout &H, pgm_graph **out, cudaStream_t s, bool ordered) {
+    if (!out) return fail(PGM_EINVAL, "out is NULL");
+    *out = nullptr;
     pgm_graph *g = new (std::nothrow) pgm_graph();
     if (!g) return fail(PGM_ENOMEM, "host allocation failed");
     cudaError_t ce = cudaGetDevice(&g->device);
@@ -742,6 +751,29 @@ pgm_status pgm::build_graph_on_stream(const pgm_graph_desc *desc, cudaStream_t s
     return st;
 }
 
+int64_t pgm::layout_device_bytes(const HostLayout &H) {
+    size_t nb = 0;
+    for (int kk = 0; kk < kNumVarKinds; ++kk) nb += H.var_bucket_identity[kk] ? 0 : H.var_bucket[kk].size();
+    size_t idx = (H.vs_off.size() + H.vin_off.size() + H.vin_es.size() + H.edge_vs.size() +
+                  H.paroff_pool.size() + H.bs_pool.size() + H.edge_var.size() + nb + H.vin_tab4.size()) *
+                     sizeof(int32_t) +
+                 H.cfg_pool.size();
+    size_t es_bytes = align_up(std::max<int64_t>(H.ES, 1) * sizeof(float), 256);
+    if (lr_eligible(H))  // the slot map, the two log-ratio arrays and the table differences
+        idx += H.E * sizeof(int32_t) + 2 * align_up((size_t)lr_slot_count(H) * sizeof(float), 256) +
+               align_up((size_t)3 * (H.E / 2) * sizeof(float), 256);
+    const size_t vs_bytes = align_up(std::max<int64_t>(H.VS, 1) * sizeof(float), 256);
+    return (int64_t)(idx + es_bytes + vs_bytes + 256 + (H.var_bucket[kVarBlock].empty() ? 0 : 2 * es_bytes) +
+                     (H.var_bucket[kVarWarp].empty() ? 0 : vs_bytes));
+}
+
+pgm_status pgm::build_layout_on_stream(const HostLayout &H, cudaStream_t s, pgm_graph **out) {
+    g_last_error.clear();
+    pgm_status st = build_from_layout(H, out, s, true);
+    if (st == PGM_OK) (*out)->use_cuda_graph = 0;
+    return st;
+}
+
 extern "C" {
 
 
@@ -785,19 +817,7 @@ pgm_status pgm_check_desc(const pgm_graph_desc *desc, pgm_info *info) {
     info->max_states = H.max_states;
     info->max_degree = H.max_degree;
     info->n_members = 1;
-    size_t nb = 0;
-    for (int kk = 0; kk < kNumVarKinds; ++kk) nb += H.var_bucket_identity[kk] ? 0 : H.var_bucket[kk].size();
-    size_t idx = (H.vs_off.size() + H.vin_off.size() + H.vin_es.size() + H.edge_vs.size() +
-                  H.paroff_pool.size() + H.bs_pool.size() + H.edge_var.size() + nb + H.vin_tab4.size()) *
-                     sizeof(int32_t) +
-                 H.cfg_pool.size();
-    size_t es_bytes = align_up(std::max<int64_t>(H.ES, 1) * sizeof(float), 256);
-    if (lr_eligible(H))  // the slot map, the two log-ratio arrays and the table differences
-        idx += H.E * sizeof(int32_t) + 2 * align_up((size_t)lr_slot_count(H) * sizeof(float), 256) +
-               align_up((size_t)3 * (H.E / 2) * sizeof(float), 256);
-    const size_t vs_bytes = align_up(std::max<int64_t>(H.VS, 1) * sizeof(float), 256);
-    info->device_bytes = (int64_t)(idx + es_bytes + vs_bytes + 256 + (H.var_bucket[kVarBlock].empty() ? 0 : 2 * es_bytes) +
-                                   (H.var_bucket[kVarWarp].empty() ? 0 : vs_bytes));
+    info->device_bytes = pgm::layout_device_bytes(H);
     return PGM_OK;
 }
 

@@ -292,8 +292,12 @@ int enum_block_resident(int threads, int smem);
 cudaError_t prepare_kernels(int max_smem_bytes);
 
 // Build a graph whose allocations, uploads and frees (pgm_free) are stream-ordered on
-// `s`, with CUDA-graph replay off (used by the serving loop; capi.cu).
+// `s`, with CUDA-graph replay off (used by the serving loop; capi.cu): from a description,
+// or from a layout compile_graph made (the serving loop compiles each request once).
 int32_t build_graph_on_stream(const pgm_graph_desc *desc, cudaStream_t s, pgm_graph **out);
+int32_t build_layout_on_stream(const HostLayout &H, cudaStream_t s, pgm_graph **out);
+// Device bytes a graph built from this layout holds (index arrays and scratch).
+int64_t layout_device_bytes(const HostLayout &H);
 
 // Records `msg` as the calling thread's last error (pgm_last_error) and returns `code`.
 int32_t set_last_error(int32_t code, const std::string &msg);

@@ -105,7 +105,7 @@ struct Request {
     const float *lp() const { return b_desc ? b_lp : log_pot.data(); }
     const float *ev() const { return b_desc ? b_ev : evidence.data(); }
     int32_t check_every = 0;    // early exit: residual checked every check_every iterations; 0 = off
-    Clock::time_point t_submit, t_done;
+    Clock::time_point t_submit, t_pop, t_compiled, t_admitted, t_done;
     int32_t state = kPending;
     pgm_status status = PGM_OK;
     std::string error;
@@ -126,7 +126,13 @@ struct pgm_server {
     int64_t next_id = 1, bytes_in_use = 0, peak_bytes = 0;
     int64_t submitted = 0, completed = 0, failed = 0, updates_done = 0;
     int32_t in_flight = 0;
-    bool admitting = false;  // a worker holds the queue's head while it waits for memory
+    // admission in arrival order: a worker takes the queue's head with a ticket, compiles
+    // it (in parallel with the other workers), then waits until its ticket is the next to
+    // be admitted and its memory fits
+    int64_t next_ticket = 0, next_admit = 0;
+    // seconds summed over completed requests: queue (submission to a worker), host
+    // compile, admission wait, device work (build, upload, run, read-back)
+    double sum_queue_s = 0.0, sum_compile_s = 0.0, sum_admit_s = 0.0, sum_run_s = 0.0;
     bool stop = false;
     Clock::time_point t_first_submit, t_last_done;
     std::vector<std::thread> workers;
@@ -149,6 +155,11 @@ void finish(pgm_server *s, const std::shared_ptr<Request> &r, pgm_status st, con
         s->completed += 1;
         s->updates_done += r->updates;
         s->t_last_done = r->t_done;
+        auto sec = [](Clock::time_point a, Clock::time_point b) { return std::chrono::duration<double>(b - a).count(); };
+        s->sum_queue_s += sec(r->t_submit, r->t_pop);
+        s->sum_compile_s += sec(r->t_pop, r->t_compiled);
+        s->sum_admit_s += sec(r->t_compiled, r->t_admitted);
+        s->sum_run_s += sec(r->t_admitted, r->t_done);
     } else {
         s->failed += 1;
     }
@@ -157,10 +168,11 @@ void finish(pgm_server *s, const std::shared_ptr<Request> &r, pgm_status st, con
     s->cv_work.notify_all();
 }
 
-// One request on one slot's stream. Returns the status; `err` gets the message.
-pgm_status run_request(Request &r, cudaStream_t st, std::string &err) {
+// One request on one slot's stream, from its compiled layout. Returns the status; `err`
+// gets the message.
+pgm_status run_request(Request &r, const pgm::HostLayout &H, cudaStream_t st, std::string &err) {
     pgm_graph *g = nullptr;
-    pgm_status rc = pgm::build_graph_on_stream(r.desc(), st, &g);
+    pgm_status rc = pgm::build_layout_on_stream(H, st, &g);
     if (rc != PGM_OK) {
         err = pgm_last_error();
         return rc;
@@ -213,9 +225,8 @@ pgm_status run_request(Request &r, cudaStream_t st, std::string &err) {
 
 // Device bytes a request holds while in flight (graph + its input/output buffers, and
 // with an early exit the residual buffers of pgm_run_bp_until).
-int64_t request_bytes(const pgm_info &I, bool until) {
-    return I.device_bytes + 4 * (I.n_potentials + 2 * I.n_var_states + I.n_edge_states + I.n_vars) + 2048 +
-           (until ? 4 * I.n_edge_states + 512 : 0);
+int64_t request_bytes(const pgm::HostLayout &H, bool until) {
+    return pgm::layout_device_bytes(H) + 4 * (H.P + 2 * H.VS + H.ES + H.V) + 2048 + (until ? 4 * H.ES + 512 : 0);
 }
 
 void worker_loop(pgm_server *s, int w) {
@@ -223,48 +234,58 @@ void worker_loop(pgm_server *s, int w) {
     cudaStream_t st = s->streams[w];
     for (;;) {
         std::shared_ptr<Request> r;
+        int64_t ticket = 0;
         {
             std::unique_lock<std::mutex> lk(s->mu);
-            s->cv_work.wait(lk, [&] { return s->stop || (!s->pending.empty() && !s->admitting); });
+            s->cv_work.wait(lk, [&] { return s->stop || !s->pending.empty(); });
             if (s->pending.empty()) {
                 if (s->stop) return;
                 continue;
             }
             r = s->pending.front();
             s->pending.pop_front();
-            s->admitting = true;
+            ticket = s->next_ticket++;
         }
-        // size check on the host (the compile is repeated by the build)
-        pgm_info I{};
-        pgm_status rc = pgm_check_desc(r->desc(), &I);
+        r->t_pop = Clock::now();
+        // compile once (the layout sizes the request and is built on the device below)
+        pgm::HostLayout H;
+        const void *one = r->desc();
+        std::string err = pgm::compile_graph(&one, 1, &H);
+        pgm_status rc = err.empty() ? PGM_OK : PGM_EINVAL;
+        if (rc == PGM_OK && H.P > 0 && !r->lp()) {
+            rc = PGM_EINVAL;
+            err = "log_pot is NULL";
+        }
         int64_t need = 0;
-        if (rc == PGM_OK && r->b_desc && I.n_potentials > 0 && !r->b_lp)
-            rc = pgm::set_last_error(PGM_EINVAL, "log_pot is NULL");
         if (rc == PGM_OK) {
-            need = request_bytes(I, r->check_every > 0);
-            if (need > s->cfg.memory_budget_bytes) rc = PGM_ENOMEM;
-        }
-        if (rc != PGM_OK) {
-            std::string err = rc == PGM_ENOMEM ? "request exceeds the server's memory budget" : pgm_last_error();
-            {
-                std::lock_guard<std::mutex> lk(s->mu);
-                s->admitting = false;
+            need = request_bytes(H, r->check_every > 0);
+            if (need > s->cfg.memory_budget_bytes) {
+                rc = PGM_ENOMEM;
+                err = "request exceeds the server's memory budget";
             }
+        }
+        r->t_compiled = Clock::now();
+        {
+            std::unique_lock<std::mutex> lk(s->mu);
+            s->cv_mem.wait(lk, [&] {
+                return s->stop ||
+                       (ticket == s->next_admit && (rc != PGM_OK || s->bytes_in_use + need <= s->cfg.memory_budget_bytes));
+            });
+            if (ticket == s->next_admit) s->next_admit += 1;
+            if (rc == PGM_OK) {
+                s->bytes_in_use += need;
+                s->peak_bytes = std::max(s->peak_bytes, s->bytes_in_use);
+                s->in_flight += 1;
+                r->state = kRunning;
+            }
+            s->cv_mem.notify_all();  // the next ticket
+        }
+        r->t_admitted = Clock::now();
+        if (rc != PGM_OK) {
             finish(s, r, rc, err, 0);
             continue;
         }
-        {
-            std::unique_lock<std::mutex> lk(s->mu);
-            s->cv_mem.wait(lk, [&] { return s->stop || s->bytes_in_use + need <= s->cfg.memory_budget_bytes; });
-            s->bytes_in_use += need;
-            s->peak_bytes = std::max(s->peak_bytes, s->bytes_in_use);
-            s->in_flight += 1;
-            s->admitting = false;
-            r->state = kRunning;
-            s->cv_work.notify_all();
-        }
-        std::string err;
-        rc = run_request(*r, st, err);
+        rc = run_request(*r, H, st, err);
         finish(s, r, rc, err, need);
     }
 }
@@ -404,6 +425,10 @@ pgm_status pgm_serve_stats(pgm_server *s, pgm_server_stats *out) {
     out->peak_bytes = s->peak_bytes;
     out->updates_done = s->updates_done;
     out->span_s = (s->completed > 0) ? std::chrono::duration<double>(s->t_last_done - s->t_first_submit).count() : 0.0;
+    out->queue_s = s->sum_queue_s;
+    out->compile_s = s->sum_compile_s;
+    out->admit_s = s->sum_admit_s;
+    out->run_s = s->sum_run_s;
     return PGM_OK;
 }
 
