@@ -65,6 +65,11 @@ def test_results_equal_alone(gpu, slots):
     srv.close()
     assert st["completed"] == len(reqs) and st["failed"] == 0
     assert st["peak_bytes"] <= 48 << 20
+    # the latency splits into queue, host compile, admission wait and device work
+    stages = st["queue_s"] + st["compile_s"] + st["admit_s"] + st["run_s"]
+    total = sum(r[2] for r in results)
+    assert st["compile_s"] > 0 and st["run_s"] > 0
+    assert abs(stages - total) <= 1e-3 * len(reqs) + 1e-3 * total, (stages, total)
     for (p, T, it), (bel, dec, lat) in zip(reqs, results):
         b1, d1 = _alone(gpu, p, T, it)
         np.testing.assert_array_equal(bel, b1, err_msg=p.name)
