@@ -278,10 +278,12 @@ pgm_status pgm_launch_times(pgm_graph *g, int32_t n, double *ms, int64_t *count,
  * call is recorded as a CUDA graph on first use of an argument tuple (up to 4 kept) and
  * replayed on the caller's stream; with it off, the scratch is a stream-ordered
  * allocation freed before the call's work ends.
- * Gradients of log-potentials shared by a group are summed over its factors in
- * arbitrary order (atomic adds), and for factors with a state sum above 64 (computed
- * in the block form, a warp or block per factor) so are those of per-factor tables and
- * of the variable-to-factor values; everything else is deterministic.
+ * Gradients of log-potentials shared by a group of factors with a state sum up to 64
+ * are summed in a fixed order (each warp of 32 factors adds its contributions by a fixed
+ * shuffle tree, then the warps' partials are added in order), so repeated calls give the
+ * same bits; for factors with a state sum above 64 (computed in the block form, a warp
+ * or block per factor) the log-potential gradients and the variable-to-factor adjoints
+ * are summed in arbitrary order (atomic adds); everything else is deterministic.
  * Logical OR / AND factors are differentiated through their closed forms (linear in the
  * fan-in); a factor whose incoming log-odds include an infinite one (a hard constraint)
  * passes no gradient to its variable-to-factor values.

@@ -128,6 +128,7 @@ struct pgm_graph {
     int32_t var_launches = 0, factor_launches = 0;
     std::vector<HostMember> members;
     FactorLaunch adj_launch{};      // pgm_grad: enumeration groups of state sum <= 64, thread per factor
+    int32_t adj_nc_max = 0;         // largest list of those groups with a shared table (0: none)
     size_t adj_seg_off = (size_t)-1;
     FactorLaunch adj_block_launch{};  // pgm_grad: the larger groups, block form (k_adj_block)
     size_t adj_block_seg_off = (size_t)-1;
@@ -316,6 +317,9 @@ pgm_status build_plan(const HostLayout &H, pgm_graph *g, Packer &pk, std::vector
             blk += (s.n_fac + 127) / 128;
             segs.push_back(s);
         }
+        g->adj_nc_max = 0;
+        for (const EnumSeg &sg : segs)
+            if (sg.shared && sg.n_fac > 0) g->adj_nc_max = std::max(g->adj_nc_max, sg.n_cfg);
         g->adj_launch = FactorLaunch{};
         g->adj_launch.variant = kEnumGeneric;
         g->adj_launch.n_seg = (int32_t)segs.size();
@@ -1868,14 +1872,22 @@ static pgm_status one_iteration(pgm_graph *g, const float *log_pot, const float 
     return PGM_OK;
 }
 
+// The warp partials of shared-table gradients (k_adj_factor): warps of the launch x the
+// largest shared list.
+static size_t grad_partials_bytes(const pgm_graph *g) {
+    if (g->adj_nc_max == 0) return 0;
+    return align_up((size_t)g->adj_launch.n_blocks * (g->adj_launch.threads / 32) * g->adj_nc_max * sizeof(float), 256);
+}
+
 // Work buffers of a gradient: checkpoints, one segment of recomputed states, two message
-// buffers, two adjoint buffers, the variable-to-factor adjoint, the damping adjoint.
+// buffers, two adjoint buffers, the variable-to-factor adjoint, the damping adjoint, the
+// warp partials of shared-table gradients.
 static size_t grad_work_bytes(const pgm_graph *g, int32_t n_iters, int32_t ckpt_every) {
     const int64_t ES = std::max<int64_t>(g->info.n_edge_states, 1);
     const size_t esb = align_up((size_t)ES * sizeof(float), 256);
     const int n_ck = n_iters > 0 ? (n_iters + ckpt_every - 1) / ckpt_every : 0;
     const int seg_len = std::min(ckpt_every, std::max(n_iters, 1));
-    return esb * ((size_t)n_ck + (size_t)seg_len + 6);
+    return esb * ((size_t)n_ck + (size_t)seg_len + 6) + grad_partials_bytes(g);
 }
 
 // Enqueues the whole gradient on s, with its work buffers at mem.
@@ -1890,6 +1902,7 @@ static pgm_status enqueue_grad(pgm_graph *g, const float *log_pot, const float *
     float *ck = buf(0), *rec = buf(n_ck), *mA = buf(n_ck + seg_len), *mB = buf(n_ck + seg_len + 1);
     float *adjA = buf(n_ck + seg_len + 2), *adjB = buf(n_ck + seg_len + 3), *dv = buf(n_ck + seg_len + 4);
     float *ddamp = buf(n_ck + seg_len + 5);
+    float *partials = g->adj_nc_max > 0 ? buf(n_ck + seg_len + 6) : nullptr;
     auto ckp = [&](int i) { return ck + (size_t)i * (esb / sizeof(float)); };
     auto recp = [&](int i) { return rec + (size_t)i * (esb / sizeof(float)); };
     pgm_status st = PGM_OK;
@@ -1923,10 +1936,10 @@ static pgm_status enqueue_grad(pgm_graph *g, const float *log_pot, const float *
             e = launch_var_pass(g->G, g->P, evidence, m_prev, g->b, kVarIter, nullptr, s);
             if (e == cudaSuccess)
                 e = launch_adj_factor(g->G, g->adj_launch, log_pot, g->b, evidence, m_prev, adjA, dv, ddamp,
-                                      d_log_pot, T, damping, s);
+                                      d_log_pot, partials, g->adj_nc_max, T, damping, s);
             if (e == cudaSuccess)
                 e = launch_adj_factor(g->G, g->adj_block_launch, log_pot, g->b, evidence, m_prev, adjA, dv, ddamp,
-                                      d_log_pot, T, damping, s);
+                                      d_log_pot, nullptr, 0, T, damping, s);
             if (e == cudaSuccess)
                 e = launch_adj_logic(g->G, g->adj_logic_launch, g->b, evidence, m_prev, adjA, dv, ddamp, T, damping, s);
             if (e == cudaSuccess) e = launch_adj_var(g->G, ddamp, dv, adjB, d_evidence, s);

@@ -2505,14 +2505,23 @@ __global__ void __launch_bounds__(128) k_adj_beliefs(DevGraph G, const float *__
 //   d log_pot(c) += sum_i gamma_i(c_i) p_i(c)
 //   dv2f_j(y)     = sum_{i != j} sum_{c: c_j = y} gamma_i(c_i) p_i(c)
 // The variable-to-factor values and mt are recomputed as the forward factor pass does.
+// A table shared by the group is not summed into d_pot here: each warp adds its factors'
+// contributions in a fixed shuffle order and writes one partial per configuration to
+// `partials` (warp w of the launch at w * nc_max), which k_adj_pot_reduce adds to d_pot in
+// warp order, so the gradient is the same on every run.
 __global__ void __launch_bounds__(128)
 k_adj_factor(DevGraph G, const EnumSeg *__restrict__ segs, int n_seg, const float *__restrict__ pot,
              const float *__restrict__ b, const float *__restrict__ ev, const float *__restrict__ m_old,
              const float *__restrict__ adj, float *__restrict__ dv2f, float *__restrict__ ddamp,
-             float *__restrict__ d_pot, float T, float invT, float damping) {
+             float *__restrict__ d_pot, float *__restrict__ partials, int nc_max, float T, float invT,
+             float damping) {
     const EnumSeg *S = segs + find_seg(segs, n_seg, blockIdx.x);
-    const int f = (blockIdx.x - S->block_begin) * blockDim.x + threadIdx.x;
-    if (f >= S->n_fac) return;
+    const int f_raw = (blockIdx.x - S->block_begin) * blockDim.x + threadIdx.x;
+    // a block lies in one group, so a warp does; idle lanes shadow the group's last
+    // factor (a warp's lanes all take part in the partial sums) and write nothing
+    const bool valid = f_raw < S->n_fac;
+    if (__all_sync(0xffffffffu, !valid)) return;
+    const int f = valid ? f_raw : S->n_fac - 1;
     const int a = S->arity, nc = S->n_cfg, ksum = S->es_per_fac;
     int Kj[kMaxArity], Ko[kMaxArity];
     for (int j = 0; j < a; ++j) {
@@ -2588,13 +2597,14 @@ k_adj_factor(DevGraph G, const EnumSeg *__restrict__ segs, int n_seg, const floa
         float sn = 0.f;
         for (int x = 0; x < K; ++x) {
             const float dd = adj[es + x] - (x == a2 ? sa : 0.f);
-            ddamp[es + x] = damping * dd;
+            if (valid) ddamp[es + x] = damping * dd;
             gam[o + x] = w1 * dd;
             sn += gam[o + x];
         }
         gam[o + a1] -= sn;
     }
     float *dphi = d_pot + S->pot_base + (S->shared ? 0 : (size_t)f * nc);
+    const int gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     for (int c = 0; c < nc; ++c) {
         const uint8_t *cc = cfg + c * a;
         float dc = 0.f;
@@ -2609,10 +2619,35 @@ k_adj_factor(DevGraph G, const EnumSeg *__restrict__ segs, int n_seg, const floa
             for (int j = 0; j < a; ++j)
                 if (j != i) dv[Ko[j] + cc[j]] += w;
         }
-        if (S->shared) atomicAdd(dphi + c, dc);
-        else dphi[c] += dc;
+        if (S->shared) {  // uniform over the warp
+            float t = valid ? dc : 0.f;
+#pragma unroll
+            for (int d = 16; d > 0; d >>= 1) t += __shfl_down_sync(0xffffffffu, t, d);
+            if (lane == 0) partials[(size_t)gwarp * nc_max + c] = t;
+        } else if (valid) {
+            dphi[c] += dc;
+        }
     }
-    for (int i = 0; i < ksum; ++i) dv2f[es_f + i] = dv[i];
+    if (valid)
+        for (int i = 0; i < ksum; ++i) dv2f[es_f + i] = dv[i];
+}
+
+// Adds the warp partials of k_adj_factor to the log-potential gradients of the tables
+// shared by a group: block = group record, thread = configuration, warps in ascending
+// order (the launch's warp w covers threads 32 w .. 32 w + 31 of its block range).
+__global__ void __launch_bounds__(256) k_adj_pot_reduce(const EnumSeg *__restrict__ segs, int n_seg,
+                                                        const float *__restrict__ partials, int nc_max,
+                                                        int threads_per_block, float *__restrict__ d_pot) {
+    const EnumSeg *S = segs + blockIdx.x;
+    if (!S->shared || S->n_fac == 0) return;
+    // the group's factors are consecutive from its first block, 32 to a warp; warps past
+    // its last factor wrote nothing
+    const int w0 = S->block_begin * (threads_per_block >> 5), w1 = w0 + (S->n_fac + 31) / 32;
+    for (int c = threadIdx.x; c < S->n_cfg; c += blockDim.x) {
+        float sum = 0.f;
+        for (int w = w0; w < w1; ++w) sum += partials[(size_t)w * nc_max + c];
+        d_pot[S->pot_base + c] += sum;
+    }
 }
 
 // k_adj_factor for listed-configuration groups with a state sum above kMaxStateSum, with
@@ -3984,14 +4019,19 @@ cudaError_t launch_adj_beliefs(const DevGraph &G, const float *ev, const float *
 
 cudaError_t launch_adj_factor(const DevGraph &G, const FactorLaunch &L, const float *pot, const float *b,
                               const float *ev, const float *m_old, const float *adj, float *dv2f, float *ddamp,
-                              float *d_pot, float T, float damping, cudaStream_t s) {
+                              float *d_pot, float *partials, int nc_max, float T, float damping, cudaStream_t s) {
     if (L.n_blocks == 0) return cudaSuccess;
-    if (L.variant == kEnumBlock)
+    if (L.variant == kEnumBlock) {
         k_adj_block<<<L.n_blocks, L.threads, L.smem, s>>>(G, static_cast<const EnumSeg *>(L.segs), L.n_seg, pot, b, ev,
                                                           m_old, adj, dv2f, ddamp, d_pot, T, 1.f / T, damping);
-    else
+    } else {
         k_adj_factor<<<L.n_blocks, L.threads, 0, s>>>(G, static_cast<const EnumSeg *>(L.segs), L.n_seg, pot, b, ev,
-                                                      m_old, adj, dv2f, ddamp, d_pot, T, 1.f / T, damping);
+                                                      m_old, adj, dv2f, ddamp, d_pot, partials, nc_max, T, 1.f / T,
+                                                      damping);
+        if (partials != nullptr)
+            k_adj_pot_reduce<<<L.n_seg, 256, 0, s>>>(static_cast<const EnumSeg *>(L.segs), L.n_seg, partials, nc_max,
+                                                     L.threads, d_pot);
+    }
     return cudaGetLastError();
 }
 

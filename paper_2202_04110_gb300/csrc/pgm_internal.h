@@ -278,9 +278,12 @@ cudaError_t launch_lr_unpack(const DevGraph &G, const float *d, float *m, cudaSt
 // Adjoint launchers (kernels.cu).
 cudaError_t launch_adj_beliefs(const DevGraph &G, const float *ev, const float *m, const float *gnb, float *d_ev,
                                float *adj, cudaStream_t s);
+// (thread-per-factor launches: `partials` [warps of the launch x nc_max] receives the
+// per-warp sums of shared-table gradients, reduced into d_pot in warp order; may be null
+// when no group shares a table)
 cudaError_t launch_adj_factor(const DevGraph &G, const FactorLaunch &L, const float *pot, const float *b,
                               const float *ev, const float *m_old, const float *adj, float *dv2f, float *ddamp,
-                              float *d_pot, float T, float damping, cudaStream_t s);
+                              float *d_pot, float *partials, int nc_max, float T, float damping, cudaStream_t s);
 cudaError_t launch_adj_logic(const DevGraph &G, const FactorLaunch &L, const float *b, const float *ev,
                              const float *m_old, const float *adj, float *dv2f, float *ddamp, float T, float damping,
                              cudaStream_t s);

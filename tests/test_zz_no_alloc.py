@@ -85,20 +85,37 @@ def _hard_grid(rows, cols, seed, scale):
 @pytest.mark.parametrize("scale", [1.0, 300.0])
 def test_noalloc_hard_evidence_and_large_messages(gpu, T, scale):
     """-inf evidence on a fifth of the cells; with scale 300 the messages exceed 128, the
-    recompute branch of the factor kernel. Against pgm_run_bp and the oracle, twice."""
+    recompute branch of the factor kernel. Against pgm_run_bp and the oracle, twice. At
+    scale 300 the raw beliefs reach 2,500, and a normalised log-belief b - LSE(b) formed
+    from them in FP32 is exact only to their ulp (2.4e-4 at 2,500), so there the tolerance
+    is 1e-4 plus two FP32 ulps of the raw belief rather than of the normalised value."""
     import torch
     rows, cols, n_iters = 29, 31, 20
     p = _hard_grid(rows, cols, 11, scale)
     g, lp, ev, m_ref = _reference(gpu, p, T, n_iters)
     nb_ref = g.beliefs(ev, m_ref, True).cpu().numpy()
-    onb, ofl = _oracle_nb(p, T, n_iters)
+    om, ofl = oracle.run_bp(p.graph, p.log_pot, p.evidence, T, 0.5, n_iters)
+    braw, onb, _, ofl2 = oracle.beliefs(p.graph, p.evidence, om)
+    ofl |= ofl2
+    fin = np.isfinite(braw)
+    rtol_raw = np.where(fin, 2.0 ** -21 * np.abs(np.where(fin, braw, 0.0)), 0.0)
+
+    def close(a, ref, what):
+        a = np.asarray(a, np.float64)
+        assert (np.isneginf(a) == np.isneginf(ref)).all(), what
+        f = np.isfinite(ref)
+        err = np.abs(a[f] - ref[f])
+        tol = 1e-4 + 2.0 ** -22 * np.abs(ref[f]) + rtol_raw[f]
+        assert (err <= tol).all(), f"{what}: max excess {np.max(err - tol):.3e}"
+
     for call in range(2):
         m = torch.zeros_like(m_ref)
         gpu.grid2_run_bp_noalloc(rows, cols, lp, ev, T, 0.5, n_iters, m)
         nb = g.beliefs(ev, m, True).cpu().numpy()
-        assert_beliefs_close(nb, nb_ref, what=f"noalloc vs pgm_run_bp, call {call}")
-        assert_beliefs_close(nb, onb, what=f"noalloc vs oracle, call {call}")
+        close(nb, np.asarray(nb_ref, np.float64), f"noalloc vs pgm_run_bp, call {call}")
+        close(nb, onb, f"noalloc vs oracle, call {call}")
         assert gpu.grid2_noalloc_flags(clear=True) == (ofl & oracle.FLAG_CONTRADICTION), call
+    close(nb_ref, onb, "pgm_run_bp vs oracle")
 
 
 def test_noalloc_contradiction_flag(gpu):
