@@ -61,6 +61,8 @@ def parse_args():
                          "configuration factors, T=0) for ncu captures of its kernels")
     ap.add_argument("--batch-probe", type=int, default=0,
                     help="only run the batched workload for N iterations (3 runs, no CUDA graphs; for ncu)")
+    ap.add_argument("--pair-form", type=int, default=0,
+                    help="with --batch-probe: the dense K-state pairwise kernel form (PGM_OPT_PAIR_FORM)")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
     ap.add_argument("--serve-rate", type=float, default=2000.0, help="mean Poisson arrival rate (requests/s)")
     ap.add_argument("--serve-duration", type=float, default=1.0, help="seconds of arrivals per serving run")
@@ -1078,13 +1080,14 @@ def batch_probe(args):
     ev = torch.as_tensor(batch.evidence).cuda()
     g = binding.Graph([m.graph for m in members])
     g.set_option(binding.OPT_CUDA_GRAPH, 0)
+    g.set_option(binding.OPT_PAIR_FORM, args.pair_form)
     m = g.new_msgs()
     for _ in range(3):
         m.zero_()
         g.run_bp(lp, ev, 1.0, 0.5, args.batch_probe, m)
     torch.cuda.synchronize()
-    print(json.dumps({"batch_probe": args.batch_probe, "launches_per_iter": g.info["launches_per_iter"],
-                      "launch_shapes": g.launches()}))
+    print(json.dumps({"batch_probe": args.batch_probe, "pair_form": args.pair_form,
+                      "launches_per_iter": g.info["launches_per_iter"], "launch_shapes": g.launches()}))
 
 
 def pool_probe(args):

@@ -1558,16 +1558,21 @@ k_pair_thr(DevGraph G, const EnumSeg *__restrict__ segs, int n_seg, const float 
 // 4q..4q+3 of both stored messages and both beliefs (16-byte loads; the group reads each
 // vector as one contiguous run) and computes the outputs of those four states in both
 // directions. The input vector of a direction is exchanged through the group's slot of
-// shared memory, and each output state's row of the table (padded rows, conflict-free
-// float4 reads) is dotted with it. Per factor this spreads the thread form's work over L
+// shared memory, and each output state's row of the table (rows swizzled in 16-byte
+// chunks, conflict-free float4 reads) is dotted with it. Per factor this spreads the thread form's work over L
 // lanes with a quarter of its registers, so four times as many factors are in flight per
 // SM. The arithmetic is the thread form's, term for term and in the same order (the
 // table rows in the same float4 chunks, the maxima exact), so both forms give the same
 // bits. The rare cases (an edge of a high-degree variable, a stored entry that is -inf
 // or large) go to pair_factor_rare on the group's first lane.
 
+// Shared tables of the K / 4-lane form: row x of a K x K table holds its 16-byte chunk j
+// at chunk slot j ^ ((x >> 2) & (K / 4 - 1)), so that the group's lanes, reading rows
+// 4q + i (q = 0 .. K/4 - 1) at the same time, hit distinct bank groups.
 template <int K>
-constexpr int kQRow = K + 4;  // padded row stride of the shared tables (floats)
+__device__ __forceinline__ int qtab_index(int x, int y) {
+    return x * K + 4 * ((y >> 2) ^ ((x >> 2) & (K / 4 - 1))) + (y & 3);
+}
 
 // Four consecutive floats of global memory: one 16-byte access when the address is
 // 16-byte aligned (a batch member's arrays start wherever the previous member's end),
@@ -1656,11 +1661,12 @@ __device__ __forceinline__ float4 quad_dir(float4 v, bool linear, const float *r
         float out[4];
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
-            const float4 *row = reinterpret_cast<const float4 *>(rows + (4 * q + i) * kQRow<K>);
+            const int x = 4 * q + i, sw = (x >> 2) & (K / 4 - 1);
+            const float4 *row = reinterpret_cast<const float4 *>(rows + x * K);
             float s = 0.f;
 #pragma unroll
             for (int j = 0; j < K / 4; ++j) {
-                const float4 a = row[j];
+                const float4 a = row[j ^ sw];  // chunk j of the row
                 s = fmaf(a.x, wa[4 * j], fmaf(a.y, wa[4 * j + 1], fmaf(a.z, wa[4 * j + 2], fmaf(a.w, wa[4 * j + 3], s))));
             }
             out[i] = vmax == kNegInf ? kNegInf : T * logf(s) + vmax + tmax;
@@ -1679,10 +1685,10 @@ __device__ __forceinline__ float4 quad_dir(float4 v, bool linear, const float *r
         float out[4];
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
-            const float *row = rows + (4 * q + i) * kQRow<K>;
+            const int x = 4 * q + i;
             float z[K];
 #pragma unroll
-            for (int y = 0; y < K; ++y) z[y] = row[y] + va[y];
+            for (int y = 0; y < K; ++y) z[y] = rows[qtab_index<K>(x, y)] + va[y];
             out[i] = lse_row<K, MAXP>(z, T, invT);
         }
         o = make_float4(out[0], out[1], out[2], out[3]);
@@ -1705,9 +1711,9 @@ k_pair_quad(DevGraph G, const EnumSeg *__restrict__ segs, int n_seg, const float
         m_old += smp * G.s_es;
         m_new += smp * G.s_es;
     }
-    __shared__ float tab[K * K];                          // phi, row-major (the rare path)
-    __shared__ __align__(16) float rows0[K * kQRow<K>];   // E (linear) or phi, padded rows
-    __shared__ __align__(16) float rows1[K * kQRow<K>];   // E^T or phi^T
+    __shared__ float tab[K * K];                   // phi, row-major (the rare path)
+    __shared__ __align__(16) float rows0[K * K];   // E (linear) or phi, rows swizzled (qtab_index)
+    __shared__ __align__(16) float rows1[K * K];   // E^T or phi^T
     __shared__ __align__(16) float xchg[256 * 4];
     __shared__ float tinfo[2];
     const EnumSeg *S = segs + find_seg(segs, n_seg, blockIdx.x);
@@ -1717,7 +1723,7 @@ k_pair_quad(DevGraph G, const EnumSeg *__restrict__ segs, int n_seg, const float
     for (int i = threadIdx.x; i < K * K; i += blockDim.x) tab[i] = __ldg(pot + pot_base + i);
     __syncthreads();
     const bool linear = prepare_linear_table<K, MAXP>(tab, rows0, tinfo, invT);  // rows0 = E, unpadded
-    // pad: E (or phi) rows to kQRow, and the transposes (blocks of at least 64 threads)
+    // E (or phi) and its transpose in the swizzled layout (blocks of at least 64 threads)
     {
         constexpr int kPer = (K * K + 63) / 64;
         float e[kPer];
@@ -1732,8 +1738,8 @@ k_pair_quad(DevGraph G, const EnumSeg *__restrict__ segs, int n_seg, const float
             const int i = threadIdx.x + k * blockDim.x;
             if (i < K * K) {
                 const int r = i / K, c = i % K;
-                rows0[r * kQRow<K> + c] = e[k];
-                rows1[c * kQRow<K> + r] = e[k];
+                rows0[qtab_index<K>(r, c)] = e[k];
+                rows1[qtab_index<K>(c, r)] = e[k];
             }
         }
         __syncthreads();
