@@ -240,8 +240,11 @@ std::string compile_graph(const void *const *vdescs, int n_desc, HostLayout *L) 
                 // threads per output state from the mean list length (about 8 configs each)
                 const int64_t mean = nl / std::max<int32_t>(off, 1);
                 while (s.lanes < 32 && mean > 8 * s.lanes) s.lanes *= 2;
-                const int64_t tb = (((int64_t)g.n_cfg * g.arity + 15) & ~15) + (int64_t)len * 4 +
-                                   (g.shared_potentials ? (int64_t)g.n_cfg * 4 : 0);
+                int64_t tb = (((int64_t)g.n_cfg * g.arity + 15) & ~15) + (int64_t)len * 4 +
+                             (g.shared_potentials ? (int64_t)g.n_cfg * 4 : 0);
+                // packed pairwise lists with a shared table: each list entry staged beside
+                // its configuration's log-potential (one 8-byte read per entry)
+                if (g.shared_potentials && s.packed) tb = ((tb + 7) & ~(int64_t)7) + 8 * nl;
                 s.table_bytes = tb <= kEnumTableSmem ? (int32_t)tb : 0;
             }
             for (int64_t f = 0; f < g.n_fac; ++f)

@@ -1993,6 +1993,69 @@ __device__ __forceinline__ void enum_team_v2f(const DevGraph &G, const float *__
     team_barrier(wteam);
 }
 
+// One output of a packed pairwise list walked by lane gl of its L lanes: entries
+// i0, i0 + L, .. < i1, each (configuration << 11) | the other neighbour's state offset,
+// scored phi(configuration) + v2f(other state). STAGED: the entries come as
+// (entry, log-potential) pairs (fl), so one 8-byte shared read replaces the entry read
+// and the dependent log-potential gather. Same order of operations as the unstaged walk.
+template <bool MAXP, bool STAGED>
+__device__ __forceinline__ void enum_packed_output(const int2 *fl, const int32_t *lst, const float *phi,
+                                                   const float *v2f, int i, int i1, int L, int ordered, float invT,
+                                                   float &mx, float &sm) {
+    auto score = [&](int k) {
+        if constexpr (STAGED) {
+            const int2 p = fl[k];
+            return __int_as_float(p.y) + v2f[p.x & 2047];
+        } else {
+            const int e = lst[k];
+            return phi[e >> 11] + v2f[e & 2047];
+        }
+    };
+    if (MAXP) {
+        float m1 = kNegInf, m2 = kNegInf, m3 = kNegInf;
+        for (; i + 3 * L < i1; i += 4 * L) {
+            mx = fmaxf(mx, score(i));
+            m1 = fmaxf(m1, score(i + L));
+            m2 = fmaxf(m2, score(i + 2 * L));
+            m3 = fmaxf(m3, score(i + 3 * L));
+        }
+        mx = fmaxf(fmaxf(mx, m1), fmaxf(m2, m3));
+    } else if (!ordered) {
+        float mb = kNegInf, sb = 0.f;
+        for (; i + L < i1; i += 2 * L) {
+            const float va = score(i), vb = score(i + L);
+            if (va > mx) {
+                sm = sm * expf((mx - va) * invT) + 1.f;
+                mx = va;
+            } else if (va > kNegInf) {
+                sm += expf((va - mx) * invT);
+            }
+            if (vb > mb) {
+                sb = sb * expf((mb - vb) * invT) + 1.f;
+                mb = vb;
+            } else if (vb > kNegInf) {
+                sb += expf((vb - mb) * invT);
+            }
+        }
+        const float mn = fmaxf(mx, mb);
+        if (mn != kNegInf) {
+            sm = (mx == kNegInf ? 0.f : sm * expf((mx - mn) * invT)) + (mb == kNegInf ? 0.f : sb * expf((mb - mn) * invT));
+            mx = mn;
+        }
+    }
+    for (; i < i1; i += L) {
+        const float val = score(i);
+        if (MAXP) {
+            mx = fmaxf(mx, val);
+        } else if (val > mx) {
+            sm = sm * expf((mx - val) * invT) + 1.f;
+            mx = val;
+        } else if (val > kNegInf) {
+            sm += expf((val - mx) * invT);
+        }
+    }
+}
+
 template <bool MAXP, bool MS = false>
 __global__ void __launch_bounds__(kEnumBlockThreads)
 k_enum_block(DevGraph G, const EnumSeg *__restrict__ segs, int n_seg, const float *__restrict__ pot,
@@ -2037,6 +2100,7 @@ k_enum_block(DevGraph G, const EnumSeg *__restrict__ segs, int n_seg, const floa
     const int32_t *bs = G.bs_pool + __ldg(&S->bs_base);
     const float *phi_g = pot + __ldg(&S->pot_base);
     const float *phi_tab = phi_g;
+    const int2 *flst = nullptr;  // staged (entry, log-potential) pairs of a packed shared list
     if (tb > 0) {  // 16-byte aligned sources (pool layout) and destinations
         unsigned char *t = eb_smem + ((12 * ksum * n_teams + 15) & ~15);
         const uint4 *c_src = reinterpret_cast<const uint4 *>(cfg);
@@ -2050,6 +2114,14 @@ k_enum_block(DevGraph G, const EnumSeg *__restrict__ segs, int n_seg, const floa
             float *tphi = reinterpret_cast<float *>(tbs + bs_len);
             for (int i = threadIdx.x; i < nc; i += blockDim.x) tphi[i] = __ldg(phi_g + i);
             phi_tab = tphi;
+            if (packed) {  // list entries beside their log-potentials
+                int2 *fl = reinterpret_cast<int2 *>(t + ((cfg_bytes + 4 * (bs_len + nc) + 7) & ~7));
+                for (int i = threadIdx.x; i < a * nc; i += blockDim.x) {
+                    const int e = __ldg(bs + ob + i);
+                    fl[i] = make_int2(e, __float_as_int(__ldg(phi_g + (e >> 11))));
+                }
+                flst = fl;
+            }
         }
         cfg = t;
         bs = tbs;
@@ -2069,7 +2141,10 @@ k_enum_block(DevGraph G, const EnumSeg *__restrict__ segs, int n_seg, const floa
         for (int base = 0; base < ksum; base += ng) {
             const int o = base + gi;
             float mx = kNegInf, sm = 0.f;
-            if (o < ksum && packed) {
+            if (o < ksum && flst != nullptr) {
+                // staged pairs: one 8-byte read gives the entry and its log-potential
+                enum_packed_output<MAXP, true>(flst, lst, phi, v2f, bs[o] + gl, bs[o + 1], L, ordered, invT, mx, sm);
+            } else if (o < ksum && packed) {
                 // pairwise: entry = (configuration << 11) | the other neighbour's
                 // state offset; at T = 0 four independent max chains; at T > 0 two
                 // log-sum-exp chains unless the group keeps the ascending order
