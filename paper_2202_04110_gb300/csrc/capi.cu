@@ -1688,9 +1688,9 @@ static std::vector<int> alternative_forms(int base_variant, bool all_shared) {
     switch (base_variant) {
         case kPair4: case kPairT4: return {kPairT4, kPair4};
         case kPair8: case kPairT8: case kPairQ8:
-            return all_shared ? std::vector<int>{kPairQ8, kPairT8, kPair8} : std::vector<int>{kPairT8, kPair8};
+            return all_shared ? std::vector<int>{kPairT8, kPairQ8, kPair8} : std::vector<int>{kPairT8, kPair8};
         case kPair16: case kPairT16: case kPairQ16:
-            return all_shared ? std::vector<int>{kPairQ16, kPairT16, kPair16} : std::vector<int>{kPairT16, kPair16};
+            return all_shared ? std::vector<int>{kPairT16, kPairQ16, kPair16} : std::vector<int>{kPairT16, kPair16};
         case kEnumGeneric: case kEnumBlock: return {kEnumGeneric, kEnumBlock};  // the former where every group fits
         default: return {base_variant};
     }
@@ -2087,9 +2087,12 @@ pgm_status pgm_set_option(pgm_graph *g, int32_t option, int64_t value) {
                 const int thr = K == 4 ? kPairT4 : K == 8 ? kPairT8 : kPairT16;
                 const int lanes = K == 4 ? kPair4 : K == 8 ? kPair8 : kPair16;
                 const int quad = K == 8 ? kPairQ8 : K == 16 ? kPairQ16 : thr;
-                // the K / 4-lane form runs shared tables only (the compiler's choice for them)
+                // the K / 4-lane form runs launches whose groups all share their tables
+                bool all_shared = true;
+                const EnumSeg *sg = reinterpret_cast<const EnumSeg *>(g->factor_segs_host[li].data());
+                for (int i = 0; i < L.n_seg; ++i) all_shared = all_shared && sg[i].shared != 0;
                 const int want = value == 0 ? base : value == 1 ? thr : value == 2 ? lanes
-                                                   : (base == kPairQ8 || base == kPairQ16 ? quad : thr);
+                                                   : (all_shared ? quad : thr);
                 if (L.variant == want) continue;
                 const int old_variant = L.variant;
                 L.variant = want;

@@ -197,14 +197,12 @@ std::string compile_graph(const void *const *vdescs, int n_desc, HostLayout *L) 
             int K0 = s.K[0], K1 = g.arity > 1 ? s.K[1] : 0;
             hg.variant = (off > kMaxStateSum || g.n_cfg > kEnumGenericMaxCfg) ? kEnumBlock : kEnumGeneric;
             if (g.n_fac > 0 && is_dense_pair(g, K0, K1)) {
-                // K = 4: thread per factor; K = 8, 16: K / 4 lanes per factor for a shared
-                // table, else thread per factor (the autotuner may switch a launch to
-                // another form)
-                const bool shared_tab = g.shared_potentials != 0;
+                // K = 4, 8, 16: thread per factor (the autotuner may switch a launch to
+                // another form: K lanes per factor, or for a shared table K / 4 lanes)
                 if (K0 == 2) hg.variant = kPair2;
                 else if (K0 == 4) hg.variant = kPairT4;
-                else if (K0 == 8) hg.variant = shared_tab ? kPairQ8 : kPairT8;
-                else if (K0 == 16) hg.variant = shared_tab ? kPairQ16 : kPairT16;
+                else if (K0 == 8) hg.variant = kPairT8;
+                else if (K0 == 16) hg.variant = kPairT16;
             }
             s.bs_base = -1;
             s.fpb = 1;

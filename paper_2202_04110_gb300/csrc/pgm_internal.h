@@ -47,7 +47,7 @@ enum FactorVariant : int32_t {
     kEnumBlock = 10,   // listed-configuration factors with a state sum above kMaxStateSum or
                        // a list longer than kEnumGenericMaxCfg: a block per run of factors
     kPairQ8 = 11,      // dense pairwise table shared by the group, K = 8, 16: K / 4 lanes per
-    kPairQ16 = 12,     // factor, four states each (the default form for shared tables)
+    kPairQ16 = 12,     // factor, four states each (an alternative the autotuner may pick)
     kNumFactorVariants = 13
 };
 

@@ -1,8 +1,9 @@
 """Dense K-state pairwise factors (Potts, Sec. 5.2's enumeration factors over full
 tables): the kernel forms of the factor pass give the same results.
 
-The K / 4-lane form (four states per lane, the default for tables shared by a group)
-and the thread-per-factor form run the same arithmetic in the same order, so their
+The K / 4-lane form (four states per lane, for tables shared by a group; an
+alternative the autotuner may pick) and the thread-per-factor form (the default) run
+the same arithmetic in the same order, so their
 messages are bitwise equal: with the linear-domain form of a shared table (range within
 60 T), with the exact form (a table range above 60 T), at T = 0, with hard evidence (the
 rare path), in batches whose members start at any offset, and for many samples at once.
@@ -67,8 +68,8 @@ def test_quad_equals_thread_form(gpu, K, T, case):
     p = W.potts_grid(side, K, seed=K + 3, T=T, n_iters=15, w=w)
     if case == "hard":
         p = _hard(p, 0.1, 5)
-    g_q, m_q = _run_form(gpu, p.graph, p.log_pot, p.evidence, T, 15, 0)
-    assert gpu.OPT_PAIR_FORM and g_q.launches()[-1][1] == (11 if K == 8 else 12)
+    g_q, m_q = _run_form(gpu, p.graph, p.log_pot, p.evidence, T, 15, 3)
+    assert g_q.launches()[-1][1] == (11 if K == 8 else 12)
     _, m_t = _run_form(gpu, p.graph, p.log_pot, p.evidence, T, 15, 1)
     assert np.array_equal(m_q, m_t, equal_nan=True), f"max diff {np.nanmax(np.abs(m_q - m_t))}"
     import torch
@@ -97,7 +98,7 @@ def test_quad_in_batch_at_any_offset(gpu):
           W.potts_grid(9, 8, 4, T=1.0), W.ising_grid(3, 5, 5, T=1.0), W.potts_grid(21, 16, 6, T=1.0)]
     batch = W.union(ms)
     graphs = [p.graph for p in ms]
-    g_q, m_q = _run_form(gpu, graphs, batch.log_pot, batch.evidence, 1.0, 12, 0)
+    g_q, m_q = _run_form(gpu, graphs, batch.log_pot, batch.evidence, 1.0, 12, 3)
     _, m_t = _run_form(gpu, graphs, batch.log_pot, batch.evidence, 1.0, 12, 1)
     assert np.array_equal(m_q, m_t)
     for i, p in enumerate(ms):
@@ -117,7 +118,7 @@ def test_quad_multi_sample(gpu, T):
     S = 5
     rng = np.random.default_rng(3)
     ev = (p.evidence[None, :] + rng.standard_normal((S, p.evidence.size))).astype(np.float32)
-    _, mq = _run_form(gpu, p.graph, p.log_pot, ev, T, 10, 0, samples=S)
+    _, mq = _run_form(gpu, p.graph, p.log_pot, ev, T, 10, 3, samples=S)
     _, mt = _run_form(gpu, p.graph, p.log_pot, ev, T, 10, 1, samples=S)
     assert np.array_equal(mq, mt)
     for s in range(S):
