@@ -604,12 +604,14 @@ def measure_deconv(args, binding, W, torch, dev):
     and_g, or_g = fg.logic_groups[0], fg.logic_groups[1]
     e_and = int(and_g.par_off[-1]) + and_g.n_fac
     e_or = int(or_g.par_off[-1]) + or_g.n_fac
-    impl = {"k_var_block": 12 * n_hi_es + 8 * int(ks[hi].sum()),
+    d_hi = int(deg[hi].sum())
+    impl = {"k_var_hd_sum": 4 * n_hi_es + 4 * d_hi,  # messages and incoming-edge index
+            "k_var_hd_out": 12 * n_hi_es + 4 * d_hi + 8 * int(ks[hi].sum()),  # + float-float leave-one-out values
             "k_logic_small": 4 * (4 * e_and + 2 * e_and + e_and),
             "k_logic_warp": 4 * (4 * e_or + 2 * e_or + e_or)}
     s8d = {"k_logic_small": sec8d_bytes(fg, [0]), "k_logic_warp": sec8d_bytes(fg, [1]),
-           "k_var_block": 4 * int(ks[hi].sum())}
-    names = {(0, 1): "k_var_block", (0, 2): "k_var_thread<2>", (0, 0): "k_var_thread",
+           "k_var_hd_sum": 0, "k_var_hd_out": 4 * int(ks[hi].sum())}
+    names = {(0, 8): "k_var_hd_sum", (0, 1): "k_var_hd_out", (0, 2): "k_var_thread<2>", (0, 0): "k_var_thread",
              (1, 5): "k_logic_small", (1, 6): "k_logic_warp"}
     per = {}
     for (kind, variant, threads, blocks), (ms, cnt) in zip(launches, lt):

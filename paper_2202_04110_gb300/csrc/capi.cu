@@ -129,6 +129,8 @@ struct pgm_graph {
     std::vector<HostMember> members;
     FactorLaunch adj_launch{};      // pgm_grad: enumeration groups of state sum <= 64, thread per factor
     int32_t adj_nc_max = 0;         // largest list of those groups with a shared table (0: none)
+    int64_t hd_tot_entries = 0;     // float2 tile sums of the high-degree variables
+    size_t tiles_off = 0;           // their tile list in the index memory
     size_t adj_seg_off = (size_t)-1;
     FactorLaunch adj_block_launch{};  // pgm_grad: the larger groups, block form (k_adj_block)
     size_t adj_block_seg_off = (size_t)-1;
@@ -298,8 +300,29 @@ pgm_status build_plan(const HostLayout &H, pgm_graph *g, Packer &pk, std::vector
         L.n_blocks = (kind == kVarBlock) ? L.n : (int32_t)(((int64_t)L.n * var_lanes(kind) + 255) / 256);
         L.dense_binary = H.all_binary ? 1 : 0;
         L.list = nullptr;
+        const size_t list_off = H.var_bucket_identity[kind] ? (size_t)-1 : pk.add(bucket.data(), bucket.size());
+        if (kind == kVarBlock) {
+            // the split form: a launch of tile sums, then the outputs, a block per tile
+            std::vector<int4> tiles;
+            int32_t first = 0;
+            for (size_t i = 0; i < bucket.size(); ++i) {
+                const int32_t v = bucket[i];
+                const int32_t deg = H.vin_off[v + 1] - H.vin_off[v], K = H.vs_off[v + 1] - H.vs_off[v];
+                const int32_t nt = (deg + kVarTile - 1) / kVarTile;
+                for (int32_t t = 0; t < nt; ++t) tiles.push_back(make_int4((int32_t)i, t, first, nt));
+                first += nt * K;
+            }
+            g->hd_tot_entries = first;
+            g->tiles_off = pk.add(tiles.data(), tiles.size());
+            L.n_tiles = (int32_t)tiles.size();
+            VarLaunch Ls = L;
+            Ls.kind = kVarBlockSum;
+            P.var.push_back(Ls);
+            seg_off.push_back(list_off);
+            seg_kind.push_back(-1);
+        }
         P.var.push_back(L);
-        seg_off.push_back(H.var_bucket_identity[kind] ? (size_t)-1 : pk.add(bucket.data(), bucket.size()));
+        seg_off.push_back(list_off);
         seg_kind.push_back(-1);
     }
     // adjoint factor launches: enumeration groups with a state sum up to kMaxStateSum,
@@ -655,7 +678,8 @@ static pgm_status build_from_layout(const HostLayout &H, pgm_graph **out, cudaSt
     const size_t lr_bytes = g->P.lr ? align_up((size_t)g->lr_slots * sizeof(float), 256) : 0;
     const size_t prm_bytes = g->P.lr ? align_up((size_t)3 * (H.E / 2) * sizeof(float), 256) : 0;
     const size_t blo_bytes = H.var_bucket[kVarWarp].empty() ? 0 : vs_bytes;
-    const size_t scratch_bytes = es_bytes + vs_bytes + 256 + hd_bytes + 2 * lr_bytes + prm_bytes + blo_bytes;
+    const size_t tot_bytes = align_up((size_t)g->hd_tot_entries * sizeof(float2), 256);
+    const size_t scratch_bytes = es_bytes + vs_bytes + 256 + hd_bytes + 2 * lr_bytes + prm_bytes + blo_bytes + tot_bytes;
     char *smem = nullptr;
     ce = ordered ? cudaMallocAsync(&smem, scratch_bytes, s) : cudaMalloc(&smem, scratch_bytes);
     if (ce != cudaSuccess) {
@@ -693,6 +717,9 @@ static pgm_status build_from_layout(const HostLayout &H, pgm_graph **out, cudaSt
     G.b_lo = blo_bytes ? reinterpret_cast<float *>(smem + es_bytes + vs_bytes + 256 + hd_bytes + 2 * lr_bytes +
                                                     prm_bytes)
                        : nullptr;
+    G.hd_tot = tot_bytes ? reinterpret_cast<float2 *>(smem + es_bytes + vs_bytes + 256 + hd_bytes + 2 * lr_bytes +
+                                                      prm_bytes + blo_bytes)
+                         : nullptr;
     if (g->P.lr) {
         g->lr_d = reinterpret_cast<float *>(smem + es_bytes + vs_bytes + 256 + hd_bytes);
         g->lr_lam = reinterpret_cast<float *>(smem + es_bytes + vs_bytes + 256 + hd_bytes + lr_bytes);
@@ -705,6 +732,7 @@ static pgm_status build_from_layout(const HostLayout &H, pgm_graph **out, cudaSt
         if (seg_kind[k] < 0) {
             VarLaunch &L = g->P.var[vi++];
             L.list = (seg_off[k] == (size_t)-1) ? nullptr : reinterpret_cast<const int32_t *>(dmem + seg_off[k]);
+            if (L.kind == kVarBlock || L.kind == kVarBlockSum) L.tiles = reinterpret_cast<const int4 *>(dmem + g->tiles_off);
         } else {
             FactorLaunch &L = g->P.factor[fi++];
             L.segs = dmem + seg_off[k];
@@ -767,8 +795,16 @@ int64_t pgm::layout_device_bytes(const HostLayout &H) {
         idx += H.E * sizeof(int32_t) + 2 * align_up((size_t)lr_slot_count(H) * sizeof(float), 256) +
                align_up((size_t)3 * (H.E / 2) * sizeof(float), 256);
     const size_t vs_bytes = align_up(std::max<int64_t>(H.VS, 1) * sizeof(float), 256);
+    // the high-degree variables' tile list (index memory) and tile sums (scratch)
+    int64_t n_tiles = 0, tot = 0;
+    for (int32_t v : H.var_bucket[kVarBlock]) {
+        const int64_t nt = (H.vin_off[v + 1] - H.vin_off[v] + kVarTile - 1) / kVarTile;
+        n_tiles += nt;
+        tot += nt * (H.vs_off[v + 1] - H.vs_off[v]);
+    }
+    idx += (size_t)n_tiles * sizeof(int4);
     return (int64_t)(idx + es_bytes + vs_bytes + 256 + (H.var_bucket[kVarBlock].empty() ? 0 : 2 * es_bytes) +
-                     (H.var_bucket[kVarWarp].empty() ? 0 : vs_bytes));
+                     (H.var_bucket[kVarWarp].empty() ? 0 : vs_bytes) + align_up((size_t)tot * sizeof(float2), 256));
 }
 
 pgm_status pgm::build_layout_on_stream(const HostLayout &H, cudaStream_t s, pgm_graph **out) {
@@ -1810,7 +1846,7 @@ pgm_status pgm_autotune(pgm_graph *g, const float *log_pot, const float *evidenc
     }
     // thread-per-variable launches: block size
     for (VarLaunch &L : g->P.var) {
-        if (L.kind == kVarBlock || L.n == 0 || g->G.vin_tab4) continue;
+        if (L.kind == kVarBlock || L.kind == kVarBlockSum || L.n == 0 || g->G.vin_tab4) continue;
         int best = L.threads;
         float best_ms = 1e30f;
         for (int c : {128, 256}) {
@@ -1850,9 +1886,11 @@ pgm_status pgm_launch_info(const pgm_graph *g, int32_t i, int32_t *kind, int32_t
     if (i < nv) {
         const VarLaunch &L = g->P.var[i];
         if (kind) *kind = 0;
-        if (variant) *variant = g->G.vin_tab4 ? 6 : (L.kind == kVarWarp ? 7 : L.kind);
+        if (variant) *variant = g->G.vin_tab4 ? 6 : (L.kind == kVarWarp ? 7 : L.kind == kVarBlockSum ? 8 : L.kind);
         if (threads) *threads = L.kind == kVarBlock ? kVarBlockThreads : (g->G.vin_tab4 ? 256 : L.threads);
-        if (n_blocks) *n_blocks = g->G.vin_tab4 ? (int32_t)((g->info.n_vars + 255) / 256) : L.n_blocks;
+        if (n_blocks)
+            *n_blocks = g->G.vin_tab4 ? (int32_t)((g->info.n_vars + 255) / 256)
+                                      : (L.kind == kVarBlock || L.kind == kVarBlockSum ? L.n_tiles : L.n_blocks);
     } else {
         const FactorLaunch &L = g->P.factor[i - nv];
         if (kind) *kind = 1;

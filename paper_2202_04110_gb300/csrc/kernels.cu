@@ -845,6 +845,41 @@ __device__ __forceinline__ FF block_sum(FF v, float *sh) {
     return tot;
 }
 
+// The outputs of a high-degree variable from its float-float totals sb[x] (thread 0):
+// the decode, the raw beliefs, or the beliefs relative to the best state (normalised by
+// their log-sum-exp in kVarNormalised).
+template <int MODE>
+__device__ __forceinline__ void var_block_output(const DevGraph &G, const FF *sb, int K, int vs, int v,
+                                                 float *__restrict__ out, int32_t *__restrict__ dec) {
+    int arg = 0;
+    for (int x = 1; x < K; ++x)
+        if (ff_gt(sb[x], sb[arg])) arg = x;
+    if constexpr (MODE == kVarDecode) {
+        dec[v] = arg;
+    } else if constexpr (MODE == kVarBeliefs) {
+        for (int x = 0; x < K; ++x) out[vs + x] = sb[x].hi + sb[x].lo;
+    } else {
+        bool nan = false;
+        for (int x = 0; x < K; ++x) nan |= (sb[x].hi != sb[x].hi);
+        if (MODE == kVarNormalised && nan) atomicOr(G.flags, kFlagNaN);
+        if (sb[arg].hi == kNegInf) {
+            if (MODE == kVarNormalised) atomicOr(G.flags, kFlagContradiction);
+            for (int x = 0; x < K; ++x) out[vs + x] = kNegInf;
+            return;
+        }
+        float acc = 0.f;  // sum over the other states of e^r (the best state adds 1)
+        for (int x = 0; x < K; ++x) {
+            const float r = (x == arg) ? 0.f : ff_diff(sb[x], sb[arg]);
+            out[vs + x] = r;
+            if (x != arg) acc += expf(r);
+        }
+        if (MODE == kVarNormalised) {
+            const float z = log1pf(acc);
+            for (int x = 0; x < K; ++x) out[vs + x] -= z;
+        }
+    }
+}
+
 // Block per high-degree variable (more than kVarBlockDegree factors). Incoming
 // messages are processed in tiles of kVarTile edges, kVarItems contiguous edges per
 // thread, with float-float sums in a fixed order (deterministic). In the iteration pass
@@ -933,33 +968,102 @@ __global__ void __launch_bounds__(kVarBlockThreads) k_var_block(DevGraph G, cons
         __syncthreads();
     }
     if (threadIdx.x != 0) return;
-    int arg = 0;
-    for (int x = 1; x < K; ++x)
-        if (ff_gt(sb[x], sb[arg])) arg = x;
-    if constexpr (MODE == kVarDecode) {
-        dec[v] = arg;
-    } else if constexpr (MODE == kVarBeliefs) {
-        for (int x = 0; x < K; ++x) out[vs + x] = sb[x].hi + sb[x].lo;
-    } else {
-        bool nan = false;
-        for (int x = 0; x < K; ++x) nan |= (sb[x].hi != sb[x].hi);
-        if (MODE == kVarNormalised && nan) atomicOr(G.flags, kFlagNaN);
-        if (sb[arg].hi == kNegInf) {
-            if (MODE == kVarNormalised) atomicOr(G.flags, kFlagContradiction);
-            for (int x = 0; x < K; ++x) out[vs + x] = kNegInf;
-            return;
+    var_block_output<MODE>(G, sb, K, vs, v, out, dec);
+}
+
+// The high-degree variables split over tiles of kVarTile edges, in two launches, for
+// more blocks than variables: k_var_hd_sum, a block per tile, writes the tile's
+// float-float sum of every state to G.hd_tot; k_var_hd_out, a block per tile, forms the
+// tile's exact leave-one-out values from the tile totals (as prefix + suffix, in
+// k_var_block's order of operations, so the values are the same bits) and, in the
+// variable's first tile, its beliefs or decode. tiles[i] = (position in the variable
+// list, tile, first hd_tot entry of the variable, tiles of the variable); a variable's
+// K totals of tile t are at hd_tot[first + t K .. + K).
+__global__ void __launch_bounds__(kVarBlockThreads) k_var_hd_sum(DevGraph G, const int32_t *__restrict__ list,
+                                                                 const int4 *__restrict__ tiles,
+                                                                 const float *__restrict__ m) {
+    __shared__ float sh[64];
+    const int4 tl = __ldg(tiles + blockIdx.x);
+    const int v = list ? __ldg(list + tl.x) : tl.x;
+    const int vs = __ldg(G.vs_off + v), K = __ldg(G.vs_off + v + 1) - vs;
+    const int k0 = __ldg(G.vin_off + v), deg = __ldg(G.vin_off + v + 1) - k0;
+    for (int x = 0; x < K; ++x) {
+        FF s = ff_make(0.f);
+        const int base = tl.y * kVarTile + threadIdx.x * kVarItems;
+#pragma unroll
+        for (int i = 0; i < kVarItems; ++i) {
+            const int k = base + i;
+            if (k < deg) s = ff_add(s, __ldg(m + __ldg(G.vin_es + k0 + k) + x));
         }
-        float acc = 0.f;  // sum over the other states of e^r (the best state adds 1)
-        for (int x = 0; x < K; ++x) {
-            const float r = (x == arg) ? 0.f : ff_diff(sb[x], sb[arg]);
-            out[vs + x] = r;
-            if (x != arg) acc += expf(r);
+        const FF tt = block_sum(s, sh);
+        if (threadIdx.x == 0) G.hd_tot[tl.z + tl.y * K + x] = make_float2(tt.hi, tt.lo);
+    }
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(kVarBlockThreads) k_var_hd_out(DevGraph G, const int32_t *__restrict__ list,
+                                                                 const int4 *__restrict__ tiles,
+                                                                 const float *__restrict__ ev,
+                                                                 const float *__restrict__ m,
+                                                                 float *__restrict__ out, int32_t *__restrict__ dec) {
+    __shared__ float sh[64];
+    __shared__ FF sb[kMaxStates];
+    const int4 tl = __ldg(tiles + blockIdx.x);
+    const int v = list ? __ldg(list + tl.x) : tl.x;
+    const int vs = __ldg(G.vs_off + v), K = __ldg(G.vs_off + v + 1) - vs;
+    const int k0 = __ldg(G.vin_off + v), deg = __ldg(G.vin_off + v + 1) - k0;
+    const int t = tl.y, n_tiles = tl.w;
+    auto tot = [&](int u, int x) {
+        const float2 p = __ldcg(G.hd_tot + tl.z + u * K + x);
+        return FF{p.x, p.y};
+    };
+    for (int x = 0; x < K; ++x) {
+        const float e = __ldg(ev + vs + x);
+        if (t == 0 && threadIdx.x == 0) {
+            FF tt = ff_make(e);
+            for (int u = 0; u < n_tiles; ++u) tt = ff_add(tt, tot(u, x));
+            sb[x] = tt;
         }
-        if (MODE == kVarNormalised) {
-            const float z = log1pf(acc);
-            for (int x = 0; x < K; ++x) out[vs + x] -= z;
+        if (MODE == kVarIter && G.v2f_hd != nullptr) {
+            FF carry_pre = ff_make(e);
+            for (int u = 0; u < t; ++u) carry_pre = ff_add(carry_pre, tot(u, x));
+            FF carry_suf = ff_make(0.f);
+            for (int u = n_tiles - 1; u > t; --u) carry_suf = ff_add(carry_suf, tot(u, x));
+            const int base = t * kVarTile + threadIdx.x * kVarItems;
+            float val[kVarItems];
+            int esk[kVarItems];
+            FF own = ff_make(0.f);
+#pragma unroll
+            for (int i = 0; i < kVarItems; ++i) {
+                const int k = base + i;
+                esk[i] = (k < deg) ? __ldg(G.vin_es + k0 + k) : 0;
+                val[i] = (k < deg) ? __ldg(m + esk[i] + x) : 0.f;
+                own = ff_add(own, val[i]);
+            }
+            const FF tp = block_scan_excl(own, false, sh);
+            const FF ts = block_scan_excl(own, true, sh);
+            FF suf_local[kVarItems];
+            FF acc = ff_make(0.f);
+#pragma unroll
+            for (int i = kVarItems - 1; i >= 0; --i) {
+                suf_local[i] = acc;
+                acc = ff_add(acc, val[i]);
+            }
+            FF pre = ff_add(carry_pre, tp);
+            const FF suf_rest = ff_add(ts, carry_suf);
+#pragma unroll
+            for (int i = 0; i < kVarItems; ++i) {
+                const int k = base + i;
+                if (k < deg) {
+                    const FF loo = ff_add(pre, ff_add(suf_local[i], suf_rest));
+                    reinterpret_cast<float2 *>(G.v2f_hd)[esk[i] + x] = make_float2(loo.hi, loo.lo);
+                }
+                pre = ff_add(pre, val[i]);
+            }
         }
     }
+    if (t != 0 || threadIdx.x != 0) return;
+    var_block_output<MODE>(G, sb, K, vs, v, out, dec);
 }
 
 // =====================================================================================
@@ -2341,27 +2445,37 @@ k_logic_small(DevGraph G, const LogicSeg *__restrict__ segs, int n_seg, const fl
     const int edge_base = __ldg(&S->edge_base), es_base = __ldg(&S->es_base);
     const int e0 = edge_base + p0 + f;
     const float sgn = __ldg(&S->kind) == 1 ? -1.f : 1.f;
-    float x[kLogicSmallFan + 1];
-    float2 mo[kLogicSmallFan + 1];
+    // parents in unrolled slots (j < n valid) and the child apart, so that every array
+    // index is a constant and the values stay in registers
+    constexpr int F = kLogicSmallFan;
+    float x[F];
+    float2 mo[F], moc;
 #pragma unroll
-    for (int k = 0; k <= kLogicSmallFan; ++k) {
-        if (k > n) break;
-        const int e = e0 + k;
-        x[k] = edge_logodds(G, ev, b, m_old, e, es_base + 2 * (e - edge_base), sgn, mo[k]);
+    for (int k = 0; k < F; ++k) {
+        x[k] = 0.f;
+        mo[k] = make_float2(0.f, 0.f);
+        if (k < n) {
+            const int e = e0 + k;
+            x[k] = edge_logodds(G, ev, b, m_old, e, es_base + 2 * (e - edge_base), sgn, mo[k]);
+        }
     }
-    const float xc = x[n];
-    float out[kLogicSmallFan + 1];
+    const float xc = edge_logodds(G, ev, b, m_old, e0 + n, es_base + 2 * (e0 + n - edge_base), sgn, moc);
+    float out[F], outc;
     if (MAXP) {
         float A = 0.f, Mall = kNegInf;
-        for (int j = 0; j < n; ++j) {
-            A += fmaxf(x[j], 0.f);
-            Mall = fmaxf(Mall, x[j]);
-        }
-        out[n] = A + (Mall < 0.f ? Mall : 0.f);
-        for (int i = 0; i < n; ++i) {
+#pragma unroll
+        for (int j = 0; j < F; ++j)
+            if (j < n) {
+                A += fmaxf(x[j], 0.f);
+                Mall = fmaxf(Mall, x[j]);
+            }
+        outc = A + (Mall < 0.f ? Mall : 0.f);
+#pragma unroll
+        for (int i = 0; i < F; ++i) {
             float Si = 0.f, Mi = kNegInf;
-            for (int j = 0; j < n; ++j)
-                if (j != i) {
+#pragma unroll
+            for (int j = 0; j < F; ++j)
+                if (j < n && j != i) {
                     Si += fmaxf(x[j], 0.f);
                     Mi = fmaxf(Mi, x[j]);
                 }
@@ -2369,24 +2483,30 @@ k_logic_small(DevGraph G, const LogicSeg *__restrict__ segs, int n_seg, const fl
         }
     } else {
         const double Td = T;
-        double t[kLogicSmallFan + 1];
+        double t[F];
         double all = -CUDART_INF;
-        for (int j = 0; j < n; ++j) {
-            t[j] = (x[j] == kNegInf) ? -CUDART_INF : log_softplus_d((double)x[j] / Td);
-            all = lse2_d(all, t[j]);
+#pragma unroll
+        for (int j = 0; j < F; ++j) {
+            t[j] = (j >= n || x[j] == kNegInf) ? -CUDART_INF : log_softplus_d((double)x[j] / Td);
+            if (j < n) all = lse2_d(all, t[j]);
         }
-        out[n] = (float)(Td * log_expm1_from_log_d(all));
-        for (int i = 0; i < n; ++i) {
+        outc = (float)(Td * log_expm1_from_log_d(all));
+#pragma unroll
+        for (int i = 0; i < F; ++i) {
             double li = -CUDART_INF;
-            for (int j = 0; j < n; ++j)
-                if (j != i) li = lse2_d(li, t[j]);
+#pragma unroll
+            for (int j = 0; j < F; ++j)
+                if (j < n && j != i) li = lse2_d(li, t[j]);
             out[i] = or_parent_soft(li, xc, Td);
         }
     }
-    for (int k = 0; k <= n; ++k) {
-        const int e = e0 + k;
-        write_logic_edge(sgn * out[k], mo[k], m_new, es_base + 2 * (e - edge_base), damping, G.flags);
-    }
+#pragma unroll
+    for (int k = 0; k < F; ++k)
+        if (k < n) {
+            const int e = e0 + k;
+            write_logic_edge(sgn * out[k], mo[k], m_new, es_base + 2 * (e - edge_base), damping, G.flags);
+        }
+    write_logic_edge(sgn * outc, moc, m_new, es_base + 2 * (e0 + n - edge_base), damping, G.flags);
 }
 
 // Scan element of the warp OR / AND kernel. T = 0: (a, b) = (sum of max(x_j, 0),
@@ -3806,8 +3926,15 @@ static void var_pass_mode(const DevGraph &G, const Plan &P, const float *ev, con
     for (const VarLaunch &L : P.var) {
         if (L.n == 0) continue;
         switch (L.kind) {
+            case kVarBlockSum:  // the tile sums of the split form (single-sample launches)
+                if (MS || S > 1 || L.tiles == nullptr || G.hd_tot == nullptr) continue;
+                k_var_hd_sum<<<L.n_tiles, kVarBlockThreads, 0, s>>>(G, L.list, L.tiles, m);
+                break;
             case kVarBlock:
-                k_var_block<MODE, MS><<<dim3(L.n, S), kVarBlockThreads, 0, s>>>(G, L.list, ev, m, out, dec);
+                if (!MS && S == 1 && L.tiles != nullptr && G.hd_tot != nullptr)
+                    k_var_hd_out<MODE><<<L.n_tiles, kVarBlockThreads, 0, s>>>(G, L.list, L.tiles, ev, m, out, dec);
+                else
+                    k_var_block<MODE, MS><<<dim3(L.n, S), kVarBlockThreads, 0, s>>>(G, L.list, ev, m, out, dec);
                 break;
             case kVarBinary:
                 k_var_thread<2, MODE, MS><<<dim3(L.n_blocks, S), L.threads, 0, s>>>(G, L.list, L.n, L.dense_binary, ev, m, out, dec);

@@ -124,6 +124,8 @@ struct DevGraph {
                              // arrays (k V + v with vin_tab4, else its CSR index); else null
     const float *mem_prm;    // [4 n_members] batch runs with parameters per member: each
                              // member's (T, 1 / T, damping, 0); null otherwise
+    float2 *hd_tot;          // tile sums of the high-degree variables' states (float-float),
+                             // VarLaunch::tiles; null if there are none
 };
 
 struct FactorLaunch {
@@ -148,7 +150,9 @@ enum VarKind : int32_t {
     kVarGroup8 = 4,
     kVarGroup16 = 5,
     kVarWarp = 6,     // warp per variable, K > 16 (pgm_launch_info reports 7)
-    kNumVarKinds = 7
+    kNumVarKinds = 7,
+    kVarBlockSum = 7  // the tile sums of the high-degree variables (a launch before
+                      // kVarBlock's; pgm_launch_info reports 8); no bucket of its own
 };
 
 struct VarLaunch {
@@ -158,6 +162,10 @@ struct VarLaunch {
     int32_t n_blocks;
     int32_t threads;
     int32_t dense_binary;    // every variable of the graph is binary (state offset = 2 v)
+    // kVarBlock / kVarBlockSum: the variables' tiles of kVarTile edges (int4: position in
+    // the list, tile, first DevGraph::hd_tot entry of the variable, its tile count)
+    const int4 *tiles;
+    int32_t n_tiles;
 };
 
 struct Plan {
