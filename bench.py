@@ -61,6 +61,8 @@ def parse_args():
                          "configuration factors, T=0) for ncu captures of its kernels")
     ap.add_argument("--batch-probe", type=int, default=0,
                     help="only run the batched workload for N iterations (3 runs, no CUDA graphs; for ncu)")
+    ap.add_argument("--deconv-probe", type=int, default=0,
+                    help="only run the deconvolution workload for N iterations (3 runs, no CUDA graphs; for ncu)")
     ap.add_argument("--pair-form", type=int, default=0,
                     help="with --batch-probe: the dense K-state pairwise kernel form (PGM_OPT_PAIR_FORM)")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
@@ -1092,6 +1094,27 @@ def batch_probe(args):
                       "launches_per_iter": g.info["launches_per_iter"], "launch_shapes": g.launches()}))
 
 
+def deconv_probe(args):
+    """A short, uncaptured run of the deconvolution workload (T=0, damping 0.5) for ncu
+    captures of its kernels: three runs of `--deconv-probe` iterations, CUDA graphs off.
+    Prints one JSON line with the launch shapes."""
+    import torch
+    from paper_2202_04110_gb300 import binding, build
+    from paper_2202_04110_gb300 import workloads as W
+    build.build()
+    p = W.deconvolution(0, n_iters=args.deconv_probe)
+    ev = torch.as_tensor(p.evidence).cuda()
+    g = binding.Graph(p.graph)
+    g.set_option(binding.OPT_CUDA_GRAPH, 0)
+    m = g.new_msgs()
+    for _ in range(3):
+        m.zero_()
+        g.run_bp(None, ev, 0.0, 0.5, args.deconv_probe, m)
+    torch.cuda.synchronize()
+    print(json.dumps({"deconv_probe": args.deconv_probe, "launches_per_iter": g.info["launches_per_iter"],
+                      "launch_shapes": g.launches()}))
+
+
 def pool_probe(args):
     """A short, uncaptured run of a pool grid (`--pool-probe SIDE,RADIUS,SLACK`, T=0,
     damping 0.5) for ncu captures of the block-form enumeration kernel: three runs of 10
@@ -1119,6 +1142,8 @@ def main():
     args = parse_args()
     if args.pool_probe:
         pool_probe(args)
+    elif args.deconv_probe:
+        deconv_probe(args)
     elif args.batch_probe:
         batch_probe(args)
     elif args.impl == "reference":
