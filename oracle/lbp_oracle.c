@@ -13,7 +13,9 @@
  *   - Enumeration factors given by their list of valid configurations and one
  *     log-potential per configuration (Sec. 5.2). Unlisted configurations have
  *     potential -inf.
- *   - Logical OR / AND factors with message updates linear in the fan-in (Sec. 3).
+ *   - Logical OR / AND / XOR factors with message updates linear in the fan-in (Sec. 3;
+ *     the paper counts three kinds and names none; XOR, the parity check, is the third
+ *     taken here).
  *   - Temperature T on the factor log-sum-exp: T = 1 is sum-product, T = 0 is the
  *     max-product limit used for MAP (Sec. 5.1).
  *   - MAP decode: per-variable argmax of the beliefs (Sec. 5.1), lowest state on ties.
@@ -48,6 +50,7 @@
 
 #define OG_OR 0
 #define OG_AND 1
+#define OG_XOR 2
 #define OG_FLAG_CONTRADICTION 1u
 #define OG_FLAG_NAN 2u
 #define PGM_ORACLE_KMAX 256
@@ -207,6 +210,16 @@ static void or_update(int n, const double *x, double xc, double T, double *out) 
     free(smax);
 }
 
+/* The child's value for parent configuration p: OR, AND, or XOR (the parity of the
+ * parents; the factor admits exactly the configurations of even total parity). */
+static int logic_child(int kind, int any, int all, int64_t p, int n) {
+    if (kind == OG_OR) return any;
+    if (kind == OG_AND) return all;
+    int par = 0;
+    for (int j = 0; j < n; ++j) par ^= (int)((p >> j) & 1);
+    return par;
+}
+
 /*
  * Brute force over all 2^n parent configurations (the definition the closed form must
  * reproduce). v2f holds the incoming 2-vectors, parents then child. mt receives the
@@ -226,7 +239,7 @@ static void logic_brute(int kind, int n, const double *v2f, double T, double *mt
                     any |= bit;
                     all &= bit;
                 }
-                int c = (kind == OG_OR) ? any : all;
+                int c = logic_child(kind, any, all, p, n);
                 int state_i = (i < n) ? (int)((p >> i) & 1) : c;
                 if (state_i != xi) continue;
                 double s = 0.0;
@@ -246,8 +259,114 @@ static double log_odds(const double *m2) {
     return m2[1] - m2[0];
 }
 
+/*
+ * XOR factor, child c = XOR(p_1..p_n): the n + 1 variables have even total parity, so
+ * every member's message depends on all the others alike. With log-odds a_j = x_j / T of
+ * the others, summing their configurations of each parity gives (the product rule of
+ * parity checks)
+ *   D = prod_{j != i} tanh(-a_j / 2),   out_i = T log((1 - D) / (1 + D)),
+ * and the T = 0 limit (max over configurations: flip the cheapest of the others when the
+ * best configuration has the wrong parity)
+ *   out_i = -(prod_{j != i} s_j) min_{j != i} |x_j|,   s_j = -1 if x_j > 0 else +1.
+ * An empty set of others (the child of a parentless factor) gives D = 1, out = -inf.
+ * For T > 0 the product is kept as a sign and the magnitude as
+ *   u_j = -log |tanh(a_j / 2)| >= 0,  held as l_j = log u_j,
+ * so that log |D| = -sum_j u_j keeps its precision when every other member is decided
+ * (u_j ~ 2 e^{-|a_j|}, far below the smallest double): lambda = LSE_{j != i} l_j and
+ *   log((1 - |D|) / (1 + |D|)) = log(-expm1(-e^lambda)) - log1p(e^{-e^lambda}),
+ * which is lambda - log 2 to double precision once e^lambda < 1e-9. Leave-one-out values
+ * are prefix + suffix, O(n). x holds the n + 1 members' log-odds.
+ */
+/* log u with u = -log tanh(|a| / 2) = log1p(2 / expm1(|a|)); for |a| > 30,
+ * u = 2 e^{-|a|} (1 + O(e^{-|a|})), so log u = log 2 - |a| to 1e-13. */
+static double log_u_tanh_half(double a) {
+    a = fabs(a);
+    if (a == 0.0) return INFINITY;       /* tanh 0 = 0: u = +inf */
+    if (a == INFINITY) return -INFINITY; /* tanh = 1: u = 0 */
+    if (a > 30.0) return log(2.0) - a;
+    return log(log1p(2.0 / expm1(a)));
+}
+
+static void xor_update(int m, const double *x, double T, double *out) {
+    double *pl = (double *)malloc(sizeof(double) * (size_t)(m + 1));
+    double *sl = (double *)malloc(sizeof(double) * (size_t)(m + 1));
+    int *ps = (int *)malloc(sizeof(int) * (size_t)(m + 1));
+    int *ss = (int *)malloc(sizeof(int) * (size_t)(m + 1));
+    if (T == 0.0) {
+        /* pl / sl: prefix / suffix minima of |x|; ps / ss: parities of the positive x */
+        pl[0] = INFINITY;
+        ps[0] = 0;
+        for (int j = 0; j < m; ++j) {
+            pl[j + 1] = fabs(x[j]) < pl[j] ? fabs(x[j]) : pl[j];
+            ps[j + 1] = ps[j] ^ (x[j] > 0.0);
+        }
+        sl[m] = INFINITY;
+        ss[m] = 0;
+        for (int j = m - 1; j >= 0; --j) {
+            sl[j] = fabs(x[j]) < sl[j + 1] ? fabs(x[j]) : sl[j + 1];
+            ss[j] = ss[j + 1] ^ (x[j] > 0.0);
+        }
+        for (int i = 0; i < m; ++i) {
+            double mn = pl[i] < sl[i + 1] ? pl[i] : sl[i + 1];
+            int odd = ps[i] ^ ss[i + 1];
+            out[i] = odd ? mn : -mn;
+        }
+    } else {
+        /* pl / sl: prefix / suffix LSE of l_j; ps / ss: parities of the positive x (the
+         * negative factors tanh(-a_j / 2)) */
+        pl[0] = -INFINITY;
+        ps[0] = 0;
+        for (int j = 0; j < m; ++j) {
+            pl[j + 1] = lse2(pl[j], log_u_tanh_half(x[j] / T));
+            ps[j + 1] = ps[j] ^ (x[j] > 0.0);
+        }
+        sl[m] = -INFINITY;
+        ss[m] = 0;
+        for (int j = m - 1; j >= 0; --j) {
+            sl[j] = lse2(sl[j + 1], log_u_tanh_half(x[j] / T));
+            ss[j] = ss[j + 1] ^ (x[j] > 0.0);
+        }
+        for (int i = 0; i < m; ++i) {
+            double lam = lse2(pl[i], sl[i + 1]);
+            int neg = ps[i] ^ ss[i + 1]; /* D < 0 */
+            double r;                    /* log((1 - |D|) / (1 + |D|)) <= 0 */
+            if (lam == INFINITY) r = 0.0;
+            else if (lam == -INFINITY) r = -INFINITY;
+            else if (lam < -20.7) r = lam - log(2.0);
+            else {
+                double u = exp(lam);
+                r = log(-expm1(-u)) - log1p(exp(-u));
+            }
+            out[i] = T * (neg ? -r : r);
+        }
+    }
+    free(pl);
+    free(sl);
+    free(ps);
+    free(ss);
+}
+
 /* Closed-form logical update; v2f and mt as in logic_brute(); mt is normalised. */
 static void logic_closed(int kind, int n, const double *v2f, double T, double *mt) {
+    if (kind == OG_XOR) {
+        double *x = (double *)malloc(sizeof(double) * (size_t)(n + 1));
+        double *out = (double *)malloc(sizeof(double) * (size_t)(n + 1));
+        for (int j = 0; j <= n; ++j) x[j] = log_odds(v2f + 2 * j);
+        xor_update(n + 1, x, T, out);
+        for (int i = 0; i <= n; ++i) {
+            double o = out[i];
+            if (o >= 0.0) {
+                mt[2 * i] = -o;
+                mt[2 * i + 1] = 0.0;
+            } else {
+                mt[2 * i] = 0.0;
+                mt[2 * i + 1] = o;
+            }
+        }
+        free(x);
+        free(out);
+        return;
+    }
     double sgn = (kind == OG_AND) ? -1.0 : 1.0; /* AND(p) = not OR(not p) */
     double *x = (double *)malloc(sizeof(double) * (size_t)(n + 1));
     double *out = (double *)malloc(sizeof(double) * (size_t)(n + 1));
@@ -720,7 +839,7 @@ int og_grad(const og_graph *g, const double *log_pot, const double *evidence, do
                         any |= (int)((p >> j) & 1);
                         all &= (int)((p >> j) & 1);
                     }
-                    int c = (g->l_kind[k] == OG_OR) ? any : all;
+                    int c = logic_child(g->l_kind[k], any, all, p, n);
                     for (int i = 0; i <= n; ++i) {
                         int xi = (i < n) ? (int)((p >> i) & 1) : c;
                         double sv = 0.0;

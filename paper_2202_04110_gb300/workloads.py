@@ -34,6 +34,7 @@ import numpy as np
 
 OR = 0
 AND = 1
+XOR = 2  # the child is the parity of the parents
 
 
 @dataclass
@@ -365,7 +366,8 @@ def potts_rbm_batch(seed: int = 0, n_grids: int = 256, n_iters: int = 100,
 
 def random_graph(seed: int, n_vars: int = 8, max_K: int = 3, n_pair: int = 6,
                  n_triple: int = 2, n_or: int = 1, n_and: int = 1, sparse: bool = True,
-                 tree: bool = False, shared: bool = False, scale: float = 1.0) -> tuple[FactorGraph, np.ndarray, np.ndarray]:
+                 tree: bool = False, shared: bool = False, scale: float = 1.0,
+                 n_xor: int = 0) -> tuple[FactorGraph, np.ndarray, np.ndarray]:
     """Small random factor graph with mixed state counts, pairwise and triple
     enumeration factors (optionally with sparse configuration lists) and logical
     factors over the binary variables. With ``tree=True`` only pairwise factors along
@@ -426,7 +428,7 @@ def random_graph(seed: int, n_vars: int = 8, max_K: int = 3, n_pair: int = 6,
             pots.append(rng.normal(0, scale, n_pot))
         # logical factors over binary variables
         binary = np.flatnonzero(K == 2)
-        for kind, count in ((OR, n_or), (AND, n_and)):
+        for kind, count in ((OR, n_or), (AND, n_and), (XOR, n_xor)):
             if count == 0 or binary.size < 2:
                 continue
             offs, pars, ch = [0], [], []
@@ -445,26 +447,32 @@ def random_graph(seed: int, n_vars: int = 8, max_K: int = 3, n_pair: int = 6,
 
 
 def random_factor_tree(seed: int, n_vars: int = 9, max_K: int = 3, shared: bool = False,
-                       logical: bool = True, scale: float = 1.0) -> tuple[FactorGraph, np.ndarray, np.ndarray]:
+                       logical: bool = True, scale: float = 1.0,
+                       xor: bool = False) -> tuple[FactorGraph, np.ndarray, np.ndarray]:
     """Random factor graph whose variable-factor graph is a tree: starting from one
     variable, each new factor joins one existing variable to 1-3 new ones. Factors are
     enumeration factors (dense or with a sparse configuration list) or, when all their
-    variables are binary and ``logical`` is set, OR / AND factors."""
+    variables are binary and ``logical`` is set, OR / AND factors (and XOR with ``xor``)."""
     rng = np.random.default_rng(seed)
     K = [int(rng.integers(2, max_K + 1))]
     enum_by_sig: dict = {}
-    logic: dict = {OR: ([0], [], []), AND: ([0], [], [])}
+    logic: dict = {OR: ([0], [], []), AND: ([0], [], []), XOR: ([0], [], [])}
+    ENUM = -1
     while len(K) < n_vars:
         anchor = int(rng.integers(0, len(K)))
         n_new = int(min(rng.integers(1, 4), n_vars - len(K)))
         new = list(range(len(K), len(K) + n_new))
-        kind = int(rng.integers(0, 3)) if logical else 2
-        if kind in (OR, AND):
+        if logical:
+            draw = int(rng.integers(0, 4 if xor else 3))
+            kind = {0: OR, 1: AND, 2: ENUM, 3: XOR}[draw]
+        else:
+            kind = ENUM
+        if kind != ENUM:
             for _ in new:
                 K.append(2)
             if K[anchor] != 2:
-                kind = 2
-        if kind not in (OR, AND):
+                kind = ENUM
+        if kind == ENUM:
             for v in new:
                 if len(K) <= v:
                     K.append(int(rng.integers(2, max_K + 1)))
@@ -494,7 +502,7 @@ def random_factor_tree(seed: int, n_vars: int = 9, max_K: int = 3, shared: bool 
         n_pot = cfg.shape[0] if shared else cfg.shape[0] * vars_.shape[0]
         pots.append(rng.normal(0, scale, n_pot))
     logic_groups = []
-    for kind in (OR, AND):
+    for kind in (OR, AND, XOR):
         offs, pars, ch = logic[kind]
         if ch:
             logic_groups.append(LogicGroup(kind, np.asarray(offs, np.int32),

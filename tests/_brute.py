@@ -21,7 +21,7 @@ import itertools
 
 import numpy as np
 
-from paper_2202_04110_gb300.workloads import AND, OR
+from paper_2202_04110_gb300.workloads import AND, OR, XOR
 
 
 def lse(z, axis=None, T=1.0):
@@ -57,7 +57,7 @@ def dense_factors(graph, log_pot):
             n = len(pars)
             t = np.full([2] * (n + 1), -np.inf)
             for p in itertools.product((0, 1), repeat=n):
-                c = int(any(p)) if g.kind == OR else int(all(p))
+                c = int(any(p)) if g.kind == OR else int(all(p)) if g.kind == AND else sum(p) % 2
                 t[tuple(p) + (c,)] = 0.0
             out.append((scope, t))
     return out
@@ -179,7 +179,7 @@ def logic_dense(kind, v2f, T):
     n = v2f.shape[0] - 1
     t = np.full([2] * (n + 1), -np.inf)
     for p in itertools.product((0, 1), repeat=n):
-        c = int(any(p)) if kind == OR else int(all(p))
+        c = int(any(p)) if kind == OR else int(all(p)) if kind == AND else sum(p) % 2
         t[tuple(p) + (c,)] = 0.0
     outs = factor_messages_dense(list(range(n + 1)), t, list(v2f), T)
     res = []

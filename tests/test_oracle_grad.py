@@ -42,6 +42,10 @@ def _cases():
     for seed in (4, 5, 9):
         g, lp, ev = W.random_graph(seed, n_vars=8, max_K=2, n_pair=5, n_triple=1, n_or=2, n_and=2)
         out.append((f"logic{seed}", g, lp, ev))
+    # XOR (parity) factors with OR / AND
+    for seed in (4, 5):
+        g, lp, ev = W.random_graph(seed, n_vars=8, max_K=2, n_pair=5, n_triple=1, n_or=1, n_and=1, n_xor=2)
+        out.append((f"xor{seed}", g, lp, ev))
     return out
 
 

@@ -26,7 +26,13 @@ from tests import _brute as B
 def _tree_cases():
     cases = []
     for seed in range(12):
-        cases.append(dict(seed=seed, logical=True, shared=(seed % 3 == 0)))
+        cases.append(dict(seed=seed, logical=True, shared=(seed % 3 == 0), xor=False))
+    seed = 300
+    while sum(c["xor"] for c in cases) < 6:  # trees that also hold XOR (parity) factors
+        g, _, _ = W.random_factor_tree(seed, n_vars=9, logical=True, xor=True)
+        if any(lg.kind == W.XOR for lg in g.logic_groups):
+            cases.append(dict(seed=seed, logical=True, shared=(seed % 2 == 0), xor=True))
+        seed += 1
     return cases
 
 
@@ -34,7 +40,9 @@ def _tree_cases():
 @pytest.mark.parametrize("T", [1.0, 0.0])
 def test_tree_exact(case, T):
     g, lp, ev = W.random_factor_tree(case["seed"], n_vars=9, shared=case["shared"],
-                                     logical=case["logical"])
+                                     logical=case["logical"], xor=case["xor"])
+    if case["xor"]:
+        assert any(lg.kind == W.XOR for lg in g.logic_groups), "the tree should hold an XOR factor"
     msgs, fl = oracle.run_bp(g, lp, ev, T, 0.0, g.n_vars + 1)
     _, nb, dec, fl2 = oracle.beliefs(g, ev, msgs)
     assert fl == 0 and fl2 == 0
@@ -75,7 +83,7 @@ def test_tree_exact_with_damping(seed, T):
 @pytest.mark.parametrize("damping", [0.0, 0.5])
 def test_loopy_matches_dense_definition(seed, T, damping):
     g, lp, ev = W.random_graph(seed, n_vars=9, max_K=3, n_pair=8, n_triple=2, n_or=2, n_and=2,
-                               sparse=True, shared=(seed % 2 == 1))
+                               sparse=True, shared=(seed % 2 == 1), n_xor=(2 if seed >= 4 else 0))
     n_it = 7
     msgs, fl = oracle.run_bp(g, lp, ev, T, damping, n_it)
     _, nb, _, _ = oracle.beliefs(g, ev, msgs)
@@ -94,7 +102,7 @@ def test_warm_start_composes(seed):
     np.testing.assert_array_equal(m2, m3)
 
 
-@pytest.mark.parametrize("kind", [W.OR, W.AND])
+@pytest.mark.parametrize("kind", [W.OR, W.AND, W.XOR])
 @pytest.mark.parametrize("T", [0.0, 0.5, 1.0])
 @pytest.mark.parametrize("n", [1, 2, 3, 5, 8, 11])
 def test_logical_closed_form_vs_enumeration(kind, T, n):
@@ -111,6 +119,41 @@ def test_logical_closed_form_vs_enumeration(kind, T, n):
         np.testing.assert_allclose(closed, ref, atol=1e-9, rtol=1e-9)
         brute = oracle.logic_update(kind, v2f, T, brute=True)
         np.testing.assert_allclose(brute, ref, atol=1e-9, rtol=1e-9)
+
+
+@pytest.mark.parametrize("T", [0.0, 0.5, 1.0])
+def test_xor_special_cases(T):
+    # one parent: XOR(p) = p, so each side receives the other's log-odds
+    v2f = np.array([[0.0, 1.3], [0.2, -0.5]])
+    out = oracle.logic_update(W.XOR, v2f, T)
+    assert np.isclose(out[0, 1] - out[0, 0], -0.7)
+    assert np.isclose(out[1, 1] - out[1, 0], 1.3)
+    # no parents: XOR of nothing is 0
+    out = oracle.logic_update(W.XOR, np.array([[0.4, -0.1]]), T)
+    assert out[0, 0] == 0.0 and out[0, 1] == -np.inf
+    # a parent with even odds (log-odds 0) makes every other member's message flat
+    v2f = np.array([[0.3, 0.3], [0.0, 2.0], [1.0, -1.5]])
+    out = oracle.logic_update(W.XOR, v2f, T)
+    assert np.allclose(out[1], 0.0) and np.allclose(out[2], 0.0)
+    # all others certain: the member receives their parity with certainty
+    v2f = np.array([[-np.inf, 0.0], [-np.inf, 0.0], [0.1, 0.2]])  # parents 1, 1 -> child 0
+    out = oracle.logic_update(W.XOR, v2f, T)
+    assert out[2, 0] == 0.0 and out[2, 1] == -np.inf
+    ref = B.logic_dense(W.XOR, v2f, T)
+    np.testing.assert_allclose(out, ref, atol=1e-12)
+    # the two-member parity (child = one parent) at T = 1 is the pairwise equality factor
+    if T == 1.0:
+        x = 0.8
+        v2f = np.array([[0.0, x], [0.0, 0.0]])
+        out = oracle.logic_update(W.XOR, v2f, T)
+        assert np.isclose(out[1, 1] - out[1, 0], x)
+    # three members at T = 1: the parity check's product rule tanh(out/2) = -prod tanh(-x/2)
+    if T == 1.0:
+        x1, x2 = 0.9, -1.7
+        v2f = np.array([[0.0, x1], [0.0, x2], [0.0, 0.0]])
+        out = oracle.logic_update(W.XOR, v2f, T)
+        d = np.tanh(-x1 / 2) * np.tanh(-x2 / 2)
+        assert np.isclose(out[2, 1] - out[2, 0], np.log((1 - d) / (1 + d)))
 
 
 @pytest.mark.parametrize("T", [0.0, 1.0])
