@@ -56,6 +56,7 @@ typedef int32_t pgm_status;
 
 #define PGM_LOGIC_OR 0  /* child = OR(parents)  */
 #define PGM_LOGIC_AND 1 /* child = AND(parents) */
+#define PGM_LOGIC_XOR 2 /* child = XOR(parents): parents and child have even parity */
 
 /* Bits of the device status word (pgm_device_flags). */
 #define PGM_FLAG_CONTRADICTION 1u /* a message or belief had every state at -inf */
@@ -85,12 +86,14 @@ typedef struct {
 } pgm_enum_group;
 
 /*
- * Logical factors (Sec. 3: logical factors whose updates are linear in the fan-in): child =
+ * Logical factors (Sec. 3: three kinds of logical factor whose updates are linear in the
+ * fan-in; the paper names none of them, and OR, AND and XOR are the three built): child =
  * OP(parents) over binary variables, log-potential 0 on valid configurations and -inf
- * otherwise. A factor may have zero parents (OR of nothing is 0, AND of nothing is 1).
+ * otherwise. A factor may have zero parents (OR and XOR of nothing are 0, AND of nothing
+ * is 1). pgm_grad supports OR and AND groups only (PGM_ENOTSUP for a graph with XOR).
  */
 typedef struct {
-    int32_t kind;            /* PGM_LOGIC_OR or PGM_LOGIC_AND */
+    int32_t kind;            /* PGM_LOGIC_OR, PGM_LOGIC_AND or PGM_LOGIC_XOR */
     int32_t n_fac;           /* factors in the group */
     const int32_t *par_off;  /* host [n_fac + 1], par_off[0] = 0, non-decreasing */
     const int32_t *parents;  /* host [par_off[n_fac]] */

@@ -61,6 +61,7 @@ struct pgm_graph {
     int device = 0;
     int n_sm = 1;
     bool ordered = false;              // allocations stream-ordered on alloc_stream
+    bool has_xor = false;              // a logical group of kind PGM_LOGIC_XOR (no adjoint)
     cudaStream_t alloc_stream = nullptr;
     pgm_info info{};
     DevGraph G{};
@@ -366,8 +367,10 @@ pgm_status build_plan(const HostLayout &H, pgm_graph *g, Packer &pk, std::vector
         // logical groups: thread per factor
         std::vector<LogicSeg> lsegs;
         int32_t lblk = 0;
+        g->has_xor = false;
         for (const HostLogicGroup &hg : H.logic_groups) {
             LogicSeg ls = hg.seg;
+            g->has_xor |= ls.kind == PGM_LOGIC_XOR && ls.n_fac > 0;
             ls.block_begin = lblk;
             lblk += (ls.n_fac + 127) / 128;
             lsegs.push_back(ls);
@@ -677,7 +680,7 @@ static pgm_status build_from_layout(const HostLayout &H, pgm_graph **out, cudaSt
     size_t hd_bytes = H.var_bucket[kVarBlock].empty() ? 0 : 2 * es_bytes;
     const size_t lr_bytes = g->P.lr ? align_up((size_t)g->lr_slots * sizeof(float), 256) : 0;
     const size_t prm_bytes = g->P.lr ? align_up((size_t)3 * (H.E / 2) * sizeof(float), 256) : 0;
-    const size_t blo_bytes = H.var_bucket[kVarWarp].empty() ? 0 : vs_bytes;
+    const size_t blo_bytes = keeps_b_lo(H) ? vs_bytes : 0;
     const size_t tot_bytes = align_up((size_t)g->hd_tot_entries * sizeof(float2), 256);
     const size_t scratch_bytes = es_bytes + vs_bytes + 256 + hd_bytes + 2 * lr_bytes + prm_bytes + blo_bytes + tot_bytes;
     char *smem = nullptr;
@@ -804,7 +807,7 @@ int64_t pgm::layout_device_bytes(const HostLayout &H) {
     }
     idx += (size_t)n_tiles * sizeof(int4);
     return (int64_t)(idx + es_bytes + vs_bytes + 256 + (H.var_bucket[kVarBlock].empty() ? 0 : 2 * es_bytes) +
-                     (H.var_bucket[kVarWarp].empty() ? 0 : vs_bytes) + align_up((size_t)tot * sizeof(float2), 256));
+                     (keeps_b_lo(H) ? vs_bytes : 0) + align_up((size_t)tot * sizeof(float2), 256));
 }
 
 pgm_status pgm::build_layout_on_stream(const HostLayout &H, cudaStream_t s, pgm_graph **out) {
@@ -2003,6 +2006,7 @@ pgm_status pgm_grad(pgm_graph *g, const float *log_pot, const float *evidence, f
     if (n_iters < 0 || ckpt_every < 1) return fail(PGM_EINVAL, "n_iters >= 0 and ckpt_every >= 1 required");
     if (!evidence || !d_beliefs || !d_evidence || (g->info.n_potentials > 0 && (!log_pot || !d_log_pot)))
         return fail(PGM_EINVAL, "NULL argument");
+    if (g->has_xor) return fail(PGM_ENOTSUP, "pgm_grad: XOR factors have no adjoint in this build");
     if (pgm_status st = checked_gate(g, stream); st != PGM_OK) return st;
     DeviceGuard dg(g->device);
     cudaStream_t s = static_cast<cudaStream_t>(stream);

@@ -124,7 +124,8 @@ std::string compile_graph(const void *const *vdescs, int n_desc, HostLayout *L) 
         }
         for (int gi = 0; gi < d->n_logic_groups; ++gi) {
             const pgm_logic_group &g = d->logic_groups[gi];
-            if (g.kind != PGM_LOGIC_OR && g.kind != PGM_LOGIC_AND) return fmt("logic group %lld: unknown kind %lld", gi, g.kind);
+            if (g.kind != PGM_LOGIC_OR && g.kind != PGM_LOGIC_AND && g.kind != PGM_LOGIC_XOR)
+                return fmt("logic group %lld: unknown kind %lld", gi, g.kind);
             if (g.n_fac < 0) return fmt("logic group %lld: negative n_fac", gi);
             if (!g.par_off) return fmt("logic group %lld: par_off is NULL", gi);
             if (g.par_off[0] != 0) return fmt("logic group %lld: par_off[0] must be 0", gi);
@@ -240,9 +241,9 @@ std::string compile_graph(const void *const *vdescs, int n_desc, HostLayout *L) 
                 while (s.lanes < 32 && mean > 8 * s.lanes) s.lanes *= 2;
                 int64_t tb = (((int64_t)g.n_cfg * g.arity + 15) & ~15) + (int64_t)len * 4 +
                              (g.shared_potentials ? (int64_t)g.n_cfg * 4 : 0);
-                // packed pairwise lists with a shared table: each list entry staged beside
-                // its configuration's log-potential (one 8-byte read per entry)
-                if (g.shared_potentials && s.packed) tb = ((tb + 7) & ~(int64_t)7) + 8 * nl;
+                // packed pairwise lists with a shared table: only the offsets and each list
+                // entry beside its configuration's log-potential (one 8-byte read per entry)
+                if (g.shared_potentials && s.packed) tb = 4 * ob + 8 * nl;
                 s.table_bytes = tb <= kEnumTableSmem ? (int32_t)tb : 0;
             }
             for (int64_t f = 0; f < g.n_fac; ++f)

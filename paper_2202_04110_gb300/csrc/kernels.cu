@@ -25,8 +25,11 @@
 // (float-float) and the beliefs the factor pass reads are stored relative to each
 // variable's largest state. An edge whose stored message has an entry that is -inf or
 // larger in magnitude than kExactThreshold takes its variable-to-factor values from an
-// explicit leave-one-out sum (v2f_slow_edge) instead of b - m; edges of variables with
-// more than kVarBlockDegree factors always do (computed by the block variable pass).
+// explicit leave-one-out sum (v2f_slow_edge) instead of b - m -- or, on graphs that keep
+// belief residuals (variables of more than 16 states, logical factors) and for finite
+// entries, from (b - m) + b_lo, b_lo being what the rounding of b dropped, written by the
+// variable pass for every variable that has such an entry; edges of variables with more
+// than kVarBlockDegree factors always take the exact sums of the block variable pass.
 #include <algorithm>
 #include <cstdint>
 
@@ -167,6 +170,27 @@ __device__ __forceinline__ bool ff_gt(FF a, FF b) {
     if (a.hi == kNegInf) return false;
     if (b.hi == kNegInf) return true;
     return ff_diff(a, b) > 0.f;
+}
+
+// What r = ff_diff(a, b) dropped: (a - b) - r, from the two-sum of the high parts plus
+// the low parts; 0 where a or b is not finite.
+__device__ __forceinline__ float ff_diff_lo(FF a, FF b, float r) {
+    if (!isfinite(a.hi) || !isfinite(b.hi)) return 0.f;
+    const float th = a.hi - b.hi, bb = th - a.hi;
+    const float te = (a.hi - (th - bb)) + (-b.hi - bb);
+    return (th - r) + (te + (a.lo - b.lo));
+}
+
+// Belief residuals of a binary variable whose relative beliefs (r0, r1) came from the
+// float-float sums (s0, s1): the larger state is exact (0), the other keeps what its
+// rounding dropped.
+__device__ __forceinline__ void write_b_lo2(float *p, FF s0, FF s1, float r0, float r1) {
+    float l0 = 0.f, l1 = 0.f;
+    if (r0 != 0.f || r1 != 0.f) {
+        if (r1 == 0.f) l0 = ff_diff_lo(s0, s1, r0);
+        else l1 = ff_diff_lo(s1, s0, r1);
+    }
+    reinterpret_cast<float2 *>(p)[0] = make_float2(l0, l1);
 }
 
 // ---- variable-to-factor value -------------------------------------------------------
@@ -328,6 +352,38 @@ __device__ __forceinline__ float or_parent_max(float S, float M, float xc) {
     return (z >= 0.f) ? -mn : xc + S;
 }
 
+// XOR (parity) factors: the parents and the child have even parity, and a member's
+// message depends on all the others alike. With log-odds a_j = x_j / T of the others,
+// the product rule of parity checks gives D = prod tanh(-a_j / 2) and the log-odds
+// T log((1 - D) / (1 + D)). The magnitude is carried as l_j = log u_j,
+// u_j = -log tanh(|a_j| / 2) = log1p(2 / expm1(|a_j|)) (log 2 - |a_j| beyond 30), and the
+// others' LSE lambda of the l_j gives log((1 - |D|) / (1 + |D|)) =
+// log(-expm1(-e^lambda)) - log1p(e^-e^lambda) (lambda - log 2 once e^lambda < 1e-9); the
+// sign is the parity of the others' positive log-odds. T = 0: the others' smallest |x|,
+// positive when an odd number of them is positive. FP64 at T > 0, as the OR / AND forms.
+__device__ __forceinline__ double xor_log_u(double a) {
+    a = fabs(a);
+    if (a == 0.0) return CUDART_INF;
+    if (isinf(a)) return -CUDART_INF;
+    if (a > 30.0) return 0.6931471805599453 - a;
+    return log(log1p(2.0 / expm1(a)));
+}
+
+// XOR output (T > 0) from the others' LSE lambda and their parity.
+__device__ __forceinline__ float xor_out_soft(double lam, bool odd, double T) {
+    double r;
+    if (lam == CUDART_INF) r = 0.0;
+    else if (lam == -CUDART_INF) r = -CUDART_INF;
+    else if (lam < -20.7) r = lam - 0.6931471805599453;
+    else {
+        const double u = exp(lam);
+        r = log(-expm1(-u)) - log1p(exp(-u));
+    }
+    return (float)(T * (odd ? -r : r));
+}
+
+__device__ __forceinline__ float xor_out_max(float mn, bool odd) { return odd ? mn : -mn; }
+
 __device__ __forceinline__ float log_odds(float a0, float a1) {
     return (a0 == kNegInf && a1 == kNegInf) ? 0.f : a1 - a0;
 }
@@ -436,11 +492,13 @@ __global__ void __launch_bounds__(256) k_var_thread(DevGraph G, const int32_t *_
         const int vs = dense_binary ? 2 * v : __ldg(G.vs_off + v);
         const float2 e = __ldg(reinterpret_cast<const float2 *>(ev + vs));
         FF s0 = ff_make(e.x), s1 = ff_make(e.y);
+        bool big = false;
         for (int k = k0; k < k1; ++k) {
             const int es = __ldg(G.vin_es + k);
             const float2 q = __ldg(reinterpret_cast<const float2 *>(m + es));
             s0 = ff_add(s0, q.x);
             s1 = ff_add(s1, q.y);
+            big |= needs_exact(q.x) | needs_exact(q.y);
         }
         if constexpr (MODE == kVarDecode) {
             dec[v] = ff_gt(s1, s0) ? 1 : 0;
@@ -463,6 +521,7 @@ __global__ void __launch_bounds__(256) k_var_thread(DevGraph G, const int32_t *_
         }
         if constexpr (MODE == kVarIter) {
             reinterpret_cast<float2 *>(out + vs)[0] = make_float2(r0, r1);
+            if (big && G.b_lo != nullptr) write_b_lo2(G.b_lo + vs, s0, s1, r0, r1);
         } else {  // kVarNormalised
             if (r0 == kNegInf && r1 == kNegInf) {
                 atomicOr(G.flags, kFlagContradiction);
@@ -477,10 +536,14 @@ __global__ void __launch_bounds__(256) k_var_thread(DevGraph G, const int32_t *_
         const int vs = __ldg(G.vs_off + v), K = __ldg(G.vs_off + v + 1) - vs;
         FF best = ff_make(kNegInf);
         int arg = 0;
-        bool nan = false;
+        bool nan = false, big = false;  // big: an incoming entry needs the exact form
         for (int x = 0; x < K; ++x) {
             FF s = ff_make(__ldg(ev + vs + x));
-            for (int k = k0; k < k1; ++k) s = ff_add(s, __ldg(m + __ldg(G.vin_es + k) + x));
+            for (int k = k0; k < k1; ++k) {
+                const float q = __ldg(m + __ldg(G.vin_es + k) + x);
+                s = ff_add(s, q);
+                big |= needs_exact(q);
+            }
             nan |= (s.hi != s.hi);
             if (x == 0 || ff_gt(s, best)) {
                 best = s;
@@ -505,6 +568,7 @@ __global__ void __launch_bounds__(256) k_var_thread(DevGraph G, const int32_t *_
                 const float r = (x == arg) ? 0.f : ff_diff(s, best);
                 out[vs + x] = r;
                 if (MODE == kVarNormalised && x != arg) acc += expf(r);
+                if (MODE == kVarIter && big && G.b_lo != nullptr) G.b_lo[vs + x] = x == arg ? 0.f : ff_diff_lo(s, best, r);
             }
             if constexpr (MODE == kVarNormalised) {
                 const float z = log1pf(acc);
@@ -654,6 +718,8 @@ __global__ void __launch_bounds__(256) k_var_tab4(DevGraph G, int n, const float
     if (t.y >= 0) { s0 = ff_add(s0, q1.x); s1 = ff_add(s1, q1.y); }
     if (t.z >= 0) { s0 = ff_add(s0, q2.x); s1 = ff_add(s1, q2.y); }
     if (t.w >= 0) { s0 = ff_add(s0, q3.x); s1 = ff_add(s1, q3.y); }
+    const bool big = needs_exact(q0.x) | needs_exact(q0.y) | needs_exact(q1.x) | needs_exact(q1.y) |
+                     needs_exact(q2.x) | needs_exact(q2.y) | needs_exact(q3.x) | needs_exact(q3.y);
     if constexpr (MODE == kVarDecode) {
         dec[v] = ff_gt(s1, s0) ? 1 : 0;
         return;
@@ -674,6 +740,7 @@ __global__ void __launch_bounds__(256) k_var_tab4(DevGraph G, int n, const float
     }
     if constexpr (MODE == kVarIter) {
         reinterpret_cast<float2 *>(out)[v] = make_float2(r0, r1);
+        if (big && G.b_lo != nullptr) write_b_lo2(G.b_lo + 2 * v, s0, s1, r0, r1);
     } else {
         if (r0 == kNegInf && r1 == kNegInf) {
             atomicOr(G.flags, kFlagContradiction);
@@ -2205,7 +2272,21 @@ k_enum_block(DevGraph G, const EnumSeg *__restrict__ segs, int n_seg, const floa
     const float *phi_g = pot + __ldg(&S->pot_base);
     const float *phi_tab = phi_g;
     const int2 *flst = nullptr;  // staged (entry, log-potential) pairs of a packed shared list
-    if (tb > 0) {  // 16-byte aligned sources (pool layout) and destinations
+    if (tb > 0 && shared && packed) {
+        // packed pairwise lists with a shared table: the offsets, then each list entry
+        // beside its configuration's log-potential (one 8-byte read per entry); the
+        // configuration table and the log-potentials are not read in this form
+        unsigned char *t = eb_smem + ((12 * ksum * n_teams + 15) & ~15);
+        int32_t *tbs = reinterpret_cast<int32_t *>(t);
+        for (int i = threadIdx.x; i < ob; i += blockDim.x) tbs[i] = __ldg(bs + i);
+        int2 *fl = reinterpret_cast<int2 *>(t + 4 * ob);  // 4 ob is a multiple of 16
+        for (int i = threadIdx.x; i < a * nc; i += blockDim.x) {
+            const int e = __ldg(bs + ob + i);
+            fl[i] = make_int2(e, __float_as_int(__ldg(phi_g + (e >> 11))));
+        }
+        flst = fl;
+        bs = tbs;
+    } else if (tb > 0) {  // 16-byte aligned sources (pool layout) and destinations
         unsigned char *t = eb_smem + ((12 * ksum * n_teams + 15) & ~15);
         const uint4 *c_src = reinterpret_cast<const uint4 *>(cfg);
         uint4 *c_dst = reinterpret_cast<uint4 *>(t);
@@ -2218,14 +2299,6 @@ k_enum_block(DevGraph G, const EnumSeg *__restrict__ segs, int n_seg, const floa
             float *tphi = reinterpret_cast<float *>(tbs + bs_len);
             for (int i = threadIdx.x; i < nc; i += blockDim.x) tphi[i] = __ldg(phi_g + i);
             phi_tab = tphi;
-            if (packed) {  // list entries beside their log-potentials
-                int2 *fl = reinterpret_cast<int2 *>(t + ((cfg_bytes + 4 * (bs_len + nc) + 7) & ~7));
-                for (int i = threadIdx.x; i < a * nc; i += blockDim.x) {
-                    const int e = __ldg(bs + ob + i);
-                    fl[i] = make_int2(e, __float_as_int(__ldg(phi_g + (e >> 11))));
-                }
-                flst = fl;
-            }
         }
         cfg = t;
         bs = tbs;
@@ -2411,10 +2484,18 @@ __device__ __forceinline__ float edge_logodds(const DevGraph &G, const float *ev
         a0 = t[0];
         a1 = t[1];
     } else if (needs_exact(mo.x) || needs_exact(mo.y)) {
-        float t[2];
-        v2f_slow_edge(G, ev, m_old, vs, es, 2, t);
-        a0 = t[0];
-        a1 = t[1];
+        if (G.b_lo != nullptr && isfinite(mo.x) && isfinite(mo.y)) {
+            // the variable pass saw this large entry and wrote the belief residuals:
+            // b - m without the cancellation, rounded twice
+            const float2 bb = ld2(b + vs), bl = ld2(G.b_lo + vs);
+            a0 = (bb.x - mo.x) + bl.x;
+            a1 = (bb.y - mo.y) + bl.y;
+        } else {
+            float t[2];
+            v2f_slow_edge(G, ev, m_old, vs, es, 2, t);
+            a0 = t[0];
+            a1 = t[1];
+        }
     } else {
         const float2 bb = ld2(b + vs);
         a0 = bb.x - mo.x;
@@ -2444,7 +2525,7 @@ k_logic_small(DevGraph G, const LogicSeg *__restrict__ segs, int n_seg, const fl
     const int p0 = __ldg(po + f), n = __ldg(po + f + 1) - p0;
     const int edge_base = __ldg(&S->edge_base), es_base = __ldg(&S->es_base);
     const int e0 = edge_base + p0 + f;
-    const float sgn = __ldg(&S->kind) == 1 ? -1.f : 1.f;
+    const float sgn = __ldg(&S->kind) == PGM_LOGIC_AND ? -1.f : 1.f;
     // parents in unrolled slots (j < n valid) and the child apart, so that every array
     // index is a constant and the values stay in registers
     constexpr int F = kLogicSmallFan;
@@ -2461,7 +2542,51 @@ k_logic_small(DevGraph G, const LogicSeg *__restrict__ segs, int n_seg, const fl
     }
     const float xc = edge_logodds(G, ev, b, m_old, e0 + n, es_base + 2 * (e0 + n - edge_base), sgn, moc);
     float out[F], outc;
-    if (MAXP) {
+    if (__ldg(&S->kind) == PGM_LOGIC_XOR) {  // sgn = +1
+        bool pos_all = xc > 0.f;  // parity of all members' positive log-odds
+#pragma unroll
+        for (int j = 0; j < F; ++j)
+            if (j < n) pos_all ^= x[j] > 0.f;
+        if (MAXP) {
+            float mall = CUDART_INF_F;  // smallest |x| over the parents
+#pragma unroll
+            for (int j = 0; j < F; ++j)
+                if (j < n) mall = fminf(mall, fabsf(x[j]));
+            outc = xor_out_max(mall, pos_all ^ (xc > 0.f));
+#pragma unroll
+            for (int i = 0; i < F; ++i) {
+                float mn = fabsf(xc);
+#pragma unroll
+                for (int j = 0; j < F; ++j)
+                    if (j < n && j != i) mn = fminf(mn, fabsf(x[j]));
+                out[i] = xor_out_max(mn, pos_all ^ (x[i] > 0.f));
+            }
+        } else {
+            const double Td = T;
+            double l[F];
+#pragma unroll
+            for (int j = 0; j < F; ++j) l[j] = j < n ? xor_log_u((double)x[j] / Td) : -CUDART_INF;
+            const double lc = xor_log_u((double)xc / Td);
+            double all = -CUDART_INF;
+#pragma unroll
+            for (int j = 0; j < F; ++j)
+                if (j < n) all = lse2_d(all, l[j]);
+            outc = xor_out_soft(all, pos_all ^ (xc > 0.f), Td);
+#pragma unroll
+            for (int i = 0; i < F; ++i) {
+                // the others as prefix (parents before i, ascending) and suffix (the
+                // child, then the parents after i, descending)
+                double pre = -CUDART_INF, suf = lc;
+#pragma unroll
+                for (int j = 0; j < F; ++j)
+                    if (j < i) pre = lse2_d(pre, l[j]);
+#pragma unroll
+                for (int j = F - 1; j >= 0; --j)
+                    if (j < n && j > i) suf = lse2_d(suf, l[j]);
+                out[i] = xor_out_soft(lse2_d(pre, suf), pos_all ^ (x[i] > 0.f), Td);
+            }
+        }
+    } else if (MAXP) {
         float A = 0.f, Mall = kNegInf;
 #pragma unroll
         for (int j = 0; j < F; ++j)
@@ -2523,19 +2648,23 @@ __device__ __forceinline__ ScanEl d_el(double d) {
     return ScanEl{__int_as_float(__double2hiint(d)), __int_as_float(__double2loint(d))};
 }
 
-template <bool MAXP>
+// XOR: T = 0, a = smallest |x_j| (b unused); T > 0, the FP64 LSE of xor_log_u(x_j / T).
+template <bool MAXP, bool XOR = false>
 __device__ __forceinline__ ScanEl scan_ident() {
+    if (XOR && MAXP) return ScanEl{CUDART_INF_F, 0.f};
     return MAXP ? ScanEl{0.f, kNegInf} : d_el(-CUDART_INF);
 }
 
-template <bool MAXP>
+template <bool MAXP, bool XOR = false>
 __device__ __forceinline__ ScanEl scan_comb(ScanEl p, ScanEl q) {
+    if (XOR && MAXP) return ScanEl{fminf(p.a, q.a), 0.f};
     if (MAXP) return ScanEl{p.a + q.a, fmaxf(p.b, q.b)};
     return d_el(lse2_d(el_d(p), el_d(q)));
 }
 
-template <bool MAXP>
+template <bool MAXP, bool XOR = false>
 __device__ __forceinline__ ScanEl scan_elem(float x, double T) {
+    if (XOR) return MAXP ? ScanEl{fabsf(x), 0.f} : d_el(xor_log_u((double)x / T));
     if (MAXP) return ScanEl{fmaxf(x, 0.f), x};
     return d_el(x == kNegInf ? -CUDART_INF : log_softplus_d((double)x / T));
 }
@@ -2550,6 +2679,94 @@ __device__ __forceinline__ ScanEl shfl_down_el(ScanEl v, int d) {
 }
 __device__ __forceinline__ ScanEl shfl_el(ScanEl v, int src) {
     return ScanEl{__shfl_sync(0xffffffffu, v.a, src), __shfl_sync(0xffffffffu, v.b, src)};
+}
+
+// One factor of k_logic_warp (XOR: the parity form; the suffix scan starts from the
+// child's element, so that the leave-one-out combination of a parent covers the child).
+template <bool MAXP, bool XOR>
+__device__ __forceinline__ void logic_warp_factor(const DevGraph &G, const float *__restrict__ b,
+                                                  const float *__restrict__ ev, const float *__restrict__ m_old,
+                                                  float *__restrict__ m_new, float T, float damping, int e0, int n,
+                                                  int edge_base, int es_base, float sgn, float *sx, float *spa,
+                                                  float *spb, int lane) {
+    const ScanEl ident = scan_ident<MAXP, XOR>();
+    // child
+    float2 moc = make_float2(0.f, 0.f);
+    float xc = 0.f;
+    if (lane == 0) xc = edge_logodds(G, ev, b, m_old, e0 + n, es_base + 2 * (e0 + n - edge_base), sgn, moc);
+    xc = __shfl_sync(0xffffffffu, xc, 0);
+    // forward pass: exclusive prefix (XOR: and the parity of the parents' positive log-odds)
+    ScanEl carry = ident;
+    bool par = false;
+    for (int base = 0; base < n; base += 32) {
+        const int j = base + lane;
+        const bool valid = j < n;
+        float xv = 0.f;
+        ScanEl v = ident;
+        if (valid) {
+            float2 mo;
+            const int e = e0 + j;
+            xv = edge_logodds(G, ev, b, m_old, e, es_base + 2 * (e - edge_base), sgn, mo);
+            v = scan_elem<MAXP, XOR>(xv, (double)T);
+        }
+        if (XOR) par ^= __popc(__ballot_sync(0xffffffffu, valid && xv > 0.f)) & 1;
+        ScanEl inc = v;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const ScanEl y = shfl_up_el<MAXP>(inc, d);
+            if (lane >= d) inc = scan_comb<MAXP, XOR>(y, inc);
+        }
+        ScanEl exc = shfl_up_el<MAXP>(inc, 1);
+        if (lane == 0) exc = ident;
+        if (valid) {
+            const ScanEl pre = scan_comb<MAXP, XOR>(carry, exc);
+            sx[j] = xv;
+            spa[j] = pre.a;
+            spb[j] = pre.b;
+        }
+        carry = scan_comb<MAXP, XOR>(carry, shfl_el(inc, 31));
+    }
+    __syncwarp();
+    const bool pos_all = par ^ (xc > 0.f);  // XOR: parity of all members' positive log-odds
+    float out_c;
+    if (XOR) out_c = MAXP ? xor_out_max(carry.a, par) : xor_out_soft(el_d(carry), par, (double)T);
+    else if (MAXP) out_c = carry.a + (carry.b < 0.f ? carry.b : 0.f);
+    else out_c = (float)((double)T * log_expm1_from_log_d(el_d(carry)));
+    // backward pass: exclusive suffix, outputs
+    ScanEl sc = XOR ? scan_elem<MAXP, XOR>(xc, (double)T) : ident;
+    for (int base = n > 0 ? ((n - 1) & ~31) : -32; base >= 0; base -= 32) {
+        const int j = base + lane;
+        const bool valid = j < n;
+        const float xv = valid ? sx[j] : 0.f;
+        const ScanEl v = valid ? scan_elem<MAXP, XOR>(xv, (double)T) : ident;
+        ScanEl inc = v;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const ScanEl y = shfl_down_el<MAXP>(inc, d);
+            if (lane + d < 32) inc = scan_comb<MAXP, XOR>(inc, y);
+        }
+        ScanEl exc = shfl_down_el<MAXP>(inc, 1);
+        if (lane == 31) exc = ident;
+        if (valid) {
+            const ScanEl suf = scan_comb<MAXP, XOR>(exc, sc);
+            const ScanEl loo = scan_comb<MAXP, XOR>(ScanEl{spa[j], spb[j]}, suf);
+            float o;
+            if (XOR) {
+                const bool odd = pos_all ^ (xv > 0.f);
+                o = MAXP ? xor_out_max(loo.a, odd) : xor_out_soft(el_d(loo), odd, (double)T);
+            } else {
+                o = MAXP ? or_parent_max(loo.a, loo.b, xc) : or_parent_soft(el_d(loo), xc, (double)T);
+            }
+            const int e = e0 + j;
+            const int es = es_base + 2 * (e - edge_base);
+            write_logic_edge(sgn * o, ld2(m_old + es), m_new, es, damping, G.flags);
+        }
+        sc = scan_comb<MAXP, XOR>(sc, shfl_el(inc, 0));
+    }
+    if (lane == 0) {
+        const int e = e0 + n;
+        write_logic_edge(sgn * out_c, moc, m_new, es_base + 2 * (e - edge_base), damping, G.flags);
+    }
 }
 
 // Warp per factor, any fan-in. Leave-one-out sums as exclusive prefix (first pass) and
@@ -2580,75 +2797,14 @@ k_logic_warp(DevGraph G, const LogicSeg *__restrict__ segs, int n_seg, const flo
     const int p0 = __ldg(po + f), n = __ldg(po + f + 1) - p0;
     const int edge_base = __ldg(&S->edge_base), es_base = __ldg(&S->es_base);
     const int e0 = edge_base + p0 + f;
-    const float sgn = __ldg(&S->kind) == 1 ? -1.f : 1.f;
-    const ScanEl ident = scan_ident<MAXP>();
-    // child
-    float2 moc = make_float2(0.f, 0.f);
-    float xc = 0.f;
-    if (lane == 0) xc = edge_logodds(G, ev, b, m_old, e0 + n, es_base + 2 * (e0 + n - edge_base), sgn, moc);
-    xc = __shfl_sync(0xffffffffu, xc, 0);
-    // forward pass: exclusive prefix
-    ScanEl carry = ident;
-    for (int base = 0; base < n; base += 32) {
-        const int j = base + lane;
-        const bool valid = j < n;
-        float xv = 0.f;
-        ScanEl v = ident;
-        if (valid) {
-            float2 mo;
-            const int e = e0 + j;
-            xv = edge_logodds(G, ev, b, m_old, e, es_base + 2 * (e - edge_base), sgn, mo);
-            v = scan_elem<MAXP>(xv, (double)T);
-        }
-        ScanEl inc = v;
-#pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-            const ScanEl y = shfl_up_el<MAXP>(inc, d);
-            if (lane >= d) inc = scan_comb<MAXP>(y, inc);
-        }
-        ScanEl exc = shfl_up_el<MAXP>(inc, 1);
-        if (lane == 0) exc = ident;
-        if (valid) {
-            const ScanEl pre = scan_comb<MAXP>(carry, exc);
-            sx[j] = xv;
-            spa[j] = pre.a;
-            spb[j] = pre.b;
-        }
-        carry = scan_comb<MAXP>(carry, shfl_el(inc, 31));
-    }
-    __syncwarp();
-    float out_c;
-    if (MAXP) out_c = carry.a + (carry.b < 0.f ? carry.b : 0.f);
-    else out_c = (float)((double)T * log_expm1_from_log_d(el_d(carry)));
-    // backward pass: exclusive suffix, outputs
-    ScanEl sc = ident;
-    for (int base = n > 0 ? ((n - 1) & ~31) : -32; base >= 0; base -= 32) {
-        const int j = base + lane;
-        const bool valid = j < n;
-        const float xv = valid ? sx[j] : 0.f;
-        const ScanEl v = valid ? scan_elem<MAXP>(xv, (double)T) : ident;
-        ScanEl inc = v;
-#pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-            const ScanEl y = shfl_down_el<MAXP>(inc, d);
-            if (lane + d < 32) inc = scan_comb<MAXP>(inc, y);
-        }
-        ScanEl exc = shfl_down_el<MAXP>(inc, 1);
-        if (lane == 31) exc = ident;
-        if (valid) {
-            const ScanEl suf = scan_comb<MAXP>(exc, sc);
-            const ScanEl loo = scan_comb<MAXP>(ScanEl{spa[j], spb[j]}, suf);
-            const float o = MAXP ? or_parent_max(loo.a, loo.b, xc) : or_parent_soft(el_d(loo), xc, (double)T);
-            const int e = e0 + j;
-            const int es = es_base + 2 * (e - edge_base);
-            write_logic_edge(sgn * o, ld2(m_old + es), m_new, es, damping, G.flags);
-        }
-        sc = scan_comb<MAXP>(sc, shfl_el(inc, 0));
-    }
-    if (lane == 0) {
-        const int e = e0 + n;
-        write_logic_edge(sgn * out_c, moc, m_new, es_base + 2 * (e - edge_base), damping, G.flags);
-    }
+    const int kind = __ldg(&S->kind);
+    const float sgn = kind == PGM_LOGIC_AND ? -1.f : 1.f;
+    if (kind == PGM_LOGIC_XOR)  // uniform over the block (one group per block)
+        logic_warp_factor<MAXP, true>(G, b, ev, m_old, m_new, T, damping, e0, n, edge_base, es_base, sgn, sx, spa,
+                                      spb, lane);
+    else
+        logic_warp_factor<MAXP, false>(G, b, ev, m_old, m_new, T, damping, e0, n, edge_base, es_base, sgn, sx, spa,
+                                       spb, lane);
 }
 
 // =====================================================================================

@@ -117,9 +117,11 @@ struct DevGraph {
     const int32_t *frozen;   // [n_members] batches: nonzero = the factor pass skips the
                              // member (per-member early exit; zero outside such runs);
                              // null for single graphs and until first needed
-    float *b_lo;             // [VS] for variables of the warp pass (K > 16): what the
-                             // iteration's beliefs b lost to rounding (b + b_lo is the
-                             // float-float value); null if there are none
+    float *b_lo;             // [VS] graphs with variables of the warp pass (K > 16) or
+                             // logical factors: what the iteration's beliefs b lost to
+                             // rounding (b + b_lo is the float-float value), written for
+                             // every warp-pass variable and for every other variable with
+                             // an incoming entry beyond kExactThreshold; else null
     const int32_t *lr_pos;   // [E] Plan::lr graphs: each edge's slot in the log-ratio
                              // arrays (k V + v with vin_tab4, else its CSR index); else null
     const float *mem_prm;    // [4 n_members] batch runs with parameters per member: each
@@ -210,6 +212,10 @@ struct HostLayout {
     std::vector<int32_t> vin_tab4;  // [4 * V] (see DevGraph::vin_tab4), empty if unused
     std::vector<HostMember> members;
 };
+
+// Graphs that keep belief residuals (DevGraph::b_lo): those with variables of the warp
+// pass (K > 16) and those with logical factors.
+inline bool keeps_b_lo(const HostLayout &H) { return !H.var_bucket[kVarWarp].empty() || !H.logic_groups.empty(); }
 
 // Compiles n_desc graph descriptions (const pgm_graph_desc*) into one graph whose flat
 // arrays hold the members one after the other. Returns "" on success, else an error.

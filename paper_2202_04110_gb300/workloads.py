@@ -62,7 +62,7 @@ class EnumGroup:
 
 @dataclass
 class LogicGroup:
-    kind: int  # OR or AND
+    kind: int  # OR, AND or XOR
     par_off: np.ndarray  # int32 [n_fac + 1]
     parents: np.ndarray  # int32 [par_off[-1]]
     child: np.ndarray  # int32 [n_fac]

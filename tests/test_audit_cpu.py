@@ -24,7 +24,8 @@ def lib():
 
 
 def _graphs():
-    g_rand, _, _ = W.random_graph(3, n_vars=30, max_K=4, n_pair=40, n_triple=5, n_or=4, n_and=4, sparse=True)
+    g_rand, _, _ = W.random_graph(3, n_vars=30, max_K=4, n_pair=40, n_triple=5, n_or=4, n_and=4, n_xor=4,
+                                  sparse=True)
     return {"ising": W.ising_grid(7, 9, 0).graph, "potts": W.potts_grid(6, 8, 1).graph,
             "rbm": W.rbm(70, 80, 2).graph, "deconv": W.deconvolution(3, n_img=1).graph,
             "random": g_rand, "pool": W.pool_grid(5, 2, 1, 4).graph,
@@ -111,3 +112,15 @@ def test_bad_requests_are_rejected(lib):
         lib.audit_desc(fg, VIN_ES, 10 ** 9, 0)
     with pytest.raises(lib.PgmError):
         lib.audit_desc(fg, 99, 0, 0)
+
+
+def test_logical_kinds(lib):
+    """OR, AND and XOR groups compile; any other kind is rejected by the host compiler."""
+    g, _, _ = W.random_graph(3, n_vars=30, max_K=2, n_pair=10, n_triple=0, n_or=2, n_and=2, n_xor=2)
+    assert sorted(lg.kind for lg in g.logic_groups) == [W.OR, W.AND, W.XOR]
+    assert lib.audit_desc(g) == (-1, -1)
+    bad = W.FactorGraph(g.num_states, g.enum_groups,
+                        [W.LogicGroup(3, lg.par_off, lg.parents, lg.child) for lg in g.logic_groups])
+    with pytest.raises(lib.PgmError) as ei:
+        lib.audit_desc(bad)
+    assert ei.value.status == -1 and "kind" in str(ei.value)

@@ -85,10 +85,12 @@ def _hard_grid(rows, cols, seed, scale):
 @pytest.mark.parametrize("scale", [1.0, 300.0])
 def test_noalloc_hard_evidence_and_large_messages(gpu, T, scale):
     """-inf evidence on a fifth of the cells; with scale 300 the messages exceed 128, the
-    recompute branch of the factor kernel. Against pgm_run_bp and the oracle, twice. At
+    recompute branch of the factor kernel. Against the oracle and pgm_run_bp, twice. At
     scale 300 the raw beliefs reach 2,500, and a normalised log-belief b - LSE(b) formed
     from them in FP32 is exact only to their ulp (2.4e-4 at 2,500), so there the tolerance
-    is 1e-4 plus two FP32 ulps of the raw belief rather than of the normalised value."""
+    is 1e-4 plus two FP32 ulps of the raw belief rather than of the normalised value. Each
+    CUDA path is held to that bound against the oracle; the two paths round in different
+    orders, so against each other they are held to the sum of their two bounds."""
     import torch
     rows, cols, n_iters = 29, 31, 20
     p = _hard_grid(rows, cols, 11, scale)
@@ -100,22 +102,24 @@ def test_noalloc_hard_evidence_and_large_messages(gpu, T, scale):
     fin = np.isfinite(braw)
     rtol_raw = np.where(fin, 2.0 ** -21 * np.abs(np.where(fin, braw, 0.0)), 0.0)
 
-    def close(a, ref, what):
+    fin_o = np.isfinite(onb)
+    tol_o = 1e-4 + 2.0 ** -22 * np.abs(np.where(fin_o, onb, 0.0)) + rtol_raw
+
+    def close(a, ref, tol, what):
         a = np.asarray(a, np.float64)
         assert (np.isneginf(a) == np.isneginf(ref)).all(), what
         f = np.isfinite(ref)
         err = np.abs(a[f] - ref[f])
-        tol = 1e-4 + 2.0 ** -22 * np.abs(ref[f]) + rtol_raw[f]
-        assert (err <= tol).all(), f"{what}: max excess {np.max(err - tol):.3e}"
+        assert (err <= tol[f]).all(), f"{what}: max excess {np.max(err - tol[f]):.3e}"
 
+    close(nb_ref, onb, tol_o, "pgm_run_bp vs oracle")
     for call in range(2):
         m = torch.zeros_like(m_ref)
         gpu.grid2_run_bp_noalloc(rows, cols, lp, ev, T, 0.5, n_iters, m)
         nb = g.beliefs(ev, m, True).cpu().numpy()
-        close(nb, np.asarray(nb_ref, np.float64), f"noalloc vs pgm_run_bp, call {call}")
-        close(nb, onb, f"noalloc vs oracle, call {call}")
+        close(nb, onb, tol_o, f"noalloc vs oracle, call {call}")
+        close(nb, np.asarray(nb_ref, np.float64), 2.0 * tol_o, f"noalloc vs pgm_run_bp, call {call}")
         assert gpu.grid2_noalloc_flags(clear=True) == (ofl & oracle.FLAG_CONTRADICTION), call
-    close(nb_ref, onb, "pgm_run_bp vs oracle")
 
 
 def test_noalloc_contradiction_flag(gpu):
