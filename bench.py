@@ -302,6 +302,7 @@ def measure_batched(args, binding, W, torch, dev):
     t_single = timed(run_singles, 2)
     upd = ES * iters
     launches = [dict(zip(("kind", "variant", "threads", "blocks"), x)) for x in gb.launches()]
+    kernels = batched_kernel_rooflines(gb, members, lp, ev, iters)
     # f4 inside the batch: each member stops once its own residual is <= 1e-4 (checked
     # every 10 iterations, at most `iters`), the stopped members' factors are skipped
     out_ee = {}
@@ -346,7 +347,56 @@ def measure_batched(args, binding, W, torch, dev):
             "batched": upd / t_batched, "per_graph": upd / t_single, "unit": UNIT,
             "batched_ms_per_run": 1e3 * t_batched, "per_graph_ms_per_run": 1e3 * t_single,
             "speedup": t_single / t_batched, "autotune_s": round(tune_s, 2), "launch_shapes": launches,
+            "kernels": kernels,
+            "kernel_timing": "CUDA events around each launch of every 10th iteration of one batched run (event "
+                             "nodes in its CUDA graph); an event pair includes the launch's latency",
             **out_ee}
+
+
+# factor-pass variants of the dense K-state pairwise groups -> (K, kernel name)
+PAIR_VARIANTS = {0: (2, "k_pair<2>"), 1: (4, "k_pair_group<4>"), 2: (8, "k_pair_group<8>"),
+                 3: (16, "k_pair_group<16>"), 7: (4, "k_pair_thr<4>"), 8: (8, "k_pair_thr<8>"),
+                 9: (16, "k_pair_thr<16>"), 11: (8, "k_pair_quad<8>"), 12: (16, "k_pair_quad<16>"),
+                 13: (4, "k_pair_dir<4>"), 14: (8, "k_pair_dir<8>"), 15: (16, "k_pair_dir<16>")}
+
+
+def batched_kernel_rooflines(gb, members, lp, ev, iters):
+    """Per-launch CUDA-event times of one batched run and, for the dense pairwise factor
+    launches, their algorithmic bytes and fraction of the HBM peak. A K-state pairwise
+    factor moves 4 (2K old-message reads + 2K new-message writes + 2K belief gathers + 2
+    edge indices) = 24 K + 8 bytes, plus its K^2 table when the table is its own."""
+    import torch
+    peak, _ = measured_peaks()
+    fac_bytes = {}  # K -> bytes of all pairwise factors with K states
+    for m in members:
+        for grp in m.graph.enum_groups:
+            if grp.arity != 2:
+                continue
+            K = int(m.graph.num_states[grp.vars[0, 0]]) if grp.vars.shape[0] else 0
+            n = int(grp.vars.shape[0])
+            fac_bytes[K] = fac_bytes.get(K, 0) + n * (24 * K + 8) + (0 if grp.shared else 4 * n * K * K)
+    period = 10
+    gb.set_profiling(period)
+    mb = gb.new_msgs()
+    gb.run_bp(lp, ev, 1.0, 0.5, iters, mb)
+    torch.cuda.synchronize()
+    lt = gb.launch_times()
+    gb.set_profiling(0)
+    out = []
+    for (kind, variant, threads, blocks), (ms, cnt) in zip(gb.launches(), lt):
+        if cnt == 0:
+            continue
+        us = 1e3 * ms / cnt
+        d = {"kind": "factor" if kind == 1 else "variable", "variant": variant, "threads": threads,
+             "blocks": blocks, "mean_launch_us": round(us, 2)}
+        if kind == 1 and variant in PAIR_VARIANTS and PAIR_VARIANTS[variant][0] in fac_bytes:
+            K, name = PAIR_VARIANTS[variant]
+            d["kernel"] = name
+            d["algorithmic_bytes_per_launch"] = fac_bytes[K]
+            d["achieved_gbs"] = round(fac_bytes[K] / (us * 1e-6) / 1e9, 1)
+            d["frac"] = round(fac_bytes[K] / (us * 1e-6) / 1e9 / peak, 4)
+        out.append(d)
+    return out
 
 
 def measure_multi(args, binding, W, torch, dev):

@@ -492,10 +492,10 @@ pgm_status pgm_run_bp_until_members(pgm_graph *g, const float *log_pot, const fl
  * PGM_OPT_PAIR_FORM (default 0): the kernel form of dense K-state pairwise groups (K = 4,
  * 8, 16). 0 the compiler's choice (a thread per factor), 1 a thread per factor, 2 K
  * lanes per factor, 3 K / 4 lanes per factor with four states each (K = 8, 16, for
- * launches whose groups all share their tables; else a thread per factor). The thread
- * and K / 4-lane forms give the same bits.
+ * launches whose groups all share their tables; else a thread per factor), 4 a thread per
+ * factor and direction. The thread, K / 4-lane and direction forms give the same bits.
  * Blocking like PGM_OPT_ENUM_BLOCK; pgm_autotune may change the forms afterwards.
- * Values outside 0..3: PGM_EINVAL.
+ * Values outside 0..4: PGM_EINVAL.
  */
 #define PGM_OPT_PAIR_FORM 4
 /*
@@ -546,12 +546,13 @@ pgm_status pgm_autotune(pgm_graph *g, const float *log_pot, const float *evidenc
  * thread per binary variable, 3..5 K = 4, 8, 16 lanes per variable, 6 padded 4-edge
  * table, 7 warp per variable with K > 16),
  * kind 1 = factor pass (variant: 0 dense pairwise K = 2; 1..3 dense pairwise K = 4, 8,
- * 16 with K lanes per factor; 4 listed configurations; 5 OR/AND thread per factor; 6
- * OR/AND warp per factor; 7..9 dense pairwise K = 4, 8, 16 with a thread per factor,
- * the default form for K = 4 and per-factor tables, which pgm_autotune may exchange with
- * 1..3 or 11, 12; 10 listed configurations with a block per run of factors; 11, 12 dense
- * pairwise K = 8, 16 with K / 4 lanes per factor, for shared tables); threads per block
- * and blocks. Any output pointer may be NULL.
+ * 16 with K lanes per factor; 4 listed configurations; 5 logical (OR / AND / XOR) thread
+ * per factor; 6 logical warp per factor; 7..9 dense pairwise K = 4, 8, 16 with a thread
+ * per factor, the default form, which pgm_autotune may exchange with 1..3, 11, 12 or
+ * 13..15; 10 listed configurations with a block per run of factors; 11, 12 dense
+ * pairwise K = 8, 16 with K / 4 lanes per factor, for shared tables; 13..15 dense
+ * pairwise K = 4, 8, 16 with a thread per factor and direction); threads per block and
+ * blocks. Any output pointer may be NULL.
  */
 pgm_status pgm_launch_info(const pgm_graph *g, int32_t i, int32_t *kind, int32_t *variant,
                            int32_t *threads, int32_t *n_blocks);

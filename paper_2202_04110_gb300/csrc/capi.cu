@@ -218,6 +218,7 @@ int lanes_per_factor(int variant) {
         case kPair16: return 16;
         case kPairQ8: return 2;
         case kPairQ16: return 4;
+        case kPairD4: case kPairD8: case kPairD16: return 2;  // a thread per direction
         case kLogicWarp: return 32;
         default: return 1;
     }
@@ -1725,11 +1726,13 @@ pgm_status pgm_run_bp(pgm_graph *g, const float *log_pot, const float *evidence,
 // tables shared by the group, K / 4 lanes per factor (kPairQ8 / 16).
 static std::vector<int> alternative_forms(int base_variant, bool all_shared) {
     switch (base_variant) {
-        case kPair4: case kPairT4: return {kPairT4, kPair4};
-        case kPair8: case kPairT8: case kPairQ8:
-            return all_shared ? std::vector<int>{kPairT8, kPairQ8, kPair8} : std::vector<int>{kPairT8, kPair8};
-        case kPair16: case kPairT16: case kPairQ16:
-            return all_shared ? std::vector<int>{kPairT16, kPairQ16, kPair16} : std::vector<int>{kPairT16, kPair16};
+        case kPair4: case kPairT4: case kPairD4: return {kPairT4, kPairD4, kPair4};
+        case kPair8: case kPairT8: case kPairQ8: case kPairD8:
+            return all_shared ? std::vector<int>{kPairT8, kPairD8, kPairQ8, kPair8}
+                              : std::vector<int>{kPairT8, kPairD8, kPair8};
+        case kPair16: case kPairT16: case kPairQ16: case kPairD16:
+            return all_shared ? std::vector<int>{kPairT16, kPairD16, kPairQ16, kPair16}
+                              : std::vector<int>{kPairT16, kPairD16, kPair16};
         case kEnumGeneric: case kEnumBlock: return {kEnumGeneric, kEnumBlock};  // the former where every group fits
         default: return {base_variant};
     }
@@ -1742,6 +1745,7 @@ static std::vector<int> shape_candidates(int variant) {
         case kPairT4: case kPairT8: return {64, 128, 256};
         case kPairT16: return {64, 128};
         case kPairQ8: case kPairQ16: return {64, 128, 256};
+        case kPairD4: case kPairD8: case kPairD16: return {64, 128, 256};  // warp pairs
         case kEnumGeneric: return {32, 64, 128};
         case kEnumBlock: return {128, 256};
         case kLogicWarp: return {32, 64, 128};
@@ -2113,7 +2117,7 @@ pgm_status pgm_set_option(pgm_graph *g, int32_t option, int64_t value) {
             g->checked = (int32_t)value;
             return PGM_OK;
         case PGM_OPT_PAIR_FORM: {
-            if (value < 0 || value > 3) return fail(PGM_EINVAL, "PGM_OPT_PAIR_FORM must be 0..3");
+            if (value < 0 || value > 4) return fail(PGM_EINVAL, "PGM_OPT_PAIR_FORM must be 0..4");
             DeviceGuard dg(g->device);
             cudaError_t e = cudaDeviceSynchronize();  // a replay may be reading the segments
             if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceSynchronize");
@@ -2122,19 +2126,20 @@ pgm_status pgm_set_option(pgm_graph *g, int32_t option, int64_t value) {
                 FactorLaunch &L = g->P.factor[li];
                 const int base = L.base_variant;
                 int K = 0;
-                if (base == kPairT4 || base == kPair4) K = 4;
-                else if (base == kPairT8 || base == kPairQ8 || base == kPair8) K = 8;
-                else if (base == kPairT16 || base == kPairQ16 || base == kPair16) K = 16;
+                if (base == kPairT4 || base == kPair4 || base == kPairD4) K = 4;
+                else if (base == kPairT8 || base == kPairQ8 || base == kPair8 || base == kPairD8) K = 8;
+                else if (base == kPairT16 || base == kPairQ16 || base == kPair16 || base == kPairD16) K = 16;
                 if (K == 0) continue;
                 const int thr = K == 4 ? kPairT4 : K == 8 ? kPairT8 : kPairT16;
                 const int lanes = K == 4 ? kPair4 : K == 8 ? kPair8 : kPair16;
                 const int quad = K == 8 ? kPairQ8 : K == 16 ? kPairQ16 : thr;
+                const int dir = K == 4 ? kPairD4 : K == 8 ? kPairD8 : kPairD16;
                 // the K / 4-lane form runs launches whose groups all share their tables
                 bool all_shared = true;
                 const EnumSeg *sg = reinterpret_cast<const EnumSeg *>(g->factor_segs_host[li].data());
                 for (int i = 0; i < L.n_seg; ++i) all_shared = all_shared && sg[i].shared != 0;
                 const int want = value == 0 ? base : value == 1 ? thr : value == 2 ? lanes
-                                                   : (all_shared ? quad : thr);
+                                 : value == 3 ? (all_shared ? quad : thr) : dir;
                 if (L.variant == want) continue;
                 const int old_variant = L.variant;
                 L.variant = want;

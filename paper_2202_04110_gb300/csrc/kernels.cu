@@ -1723,6 +1723,82 @@ k_pair_thr(DevGraph G, const EnumSeg *__restrict__ segs, int n_seg, const float 
     store_n<K>(m_new + es1, o);
 }
 
+// ---- K-state pairwise tables, a thread per factor and direction ------------------------
+//
+// The two directions of a pairwise factor are independent given the stored messages: the
+// message to variable 0 needs only v1 = b1 - m1 and the old m0 (for damping), the message
+// to variable 1 only v0 and m1. Here a pair of warps takes 32 factors, the even warp the
+// direction to variable 0 and the odd one the direction to variable 1, so a thread holds
+// one input vector, one output and one old message (3K values instead of the thread
+// form's 4K plus a second output) and twice as many factors are in flight per SM at the
+// same arithmetic per factor. Each thread runs the thread form's direction code on the
+// same inputs, so both forms give the same bits; a factor with a rare case (an edge of a
+// high-degree variable, a stored entry that is -inf or large) is finished whole by the
+// even warp's thread through pair_factor_rare, as in the thread form.
+template <int K, bool MAXP, bool MS = false>
+__global__ void __launch_bounds__(256, K >= 16 ? 3 : 5)
+k_pair_dir(DevGraph G, const EnumSeg *__restrict__ segs, int n_seg, const float *__restrict__ pot,
+           const float *__restrict__ b, const float *__restrict__ ev, const float *__restrict__ m_old,
+           float *__restrict__ m_new, float T, float invT, float damping) {
+    if constexpr (MS) {  // multi-sample launches: this block's sample
+        const int64_t smp = sample_select(G);
+        pot += smp * G.s_pot;
+        b += smp * G.s_vs;
+        ev += smp * G.s_vs;
+        m_old += smp * G.s_es;
+        m_new += smp * G.s_es;
+    }
+    __shared__ float tab[K * K];
+    __shared__ __align__(16) float tabE[MAXP ? 4 : K * K];
+    __shared__ __align__(16) float tabET[MAXP ? 4 : K * K];
+    __shared__ float tinfo[2];
+    const EnumSeg *S = segs + find_seg(segs, n_seg, blockIdx.x);
+    if (member_skip<MAXP>(G, S->member, T, invT, damping)) return;  // the whole block
+    const int n_fac = __ldg(&S->n_fac), shared = __ldg(&S->shared), pot_base = __ldg(&S->pot_base);
+    bool linear = false;
+    if (shared) {  // uniform over the block (a block lies in one segment)
+        for (int i = threadIdx.x; i < K * K; i += blockDim.x) tab[i] = __ldg(pot + pot_base + i);
+        __syncthreads();
+        linear = prepare_linear_table<K, MAXP>(tab, tabE, tinfo, invT);
+        if (linear) {
+            for (int i = threadIdx.x; i < K * K; i += blockDim.x) tabET[(i % K) * K + i / K] = tabE[i];
+            __syncthreads();
+        }
+    }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, d = warp & 1;  // d: warp-uniform
+    const int f = (blockIdx.x - __ldg(&S->block_begin)) * (blockDim.x >> 1) + (warp >> 1) * 32 + lane;
+    if (f >= n_fac) return;
+    const int e = __ldg(&S->edge_base) + 2 * f;
+    const int es0 = __ldg(&S->es_base) + 2 * K * f, es1 = es0 + K;
+    const int vs0 = __ldg(G.edge_vs + e), vs1 = __ldg(G.edge_vs + e + 1);
+    const float *phi = shared ? tab : pot + pot_base + (size_t)f * (K * K);
+    // this thread's output edge (target) and input edge (source)
+    const int es_t = d ? es1 : es0, es_s = d ? es0 : es1, vs_s = d ? vs0 : vs1;
+    float mo_t[K], v[K];
+    load_n<K>(mo_t, m_old + es_t);
+    load_n<K>(v, m_old + es_s);
+    bool rare = (vs0 < 0) | (vs1 < 0);
+#pragma unroll
+    for (int x = 0; x < K; ++x) rare |= needs_exact(mo_t[x]) | needs_exact(v[x]);
+    if (rare) {  // both warps see the same rare flag; the even one finishes the factor
+        if (d == 0)
+            pair_factor_rare<K, MAXP>(G, shared ? tab : nullptr, pot + pot_base + (size_t)f * (K * K), b, ev, m_old,
+                                      m_new, vs0, vs1, es0, es1, T, invT, damping);
+        return;
+    }
+    const float tmax = linear ? tinfo[0] : 0.f;
+    float bs[K], o[K];
+    load_n<K>(bs, b + vs_s);
+#pragma unroll
+    for (int y = 0; y < K; ++y) v[y] = bs[y] - v[y];
+    if (d == 0)  // to variable 0: rows of phi against v1
+        pair_dir_thr<K, MAXP, false>(v, o, linear, tabE, phi, shared, tmax, T, invT);
+    else  // to variable 1: columns of phi against v0
+        pair_dir_thr<K, MAXP, true>(v, o, linear, tabET, phi, shared, tmax, T, invT);
+    finish_k<K>(o, mo_t, damping, G.flags);
+    store_n<K>(m_new + es_t, o);
+}
+
 // ---- K / 4 lanes per factor, four consecutive states each (K = 8, 16, shared tables) ----
 //
 // The factor's L = K / 4 lanes form an aligned group of a warp: lane q loads the states
@@ -4155,6 +4231,15 @@ static void factor_pass_t(const DevGraph &G, const Plan &P, const float *pot, co
                 break;
             case kPairT16:
                 k_pair_thr<16, MAXP, MS><<<dim3(L.n_blocks, S), L.threads, 0, s>>>(G, es, L.n_seg, pot, b, ev, m_old, m_new, T, invT, damping);
+                break;
+            case kPairD4:
+                k_pair_dir<4, MAXP, MS><<<dim3(L.n_blocks, S), L.threads, 0, s>>>(G, es, L.n_seg, pot, b, ev, m_old, m_new, T, invT, damping);
+                break;
+            case kPairD8:
+                k_pair_dir<8, MAXP, MS><<<dim3(L.n_blocks, S), L.threads, 0, s>>>(G, es, L.n_seg, pot, b, ev, m_old, m_new, T, invT, damping);
+                break;
+            case kPairD16:
+                k_pair_dir<16, MAXP, MS><<<dim3(L.n_blocks, S), L.threads, 0, s>>>(G, es, L.n_seg, pot, b, ev, m_old, m_new, T, invT, damping);
                 break;
             case kPairQ8:
                 k_pair_quad<8, MAXP, MS><<<dim3(L.n_blocks, S), L.threads, 0, s>>>(G, es, L.n_seg, pot, b, ev, m_old, m_new, T, invT, damping);

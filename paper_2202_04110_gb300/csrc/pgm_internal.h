@@ -48,7 +48,10 @@ enum FactorVariant : int32_t {
                        // a list longer than kEnumGenericMaxCfg: a block per run of factors
     kPairQ8 = 11,      // dense pairwise table shared by the group, K = 8, 16: K / 4 lanes per
     kPairQ16 = 12,     // factor, four states each (an alternative the autotuner may pick)
-    kNumFactorVariants = 13
+    kPairD4 = 13,      // dense pairwise table, K = 4, 8, 16: a thread per factor and
+    kPairD8 = 14,      // direction (a warp pair per 32 factors; an alternative the autotuner
+    kPairD16 = 15,     // may pick)
+    kNumFactorVariants = 16
 };
 
 // One enumeration group as seen by a launch. Edges of factor f are

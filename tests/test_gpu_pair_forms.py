@@ -1,10 +1,10 @@
 """Dense K-state pairwise factors (Potts, Sec. 5.2's enumeration factors over full
 tables): the kernel forms of the factor pass give the same results.
 
-The K / 4-lane form (four states per lane, for tables shared by a group; an
-alternative the autotuner may pick) and the thread-per-factor form (the default) run
-the same arithmetic in the same order, so their
-messages are bitwise equal: with the linear-domain form of a shared table (range within
+The K / 4-lane form (four states per lane, for tables shared by a group), the
+direction form (a thread per factor and direction) -- alternatives the autotuner may
+pick -- and the thread-per-factor form (the default) run the same arithmetic in the same
+order, so their messages are bitwise equal: with the linear-domain form of a shared table (range within
 60 T), with the exact form (a table range above 60 T), at T = 0, with hard evidence (the
 rare path), in batches whose members start at any offset, and for many samples at once.
 Both are held to the FP64 oracle as well.
@@ -124,3 +124,57 @@ def test_quad_multi_sample(gpu, T):
     for s in range(S):
         _, m1 = _run_form(gpu, p.graph, p.log_pot, ev[s], T, 10, 0)
         assert np.array_equal(mq[s], m1), s
+
+
+def _per_factor_tables(p, seed):
+    """The Potts grid with its own table per factor: the shared table plus N(0, 0.3)."""
+    rng = np.random.default_rng(seed)
+    g0 = p.graph.enum_groups[0]
+    n_fac = g0.vars.shape[0]
+    lp = (np.tile(p.log_pot, n_fac) + rng.normal(0, 0.3, n_fac * p.log_pot.size)).astype(np.float32)
+    graph = W.FactorGraph(p.graph.num_states, [W.EnumGroup(g0.cfg, g0.vars, False)], [])
+    return graph, lp
+
+
+@pytest.mark.parametrize("K", [4, 8, 16])
+@pytest.mark.parametrize("T", [1.0, 0.0, 0.4])
+@pytest.mark.parametrize("case", ["plain", "wide_table", "hard", "per_factor"])
+def test_direction_form_equals_thread_form(gpu, K, T, case):
+    """A thread per factor and direction (form 4) against the thread form: bitwise, on
+    shared tables (linear and exact forms), hard evidence (the rare path, finished by the
+    even warp) and per-factor tables; and the oracle at 1e-4 on the plain case."""
+    side = 37
+    w = 40.0 if case == "wide_table" else None
+    p = W.potts_grid(side, K, seed=K + 7, T=T, n_iters=15, w=w)
+    if case == "hard":
+        p = _hard(p, 0.1, 6)
+    graph, lp = (p.graph, p.log_pot) if case != "per_factor" else _per_factor_tables(p, K)
+    g_d, m_d = _run_form(gpu, graph, lp, p.evidence, T, 15, 4)
+    assert g_d.launches()[-1][1] == {4: 13, 8: 14, 16: 15}[K]
+    _, m_t = _run_form(gpu, graph, lp, p.evidence, T, 15, 1)
+    assert np.array_equal(m_d, m_t, equal_nan=True), f"max diff {np.nanmax(np.abs(m_d - m_t))}"
+    if case == "plain":
+        import torch
+        evt = torch.as_tensor(p.evidence).cuda()
+        nb = g_d.beliefs(evt, torch.as_tensor(m_d).cuda(), True).cpu().numpy()
+        om, _ = oracle.run_bp(graph, lp, p.evidence, T, 0.5, 15)
+        _, onb, _, _ = oracle.beliefs(graph, p.evidence, om)
+        assert_beliefs_close(nb, onb, what=f"direction form K={K} T={T}")
+
+
+def test_direction_form_batch_and_samples(gpu):
+    """The direction form in a batch whose members start at any offset, and for many
+    samples at once: bitwise equal to the thread form."""
+    ms = [W.potts_grid(13, 2, 1, T=1.0), W.potts_grid(17, 16, 2, T=1.0), W.potts_grid(11, 4, 3, T=1.0),
+          W.potts_grid(9, 8, 4, T=1.0), W.ising_grid(3, 5, 5, T=1.0), W.potts_grid(21, 16, 6, T=1.0)]
+    batch = W.union(ms)
+    graphs = [p.graph for p in ms]
+    _, m_d = _run_form(gpu, graphs, batch.log_pot, batch.evidence, 1.0, 12, 4)
+    _, m_t = _run_form(gpu, graphs, batch.log_pot, batch.evidence, 1.0, 12, 1)
+    assert np.array_equal(m_d, m_t)
+    p = W.potts_grid(29, 8, 9, T=0.0, n_iters=10)
+    rng = np.random.default_rng(4)
+    ev = (p.evidence[None, :] + rng.standard_normal((4, p.evidence.size))).astype(np.float32)
+    _, md = _run_form(gpu, p.graph, p.log_pot, ev, 0.0, 10, 4, samples=4)
+    _, mt = _run_form(gpu, p.graph, p.log_pot, ev, 0.0, 10, 1, samples=4)
+    assert np.array_equal(md, mt)
