@@ -63,6 +63,8 @@ def parse_args():
                     help="only run the batched workload for N iterations (3 runs, no CUDA graphs; for ncu)")
     ap.add_argument("--deconv-probe", type=int, default=0,
                     help="only run the deconvolution workload for N iterations (3 runs, no CUDA graphs; for ncu)")
+    ap.add_argument("--grad-probe", type=int, default=0,
+                    help="run only N gradient calls of the gradient workload, CUDA graphs off (for ncu)")
     ap.add_argument("--pair-form", type=int, default=0,
                     help="with --batch-probe: the dense K-state pairwise kernel form (PGM_OPT_PAIR_FORM)")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
@@ -649,16 +651,19 @@ def measure_deconv(args, binding, W, torch, dev):
         np.add.at(deg, lg_.parents, 1)
         np.add.at(deg, lg_.child, 1)
     hi = deg > 64
-    # implementation bytes per launch (two-pass design): block variable pass reads K d
-    # messages and writes 2 K d float-float leave-one-out values; a logical factor reads
-    # its old messages, the beliefs of its edges and their index, and writes its messages
+    # implementation bytes per launch: the tile sums read the high-degree variables' K d
+    # messages and their incoming-edge index; the second launch reads the tile totals
+    # (16 bytes per tile and state) and writes each state's totals (16 bytes) and belief;
+    # a logical factor reads its old messages, the beliefs of its edges (the totals of a
+    # high-degree variable) and their index, and writes its messages
     n_hi_es = int((ks[hi] * deg[hi]).sum())
     and_g, or_g = fg.logic_groups[0], fg.logic_groups[1]
     e_and = int(and_g.par_off[-1]) + and_g.n_fac
     e_or = int(or_g.par_off[-1]) + or_g.n_fac
     d_hi = int(deg[hi].sum())
+    n_tiles_st = int((ks[hi] * ((deg[hi] + 2047) // 2048)).sum())
     impl = {"k_var_hd_sum": 4 * n_hi_es + 4 * d_hi,  # messages and incoming-edge index
-            "k_var_hd_out": 12 * n_hi_es + 4 * d_hi + 8 * int(ks[hi].sum()),  # + float-float leave-one-out values
+            "k_var_hd_out": 16 * n_tiles_st + 20 * int(ks[hi].sum()),
             "k_logic_small": 4 * (4 * e_and + 2 * e_and + e_and),
             "k_logic_warp": 4 * (4 * e_or + 2 * e_or + e_or)}
     s8d = {"k_logic_small": sec8d_bytes(fg, [0]), "k_logic_warp": sec8d_bytes(fg, [1]),
@@ -1140,8 +1145,17 @@ def batch_probe(args):
         m.zero_()
         g.run_bp(lp, ev, 1.0, 0.5, args.batch_probe, m)
     torch.cuda.synchronize()
+    # per-launch CUDA-event times of a fourth run (every iteration sampled)
+    g.set_profiling(1)
+    m.zero_()
+    g.run_bp(lp, ev, 1.0, 0.5, args.batch_probe, m)
+    torch.cuda.synchronize()
+    lt = g.launch_times()
+    g.set_profiling(0)
+    times = [round(1e3 * ms / cnt, 2) if cnt else None for ms, cnt in lt]
     print(json.dumps({"batch_probe": args.batch_probe, "pair_form": args.pair_form,
-                      "launches_per_iter": g.info["launches_per_iter"], "launch_shapes": g.launches()}))
+                      "launches_per_iter": g.info["launches_per_iter"], "launch_shapes": g.launches(),
+                      "mean_launch_us": times}))
 
 
 def deconv_probe(args):
@@ -1163,6 +1177,28 @@ def deconv_probe(args):
     torch.cuda.synchronize()
     print(json.dumps({"deconv_probe": args.deconv_probe, "launches_per_iter": g.info["launches_per_iter"],
                       "launch_shapes": g.launches()}))
+
+
+def grad_probe(args):
+    """`--grad-probe N` gradient calls of the gradient workload (64x64 Ising, T=1, damping
+    0.5, 100 iterations, a checkpoint every 10), CUDA graphs off, for an ncu launch list of
+    the reverse pass. Prints one JSON line with the launches per call."""
+    import numpy as np
+    import torch
+    from paper_2202_04110_gb300 import binding, build
+    from paper_2202_04110_gb300 import workloads as W
+    build.build()
+    p = W.ising_grid(64, 64, 0, T=1.0, n_iters=100)
+    g = binding.Graph(p.graph)
+    g.set_option(binding.OPT_CUDA_GRAPH, 0)
+    lp = torch.as_tensor(p.log_pot).cuda()
+    ev = torch.as_tensor(p.evidence).cuda()
+    gnb = torch.as_tensor(np.random.default_rng(1).standard_normal(p.graph.n_var_states).astype(np.float32)).cuda()
+    for _ in range(args.grad_probe):
+        g.grad(lp, ev, 1.0, 0.5, 100, 10, gnb)
+    torch.cuda.synchronize()
+    print(json.dumps({"grad_probe": args.grad_probe, "workload": "ising64x64, T=1, damping 0.5, 100 iterations, "
+                      "checkpoint every 10", "launches_per_iter": g.info["launches_per_iter"]}))
 
 
 def pool_probe(args):
@@ -1196,6 +1232,8 @@ def main():
         deconv_probe(args)
     elif args.batch_probe:
         batch_probe(args)
+    elif args.grad_probe:
+        grad_probe(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

@@ -24,7 +24,7 @@ enum AuditArrayId : int32_t {
     kAuditVsOff = 0,      // vs_off [V+1]: 0..VS
     kAuditVinOff = 1,     // vin_off [V+1]: 0..E
     kAuditVinEs = 2,      // vin_es [E]: 0..ES-1
-    kAuditEdgeVs = 3,     // edge_vs [E]: -1 or 0..VS-1
+    kAuditEdgeVs = 3,     // edge_vs [E]: 0..VS-1, with the sign bit set for high-degree variables
     kAuditEdgeVar = 4,    // edge_var [E]: 0..V-1
     kAuditTab4 = 5,       // vin_tab4 [4V]: -1 or 0..ES-1
     kAuditLrPos = 6,      // lr_pos [E]: 0..slots-1
@@ -37,7 +37,9 @@ enum AuditArrayId : int32_t {
     kAuditNumArrays = 13
 };
 
-// One flat int32 array and its entries' range [lo, hi) (allow_neg: -1 also valid).
+// One flat int32 array and its entries' range [lo, hi). allow_neg: 0 nothing else; 1 -1
+// also valid (padding); 2 an entry with the sign bit set also valid when its other bits
+// are in range (the marked edges of high-degree variables).
 struct AuditArray {
     const int32_t *p;
     int64_t n;
@@ -55,7 +57,13 @@ struct AuditSizes {
 };
 
 __host__ __device__ __forceinline__ bool audit_entry_ok(int64_t x, const AuditArray &a) {
-    return (a.allow_neg && x == -1) || (x >= a.lo && x < a.hi);
+    if (x >= a.lo && x < a.hi) return true;
+    if (a.allow_neg == 1) return x == -1;
+    if (a.allow_neg == 2 && x < 0) {
+        const int64_t y = x & 0x7fffffff;
+        return y >= a.lo && y < a.hi;
+    }
+    return false;
 }
 
 // A group's lists by output state: es_per_fac + 1 offsets padded to a multiple of four

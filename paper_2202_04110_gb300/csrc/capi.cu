@@ -130,7 +130,7 @@ struct pgm_graph {
     std::vector<HostMember> members;
     FactorLaunch adj_launch{};      // pgm_grad: enumeration groups of state sum <= 64, thread per factor
     int32_t adj_nc_max = 0;         // largest list of those groups with a shared table (0: none)
-    int64_t hd_tot_entries = 0;     // float2 tile sums of the high-degree variables
+    int64_t hd_tot_entries = 0;     // float4 tile totals of the high-degree variables
     size_t tiles_off = 0;           // their tile list in the index memory
     size_t adj_seg_off = (size_t)-1;
     FactorLaunch adj_block_launch{};  // pgm_grad: the larger groups, block form (k_adj_block)
@@ -508,13 +508,13 @@ std::vector<AuditArray> device_audit_arrays(const pgm_graph *g) {
     const DevGraph &G = g->G;
     const int64_t V = G.V, VS = G.VS, E = G.E, ES = G.ES;
     std::vector<AuditArray> a;
-    auto add = [&](const int32_t *p, int64_t n, int64_t lo, int64_t hi, bool neg, int id) {
-        if (p && n > 0) a.push_back(AuditArray{p, n, lo, hi, neg ? 1 : 0, id});
+    auto add = [&](const int32_t *p, int64_t n, int64_t lo, int64_t hi, int neg, int id) {
+        if (p && n > 0) a.push_back(AuditArray{p, n, lo, hi, neg, id});
     };
     add(G.vs_off, V + 1, 0, VS + 1, false, kAuditVsOff);
     add(G.vin_off, V + 1, 0, E + 1, false, kAuditVinOff);
     add(G.vin_es, E, 0, ES, false, kAuditVinEs);
-    add(G.edge_vs, E, 0, VS, true, kAuditEdgeVs);
+    add(G.edge_vs, E, 0, VS, 2, kAuditEdgeVs);
     add(G.edge_var, E, 0, V, false, kAuditEdgeVar);
     add(reinterpret_cast<const int32_t *>(G.vin_tab4), 4 * V, 0, ES, true, kAuditTab4);
     add(G.lr_pos, E, 0, g->lr_slots, false, kAuditLrPos);
@@ -678,11 +678,11 @@ static pgm_status build_from_layout(const HostLayout &H, pgm_graph **out, cudaSt
     g->index_mem = dmem;
     size_t es_bytes = align_up(std::max<int64_t>(H.ES, 1) * sizeof(float), 256);
     size_t vs_bytes = align_up(std::max<int64_t>(H.VS, 1) * sizeof(float), 256);
-    size_t hd_bytes = H.var_bucket[kVarBlock].empty() ? 0 : 2 * es_bytes;
+    size_t hd_bytes = H.var_bucket[kVarBlock].empty() ? 0 : 4 * vs_bytes;
     const size_t lr_bytes = g->P.lr ? align_up((size_t)g->lr_slots * sizeof(float), 256) : 0;
     const size_t prm_bytes = g->P.lr ? align_up((size_t)3 * (H.E / 2) * sizeof(float), 256) : 0;
     const size_t blo_bytes = keeps_b_lo(H) ? vs_bytes : 0;
-    const size_t tot_bytes = align_up((size_t)g->hd_tot_entries * sizeof(float2), 256);
+    const size_t tot_bytes = align_up((size_t)g->hd_tot_entries * sizeof(float4), 256);
     const size_t scratch_bytes = es_bytes + vs_bytes + 256 + hd_bytes + 2 * lr_bytes + prm_bytes + blo_bytes + tot_bytes;
     char *smem = nullptr;
     ce = ordered ? cudaMallocAsync(&smem, scratch_bytes, s) : cudaMalloc(&smem, scratch_bytes);
@@ -716,12 +716,12 @@ static pgm_status build_from_layout(const HostLayout &H, pgm_graph **out, cudaSt
     G.edge_var = H.edge_var.empty() ? nullptr : reinterpret_cast<const int32_t *>(dmem + o_ev);
     G.vin_tab4 = H.vin_tab4.empty() ? nullptr : reinterpret_cast<const int4 *>(dmem + o_tab4);
     G.flags = flags;
-    G.v2f_hd = hd_bytes ? reinterpret_cast<float *>(smem + es_bytes + vs_bytes + 256) : nullptr;
+    G.hd_b = hd_bytes ? reinterpret_cast<float *>(smem + es_bytes + vs_bytes + 256) : nullptr;
     G.lr_pos = g->P.lr ? reinterpret_cast<const int32_t *>(dmem + o_lr_pos) : nullptr;
     G.b_lo = blo_bytes ? reinterpret_cast<float *>(smem + es_bytes + vs_bytes + 256 + hd_bytes + 2 * lr_bytes +
                                                     prm_bytes)
                        : nullptr;
-    G.hd_tot = tot_bytes ? reinterpret_cast<float2 *>(smem + es_bytes + vs_bytes + 256 + hd_bytes + 2 * lr_bytes +
+    G.hd_tot = tot_bytes ? reinterpret_cast<float4 *>(smem + es_bytes + vs_bytes + 256 + hd_bytes + 2 * lr_bytes +
                                                       prm_bytes + blo_bytes)
                          : nullptr;
     if (g->P.lr) {
@@ -807,8 +807,8 @@ int64_t pgm::layout_device_bytes(const HostLayout &H) {
         tot += nt * (H.vs_off[v + 1] - H.vs_off[v]);
     }
     idx += (size_t)n_tiles * sizeof(int4);
-    return (int64_t)(idx + es_bytes + vs_bytes + 256 + (H.var_bucket[kVarBlock].empty() ? 0 : 2 * es_bytes) +
-                     (keeps_b_lo(H) ? vs_bytes : 0) + align_up((size_t)tot * sizeof(float2), 256));
+    return (int64_t)(idx + es_bytes + vs_bytes + 256 + (H.var_bucket[kVarBlock].empty() ? 0 : 4 * vs_bytes) +
+                     (keeps_b_lo(H) ? vs_bytes : 0) + align_up((size_t)tot * sizeof(float4), 256));
 }
 
 pgm_status pgm::build_layout_on_stream(const HostLayout &H, cudaStream_t s, pgm_graph **out) {
@@ -1122,7 +1122,7 @@ static pgm_status run_multi_es(pgm_graph *g, int32_t n_samples, const float *log
                                const float *evidence, float T, float damping, int32_t n_iters, float *msgs,
                                void *stream) {
     const int64_t VS = g->info.n_var_states, ES = g->info.n_edge_states, P = g->info.n_potentials;
-    const int64_t hd = g->G.v2f_hd ? 2 * ES : 0, blo = g->G.b_lo ? VS : 0;
+    const int64_t hd = g->G.hd_b ? 4 * VS : 0, blo = g->G.b_lo ? VS : 0;
     const int64_t per = 4 * (ES + VS + hd + blo);
     const int64_t chunk = std::min<int64_t>({(int64_t)n_samples, 65535, std::max<int64_t>(1, ((int64_t)1 << 30) / per)});
     if (chunk <= 1) {
@@ -1151,7 +1151,7 @@ static pgm_status run_multi_es(pgm_graph *g, int32_t n_samples, const float *log
         Gs.s_es = ES;
         Gs.s_vs = VS;
         Gs.s_pot = pot_per_sample ? P : 0;
-        Gs.v2f_hd = hd ? reinterpret_cast<float *>(g->mse_mem + r_mt + r_b) : nullptr;
+        Gs.hd_b = hd ? reinterpret_cast<float *>(g->mse_mem + r_mt + r_b) : nullptr;
         Gs.b_lo = blo ? reinterpret_cast<float *>(g->mse_mem + r_mt + r_b + r_hd) : nullptr;
         const float *lp = log_pot + (pot_per_sample ? (size_t)s0 * P : 0);
         const float *ev = evidence + (size_t)s0 * VS;
@@ -2374,13 +2374,13 @@ pgm_status pgm_audit_desc(const pgm_graph_desc *desc, int32_t corrupt_array, int
         if (st != PGM_OK) return st;
     }
     std::vector<AuditArray> flat;
-    auto add = [&](const int32_t *p, int64_t n, int64_t lo, int64_t hi, bool neg, int id) {
-        if (n > 0) flat.push_back(AuditArray{p, n, lo, hi, neg ? 1 : 0, id});
+    auto add = [&](const int32_t *p, int64_t n, int64_t lo, int64_t hi, int neg, int id) {
+        if (n > 0) flat.push_back(AuditArray{p, n, lo, hi, neg, id});
     };
     add(H.vs_off.data(), H.V + 1, 0, H.VS + 1, false, kAuditVsOff);
     add(H.vin_off.data(), H.V + 1, 0, H.E + 1, false, kAuditVinOff);
     add(H.vin_es.data(), (int64_t)H.vin_es.size(), 0, H.ES, false, kAuditVinEs);
-    add(H.edge_vs.data(), (int64_t)H.edge_vs.size(), 0, H.VS, true, kAuditEdgeVs);
+    add(H.edge_vs.data(), (int64_t)H.edge_vs.size(), 0, H.VS, 2, kAuditEdgeVs);
     add(H.edge_var.data(), (int64_t)H.edge_var.size(), 0, H.V, false, kAuditEdgeVar);
     add(H.vin_tab4.data(), (int64_t)H.vin_tab4.size(), 0, H.ES, true, kAuditTab4);
     add(lr.data(), (int64_t)lr.size(), 0, lr_slot_count(H), false, kAuditLrPos);

@@ -312,7 +312,7 @@ std::string compile_graph(const void *const *vdescs, int n_desc, HostLayout *L) 
     for (int64_t i = 0; i < E; ++i) L->vin_es[fill[edge_var[i]]++] = edge_es[i];
 
     // ---- degree buckets; edges of high-degree variables take their variable-to-factor
-    // values from the exact leave-one-out buffer (edge_vs = -1 marks them)
+    // values from their variable's totals (the sign bit of edge_vs marks them)
     if ((int64_t)maxdeg > (int64_t)kVarMaxTiles * kVarTile)
         return fmt("a variable has %lld factors; at most %lld are supported", maxdeg, (long long)kVarMaxTiles * kVarTile);
     for (int kk = 0; kk < kNumVarKinds; ++kk) L->var_bucket[kk].clear();
@@ -341,7 +341,10 @@ std::string compile_graph(const void *const *vdescs, int n_desc, HostLayout *L) 
     for (int kk = 0; kk < kNumVarKinds; ++kk) L->var_bucket_identity[kk] = ((int64_t)L->var_bucket[kk].size() == V);
     for (int64_t i = 0; i < E; ++i) {
         int32_t v = edge_var[i];
-        if (L->vin_off[v + 1] - L->vin_off[v] > kVarBlockDegree) L->edge_vs[i] = -1;
+        // high-degree variables: the sign bit marks the edge (its variable's first state
+        // stays in the other bits, where the factor finds the variable's totals)
+        if (L->vin_off[v + 1] - L->vin_off[v] > kVarBlockDegree)
+            L->edge_vs[i] = (int32_t)((uint32_t)L->vs_off[v] | 0x80000000u);
     }
 
     // each edge's variable, for the block-per-factor kernel's explicit sums

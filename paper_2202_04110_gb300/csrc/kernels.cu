@@ -224,11 +224,26 @@ __device__ __noinline__ void v2f_slow_edge(const DevGraph G, const float *__rest
 
 __device__ __forceinline__ bool needs_exact(float mv) { return !(fabsf(mv) <= kExactThreshold); }
 
-// Exact leave-one-out values of a high-degree variable's edge, stored as float-float
-// (hi, lo) pairs in G.v2f_hd, shifted so that the edge's largest state is 0 (factor
-// updates are invariant to a per-edge constant) and rounded once to FP32.
-__device__ __forceinline__ float2 hd_pair(const DevGraph &G, int es, int x) {
-    return __ldg(reinterpret_cast<const float2 *>(G.v2f_hd) + es + x);
+// High-degree variables (more than kVarBlockDegree factors; their edges carry edge_vs
+// with the sign bit set, the variable's first state in the other bits): the variable pass
+// keeps, per state, the float-float sum of the finite evidence and incoming entries and
+// the count of the -inf ones (G.hd_b, float4 (hi, lo, count, 0)). An edge's exact
+// leave-one-out value is that sum less the edge's own entry -- -inf when another entry
+// or the evidence is -inf -- formed in float-float from the four numbers and the entry,
+// so that the pass writes nothing per edge. Returned as a (hi, lo) pair.
+__device__ __forceinline__ float2 hd_pair(const DevGraph &G, int vs, int x, float mo) {
+    const float4 t = __ldg(reinterpret_cast<const float4 *>(G.hd_b) + (vs & 0x7fffffff) + x);
+    const bool own = (mo == -CUDART_INF_F);
+    if (t.z > (own ? 1.f : 0.f)) return make_float2(-CUDART_INF_F, 0.f);
+    if (own) return make_float2(t.x, t.y);
+    const float sh = t.x - mo;
+    if (!isfinite(sh)) return make_float2(sh, 0.f);
+    // two-sum of the high parts, then the low part, renormalised
+    const float bb = sh - t.x;
+    const float err = (t.x - (sh - bb)) + (-mo - bb);
+    const float lo = err + t.y;
+    const float hi = sh + lo;
+    return make_float2(hi, lo - (hi - sh));
 }
 
 __device__ __forceinline__ float hd_rel(float2 a, float2 mx) {
@@ -242,13 +257,15 @@ __device__ __forceinline__ bool hd_gt(float2 a, float2 b) {
     return hd_rel(a, b) > 0.f;
 }
 
+// The variable-to-factor values of an edge of a high-degree variable (vs: its edge_vs,
+// mo: the edge's stored entries), relative to the edge's largest state.
 template <int K>
-__device__ __forceinline__ void hd_v2f(const DevGraph &G, int es, float (&v)[K]) {
+__device__ __forceinline__ void hd_v2f(const DevGraph &G, int vs, const float (&mo)[K], float (&v)[K]) {
     float2 d[K];
     int arg = 0;
 #pragma unroll
     for (int x = 0; x < K; ++x) {
-        d[x] = hd_pair(G, es, x);
+        d[x] = hd_pair(G, vs, x, mo[x]);
         if (x > 0 && hd_gt(d[x], d[arg])) arg = x;
     }
     float2 mx = d[0];
@@ -265,14 +282,14 @@ __device__ __forceinline__ void hd_v2f(const DevGraph &G, int es, float (&v)[K])
 }
 
 // Variable-to-factor values of one K-state edge. Edges of high-degree variables
-// (edge_vs < 0) read the exact leave-one-out sums the block variable pass wrote to
-// G.v2f_hd; all others use b - m, or the explicit sum when an entry needs it.
+// (edge_vs < 0) take the exact leave-one-out values from the variable's totals (hd_pair);
+// all others use b - m, or the explicit sum when an entry needs it.
 template <int K>
 __device__ __forceinline__ void gather_v2f(const DevGraph &G, const float *__restrict__ b,
                                            const float *__restrict__ ev, const float *__restrict__ m_old,
                                            int vs, int es, const float (&mo)[K], float (&v)[K]) {
     if (vs < 0) {
-        hd_v2f<K>(G, es, v);
+        hd_v2f<K>(G, vs, mo, v);
         return;
     }
     bool exact = false;
@@ -462,7 +479,7 @@ __device__ __forceinline__ float lse_row(const float (&z)[K], float T, float inv
 __device__ __forceinline__ int64_t sample_select(DevGraph &G) {
     const int64_t smp = blockIdx.y;
     if (smp != 0) {
-        if (G.v2f_hd) G.v2f_hd += smp * 2 * G.s_es;
+        if (G.hd_b) G.hd_b += smp * 4 * G.s_vs;
         if (G.b_lo) G.b_lo += smp * G.s_vs;
     }
     return smp;
@@ -869,34 +886,6 @@ __global__ void __launch_bounds__(256) k_var_group(DevGraph G, const int32_t *__
     }
 }
 
-// Block-wide exclusive scan (forward or reverse in thread order) of one float-float
-// per thread; `sh` holds >= 64 floats. Sums without subtraction.
-__device__ __forceinline__ FF block_scan_excl(FF v, bool reverse, float *sh) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    FF inc = v;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-        const FF y = reverse ? ff_shfl_down(inc, d) : ff_shfl_up(inc, d);
-        if (reverse ? (lane + d < 32) : (lane >= d)) inc = reverse ? ff_add(inc, y) : ff_add(y, inc);
-    }
-    FF exc = reverse ? ff_shfl_down(inc, 1) : ff_shfl_up(inc, 1);
-    if (reverse ? lane == 31 : lane == 0) exc = ff_make(0.f);
-    const FF wt = reverse ? ff_shfl(inc, 0) : ff_shfl(inc, 31);
-    if (lane == 0) {
-        sh[2 * warp] = wt.hi;
-        sh[2 * warp + 1] = wt.lo;
-    }
-    __syncthreads();
-    FF off = ff_make(0.f);
-    if (reverse) {
-        for (int w = nw - 1; w > warp; --w) off = ff_add(off, FF{sh[2 * w], sh[2 * w + 1]});
-    } else {
-        for (int w = 0; w < warp; ++w) off = ff_add(off, FF{sh[2 * w], sh[2 * w + 1]});
-    }
-    __syncthreads();
-    return reverse ? ff_add(exc, off) : ff_add(off, exc);
-}
-
 __device__ __forceinline__ FF block_sum(FF v, float *sh) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
@@ -947,12 +936,71 @@ __device__ __forceinline__ void var_block_output(const DevGraph &G, const FF *sb
     }
 }
 
-// Block per high-degree variable (more than kVarBlockDegree factors). Incoming
-// messages are processed in tiles of kVarTile edges, kVarItems contiguous edges per
-// thread, with float-float sums in a fixed order (deterministic). In the iteration pass
-// (kVarIter) the block also writes, for every incoming edge-state, the exact
-// leave-one-out sum e_v(x) + sum_{other edges} m(x), as prefix + suffix (no subtraction),
-// to G.v2f_hd as a (hi, lo) pair; the factor kernels read it for these edges.
+// Block-wide float-float sum of v and plain sum of c (a count) in a fixed order; sh holds
+// 3 floats per warp.
+__device__ __forceinline__ FF block_sum_count(FF v, float &c, float *sh) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+        v = ff_add(v, ff_shfl_down(v, d));
+        c += __shfl_down_sync(0xffffffffu, c, d);
+    }
+    if (lane == 0) {
+        sh[3 * warp] = v.hi;
+        sh[3 * warp + 1] = v.lo;
+        sh[3 * warp + 2] = c;
+    }
+    __syncthreads();
+    FF tot = ff_make(0.f);
+    c = 0.f;
+    for (int w = 0; w < nw; ++w) {
+        tot = ff_add(tot, FF{sh[3 * w], sh[3 * w + 1]});
+        c += sh[3 * w + 2];
+    }
+    __syncthreads();
+    return tot;
+}
+
+// One state's share of a tile of a high-degree variable's incoming edges: kVarItems
+// contiguous edges per thread, the finite entries summed in float-float (ascending edge
+// order), the -inf ones counted.
+__device__ __forceinline__ FF hd_tile_part(const DevGraph &G, const float *__restrict__ m, int k0, int deg,
+                                           int tile, int x, float &c) {
+    FF s = ff_make(0.f);
+    c = 0.f;
+    const int base = tile * kVarTile + threadIdx.x * kVarItems;
+#pragma unroll
+    for (int i = 0; i < kVarItems; ++i) {
+        const int k = base + i;
+        if (k < deg) {
+            const float q = __ldg(m + __ldg(G.vin_es + k0 + k) + x);
+            if (q == kNegInf) c += 1.f;
+            else s = ff_add(s, q);
+        }
+    }
+    return s;
+}
+
+// A state's totals from its evidence and its tile totals (added in tile order): the
+// float-float sum of the finite terms and the count of -inf ones; written to G.hd_b in the
+// iteration pass. Returns the belief sum: -inf when a term is -inf (NaN stays NaN).
+template <int MODE, class TileTot>
+__device__ __forceinline__ FF hd_state_total(const DevGraph &G, float e, int n_tiles, TileTot tile, int vs, int x) {
+    FF tot = ff_make(e == kNegInf ? 0.f : e);
+    float c = e == kNegInf ? 1.f : 0.f;
+    for (int t = 0; t < n_tiles; ++t) {
+        const float4 q = tile(t);
+        tot = ff_add(tot, FF{q.x, q.y});
+        c += q.z;
+    }
+    if (MODE == kVarIter && G.hd_b != nullptr)
+        reinterpret_cast<float4 *>(G.hd_b)[vs + x] = make_float4(tot.hi, tot.lo, c, 0.f);
+    return (c > 0.f && tot.hi == tot.hi) ? ff_make(kNegInf) : tot;
+}
+
+// Block per high-degree variable (more than kVarBlockDegree factors): every state's
+// tile totals over tiles of kVarTile edges, then the state's totals (hd_state_total) and
+// the outputs of MODE. The split form below computes the same totals in the same order.
 template <int MODE, bool MS = false>
 __global__ void __launch_bounds__(kVarBlockThreads) k_var_block(DevGraph G, const int32_t *__restrict__ list,
                                                                 const float *__restrict__ ev,
@@ -966,8 +1014,8 @@ __global__ void __launch_bounds__(kVarBlockThreads) k_var_block(DevGraph G, cons
         out += smp * G.s_vs;
         if (dec) dec += smp * G.V;
     }
-    __shared__ float sh[64];
-    __shared__ FF tile_tot[kVarMaxTiles];
+    __shared__ float sh[96];
+    __shared__ float4 tile_tot[kVarMaxTiles];
     __shared__ FF sb[kMaxStates];
     const int v = list ? __ldg(list + blockIdx.x) : (int)blockIdx.x;
     const int vs = __ldg(G.vs_off + v), K = __ldg(G.vs_off + v + 1) - vs;
@@ -976,62 +1024,14 @@ __global__ void __launch_bounds__(kVarBlockThreads) k_var_block(DevGraph G, cons
     const int n_tiles = (deg + kVarTile - 1) / kVarTile;
     for (int x = 0; x < K; ++x) {
         for (int t = 0; t < n_tiles; ++t) {
-            FF s = ff_make(0.f);
-            const int base = t * kVarTile + threadIdx.x * kVarItems;
-#pragma unroll
-            for (int i = 0; i < kVarItems; ++i) {
-                const int k = base + i;
-                if (k < deg) s = ff_add(s, __ldg(m + __ldg(G.vin_es + k0 + k) + x));
-            }
-            const FF tt = block_sum(s, sh);
-            if (threadIdx.x == 0) tile_tot[t] = tt;
+            float c;
+            const FF s = hd_tile_part(G, m, k0, deg, t, x, c);
+            const FF tt = block_sum_count(s, c, sh);
+            if (threadIdx.x == 0) tile_tot[t] = make_float4(tt.hi, tt.lo, c, 0.f);
         }
         __syncthreads();
-        const float e = __ldg(ev + vs + x);
-        if (threadIdx.x == 0) {
-            FF tot = ff_make(e);
-            for (int t = 0; t < n_tiles; ++t) tot = ff_add(tot, tile_tot[t]);
-            sb[x] = tot;
-        }
-        if (MODE == kVarIter && G.v2f_hd != nullptr) {
-            FF carry_pre = ff_make(e);
-            for (int t = 0; t < n_tiles; ++t) {
-                FF carry_suf = ff_make(0.f);
-                for (int u = n_tiles - 1; u > t; --u) carry_suf = ff_add(carry_suf, tile_tot[u]);
-                const int base = t * kVarTile + threadIdx.x * kVarItems;
-                float val[kVarItems];
-                int esk[kVarItems];
-                FF own = ff_make(0.f);
-#pragma unroll
-                for (int i = 0; i < kVarItems; ++i) {
-                    const int k = base + i;
-                    esk[i] = (k < deg) ? __ldg(G.vin_es + k0 + k) : 0;
-                    val[i] = (k < deg) ? __ldg(m + esk[i] + x) : 0.f;
-                    own = ff_add(own, val[i]);
-                }
-                const FF tp = block_scan_excl(own, false, sh);
-                const FF ts = block_scan_excl(own, true, sh);
-                FF suf_local[kVarItems];
-                FF acc = ff_make(0.f);
-#pragma unroll
-                for (int i = kVarItems - 1; i >= 0; --i) {
-                    suf_local[i] = acc;
-                    acc = ff_add(acc, val[i]);
-                }
-                FF pre = ff_add(carry_pre, tp);
-                const FF suf_rest = ff_add(ts, carry_suf);
-#pragma unroll
-                for (int i = 0; i < kVarItems; ++i) {
-                    const int k = base + i;
-                    if (k < deg) {
-                        const FF loo = ff_add(pre, ff_add(suf_local[i], suf_rest));
-                        reinterpret_cast<float2 *>(G.v2f_hd)[esk[i] + x] = make_float2(loo.hi, loo.lo);
-                    }
-                    pre = ff_add(pre, val[i]);
-                }
-                carry_pre = ff_add(carry_pre, tile_tot[t]);
-            }
-        }
+        if (threadIdx.x == 0)
+            sb[x] = hd_state_total<MODE>(G, __ldg(ev + vs + x), n_tiles, [&](int t) { return tile_tot[t]; }, vs, x);
         __syncthreads();
     }
     if (threadIdx.x != 0) return;
@@ -1039,31 +1039,51 @@ __global__ void __launch_bounds__(kVarBlockThreads) k_var_block(DevGraph G, cons
 }
 
 // The high-degree variables split over tiles of kVarTile edges, in two launches, for
-// more blocks than variables: k_var_hd_sum, a block per tile, writes the tile's
-// float-float sum of every state to G.hd_tot; k_var_hd_out, a block per tile, forms the
-// tile's exact leave-one-out values from the tile totals (as prefix + suffix, in
-// k_var_block's order of operations, so the values are the same bits) and, in the
-// variable's first tile, its beliefs or decode. tiles[i] = (position in the variable
-// list, tile, first hd_tot entry of the variable, tiles of the variable); a variable's
-// K totals of tile t are at hd_tot[first + t K .. + K).
+// more blocks than variables: k_var_hd_sum, a block per tile, writes the tile's totals
+// of every state to G.hd_tot (float4: float-float sum of the finite entries, count of
+// -inf ones); k_var_hd_out, launched over the same tiles, finishes each variable in the
+// block of its first tile (a thread per state: hd_state_total, then the outputs), the
+// other blocks returning at once. tiles[i] = (position in the variable list, tile, first
+// hd_tot entry of the variable, tiles of the variable); a variable's K totals of tile t
+// are at hd_tot[first + t K .. + K).
 __global__ void __launch_bounds__(kVarBlockThreads) k_var_hd_sum(DevGraph G, const int32_t *__restrict__ list,
                                                                  const int4 *__restrict__ tiles,
                                                                  const float *__restrict__ m) {
-    __shared__ float sh[64];
+    __shared__ float sh[96];
     const int4 tl = __ldg(tiles + blockIdx.x);
     const int v = list ? __ldg(list + tl.x) : tl.x;
     const int vs = __ldg(G.vs_off + v), K = __ldg(G.vs_off + v + 1) - vs;
     const int k0 = __ldg(G.vin_off + v), deg = __ldg(G.vin_off + v + 1) - k0;
-    for (int x = 0; x < K; ++x) {
-        FF s = ff_make(0.f);
+    if (K == 2) {  // both states in one pass over the tile (the same sums as hd_tile_part)
+        FF s0 = ff_make(0.f), s1 = ff_make(0.f);
+        float c0 = 0.f, c1 = 0.f;
         const int base = tl.y * kVarTile + threadIdx.x * kVarItems;
 #pragma unroll
         for (int i = 0; i < kVarItems; ++i) {
             const int k = base + i;
-            if (k < deg) s = ff_add(s, __ldg(m + __ldg(G.vin_es + k0 + k) + x));
+            if (k < deg) {
+                const int es = __ldg(G.vin_es + k0 + k);
+                const float2 q = (es & 1) ? make_float2(__ldg(m + es), __ldg(m + es + 1))
+                                          : __ldg(reinterpret_cast<const float2 *>(m + es));
+                if (q.x == kNegInf) c0 += 1.f;
+                else s0 = ff_add(s0, q.x);
+                if (q.y == kNegInf) c1 += 1.f;
+                else s1 = ff_add(s1, q.y);
+            }
         }
-        const FF tt = block_sum(s, sh);
-        if (threadIdx.x == 0) G.hd_tot[tl.z + tl.y * K + x] = make_float2(tt.hi, tt.lo);
+        const FF t0 = block_sum_count(s0, c0, sh);
+        const FF t1 = block_sum_count(s1, c1, sh);
+        if (threadIdx.x == 0) {
+            G.hd_tot[tl.z + tl.y * 2] = make_float4(t0.hi, t0.lo, c0, 0.f);
+            G.hd_tot[tl.z + tl.y * 2 + 1] = make_float4(t1.hi, t1.lo, c1, 0.f);
+        }
+        return;
+    }
+    for (int x = 0; x < K; ++x) {
+        float c;
+        const FF s = hd_tile_part(G, m, k0, deg, tl.y, x, c);
+        const FF tt = block_sum_count(s, c, sh);
+        if (threadIdx.x == 0) G.hd_tot[tl.z + tl.y * K + x] = make_float4(tt.hi, tt.lo, c, 0.f);
     }
 }
 
@@ -1071,65 +1091,18 @@ template <int MODE>
 __global__ void __launch_bounds__(kVarBlockThreads) k_var_hd_out(DevGraph G, const int32_t *__restrict__ list,
                                                                  const int4 *__restrict__ tiles,
                                                                  const float *__restrict__ ev,
-                                                                 const float *__restrict__ m,
                                                                  float *__restrict__ out, int32_t *__restrict__ dec) {
-    __shared__ float sh[64];
     __shared__ FF sb[kMaxStates];
     const int4 tl = __ldg(tiles + blockIdx.x);
+    if (tl.y != 0) return;  // one block per variable finishes it
     const int v = list ? __ldg(list + tl.x) : tl.x;
     const int vs = __ldg(G.vs_off + v), K = __ldg(G.vs_off + v + 1) - vs;
-    const int k0 = __ldg(G.vin_off + v), deg = __ldg(G.vin_off + v + 1) - k0;
-    const int t = tl.y, n_tiles = tl.w;
-    auto tot = [&](int u, int x) {
-        const float2 p = __ldcg(G.hd_tot + tl.z + u * K + x);
-        return FF{p.x, p.y};
-    };
-    for (int x = 0; x < K; ++x) {
-        const float e = __ldg(ev + vs + x);
-        if (t == 0 && threadIdx.x == 0) {
-            FF tt = ff_make(e);
-            for (int u = 0; u < n_tiles; ++u) tt = ff_add(tt, tot(u, x));
-            sb[x] = tt;
-        }
-        if (MODE == kVarIter && G.v2f_hd != nullptr) {
-            FF carry_pre = ff_make(e);
-            for (int u = 0; u < t; ++u) carry_pre = ff_add(carry_pre, tot(u, x));
-            FF carry_suf = ff_make(0.f);
-            for (int u = n_tiles - 1; u > t; --u) carry_suf = ff_add(carry_suf, tot(u, x));
-            const int base = t * kVarTile + threadIdx.x * kVarItems;
-            float val[kVarItems];
-            int esk[kVarItems];
-            FF own = ff_make(0.f);
-#pragma unroll
-            for (int i = 0; i < kVarItems; ++i) {
-                const int k = base + i;
-                esk[i] = (k < deg) ? __ldg(G.vin_es + k0 + k) : 0;
-                val[i] = (k < deg) ? __ldg(m + esk[i] + x) : 0.f;
-                own = ff_add(own, val[i]);
-            }
-            const FF tp = block_scan_excl(own, false, sh);
-            const FF ts = block_scan_excl(own, true, sh);
-            FF suf_local[kVarItems];
-            FF acc = ff_make(0.f);
-#pragma unroll
-            for (int i = kVarItems - 1; i >= 0; --i) {
-                suf_local[i] = acc;
-                acc = ff_add(acc, val[i]);
-            }
-            FF pre = ff_add(carry_pre, tp);
-            const FF suf_rest = ff_add(ts, carry_suf);
-#pragma unroll
-            for (int i = 0; i < kVarItems; ++i) {
-                const int k = base + i;
-                if (k < deg) {
-                    const FF loo = ff_add(pre, ff_add(suf_local[i], suf_rest));
-                    reinterpret_cast<float2 *>(G.v2f_hd)[esk[i] + x] = make_float2(loo.hi, loo.lo);
-                }
-                pre = ff_add(pre, val[i]);
-            }
-        }
-    }
-    if (t != 0 || threadIdx.x != 0) return;
+    const int n_tiles = tl.w;
+    for (int x = threadIdx.x; x < K; x += blockDim.x)
+        sb[x] = hd_state_total<MODE>(G, __ldg(ev + vs + x), n_tiles,
+                                     [&](int t) { return __ldcg(G.hd_tot + tl.z + t * K + x); }, vs, x);
+    __syncthreads();
+    if (threadIdx.x != 0) return;
     var_block_output<MODE>(G, sb, K, vs, v, out, dec);
 }
 
@@ -1383,7 +1356,7 @@ template <int K>
 __device__ __noinline__ float group_v2f_rare(const DevGraph G, const float *ev, const float *m_old, int vs,
                                              int es, int x, unsigned gmask) {
     if (vs < 0) {
-        const float2 p = hd_pair(G, es, x);
+        const float2 p = hd_pair(G, vs, x, __ldg(m_old + es + x));
         // the edge's largest state, compared exactly on the pairs
         float2 best = p;
 #pragma unroll
@@ -2071,11 +2044,6 @@ k_enum_generic(DevGraph G, const EnumSeg *__restrict__ segs, int n_seg, const fl
         const int vs = __ldg(G.edge_vs + e_f + j);
         const int es = es_f + Ko[j];
         float2 hmx = make_float2(-CUDART_INF_F, 0.f);
-        if (vs < 0)
-            for (int x = 0; x < Kj[j]; ++x) {
-                const float2 q = hd_pair(G, es, x);
-                if (x == 0 || hd_gt(q, hmx)) hmx = q;
-            }
         bool exact = false;
         const bool lo = G.b_lo != nullptr && Kj[j] > 16;  // a variable of the warp pass
         for (int x = 0; x < Kj[j]; ++x) {
@@ -2083,9 +2051,15 @@ k_enum_generic(DevGraph G, const EnumSeg *__restrict__ segs, int n_seg, const fl
             mo[Ko[j] + x] = mv;
             exact |= lo ? !isfinite(mv) : needs_exact(mv);
         }
+        if (vs < 0)
+            for (int x = 0; x < Kj[j]; ++x) {
+                const float2 q = hd_pair(G, vs, x, mo[Ko[j] + x]);
+                if (x == 0 || hd_gt(q, hmx)) hmx = q;
+            }
         if (vs < 0) {
             for (int x = 0; x < Kj[j]; ++x)
-                v2f[Ko[j] + x] = hmx.x == -CUDART_INF_F ? -CUDART_INF_F : hd_rel(hd_pair(G, es, x), hmx);
+                v2f[Ko[j] + x] =
+                    hmx.x == -CUDART_INF_F ? -CUDART_INF_F : hd_rel(hd_pair(G, vs, x, mo[Ko[j] + x]), hmx);
         } else if (exact) {
             v2f_slow_edge(G, ev, m_old, vs, es, Kj[j], v2f + Ko[j]);
         } else if (lo) {
@@ -2218,7 +2192,7 @@ __device__ __forceinline__ void enum_team_v2f(const DevGraph &G, const float *__
         float2 hmx = make_float2(-CUDART_INF_F, 0.f);
         int hx = K;
         for (int x = lane; x < K; x += 32) {
-            const float2 q = hd_pair(G, es, x);
+            const float2 q = hd_pair(G, vs, x, __ldg(m_old + es + x));
             if (hx == K || hd_gt(q, hmx)) {
                 hmx = q;
                 hx = x;
@@ -2235,7 +2209,7 @@ __device__ __forceinline__ void enum_team_v2f(const DevGraph &G, const float *__
             }
         }
         for (int x = lane; x < K; x += 32)
-            vj[x] = hmx.x == -CUDART_INF_F ? -CUDART_INF_F : hd_rel(hd_pair(G, es, x), hmx);
+            vj[x] = hmx.x == -CUDART_INF_F ? -CUDART_INF_F : hd_rel(hd_pair(G, vs, x, __ldg(m_old + es + x)), hmx);
     }
     team_barrier(wteam);
 }
@@ -2556,7 +2530,8 @@ __device__ __forceinline__ float edge_logodds(const DevGraph &G, const float *ev
     float a0, a1;
     if (vs < 0) {
         float t[2];
-        hd_v2f<2>(G, es, t);
+        const float m2[2] = {mo.x, mo.y};
+        hd_v2f<2>(G, vs, m2, t);
         a0 = t[0];
         a1 = t[1];
     } else if (needs_exact(mo.x) || needs_exact(mo.y)) {
@@ -2972,11 +2947,12 @@ k_adj_factor(DevGraph G, const EnumSeg *__restrict__ segs, int n_seg, const floa
         if (vs < 0) {
             float2 hmx = make_float2(-CUDART_INF_F, 0.f);
             for (int x = 0; x < Kj[j]; ++x) {
-                const float2 q = hd_pair(G, es, x);
+                const float2 q = hd_pair(G, vs, x, m_old[es + x]);
                 if (x == 0 || hd_gt(q, hmx)) hmx = q;
             }
             for (int x = 0; x < Kj[j]; ++x)
-                v2f[Ko[j] + x] = hmx.x == -CUDART_INF_F ? -CUDART_INF_F : hd_rel(hd_pair(G, es, x), hmx);
+                v2f[Ko[j] + x] =
+                    hmx.x == -CUDART_INF_F ? -CUDART_INF_F : hd_rel(hd_pair(G, vs, x, m_old[es + x]), hmx);
         } else if (exact) {
             v2f_slow_edge(G, ev, m_old, vs, es, Kj[j], v2f + Ko[j]);
         } else {
@@ -4164,7 +4140,7 @@ static void var_pass_mode(const DevGraph &G, const Plan &P, const float *ev, con
                 break;
             case kVarBlock:
                 if (!MS && S == 1 && L.tiles != nullptr && G.hd_tot != nullptr)
-                    k_var_hd_out<MODE><<<L.n_tiles, kVarBlockThreads, 0, s>>>(G, L.list, L.tiles, ev, m, out, dec);
+                    k_var_hd_out<MODE><<<L.n_tiles, kVarBlockThreads, 0, s>>>(G, L.list, L.tiles, ev, out, dec);
                 else
                     k_var_block<MODE, MS><<<dim3(L.n, S), kVarBlockThreads, 0, s>>>(G, L.list, ev, m, out, dec);
                 break;

@@ -102,16 +102,19 @@ struct DevGraph {
     const int32_t *vs_off;   // [V + 1]  first state of each variable
     const int32_t *vin_off;  // [V + 1]  CSR: incoming edges of each variable
     const int32_t *vin_es;   // [E]      first edge-state of each incoming edge
-    const int32_t *edge_vs;  // [E]      first variable-state of each edge's variable
+    const int32_t *edge_vs;  // [E]      first variable-state of each edge's variable; for
+                             // a high-degree variable's edges with the sign bit set
     const uint8_t *cfg_pool;
     const int32_t *paroff_pool;
     uint32_t *flags;         // device status word
     const int4 *vin_tab4;    // [V] when every variable is binary with <= 4 factors: the
                              // first edge-states of its incoming edges, ascending, padded
                              // with -1 (else null)
-    float *v2f_hd;           // [2 * ES] exact leave-one-out sums, float-float (hi, lo)
-                             // pairs, for edges of high-degree variables (edge_vs = -1);
-                             // null if there are none
+    float *hd_b;             // [4 * VS] per state of a high-degree variable: the
+                             // float-float sum of its finite evidence and incoming entries
+                             // and the count of -inf ones (hi, lo, count, 0), from which a
+                             // factor forms an edge's exact leave-one-out value; null if
+                             // there are none
     const int32_t *bs_pool;  // configuration lists by output state (EnumSeg::bs_base)
     const int32_t *edge_var; // [E] each edge's variable (graphs with such lists), else null
     int64_t s_es, s_vs, s_pot;  // multi-sample launches (gridDim.y samples): per-sample
@@ -129,7 +132,8 @@ struct DevGraph {
                              // arrays (k V + v with vin_tab4, else its CSR index); else null
     const float *mem_prm;    // [4 n_members] batch runs with parameters per member: each
                              // member's (T, 1 / T, damping, 0); null otherwise
-    float2 *hd_tot;          // tile sums of the high-degree variables' states (float-float),
+    float4 *hd_tot;          // tile totals of the high-degree variables' states (float-float
+                             // sum of the finite entries, count of -inf ones, 0),
                              // VarLaunch::tiles; null if there are none
 };
 

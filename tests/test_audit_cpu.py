@@ -47,8 +47,11 @@ def test_corrupted_flat_arrays_are_found(lib, name):
     fg = _graphs()[name]
     V, VS, E, ES = _sizes(fg)
     rng = np.random.default_rng(len(name))
+    # edge_vs: an edge of a high-degree variable carries its variable's first state with
+    # the sign bit set (-2**31 is state 0 so marked; -1 would be state 2**31 - 1)
     cases = [(VS_OFF, V, VS + 1, VS), (VIN_OFF, V // 2, E + 1, E), (VIN_ES, E - 1, ES, ES - 1),
-             (VIN_ES, 0, -1, 0), (EDGE_VS, E // 3, -2, -1), (EDGE_VS, E - 1, VS, VS - 1)]
+             (VIN_ES, 0, -1, 0), (EDGE_VS, E // 3, -1, -2 ** 31), (EDGE_VS, E - 1, VS, VS - 1),
+             (EDGE_VS, 0, -2 ** 31 + VS, -2 ** 31 + VS - 1)]
     for arr, pos, bad, good in cases:
         pos = int(min(max(pos, 0), (V if arr in (VS_OFF, VIN_OFF) else E - 1)))
         assert lib.audit_desc(fg, arr, pos, bad) == (arr, pos), (name, arr, pos, bad)
