@@ -1924,15 +1924,30 @@ static size_t grad_partials_bytes(const pgm_graph *g) {
     return align_up((size_t)g->adj_launch.n_blocks * (g->adj_launch.threads / 32) * g->adj_nc_max * sizeof(float), 256);
 }
 
+// The variable pass's outputs of one recomputed iteration, kept for its reverse step: the
+// beliefs, and the high-degree totals and belief residuals where the graph has them.
+static size_t grad_step_bytes(const pgm_graph *g) {
+    const size_t vsb = align_up((size_t)std::max<int64_t>(g->info.n_var_states, 1) * sizeof(float), 256);
+    return vsb * (1 + (g->G.hd_b ? 4 : 0) + (g->G.b_lo ? 1 : 0));
+}
+
+// Whether a gradient keeps each recomputed iteration's variable-pass outputs (so that its
+// reverse step launches no variable pass): when one segment's worth fits in 256 MiB.
+static bool grad_keeps_steps(const pgm_graph *g, int32_t n_iters, int32_t ckpt_every) {
+    const int seg_len = std::min(ckpt_every, std::max(n_iters, 1));
+    return (size_t)seg_len * grad_step_bytes(g) <= ((size_t)256 << 20);
+}
+
 // Work buffers of a gradient: checkpoints, one segment of recomputed states, two message
 // buffers, two adjoint buffers, the variable-to-factor adjoint, the damping adjoint, the
-// warp partials of shared-table gradients.
+// warp partials of shared-table gradients, and the kept variable-pass outputs.
 static size_t grad_work_bytes(const pgm_graph *g, int32_t n_iters, int32_t ckpt_every) {
     const int64_t ES = std::max<int64_t>(g->info.n_edge_states, 1);
     const size_t esb = align_up((size_t)ES * sizeof(float), 256);
     const int n_ck = n_iters > 0 ? (n_iters + ckpt_every - 1) / ckpt_every : 0;
     const int seg_len = std::min(ckpt_every, std::max(n_iters, 1));
-    return esb * ((size_t)n_ck + (size_t)seg_len + 6) + grad_partials_bytes(g);
+    return esb * ((size_t)n_ck + (size_t)seg_len + 6) + grad_partials_bytes(g) +
+           (grad_keeps_steps(g, n_iters, ckpt_every) ? (size_t)seg_len * grad_step_bytes(g) : 0);
 }
 
 // Enqueues the whole gradient on s, with its work buffers at mem.
@@ -1950,6 +1965,22 @@ static pgm_status enqueue_grad(pgm_graph *g, const float *log_pot, const float *
     float *partials = g->adj_nc_max > 0 ? buf(n_ck + seg_len + 6) : nullptr;
     auto ckp = [&](int i) { return ck + (size_t)i * (esb / sizeof(float)); };
     auto recp = [&](int i) { return rec + (size_t)i * (esb / sizeof(float)); };
+    // kept variable-pass outputs of the segment's iterations: step i's graph view points its
+    // high-degree totals and belief residuals at the step's own buffers
+    const bool keep = grad_keeps_steps(g, n_iters, ckpt_every);
+    char *steps = mem + esb * ((size_t)n_ck + (size_t)seg_len + 6) + grad_partials_bytes(g);
+    const size_t vsb = align_up((size_t)std::max<int64_t>(g->info.n_var_states, 1) * sizeof(float), 256);
+    auto step_b = [&](int i) { return reinterpret_cast<float *>(steps + (size_t)i * grad_step_bytes(g)); };
+    auto step_G = [&](int i) {
+        DevGraph Gs = g->G;
+        char *p = steps + (size_t)i * grad_step_bytes(g) + vsb;
+        if (Gs.hd_b) {
+            Gs.hd_b = reinterpret_cast<float *>(p);
+            p += 4 * vsb;
+        }
+        if (Gs.b_lo) Gs.b_lo = reinterpret_cast<float *>(p);
+        return Gs;
+    };
     pgm_status st = PGM_OK;
     cudaError_t e = cudaSuccess;
     if (g->info.n_potentials > 0) e = cudaMemsetAsync(d_log_pot, 0, (size_t)g->info.n_potentials * sizeof(float), s);
@@ -1974,20 +2005,35 @@ static pgm_status enqueue_grad(pgm_graph *g, const float *log_pot, const float *
         const int t0 = sgi * ckpt_every, t1 = std::min(t0 + ckpt_every, (int)n_iters);
         e = cudaMemcpyAsync(recp(0), ckp(sgi), esb, cudaMemcpyDeviceToDevice, s);
         if (e != cudaSuccess) st = cuda_fail(e, "recompute copy");
-        for (int i = 1; i < t1 - t0 && st == PGM_OK; ++i)
-            st = one_iteration(g, log_pot, evidence, T, damping, recp(i - 1), recp(i), s);
+        if (keep) {
+            // each recomputed iteration's variable pass writes into its step's buffers,
+            // which its reverse step reads; the segment's last state needs one more pass
+            for (int i = 1; i <= t1 - t0 && st == PGM_OK; ++i) {
+                const DevGraph Gs = step_G(i - 1);
+                e = launch_var_pass(Gs, g->P, evidence, recp(i - 1), step_b(i - 1), kVarIter, nullptr, s);
+                if (e == cudaSuccess && i < t1 - t0)
+                    e = launch_factor_pass(Gs, g->P, log_pot, step_b(i - 1), evidence, recp(i - 1), recp(i), T,
+                                           damping, s);
+                if (e != cudaSuccess) st = cuda_fail(e, "recompute launch");
+            }
+        } else {
+            for (int i = 1; i < t1 - t0 && st == PGM_OK; ++i)
+                st = one_iteration(g, log_pot, evidence, T, damping, recp(i - 1), recp(i), s);
+        }
         for (int t = t1; t > t0 && st == PGM_OK; --t) {
             const float *m_prev = recp(t - 1 - t0);
-            e = launch_var_pass(g->G, g->P, evidence, m_prev, g->b, kVarIter, nullptr, s);
+            const DevGraph Gs = keep ? step_G(t - 1 - t0) : g->G;
+            float *bt = keep ? step_b(t - 1 - t0) : g->b;
+            e = keep ? cudaSuccess : launch_var_pass(Gs, g->P, evidence, m_prev, bt, kVarIter, nullptr, s);
             if (e == cudaSuccess)
-                e = launch_adj_factor(g->G, g->adj_launch, log_pot, g->b, evidence, m_prev, adjA, dv, ddamp,
-                                      d_log_pot, partials, g->adj_nc_max, T, damping, s);
+                e = launch_adj_factor(Gs, g->adj_launch, log_pot, bt, evidence, m_prev, adjA, dv, ddamp, d_log_pot,
+                                      partials, g->adj_nc_max, T, damping, s);
             if (e == cudaSuccess)
-                e = launch_adj_factor(g->G, g->adj_block_launch, log_pot, g->b, evidence, m_prev, adjA, dv, ddamp,
+                e = launch_adj_factor(Gs, g->adj_block_launch, log_pot, bt, evidence, m_prev, adjA, dv, ddamp,
                                       d_log_pot, nullptr, 0, T, damping, s);
             if (e == cudaSuccess)
-                e = launch_adj_logic(g->G, g->adj_logic_launch, g->b, evidence, m_prev, adjA, dv, ddamp, T, damping, s);
-            if (e == cudaSuccess) e = launch_adj_var(g->G, ddamp, dv, adjB, d_evidence, s);
+                e = launch_adj_logic(Gs, g->adj_logic_launch, bt, evidence, m_prev, adjA, dv, ddamp, T, damping, s);
+            if (e == cudaSuccess) e = launch_adj_var(Gs, ddamp, dv, adjB, d_evidence, s);
             if (e != cudaSuccess) st = cuda_fail(e, "adjoint step launch");
             std::swap(adjA, adjB);
         }

@@ -212,6 +212,7 @@ std::string compile_graph(const void *const *vdescs, int n_desc, HostLayout *L) 
             s.packed = 0;
             s.ordered = 0;
             s.member = m;
+            s.dense = (g.n_fac > 0 && is_dense_pair(g, K0, K1)) ? 1 : 0;
             if (g.n_fac > 0 && (hg.variant == kEnumGeneric || hg.variant == kEnumBlock)) {
                 // configuration lists by output state: for neighbour j and state x, the
                 // configurations with state x at j (the block form's gather order)

@@ -2906,6 +2906,141 @@ __global__ void __launch_bounds__(128) k_adj_beliefs(DevGraph G, const float *__
     }
 }
 
+// k_adj_factor for a dense pairwise table (K x K, configuration c = x K + y) with K a
+// compile-time constant, so that every per-state array stays in registers: the same
+// steps, in the same order of operations, as the general loop below (whose arrays of
+// kMaxStateSum entries, indexed at run time, live in local memory).
+template <int K>
+__device__ __forceinline__ void adj_pair_factor(const DevGraph &G, const EnumSeg *S, int f, bool valid,
+                                                const float *__restrict__ pot, const float *__restrict__ b,
+                                                const float *__restrict__ ev, const float *__restrict__ m_old,
+                                                const float *__restrict__ adj, float *__restrict__ dv2f,
+                                                float *__restrict__ ddamp, float *__restrict__ d_pot,
+                                                float *__restrict__ partials, int nc_max, float T, float invT,
+                                                float damping) {
+    const int es0 = S->es_base + f * 2 * K, es1 = es0 + K;
+    const int e0 = S->edge_base + f * 2;
+    float mo0[K], mo1[K], v0[K], v1[K];
+    load_n<K>(mo0, m_old + es0);
+    load_n<K>(mo1, m_old + es1);
+    gather_v2f<K>(G, b, ev, m_old, G.edge_vs[e0], es0, mo0, v0);
+    gather_v2f<K>(G, b, ev, m_old, G.edge_vs[e0 + 1], es1, mo1, v1);
+    const float *phi = pot + S->pot_base + (S->shared ? 0 : (size_t)f * (K * K));
+    // forward values: output 0 at x over y, output 1 at y over x (configurations ascending)
+    float l0[K], s0[K], l1[K], s1[K];
+#pragma unroll
+    for (int i = 0; i < K; ++i) {
+        l0[i] = kNegInf;
+        s0[i] = 0.f;
+        l1[i] = kNegInf;
+        s1[i] = 0.f;
+    }
+    auto acc = [&](float &lm, float &ls, float s) {
+        if (s > lm) {
+            ls = ls * expf((lm - s) * invT) + 1.f;
+            lm = s;
+        } else if (s > kNegInf) {
+            ls += expf((s - lm) * invT);
+        }
+    };
+#pragma unroll
+    for (int x = 0; x < K; ++x)
+#pragma unroll
+        for (int y = 0; y < K; ++y) {
+            const float p = phi[x * K + y];
+            acc(l0[x], s0[x], p + v1[y]);
+            acc(l1[y], s1[y], p + v0[x]);
+        }
+#pragma unroll
+    for (int i = 0; i < K; ++i) {
+        if (l0[i] != kNegInf) l0[i] += T * logf(s0[i]);
+        if (l1[i] != kNegInf) l1[i] += T * logf(s1[i]);
+    }
+    // reverse of normalise - damp - normalise, per edge (gam overwrites s)
+    const float w1 = (damping != 0.f) ? 1.f - damping : 1.f;
+    auto reverse_edge = [&](const float (&lm)[K], const float (&mo)[K], int es, float (&gam)[K]) {
+        int a1 = 0;
+#pragma unroll
+        for (int x = 1; x < K; ++x)
+            if (lm[x] > lm[a1]) a1 = x;
+        float mx = lm[0];
+#pragma unroll
+        for (int x = 1; x < K; ++x)
+            if (x == a1) mx = lm[x];
+        int a2 = 0;
+        float d2 = 0.f, sa = 0.f, ad[K];
+#pragma unroll
+        for (int x = 0; x < K; ++x) {
+            const float n = (mx == kNegInf) ? 0.f : lm[x] - mx;
+            const float d = (damping != 0.f) ? damping * mo[x] + w1 * n : n;
+            if (x == 0 || d > d2) {
+                d2 = d;
+                a2 = x;
+            }
+            ad[x] = adj[es + x];
+            sa += ad[x];
+        }
+        float sn = 0.f;
+#pragma unroll
+        for (int x = 0; x < K; ++x) {
+            const float dd = ad[x] - (x == a2 ? sa : 0.f);
+            if (valid) ddamp[es + x] = damping * dd;
+            gam[x] = w1 * dd;
+            sn += gam[x];
+        }
+#pragma unroll
+        for (int x = 0; x < K; ++x)
+            if (x == a1) gam[x] -= sn;
+    };
+    float g0[K], g1[K];
+    reverse_edge(l0, mo0, es0, g0);
+    reverse_edge(l1, mo1, es1, g1);
+    // back through the log-sum-exp
+    float dv0[K], dv1[K];
+#pragma unroll
+    for (int i = 0; i < K; ++i) {
+        dv0[i] = 0.f;
+        dv1[i] = 0.f;
+    }
+    float *dphi = d_pot + S->pot_base + (S->shared ? 0 : (size_t)f * (K * K));
+    const int gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+    for (int x = 0; x < K; ++x)
+#pragma unroll
+        for (int y = 0; y < K; ++y) {
+            const int c = x * K + y;
+            const float p = phi[c];
+            float dc = 0.f;
+            const float sa = p + v1[y];  // output 0 at x
+            if (sa != kNegInf && l0[x] != kNegInf) {
+                const float w = g0[x] * expf((sa - l0[x]) * invT);
+                dc += w;
+                dv1[y] += w;
+            }
+            const float sb = p + v0[x];  // output 1 at y
+            if (sb != kNegInf && l1[y] != kNegInf) {
+                const float w = g1[y] * expf((sb - l1[y]) * invT);
+                dc += w;
+                dv0[x] += w;
+            }
+            if (S->shared) {  // uniform over the warp
+                float t = valid ? dc : 0.f;
+#pragma unroll
+                for (int d = 16; d > 0; d >>= 1) t += __shfl_down_sync(0xffffffffu, t, d);
+                if (lane == 0) partials[(size_t)gwarp * nc_max + c] = t;
+            } else if (valid) {
+                dphi[c] += dc;
+            }
+        }
+    if (valid) {
+#pragma unroll
+        for (int x = 0; x < K; ++x) {
+            dv2f[es0 + x] = dv0[x];
+            dv2f[es1 + x] = dv1[x];
+        }
+    }
+}
+
 // Factor step in reverse, thread per enumeration factor. From the adjoint a of the new
 // messages: dd = a - sum(a) [x == argmax d] (second normalisation), the damping term
 // delta * dd goes to `ddamp`, dn = (1 - delta) dd, gamma = dn - sum(dn) [x == argmax mt]
@@ -2931,6 +3066,18 @@ k_adj_factor(DevGraph G, const EnumSeg *__restrict__ segs, int n_seg, const floa
     if (__all_sync(0xffffffffu, !valid)) return;
     const int f = valid ? f_raw : S->n_fac - 1;
     const int a = S->arity, nc = S->n_cfg, ksum = S->es_per_fac;
+    if (S->dense) {  // uniform over the block
+        if (S->K[0] == 2) {
+            adj_pair_factor<2>(G, S, f, valid, pot, b, ev, m_old, adj, dv2f, ddamp, d_pot, partials, nc_max, T, invT,
+                               damping);
+            return;
+        }
+        if (S->K[0] == 4) {
+            adj_pair_factor<4>(G, S, f, valid, pot, b, ev, m_old, adj, dv2f, ddamp, d_pot, partials, nc_max, T, invT,
+                               damping);
+            return;
+        }
+    }
     int Kj[kMaxArity], Ko[kMaxArity];
     for (int j = 0; j < a; ++j) {
         Kj[j] = S->K[j];
@@ -3345,6 +3492,39 @@ k_adj_logic(DevGraph G, const LogicSeg *__restrict__ segs, int n_seg, const floa
     }
     dv2f[es_of(n)] = (float)(-sgn * dxc);
     dv2f[es_of(n) + 1] = (float)(sgn * dxc);
+}
+
+// Variable step in reverse for binary graphs with the padded 4-edge table (vin_tab4):
+// the same sums in the same order as k_adj_var below, both states at once (8-byte loads
+// and stores, one table row instead of the CSR offsets and list), so the same bits.
+__global__ void __launch_bounds__(64) k_adj_var_tab4(DevGraph G, const float *__restrict__ ddamp,
+                                                     const float *__restrict__ dv2f, float *__restrict__ adj_prev,
+                                                     float *__restrict__ d_ev) {
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= G.V) return;
+    const int4 t = __ldg(G.vin_tab4 + v);
+    const int es[4] = {t.x, t.y, t.z, t.w};
+    float2 q[4];
+    FF d0 = ff_make(0.f), d1 = ff_make(0.f);
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+        if (es[k] >= 0) {
+            q[k] = *reinterpret_cast<const float2 *>(dv2f + es[k]);
+            d0 = ff_add(d0, q[k].x);
+            d1 = ff_add(d1, q[k].y);
+        }
+    const float a0 = d0.hi + d0.lo, a1 = d1.hi + d1.lo;
+    float2 *de = reinterpret_cast<float2 *>(d_ev) + v;  // binary: states at 2v
+    float2 e = *de;
+    e.x += a0;
+    e.y += a1;
+    *de = e;
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+        if (es[k] >= 0) {
+            const float2 dd = *reinterpret_cast<const float2 *>(ddamp + es[k]);
+            *reinterpret_cast<float2 *>(adj_prev + es[k]) = make_float2(dd.x - q[k].x + a0, dd.y - q[k].y + a1);
+        }
 }
 
 // Variable step in reverse, thread per variable: db(x) = sum over incoming edges of
@@ -4471,7 +4651,8 @@ cudaError_t launch_adj_logic(const DevGraph &G, const FactorLaunch &L, const flo
 
 cudaError_t launch_adj_var(const DevGraph &G, const float *ddamp, const float *dv2f, float *adj_prev, float *d_ev,
                            cudaStream_t s) {
-    k_adj_var<<<(G.V + 127) / 128, 128, 0, s>>>(G, ddamp, dv2f, adj_prev, d_ev);
+    if (G.vin_tab4 != nullptr) k_adj_var_tab4<<<(G.V + 63) / 64, 64, 0, s>>>(G, ddamp, dv2f, adj_prev, d_ev);
+    else k_adj_var<<<(G.V + 127) / 128, 128, 0, s>>>(G, ddamp, dv2f, adj_prev, d_ev);
     return cudaGetLastError();
 }
 

@@ -80,6 +80,7 @@ struct EnumSeg {
     int32_t packed;       // 1: pairwise, list entries (c << 11) | (Koff[other] + state)
     int32_t ordered;      // 1: reduce each output's configurations in ascending order
     int32_t member;       // the batch member the group belongs to
+    int32_t dense;        // 1: a dense pairwise table, K0 = K1, configuration c = x K1 + y
 };
 
 // One logical group as seen by a launch. Factor f owns edges
@@ -88,7 +89,7 @@ struct EnumSeg {
 struct LogicSeg {
     int32_t block_begin;
     int32_t n_fac;
-    int32_t kind;         // 0 OR, 1 AND
+    int32_t kind;         // 0 OR, 1 AND, 2 XOR
     int32_t edge_base;
     int32_t es_base;
     int32_t paroff_base;  // offset of the group's par_off[n_fac + 1] in the pool

@@ -176,7 +176,7 @@ def test_logical_factor_gradient_vs_oracle(gpu, case):
     _close(dev, oev, f"{name} d evidence")
 
 
-@pytest.mark.parametrize("K", [4, 8])
+@pytest.mark.parametrize("K", [2, 4, 8])
 def test_shared_table_gradient_is_deterministic(gpu, K):
     """Potts grids share one table per grid, so every factor adds to the same K^2
     log-potential gradients: they are summed in a fixed order (warp partials added in
@@ -200,3 +200,17 @@ def test_shared_table_gradient_is_deterministic(gpu, K):
     olp, oev = oracle.grad(p.graph, p.log_pot, p.evidence, 1.0, 0.5, 12, g)
     _close(outs[0][0].astype(np.float64), olp, f"Potts K={K} d log_pot")
     _close(outs[0][1].astype(np.float64), oev, f"Potts K={K} d evidence")
+
+
+@pytest.mark.parametrize("T,damping", [(1.0, 0.5), (0.6, 0.0)])
+def test_rbm_high_degree_gradient_vs_oracle(gpu, T, damping):
+    """An RBM whose units all have more than 64 factors (the variable pass keeps per-state
+    totals, the factors form each edge's leave-one-out value from them) and whose 2 x 2
+    tables are the factors' own: the register-resident dense-pairwise adjoint, with every
+    reverse step reading the kept variable-pass outputs of its recomputed iteration."""
+    p = W.rbm(70, 80, seed=4, w_std=0.3, T=T)
+    g = np.random.default_rng(5).standard_normal(p.graph.n_var_states)
+    dlp, dev = _gpu_grad(gpu, p.graph, p.log_pot, p.evidence, T, damping, 7, 3, g)
+    olp, oev = oracle.grad(p.graph, p.log_pot, p.evidence, T, damping, 7, g)
+    _close(dlp, olp, "rbm d log_pot")
+    _close(dev, oev, "rbm d evidence")
