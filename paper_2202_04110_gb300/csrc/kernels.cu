@@ -46,6 +46,14 @@ constexpr uint32_t kFlagNaN = 2u;
 
 #define kNegInf (-CUDART_INF_F)
 
+// Programmatic dependent launch (griddepcontrol): a kernel launched with the
+// programmatic-serialization attribute may be scheduled before the previous kernel of
+// its stream has finished. pdl_wait() returns once that kernel has completed and its
+// writes are visible (at once for a kernel launched without the attribute);
+// pdl_launch_dependents() lets the next kernel be scheduled before this one ends.
+__device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 template <class Seg>
 __device__ __forceinline__ int find_seg(const Seg *__restrict__ segs, int n, int blk) {
     int lo = 0, hi = n - 1;
@@ -494,6 +502,8 @@ __global__ void __launch_bounds__(256) k_var_thread(DevGraph G, const int32_t *_
                                                     const float *__restrict__ m,
                                                     float *__restrict__ out,
                                                     int32_t *__restrict__ dec) {
+    pdl_wait();  // inputs of the previous launch
+    pdl_launch_dependents();  // the next launch may be scheduled (it waits likewise)
     if constexpr (MS) {  // multi-sample launches: this block's sample
         const int64_t smp = sample_select(G);
         ev += smp * G.s_vs;
@@ -510,7 +520,8 @@ __global__ void __launch_bounds__(256) k_var_thread(DevGraph G, const int32_t *_
         const float2 e = __ldg(reinterpret_cast<const float2 *>(ev + vs));
         FF s0 = ff_make(e.x), s1 = ff_make(e.y);
         bool big = false;
-        for (int k = k0; k < k1; ++k) {
+#pragma unroll 4
+        for (int k = k0; k < k1; ++k) {  // (unrolled: the gathers of later edges issue early)
             const int es = __ldg(G.vin_es + k);
             const float2 q = __ldg(reinterpret_cast<const float2 *>(m + es));
             s0 = ff_add(s0, q.x);
@@ -606,6 +617,8 @@ template <int MODE, bool MS = false>
 __global__ void __launch_bounds__(256) k_var_warp(DevGraph G, const int32_t *__restrict__ list, int n,
                                                   const float *__restrict__ ev, const float *__restrict__ m,
                                                   float *__restrict__ out, int32_t *__restrict__ dec) {
+    pdl_wait();  // inputs of the previous launch
+    pdl_launch_dependents();  // the next launch may be scheduled (it waits likewise)
     if constexpr (MS) {  // multi-sample launches: this block's sample
         const int64_t smp = sample_select(G);
         ev += smp * G.s_vs;
@@ -714,6 +727,8 @@ template <int MODE, bool MS = false>
 __global__ void __launch_bounds__(256) k_var_tab4(DevGraph G, int n, const float *__restrict__ ev,
                                                   const float *__restrict__ m, float *__restrict__ out,
                                                   int32_t *__restrict__ dec) {
+    pdl_wait();  // inputs of the previous launch
+    pdl_launch_dependents();  // the next launch may be scheduled (it waits likewise)
     if constexpr (MS) {  // multi-sample launches: this block's sample
         const int64_t smp = sample_select(G);
         ev += smp * G.s_vs;
@@ -802,6 +817,8 @@ template <int K, int MODE, bool MS = false>
 __global__ void __launch_bounds__(256) k_var_group(DevGraph G, const int32_t *__restrict__ list, int n,
                                                    const float *__restrict__ ev, const float *__restrict__ m,
                                                    float *__restrict__ out, int32_t *__restrict__ dec) {
+    pdl_wait();  // inputs of the previous launch
+    pdl_launch_dependents();  // the next launch may be scheduled (it waits likewise)
     if constexpr (MS) {  // multi-sample launches: this block's sample
         const int64_t smp = sample_select(G);
         ev += smp * G.s_vs;
@@ -1007,6 +1024,8 @@ __global__ void __launch_bounds__(kVarBlockThreads) k_var_block(DevGraph G, cons
                                                                 const float *__restrict__ m,
                                                                 float *__restrict__ out,
                                                                 int32_t *__restrict__ dec) {
+    pdl_wait();  // inputs of the previous launch
+    pdl_launch_dependents();  // the next launch may be scheduled (it waits likewise)
     if constexpr (MS) {  // multi-sample launches: this block's sample
         const int64_t smp = sample_select(G);
         ev += smp * G.s_vs;
@@ -1049,6 +1068,8 @@ __global__ void __launch_bounds__(kVarBlockThreads) k_var_block(DevGraph G, cons
 __global__ void __launch_bounds__(kVarBlockThreads) k_var_hd_sum(DevGraph G, const int32_t *__restrict__ list,
                                                                  const int4 *__restrict__ tiles,
                                                                  const float *__restrict__ m) {
+    pdl_wait();  // inputs of the previous launch
+    pdl_launch_dependents();  // the next launch may be scheduled (it waits likewise)
     __shared__ float sh[96];
     const int4 tl = __ldg(tiles + blockIdx.x);
     const int v = list ? __ldg(list + tl.x) : tl.x;
@@ -1092,6 +1113,8 @@ __global__ void __launch_bounds__(kVarBlockThreads) k_var_hd_out(DevGraph G, con
                                                                  const int4 *__restrict__ tiles,
                                                                  const float *__restrict__ ev,
                                                                  float *__restrict__ out, int32_t *__restrict__ dec) {
+    pdl_wait();  // inputs of the previous launch
+    pdl_launch_dependents();  // the next launch may be scheduled (it waits likewise)
     __shared__ FF sb[kMaxStates];
     const int4 tl = __ldg(tiles + blockIdx.x);
     if (tl.y != 0) return;  // one block per variable finishes it
@@ -1261,6 +1284,8 @@ __global__ void __launch_bounds__(K >= 16 ? 128 : 256, K == 2 ? 8 : 1)
 k_pair(DevGraph G, const EnumSeg *__restrict__ segs, int n_seg, const float *__restrict__ pot,
        const float *__restrict__ b, const float *__restrict__ ev, const float *__restrict__ m_old,
        float *__restrict__ m_new, float T, float invT, float damping) {
+    pdl_wait();  // inputs of the previous launch
+    pdl_launch_dependents();  // the next launch may be scheduled (it waits likewise)
     if constexpr (MS) {  // multi-sample launches: this block's sample
         const int64_t smp = sample_select(G);
         pot += smp * G.s_pot;
@@ -1455,6 +1480,8 @@ __global__ void __launch_bounds__(256, 4)
 k_pair_group(DevGraph G, const EnumSeg *__restrict__ segs, int n_seg, int n_vblocks, const float *__restrict__ pot,
              const float *__restrict__ b, const float *__restrict__ ev, const float *__restrict__ m_old,
              float *__restrict__ m_new, float T, float invT, float damping) {
+    pdl_wait();  // inputs of the previous launch
+    pdl_launch_dependents();  // the next launch may be scheduled (it waits likewise)
     if constexpr (MS) {  // multi-sample launches: this block's sample
         const int64_t smp = sample_select(G);
         pot += smp * G.s_pot;
@@ -1636,6 +1663,8 @@ __global__ void __launch_bounds__(K >= 16 ? 128 : 256)
 k_pair_thr(DevGraph G, const EnumSeg *__restrict__ segs, int n_seg, const float *__restrict__ pot,
            const float *__restrict__ b, const float *__restrict__ ev, const float *__restrict__ m_old,
            float *__restrict__ m_new, float T, float invT, float damping) {
+    pdl_wait();  // inputs of the previous launch
+    pdl_launch_dependents();  // the next launch may be scheduled (it waits likewise)
     if constexpr (MS) {  // multi-sample launches: this block's sample
         const int64_t smp = sample_select(G);
         pot += smp * G.s_pot;
@@ -1713,6 +1742,8 @@ __global__ void __launch_bounds__(256, K >= 16 ? 3 : 5)
 k_pair_dir(DevGraph G, const EnumSeg *__restrict__ segs, int n_seg, const float *__restrict__ pot,
            const float *__restrict__ b, const float *__restrict__ ev, const float *__restrict__ m_old,
            float *__restrict__ m_new, float T, float invT, float damping) {
+    pdl_wait();  // inputs of the previous launch
+    pdl_launch_dependents();  // the next launch may be scheduled (it waits likewise)
     if constexpr (MS) {  // multi-sample launches: this block's sample
         const int64_t smp = sample_select(G);
         pot += smp * G.s_pot;
@@ -1921,6 +1952,8 @@ __global__ void __launch_bounds__(256, 4)
 k_pair_quad(DevGraph G, const EnumSeg *__restrict__ segs, int n_seg, const float *__restrict__ pot,
             const float *__restrict__ b, const float *__restrict__ ev, const float *__restrict__ m_old,
             float *__restrict__ m_new, float T, float invT, float damping) {
+    pdl_wait();  // inputs of the previous launch
+    pdl_launch_dependents();  // the next launch may be scheduled (it waits likewise)
     static_assert(K == 8 || K == 16, "four states per lane, K / 4 lanes per factor");
     constexpr int L = K / 4;
     if constexpr (MS) {  // multi-sample launches: this block's sample
@@ -2019,6 +2052,8 @@ k_enum_generic(DevGraph G, const EnumSeg *__restrict__ segs, int n_seg, const fl
                const float *__restrict__ b, const float *__restrict__ ev,
                const float *__restrict__ m_old, float *__restrict__ m_new, float T, float invT,
                float damping) {
+    pdl_wait();  // inputs of the previous launch
+    pdl_launch_dependents();  // the next launch may be scheduled (it waits likewise)
     if constexpr (MS) {  // multi-sample launches: this block's sample
         const int64_t smp = sample_select(G);
         pot += smp * G.s_pot;
@@ -2282,6 +2317,8 @@ __global__ void __launch_bounds__(kEnumBlockThreads)
 k_enum_block(DevGraph G, const EnumSeg *__restrict__ segs, int n_seg, const float *__restrict__ pot,
              const float *__restrict__ b, const float *__restrict__ ev, const float *__restrict__ m_old,
              float *__restrict__ m_new, float T, float invT, float damping) {
+    pdl_wait();  // inputs of the previous launch
+    pdl_launch_dependents();  // the next launch may be scheduled (it waits likewise)
     if constexpr (MS) {  // multi-sample launches: this block's sample
         const int64_t smp = sample_select(G);
         pot += smp * G.s_pot;
@@ -2555,12 +2592,16 @@ __device__ __forceinline__ float edge_logodds(const DevGraph &G, const float *ev
     return sgn * log_odds(a0, a1);
 }
 
-// Thread per factor, fan-in <= kLogicSmallFan; leave-one-out sums written out directly.
-template <bool MAXP, bool MS = false>
+// Thread per factor, fan-in <= F (F = kLogicSmallFan, or 2 for launches whose groups
+// have at most two parents, which keeps fewer registers); leave-one-out sums written out
+// directly.
+template <bool MAXP, bool MS = false, int F = kLogicSmallFan>
 __global__ void __launch_bounds__(256)
 k_logic_small(DevGraph G, const LogicSeg *__restrict__ segs, int n_seg, const float *__restrict__ b,
               const float *__restrict__ ev, const float *__restrict__ m_old,
               float *__restrict__ m_new, float T, float invT, float damping) {
+    pdl_wait();  // inputs of the previous launch
+    pdl_launch_dependents();  // the next launch may be scheduled (it waits likewise)
     if constexpr (MS) {  // multi-sample launches: this block's sample
         const int64_t smp = sample_select(G);
         b += smp * G.s_vs;
@@ -2579,7 +2620,6 @@ k_logic_small(DevGraph G, const LogicSeg *__restrict__ segs, int n_seg, const fl
     const float sgn = __ldg(&S->kind) == PGM_LOGIC_AND ? -1.f : 1.f;
     // parents in unrolled slots (j < n valid) and the child apart, so that every array
     // index is a constant and the values stay in registers
-    constexpr int F = kLogicSmallFan;
     float x[F];
     float2 mo[F], moc;
 #pragma unroll
@@ -2828,6 +2868,8 @@ __global__ void __launch_bounds__(128)
 k_logic_warp(DevGraph G, const LogicSeg *__restrict__ segs, int n_seg, const float *__restrict__ b,
              const float *__restrict__ ev, const float *__restrict__ m_old,
              float *__restrict__ m_new, float T, float invT, float damping, int cap) {
+    pdl_wait();  // inputs of the previous launch
+    pdl_launch_dependents();  // the next launch may be scheduled (it waits likewise)
     if constexpr (MS) {  // multi-sample launches: this block's sample
         const int64_t smp = sample_select(G);
         b += smp * G.s_vs;
@@ -2874,6 +2916,8 @@ k_logic_warp(DevGraph G, const LogicSeg *__restrict__ segs, int n_seg, const flo
 __global__ void __launch_bounds__(128) k_adj_beliefs(DevGraph G, const float *__restrict__ ev,
                                                      const float *__restrict__ m, const float *__restrict__ gnb,
                                                      float *__restrict__ d_ev, float *__restrict__ adj) {
+    pdl_wait();  // inputs of the previous launch
+    pdl_launch_dependents();  // the next launch may be scheduled (it waits likewise)
     const int v = blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= G.V) return;
     const int vs = G.vs_off[v], K = G.vs_off[v + 1] - vs, k0 = G.vin_off[v], k1 = G.vin_off[v + 1];
@@ -3058,6 +3102,8 @@ k_adj_factor(DevGraph G, const EnumSeg *__restrict__ segs, int n_seg, const floa
              const float *__restrict__ adj, float *__restrict__ dv2f, float *__restrict__ ddamp,
              float *__restrict__ d_pot, float *__restrict__ partials, int nc_max, float T, float invT,
              float damping) {
+    pdl_wait();  // inputs of the previous launch
+    pdl_launch_dependents();  // the next launch may be scheduled (it waits likewise)
     const EnumSeg *S = segs + find_seg(segs, n_seg, blockIdx.x);
     const int f_raw = (blockIdx.x - S->block_begin) * blockDim.x + threadIdx.x;
     // a block lies in one group, so a warp does; idle lanes shadow the group's last
@@ -3194,6 +3240,8 @@ k_adj_factor(DevGraph G, const EnumSeg *__restrict__ segs, int n_seg, const floa
 __global__ void __launch_bounds__(256) k_adj_pot_reduce(const EnumSeg *__restrict__ segs, int n_seg,
                                                         const float *__restrict__ partials, int nc_max,
                                                         int threads_per_block, float *__restrict__ d_pot) {
+    pdl_wait();  // inputs of the previous launch
+    pdl_launch_dependents();  // the next launch may be scheduled (it waits likewise)
     const EnumSeg *S = segs + blockIdx.x;
     if (!S->shared || S->n_fac == 0) return;
     // the group's factors are consecutive from its first block, 32 to a warp; warps past
@@ -3220,6 +3268,8 @@ k_adj_block(DevGraph G, const EnumSeg *__restrict__ segs, int n_seg, const float
             const float *__restrict__ b, const float *__restrict__ ev, const float *__restrict__ m_old,
             const float *__restrict__ adj, float *__restrict__ dv2f, float *__restrict__ ddamp,
             float *__restrict__ d_pot, float T, float invT, float damping) {
+    pdl_wait();  // inputs of the previous launch
+    pdl_launch_dependents();  // the next launch may be scheduled (it waits likewise)
     extern __shared__ __align__(16) float ab_smem[];
     __shared__ int sK[kMaxArity], sKo[kMaxArity];
     __shared__ int s_fix[kEnumBlockThreads / 32][kMaxArity];
@@ -3402,6 +3452,8 @@ __global__ void __launch_bounds__(128)
 k_adj_logic(DevGraph G, const LogicSeg *__restrict__ segs, int n_seg, const float *__restrict__ b,
             const float *__restrict__ ev, const float *__restrict__ m_old, const float *__restrict__ adj,
             float *__restrict__ dv2f, float *__restrict__ ddamp, float T, float damping) {
+    pdl_wait();  // inputs of the previous launch
+    pdl_launch_dependents();  // the next launch may be scheduled (it waits likewise)
     const LogicSeg *S = segs + find_seg(segs, n_seg, blockIdx.x);
     const int f = (blockIdx.x - __ldg(&S->block_begin)) * blockDim.x + threadIdx.x;
     if (f >= __ldg(&S->n_fac)) return;
@@ -3500,6 +3552,8 @@ k_adj_logic(DevGraph G, const LogicSeg *__restrict__ segs, int n_seg, const floa
 __global__ void __launch_bounds__(64) k_adj_var_tab4(DevGraph G, const float *__restrict__ ddamp,
                                                      const float *__restrict__ dv2f, float *__restrict__ adj_prev,
                                                      float *__restrict__ d_ev) {
+    pdl_wait();  // inputs of the previous launch
+    pdl_launch_dependents();  // the next launch may be scheduled (it waits likewise)
     const int v = blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= G.V) return;
     const int4 t = __ldg(G.vin_tab4 + v);
@@ -3533,6 +3587,8 @@ __global__ void __launch_bounds__(64) k_adj_var_tab4(DevGraph G, const float *__
 __global__ void __launch_bounds__(128) k_adj_var(DevGraph G, const float *__restrict__ ddamp,
                                                  const float *__restrict__ dv2f, float *__restrict__ adj_prev,
                                                  float *__restrict__ d_ev) {
+    pdl_wait();  // inputs of the previous launch
+    pdl_launch_dependents();  // the next launch may be scheduled (it waits likewise)
     const int v = blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= G.V) return;
     const int vs = G.vs_off[v], K = G.vs_off[v + 1] - vs, k0 = G.vin_off[v], k1 = G.vin_off[v + 1];
@@ -3582,8 +3638,6 @@ constexpr uint32_t kLamBothNegInf = 0x7fc00001u;
 // passes exchange only after it. pdl_wait() returns once the previous kernel of the
 // stream has completed and its writes are visible (at once when there is none); as
 // that kernel waited the same way, every earlier one has completed too.
-__device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;"); }
-__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
 __device__ __forceinline__ float2 lr_decode(float d) {
     return d > 0.f ? make_float2(-d, 0.f) : make_float2(0.f, d);
@@ -4302,6 +4356,25 @@ cudaError_t prepare_kernels(int max_smem_bytes) {
     return cudaSuccess;
 }
 
+// Launches a kernel of the iteration or the adjoint chain with the programmatic
+// attribute: its launch and block dispatch overlap the previous kernel's last blocks, and
+// the kernel itself waits (pdl_wait) before it touches global memory.
+template <typename... KArgs, typename... Args>
+static void launch_dep(void (*kernel)(KArgs...), dim3 grid, int threads, size_t smem, cudaStream_t s,
+                       Args... args) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = grid;
+    cfg.blockDim = dim3((unsigned)threads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kernel, args...);  // errors surface through cudaGetLastError
+}
+
 template <int MODE, bool MS>
 static void var_pass_mode(const DevGraph &G, const Plan &P, const float *ev, const float *m,
                           float *out, int32_t *dec, cudaStream_t s, int S, const LaunchHook *hook) {
@@ -4316,31 +4389,31 @@ static void var_pass_mode(const DevGraph &G, const Plan &P, const float *ev, con
         switch (L.kind) {
             case kVarBlockSum:  // the tile sums of the split form (single-sample launches)
                 if (MS || S > 1 || L.tiles == nullptr || G.hd_tot == nullptr) continue;
-                k_var_hd_sum<<<L.n_tiles, kVarBlockThreads, 0, s>>>(G, L.list, L.tiles, m);
+                launch_dep(k_var_hd_sum, dim3(L.n_tiles), kVarBlockThreads, 0, s, G, L.list, L.tiles, m);
                 break;
             case kVarBlock:
                 if (!MS && S == 1 && L.tiles != nullptr && G.hd_tot != nullptr)
-                    k_var_hd_out<MODE><<<L.n_tiles, kVarBlockThreads, 0, s>>>(G, L.list, L.tiles, ev, out, dec);
+                    launch_dep(k_var_hd_out<MODE>, dim3(L.n_tiles), kVarBlockThreads, 0, s, G, L.list, L.tiles, ev, out, dec);
                 else
-                    k_var_block<MODE, MS><<<dim3(L.n, S), kVarBlockThreads, 0, s>>>(G, L.list, ev, m, out, dec);
+                    launch_dep(k_var_block<MODE, MS>, dim3(dim3(L.n, S)), kVarBlockThreads, 0, s, G, L.list, ev, m, out, dec);
                 break;
             case kVarBinary:
-                k_var_thread<2, MODE, MS><<<dim3(L.n_blocks, S), L.threads, 0, s>>>(G, L.list, L.n, L.dense_binary, ev, m, out, dec);
+                launch_dep(k_var_thread<2, MODE, MS>, dim3(dim3(L.n_blocks, S)), L.threads, 0, s, G, L.list, L.n, L.dense_binary, ev, m, out, dec);
                 break;
             case kVarGroup4:
-                k_var_group<4, MODE, MS><<<dim3(L.n_blocks, S), L.threads, 0, s>>>(G, L.list, L.n, ev, m, out, dec);
+                launch_dep(k_var_group<4, MODE, MS>, dim3(dim3(L.n_blocks, S)), L.threads, 0, s, G, L.list, L.n, ev, m, out, dec);
                 break;
             case kVarGroup8:
-                k_var_group<8, MODE, MS><<<dim3(L.n_blocks, S), L.threads, 0, s>>>(G, L.list, L.n, ev, m, out, dec);
+                launch_dep(k_var_group<8, MODE, MS>, dim3(dim3(L.n_blocks, S)), L.threads, 0, s, G, L.list, L.n, ev, m, out, dec);
                 break;
             case kVarGroup16:
-                k_var_group<16, MODE, MS><<<dim3(L.n_blocks, S), L.threads, 0, s>>>(G, L.list, L.n, ev, m, out, dec);
+                launch_dep(k_var_group<16, MODE, MS>, dim3(dim3(L.n_blocks, S)), L.threads, 0, s, G, L.list, L.n, ev, m, out, dec);
                 break;
             case kVarWarp:
-                k_var_warp<MODE, MS><<<dim3(L.n_blocks, S), L.threads, 0, s>>>(G, L.list, L.n, ev, m, out, dec);
+                launch_dep(k_var_warp<MODE, MS>, dim3(dim3(L.n_blocks, S)), L.threads, 0, s, G, L.list, L.n, ev, m, out, dec);
                 break;
             default:
-                k_var_thread<0, MODE, MS><<<dim3(L.n_blocks, S), L.threads, 0, s>>>(G, L.list, L.n, 0, ev, m, out, dec);
+                launch_dep(k_var_thread<0, MODE, MS>, dim3(dim3(L.n_blocks, S)), L.threads, 0, s, G, L.list, L.n, 0, ev, m, out, dec);
                 break;
         }
         if (hook) hook->after(hook->ctx);
@@ -4368,7 +4441,7 @@ static void factor_pass_t(const DevGraph &G, const Plan &P, const float *pot, co
         const LogicSeg *ls = static_cast<const LogicSeg *>(L.segs);
         switch (L.variant) {
             case kPair2:
-                k_pair<2, MAXP, MS><<<dim3(L.n_blocks, S), L.threads, 0, s>>>(G, es, L.n_seg, pot, b, ev, m_old, m_new, T, invT, damping);
+                launch_dep(k_pair<2, MAXP, MS>, dim3(dim3(L.n_blocks, S)), L.threads, 0, s, G, es, L.n_seg, pot, b, ev, m_old, m_new, T, invT, damping);
                 break;
             case kPair4:
                 k_pair_group<4, MAXP, MS><<<dim3(min(L.n_blocks, L.max_blocks), S), L.threads, 0, s>>>(G, es, L.n_seg, L.n_blocks, pot, b, ev, m_old, m_new, T, invT, damping);
@@ -4380,40 +4453,43 @@ static void factor_pass_t(const DevGraph &G, const Plan &P, const float *pot, co
                 k_pair_group<16, MAXP, MS><<<dim3(min(L.n_blocks, L.max_blocks), S), L.threads, 0, s>>>(G, es, L.n_seg, L.n_blocks, pot, b, ev, m_old, m_new, T, invT, damping);
                 break;
             case kPairT4:
-                k_pair_thr<4, MAXP, MS><<<dim3(L.n_blocks, S), L.threads, 0, s>>>(G, es, L.n_seg, pot, b, ev, m_old, m_new, T, invT, damping);
+                launch_dep(k_pair_thr<4, MAXP, MS>, dim3(dim3(L.n_blocks, S)), L.threads, 0, s, G, es, L.n_seg, pot, b, ev, m_old, m_new, T, invT, damping);
                 break;
             case kPairT8:
-                k_pair_thr<8, MAXP, MS><<<dim3(L.n_blocks, S), L.threads, 0, s>>>(G, es, L.n_seg, pot, b, ev, m_old, m_new, T, invT, damping);
+                launch_dep(k_pair_thr<8, MAXP, MS>, dim3(dim3(L.n_blocks, S)), L.threads, 0, s, G, es, L.n_seg, pot, b, ev, m_old, m_new, T, invT, damping);
                 break;
             case kPairT16:
-                k_pair_thr<16, MAXP, MS><<<dim3(L.n_blocks, S), L.threads, 0, s>>>(G, es, L.n_seg, pot, b, ev, m_old, m_new, T, invT, damping);
+                launch_dep(k_pair_thr<16, MAXP, MS>, dim3(dim3(L.n_blocks, S)), L.threads, 0, s, G, es, L.n_seg, pot, b, ev, m_old, m_new, T, invT, damping);
                 break;
             case kPairD4:
-                k_pair_dir<4, MAXP, MS><<<dim3(L.n_blocks, S), L.threads, 0, s>>>(G, es, L.n_seg, pot, b, ev, m_old, m_new, T, invT, damping);
+                launch_dep(k_pair_dir<4, MAXP, MS>, dim3(dim3(L.n_blocks, S)), L.threads, 0, s, G, es, L.n_seg, pot, b, ev, m_old, m_new, T, invT, damping);
                 break;
             case kPairD8:
-                k_pair_dir<8, MAXP, MS><<<dim3(L.n_blocks, S), L.threads, 0, s>>>(G, es, L.n_seg, pot, b, ev, m_old, m_new, T, invT, damping);
+                launch_dep(k_pair_dir<8, MAXP, MS>, dim3(dim3(L.n_blocks, S)), L.threads, 0, s, G, es, L.n_seg, pot, b, ev, m_old, m_new, T, invT, damping);
                 break;
             case kPairD16:
-                k_pair_dir<16, MAXP, MS><<<dim3(L.n_blocks, S), L.threads, 0, s>>>(G, es, L.n_seg, pot, b, ev, m_old, m_new, T, invT, damping);
+                launch_dep(k_pair_dir<16, MAXP, MS>, dim3(dim3(L.n_blocks, S)), L.threads, 0, s, G, es, L.n_seg, pot, b, ev, m_old, m_new, T, invT, damping);
                 break;
             case kPairQ8:
-                k_pair_quad<8, MAXP, MS><<<dim3(L.n_blocks, S), L.threads, 0, s>>>(G, es, L.n_seg, pot, b, ev, m_old, m_new, T, invT, damping);
+                launch_dep(k_pair_quad<8, MAXP, MS>, dim3(dim3(L.n_blocks, S)), L.threads, 0, s, G, es, L.n_seg, pot, b, ev, m_old, m_new, T, invT, damping);
                 break;
             case kPairQ16:
-                k_pair_quad<16, MAXP, MS><<<dim3(L.n_blocks, S), L.threads, 0, s>>>(G, es, L.n_seg, pot, b, ev, m_old, m_new, T, invT, damping);
+                launch_dep(k_pair_quad<16, MAXP, MS>, dim3(dim3(L.n_blocks, S)), L.threads, 0, s, G, es, L.n_seg, pot, b, ev, m_old, m_new, T, invT, damping);
                 break;
             case kEnumGeneric:
-                k_enum_generic<MAXP, MS><<<dim3(L.n_blocks, S), L.threads, 0, s>>>(G, es, L.n_seg, pot, b, ev, m_old, m_new, T, invT, damping);
+                launch_dep(k_enum_generic<MAXP, MS>, dim3(dim3(L.n_blocks, S)), L.threads, 0, s, G, es, L.n_seg, pot, b, ev, m_old, m_new, T, invT, damping);
                 break;
             case kEnumBlock:
-                k_enum_block<MAXP, MS><<<dim3(L.n_blocks, S), L.threads, L.smem, s>>>(G, es, L.n_seg, pot, b, ev, m_old, m_new, T, invT, damping);
+                launch_dep(k_enum_block<MAXP, MS>, dim3(dim3(L.n_blocks, S)), L.threads, L.smem, s, G, es, L.n_seg, pot, b, ev, m_old, m_new, T, invT, damping);
                 break;
             case kLogicSmall:
-                k_logic_small<MAXP, MS><<<dim3(L.n_blocks, S), L.threads, 0, s>>>(G, ls, L.n_seg, b, ev, m_old, m_new, T, invT, damping);
+                if (L.max_fan <= 2)
+                    launch_dep(k_logic_small<MAXP, MS, 2>, dim3(dim3(L.n_blocks, S)), L.threads, 0, s, G, ls, L.n_seg, b, ev, m_old, m_new, T, invT, damping);
+                else
+                    launch_dep(k_logic_small<MAXP, MS>, dim3(dim3(L.n_blocks, S)), L.threads, 0, s, G, ls, L.n_seg, b, ev, m_old, m_new, T, invT, damping);
                 break;
             case kLogicWarp:
-                k_logic_warp<MAXP, MS><<<dim3(L.n_blocks, S), L.threads, L.smem, s>>>(G, ls, L.n_seg, b, ev, m_old, m_new, T, invT, damping, L.max_fan);
+                launch_dep(k_logic_warp<MAXP, MS>, dim3(dim3(L.n_blocks, S)), L.threads, L.smem, s, G, ls, L.n_seg, b, ev, m_old, m_new, T, invT, damping, L.max_fan);
                 break;
             default:
                 break;
@@ -4618,7 +4694,7 @@ namespace pgm {
 
 cudaError_t launch_adj_beliefs(const DevGraph &G, const float *ev, const float *m, const float *gnb, float *d_ev,
                                float *adj, cudaStream_t s) {
-    k_adj_beliefs<<<(G.V + 127) / 128, 128, 0, s>>>(G, ev, m, gnb, d_ev, adj);
+    launch_dep(k_adj_beliefs, dim3((G.V + 127) / 128), 128, 0, s, G, ev, m, gnb, d_ev, adj);
     return cudaGetLastError();
 }
 
@@ -4627,14 +4703,14 @@ cudaError_t launch_adj_factor(const DevGraph &G, const FactorLaunch &L, const fl
                               float *d_pot, float *partials, int nc_max, float T, float damping, cudaStream_t s) {
     if (L.n_blocks == 0) return cudaSuccess;
     if (L.variant == kEnumBlock) {
-        k_adj_block<<<L.n_blocks, L.threads, L.smem, s>>>(G, static_cast<const EnumSeg *>(L.segs), L.n_seg, pot, b, ev,
+        launch_dep(k_adj_block, dim3(L.n_blocks), L.threads, L.smem, s, G, static_cast<const EnumSeg *>(L.segs), L.n_seg, pot, b, ev,
                                                           m_old, adj, dv2f, ddamp, d_pot, T, 1.f / T, damping);
     } else {
-        k_adj_factor<<<L.n_blocks, L.threads, 0, s>>>(G, static_cast<const EnumSeg *>(L.segs), L.n_seg, pot, b, ev,
+        launch_dep(k_adj_factor, dim3(L.n_blocks), L.threads, 0, s, G, static_cast<const EnumSeg *>(L.segs), L.n_seg, pot, b, ev,
                                                       m_old, adj, dv2f, ddamp, d_pot, partials, nc_max, T, 1.f / T,
                                                       damping);
         if (partials != nullptr)
-            k_adj_pot_reduce<<<L.n_seg, 256, 0, s>>>(static_cast<const EnumSeg *>(L.segs), L.n_seg, partials, nc_max,
+            launch_dep(k_adj_pot_reduce, dim3(L.n_seg), 256, 0, s, static_cast<const EnumSeg *>(L.segs), L.n_seg, partials, nc_max,
                                                      L.threads, d_pot);
     }
     return cudaGetLastError();
@@ -4644,15 +4720,15 @@ cudaError_t launch_adj_logic(const DevGraph &G, const FactorLaunch &L, const flo
                              const float *m_old, const float *adj, float *dv2f, float *ddamp, float T, float damping,
                              cudaStream_t s) {
     if (L.n_blocks == 0) return cudaSuccess;
-    k_adj_logic<<<L.n_blocks, L.threads, 0, s>>>(G, static_cast<const LogicSeg *>(L.segs), L.n_seg, b, ev, m_old, adj,
+    launch_dep(k_adj_logic, dim3(L.n_blocks), L.threads, 0, s, G, static_cast<const LogicSeg *>(L.segs), L.n_seg, b, ev, m_old, adj,
                                                  dv2f, ddamp, T, damping);
     return cudaGetLastError();
 }
 
 cudaError_t launch_adj_var(const DevGraph &G, const float *ddamp, const float *dv2f, float *adj_prev, float *d_ev,
                            cudaStream_t s) {
-    if (G.vin_tab4 != nullptr) k_adj_var_tab4<<<(G.V + 63) / 64, 64, 0, s>>>(G, ddamp, dv2f, adj_prev, d_ev);
-    else k_adj_var<<<(G.V + 127) / 128, 128, 0, s>>>(G, ddamp, dv2f, adj_prev, d_ev);
+    if (G.vin_tab4 != nullptr) launch_dep(k_adj_var_tab4, dim3((G.V + 63) / 64), 64, 0, s, G, ddamp, dv2f, adj_prev, d_ev);
+    else launch_dep(k_adj_var, dim3((G.V + 127) / 128), 128, 0, s, G, ddamp, dv2f, adj_prev, d_ev);
     return cudaGetLastError();
 }
 
