@@ -651,9 +651,9 @@ def measure_deconv(args, binding, W, torch, dev):
         np.add.at(deg, lg_.parents, 1)
         np.add.at(deg, lg_.child, 1)
     hi = deg > 64
-    # implementation bytes per launch: the tile sums read the high-degree variables' K d
-    # messages and their incoming-edge index; the second launch reads the tile totals
-    # (16 bytes per tile and state) and writes each state's totals (16 bytes) and belief;
+    # implementation bytes per launch: the high-degree pass reads the variables' K d
+    # messages and their incoming-edge index, writes and re-reads the tile totals (16 bytes
+    # per tile and state) and writes each state's totals (16 bytes) and belief;
     # a logical factor reads its old messages, the beliefs of its edges (the totals of a
     # high-degree variable) and their index, and writes its messages
     n_hi_es = int((ks[hi] * deg[hi]).sum())
@@ -662,13 +662,12 @@ def measure_deconv(args, binding, W, torch, dev):
     e_or = int(or_g.par_off[-1]) + or_g.n_fac
     d_hi = int(deg[hi].sum())
     n_tiles_st = int((ks[hi] * ((deg[hi] + 2047) // 2048)).sum())
-    impl = {"k_var_hd_sum": 4 * n_hi_es + 4 * d_hi,  # messages and incoming-edge index
-            "k_var_hd_out": 16 * n_tiles_st + 20 * int(ks[hi].sum()),
+    impl = {"k_var_hd": 4 * n_hi_es + 4 * d_hi + 32 * n_tiles_st + 20 * int(ks[hi].sum()),
             "k_logic_small": 4 * (4 * e_and + 2 * e_and + e_and),
             "k_logic_warp": 4 * (4 * e_or + 2 * e_or + e_or)}
     s8d = {"k_logic_small": sec8d_bytes(fg, [0]), "k_logic_warp": sec8d_bytes(fg, [1]),
-           "k_var_hd_sum": 0, "k_var_hd_out": 4 * int(ks[hi].sum())}
-    names = {(0, 8): "k_var_hd_sum", (0, 1): "k_var_hd_out", (0, 2): "k_var_thread<2>", (0, 0): "k_var_thread",
+           "k_var_hd": 4 * int(ks[hi].sum())}
+    names = {(0, 1): "k_var_hd", (0, 2): "k_var_thread<2>", (0, 0): "k_var_thread",
              (1, 5): "k_logic_small", (1, 6): "k_logic_warp"}
     per = {}
     for (kind, variant, threads, blocks), (ms, cnt) in zip(launches, lt):

@@ -542,9 +542,9 @@ pgm_status pgm_autotune(pgm_graph *g, const float *log_pot, const float *evidenc
 /*
  * Launch i of one iteration (0 <= i < pgm_info.launches_per_iter): kind 0 = variable
  * pass (variant 0 thread per variable, 1 variables with more than 64 factors: a block
- * per tile of 2048 incoming edges, after the launch of their tile sums, variant 8; 2
- * thread per binary variable, 3..5 K = 4, 8, 16 lanes per variable, 6 padded 4-edge
- * table, 7 warp per variable with K > 16),
+ * per tile of 2048 incoming edges, the last tile of a variable finishing it; 2 thread
+ * per binary variable, 3..5 K = 4, 8, 16 lanes per variable, 6 padded 4-edge table, 7
+ * warp per variable with K > 16),
  * kind 1 = factor pass (variant: 0 dense pairwise K = 2; 1..3 dense pairwise K = 4, 8,
  * 16 with K lanes per factor; 4 listed configurations; 5 logical (OR / AND / XOR) thread
  * per factor; 6 logical warp per factor; 7..9 dense pairwise K = 4, 8, 16 with a thread

@@ -131,6 +131,7 @@ struct pgm_graph {
     FactorLaunch adj_launch{};      // pgm_grad: enumeration groups of state sum <= 64, thread per factor
     int32_t adj_nc_max = 0;         // largest list of those groups with a shared table (0: none)
     int64_t hd_tot_entries = 0;     // float4 tile totals of the high-degree variables
+    int64_t hd_vars = 0;            // high-degree variables (their tile tickets)
     size_t tiles_off = 0;           // their tile list in the index memory
     size_t adj_seg_off = (size_t)-1;
     FactorLaunch adj_block_launch{};  // pgm_grad: the larger groups, block form (k_adj_block)
@@ -304,7 +305,7 @@ pgm_status build_plan(const HostLayout &H, pgm_graph *g, Packer &pk, std::vector
         L.list = nullptr;
         const size_t list_off = H.var_bucket_identity[kind] ? (size_t)-1 : pk.add(bucket.data(), bucket.size());
         if (kind == kVarBlock) {
-            // the split form: a launch of tile sums, then the outputs, a block per tile
+            // the split form: a block per tile of 2048 edges (single-sample launches)
             std::vector<int4> tiles;
             int32_t first = 0;
             for (size_t i = 0; i < bucket.size(); ++i) {
@@ -315,13 +316,9 @@ pgm_status build_plan(const HostLayout &H, pgm_graph *g, Packer &pk, std::vector
                 first += nt * K;
             }
             g->hd_tot_entries = first;
+            g->hd_vars = (int64_t)bucket.size();
             g->tiles_off = pk.add(tiles.data(), tiles.size());
             L.n_tiles = (int32_t)tiles.size();
-            VarLaunch Ls = L;
-            Ls.kind = kVarBlockSum;
-            P.var.push_back(Ls);
-            seg_off.push_back(list_off);
-            seg_kind.push_back(-1);
         }
         P.var.push_back(L);
         seg_off.push_back(list_off);
@@ -682,7 +679,8 @@ static pgm_status build_from_layout(const HostLayout &H, pgm_graph **out, cudaSt
     const size_t lr_bytes = g->P.lr ? align_up((size_t)g->lr_slots * sizeof(float), 256) : 0;
     const size_t prm_bytes = g->P.lr ? align_up((size_t)3 * (H.E / 2) * sizeof(float), 256) : 0;
     const size_t blo_bytes = keeps_b_lo(H) ? vs_bytes : 0;
-    const size_t tot_bytes = align_up((size_t)g->hd_tot_entries * sizeof(float4), 256);
+    const size_t tot_bytes = align_up((size_t)g->hd_tot_entries * sizeof(float4), 256) +
+                             align_up((size_t)g->hd_vars * sizeof(int32_t), 256);
     const size_t scratch_bytes = es_bytes + vs_bytes + 256 + hd_bytes + 2 * lr_bytes + prm_bytes + blo_bytes + tot_bytes;
     char *smem = nullptr;
     ce = ordered ? cudaMallocAsync(&smem, scratch_bytes, s) : cudaMalloc(&smem, scratch_bytes);
@@ -724,6 +722,17 @@ static pgm_status build_from_layout(const HostLayout &H, pgm_graph **out, cudaSt
     G.hd_tot = tot_bytes ? reinterpret_cast<float4 *>(smem + es_bytes + vs_bytes + 256 + hd_bytes + 2 * lr_bytes +
                                                       prm_bytes + blo_bytes)
                          : nullptr;
+    G.hd_cnt = g->hd_vars ? reinterpret_cast<int32_t *>(reinterpret_cast<char *>(G.hd_tot) +
+                                                        align_up((size_t)g->hd_tot_entries * sizeof(float4), 256))
+                          : nullptr;
+    if (G.hd_cnt) {  // the tile tickets start at zero (each launch leaves them so)
+        ce = ordered ? cudaMemsetAsync(G.hd_cnt, 0, (size_t)g->hd_vars * sizeof(int32_t), s)
+                     : cudaMemset(G.hd_cnt, 0, (size_t)g->hd_vars * sizeof(int32_t));
+        if (ce != cudaSuccess) {
+            pgm_free(g);
+            return cuda_fail(ce, "cudaMemset(tile tickets)");
+        }
+    }
     if (g->P.lr) {
         g->lr_d = reinterpret_cast<float *>(smem + es_bytes + vs_bytes + 256 + hd_bytes);
         g->lr_lam = reinterpret_cast<float *>(smem + es_bytes + vs_bytes + 256 + hd_bytes + lr_bytes);
@@ -736,7 +745,7 @@ static pgm_status build_from_layout(const HostLayout &H, pgm_graph **out, cudaSt
         if (seg_kind[k] < 0) {
             VarLaunch &L = g->P.var[vi++];
             L.list = (seg_off[k] == (size_t)-1) ? nullptr : reinterpret_cast<const int32_t *>(dmem + seg_off[k]);
-            if (L.kind == kVarBlock || L.kind == kVarBlockSum) L.tiles = reinterpret_cast<const int4 *>(dmem + g->tiles_off);
+            if (L.kind == kVarBlock) L.tiles = reinterpret_cast<const int4 *>(dmem + g->tiles_off);
         } else {
             FactorLaunch &L = g->P.factor[fi++];
             L.segs = dmem + seg_off[k];
@@ -799,7 +808,7 @@ int64_t pgm::layout_device_bytes(const HostLayout &H) {
         idx += H.E * sizeof(int32_t) + 2 * align_up((size_t)lr_slot_count(H) * sizeof(float), 256) +
                align_up((size_t)3 * (H.E / 2) * sizeof(float), 256);
     const size_t vs_bytes = align_up(std::max<int64_t>(H.VS, 1) * sizeof(float), 256);
-    // the high-degree variables' tile list (index memory) and tile sums (scratch)
+    // the high-degree variables' tile list (index memory), tile totals and tickets (scratch)
     int64_t n_tiles = 0, tot = 0;
     for (int32_t v : H.var_bucket[kVarBlock]) {
         const int64_t nt = (H.vin_off[v + 1] - H.vin_off[v] + kVarTile - 1) / kVarTile;
@@ -808,7 +817,8 @@ int64_t pgm::layout_device_bytes(const HostLayout &H) {
     }
     idx += (size_t)n_tiles * sizeof(int4);
     return (int64_t)(idx + es_bytes + vs_bytes + 256 + (H.var_bucket[kVarBlock].empty() ? 0 : 4 * vs_bytes) +
-                     (keeps_b_lo(H) ? vs_bytes : 0) + align_up((size_t)tot * sizeof(float4), 256));
+                     (keeps_b_lo(H) ? vs_bytes : 0) + align_up((size_t)tot * sizeof(float4), 256) +
+                     align_up(H.var_bucket[kVarBlock].size() * sizeof(int32_t), 256));
 }
 
 pgm_status pgm::build_layout_on_stream(const HostLayout &H, cudaStream_t s, pgm_graph **out) {
@@ -1853,7 +1863,7 @@ pgm_status pgm_autotune(pgm_graph *g, const float *log_pot, const float *evidenc
     }
     // thread-per-variable launches: block size
     for (VarLaunch &L : g->P.var) {
-        if (L.kind == kVarBlock || L.kind == kVarBlockSum || L.n == 0 || g->G.vin_tab4) continue;
+        if (L.kind == kVarBlock || L.n == 0 || g->G.vin_tab4) continue;
         int best = L.threads;
         float best_ms = 1e30f;
         for (int c : {128, 256}) {
@@ -1893,11 +1903,11 @@ pgm_status pgm_launch_info(const pgm_graph *g, int32_t i, int32_t *kind, int32_t
     if (i < nv) {
         const VarLaunch &L = g->P.var[i];
         if (kind) *kind = 0;
-        if (variant) *variant = g->G.vin_tab4 ? 6 : (L.kind == kVarWarp ? 7 : L.kind == kVarBlockSum ? 8 : L.kind);
+        if (variant) *variant = g->G.vin_tab4 ? 6 : (L.kind == kVarWarp ? 7 : L.kind);
         if (threads) *threads = L.kind == kVarBlock ? kVarBlockThreads : (g->G.vin_tab4 ? 256 : L.threads);
         if (n_blocks)
             *n_blocks = g->G.vin_tab4 ? (int32_t)((g->info.n_vars + 255) / 256)
-                                      : (L.kind == kVarBlock || L.kind == kVarBlockSum ? L.n_tiles : L.n_blocks);
+                                      : (L.kind == kVarBlock ? L.n_tiles : L.n_blocks);
     } else {
         const FactorLaunch &L = g->P.factor[i - nv];
         if (kind) *kind = 1;

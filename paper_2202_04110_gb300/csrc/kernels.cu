@@ -1057,20 +1057,26 @@ __global__ void __launch_bounds__(kVarBlockThreads) k_var_block(DevGraph G, cons
     var_block_output<MODE>(G, sb, K, vs, v, out, dec);
 }
 
-// The high-degree variables split over tiles of kVarTile edges, in two launches, for
-// more blocks than variables: k_var_hd_sum, a block per tile, writes the tile's totals
-// of every state to G.hd_tot (float4: float-float sum of the finite entries, count of
-// -inf ones); k_var_hd_out, launched over the same tiles, finishes each variable in the
-// block of its first tile (a thread per state: hd_state_total, then the outputs), the
-// other blocks returning at once. tiles[i] = (position in the variable list, tile, first
+// The high-degree variables split over tiles of kVarTile edges, a block per tile, for
+// more blocks than variables: each block writes its tile's totals of every state to
+// G.hd_tot (float4: float-float sum of the finite entries, count of -inf ones), and the
+// last of a variable's tiles to finish (a ticket per variable, G.hd_cnt, taken after a
+// memory fence and reset by the taker) adds the variable's tile totals in tile order
+// (hd_state_total, a thread per state) and writes its outputs -- the same sums in the
+// same order as k_var_block. tiles[i] = (position in the variable list, tile, first
 // hd_tot entry of the variable, tiles of the variable); a variable's K totals of tile t
 // are at hd_tot[first + t K .. + K).
-__global__ void __launch_bounds__(kVarBlockThreads) k_var_hd_sum(DevGraph G, const int32_t *__restrict__ list,
-                                                                 const int4 *__restrict__ tiles,
-                                                                 const float *__restrict__ m) {
+template <int MODE>
+__global__ void __launch_bounds__(kVarBlockThreads) k_var_hd(DevGraph G, const int32_t *__restrict__ list,
+                                                             const int4 *__restrict__ tiles,
+                                                             const float *__restrict__ ev,
+                                                             const float *__restrict__ m, float *__restrict__ out,
+                                                             int32_t *__restrict__ dec) {
     pdl_wait();  // inputs of the previous launch
     pdl_launch_dependents();  // the next launch may be scheduled (it waits likewise)
     __shared__ float sh[96];
+    __shared__ FF sb[kMaxStates];
+    __shared__ int s_last;
     const int4 tl = __ldg(tiles + blockIdx.x);
     const int v = list ? __ldg(list + tl.x) : tl.x;
     const int vs = __ldg(G.vs_off + v), K = __ldg(G.vs_off + v + 1) - vs;
@@ -1098,31 +1104,26 @@ __global__ void __launch_bounds__(kVarBlockThreads) k_var_hd_sum(DevGraph G, con
             G.hd_tot[tl.z + tl.y * 2] = make_float4(t0.hi, t0.lo, c0, 0.f);
             G.hd_tot[tl.z + tl.y * 2 + 1] = make_float4(t1.hi, t1.lo, c1, 0.f);
         }
-        return;
+    } else {
+        for (int x = 0; x < K; ++x) {
+            float c;
+            const FF s = hd_tile_part(G, m, k0, deg, tl.y, x, c);
+            const FF tt = block_sum_count(s, c, sh);
+            if (threadIdx.x == 0) G.hd_tot[tl.z + tl.y * K + x] = make_float4(tt.hi, tt.lo, c, 0.f);
+        }
     }
-    for (int x = 0; x < K; ++x) {
-        float c;
-        const FF s = hd_tile_part(G, m, k0, deg, tl.y, x, c);
-        const FF tt = block_sum_count(s, c, sh);
-        if (threadIdx.x == 0) G.hd_tot[tl.z + tl.y * K + x] = make_float4(tt.hi, tt.lo, c, 0.f);
+    // the variable's last tile to finish completes it
+    if (threadIdx.x == 0) {
+        __threadfence();  // this tile's totals are visible before its ticket
+        const int ticket = atomicAdd(G.hd_cnt + tl.x, 1);
+        s_last = (ticket == tl.w - 1);
+        if (s_last) G.hd_cnt[tl.x] = 0;  // for the next launch
     }
-}
-
-template <int MODE>
-__global__ void __launch_bounds__(kVarBlockThreads) k_var_hd_out(DevGraph G, const int32_t *__restrict__ list,
-                                                                 const int4 *__restrict__ tiles,
-                                                                 const float *__restrict__ ev,
-                                                                 float *__restrict__ out, int32_t *__restrict__ dec) {
-    pdl_wait();  // inputs of the previous launch
-    pdl_launch_dependents();  // the next launch may be scheduled (it waits likewise)
-    __shared__ FF sb[kMaxStates];
-    const int4 tl = __ldg(tiles + blockIdx.x);
-    if (tl.y != 0) return;  // one block per variable finishes it
-    const int v = list ? __ldg(list + tl.x) : tl.x;
-    const int vs = __ldg(G.vs_off + v), K = __ldg(G.vs_off + v + 1) - vs;
-    const int n_tiles = tl.w;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
     for (int x = threadIdx.x; x < K; x += blockDim.x)
-        sb[x] = hd_state_total<MODE>(G, __ldg(ev + vs + x), n_tiles,
+        sb[x] = hd_state_total<MODE>(G, __ldg(ev + vs + x), tl.w,
                                      [&](int t) { return __ldcg(G.hd_tot + tl.z + t * K + x); }, vs, x);
     __syncthreads();
     if (threadIdx.x != 0) return;
@@ -4387,13 +4388,9 @@ static void var_pass_mode(const DevGraph &G, const Plan &P, const float *ev, con
     for (const VarLaunch &L : P.var) {
         if (L.n == 0) continue;
         switch (L.kind) {
-            case kVarBlockSum:  // the tile sums of the split form (single-sample launches)
-                if (MS || S > 1 || L.tiles == nullptr || G.hd_tot == nullptr) continue;
-                launch_dep(k_var_hd_sum, dim3(L.n_tiles), kVarBlockThreads, 0, s, G, L.list, L.tiles, m);
-                break;
-            case kVarBlock:
-                if (!MS && S == 1 && L.tiles != nullptr && G.hd_tot != nullptr)
-                    launch_dep(k_var_hd_out<MODE>, dim3(L.n_tiles), kVarBlockThreads, 0, s, G, L.list, L.tiles, ev, out, dec);
+            case kVarBlock:  // single-sample launches: a block per tile; else a block per variable
+                if (!MS && S == 1 && L.tiles != nullptr && G.hd_tot != nullptr && G.hd_cnt != nullptr)
+                    launch_dep(k_var_hd<MODE>, dim3(L.n_tiles), kVarBlockThreads, 0, s, G, L.list, L.tiles, ev, m, out, dec);
                 else
                     launch_dep(k_var_block<MODE, MS>, dim3(dim3(L.n, S)), kVarBlockThreads, 0, s, G, L.list, ev, m, out, dec);
                 break;

@@ -136,6 +136,8 @@ struct DevGraph {
     float4 *hd_tot;          // tile totals of the high-degree variables' states (float-float
                              // sum of the finite entries, count of -inf ones, 0),
                              // VarLaunch::tiles; null if there are none
+    int32_t *hd_cnt;         // [high-degree variables] tile tickets of k_var_hd (zero
+                             // between launches); null if there are none
 };
 
 struct FactorLaunch {
@@ -160,9 +162,7 @@ enum VarKind : int32_t {
     kVarGroup8 = 4,
     kVarGroup16 = 5,
     kVarWarp = 6,     // warp per variable, K > 16 (pgm_launch_info reports 7)
-    kNumVarKinds = 7,
-    kVarBlockSum = 7  // the tile sums of the high-degree variables (a launch before
-                      // kVarBlock's; pgm_launch_info reports 8); no bucket of its own
+    kNumVarKinds = 7
 };
 
 struct VarLaunch {
@@ -172,7 +172,7 @@ struct VarLaunch {
     int32_t n_blocks;
     int32_t threads;
     int32_t dense_binary;    // every variable of the graph is binary (state offset = 2 v)
-    // kVarBlock / kVarBlockSum: the variables' tiles of kVarTile edges (int4: position in
+    // kVarBlock: the variables' tiles of kVarTile edges (int4: position in
     // the list, tile, first DevGraph::hd_tot entry of the variable, its tile count)
     const int4 *tiles;
     int32_t n_tiles;
