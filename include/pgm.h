@@ -281,12 +281,13 @@ pgm_status pgm_launch_times(pgm_graph *g, int32_t n, double *ms, int64_t *count,
  * call is recorded as a CUDA graph on first use of an argument tuple (up to 4 kept) and
  * replayed on the caller's stream; with it off, the scratch is a stream-ordered
  * allocation freed before the call's work ends.
- * Gradients of log-potentials shared by a group of factors with a state sum up to 64
- * are summed in a fixed order (each warp of 32 factors adds its contributions by a fixed
- * shuffle tree, then the warps' partials are added in order), so repeated calls give the
- * same bits; for factors with a state sum above 64 (computed in the block form, a warp
- * or block per factor) the log-potential gradients and the variable-to-factor adjoints
- * are summed in arbitrary order (atomic adds); everything else is deterministic.
+ * Every sum is taken in a fixed order, so repeated calls give the same bits: gradients of
+ * log-potentials shared by a group of factors with a state sum up to 64 through warp
+ * partials (each warp of 32 factors adds its contributions by a fixed shuffle tree, then
+ * the warps' partials are added in order); in the block form (state sums above 64) each
+ * variable-to-factor adjoint and each configuration's gradient is gathered by one thread
+ * in list order, shared tables through per-team rows added in order. (A block-form
+ * shared table whose rows would exceed 512 MiB of scratch falls back to atomic adds.)
  * Logical OR / AND factors are differentiated through their closed forms (linear in the
  * fan-in); a factor whose incoming log-odds include an infinite one (a hard constraint)
  * passes no gradient to its variable-to-factor values.

@@ -130,6 +130,7 @@ struct pgm_graph {
     std::vector<HostMember> members;
     FactorLaunch adj_launch{};      // pgm_grad: enumeration groups of state sum <= 64, thread per factor
     int32_t adj_nc_max = 0;         // largest list of those groups with a shared table (0: none)
+    int32_t adj_block_nc_max = 0;   // the same for the block-form adjoint's groups
     int64_t hd_tot_entries = 0;     // float4 tile totals of the high-degree variables
     int64_t hd_vars = 0;            // high-degree variables (their tile tickets)
     size_t tiles_off = 0;           // their tile list in the index memory
@@ -359,6 +360,9 @@ pgm_status build_plan(const HostLayout &H, pgm_graph *g, Packer &pk, std::vector
                 sm = std::max(sm, 16 * sg.es_per_fac * (sg.es_per_fac <= kEnumWarpStateSum ? kEnumBlockThreads / 32 : 1));
             g->adj_block_launch.smem = sm;
             g->adj_block_launch.n_seg = (int32_t)bsegs.size();
+            g->adj_block_nc_max = 0;
+            for (const EnumSeg &sg : bsegs)
+                if (sg.shared && sg.n_fac > 0) g->adj_block_nc_max = std::max(g->adj_block_nc_max, sg.n_cfg);
             g->adj_block_launch.threads = kEnumBlockThreads;
             g->adj_block_seg_off = pk.add(bsegs.data(), bsegs.size());
         }
@@ -1941,6 +1945,15 @@ static size_t grad_step_bytes(const pgm_graph *g) {
     return vsb * (1 + (g->G.hd_b ? 4 : 0) + (g->G.b_lo ? 1 : 0));
 }
 
+// The team rows of block-form shared-table gradients (k_adj_block): blocks x 8 teams x the
+// largest such list; 0 (the kernel then adds with atomics) beyond 512 MiB.
+static size_t grad_block_partials_bytes(const pgm_graph *g) {
+    if (g->adj_block_nc_max == 0 || g->adj_block_launch.n_blocks == 0) return 0;
+    const size_t b = align_up((size_t)g->adj_block_launch.n_blocks * (kEnumBlockThreads / 32) *
+                                  (size_t)g->adj_block_nc_max * sizeof(float), 256);
+    return b <= ((size_t)512 << 20) ? b : 0;
+}
+
 // Whether a gradient keeps each recomputed iteration's variable-pass outputs (so that its
 // reverse step launches no variable pass): when one segment's worth fits in 256 MiB.
 static bool grad_keeps_steps(const pgm_graph *g, int32_t n_iters, int32_t ckpt_every) {
@@ -1956,7 +1969,7 @@ static size_t grad_work_bytes(const pgm_graph *g, int32_t n_iters, int32_t ckpt_
     const size_t esb = align_up((size_t)ES * sizeof(float), 256);
     const int n_ck = n_iters > 0 ? (n_iters + ckpt_every - 1) / ckpt_every : 0;
     const int seg_len = std::min(ckpt_every, std::max(n_iters, 1));
-    return esb * ((size_t)n_ck + (size_t)seg_len + 6) + grad_partials_bytes(g) +
+    return esb * ((size_t)n_ck + (size_t)seg_len + 6) + grad_partials_bytes(g) + grad_block_partials_bytes(g) +
            (grad_keeps_steps(g, n_iters, ckpt_every) ? (size_t)seg_len * grad_step_bytes(g) : 0);
 }
 
@@ -1978,7 +1991,12 @@ static pgm_status enqueue_grad(pgm_graph *g, const float *log_pot, const float *
     // kept variable-pass outputs of the segment's iterations: step i's graph view points its
     // high-degree totals and belief residuals at the step's own buffers
     const bool keep = grad_keeps_steps(g, n_iters, ckpt_every);
-    char *steps = mem + esb * ((size_t)n_ck + (size_t)seg_len + 6) + grad_partials_bytes(g);
+    float *bpartials = grad_block_partials_bytes(g)
+                           ? reinterpret_cast<float *>(mem + esb * ((size_t)n_ck + (size_t)seg_len + 6) +
+                                                       grad_partials_bytes(g))
+                           : nullptr;
+    char *steps = mem + esb * ((size_t)n_ck + (size_t)seg_len + 6) + grad_partials_bytes(g) +
+                  grad_block_partials_bytes(g);
     const size_t vsb = align_up((size_t)std::max<int64_t>(g->info.n_var_states, 1) * sizeof(float), 256);
     auto step_b = [&](int i) { return reinterpret_cast<float *>(steps + (size_t)i * grad_step_bytes(g)); };
     auto step_G = [&](int i) {
@@ -2040,7 +2058,7 @@ static pgm_status enqueue_grad(pgm_graph *g, const float *log_pot, const float *
                                       partials, g->adj_nc_max, T, damping, s);
             if (e == cudaSuccess)
                 e = launch_adj_factor(Gs, g->adj_block_launch, log_pot, bt, evidence, m_prev, adjA, dv, ddamp,
-                                      d_log_pot, nullptr, 0, T, damping, s);
+                                      d_log_pot, bpartials, g->adj_block_nc_max, T, damping, s);
             if (e == cudaSuccess)
                 e = launch_adj_logic(Gs, g->adj_logic_launch, bt, evidence, m_prev, adjA, dv, ddamp, T, damping, s);
             if (e == cudaSuccess) e = launch_adj_var(Gs, ddamp, dv, adjB, d_evidence, s);

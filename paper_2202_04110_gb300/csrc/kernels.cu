@@ -1697,6 +1697,7 @@ k_pair_thr(DevGraph G, const EnumSeg *__restrict__ segs, int n_seg, const float 
     const int es0 = __ldg(&S->es_base) + 2 * K * f, es1 = es0 + K;
     const int vs0 = __ldg(G.edge_vs + e), vs1 = __ldg(G.edge_vs + e + 1);
     const float *phi = shared ? tab : pot + pot_base + (size_t)f * (K * K);
+    const float tmax = linear ? tinfo[0] : 0.f;
     float mo0[K], mo1[K];
     load_n_stream<K>(mo0, m_old + es0);
     load_n_stream<K>(mo1, m_old + es1);
@@ -1708,7 +1709,6 @@ k_pair_thr(DevGraph G, const EnumSeg *__restrict__ segs, int n_seg, const float 
                                   m_new, vs0, vs1, es0, es1, T, invT, damping);
         return;
     }
-    const float tmax = linear ? tinfo[0] : 0.f;
     float v[K], o[K];
     // to variable 0: rows of phi against v1 = b1 - m1
     load_n<K>(v, b + vs1);
@@ -3260,15 +3260,19 @@ __global__ void __launch_bounds__(256) k_adj_pot_reduce(const EnumSeg *__restric
 // block; fpb factors per block; configuration tables read in place). Per factor: the
 // variable-to-factor values (enum_team_v2f); each output's forward value lm = LSE_T over
 // its configurations (ascending, as k_adj_factor); a warp per edge reverses
-// normalise - damp - normalise into gam and ddamp; each output then walks its
-// configurations again and adds gam e^((s - lm) / T) to the configuration's
-// log-potential gradient (global atomics) and to the other neighbours' variable-to-factor
-// adjoints (shared-memory atomics), which are written to dv2f at the end.
+// normalise - damp - normalise into gam and ddamp; then gathers in a fixed order: each
+// output state walks its configurations and sums the other edges' weights into its
+// variable-to-factor adjoint, and each configuration sums its edges' weights into the
+// log-potential gradient -- the factor's own table directly, a shared table into the
+// team's row of `partials` (team w of block b at (8 b + w) nc_max), which
+// k_adj_block_reduce adds to d_pot in order. So the gradient is the same on every run
+// (with `partials` null, shared tables fall back to atomic adds).
 __global__ void __launch_bounds__(kEnumBlockThreads)
 k_adj_block(DevGraph G, const EnumSeg *__restrict__ segs, int n_seg, const float *__restrict__ pot,
             const float *__restrict__ b, const float *__restrict__ ev, const float *__restrict__ m_old,
             const float *__restrict__ adj, float *__restrict__ dv2f, float *__restrict__ ddamp,
-            float *__restrict__ d_pot, float T, float invT, float damping) {
+            float *__restrict__ d_pot, float *__restrict__ partials, int nc_max, float T, float invT,
+            float damping) {
     pdl_wait();  // inputs of the previous launch
     pdl_launch_dependents();  // the next launch may be scheduled (it waits likewise)
     extern __shared__ __align__(16) float ab_smem[];
@@ -3387,32 +3391,82 @@ k_adj_block(DevGraph G, const EnumSeg *__restrict__ segs, int n_seg, const float
             if (lane == 0) gam[o + a1] -= sn;
         }
         team_barrier(wteam);
-        // (4) back through the log-sum-exp: log-potentials and variable-to-factor values
+        // (4) back through the log-sum-exp, as gathers in a fixed order (no atomics): the
+        // weight of configuration c seen from output o = (j, c_j) is
+        // w_j(c) = gam[o] e^((s_j(c) - lm[o]) / T). (4a) The variable-to-factor adjoint of
+        // state t of edge k sums w_j(c) over the configurations with c_k = t -- the list of
+        // output t -- and the other edges j.
+        auto weight = [&](int oj, float sv) -> float {
+            if (lm[oj] == kNegInf || sv == kNegInf) return 0.f;
+            return gam[oj] * expf((sv - lm[oj]) * invT);
+        };
         for (int o = trank; o < ksum; o += tsize) {
-            if (lm[o] == kNegInf) continue;
-            int j = 0;
-            for (int k = 1; k < a; ++k)
-                if (o >= sKo[k]) j = k;
-            const float go = gam[o], lo = lm[o];
+            int k = 0;
+            for (int q = 1; q < a; ++q)
+                if (o >= sKo[q]) k = q;
+            float acc = 0.f;
             for (int i = __ldg(bs + o); i < __ldg(bs + o + 1); ++i) {
                 const int ent = __ldg(lst + i);
-                int c;
-                const float sv = value(o, j, ent, c);
-                if (sv == kNegInf) continue;
-                const float w = go * expf((sv - lo) * invT);
-                atomicAdd(dphi + c, w);
-                if (packed) {
-                    atomicAdd(dv + (ent & 2047), w);
+                if (packed) {  // the other edge's output: its state offset is in the entry
+                    const int oj = ent & 2047;
+                    acc += weight(oj, __ldg(phi + (ent >> 11)) + v2f[o]);
                 } else {
-                    const uint8_t *cc = cfg + (size_t)c * a;
-                    for (int k = 0; k < a; ++k)
-                        if (k != j) atomicAdd(dv + sKo[k] + __ldg(cc + k), w);
+                    const uint8_t *cc = cfg + (size_t)ent * a;
+                    for (int j = 0; j < a; ++j) {
+                        if (j == k) continue;
+                        const int oj = sKo[j] + __ldg(cc + j);
+                        int c;
+                        acc += weight(oj, value(oj, j, ent, c));
+                    }
                 }
+            }
+            dv[o] = acc;
+        }
+        // (4b) the log-potential gradient of configuration c sums w_j(c) over the edges j
+        const bool own = partials == nullptr || !shared;
+        float *prow = own ? nullptr : partials + ((size_t)blockIdx.x * (kEnumBlockThreads / 32) + team) * nc_max;
+        const bool first = (f == f0 + team);  // this team's first factor of the launch
+        for (int c = trank; c < nc; c += tsize) {
+            const uint8_t *cc = cfg + (size_t)c * a;
+            float dc = 0.f;
+            for (int j = 0; j < a; ++j) {
+                const int oj = sKo[j] + __ldg(cc + j);
+                int cx;
+                dc += weight(oj, value(oj, j, packed ? ((c << 11) | (sKo[1 - j] + __ldg(cc + 1 - j))) : c, cx));
+            }
+            if (own) {
+                if (partials == nullptr && shared) atomicAdd(dphi + c, dc);  // no scratch: atomics
+                else dphi[c] += dc;  // the factor's own table, only this lane writes c
+            } else {
+                prow[c] = first ? dc : prow[c] + dc;  // the team's row, added over its factors in order
             }
         }
         team_barrier(wteam);
         for (int t = trank; t < ksum; t += tsize) dv2f[es_f + t] = dv[t];
         team_barrier(wteam);  // v2f / lm / dv are reused by the team's next factor
+    }
+}
+
+// Adds k_adj_block's team rows of the log-potential gradients of shared tables to d_pot:
+// block = group record, thread = configuration; the group's blocks in order, and in each
+// block the teams that had a factor, in order.
+__global__ void __launch_bounds__(256) k_adj_block_reduce(const EnumSeg *__restrict__ segs, int n_seg,
+                                                          const float *__restrict__ partials, int nc_max,
+                                                          float *__restrict__ d_pot) {
+    pdl_wait();  // inputs of the previous launch
+    pdl_launch_dependents();  // the next launch may be scheduled (it waits likewise)
+    const EnumSeg *S = segs + blockIdx.x;
+    if (!S->shared || S->n_fac == 0) return;
+    const int teams = S->es_per_fac <= kEnumWarpStateSum ? kEnumBlockThreads / 32 : 1;
+    const int n_blk = (S->n_fac + S->fpb - 1) / S->fpb;
+    for (int c = threadIdx.x; c < S->n_cfg; c += blockDim.x) {
+        float sum = 0.f;
+        for (int bl = 0; bl < n_blk; ++bl) {
+            const int nf = min(S->fpb, S->n_fac - bl * S->fpb);  // factors of this block
+            for (int t = 0; t < min(teams, nf); ++t)
+                sum += partials[((size_t)(S->block_begin + bl) * (kEnumBlockThreads / 32) + t) * nc_max + c];
+        }
+        d_pot[S->pot_base + c] += sum;
     }
 }
 
@@ -4701,7 +4755,10 @@ cudaError_t launch_adj_factor(const DevGraph &G, const FactorLaunch &L, const fl
     if (L.n_blocks == 0) return cudaSuccess;
     if (L.variant == kEnumBlock) {
         launch_dep(k_adj_block, dim3(L.n_blocks), L.threads, L.smem, s, G, static_cast<const EnumSeg *>(L.segs), L.n_seg, pot, b, ev,
-                                                          m_old, adj, dv2f, ddamp, d_pot, T, 1.f / T, damping);
+                   m_old, adj, dv2f, ddamp, d_pot, partials, nc_max, T, 1.f / T, damping);
+        if (partials != nullptr)
+            launch_dep(k_adj_block_reduce, dim3(L.n_seg), 256, 0, s, static_cast<const EnumSeg *>(L.segs), L.n_seg,
+                       partials, nc_max, d_pot);
     } else {
         launch_dep(k_adj_factor, dim3(L.n_blocks), L.threads, 0, s, G, static_cast<const EnumSeg *>(L.segs), L.n_seg, pot, b, ev,
                                                       m_old, adj, dv2f, ddamp, d_pot, partials, nc_max, T, 1.f / T,
