@@ -2553,11 +2553,21 @@ __device__ __forceinline__ void write_logic_edge(float o, const float2 mo, float
         t[1] = o;
     }
     finish_k<2>(t, old, damping, flags);
-    m_new[es] = t[0];
-    m_new[es + 1] = t[1];
+    float *q = m_new + es;
+    if ((reinterpret_cast<uintptr_t>(q) & 7u) == 0) {
+        *reinterpret_cast<float2 *>(q) = make_float2(t[0], t[1]);
+    } else {
+        q[0] = t[0];
+        q[1] = t[1];
+    }
 }
 
-__device__ __forceinline__ float2 ld2(const float *p) { return make_float2(__ldg(p), __ldg(p + 1)); }
+// Two consecutive floats: one 8-byte load when the address allows it (edge-states of
+// binary edges start on even offsets when every edge before them is binary), else two.
+__device__ __forceinline__ float2 ld2(const float *p) {
+    if ((reinterpret_cast<uintptr_t>(p) & 7u) == 0) return __ldg(reinterpret_cast<const float2 *>(p));
+    return make_float2(__ldg(p), __ldg(p + 1));
+}
 
 // Incoming log-odds of one edge (times sgn) and its stored message.
 __device__ __forceinline__ float edge_logodds(const DevGraph &G, const float *ev, const float *b,
