@@ -1118,6 +1118,15 @@ def run_ours(args):
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                                 "sample": f"{args.cpu_iters} iterations at T=1 and {args.cpu_iters} at T=0 on the "
                                           f"full {args.side}x{args.side} grid, FP64, {dt:.1f} s"}
+        # the same oracle on one core (a quarter of the sample), for the per-core rate
+        import oracle
+        n_all = oracle.num_threads()
+        oracle.set_num_threads(1)
+        v1, dt1, _ = cpu_sample(p, max(1, args.cpu_iters // 4))
+        oracle.set_num_threads(n_all)
+        line["cpu_baseline"]["single_core"] = {"value": v1, "unit": UNIT, "cores": 1,
+                                               "sample": f"{max(1, args.cpu_iters // 4)} iterations per T, "
+                                                         f"FP64, {dt1:.1f} s"}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:

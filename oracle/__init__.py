@@ -85,6 +85,8 @@ def _load():
                                 ctypes.c_double, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                                 ctypes.c_void_p]
         lib.og_num_threads.restype = ctypes.c_int
+        lib.og_set_num_threads.restype = ctypes.c_int
+        lib.og_set_num_threads.argtypes = [ctypes.c_int]
         _lib = lib
     return _lib
 
@@ -232,3 +234,9 @@ def loss(graph, log_pot, evidence, T, damping, n_iters, g_nb) -> float:
 
 def num_threads() -> int:
     return int(_load().og_num_threads())
+
+
+def set_num_threads(n: int) -> int:
+    """OpenMP threads of the following calls (timing only; results do not depend on it).
+    Returns the count in effect."""
+    return int(_load().og_set_num_threads(int(n)))

@@ -674,6 +674,19 @@ int og_num_threads(void) {
 #endif
 }
 
+/* Threads of the following calls (n >= 1; timing only: every result is independent of
+ * the thread count, each factor and variable being computed by one thread). Returns the
+ * count in effect. */
+int og_set_num_threads(int n) {
+#ifdef _OPENMP
+    if (n >= 1) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
+}
+
 /* ---- adjoint (gradient) -------------------------------------------------------------- */
 
 /* argmax over K values, lowest index on ties */

@@ -1325,20 +1325,30 @@ k_pair(DevGraph G, const EnumSeg *__restrict__ segs, int n_seg, const float *__r
     float mo0[K], mo1[K];
     load_n<K>(mo0, m_old + es0);
     load_n<K>(mo1, m_old + es1);
-    bool rare = (vs0 < 0) | (vs1 < 0);
+    // an edge of a high-degree variable is exact from its variable's totals (hd_v2f);
+    // only a large or -inf stored entry of another edge takes the out-of-line path
+    bool rare = false;
 #pragma unroll
-    for (int x = 0; x < K; ++x) rare |= needs_exact(mo0[x]) | needs_exact(mo1[x]);
+    for (int x = 0; x < K; ++x)
+        rare |= (vs0 >= 0 && needs_exact(mo0[x])) | (vs1 >= 0 && needs_exact(mo1[x]));
     if (rare) {
         pair_factor_rare<K, MAXP>(G, phi_sh, phi_g, b, ev, m_old, m_new, vs0, vs1, es0, es1, T, invT, damping);
         return;
     }
     float v0[K], v1[K];
-    load_n<K>(v0, b + vs0);
-    load_n<K>(v1, b + vs1);
+    if (vs0 < 0) {
+        hd_v2f<K>(G, vs0, mo0, v0);
+    } else {
+        load_n<K>(v0, b + vs0);
 #pragma unroll
-    for (int x = 0; x < K; ++x) {
-        v0[x] -= mo0[x];
-        v1[x] -= mo1[x];
+        for (int x = 0; x < K; ++x) v0[x] -= mo0[x];
+    }
+    if (vs1 < 0) {
+        hd_v2f<K>(G, vs1, mo1, v1);
+    } else {
+        load_n<K>(v1, b + vs1);
+#pragma unroll
+        for (int x = 0; x < K; ++x) v1[x] -= mo1[x];
     }
     pair_update<K, MAXP>(phi_sh, phi_g, v0, v1, mo0, mo1, m_new + es0, m_new + es1, T, invT, damping, G.flags,
                          linear ? tabE : nullptr, linear ? tinfo[0] : 0.f);
