@@ -2,14 +2,15 @@
 //
 // Method (PGMax, arXiv 2202.04110): log-space loopy belief propagation with parallel
 // updates and damping (Sec. 3), enumeration factors over listed configurations
-// (Sec. 5.2), OR / AND factors with updates linear in the fan-in (Sec. 3), flat
-// message arrays updated by gather / scatter (Sec. 4), MAP decode (Sec. 5.1).
+// (Sec. 5.2), logical factors with updates linear in the fan-in (Sec. 3: OR, AND and,
+// as the third kind, XOR), flat message arrays updated by gather / scatter (Sec. 4), MAP
+// decode (Sec. 5.1).
 //
 // One iteration is two passes over HBM-resident flat arrays:
 //   variable pass  b_v = e_v + sum_{f in N(v)} m_{f->v}            (k_var_*)
 //   factor pass    m_{v->f} = b_v - m_{f->v}   (gathered per edge)
 //                  mt_{f->i} = factor update (LSE_T over configurations, or the
-//                              closed-form OR / AND update)
+//                              closed-form logical update)
 //                  m_{f->i} <- norm(delta * m_{f->i} + (1 - delta) * norm(mt_{f->i}))
 //                  written to the other buffer of a ping-pong pair   (k_pair, k_enum_generic,
 //                                                                     k_logic_small, k_logic_warp)
@@ -29,7 +30,11 @@
 // belief residuals (variables of more than 16 states, logical factors) and for finite
 // entries, from (b - m) + b_lo, b_lo being what the rounding of b dropped, written by the
 // variable pass for every variable that has such an entry; edges of variables with more
-// than kVarBlockDegree factors always take the exact sums of the block variable pass.
+// than kVarBlockDegree factors always take the exact value from the variable's per-state
+// totals of finite entries and counts of -inf ones (hd_pair).
+//
+// Launches: the iteration's kernels go out with programmatic dependent launch (each
+// waits, pdl_wait, before touching memory), inside CUDA graphs when the graph allows.
 #include <algorithm>
 #include <cstdint>
 

@@ -104,3 +104,19 @@ def test_star_multi_sample_equals_single(gpu, T):
         ms = G.new_msgs()
         G.run_bp(lpt, torch.as_tensor(evs[s]).cuda(), T, 0.5, 7, ms)
         assert torch.equal(ms, m[s]), s
+
+
+@pytest.mark.parametrize("n_leaves", [64, 65, 2048, 2049, 4097])
+def test_star_degree_boundaries(gpu, n_leaves):
+    """Hub degrees at the boundaries: 64 (thread per variable) and 65 (high-degree
+    pass), one tile of 2048 edges exactly, one edge into a second tile, and three tiles
+    with a one-edge tail; binary and 3-state hubs, T = 0 and 1."""
+    for K in (2, 3):
+        g, lp, ev = _star(n_leaves, K, seed=n_leaves + K, p_zero=0.2, leaf_zero=0.1)
+        for T in (0.0, 1.0):
+            _, m, nb, dec, flags = _run(gpu, g, lp, ev, T, 5)
+            om, ofl = oracle.run_bp(g, lp, ev, T, 0.5, 5)
+            _, onb, _, ofl2 = oracle.beliefs(g, ev, om)
+            assert_beliefs_close(nb, onb, what=f"star {n_leaves} K={K} T={T}")
+            assert_decode_ok(dec, onb, g.num_states, what=f"star {n_leaves} K={K} T={T}")
+            assert bool(flags & 1) == bool((ofl | ofl2) & 1)

@@ -186,3 +186,19 @@ def test_xor_gradient_not_supported(gpu):
         g.grad(torch.as_tensor(lp).cuda(), torch.as_tensor(ev).cuda(), 1.0, 0.5, 4, 2,
                torch.zeros(ev.size, device="cuda"))
     assert ei.value.status == -4
+
+
+def test_xor_empty_and_single_factor_groups(gpu):
+    """A group with no factors next to XOR groups of one factor (fan-in 0 and 1): the
+    compiler keeps the empty group out of the launches, and the others match the oracle."""
+    fg0, lp0, ev0 = _xor_graph([0], seed=21)
+    fg1, lp1, ev1 = _xor_graph([1], seed=22)
+    groups = [W.LogicGroup(W.XOR, np.array([0], np.int32), np.zeros(0, np.int32), np.zeros(0, np.int32))]
+    groups += fg0.logic_groups
+    g1 = fg1.logic_groups[0]
+    n0 = fg0.num_states.size
+    groups.append(W.LogicGroup(W.XOR, g1.par_off, g1.parents + n0, g1.child + n0))
+    fg = W.FactorGraph(np.concatenate([fg0.num_states, fg1.num_states]), [], groups)
+    ev = np.concatenate([ev0, ev1])
+    for T in (0.0, 1.0):
+        _check(gpu, fg, np.zeros(0, np.float32), ev, T, 0.5, 3, f"xor small groups T={T}")
