@@ -1,6 +1,6 @@
 """Seeded random graphs that mix every kind of group the compiler knows -- dense pairwise
 tables of mixed state counts, listed triple factors, OR / AND / XOR factors of fan-in
-0..6 and one wide enough for the warp kernel, a hub with more than 64 factors, hard
+1..6 and one wide enough for the warp kernel, a hub with more than 64 factors, hard
 evidence -- against the FP64 oracle (short horizon, strict 1e-4), and in one batch
 against the same graphs run alone (bitwise).
 """
@@ -29,7 +29,7 @@ def mixed_graph(seed: int):
     """80 variables (K in {2, 3, 5}), pairwise groups per state-count signature (dense
     tables, shared or per factor), one listed triple group, a binary hub joined to 70
     binary variables, logical groups over the binary variables, hard evidence on a tenth
-    of the variables."""
+    of the variables (multi-state ones)."""
     rng = np.random.default_rng(seed)
     n = 80
     K = rng.choice([2, 2, 3, 5], size=n).astype(np.int32)
@@ -71,7 +71,9 @@ def mixed_graph(seed: int):
     logic = []
     for kind in (W.OR, W.AND, W.XOR):
         offs, pars, ch = [0], [], []
-        fans = list(rng.integers(0, 7, size=4)) + ([40] if kind == W.OR else [])
+        # fan-in 1..6 (a factor of no parents forces its child, and two such factors of
+        # different kinds on one child are the undefined case above; tested elsewhere)
+        fans = list(rng.integers(1, 7, size=4)) + ([40] if kind == W.OR else [])
         for fan in fans:
             sel = rng.choice(binary[1:], size=min(int(fan) + 1, binary.size - 1), replace=False)
             pars.extend(int(x) for x in sel[:-1])
@@ -82,7 +84,11 @@ def mixed_graph(seed: int):
     g = W.FactorGraph(K, enum, logic)
     ev = rng.normal(0, 1, int(K.sum()))
     off = np.concatenate([[0], np.cumsum(K)])
-    for v in rng.choice(n, n // 10, replace=False):  # hard evidence: one state off
+    # hard evidence (one state off) on a tenth of the variables, the multi-state ones: the
+    # logical factors then see finite log-odds (two certain inputs of opposite sense would
+    # make an OR update inf - inf, a case the method leaves undefined)
+    multi = np.flatnonzero(K > 2)
+    for v in rng.choice(multi, min(n // 10, multi.size), replace=False):
         ev[off[v] + rng.integers(0, K[v])] = -np.inf
     return g, np.concatenate(pots).astype(np.float32), ev.astype(np.float32)
 
