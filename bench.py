@@ -713,27 +713,35 @@ def measure_small(args, binding, W, torch, dev):
     damping 0.5, 50 iterations: CUDA events around 200 back-to-back pgm_run_bp calls (one
     CUDA graph replay each), and the FP64 oracle's time for the same run on the host."""
     p = W.ising_small(0)
-    g = binding.Graph(p.graph)
     lp = torch.as_tensor(p.log_pot).to(dev)
     ev = torch.as_tensor(p.evidence).to(dev)
-    m = g.new_msgs()
     stream = torch.cuda.current_stream()
-    for _ in range(10):
-        g.run_bp(lp, ev, 1.0, 0.5, p.n_iters, m)
-    torch.cuda.synchronize()
-    reps = 200
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(reps):
-        g.run_bp(lp, ev, 1.0, 0.5, p.n_iters, m)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    t = e0.elapsed_time(e1) / 1e3 / reps
+
+    def per_run(small):
+        g = binding.Graph(p.graph)
+        g.set_option(binding.OPT_SMALL_RUN, small)
+        m = g.new_msgs()
+        for _ in range(10):
+            g.run_bp(lp, ev, 1.0, 0.5, p.n_iters, m)
+        torch.cuda.synchronize()
+        reps = 200
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            g.run_bp(lp, ev, 1.0, 0.5, p.n_iters, m)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        launches = 1 if g.get_option(binding.OPT_SMALL_RUN) else p.n_iters * g.info["launches_per_iter"] + 3
+        return e0.elapsed_time(e1) / 1e3 / reps, launches, g.info["n_edge_states"]
+
+    t, launches, n_es = per_run(1)  # the default: one block runs the whole run
+    t_multi, launches_multi, _ = per_run(0)
     out = {"workload": "ising10x10, T=1, damping 0.5, 50 iterations", "us_per_run": round(1e6 * t, 2),
            "us_per_iteration": round(1e6 * t / p.n_iters, 3),
-           "value": p.n_iters * g.info["n_edge_states"] / t, "unit": UNIT,
-           "launches_per_run": p.n_iters * g.info["launches_per_iter"] + 3}
+           "value": p.n_iters * n_es / t, "unit": UNIT, "launches_per_run": launches,
+           "multi_launch": {"us_per_run": round(1e6 * t_multi, 2), "launches_per_run": launches_multi,
+                            "note": "PGM_OPT_SMALL_RUN 0: two launches per iteration"}}
     if not args.no_cpu_baseline:
         import oracle
         oracle.build()

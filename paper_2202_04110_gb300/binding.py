@@ -32,6 +32,7 @@ OPT_LOG_RATIO = 2
 OPT_ENUM_BLOCK = 3
 OPT_PAIR_FORM = 4
 OPT_CHECKED = 5
+OPT_SMALL_RUN = 6
 
 
 class PgmError(RuntimeError):

@@ -168,6 +168,7 @@ struct pgm_graph {
     double graph_var_ms = 0.0, graph_factor_ms = 0.0;  // summed over the sampled passes
     int32_t use_cuda_graph = 1;
     int32_t log_ratio_min_iters = 4;  // PGM_OPT_LOG_RATIO
+    int32_t small_run = 1;            // PGM_OPT_SMALL_RUN
     cudaStream_t capture_stream = nullptr;
     std::vector<CachedRun> runs;
     // pgm_grad as CUDA graphs (PGM_OPT_CUDA_GRAPH): persistent work buffers and the
@@ -928,6 +929,12 @@ static bool log_ratio_run(const pgm_graph *g, int32_t n_iters) {
     return g->P.lr && !g->force_es && g->log_ratio_min_iters > 0 && n_iters >= g->log_ratio_min_iters;
 }
 
+// A log-ratio run of this graph goes to the single-block kernel (k_lr_small): the option
+// is on and the graph has the 4-slot layout and fits the kernel's limits.
+static bool small_run_used(const pgm_graph *g) {
+    return g->small_run != 0 && g->P.lr && g->G.vin_tab4 != nullptr && lr_small_fits(g->G.V, g->G.E / 2);
+}
+
 static pgm_status enqueue_iterations(pgm_graph *g, const float *log_pot, const float *evidence, float T,
                                      float damping, int32_t n_iters, float *msgs, cudaStream_t s,
                                      bool profile) {
@@ -937,6 +944,12 @@ static pgm_status enqueue_iterations(pgm_graph *g, const float *log_pot, const f
     // binary graph), which log-ratio iterations do not otherwise use
     float *d = g->lr_d, *lam = g->lr_lam;
     float2 *Dv = reinterpret_cast<float2 *>(g->b);
+    // a small graph: the whole run in one launch (per-pass profiling keeps the passes)
+    if (lr && small_run_used(g) && !(profile && g->profiling > 0)) {
+        cudaError_t e = launch_lr_small_run(g->G, g->P, log_pot, evidence, msgs, lam, T, damping, n_iters, s);
+        if (e != cudaSuccess) return cuda_fail(e, "small-graph run launch");
+        return PGM_OK;
+    }
     if (lr) {
         cudaError_t e = launch_lr_pack(g->G, msgs, d, s);
         if (e == cudaSuccess) e = launch_lr_params(g->G, g->P, log_pot, g->lr_prm, s);
@@ -2163,6 +2176,11 @@ pgm_status pgm_set_option(pgm_graph *g, int32_t option, int64_t value) {
             if (value != g->log_ratio_min_iters) drop_cached_runs(g);
             g->log_ratio_min_iters = (int32_t)value;
             return PGM_OK;
+        case PGM_OPT_SMALL_RUN:
+            if (value != 0 && value != 1) return fail(PGM_EINVAL, "PGM_OPT_SMALL_RUN must be 0 or 1");
+            if (value != g->small_run) drop_cached_runs(g);
+            g->small_run = (int32_t)value;
+            return PGM_OK;
         case PGM_OPT_ENUM_BLOCK: {
             if (value != 0 && value != 1) return fail(PGM_EINVAL, "PGM_OPT_ENUM_BLOCK must be 0 or 1");
             DeviceGuard dg(g->device);
@@ -2249,6 +2267,9 @@ pgm_status pgm_get_option(const pgm_graph *g, int32_t option, int64_t *value) {
             return PGM_OK;
         case PGM_OPT_CHECKED:
             *value = g->checked;
+            return PGM_OK;
+        case PGM_OPT_SMALL_RUN:
+            *value = small_run_used(g) ? 1 : 0;
             return PGM_OK;
         default:
             return fail(PGM_EINVAL, "unknown option");
