@@ -63,6 +63,8 @@ def parse_args():
                     help="only run the batched workload for N iterations (3 runs, no CUDA graphs; for ncu)")
     ap.add_argument("--deconv-probe", type=int, default=0,
                     help="only run the deconvolution workload for N iterations (3 runs, no CUDA graphs; for ncu)")
+    ap.add_argument("--small-probe", type=int, default=0,
+                    help="only run N runs of the 10x10 grid workload (50 iterations, T=1, one launch each; for ncu)")
     ap.add_argument("--grad-probe", type=int, default=0,
                     help="run only N gradient calls of the gradient workload, CUDA graphs off (for ncu)")
     ap.add_argument("--pair-form", type=int, default=0,
@@ -1195,6 +1197,28 @@ def deconv_probe(args):
                       "launch_shapes": g.launches()}))
 
 
+def small_probe(args):
+    """`--small-probe N` runs of the 10x10 Ising workload (T=1, damping 0.5, 50
+    iterations: one k_lr_small launch each), CUDA graphs off, for ncu captures of the
+    single-block run. Prints one JSON line."""
+    import torch
+    from paper_2202_04110_gb300 import binding, build
+    from paper_2202_04110_gb300 import workloads as W
+    build.build()
+    p = W.ising_small(0)
+    lp = torch.as_tensor(p.log_pot).cuda()
+    ev = torch.as_tensor(p.evidence).cuda()
+    g = binding.Graph(p.graph)
+    g.set_option(binding.OPT_CUDA_GRAPH, 0)
+    m = g.new_msgs()
+    for _ in range(args.small_probe):
+        m.zero_()
+        g.run_bp(lp, ev, 1.0, 0.5, p.n_iters, m)
+    torch.cuda.synchronize()
+    print(json.dumps({"small_probe": args.small_probe, "small_run": g.get_option(binding.OPT_SMALL_RUN),
+                      "n_edge_states": g.info["n_edge_states"]}))
+
+
 def grad_probe(args):
     """`--grad-probe N` gradient calls of the gradient workload (64x64 Ising, T=1, damping
     0.5, 100 iterations, a checkpoint every 10), CUDA graphs off, for an ncu launch list of
@@ -1250,6 +1274,8 @@ def main():
         batch_probe(args)
     elif args.grad_probe:
         grad_probe(args)
+    elif args.small_probe:
+        small_probe(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

@@ -4393,9 +4393,10 @@ __global__ void k_until_control(cudaGraphConditionalHandle h, const unsigned *__
 // k_lr_pack_slot4), forms its factors' table numbers in registers (as k_lr_params), runs
 // every iteration with block barriers between the steps, and writes the messages back (as
 // k_lr_unpack). Per iteration a variable pass (thread t owns variable t; the totals Dv in
-// shared memory) and a factor pass (thread t owns factors t and t + n_t, whose slot pairs
-// and table numbers it keeps in registers for the whole run), with a block barrier after
-// each. A thread loads both factors' shared-memory inputs before it computes and stores
+// shared memory) and a factor pass (thread t owns factor t, or factors t and t + n_t when
+// there are more factors than a block has threads, and keeps their slot pairs and table
+// numbers in registers for the whole run), with a block barrier after each. A thread with
+// two factors loads both factors' shared-memory inputs before it computes and stores
 // either (a factor's slots belong to that factor alone), so their latencies overlap. The
 // per-item arithmetic is that of k_var_slot4_lr and k_pair2_lr step for step, so the
 // messages are bitwise those of the multi-launch run. A variable on the explicit-sum path
@@ -4488,7 +4489,7 @@ __device__ __forceinline__ void lr_small_var(float2 e, const float (&dk)[4], int
     *Dv = make_float2(__uint_as_float(kDvSlow), 0.f);
 }
 
-template <bool MAXP>
+template <bool MAXP, int NF>
 __global__ void __launch_bounds__(kLrSmallThreads)
 k_lr_small(DevGraph G, const EnumSeg *__restrict__ segs, int n_seg, const float *__restrict__ pot,
             const float *__restrict__ ev, float *__restrict__ msgs, float *__restrict__ lam, float k, float Tln2,
@@ -4499,9 +4500,9 @@ k_lr_small(DevGraph G, const EnumSeg *__restrict__ segs, int n_seg, const float 
     float *d = lr_sm + 2 * (size_t)V;                // 4 V floats
     lr_small_pack(G, msgs, d);
     const float2 e = tid < V ? __ldg(reinterpret_cast<const float2 *>(ev) + tid) : make_float2(0.f, 0.f);
-    LrSmallFactor f[2];
+    LrSmallFactor f[NF];
 #pragma unroll
-    for (int j = 0; j < 2; ++j) f[j] = lr_small_factor(G, segs, n_seg, pot, tid + j * nt, F);
+    for (int j = 0; j < NF; ++j) f[j] = lr_small_factor(G, segs, n_seg, pot, tid + j * nt, F);
     const float w = 1.f - damping;
     __syncthreads();
     for (int it = 0; it < n_iters; ++it) {
@@ -4512,10 +4513,10 @@ k_lr_small(DevGraph G, const EnumSeg *__restrict__ segs, int n_seg, const float 
             lr_small_var(e, dk, tid, V, Dv + tid, lam);
         }
         __syncthreads();
-        float mo0[2], mo1[2];  // factor pass (k_pair2_lr<MAXP, true>)
-        float2 D0[2], D1[2];
+        float mo0[NF], mo1[NF];  // factor pass (k_pair2_lr<MAXP, true>)
+        float2 D0[NF], D1[NF];
 #pragma unroll
-        for (int j = 0; j < 2; ++j) {
+        for (int j = 0; j < NF; ++j) {
             const int2 p = f[j].p;
             mo0[j] = d[p.x];
             mo1[j] = d[p.y];
@@ -4523,7 +4524,7 @@ k_lr_small(DevGraph G, const EnumSeg *__restrict__ segs, int n_seg, const float 
             D1[j] = Dv[p.y - V * ((p.y >= V) + (p.y >= 2 * V) + (p.y >= 3 * V))];
         }
 #pragma unroll
-        for (int j = 0; j < 2; ++j) {
+        for (int j = 0; j < NF; ++j) {
             const int g = tid + j * nt;
             if (g >= F) continue;
             const int2 p = f[j].p;
@@ -4913,13 +4914,15 @@ cudaError_t launch_lr_small_run(const DevGraph &G, const Plan &P, const float *l
     const float Tln2 = (float)((double)T * 0.6931471805599453);
     const int F = G.E / 2, V = G.V;
     if (!lr_small_fits(V, F) || G.vin_tab4 == nullptr || G.lr_pos == nullptr) return cudaErrorInvalidValue;
-    // one variable and two factors per thread at most
-    const int per = std::max(V, (F + 1) / 2);
+    // one variable and one factor per thread where a block holds them, else two factors
+    const bool one = F <= kLrSmallThreads;
+    const int per = one ? std::max(V, F) : std::max(V, (F + 1) / 2);
     const int threads = std::max(32, ((per + 31) / 32) * 32);
     const size_t smem = (size_t)V * 6 * sizeof(float);
     for (const FactorLaunch &L : P.factor) {  // the one kPair2 launch: every factor
         if (L.n_blocks == 0 || n_iters <= 0) continue;
-        auto kern = T == 0.f ? k_lr_small<true> : k_lr_small<false>;
+        auto kern = T == 0.f ? (one ? k_lr_small<true, 1> : k_lr_small<true, 2>)
+                             : (one ? k_lr_small<false, 1> : k_lr_small<false, 2>);
         kern<<<1, threads, smem, s>>>(G, static_cast<const EnumSeg *>(L.segs), L.n_seg, log_pot, ev, msgs, lam, k,
                                       Tln2, damping, n_iters);
     }

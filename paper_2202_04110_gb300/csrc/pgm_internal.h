@@ -298,8 +298,9 @@ cudaError_t launch_pmp_perturb(int64_t VS, int S, const float *ev, const float *
 cudaError_t launch_lr_pack(const DevGraph &G, const float *m, float *d, cudaStream_t s);
 cudaError_t launch_lr_unpack(const DevGraph &G, const float *d, float *m, cudaStream_t s);
 // One block runs a whole log-ratio run of a small graph (4-slot layout, at most
-// kLrSmallMaxV variables and kLrSmallMaxF factors: one variable and two factors per
-// thread at most; 24 V bytes of shared memory), msgs in and out.
+// kLrSmallMaxV variables and kLrSmallMaxF factors: one variable and one factor per
+// thread, or two factors above kLrSmallThreads of them; 24 V bytes of shared memory),
+// msgs in and out.
 constexpr int kLrSmallThreads = 1024, kLrSmallMaxV = 1024, kLrSmallMaxF = 2048;
 inline bool lr_small_fits(int V, int F) { return V > 0 && V <= kLrSmallMaxV && F <= kLrSmallMaxF; }
 cudaError_t launch_lr_small_run(const DevGraph &G, const Plan &P, const float *log_pot, const float *ev,
