@@ -523,7 +523,8 @@ pgm_status pgm_run_bp_until_members(pgm_graph *g, const float *log_pot, const fl
  * each pass, and writes msgs back, instead of 2 launches per iteration plus 3. The
  * arithmetic per variable and per factor is that of the multi-launch iterations, so the
  * messages and flags are bitwise the same. 0 turns it off. Per-pass profiling
- * (pgm_set_profiling) keeps the multi-launch form. Changing it drops the cached CUDA
+ * (pgm_set_profiling) keeps the multi-launch form, which is also the one that
+ * launches_per_iter and pgm_launch_info describe. Changing it drops the cached CUDA
  * graphs. pgm_get_option returns 1 where a log-ratio run of the graph takes this form,
  * else 0. Values other than 0 and 1: PGM_EINVAL.
  */
