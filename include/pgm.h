@@ -517,25 +517,29 @@ pgm_status pgm_run_bp_until_members(pgm_graph *g, const float *log_pot, const fl
 #define PGM_OPT_CHECKED 5
 /*
  * PGM_OPT_SMALL_RUN (default 1): a log-ratio run (PGM_OPT_LOG_RATIO) of a graph whose
- * variables have at most 4 factors each, with at most 1,024 variables and 2,048 factors,
- * is one kernel launch: one thread block converts msgs, runs every iteration with the
- * exchanged arrays in shared memory (24 bytes per variable) and a block barrier after
- * each pass, and writes msgs back, instead of 2 launches per iteration plus 3. The
- * arithmetic per variable and per factor is that of the multi-launch iterations, so the
- * messages and flags are bitwise the same. 0 turns it off. Per-pass profiling
- * (pgm_set_profiling) keeps the multi-launch form, which is also the one that
+ * variables have at most 4 factors each is one kernel launch: one thread block for at most
+ * 700 variables (and 2,048 factors), else a cluster of 8 thread blocks on 8 SMs, whose
+ * shared memories together hold the run's state, for at most 8,192 variables and 16,384
+ * factors (where the device can place such a cluster). 2 takes the cluster at every size
+ * up to its limits. The launch converts msgs, runs
+ * every iteration with the exchanged arrays in shared memory (24 bytes per variable) and a
+ * block or cluster barrier after each pass, and writes msgs back, instead of 2 launches per
+ * iteration plus 3. The arithmetic per variable and per factor is that of the multi-launch
+ * iterations, so the messages and flags are bitwise the same. 0 turns it off. Per-pass
+ * profiling (pgm_set_profiling) keeps the multi-launch form, which is also the one that
  * launches_per_iter and pgm_launch_info describe. Changing it drops the cached CUDA
- * graphs. pgm_get_option returns 1 where a log-ratio run of the graph takes this form,
- * else 0. Values other than 0 and 1: PGM_EINVAL.
+ * graphs. pgm_get_option returns the setting where a log-ratio run of the graph takes
+ * this form, else 0 (it asks the device once whether the cluster fits). Values outside
+ * 0..2: PGM_EINVAL.
  */
 #define PGM_OPT_SMALL_RUN 6
 pgm_status pgm_set_option(pgm_graph *g, int32_t option, int64_t value);
 /*
  * The option's effective value in *value: for PGM_OPT_CUDA_GRAPH, PGM_OPT_ENUM_BLOCK,
  * PGM_OPT_PAIR_FORM and PGM_OPT_CHECKED the setting; for PGM_OPT_LOG_RATIO the setting
- * if the graph qualifies, else 0; for PGM_OPT_SMALL_RUN 1 if it is on and the graph
- * qualifies, else 0. PGM_EINVAL for a NULL argument or an unknown option. No
- * device work.
+ * if the graph qualifies, else 0; for PGM_OPT_SMALL_RUN the setting if it is on and the
+ * graph qualifies, else 0. PGM_EINVAL for a NULL argument or an unknown option. No
+ * device work (beyond one occupancy query per device for PGM_OPT_SMALL_RUN).
  */
 pgm_status pgm_get_option(const pgm_graph *g, int32_t option, int64_t *value);
 

@@ -765,6 +765,8 @@ static pgm_status build_from_layout(const HostLayout &H, pgm_graph **out, cudaSt
         pgm_free(g);
         return cuda_fail(ce, "cudaFuncSetAttribute");
     }
+    // ask now, outside any stream capture, whether the device places the cluster form
+    if (g->P.lr && g->G.vin_tab4 != nullptr && g->G.V <= kLrClusterMaxV) lr_cluster_ok();
     pgm_info &I = g->info;
     I.n_vars = H.V;
     I.n_var_states = H.VS;
@@ -929,10 +931,19 @@ static bool log_ratio_run(const pgm_graph *g, int32_t n_iters) {
     return g->P.lr && !g->force_es && g->log_ratio_min_iters > 0 && n_iters >= g->log_ratio_min_iters;
 }
 
-// A log-ratio run of this graph goes to the single-block kernel (k_lr_small): the option
-// is on and the graph has the 4-slot layout and fits the kernel's limits.
+// Whether a log-ratio run of this graph is one launch, and whether that launch is the
+// cluster form: the option is on, the graph has the 4-slot layout and fits the form's limits.
+// Setting 1 takes one block up to kLrBlockAutoV variables, the cluster above; 2 the
+// cluster at any size it takes.
+static bool small_run_cluster(const pgm_graph *g) {
+    const int V = g->G.V, F = g->G.E / 2;
+    if (g->small_run == 2) return true;
+    return !(lr_block_fits(V, F) && V <= kLrBlockAutoV) && lr_cluster_fits(V, F);
+}
 static bool small_run_used(const pgm_graph *g) {
-    return g->small_run != 0 && g->P.lr && g->G.vin_tab4 != nullptr && lr_small_fits(g->G.V, g->G.E / 2);
+    if (g->small_run == 0 || !g->P.lr || g->G.vin_tab4 == nullptr) return false;
+    const int V = g->G.V, F = g->G.E / 2;
+    return small_run_cluster(g) ? lr_cluster_fits(V, F) : lr_block_fits(V, F);
 }
 
 static pgm_status enqueue_iterations(pgm_graph *g, const float *log_pot, const float *evidence, float T,
@@ -946,7 +957,8 @@ static pgm_status enqueue_iterations(pgm_graph *g, const float *log_pot, const f
     float2 *Dv = reinterpret_cast<float2 *>(g->b);
     // a small graph: the whole run in one launch (per-pass profiling keeps the passes)
     if (lr && small_run_used(g) && !(profile && g->profiling > 0)) {
-        cudaError_t e = launch_lr_small_run(g->G, g->P, log_pot, evidence, msgs, lam, T, damping, n_iters, s);
+        cudaError_t e = launch_lr_small_run(g->G, g->P, log_pot, evidence, msgs, lam, T, damping, n_iters,
+                                            small_run_cluster(g), s);
         if (e != cudaSuccess) return cuda_fail(e, "small-graph run launch");
         return PGM_OK;
     }
@@ -2177,7 +2189,7 @@ pgm_status pgm_set_option(pgm_graph *g, int32_t option, int64_t value) {
             g->log_ratio_min_iters = (int32_t)value;
             return PGM_OK;
         case PGM_OPT_SMALL_RUN:
-            if (value != 0 && value != 1) return fail(PGM_EINVAL, "PGM_OPT_SMALL_RUN must be 0 or 1");
+            if (value < 0 || value > 2) return fail(PGM_EINVAL, "PGM_OPT_SMALL_RUN must be 0, 1 or 2");
             if (value != g->small_run) drop_cached_runs(g);
             g->small_run = (int32_t)value;
             return PGM_OK;
@@ -2268,9 +2280,11 @@ pgm_status pgm_get_option(const pgm_graph *g, int32_t option, int64_t *value) {
         case PGM_OPT_CHECKED:
             *value = g->checked;
             return PGM_OK;
-        case PGM_OPT_SMALL_RUN:
-            *value = small_run_used(g) ? 1 : 0;
+        case PGM_OPT_SMALL_RUN: {
+            DeviceGuard dg(g->device);  // whether the device can place the cluster form
+            *value = small_run_used(g) ? g->small_run : 0;
             return PGM_OK;
+        }
         default:
             return fail(PGM_EINVAL, "unknown option");
     }

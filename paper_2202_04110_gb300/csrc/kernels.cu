@@ -4386,10 +4386,10 @@ __global__ void k_until_control(cudaGraphConditionalHandle h, const unsigned *__
 // Small binary pairwise graphs: one block for the whole run (Plan::lr, 4-slot layout)
 // =====================================================================================
 //
-// On a graph of up to a thousand variables the log-ratio run is bound by its launches,
-// not by memory: each pass is one short wave of blocks, two dependent launches per
-// iteration plus the conversions around the run. Here one block does the whole run in
-// one launch: it converts the messages into log-ratios in shared memory (as
+// On a graph of up to a few thousand variables the log-ratio run is bound by its
+// launches, not by memory: each pass is one short wave of blocks, two dependent launches
+// per iteration plus the conversions around the run. Here one block (below) or a cluster
+// of blocks (further below) does the whole run in one launch. The block: it converts the messages into log-ratios in shared memory (as
 // k_lr_pack_slot4), forms its factors' table numbers in registers (as k_lr_params), runs
 // every iteration with block barriers between the steps, and writes the messages back (as
 // k_lr_unpack). Per iteration a variable pass (thread t owns variable t; the totals Dv in
@@ -4538,6 +4538,133 @@ k_lr_small(DevGraph G, const EnumSeg *__restrict__ segs, int n_seg, const float 
         __syncthreads();
     }
     lr_small_unpack(G, d, msgs);
+}
+
+// ---- a cluster of blocks: graphs of up to kLrClusterMaxV variables ---------------------
+//
+// Above one block's share the same run goes to a thread-block cluster of kLrCluster blocks
+// (co-scheduled, one per SM) whose shared memories together hold d and the totals D,
+// distributed by variable: block r owns variables r Vc .. (r + 1) Vc - 1 (their four slots,
+// plane q at q Vc, and their totals) and factors r Fc .. (r + 1) Fc - 1. A factor reads and
+// writes its two slots, and reads its variables' totals, in whichever block holds them,
+// through the cluster's distributed shared memory (mapa: the generic address of the same
+// offset in another block). The passes are separated by cluster barriers (arrive with
+// release, wait with acquire, at cluster scope: they also order the explicit-sum path's
+// global lam), and a block leaves only after a last barrier, once no block reads another's
+// memory. Every thread of every block runs every barrier. The per-item arithmetic is that
+// of the multi-launch kernels, so the messages are bitwise theirs.
+
+__device__ __forceinline__ uint32_t cluster_rank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+__device__ __forceinline__ void cluster_barrier() {
+    asm volatile("barrier.cluster.arrive.release;\n\tbarrier.cluster.wait.acquire;" ::: "memory");
+}
+
+// The generic address of the same shared-memory location in block `rank` of the cluster.
+template <class Tp>
+__device__ __forceinline__ Tp *rank_ptr(Tp *p, uint32_t rank) {
+    uint64_t out;
+    asm volatile("mapa.u64 %0, %1, %2;" : "=l"(out) : "l"(reinterpret_cast<uint64_t>(p)), "r"(rank));
+    return reinterpret_cast<Tp *>(out);
+}
+
+// Slot p = k V + v of the 4-slot layout: the block that owns v and the slot's offset in its
+// d (k Vc + the variable's local index); also the local index of the variable.
+__device__ __forceinline__ void lr_slot_home(int p, int V, int Vc, uint32_t &rank, int &off, int &lv) {
+    const int k = (p >= V) + (p >= 2 * V) + (p >= 3 * V);
+    const int v = p - k * V;
+    rank = (uint32_t)(v / Vc);
+    lv = v - (int)rank * Vc;
+    off = k * Vc + lv;
+}
+
+template <bool MAXP, int NF>
+__global__ void __launch_bounds__(kLrSmallThreads)
+k_lr_cluster(DevGraph G, const EnumSeg *__restrict__ segs, int n_seg, const float *__restrict__ pot,
+             const float *__restrict__ ev, float *__restrict__ msgs, float *__restrict__ lam, float k, float Tln2,
+             float damping, int n_iters, int Vc, int Fc) {
+    extern __shared__ __align__(16) float lr_sm[];
+    const int V = G.V, F = G.E / 2, tid = threadIdx.x, nt = blockDim.x;
+    const uint32_t r = cluster_rank();
+    float2 *Dv = reinterpret_cast<float2 *>(lr_sm);  // Vc float2: this block's variables' totals
+    float *d = lr_sm + 2 * (size_t)Vc;               // 4 Vc floats: their slots
+    const int v0 = (int)r * Vc, nv = max(0, min(Vc, V - v0));
+    // this block's variables' slots from msgs (as k_lr_pack_slot4)
+    for (int lv = tid; lv < nv; lv += nt) {
+        const int4 t = __ldg(G.vin_tab4 + v0 + lv);
+        const int es[4] = {t.x, t.y, t.z, t.w};
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            d[q * Vc + lv] = es[q] >= 0 ? lr_encode(__ldcg(msgs + es[q]), __ldcg(msgs + es[q] + 1)) : 0.f;
+    }
+    const bool hv = tid < nv;
+    const float2 e = hv ? __ldg(reinterpret_cast<const float2 *>(ev) + v0 + tid) : make_float2(0.f, 0.f);
+    // this thread's factors: table numbers and where their slots and totals live
+    LrSmallFactor f[NF];
+    float *s0[NF], *s1[NF];
+    const float2 *t0[NF], *t1[NF];
+    bool hf[NF];
+#pragma unroll
+    for (int j = 0; j < NF; ++j) {
+        const int i = tid + j * nt, g = (int)r * Fc + i;
+        hf[j] = i < Fc && g < F;
+        f[j] = lr_small_factor(G, segs, n_seg, pot, hf[j] ? g : F, F);  // (0, 0) for no factor
+        uint32_t ra, rb;
+        int oa, ob, la, lb;
+        lr_slot_home(f[j].p.x, V, Vc, ra, oa, la);
+        lr_slot_home(f[j].p.y, V, Vc, rb, ob, lb);
+        s0[j] = rank_ptr(d + oa, ra);
+        s1[j] = rank_ptr(d + ob, rb);
+        t0[j] = rank_ptr(Dv + la, ra);
+        t1[j] = rank_ptr(Dv + lb, rb);
+    }
+    const float w = 1.f - damping;
+    cluster_barrier();  // every block's slots are packed
+    for (int it = 0; it < n_iters; ++it) {
+        if (hv) {  // variable pass (k_var_slot4_lr), this block's variables
+            float dk[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) dk[q] = d[q * Vc + tid];
+            lr_small_var(e, dk, v0 + tid, V, Dv + tid, lam);
+        }
+        cluster_barrier();
+        float mo0[NF], mo1[NF];  // factor pass (k_pair2_lr<MAXP, true>), this block's factors
+        float2 D0[NF], D1[NF];
+#pragma unroll
+        for (int j = 0; j < NF; ++j) {
+            mo0[j] = *s0[j];
+            mo1[j] = *s1[j];
+            D0[j] = *t0[j];
+            D1[j] = *t1[j];
+        }
+#pragma unroll
+        for (int j = 0; j < NF; ++j) {
+            if (!hf[j]) continue;
+            const int2 p = f[j].p;
+            const float l0 = __float_as_uint(D0[j].x) == kDvSlow ? __ldcg(lam + p.x) : lr_lam_from_D(D0[j], mo0[j]);
+            const float l1 = __float_as_uint(D1[j].x) == kDvSlow ? __ldcg(lam + p.y) : lr_lam_from_D(D1[j], mo1[j]);
+            const float2 dn = lr_small_update<MAXP>(f[j], segs, n_seg, pot, (int)r * Fc + tid + j * nt, l0, l1,
+                                                    mo0[j], mo1[j], k, Tln2, damping, w, G.flags);
+            *s0[j] = dn.x;
+            *s1[j] = dn.y;
+        }
+        cluster_barrier();
+    }
+    // the edges of this block's factors back into msgs (as k_lr_unpack)
+    const int e_end = 2 * min(F, ((int)r + 1) * Fc);
+    for (int ei = 2 * (int)r * Fc + tid; ei < e_end; ei += nt) {
+        uint32_t ra;
+        int oa, la;
+        lr_slot_home(__ldg(G.lr_pos + ei), V, Vc, ra, oa, la);
+        const float2 q = lr_decode(*rank_ptr(d + oa, ra));
+        msgs[2 * (size_t)ei] = q.x;
+        msgs[2 * (size_t)ei + 1] = q.y;
+    }
+    cluster_barrier();  // no block leaves while another may still read its shared memory
 }
 
 }  // namespace
@@ -4908,23 +5035,76 @@ cudaError_t launch_lr_unpack(const DevGraph &G, const float *d, float *m, cudaSt
     return cudaGetLastError();
 }
 
+// Whether a cluster of kLrCluster blocks of kLrSmallThreads threads fits this device at
+// once (asked once per device).
+bool lr_cluster_ok() {
+    static int ok[64];  // 0 unknown, 1 yes, 2 no
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return false;
+    if (ok[dev] == 0) {
+        cudaLaunchConfig_t cfg{};
+        cfg.gridDim = dim3(kLrCluster);
+        cfg.blockDim = dim3(kLrSmallThreads);
+        cfg.dynamicSmemBytes = (size_t)24 * (kLrClusterMaxV / kLrCluster);
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = kLrCluster;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        int n = 0;
+        const bool yes = cudaOccupancyMaxActiveClusters(&n, k_lr_cluster<false, 2>, &cfg) == cudaSuccess && n > 0 &&
+                         cudaOccupancyMaxActiveClusters(&n, k_lr_cluster<true, 2>, &cfg) == cudaSuccess && n > 0;
+        cudaGetLastError();  // a refused query leaves no error behind
+        ok[dev] = yes ? 1 : 2;
+    }
+    return ok[dev] == 1;
+}
+
 cudaError_t launch_lr_small_run(const DevGraph &G, const Plan &P, const float *log_pot, const float *ev,
-                                float *msgs, float *lam, float T, float damping, int n_iters, cudaStream_t s) {
+                                float *msgs, float *lam, float T, float damping, int n_iters, bool cluster,
+                                cudaStream_t s) {
     const float k = T > 0.f ? (float)(1.4426950408889634 / (double)T) : 0.f;
     const float Tln2 = (float)((double)T * 0.6931471805599453);
     const int F = G.E / 2, V = G.V;
-    if (!lr_small_fits(V, F) || G.vin_tab4 == nullptr || G.lr_pos == nullptr) return cudaErrorInvalidValue;
-    // one variable and one factor per thread where a block holds them, else two factors
-    const bool one = F <= kLrSmallThreads;
-    const int per = one ? std::max(V, F) : std::max(V, (F + 1) / 2);
-    const int threads = std::max(32, ((per + 31) / 32) * 32);
-    const size_t smem = (size_t)V * 6 * sizeof(float);
+    const bool block = !cluster;
+    if (!(block ? lr_block_fits(V, F) : lr_cluster_fits(V, F)) || G.vin_tab4 == nullptr || G.lr_pos == nullptr)
+        return cudaErrorInvalidValue;
     for (const FactorLaunch &L : P.factor) {  // the one kPair2 launch: every factor
         if (L.n_blocks == 0 || n_iters <= 0) continue;
-        auto kern = T == 0.f ? (one ? k_lr_small<true, 1> : k_lr_small<true, 2>)
-                             : (one ? k_lr_small<false, 1> : k_lr_small<false, 2>);
-        kern<<<1, threads, smem, s>>>(G, static_cast<const EnumSeg *>(L.segs), L.n_seg, log_pot, ev, msgs, lam, k,
-                                      Tln2, damping, n_iters);
+        const EnumSeg *segs = static_cast<const EnumSeg *>(L.segs);
+        if (block) {  // one block: one variable and one factor per thread, or two factors
+            const bool one = F <= kLrSmallThreads;
+            const int per = one ? std::max(V, F) : std::max(V, (F + 1) / 2);
+            const int threads = std::max(32, ((per + 31) / 32) * 32);
+            const size_t smem = (size_t)V * 6 * sizeof(float);
+            auto kern = T == 0.f ? (one ? k_lr_small<true, 1> : k_lr_small<true, 2>)
+                                 : (one ? k_lr_small<false, 1> : k_lr_small<false, 2>);
+            kern<<<1, threads, smem, s>>>(G, segs, L.n_seg, log_pot, ev, msgs, lam, k, Tln2, damping, n_iters);
+            continue;
+        }
+        // a cluster: block r owns Vc variables and Fc factors
+        const int Vc = (V + kLrCluster - 1) / kLrCluster, Fc = (F + kLrCluster - 1) / kLrCluster;
+        const bool one = Fc <= kLrSmallThreads;
+        const int per = one ? std::max(Vc, Fc) : std::max(Vc, (Fc + 1) / 2);
+        cudaLaunchConfig_t cfg{};
+        cfg.gridDim = dim3(kLrCluster);
+        cfg.blockDim = dim3(std::max(32, ((per + 31) / 32) * 32));
+        cfg.dynamicSmemBytes = (size_t)Vc * 6 * sizeof(float);
+        cfg.stream = s;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = kLrCluster;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        auto kern = T == 0.f ? (one ? k_lr_cluster<true, 1> : k_lr_cluster<true, 2>)
+                             : (one ? k_lr_cluster<false, 1> : k_lr_cluster<false, 2>);
+        cudaError_t e = cudaLaunchKernelEx(&cfg, kern, G, segs, L.n_seg, log_pot, ev, msgs, lam, k, Tln2, damping,
+                                           n_iters, Vc, Fc);
+        if (e != cudaSuccess) return e;
     }
     return cudaGetLastError();
 }

@@ -1,12 +1,14 @@
-"""The single-block run of small binary pairwise graphs (PGM_OPT_SMALL_RUN).
+"""The one-launch run of small binary pairwise graphs (PGM_OPT_SMALL_RUN).
 
-One thread block runs every iteration of the log-ratio scheme (Sec. 3's parallel damped
-updates on binary 2 x 2 factors) with the exchanged arrays in shared memory. Its per-item
-arithmetic is that of the multi-launch iterations, so its messages are held bitwise to
-the multi-launch run with the option off, and its beliefs to the FP64 oracle at the strict
-bound: on grids from 2 x 2 to the size limit, chains, hard and contradictory evidence,
-tables with -inf entries, shared tables, damping 0, warm starts, T = 0 and T > 0, with and
-without CUDA graphs.
+One thread block (up to 1,024 variables), or a cluster of 8 blocks sharing their shared
+memories (up to 8,192 variables), runs every iteration of the log-ratio scheme (Sec. 3's
+parallel damped updates on binary 2 x 2 factors) with the exchanged arrays in shared
+memory. Its per-item arithmetic is that of the multi-launch iterations, so its messages are
+held bitwise to the multi-launch run with the option off, and its beliefs to the FP64
+oracle at the strict bound: on grids from 2 x 2 to the size limits, chains, a grid whose
+variables are numbered at random (so that most factors reach into other blocks of the
+cluster), hard and contradictory evidence, tables with -inf entries, shared tables, damping
+0, warm starts, T = 0 and T > 0, with and without CUDA graphs.
 """
 import numpy as np
 import pytest
@@ -45,13 +47,13 @@ def _run(binding, graph, lp, ev, T, damping, n_iters, small, m0=None, cuda_graph
     return g, m.cpu().numpy(), nb, dec, g.flags(clear=True)
 
 
-def _both(binding, graph, lp, ev, T, damping, n_iters, m0=None, cuda_graph=1, expect_small=True):
-    """The single-block run (1) against the multi-launch run (0): bitwise equal messages,
-    equal flags."""
+def _both(binding, graph, lp, ev, T, damping, n_iters, m0=None, cuda_graph=1, expect_small=True, mode=1):
+    """The one-launch run (mode 1: one block or the cluster by size; 2: the cluster) against
+    the multi-launch run (0): bitwise equal messages, equal flags."""
     gm, mm, _, _, fm = _run(binding, graph, lp, ev, T, damping, n_iters, 0, m0, cuda_graph)
     assert gm.get_option(binding.OPT_SMALL_RUN) == 0
-    gs, ms, nbs, decs, fs = _run(binding, graph, lp, ev, T, damping, n_iters, 1, m0, cuda_graph)
-    assert gs.get_option(binding.OPT_SMALL_RUN) == (1 if expect_small else 0)
+    gs, ms, nbs, decs, fs = _run(binding, graph, lp, ev, T, damping, n_iters, mode, m0, cuda_graph)
+    assert gs.get_option(binding.OPT_SMALL_RUN) == (mode if expect_small else 0)
     assert np.array_equal(ms, mm, equal_nan=True), f"max diff {np.nanmax(np.abs(ms - mm))}"
     assert fs == fm, (fs, fm)
     return ms, nbs, decs, fs
@@ -77,11 +79,13 @@ def test_ising10x10(gpu, T):
 
 
 @pytest.mark.parametrize("shape", [(1, 2), (2, 2), (1, 50), (3, 7), (23, 23), (24, 24), (31, 31), (32, 32),
-                                   (8, 128), (1, 1024)])
+                                   (8, 128), (1, 1024), (33, 33), (1, 1025), (45, 45), (64, 64), (90, 90),
+                                   (64, 128), (1, 8192)])
 def test_sizes_up_to_the_limit(gpu, shape):
-    """From one factor to the limits: one factor per thread or two (23 x 23: 1,012
-    factors; 24 x 24: 1,104), 1,024 variables with 1,984 factors (32 x 32) and 1,024
-    variables in a chain."""
+    """From one factor to the limits: one block with one factor per thread or two (23 x 23:
+    1,012 factors; 24 x 24: 1,104), 1,024 variables with 1,984 factors (32 x 32) and in a
+    chain; then a cluster from 1,025 variables to 8,100 (90 x 90) and 8,192 (64 x 128:
+    16,192 factors, two per thread; a chain of 8,192)."""
     r, c = shape
     p = W.ising_grid(r, c, seed=r * 100 + c, T=1.0)
     for T in (1.0, 0.0):
@@ -89,9 +93,9 @@ def test_sizes_up_to_the_limit(gpu, shape):
         _oracle_check(p.graph, p.log_pot, p.evidence, T, 0.5, 20, nb, dec, f"ising{r}x{c} T={T}")
 
 
-@pytest.mark.parametrize("shape", [(33, 33), (9, 128), (1, 1025)])
+@pytest.mark.parametrize("shape", [(91, 91), (65, 128), (1, 8193)])
 def test_above_the_limit_keeps_the_launches(gpu, shape):
-    """1,089, 1,152 and 1,025 variables: above the limit, the multi-launch form."""
+    """8,281, 8,320 and 8,193 variables: above the limit, the multi-launch form."""
     r, c = shape
     p = W.ising_grid(r, c, seed=3, T=1.0)
     _both(gpu, p.graph, p.log_pot, p.evidence, 1.0, 0.5, 10, expect_small=False)
@@ -170,7 +174,7 @@ def test_qualifying_graphs(gpu):
     g.set_option(gpu.OPT_SMALL_RUN, 0)
     assert g.get_option(gpu.OPT_SMALL_RUN) == 0
     with pytest.raises(gpu.PgmError):
-        g.set_option(gpu.OPT_SMALL_RUN, 2)
+        g.set_option(gpu.OPT_SMALL_RUN, 3)
     pk = W.potts_grid(8, 4, seed=1, T=1.0)
     assert gpu.Graph(pk.graph).get_option(gpu.OPT_SMALL_RUN) == 0  # not binary
     # a hub variable with 6 factors: the CSR log-ratio layout, not the 4-slot one
@@ -183,3 +187,67 @@ def test_qualifying_graphs(gpu):
     _, mm, _, _, _ = _run(gpu, p.graph, p.log_pot, p.evidence, 1.0, 0.5, 3, 0)
     assert np.array_equal(ms, mm)
     _oracle_check(p.graph, p.log_pot, p.evidence, 1.0, 0.5, 3, nb, dec, "3 iterations")
+
+
+def _permuted(p, seed):
+    """The same grid with its variables numbered at random: a factor's two variables, and
+    a variable's four slots, then mostly live in other blocks of the cluster."""
+    rng = np.random.default_rng(seed)
+    n = p.graph.num_states.size
+    perm = rng.permutation(n).astype(np.int32)
+    g0 = p.graph.enum_groups[0]
+    graph = W.FactorGraph(p.graph.num_states, [W.EnumGroup(g0.cfg, perm[g0.vars], False)], [])
+    ev = np.empty_like(p.evidence.reshape(-1, 2))
+    ev[perm] = p.evidence.reshape(-1, 2)
+    return graph, ev.ravel()
+
+
+@pytest.mark.parametrize("T", [1.0, 0.0])
+def test_cluster_random_numbering_and_hard_evidence(gpu, T):
+    """A 60 x 60 grid (3,600 variables: a cluster) numbered at random, plain and with hard
+    and contradictory evidence: bitwise equal to the multi-launch run, and the oracle."""
+    p = W.ising_grid(60, 60, seed=21, T=T)
+    graph, ev = _permuted(p, 22)
+    _, nb, dec, _ = _both(gpu, graph, p.log_pot, ev, T, 0.5, 25)
+    _oracle_check(graph, p.log_pot, ev, T, 0.5, 25, nb, dec, f"permuted 60x60 T={T}")
+    evh = _hard(ev, 0.1, 23)
+    _, nb, dec, _ = _both(gpu, graph, p.log_pot, evh, T, 0.5, 25)
+    _oracle_check(graph, p.log_pot, evh, T, 0.5, 25, nb, dec, f"permuted 60x60 hard T={T}")
+    evc = _hard(ev, 0.05, 24, both=True)
+    _, _, _, flags = _both(gpu, graph, p.log_pot, evc, T, 0.5, 10)
+    assert flags & gpu.FLAG_CONTRADICTION
+
+
+def test_cluster_tables_damping_and_warm_start(gpu):
+    """The cluster with -inf table entries and a shared table group, damping 0 from warm
+    messages, kernels launched one by one."""
+    rng = np.random.default_rng(31)
+    p = W.ising_grid(50, 70, seed=31, T=1.0)
+    lp = p.log_pot.reshape(-1, 4).copy()
+    bad = rng.choice(lp.shape[0], 300, replace=False)
+    lp[bad, rng.integers(0, 4, bad.size)] = -np.inf
+    pairs = p.graph.enum_groups[0].vars
+    half = pairs.shape[0] // 2
+    cfg = W.PAIR2_CFG.copy()
+    graph = W.FactorGraph(p.graph.num_states, [W.EnumGroup(cfg, pairs[:half], False),
+                                               W.EnumGroup(cfg, pairs[half:], True)], [])
+    lp2 = np.concatenate([lp[:half].ravel(), np.array([0.3, -0.3, -0.3, 0.3], np.float32)])
+    _, nb, dec, _ = _both(gpu, graph, lp2, p.evidence, 1.0, 0.5, 20)
+    _oracle_check(graph, lp2, p.evidence, 1.0, 0.5, 20, nb, dec, "cluster -inf tables")
+    m0 = _run(gpu, graph, lp2, p.evidence, 1.0, 0.5, 10, 0)[1]
+    _, nb, dec, _ = _both(gpu, graph, lp2, p.evidence, 1.0, 0.0, 12, m0=m0, cuda_graph=0)
+    _oracle_check(graph, lp2, p.evidence, 1.0, 0.0, 12, nb, dec, "cluster damping 0, warm start", m0=m0)
+
+
+@pytest.mark.parametrize("shape", [(1, 2), (2, 2), (2, 3), (3, 7), (10, 10), (24, 24), (32, 32)])
+def test_cluster_forced_on_small_graphs(gpu, shape):
+    """Setting 2 runs the cluster at any size it takes: with fewer variables than blocks
+    (1 x 2, 2 x 2, 2 x 3), blocks that own no variable or no factor still take part in
+    every barrier; bitwise equal to the multi-launch run, and the oracle."""
+    r, c = shape
+    p = W.ising_grid(r, c, seed=r * 10 + c + 5, T=1.0)
+    for T in (1.0, 0.0):
+        _, nb, dec, _ = _both(gpu, p.graph, p.log_pot, p.evidence, T, 0.5, 16, mode=2)
+        _oracle_check(p.graph, p.log_pot, p.evidence, T, 0.5, 16, nb, dec, f"cluster {r}x{c} T={T}")
+    evh = _hard(p.evidence, 0.2, r + c)
+    _both(gpu, p.graph, p.log_pot, evh, 1.0, 0.5, 16, mode=2)
