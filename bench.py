@@ -65,6 +65,8 @@ def parse_args():
                     help="only run the deconvolution workload for N iterations (3 runs, no CUDA graphs; for ncu)")
     ap.add_argument("--small-probe", type=int, default=0,
                     help="only run N runs of the 10x10 grid workload (50 iterations, T=1, one launch each; for ncu)")
+    ap.add_argument("--small-side", type=int, default=10,
+                    help="with --small-probe: the grid's side (above 26 the run is one cluster launch)")
     ap.add_argument("--grad-probe", type=int, default=0,
                     help="run only N gradient calls of the gradient workload, CUDA graphs off (for ncu)")
     ap.add_argument("--pair-form", type=int, default=0,
@@ -1199,13 +1201,14 @@ def deconv_probe(args):
 
 def small_probe(args):
     """`--small-probe N` runs of the 10x10 Ising workload (T=1, damping 0.5, 50
-    iterations: one k_lr_small launch each), CUDA graphs off, for ncu captures of the
-    single-block run. Prints one JSON line."""
+    iterations: one k_lr_small launch each), or of a `--small-side` grid (one k_lr_small
+    or k_lr_cluster launch each), CUDA graphs off, for ncu captures of the one-launch
+    run. Prints one JSON line."""
     import torch
     from paper_2202_04110_gb300 import binding, build
     from paper_2202_04110_gb300 import workloads as W
     build.build()
-    p = W.ising_small(0)
+    p = W.ising_small(0) if args.small_side == 10 else W.ising_grid(args.small_side, args.small_side, 0, T=1.0)
     lp = torch.as_tensor(p.log_pot).cuda()
     ev = torch.as_tensor(p.evidence).cuda()
     g = binding.Graph(p.graph)
@@ -1215,7 +1218,8 @@ def small_probe(args):
         m.zero_()
         g.run_bp(lp, ev, 1.0, 0.5, p.n_iters, m)
     torch.cuda.synchronize()
-    print(json.dumps({"small_probe": args.small_probe, "small_run": g.get_option(binding.OPT_SMALL_RUN),
+    print(json.dumps({"small_probe": args.small_probe, "side": args.small_side,
+                      "small_run": g.get_option(binding.OPT_SMALL_RUN),
                       "n_edge_states": g.info["n_edge_states"]}))
 
 
