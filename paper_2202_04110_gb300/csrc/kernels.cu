@@ -161,14 +161,8 @@ __device__ __forceinline__ FF ff_add(FF a, FF b) {
     return r;
 }
 
-__device__ __forceinline__ FF ff_shfl_up(FF v, int d) {
-    return FF{__shfl_up_sync(0xffffffffu, v.hi, d), __shfl_up_sync(0xffffffffu, v.lo, d)};
-}
 __device__ __forceinline__ FF ff_shfl_down(FF v, int d) {
     return FF{__shfl_down_sync(0xffffffffu, v.hi, d), __shfl_down_sync(0xffffffffu, v.lo, d)};
-}
-__device__ __forceinline__ FF ff_shfl(FF v, int src) {
-    return FF{__shfl_sync(0xffffffffu, v.hi, src), __shfl_sync(0xffffffffu, v.lo, src)};
 }
 
 // a - b for float-float values, rounded to FP32 (exact up to that rounding when a and b
@@ -906,21 +900,6 @@ __global__ void __launch_bounds__(256) k_var_group(DevGraph G, const int32_t *__
             store_n<4>(out + vs + 4 * l, r);
         }
     }
-}
-
-__device__ __forceinline__ FF block_sum(FF v, float *sh) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-#pragma unroll
-    for (int d = 16; d > 0; d >>= 1) v = ff_add(v, ff_shfl_down(v, d));
-    if (lane == 0) {
-        sh[2 * warp] = v.hi;
-        sh[2 * warp + 1] = v.lo;
-    }
-    __syncthreads();
-    FF tot = ff_make(0.f);
-    for (int w = 0; w < nw; ++w) tot = ff_add(tot, FF{sh[2 * w], sh[2 * w + 1]});
-    __syncthreads();
-    return tot;
 }
 
 // The outputs of a high-degree variable from its float-float totals sb[x] (thread 0):
