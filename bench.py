@@ -715,13 +715,14 @@ def measure_deconv(args, binding, W, torch, dev):
 def measure_small(args, binding, W, torch, dev):
     """Per-iteration latency of the 10x10 Ising grid (180 factors, 720 edge-states), T=1,
     damping 0.5, 50 iterations: CUDA events around 200 back-to-back pgm_run_bp calls (one
-    CUDA graph replay each), and the FP64 oracle's time for the same run on the host."""
-    p = W.ising_small(0)
-    lp = torch.as_tensor(p.log_pot).to(dev)
-    ev = torch.as_tensor(p.evidence).to(dev)
+    CUDA graph replay each), and the FP64 oracle's time for the same run on the host; the
+    same for a 64x64 grid (one cluster launch per run), each beside the multi-launch
+    run."""
     stream = torch.cuda.current_stream()
 
-    def per_run(small):
+    def per_run(p, small):
+        lp = torch.as_tensor(p.log_pot).to(dev)
+        ev = torch.as_tensor(p.evidence).to(dev)
         g = binding.Graph(p.graph)
         g.set_option(binding.OPT_SMALL_RUN, small)
         m = g.new_msgs()
@@ -739,13 +740,21 @@ def measure_small(args, binding, W, torch, dev):
         launches = 1 if g.get_option(binding.OPT_SMALL_RUN) else p.n_iters * g.info["launches_per_iter"] + 3
         return e0.elapsed_time(e1) / 1e3 / reps, launches, g.info["n_edge_states"]
 
-    t, launches, n_es = per_run(1)  # the default: one block runs the whole run
-    t_multi, launches_multi, _ = per_run(0)
+    p = W.ising_small(0)
+    t, launches, n_es = per_run(p, 1)  # the default: one block runs the whole run
+    t_multi, launches_multi, _ = per_run(p, 0)
     out = {"workload": "ising10x10, T=1, damping 0.5, 50 iterations", "us_per_run": round(1e6 * t, 2),
            "us_per_iteration": round(1e6 * t / p.n_iters, 3),
            "value": p.n_iters * n_es / t, "unit": UNIT, "launches_per_run": launches,
            "multi_launch": {"us_per_run": round(1e6 * t_multi, 2), "launches_per_run": launches_multi,
                             "note": "PGM_OPT_SMALL_RUN 0: two launches per iteration"}}
+    pm = W.ising_grid(64, 64, 0, T=1.0)  # 4,096 variables: one launch of an 8-block cluster
+    tc, lc, n_es_m = per_run(pm, 1)
+    tm, lm, _ = per_run(pm, 0)
+    out["cluster_grid"] = {"workload": "ising64x64, T=1, damping 0.5, 50 iterations",
+                           "us_per_run": round(1e6 * tc, 2), "value": pm.n_iters * n_es_m / tc, "unit": UNIT,
+                           "launches_per_run": lc, "multi_launch_us_per_run": round(1e6 * tm, 2),
+                           "multi_launch_launches_per_run": lm}
     if not args.no_cpu_baseline:
         import oracle
         oracle.build()
