@@ -766,7 +766,7 @@ static pgm_status build_from_layout(const HostLayout &H, pgm_graph **out, cudaSt
         return cuda_fail(ce, "cudaFuncSetAttribute");
     }
     // ask now, outside any stream capture, whether the device places the cluster form
-    if (g->P.lr && g->G.vin_tab4 != nullptr && g->G.V <= kLrClusterMaxV) lr_cluster_ok();
+    if (g->P.lr && g->G.vin_tab4 != nullptr && g->G.V <= kLrClusterMax * kLrSmallMaxV) lr_cluster_size();
     pgm_info &I = g->info;
     I.n_vars = H.V;
     I.n_var_states = H.VS;

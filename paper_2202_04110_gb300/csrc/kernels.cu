@@ -4519,10 +4519,10 @@ k_lr_small(DevGraph G, const EnumSeg *__restrict__ segs, int n_seg, const float 
     lr_small_unpack(G, d, msgs);
 }
 
-// ---- a cluster of blocks: graphs of up to kLrClusterMaxV variables ---------------------
+// ---- a cluster of blocks: graphs of up to 16,384 variables -----------------------------
 //
-// Above one block's share the same run goes to a thread-block cluster of kLrCluster blocks
-// (co-scheduled, one per SM) whose shared memories together hold d and the totals D,
+// Above one block's share the same run goes to a thread-block cluster of C blocks
+// (lr_cluster_size: 16 or 8; co-scheduled, one per SM) whose shared memories together hold d and the totals D,
 // distributed by variable: block r owns variables r Vc .. (r + 1) Vc - 1 (their four slots,
 // plane q at q Vc, and their totals) and factors r Fc .. (r + 1) Fc - 1. A factor reads and
 // writes its two slots, and reads its variables' totals, in whichever block holds them,
@@ -5014,31 +5014,45 @@ cudaError_t launch_lr_unpack(const DevGraph &G, const float *d, float *m, cudaSt
     return cudaGetLastError();
 }
 
-// Whether a cluster of kLrCluster blocks of kLrSmallThreads threads fits this device at
-// once (asked once per device).
-bool lr_cluster_ok() {
-    static int ok[64];  // 0 unknown, 1 yes, 2 no
+// The cluster size of the cluster form on this device: 16 blocks of kLrSmallThreads threads
+// where the device places such a cluster (above the portable size of 8), else 8, else 0
+// (asked once per device).
+int lr_cluster_size() {
+    static int size[64];  // 0 unknown, else the size + 1
     int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return false;
-    if (ok[dev] == 0) {
-        cudaLaunchConfig_t cfg{};
-        cfg.gridDim = dim3(kLrCluster);
-        cfg.blockDim = dim3(kLrSmallThreads);
-        cfg.dynamicSmemBytes = (size_t)24 * (kLrClusterMaxV / kLrCluster);
-        cudaLaunchAttribute at[1];
-        at[0].id = cudaLaunchAttributeClusterDimension;
-        at[0].val.clusterDim.x = kLrCluster;
-        at[0].val.clusterDim.y = 1;
-        at[0].val.clusterDim.z = 1;
-        cfg.attrs = at;
-        cfg.numAttrs = 1;
-        int n = 0;
-        const bool yes = cudaOccupancyMaxActiveClusters(&n, k_lr_cluster<false, 2>, &cfg) == cudaSuccess && n > 0 &&
-                         cudaOccupancyMaxActiveClusters(&n, k_lr_cluster<true, 2>, &cfg) == cudaSuccess && n > 0;
-        cudaGetLastError();  // a refused query leaves no error behind
-        ok[dev] = yes ? 1 : 2;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
+    if (size[dev] == 0) {
+        void (*kerns[4])(DevGraph, const EnumSeg *, int, const float *, const float *, float *, float *, float,
+                         float, float, int, int, int) = {k_lr_cluster<false, 1>, k_lr_cluster<false, 2>,
+                                                         k_lr_cluster<true, 1>, k_lr_cluster<true, 2>};
+        for (auto kern : kerns) cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        int found = 0;
+        for (int C : {kLrClusterMax, 8}) {
+            cudaLaunchConfig_t cfg{};
+            cfg.gridDim = dim3(C);
+            cfg.blockDim = dim3(kLrSmallThreads);
+            cfg.dynamicSmemBytes = (size_t)24 * kLrSmallMaxV;
+            cudaLaunchAttribute at[1];
+            at[0].id = cudaLaunchAttributeClusterDimension;
+            at[0].val.clusterDim.x = C;
+            at[0].val.clusterDim.y = 1;
+            at[0].val.clusterDim.z = 1;
+            cfg.attrs = at;
+            cfg.numAttrs = 1;
+            bool yes = true;
+            for (auto kern : kerns) {
+                int n = 0;
+                yes = yes && cudaOccupancyMaxActiveClusters(&n, kern, &cfg) == cudaSuccess && n > 0;
+            }
+            cudaGetLastError();  // a refused query leaves no error behind
+            if (yes) {
+                found = C;
+                break;
+            }
+        }
+        size[dev] = found + 1;
     }
-    return ok[dev] == 1;
+    return size[dev] - 1;
 }
 
 cudaError_t launch_lr_small_run(const DevGraph &G, const Plan &P, const float *log_pot, const float *ev,
@@ -5063,18 +5077,19 @@ cudaError_t launch_lr_small_run(const DevGraph &G, const Plan &P, const float *l
             kern<<<1, threads, smem, s>>>(G, segs, L.n_seg, log_pot, ev, msgs, lam, k, Tln2, damping, n_iters);
             continue;
         }
-        // a cluster: block r owns Vc variables and Fc factors
-        const int Vc = (V + kLrCluster - 1) / kLrCluster, Fc = (F + kLrCluster - 1) / kLrCluster;
+        // a cluster of C blocks: block r owns Vc variables and Fc factors
+        const int C = lr_cluster_size();
+        const int Vc = (V + C - 1) / C, Fc = (F + C - 1) / C;
         const bool one = Fc <= kLrSmallThreads;
         const int per = one ? std::max(Vc, Fc) : std::max(Vc, (Fc + 1) / 2);
         cudaLaunchConfig_t cfg{};
-        cfg.gridDim = dim3(kLrCluster);
+        cfg.gridDim = dim3(C);
         cfg.blockDim = dim3(std::max(32, ((per + 31) / 32) * 32));
         cfg.dynamicSmemBytes = (size_t)Vc * 6 * sizeof(float);
         cfg.stream = s;
         cudaLaunchAttribute at[1];
         at[0].id = cudaLaunchAttributeClusterDimension;
-        at[0].val.clusterDim.x = kLrCluster;
+        at[0].val.clusterDim.x = C;
         at[0].val.clusterDim.y = 1;
         at[0].val.clusterDim.z = 1;
         cfg.attrs = at;

@@ -297,22 +297,24 @@ cudaError_t launch_pmp_perturb(int64_t VS, int S, const float *ev, const float *
 // Log-ratio pack (from the [2E] edge-state layout; unused slots 0) and unpack.
 cudaError_t launch_lr_pack(const DevGraph &G, const float *m, float *d, cudaStream_t s);
 cudaError_t launch_lr_unpack(const DevGraph &G, const float *d, float *m, cudaStream_t s);
-// One block, or a cluster of kLrCluster blocks sharing their shared memories, runs a whole
-// log-ratio run of a small graph (4-slot layout), msgs in and out: one block up to
-// kLrSmallMaxV variables and kLrSmallMaxF factors (one variable and one factor per thread,
-// or two factors above kLrSmallThreads of them; 24 V bytes of shared memory), a cluster up
-// to kLrClusterMaxV and kLrClusterMaxF (the same per block on its share), where the device
-// can place such a cluster (lr_cluster_ok).
+// One block, or a cluster of blocks sharing their shared memories, runs a whole log-ratio
+// run of a small graph (4-slot layout), msgs in and out: one block up to kLrSmallMaxV
+// variables and kLrSmallMaxF factors (one variable and one factor per thread, or two
+// factors above kLrSmallThreads of them; 24 V bytes of shared memory), a cluster of C blocks
+// up to C times that (the same per block on its share). C is 16 where the device places a
+// cluster of 16 such blocks (a non-portable size), else 8 where it places 8, else there is
+// no cluster form (lr_cluster_size, asked once per device).
 constexpr int kLrSmallThreads = 1024, kLrSmallMaxV = 1024, kLrSmallMaxF = 2048;
-constexpr int kLrCluster = 8, kLrClusterMaxV = kLrCluster * kLrSmallMaxV, kLrClusterMaxF = kLrCluster * kLrSmallMaxF;
-bool lr_cluster_ok();
+constexpr int kLrClusterMax = 16;
+int lr_cluster_size();
 // Setting 1 of PGM_OPT_SMALL_RUN: one block up to this many variables, the cluster above
 // (the cluster's two barriers per iteration cost about 1.1 us per iteration on a GB300; one
 // block was faster up to 24 x 24 grids, the cluster from 28 x 28).
 constexpr int kLrBlockAutoV = 700;
 inline bool lr_block_fits(int V, int F) { return V > 0 && V <= kLrSmallMaxV && F <= kLrSmallMaxF; }
 inline bool lr_cluster_fits(int V, int F) {
-    return V > 0 && V <= kLrClusterMaxV && F <= kLrClusterMaxF && lr_cluster_ok();
+    const int C = lr_cluster_size();
+    return C > 0 && V > 0 && V <= C * kLrSmallMaxV && F <= C * kLrSmallMaxF;
 }
 cudaError_t launch_lr_small_run(const DevGraph &G, const Plan &P, const float *log_pot, const float *ev,
                                 float *msgs, float *lam, float T, float damping, int n_iters, bool cluster,

@@ -1,7 +1,7 @@
 """The one-launch run of small binary pairwise graphs (PGM_OPT_SMALL_RUN).
 
-One thread block (up to 1,024 variables), or a cluster of 8 blocks sharing their shared
-memories (up to 8,192 variables), runs every iteration of the log-ratio scheme (Sec. 3's
+One thread block (up to 700 variables), or a cluster of blocks sharing their shared
+memories (16 blocks on a GB300: up to 16,384 variables), runs every iteration of the log-ratio scheme (Sec. 3's
 parallel damped updates on binary 2 x 2 factors) with the exchanged arrays in shared
 memory. Its per-item arithmetic is that of the multi-launch iterations, so its messages are
 held bitwise to the multi-launch run with the option off, and its beliefs to the FP64
@@ -78,14 +78,14 @@ def test_ising10x10(gpu, T):
     _oracle_check(p.graph, p.log_pot, p.evidence, T, 0.5, 50, nb, dec, f"ising10x10 T={T}")
 
 
-@pytest.mark.parametrize("shape", [(1, 2), (2, 2), (1, 50), (3, 7), (23, 23), (24, 24), (31, 31), (32, 32),
-                                   (8, 128), (1, 1024), (33, 33), (1, 1025), (45, 45), (64, 64), (90, 90),
-                                   (64, 128), (1, 8192)])
+@pytest.mark.parametrize("shape", [(1, 2), (2, 2), (1, 50), (3, 7), (23, 23), (24, 24), (26, 27), (31, 31),
+                                   (32, 32), (8, 128), (1, 1024), (33, 33), (1, 1025), (45, 45), (64, 64),
+                                   (90, 90), (64, 128), (1, 8192), (91, 91), (128, 128), (1, 16384)])
 def test_sizes_up_to_the_limit(gpu, shape):
     """From one factor to the limits: one block with one factor per thread or two (23 x 23:
-    1,012 factors; 24 x 24: 1,104), 1,024 variables with 1,984 factors (32 x 32) and in a
-    chain; then a cluster from 1,025 variables to 8,100 (90 x 90) and 8,192 (64 x 128:
-    16,192 factors, two per thread; a chain of 8,192)."""
+    1,012 factors; 24 x 24: 1,104) up to 700 variables; then the cluster (16 blocks on a
+    GB300) from 702 variables (26 x 27) through 1,024 and 8,192 (64 x 128: 16,192 factors)
+    to 16,384 (128 x 128: 32,512 factors, two per thread; a chain of 16,384)."""
     r, c = shape
     p = W.ising_grid(r, c, seed=r * 100 + c, T=1.0)
     for T in (1.0, 0.0):
@@ -93,9 +93,9 @@ def test_sizes_up_to_the_limit(gpu, shape):
         _oracle_check(p.graph, p.log_pot, p.evidence, T, 0.5, 20, nb, dec, f"ising{r}x{c} T={T}")
 
 
-@pytest.mark.parametrize("shape", [(91, 91), (65, 128), (1, 8193)])
+@pytest.mark.parametrize("shape", [(129, 128), (1, 16385)])
 def test_above_the_limit_keeps_the_launches(gpu, shape):
-    """8,281, 8,320 and 8,193 variables: above the limit, the multi-launch form."""
+    """16,512 and 16,385 variables: above the limit, the multi-launch form."""
     r, c = shape
     p = W.ising_grid(r, c, seed=3, T=1.0)
     _both(gpu, p.graph, p.log_pot, p.evidence, 1.0, 0.5, 10, expect_small=False)
