@@ -518,10 +518,11 @@ pgm_status pgm_run_bp_until_members(pgm_graph *g, const float *log_pot, const fl
 /*
  * PGM_OPT_SMALL_RUN (default 1): a log-ratio run (PGM_OPT_LOG_RATIO) of a graph whose
  * variables have at most 4 factors each is one kernel launch: one thread block for at most
- * 700 variables (and 2,048 factors), else a cluster of 8 thread blocks on 8 SMs, whose
- * shared memories together hold the run's state, for at most 8,192 variables and 16,384
- * factors (where the device can place such a cluster). 2 takes the cluster at every size
- * up to its limits. The launch converts msgs, runs
+ * 700 variables (and 2,048 factors), else a cluster of C thread blocks on C SMs, whose
+ * shared memories together hold the run's state, for at most 1,024 C variables and 2,048 C
+ * factors: C = 16 where the device places a cluster of 16 such blocks (GB300: up to 16,384
+ * variables), else 8 where it places 8, else no cluster form. 2 takes the cluster at every
+ * size up to its limits. The launch converts msgs, runs
  * every iteration with the exchanged arrays in shared memory (24 bytes per variable) and a
  * block or cluster barrier after each pass, and writes msgs back, instead of 2 launches per
  * iteration plus 3. The arithmetic per variable and per factor is that of the multi-launch
